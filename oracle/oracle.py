@@ -1,0 +1,248 @@
+"""ctypes binding of the CPU oracle (oracle/bolt_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests, by the smoke check and by the
+CPU-baseline leg of bench.py -- never by the product package.  The oracle is a
+plain single-threaded C implementation of the BOLT oblivious map (Alg. 1,
+Sec. 3.1; architecture Sec. 4.1-4.2) that shares no code with the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboracle.so")
+SRC_PATH = os.path.join(HERE, "bolt_oracle.c")
+
+PARAM_ALPHA, PARAM_C, PARAM_NOCRYPT, PARAM_TRACE, PARAM_BATCH = 1, 2, 3, 4, 5
+OK, E_ARG, E_NOMEM, E_OVERFLOW, E_STATE, E_DUPKEY = 0, -1, -2, -3, -4, -5
+GET, PUT, DEL = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so with the system C compiler."""
+    if force or not os.path.exists(LIB_PATH) or (
+            os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC_PATH)):
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
+                               "-o", LIB_PATH, SRC_PATH, "-lm"])
+    return LIB_PATH
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint64), ("B", ctypes.c_uint64), ("K", ctypes.c_uint64),
+                ("M", ctypes.c_uint64), ("rows", ctypes.c_uint64),
+                ("key_bytes", ctypes.c_uint32), ("val_bytes", ctypes.c_uint32),
+                ("c", ctypes.c_uint32), ("d", ctypes.c_uint32), ("lmax", ctypes.c_uint32),
+                ("R", ctypes.c_uint32), ("page_bytes", ctypes.c_uint32),
+                ("rec_bytes", ctypes.c_uint32), ("round_width", ctypes.c_uint64),
+                ("vs_cap", ctypes.c_uint64), ("alpha", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("ops", ctypes.c_uint64), ("n_hbm", ctypes.c_uint64),
+                ("n_stash", ctypes.c_uint64), ("n_host", ctypes.c_uint64),
+                ("peak_stash", ctypes.c_uint64), ("peak_hbm", ctypes.c_uint64),
+                ("max_load", ctypes.c_uint32), ("peak_load", ctypes.c_uint32),
+                ("max_row", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB_PATH)
+        P, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        L.oracle_create.argtypes = [u64, u32, u32, u64, ctypes.POINTER(P)]
+        L.oracle_set_param.argtypes = [P, i32, ctypes.c_double]
+        L.oracle_init.argtypes = [P, P, P, u64, u64]
+        L.oracle_access.argtypes = [P, P, P, P, P, P, u64]
+        L.oracle_destroy.argtypes = [P]
+        L.oracle_destroy.restype = None
+        L.oracle_info.argtypes = [P, ctypes.POINTER(Info)]
+        L.oracle_stats.argtypes = [P, ctypes.POINTER(Stats)]
+        L.oracle_pages.argtypes = [P]
+        L.oracle_pages.restype = P
+        L.oracle_loads.argtypes = [P, P]
+        L.oracle_versions.argtypes = [P, P]
+        L.oracle_rowcounts.argtypes = [P, P]
+        L.oracle_trace_len.argtypes = [P]
+        L.oracle_trace_len.restype = u64
+        L.oracle_trace_copy.argtypes = [P, P, u64]
+        L.oracle_trace_copy.restype = u64
+        L.oracle_trace_clear.argtypes = [P]
+        L.oracle_trace_clear.restype = None
+        L.oracle_decrypt_page.argtypes = [P, u64, P]
+        L.oracle_keys.argtypes = [P, P, P]
+        L.oracle_chacha20_block.argtypes = [P, u32, P, P]
+        L.oracle_chacha20_block.restype = None
+        L.oracle_chacha20_xor.argtypes = [P, u32, P, P, u64]
+        L.oracle_chacha20_xor.restype = None
+        L.oracle_sizing.argtypes = [u64, u32, ctypes.c_double, u32, ctypes.POINTER(Info)]
+        L.oracle_pair.argtypes = [P, u32, u64, u64, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def chacha20_block(key_words, counter, nonce_words) -> np.ndarray:
+    k = np.ascontiguousarray(key_words, dtype=np.uint32)
+    nn = np.ascontiguousarray(nonce_words, dtype=np.uint32)
+    out = np.zeros(16, dtype=np.uint32)
+    lib().oracle_chacha20_block(_ptr(k), counter, _ptr(nn), _ptr(out))
+    return out
+
+
+def chacha20_xor(key_words, counter, nonce_words, data: bytes) -> bytes:
+    k = np.ascontiguousarray(key_words, dtype=np.uint32)
+    nn = np.ascontiguousarray(nonce_words, dtype=np.uint32)
+    buf = np.frombuffer(bytearray(data), dtype=np.uint8).copy()
+    lib().oracle_chacha20_xor(_ptr(k), counter, _ptr(nn), _ptr(buf), len(buf))
+    return buf.tobytes()
+
+
+def sizing(N: int, c: int, alpha: float, val_bytes: int) -> dict:
+    o = Info()
+    rc = lib().oracle_sizing(N, c, alpha, val_bytes, ctypes.byref(o))
+    if rc:
+        raise ValueError(f"oracle_sizing rc={rc}")
+    return o.as_dict()
+
+
+def pair(kprf_words, dom: int, x: int, B: int):
+    k = np.ascontiguousarray(kprf_words, dtype=np.uint32)
+    a, b = ctypes.c_uint32(), ctypes.c_uint32()
+    rc = lib().oracle_pair(_ptr(k), dom, x, B, ctypes.byref(a), ctypes.byref(b))
+    if rc:
+        raise ValueError(rc)
+    return a.value, b.value
+
+
+class OracleError(RuntimeError):
+    def __init__(self, rc, what):
+        super().__init__(f"{what} failed rc={rc}")
+        self.rc = rc
+
+
+class OracleMap:
+    """One oracle map instance (same call shapes as the product C ABI)."""
+
+    def __init__(self, N, val_bytes, hbm_budget=2**64 - 1, key_bytes=8, alpha=None,
+                 c=None, nocrypt=False, trace=True, batch=None):
+        self._h = ctypes.c_void_p()
+        rc = lib().oracle_create(N, key_bytes, val_bytes, hbm_budget, ctypes.byref(self._h))
+        if rc:
+            raise OracleError(rc, "oracle_create")
+        if c is not None:
+            self.set_param(PARAM_C, c)
+        if alpha is not None:
+            self.set_param(PARAM_ALPHA, alpha)
+        if nocrypt:
+            self.set_param(PARAM_NOCRYPT, 1)
+        if not trace:
+            self.set_param(PARAM_TRACE, 0)
+        if batch is not None:
+            self.set_param(PARAM_BATCH, batch)
+        self.vb = val_bytes
+
+    def set_param(self, which, v):
+        rc = lib().oracle_set_param(self._h, which, float(v))
+        if rc:
+            raise OracleError(rc, "oracle_set_param")
+
+    def close(self):
+        if self._h:
+            lib().oracle_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, keys: np.ndarray, vals: np.ndarray, seed: int) -> int:
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        vals = np.ascontiguousarray(vals, dtype=np.uint8)
+        return lib().oracle_init(self._h, _ptr(keys), _ptr(vals), len(keys), seed)
+
+    def access(self, ops, keys, vals_in):
+        ops = np.ascontiguousarray(ops, dtype=np.uint8)
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        vin = np.ascontiguousarray(vals_in, dtype=np.uint8)
+        n = len(ops)
+        vout = np.zeros((n, self.vb), dtype=np.uint8)
+        status = np.zeros(n, dtype=np.uint8)
+        rc = lib().oracle_access(self._h, _ptr(ops), _ptr(keys), _ptr(vin), _ptr(vout),
+                                 _ptr(status), n)
+        return rc, vout, status
+
+    def info(self) -> dict:
+        o = Info()
+        lib().oracle_info(self._h, ctypes.byref(o))
+        return o.as_dict()
+
+    def stats(self) -> dict:
+        s = Stats()
+        lib().oracle_stats(self._h, ctypes.byref(s))
+        return s.as_dict()
+
+    def pages(self) -> np.ndarray:
+        i = self.info()
+        size = i["M"] * i["page_bytes"]
+        addr = lib().oracle_pages(self._h)
+        buf = (ctypes.c_uint8 * size).from_address(addr)
+        return np.frombuffer(buf, dtype=np.uint8).copy().reshape(i["M"], i["page_bytes"])
+
+    def loads(self) -> np.ndarray:
+        out = np.zeros(self.info()["B"], dtype=np.uint8)
+        lib().oracle_loads(self._h, _ptr(out))
+        return out
+
+    def versions(self) -> np.ndarray:
+        out = np.zeros(self.info()["M"], dtype=np.uint64)
+        lib().oracle_versions(self._h, _ptr(out))
+        return out
+
+    def rowcounts(self) -> np.ndarray:
+        out = np.zeros(self.info()["rows"], dtype=np.uint32)
+        lib().oracle_rowcounts(self._h, _ptr(out))
+        return out
+
+    def trace(self, clear=True) -> np.ndarray:
+        n = lib().oracle_trace_len(self._h)
+        out = np.zeros(n, dtype=np.uint32)
+        lib().oracle_trace_copy(self._h, _ptr(out), n)
+        if clear:
+            lib().oracle_trace_clear(self._h)
+        return out
+
+    def decrypt_page(self, q) -> np.ndarray:
+        out = np.zeros(self.info()["page_bytes"], dtype=np.uint8)
+        rc = lib().oracle_decrypt_page(self._h, q, _ptr(out))
+        if rc:
+            raise OracleError(rc, "oracle_decrypt_page")
+        return out
+
+    def keys(self):
+        a = np.zeros(8, dtype=np.uint32)
+        b = np.zeros(8, dtype=np.uint32)
+        rc = lib().oracle_keys(self._h, _ptr(a), _ptr(b))
+        if rc:
+            raise OracleError(rc, "oracle_keys")
+        return a, b

@@ -1,0 +1,422 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each test ties the oracle to something other than itself: an independent
+ChaCha20 implementation, the numbers the paper prints (slack table, HBM-usage
+example, validation-experiment maxima), a plain dict, brute-force recounts of
+the data-structure invariants, and exact predictions of the host trace from
+the PRF definition.  None of them needs a GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_01742_b300 import workload as W
+from tests.dict_model import DictModel
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+DOM_INIT, DOM_PM, DOM_REMAP, DOM_DUMMY = 1, 2, 3, 4
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def decode_page(plain, info):
+    """Page format: u64 bitmap, u64 zero, lmax slots of (u64 key, value)."""
+    vb, rec = info["val_bytes"], info["rec_bytes"]
+    bitmap = int(np.frombuffer(plain[:8].tobytes(), dtype=np.uint64)[0])
+    header2 = int(np.frombuffer(plain[8:16].tobytes(), dtype=np.uint64)[0])
+    cnt = 0
+    while cnt < 64 and (bitmap >> cnt) & 1:
+        cnt += 1
+    assert bitmap == (1 << cnt) - 1, "occupied slots must be a prefix"
+    assert header2 == 0
+    assert cnt <= info["lmax"]
+    keys, vals = [], []
+    for s in range(cnt):
+        off = 16 + s * rec
+        keys.append(int(np.frombuffer(plain[off:off + 8].tobytes(), dtype=np.uint64)[0]))
+        vals.append(plain[off + 8:off + 8 + vb].tobytes())
+    assert keys == sorted(keys), "reals are stored in ascending key order"
+    assert not plain[16 + cnt * rec:].any(), "dummy slots and padding are zero"
+    return keys, vals
+
+
+def check_invariants(m: O.OracleMap, model: DictModel):
+    """Every live key is in exactly one place with its current value; loads
+    equal recounted occupancies (Sec. 3.1 bins; Sec. 4.2 storage)."""
+    info, st = m.info(), m.stats()
+    loads = m.loads().astype(np.int64)
+    K, M = info["K"], info["M"]
+    page_keys = {}
+    host_total = 0
+    stash_by_page = 0
+    for q in range(M):
+        keys, vals = decode_page(m.decrypt_page(q), info)
+        host_total += len(keys)
+        assert loads[K + q] >= len(keys)
+        stash_by_page += loads[K + q] - len(keys)
+        for k, v in zip(keys, vals):
+            assert k not in page_keys
+            page_keys[k] = v
+            assert model.d[k] == v
+    assert host_total == st["n_host"]
+    assert stash_by_page == st["n_stash"]
+    assert loads[:K].sum() == st["n_hbm"]
+    assert loads.sum() == len(model.d)
+    assert st["n_hbm"] + st["n_stash"] + st["n_host"] == len(model.d)
+    assert loads.max() <= info["lmax"]
+
+
+# --------------------------------------------------------------------------
+# ChaCha20 against an independent implementation
+
+
+def test_chacha20_matches_cryptography():
+    from cryptography.hazmat.primitives.ciphers import Cipher, algorithms
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        key = rng.integers(0, 256, 32, dtype=np.uint8).tobytes()
+        nonce = rng.integers(0, 256, 12, dtype=np.uint8).tobytes()
+        counter = int(rng.integers(0, 2**31))
+        length = int(rng.integers(1, 300))
+        enc = Cipher(algorithms.ChaCha20(key, counter.to_bytes(4, "little") + nonce),
+                     mode=None).encryptor()
+        expect = enc.update(bytes(length))
+        got = O.chacha20_xor(np.frombuffer(key, dtype=np.uint32), counter,
+                             np.frombuffer(nonce, dtype=np.uint32), bytes(length))
+        assert got == expect
+
+
+def test_chacha20_block_is_keystream():
+    key = np.arange(8, dtype=np.uint32) * 0x01010101
+    nonce = np.array([9, 0x4a, 0], dtype=np.uint32)
+    blk = O.chacha20_block(key, 1, nonce)
+    ks = O.chacha20_xor(key, 1, nonce, bytes(64))
+    assert np.frombuffer(ks, dtype=np.uint32).tolist() == blk.tolist()
+
+
+# --------------------------------------------------------------------------
+# Sizing against the paper's printed numbers
+
+
+def test_lmax_pins_slack_table():
+    # Fig. 5 table: bin-load slack 2 at rel .143 (c=8) and .091 (c=16) => the
+    # analytical bin-load bounds at N=2^20 are 14 and 22.
+    for row in _golden("slack_table.txt"):
+        if row[0] != "binload":
+            continue
+        c, abs_slack, rel = int(row[1]), int(row[3]), float(row[4])
+        lmax = O.sizing(1 << 20, c, float(row[2]), 8)["lmax"]
+        assert round(abs_slack / lmax, 3) == rel
+
+
+def test_bound_pins_slack_table():
+    # Claim 3.3 (HBM sum) and Claim 3.4 (stash) bounds at N=2^20 reproduce the
+    # printed relative slacks slack/bound.
+    for row in _golden("slack_table.txt"):
+        metric, c, alpha, abs_slack, rel = row[0], int(row[1]), float(row[2]), \
+            int(row[3]), float(row[4])
+        if metric == "binload":
+            continue
+        s = O.sizing(1 << 20, c, alpha, 8)
+        bound = s["beta1"] if metric == "hbm" else s["beta2"]
+        digits = len(row[4].split(".")[1])
+        tol = 0.5 * 10 ** -digits + 1e-9 if metric == "hbm" else 0.0075
+        assert abs(abs_slack / bound - rel) <= tol, (row, bound, abs_slack / bound)
+
+
+def test_hbm_usage_example_claim_5_2():
+    # Claim 5.2 applied to the paper's example: 1e9 records, 32-bit keys, c=8,
+    # position map of N/16 rows with d=4, no HBM store (alpha = 0).
+    N = 10**9
+    for row in _golden("hbm_usage.txt"):
+        vbytes, percent = int(row[0]), float(row[1])
+        s = O.sizing(N, 8, 0.0, 8)
+        vs_bits = vbytes * 8
+        ks = 32
+        rows = N / 16
+        pm_bits = (2 * math.log2(N) + ks) * (N + rows * math.log2(math.log2(N)) / math.log2(4))
+        total_bits = (s["beta1"] + s["beta2"]) * vs_bits + pm_bits
+        raw_bits = N * (ks + vs_bits)
+        assert abs(100.0 * total_bits / raw_bits - percent) <= 1.0, (vbytes, total_bits / raw_bits)
+
+
+def test_alpha_policy_and_derived_sizes():
+    # config sizes (N, val_bytes, budget) -> alpha on the grid {.2,.1,.05,.01,0}
+    m = O.OracleMap(1 << 16, 8)
+    i = m.info()
+    assert (i["B"], i["K"], i["M"], i["lmax"], i["R"], i["page_bytes"]) == \
+        (8192, 1638, 6554, 13, 18, 256)
+    assert i["alpha"] == 0.2 and i["round_width"] == 32
+    m.close()
+    s = O.sizing(1 << 28, 8, 0.2, 24)
+    assert (s["lmax"], s["R"], s["page_bytes"], s["B"]) == (14, 19, 512, 1 << 25)
+    # a budget that only fits alpha = 0.01
+    need = {a: O.sizing(1 << 16, 8, a, 8)["vs_cap"] * 16 for a in (0.2, 0.1, 0.05, 0.01)}
+    m = O.OracleMap(1 << 16, 8, hbm_budget=need[0.01])
+    assert m.info()["alpha"] == 0.01
+    m.close()
+    with pytest.raises(O.OracleError):
+        O.OracleMap(1 << 16, 8, hbm_budget=1000)
+
+
+# --------------------------------------------------------------------------
+# The paper's validation experiment (Sec. 3.3 "Dimensions in practice")
+
+
+@pytest.mark.parametrize("alpha", [0.01, 0.2])
+def test_dimensional_validation(alpha):
+    """N=2^20, c=8, one operation per batch (Alg. 1), uniform random accesses:
+    peak bin load, HBM load and stash land on the paper's empirical maxima
+    (analytical bound minus printed slack), measured here over 10^6 accesses
+    instead of 10^9."""
+    N = 1 << 20
+    m = O.OracleMap(N, 8, alpha=alpha, nocrypt=True, trace=False, batch=1)
+    keys, vals = W.records(N, 8, 1)
+    assert m.init(keys, vals, 7) == 0
+    info = m.info()
+    stash = []
+    for rep in range(4):
+        ops, k, vin = W.op_stream(N, 250000, 8, 100 + rep)
+        rc, _, _ = m.access(ops, k, vin)
+        assert rc == 0
+        stash.append(m.stats()["n_stash"])
+    st = m.stats()
+    table = {(r[0], float(r[2])): int(r[3]) for r in _golden("slack_table.txt") if r[1] == "8"}
+    emp_hbm = info["beta1"] - table[("hbm", alpha)]
+    emp_stash = info["beta2"] - table[("stash", alpha)]
+    emp_load = info["lmax"] - table[("binload", alpha)]
+    assert st["peak_load"] == emp_load
+    assert abs(st["peak_hbm"] / emp_hbm - 1) < 0.03, (st, emp_hbm)
+    assert -0.03 < st["peak_stash"] / emp_stash - 1 < 0.01, (st, emp_stash)
+    if alpha == 0.01:
+        # drift equilibrium x* = (1+alpha) M / 2 (proof of Claim 3.4)
+        xstar = (1 + alpha) * info["M"] / 2
+        assert abs(np.mean(stash[1:]) / xstar - 1) < 0.02
+    m.close()
+
+
+# --------------------------------------------------------------------------
+# Results against the plain dictionary, invariants by brute force
+
+
+@pytest.mark.parametrize("batch", [1, 7, 4096])
+def test_results_match_dict(batch):
+    N = 1 << 12
+    n0 = 3000
+    keys, vals = W.records(n0, 8, 3)
+    m = O.OracleMap(N, 8, batch=batch)
+    assert m.init(keys, vals, 11) == 0
+    model = DictModel(keys, vals)
+    for rep in range(3):
+        ops, k, vin = W.op_stream(n0, 2000, 8, 50 + rep, get_frac=0.5, del_frac=0.1,
+                                  absent_frac=0.15)
+        # heavy duplicates inside a batch
+        k[::5] = k[0]
+        rc, vout, status = m.access(ops, k, vin)
+        assert rc == 0
+        evout, estatus = model.apply(ops, k, vin, 8)
+        assert np.array_equal(status, estatus)
+        assert np.array_equal(vout, evout)
+        check_invariants(m, model)
+    m.close()
+
+
+def test_brute_force_tiny_every_op():
+    N = 64
+    keys, vals = W.records(40, 16, 5)
+    m = O.OracleMap(N, 16, batch=1, alpha=0.25)
+    assert m.init(keys, vals, 3) == 0
+    model = DictModel(keys, vals)
+    check_invariants(m, model)
+    rng = np.random.default_rng(9)
+    for step in range(300):
+        ops, k, vin = W.op_stream(40, 1, 16, 1000 + step, get_frac=0.4, del_frac=0.2,
+                                  absent_frac=0.3)
+        rc, vout, status = m.access(ops, k, vin)
+        if rc == O.E_OVERFLOW:  # tiny maps may legitimately overflow
+            break
+        assert rc == 0
+        evout, estatus = model.apply(ops, k, vin, 16)
+        assert np.array_equal(vout, evout) and np.array_equal(status, estatus)
+        check_invariants(m, model)
+    assert step > 50
+    m.close()
+
+
+def test_init_layout_brute_force():
+    """After init every record sits in the bin P2C gives it (round-synchronous
+    rounds of W_r records on round-start loads, first choice on ties)."""
+    N = 1 << 12
+    keys, vals = W.records(N, 8, 21)
+    m = O.OracleMap(N, 8)
+    assert m.init(keys, vals, 5) == 0
+    info = m.info()
+    kprf, _ = m.keys()
+    B, K, Wr = info["B"], info["K"], info["round_width"]
+    load = np.zeros(B, dtype=np.int64)
+    dest = np.zeros(N, dtype=np.int64)
+    for lo in range(0, N, Wr):
+        idx = range(lo, min(N, lo + Wr))
+        pairs = [O.pair(kprf, DOM_INIT, i, B) for i in idx]
+        d = [a if load[a] <= load[b] else b for a, b in pairs]
+        for i, b in zip(idx, d):
+            dest[i] = b
+        for b in d:
+            load[b] += 1
+    assert np.array_equal(load, m.loads().astype(np.int64))
+    for q in range(info["M"]):
+        pk, pv = decode_page(m.decrypt_page(q), info)
+        expect = sorted(int(keys[i]) for i in np.nonzero(dest == K + q)[0])
+        assert pk == expect
+    m.close()
+
+
+# --------------------------------------------------------------------------
+# Host-access trace (obliviousness invariants)
+
+
+def _host_bins(pairs, K):
+    out = []
+    for a, b in pairs:
+        for p in (a, b):
+            if p >= K:
+                out.append(p - K)
+    return out
+
+
+def _expected_trace(reads):
+    seen, writes = set(), []
+    for q in reads:
+        if q not in seen:
+            seen.add(q)
+            writes.append(q | 0x80000000)
+    return np.array(reads + writes, dtype=np.uint32)
+
+
+def test_trace_predicted_from_prf():
+    """First batch after init: leaders of distinct existing keys read the
+    bins of their init pair, misses and duplicates the DUMMY pair of their
+    global sequence number; each distinct page is then written once in
+    first-read order (Alg. 1 lines 5-10, simulator of Sec. 3.2)."""
+    N = 1 << 12
+    keys, vals = W.records(N, 8, 4)
+    m = O.OracleMap(N, 8)
+    assert m.init(keys, vals, 77) == 0
+    info = m.info()
+    kprf, _ = m.keys()
+    B, K = info["B"], info["K"]
+    rng = np.random.default_rng(0)
+    idx = rng.choice(N, 300, replace=False)
+    k = keys[idx].copy()
+    k[10:20] = W.key_of(np.arange(N + 5, N + 15))  # absent
+    k[30] = k[29]  # duplicate
+    ops = np.zeros(300, dtype=np.uint8)
+    vin = np.zeros((300, 8), dtype=np.uint8)
+    m.trace()
+    rc, _, _ = m.access(ops, k, vin)
+    assert rc == 0
+    pairs = []
+    for i in range(300):
+        if 10 <= i < 20 or i == 30:
+            pairs.append(O.pair(kprf, DOM_DUMMY, i, B))
+        else:
+            pairs.append(O.pair(kprf, DOM_INIT, int(idx[i]), B))
+    assert np.array_equal(m.trace(), _expected_trace(_host_bins(pairs, K)))
+    # second batch: the same keys were remapped with REMAP pairs at t = their index
+    rc, _, _ = m.access(ops[:5], k[:5], vin[:5])
+    pairs2 = [O.pair(kprf, DOM_REMAP, i, B) for i in range(5)]
+    assert np.array_equal(m.trace(), _expected_trace(_host_bins(pairs2, K)))
+    m.close()
+
+
+def test_trace_independent_of_ops_and_payloads():
+    """O4: at a fixed state, opcodes and payloads leave no trace footprint."""
+    N = 1 << 12
+    keys, vals = W.records(N, 8, 4)
+    traces = []
+    for variant in range(3):
+        m = O.OracleMap(N, 8)
+        assert m.init(keys, vals, 5) == 0
+        ops, k, vin = W.op_stream(N, 1000, 8, 8, absent_frac=0.2)
+        if variant == 1:
+            ops = (ops + 1) % 3
+        if variant == 2:
+            vin = 255 - vin
+        m.trace()
+        rc, _, _ = m.access(ops, k, vin)
+        assert rc == 0
+        traces.append(m.trace())
+        m.close()
+    assert np.array_equal(traces[0], traces[1]) and np.array_equal(traces[0], traces[2])
+
+
+def test_pair_uniformity_chi2():
+    """The pair map is uniform over ordered pairs of distinct bins (Sec. 3.2)."""
+    from scipy.stats import chisquare
+    kprf = np.arange(8, dtype=np.uint32) + 17
+    B = 7
+    counts = np.zeros((B, B), dtype=np.int64)
+    for x in range(42 * 400):
+        a, b = O.pair(kprf, DOM_REMAP, x, B)
+        assert a != b and a < B and b < B
+        counts[a, b] += 1
+    obs = counts[~np.eye(B, dtype=bool)]
+    assert chisquare(obs).pvalue > 1e-3
+
+
+def test_repeated_key_trace_uniform():
+    """O3: hammering one key gives a stream of fresh uniform pairs; with
+    alpha = 0 every bin is a host page so the trace shows whole pairs."""
+    from scipy.stats import chisquare
+    m = O.OracleMap(64, 8, alpha=0.0, batch=1)
+    keys, vals = W.records(40, 8, 2)
+    assert m.init(keys, vals, 1) == 0
+    B = m.info()["B"]
+    n = 56 * 150
+    ops = np.zeros(n, dtype=np.uint8)
+    k = np.full(n, keys[3], dtype=np.uint64)
+    rc, _, _ = m.access(ops, k, np.zeros((n, 8), dtype=np.uint8))
+    assert rc == 0
+    tr = m.trace()
+    reads = tr[(tr >> 31) == 0].reshape(-1, 2)
+    assert len(reads) == n
+    counts = np.zeros((B, B), dtype=np.int64)
+    for a, b in reads:
+        counts[a, b] += 1
+    assert chisquare(counts[~np.eye(B, dtype=bool)]).pvalue > 1e-3
+    m.close()
+
+
+# --------------------------------------------------------------------------
+# Error paths
+
+
+def test_dupkey_and_overflow_poison():
+    m = O.OracleMap(64, 8)
+    k = np.array([5, 6, 5], dtype=np.uint64)
+    assert m.init(k, np.zeros((3, 8), np.uint8), 1) == O.E_DUPKEY
+    keys, vals = W.records(60, 8, 1)
+    assert m.init(keys, vals, 1) == 0
+    # insert far more keys than the capacity: some bin or row must overflow
+    newk = W.key_of(np.arange(1000, 1400))
+    rc = 0
+    for lo in range(0, 400, 50):
+        rc, _, _ = m.access(np.ones(50, np.uint8), newk[lo:lo + 50], np.ones((50, 8), np.uint8))
+        if rc:
+            break
+    assert rc == O.E_OVERFLOW
+    rc2, _, _ = m.access(np.zeros(1, np.uint8), keys[:1], np.zeros((1, 8), np.uint8))
+    assert rc2 == O.E_STATE
+    assert m.init(keys, vals, 2) == 0  # re-init clears the poison
+    m.close()
