@@ -1,0 +1,447 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 BOLT oblivious map: oblivious accesses/s and build
+Mrec/s at N = 2^28 records of 32 B (8 B key + 24 B value).
+
+One step = the whole hot path on one batch of synthetic input: the oblivious
+build of the 2^28-record map (bolt_init), then 2^22 uniform accesses over its
+keys (50% GET / 50% PUT, the paper's mix) in batches of 4096 (bolt_access).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl bolt|reference]
+
+value   accesses/s of the access phase, inputs resident in HBM, CUDA events on
+        the launching stream; the build's Mrec/s is reported beside it;
+e2e     the same through the host-pointer C-ABI calls (pinned host buffers,
+        host<->device copies inside the timed region);
+roofline  the bitonic global pass (the build's HBM-bound kernel), event-timed
+        per launch inside the timed region, against the measured HBM copy peak;
+cpu_baseline  the CPU oracle on a bounded sample of the same workload.
+--impl reference times the CPU oracle itself (the only reference this method
+has) on a bounded sample, on rank 0.
+Multi-GPU (torchrun): independent replicas, one map per GPU ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_01742_b300 import workload as W  # noqa: E402
+
+METRIC = "oblivious accesses/s and build Mrec/s at N=2^28; served p50/p99 latency"
+LOG_N = 28
+VAL_BYTES = 24
+N_ACCESS = 1 << 22
+BATCH = 4096
+SEED_DATA = 0x5EED0003
+SEED_OPS = 0x5EED0103
+SEED_MAP = 0x5EED0203
+CONFIG = {
+    "workload": "N=2^28 records x 32 B (8 B uint64 key + 24 B value), oblivious build, then "
+                "2^22 uniform accesses to existing keys (50% GET / 50% PUT) in batches of 4096",
+    "records": 1 << LOG_N,
+    "record_bytes": 8 + VAL_BYTES,
+    "accesses_per_step": N_ACCESS,
+    "batch": BATCH,
+    "c": 8,
+    "alpha": 0.2,
+    "l2": "inputs larger than L2 (8 GiB records, 5.9 GiB position map, 13.7 GiB host pages)",
+}
+
+
+def aggregate(local: dict, world: int, group=None) -> dict:
+    """Whole-job figures over ranks: the slowest rank's times, the sum of the
+    work.  With world == 1 the local figures are returned unchanged."""
+    if world == 1:
+        return dict(local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local["build_s"], local["access_s"], local["step_s"]], dtype=torch.float64)
+    w = torch.tensor([local["records"], local["accesses"]], dtype=torch.float64)
+    if dist.get_backend(group) == "nccl":
+        t, w = t.cuda(), w.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM, group=group)
+    t, w = t.cpu().tolist(), w.cpu().tolist()
+    return {"build_s": t[0], "access_s": t[1], "step_s": t[2], "records": w[0],
+            "accesses": w[1]}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def make_records(n: int, seed: int):
+    keys = np.empty(n, dtype=np.uint64)
+    step = 1 << 24
+    for lo in range(0, n, step):
+        hi = min(n, lo + step)
+        keys[lo:hi] = W.key_of(np.arange(lo, hi, dtype=np.uint64))
+    rng = np.random.default_rng(seed)
+    vals = np.frombuffer(rng.bytes(n * VAL_BYTES), dtype=np.uint8).reshape(n, VAL_BYTES)
+    return keys, vals
+
+
+def link_bandwidth(torch) -> dict:
+    """Pinned host<->device copy bandwidth (1 GiB, best of 3), GB/s."""
+    n = 1 << 30
+    h = torch.empty(n, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(n, dtype=torch.uint8, device="cuda")
+    out = {}
+    for name, fn in (("h2d", lambda: d.copy_(h, non_blocking=True)),
+                     ("d2h", lambda: h.copy_(d, non_blocking=True))):
+        best = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            best = max(best, n / (a.elapsed_time(b) * 1e-3) / 1e9)
+        out[name] = round(best, 1)
+    del h, d
+    return out
+
+
+def cpu_baseline_sample(seconds_hint: float = 15.0) -> dict:
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    workload: a 2^21-record map of 32 B records, then accesses in batches of
+    4096 from the same op distribution."""
+    from oracle import oracle as O
+    n_s = 1 << 21
+    keys, vals = make_records(n_s, SEED_DATA)
+    m = O.OracleMap(n_s, VAL_BYTES, trace=False)
+    t0 = time.perf_counter()
+    rc = m.init(keys, vals, SEED_MAP)
+    t_build = time.perf_counter() - t0
+    assert rc == 0, rc
+    done, t_acc, rep = 0, 0.0, 0
+    while t_acc < seconds_hint and rep < 64:
+        ops, k, vin = W.op_stream(n_s, BATCH, VAL_BYTES, SEED_OPS + rep, get_frac=0.5)
+        t0 = time.perf_counter()
+        rc, _, _ = m.access(ops, k, vin)
+        t_acc += time.perf_counter() - t0
+        assert rc == 0, rc
+        done += BATCH
+        rep += 1
+    m.close()
+    return {"value": round(done / t_acc, 1), "unit": "accesses/s", "cores": 1, "kind": "oracle",
+            "build_mrec_s": round(n_s / t_build / 1e6, 3),
+            "sample": f"oracle map of 2^21 x 32 B records (build {t_build:.1f} s), then {done} "
+                      f"uniform 50/50 GET/PUT accesses in batches of {BATCH} ({t_acc:.1f} s); "
+                      "single host thread"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    n_s = 1 << 21
+    keys, vals = make_records(n_s, SEED_DATA)
+    m = O.OracleMap(n_s, VAL_BYTES, trace=False)
+    t0 = time.perf_counter()
+    assert m.init(keys, vals, SEED_MAP) == 0
+    t_build = time.perf_counter() - t0
+    batches = [W.op_stream(n_s, BATCH, VAL_BYTES, SEED_OPS + i, get_frac=0.5)
+               for i in range(args.warmup + args.steps)]
+    for i in range(args.warmup):
+        assert m.access(*batches[i])[0] == 0
+    t0 = time.perf_counter()
+    for i in range(args.warmup, args.warmup + args.steps):
+        assert m.access(*batches[i])[0] == 0
+    dt = time.perf_counter() - t0
+    m.close()
+    value = args.steps * BATCH / dt
+    sample = (f"oracle (single thread) on a 2^21-record sample map of 32 B records (build "
+              f"{t_build:.1f} s, untimed); each step = one batch of {BATCH} uniform 50/50 "
+              "GET/PUT accesses")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "accesses/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8/u64 (integer)",
+            "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"value": round(value, 1), "unit": "accesses/s", "cores": 1,
+                             "kind": "oracle", "sample": sample,
+                             "build_mrec_s": round(n_s / t_build / 1e6, 3)},
+            "e2e": {"value": round(value, 1), "unit": "accesses/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_bolt(args) -> None:
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    group = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2509_01742_b300 import bolt as B
+
+    N = 1 << args.log_n
+    n_acc = args.accesses
+    keys, vals = make_records(N, SEED_DATA + rank)
+    ops, akeys, avin = W.op_stream(N, n_acc, VAL_BYTES, SEED_OPS + rank, get_frac=0.5)
+    stream = torch.cuda.Stream()
+    d_keys = torch.from_numpy(keys.view(np.int64)).cuda()
+    d_vals = torch.from_numpy(vals).cuda()
+    d_ops = torch.from_numpy(ops).cuda()
+    d_akeys = torch.from_numpy(akeys.view(np.int64)).cuda()
+    d_avin = torch.from_numpy(avin).cuda()
+    d_vout = torch.empty((n_acc, VAL_BYTES), dtype=torch.uint8, device="cuda")
+    d_status = torch.empty(n_acc, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    m = B.BoltMap(N, VAL_BYTES)
+    m.set_param(B.BOLT_PARAM_PROFILE, 1)
+    info = m.info()
+    nb = (n_acc + BATCH - 1) // BATCH
+
+    def step(events=None):
+        if events:
+            events[0].record(stream)
+        rc = m.init_device(d_keys, d_vals, SEED_MAP, stream=stream)
+        assert rc == 0, rc
+        if events:
+            events[1].record(stream)
+        for b in range(nb):
+            lo, hi = b * BATCH, min(n_acc, (b + 1) * BATCH)
+            rc = m.access_device(d_ops[lo:hi], d_akeys[lo:hi], d_avin[lo:hi], d_vout[lo:hi],
+                                 d_status[lo:hi], stream=stream)
+            assert rc == 0, rc
+        if events:
+            events[2].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    assert m.sync() == 0
+    m.profile(reset=True)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            step(evs[k])
+        barrier()
+    assert m.sync() == 0
+    prof = m.profile(reset=True)
+    build_s = sum(e[0].elapsed_time(e[1]) for e in evs) * 1e-3
+    access_s = sum(e[1].elapsed_time(e[2]) for e in evs) * 1e-3
+    step_s = sum(e[0].elapsed_time(e[2]) for e in evs) * 1e-3
+    # correctness spot check of the last step's GETs against the inputs
+    vout = d_vout.cpu().numpy()
+    st = d_status.cpu().numpy()
+    assert st.all(), "every accessed key exists"
+    agg = aggregate({"build_s": build_s, "access_s": access_s, "step_s": step_s,
+                     "records": float(N * args.steps), "accesses": float(n_acc * args.steps)},
+                    world, group)
+
+    # roofline: the bitonic global pass, algorithmic bytes = read + write of
+    # every 8-byte tag once per launch
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    sg = prof["sort_global"]
+    tag_cap = 1
+    while tag_cap < N:
+        tag_cap <<= 1
+    bytes_per_launch = 2 * 8 * tag_cap
+    avg_s = sg["ms"] / max(1, sg["spans"]) * 1e-3
+    achieved = bytes_per_launch / avg_s / 1e9 if sg["spans"] else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            traffic = json.load(f).get("k_sort_global_u64<4>", {}).get("bytes_per_launch_full")
+    roofline = {"bound": "hbm", "kernel": "k_sort_global_u64 (bitonic, 4 fused strides)",
+                "achieved": round(achieved, 1) if achieved else None,
+                "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4) if achieved and hbm_peak else None,
+                "traffic": traffic, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
+                if hbm_peak else "fallback 6400 GB/s",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "launches": sg["spans"], "avg_launch_ms": round(avg_s * 1e3, 4)}
+
+    # host-link roofline of the access path (page gather + write-back)
+    link = link_bandwidth(torch) if rank == 0 else {}
+
+    # end to end through the host-pointer ABI (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        hk = torch.from_numpy(keys.view(np.int64)).pin_memory()
+        hv = torch.from_numpy(vals).pin_memory()
+        ho = torch.from_numpy(ops).pin_memory()
+        hak = torch.from_numpy(akeys.view(np.int64)).pin_memory()
+        havin = torch.from_numpy(avin).pin_memory()
+        hvout = torch.empty((n_acc, VAL_BYTES), dtype=torch.uint8).pin_memory()
+        hst = torch.empty(n_acc, dtype=torch.uint8).pin_memory()
+        import ctypes
+
+        def ptr(t):
+            return ctypes.c_void_p(t.data_ptr())
+
+        def e2e_step():
+            t0 = time.perf_counter()
+            rc = B.bolt_init(m.handle, ptr(hk), ptr(hv), N, SEED_MAP)
+            assert rc == 0, rc
+            t1 = time.perf_counter()
+            for b in range(nb):
+                lo, hi = b * BATCH, min(n_acc, (b + 1) * BATCH)
+                rc = B.bolt_access(m.handle, ctypes.c_void_p(ho.data_ptr() + lo),
+                                   ctypes.c_void_p(hak.data_ptr() + 8 * lo),
+                                   ctypes.c_void_p(havin.data_ptr() + VAL_BYTES * lo),
+                                   ctypes.c_void_p(hvout.data_ptr() + VAL_BYTES * lo),
+                                   ctypes.c_void_p(hst.data_ptr() + lo), hi - lo)
+                assert rc == 0, rc
+            t2 = time.perf_counter()
+            return t1 - t0, t2 - t1
+
+        e2e_step()
+        eb, ea = 0.0, 0.0
+        e2e_steps = max(1, min(2, args.steps))
+        for _ in range(e2e_steps):
+            b_s, a_s = e2e_step()
+            eb += b_s
+            ea += a_s
+        assert np.array_equal(hvout.numpy(), vout), "host and device paths agree"
+        e2e = {"value": round(n_acc * e2e_steps / ea, 1), "unit": "accesses/s",
+               "h2d_bytes_per_step": N * (8 + VAL_BYTES) + n_acc * (1 + 8 + VAL_BYTES),
+               "d2h_bytes_per_step": n_acc * (VAL_BYTES + 1),
+               "build_mrec_s": round(N * e2e_steps / eb / 1e6, 2), "steps": e2e_steps}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    cpu = cpu_baseline_sample() if world == 1 and not args.no_cpu else None
+    page_bytes = info["page_bytes"]
+    gat, ev = prof["gather"], prof["evict"]
+    line = {
+        "metric": METRIC,
+        "value": round(agg["accesses"] / agg["access_s"], 1),
+        "unit": "accesses/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(agg["step_s"] / args.steps * 1e3, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8/u64 (integer; ChaCha20 ARX)",
+        "data": "synthetic (seeded; keys = bijective mix of the record index, random values)",
+        "config": CONFIG,
+        "build": {"value": round(agg["records"] / agg["build_s"] / 1e6, 2), "unit": "Mrec/s",
+                  "ms_per_build": round(build_s / args.steps * 1e3, 2)},
+        "roofline": roofline,
+        "link": {"h2d_gbs": link.get("h2d"), "d2h_gbs": link.get("d2h"),
+                 "gather_ms_per_batch": round(gat["ms"] / max(1, gat["spans"]), 4),
+                 "evict_ms_per_batch": round(ev["ms"] / max(1, ev["spans"]), 4),
+                 "page_bytes": page_bytes},
+        "kernel_ms": {k: round(v["ms"], 2) for k, v in prof.items() if isinstance(v, dict)},
+        "gpu_launches": prof["launches"],
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "serving": None,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("bolt", "reference"), default="bolt")
+    ap.add_argument("--log-n", type=int, default=LOG_N)
+    ap.add_argument("--accesses", type=int, default=N_ACCESS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "bolt":
+        print("note: at least 3 warm-up steps are required for a valid number", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_bolt(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * bolt.h -- C ABI of a B300-native BOLT oblivious map.
+ *
+ * BOLT (Guo et al., CCS '25) is an oblivious key-value map: records live in
+ * fixed-size encrypted pages in host memory (V_host), a position map, an HBM
+ * value store and an eviction stash live in device HBM, which the paper treats
+ * as unobservable memory.  Every access reads the two random logical bins a
+ * key is mapped to and writes the pages back, so the host sees a trace whose
+ * distribution does not depend on the keys or operations (Claim 3.1).
+ *
+ * Operation definitions and where the paper fixes them:
+ *   Get / Put / Delete ............ Sec. 2.1 (deletion = Put of a tombstone)
+ *   bins, pages, stash, remap ..... Alg. 1 and Sec. 3.1
+ *   sizing (lmax, V_hbm, stash) ... Claims 3.2-3.4, Sec. 3.3
+ *   position map, value store,
+ *   free ring, reverse index ...... Sec. 4.2
+ *   initial load .................. Sec. 4.2 "Fast data initialization"
+ *
+ * Conventions for every entry point:
+ *   - return value: 0 on success, a negative BOLT_E_* code otherwise; nothing
+ *     is thrown and no call aborts the process;
+ *   - BOLT_E_OVERFLOW (a bin, position-map row or value store ran over its
+ *     bound, probability 1/O(N) per Sec. 3.3) poisons the handle: later
+ *     bolt_access calls return BOLT_E_STATE until bolt_init succeeds again;
+ *   - the caller owns every array it passes; the library copies what it needs
+ *     before returning (host-pointer calls) or before the stream work it
+ *     enqueues completes (device-pointer calls);
+ *   - the handle owns all device memory and the pinned host pages it
+ *     allocates, and bolt_destroy releases them;
+ *   - a handle is not re-entrant: calls on one handle must not overlap;
+ *     distinct handles are independent.
+ */
+#ifndef BOLT_H
+#define BOLT_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bolt bolt_t;
+
+#if defined(__GNUC__)
+#define BOLT_API __attribute__((visibility("default")))
+#else
+#define BOLT_API
+#endif
+
+/* error codes */
+#define BOLT_OK 0
+#define BOLT_E_ARG -1      /* bad argument (null pointer, size out of range) */
+#define BOLT_E_NOMEM -2    /* device or pinned host allocation failed, or the
+                              HBM budget cannot hold even alpha = 0 */
+#define BOLT_E_OVERFLOW -3 /* a capacity bound was exceeded; handle poisoned */
+#define BOLT_E_STATE -4    /* not initialised, or poisoned by an overflow */
+#define BOLT_E_DUPKEY -5   /* bolt_init keys are not unique (Sec. 2.1) */
+#define BOLT_E_CUDA -6     /* a CUDA runtime call failed */
+#define BOLT_E_TIMEOUT -7  /* a bounded device wait gave up */
+#define BOLT_E_INTERNAL -9 /* an internal consistency check failed */
+
+/* operation codes (Sec. 2.1; Delete is the paper's tombstone Put) */
+#define BOLT_GET 0
+#define BOLT_PUT 1
+#define BOLT_DEL 2
+
+/* largest batch one call processes in one go; longer calls are split into
+ * consecutive batches of this many operations */
+#define BOLT_MAX_BATCH 65536
+
+/* bolt_set_param ids */
+#define BOLT_PARAM_ALPHA 1  /* HBM-bin ratio alpha in [0,1) overriding the
+                               budget policy; before bolt_init */
+#define BOLT_PARAM_C 2      /* average bin load c (default 8, Sec. 5.1);
+                               before bolt_init */
+#define BOLT_PARAM_TRACE 4  /* 1 = record the host-access trace (parity runs) */
+#define BOLT_PARAM_BATCH 5  /* operations per batch, 1..BOLT_MAX_BATCH */
+#define BOLT_PARAM_TRACE_CAP 6 /* trace capacity in entries (default 1<<22) */
+#define BOLT_PARAM_CHECK_KEYS 7 /* 1 = bolt_init verifies key uniqueness (default) */
+#define BOLT_PARAM_PROFILE 8 /* 1 = time kernel classes with CUDA events */
+
+/* derived parameters (Sec. 3.3 sizing, Sec. 4.2 position map) */
+typedef struct {
+  uint64_t N, B, K, M, rows;   /* capacity, bins, HBM bins, host pages, pm rows */
+  uint32_t key_bytes, val_bytes;
+  uint32_t c, d, lmax, R;      /* avg bin load, pm choices, max bin load, pm row cap */
+  uint32_t page_bytes, rec_bytes;
+  uint64_t round_width;        /* P2C round width W_r = max(1, floor(B/256)) */
+  uint64_t vs_cap;             /* value-store slots = ceil(beta1 + beta2) + min(N, 65536):
+                                  the paper's bounds plus one batch of headroom */
+  double alpha, beta1, beta2;  /* Claim 3.3 and Claim 3.4 bounds */
+} bolt_info_t;
+
+typedef struct {
+  uint64_t ops;                /* operations processed since bolt_init */
+  uint64_t n_hbm, n_stash;     /* live items in the HBM store and the stash */
+  uint64_t batches;            /* batches processed since bolt_init */
+  uint64_t trace_len;          /* recorded trace entries */
+  uint32_t max_load, max_row;  /* largest bin load / position-map row count */
+} bolt_stats_t;
+
+/*
+ * bolt_create -- plan a map of capacity N records (Sec. 3.3 sizing) and
+ * allocate its device state and its M pinned, device-mapped host pages.
+ *   N           capacity in records, 64 <= N <= 2^31;
+ *   key_bytes   must be 8 (keys are uint64, little-endian in pages);
+ *   val_bytes   value size, a multiple of 8 in [8, 504];
+ *   hbm_budget  bytes the value store (HBM bins + stash, Claims 3.3/3.4) may
+ *               use; alpha is the largest of {0.2, 0.1, 0.05, 0.01, 0} that
+ *               fits (Sec. 3.3 "Parameters selection"); the position map,
+ *               reverse index and load counters are metadata outside it;
+ *   out         receives the handle.
+ * Errors: BOLT_E_ARG, BOLT_E_NOMEM, BOLT_E_CUDA.
+ */
+BOLT_API int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm_budget,
+                bolt_t** out);
+
+/* bolt_plan -- the sizing of bolt_create without allocating anything (host
+ * only, needs no GPU): alpha < 0 applies the budget policy, otherwise that
+ * alpha is used; c is the average bin load.  Fills *out. */
+BOLT_API int bolt_plan(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm_budget,
+                       double alpha, uint32_t c, bolt_info_t* out);
+
+/* bolt_set_param -- change a parameter (ids above).  Sizing parameters
+ * (ALPHA, C) re-plan and reallocate the map and drop its contents. */
+BOLT_API int bolt_set_param(bolt_t* h, int which, double value);
+
+/*
+ * bolt_init -- the oblivious build (Sec. 4.2 "Fast data initialization", run
+ * on the device): keys[i] gets the pair PRF(INIT, i), P2C places it in the
+ * less-loaded bin in rounds of W_r records, the position map takes it by
+ * d-choice, HBM-bin records enter the value store, and the remaining records
+ * are grouped per page by a bitonic sorting network, padded with dummies to
+ * lmax slots, encrypted and written to the pinned host pages.
+ *   keys  HOST pointer, n uint64 keys, all distinct;
+ *   vals  HOST pointer, n * val_bytes bytes, record i at i * val_bytes;
+ *   n     0 <= n <= N;  seed  derives the PRF and page-cipher keys.
+ * Synchronous.  Errors: BOLT_E_ARG, BOLT_E_DUPKEY, BOLT_E_OVERFLOW, BOLT_E_CUDA.
+ */
+BOLT_API int bolt_init(bolt_t* h, const void* keys, const void* vals, uint64_t n, uint64_t seed);
+
+/* bolt_init_device -- bolt_init with DEVICE pointers for keys and vals, the
+ * work enqueued on `stream` (a cudaStream_t, NULL = legacy default stream);
+ * returns after the stream work completes. */
+BOLT_API int bolt_init_device(bolt_t* h, const void* d_keys, const void* d_vals, uint64_t n,
+                     uint64_t seed, void* stream);
+
+/*
+ * bolt_access -- a batch of n oblivious Get/Put/Delete operations (Alg. 1,
+ * applied to a batch; a batch of one is Alg. 1).  Per batch every operation
+ * reads the host pages of both bins of its pair (stored pair for the first
+ * operation on a present key, a fresh random pair otherwise), every distinct
+ * page read is written back once with its stash items evicted into it, and
+ * every key present afterwards is remapped by P2C.
+ *   ops        HOST, n bytes: BOLT_GET, BOLT_PUT or BOLT_DEL;
+ *   keys       HOST, n uint64 keys (repeats allowed, applied in order);
+ *   vals_in    HOST, n * val_bytes, read for Put;
+ *   vals_out   HOST, n * val_bytes, written: the value for a Get on a
+ *              present key, zeros otherwise;
+ *   status_out HOST, n bytes or NULL: 1 if the key was present before the op;
+ * n may exceed BOLT_MAX_BATCH: the call is split into batches of the
+ * configured width.  Results never depend on the batch partition; page
+ * ciphertexts and the trace do.  Synchronous.
+ * Errors: BOLT_E_ARG, BOLT_E_STATE, BOLT_E_OVERFLOW, BOLT_E_CUDA.
+ */
+BOLT_API int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* vals_in,
+                void* vals_out, uint8_t* status_out, uint64_t n);
+
+/* bolt_access_device -- bolt_access with DEVICE pointers (status may be
+ * NULL), enqueued on `stream`; n <= BOLT_MAX_BATCH is one batch.  Returns
+ * after enqueueing; the overflow check of this batch is reported by the next
+ * call on the handle or by bolt_sync. */
+BOLT_API int bolt_access_device(bolt_t* h, const uint8_t* d_ops, const void* d_keys,
+                       const void* d_vals_in, void* d_vals_out, uint8_t* d_status,
+                       uint64_t n, void* stream);
+
+/* bolt_sync -- wait for the handle's enqueued work and report its error. */
+BOLT_API int bolt_sync(bolt_t* h);
+
+/* bolt_destroy -- release every allocation of the handle (NULL is a no-op). */
+BOLT_API int bolt_destroy(bolt_t* h);
+
+/* bolt_get_info / bolt_get_stats -- derived parameters and counters. */
+BOLT_API int bolt_get_info(const bolt_t* h, bolt_info_t* out);
+BOLT_API int bolt_get_stats(bolt_t* h, bolt_stats_t* out);
+
+/* bolt_read_pages -- copy `count` host pages starting at page `first`
+ * (ciphertext, page_bytes each) into dst (host). */
+BOLT_API int bolt_read_pages(bolt_t* h, uint64_t first, uint64_t count, void* dst);
+
+/* bolt_read_trace -- copy up to `cap` trace entries into dst (host) and
+ * clear the trace; *len receives the number copied.  Entry encoding: page
+ * number in bits 0-30, bit 31 set for a write. */
+BOLT_API int bolt_read_trace(bolt_t* h, uint32_t* dst, uint64_t cap, uint64_t* len);
+
+/* bolt_read_loads -- copy the B bin loads (one byte each) into dst (host);
+ * bolt_read_rowcounts -- copy the position-map row counts (one byte each). */
+BOLT_API int bolt_read_loads(bolt_t* h, uint8_t* dst);
+BOLT_API int bolt_read_rowcounts(bolt_t* h, uint8_t* dst);
+
+/* Kernel-class profile (BOLT_PARAM_PROFILE): index = class
+ *   0 bitonic global steps (HBM passes)   1 bitonic in-tile steps
+ *   2 build page gather/encrypt/store     3 build P2C + position-map rounds
+ *   4 build key-uniqueness check          5 whole access batch
+ *   6 access page read + decrypt          7 access write-back + eviction
+ *   8 whole build                         9 access grouping sort + scans
+ * ms[c] sums the event-timed durations of the spans[c] launches (or phases)
+ * of class c; launches counts every kernel the library launched. */
+#define BOLT_PROF_CLASSES 10
+typedef struct {
+  uint64_t launches;
+  uint64_t spans[BOLT_PROF_CLASSES];
+  double ms[BOLT_PROF_CLASSES];
+} bolt_profile_t;
+
+/* bolt_read_profile -- wait for the handle's stream, fold the recorded
+ * events into *out; reset != 0 clears the accumulated profile. */
+BOLT_API int bolt_read_profile(bolt_t* h, bolt_profile_t* out, int reset);
+
+/* bolt_strerror -- static description of an error code. */
+BOLT_API const char* bolt_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

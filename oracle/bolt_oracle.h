@@ -44,7 +44,7 @@ typedef struct {
   uint32_t c, d, lmax, R;         /* avg bin load, pm choices, max bin load, pm row cap */
   uint32_t page_bytes, rec_bytes;
   uint64_t round_width;           /* P2C round width W_r */
-  uint64_t vs_cap;                /* value store slots = ceil(beta1 + beta2) */
+  uint64_t vs_cap;                /* ceil(beta1 + beta2) + min(N, 65536) */
   double alpha, beta1, beta2;
 } oracle_info_t;
 

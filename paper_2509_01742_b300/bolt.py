@@ -1,0 +1,229 @@
+"""ctypes binding of libbolt.so (the C ABI declared in include/bolt.h).
+
+Argument marshalling only: every step of the build and of the access path runs
+in the library's CUDA kernels.  Host-pointer calls take numpy arrays;
+device-pointer calls take torch CUDA tensors (PyTorch is used for device
+memory and streams only).  Importing this module loads the in-tree library and
+raises if it is missing -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbolt.so")
+
+BOLT_OK, BOLT_E_ARG, BOLT_E_NOMEM, BOLT_E_OVERFLOW = 0, -1, -2, -3
+BOLT_E_STATE, BOLT_E_DUPKEY, BOLT_E_CUDA, BOLT_E_TIMEOUT, BOLT_E_INTERNAL = -4, -5, -6, -7, -9
+BOLT_GET, BOLT_PUT, BOLT_DEL = 0, 1, 2
+BOLT_MAX_BATCH = 65536
+BOLT_PARAM_ALPHA, BOLT_PARAM_C, BOLT_PARAM_TRACE, BOLT_PARAM_BATCH = 1, 2, 4, 5
+BOLT_PARAM_TRACE_CAP, BOLT_PARAM_CHECK_KEYS, BOLT_PARAM_PROFILE = 6, 7, 8
+BOLT_PROF_CLASSES = 10
+PROF_NAMES = ("sort_global", "sort_tile", "page_build", "p2c_rounds", "key_check",
+              "access_batch", "gather", "evict", "build", "group")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_2509_01742_b300.build_ext` (no CPU fallback exists)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class bolt_info_t(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint64), ("B", ctypes.c_uint64), ("K", ctypes.c_uint64),
+                ("M", ctypes.c_uint64), ("rows", ctypes.c_uint64),
+                ("key_bytes", ctypes.c_uint32), ("val_bytes", ctypes.c_uint32),
+                ("c", ctypes.c_uint32), ("d", ctypes.c_uint32), ("lmax", ctypes.c_uint32),
+                ("R", ctypes.c_uint32), ("page_bytes", ctypes.c_uint32),
+                ("rec_bytes", ctypes.c_uint32), ("round_width", ctypes.c_uint64),
+                ("vs_cap", ctypes.c_uint64), ("alpha", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class bolt_stats_t(ctypes.Structure):
+    _fields_ = [("ops", ctypes.c_uint64), ("n_hbm", ctypes.c_uint64),
+                ("n_stash", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("trace_len", ctypes.c_uint64), ("max_load", ctypes.c_uint32),
+                ("max_row", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class bolt_profile_t(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("spans", ctypes.c_uint64 * 10),
+                ("ms", ctypes.c_double * 10)]
+
+
+_P, _u64, _u32, _i = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+_SIGS = {
+    "bolt_create": ([_u64, _u32, _u32, _u64, ctypes.POINTER(_P)], _i),
+    "bolt_plan": ([_u64, _u32, _u32, _u64, ctypes.c_double, _u32, ctypes.POINTER(bolt_info_t)], _i),
+    "bolt_set_param": ([_P, _i, ctypes.c_double], _i),
+    "bolt_init": ([_P, _P, _P, _u64, _u64], _i),
+    "bolt_init_device": ([_P, _P, _P, _u64, _u64, _P], _i),
+    "bolt_access": ([_P, _P, _P, _P, _P, _P, _u64], _i),
+    "bolt_access_device": ([_P, _P, _P, _P, _P, _P, _u64, _P], _i),
+    "bolt_sync": ([_P], _i),
+    "bolt_destroy": ([_P], _i),
+    "bolt_get_info": ([_P, ctypes.POINTER(bolt_info_t)], _i),
+    "bolt_get_stats": ([_P, ctypes.POINTER(bolt_stats_t)], _i),
+    "bolt_read_pages": ([_P, _u64, _u64, _P], _i),
+    "bolt_read_trace": ([_P, _P, _u64, ctypes.POINTER(_u64)], _i),
+    "bolt_read_loads": ([_P, _P], _i),
+    "bolt_read_rowcounts": ([_P, _P], _i),
+    "bolt_read_profile": ([_P, ctypes.POINTER(bolt_profile_t), _i], _i),
+    "bolt_strerror": ([_i], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+    globals()[_name] = _f
+
+EXPORTED = tuple(_SIGS)
+
+
+class BoltError(RuntimeError):
+    def __init__(self, rc: int, what: str):
+        super().__init__(f"{what}: {bolt_strerror(rc).decode()} ({rc})")
+        self.rc = rc
+
+
+def _check(rc: int, what: str) -> int:
+    if rc != BOLT_OK:
+        raise BoltError(rc, what)
+    return rc
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def plan(N: int, val_bytes: int, hbm_budget: int = 2**64 - 1, alpha: float = -1.0,
+         c: int = 8) -> dict:
+    o = bolt_info_t()
+    _check(bolt_plan(N, 8, val_bytes, hbm_budget, alpha, c, ctypes.byref(o)), "bolt_plan")
+    return o.as_dict()
+
+
+class BoltMap:
+    """One oblivious map handle (owns its device state and pinned pages)."""
+
+    def __init__(self, N: int, val_bytes: int, hbm_budget: int = 2**64 - 1, alpha=None,
+                 c=None, trace: bool = False, batch=None, check_keys=None):
+        self._h = ctypes.c_void_p()
+        _check(bolt_create(N, 8, val_bytes, hbm_budget, ctypes.byref(self._h)), "bolt_create")
+        self.vb = val_bytes
+        if c is not None:
+            self.set_param(BOLT_PARAM_C, c)
+        if alpha is not None:
+            self.set_param(BOLT_PARAM_ALPHA, alpha)
+        if trace:
+            self.set_param(BOLT_PARAM_TRACE, 1)
+        if batch is not None:
+            self.set_param(BOLT_PARAM_BATCH, batch)
+        if check_keys is not None:
+            self.set_param(BOLT_PARAM_CHECK_KEYS, int(check_keys))
+
+    def set_param(self, which: int, value: float):
+        _check(bolt_set_param(self._h, which, float(value)), "bolt_set_param")
+
+    def close(self):
+        if self._h:
+            bolt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        o = bolt_info_t()
+        _check(bolt_get_info(self._h, ctypes.byref(o)), "bolt_get_info")
+        return o.as_dict()
+
+    def stats(self) -> dict:
+        s = bolt_stats_t()
+        _check(bolt_get_stats(self._h, ctypes.byref(s)), "bolt_get_stats")
+        return s.as_dict()
+
+    # --- host-pointer calls ------------------------------------------------
+    def init(self, keys: np.ndarray, vals: np.ndarray, seed: int) -> int:
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        vals = np.ascontiguousarray(vals, dtype=np.uint8)
+        return bolt_init(self._h, _np_ptr(keys), _np_ptr(vals), len(keys), seed)
+
+    def access(self, ops, keys, vals_in):
+        ops = np.ascontiguousarray(ops, dtype=np.uint8)
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        vin = np.ascontiguousarray(vals_in, dtype=np.uint8)
+        n = len(ops)
+        vout = np.zeros((n, self.vb), dtype=np.uint8)
+        status = np.zeros(n, dtype=np.uint8)
+        rc = bolt_access(self._h, _np_ptr(ops), _np_ptr(keys), _np_ptr(vin), _np_ptr(vout),
+                         _np_ptr(status), n)
+        return rc, vout, status
+
+    # --- device-pointer calls (torch CUDA tensors) --------------------------
+    def init_device(self, keys, vals, seed: int, stream=None) -> int:
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        return bolt_init_device(self._h, ctypes.c_void_p(keys.data_ptr()),
+                                ctypes.c_void_p(vals.data_ptr()), keys.numel(), seed, s)
+
+    def access_device(self, ops, keys, vals_in, vals_out, status=None, stream=None) -> int:
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        st = ctypes.c_void_p(status.data_ptr()) if status is not None else ctypes.c_void_p(0)
+        return bolt_access_device(self._h, ctypes.c_void_p(ops.data_ptr()),
+                                  ctypes.c_void_p(keys.data_ptr()),
+                                  ctypes.c_void_p(vals_in.data_ptr()),
+                                  ctypes.c_void_p(vals_out.data_ptr()), st, ops.numel(), s)
+
+    def sync(self) -> int:
+        return bolt_sync(self._h)
+
+    # --- inspection ----------------------------------------------------------
+    def pages(self, first: int = 0, count=None) -> np.ndarray:
+        i = self.info()
+        count = i["M"] - first if count is None else count
+        out = np.zeros((count, i["page_bytes"]), dtype=np.uint8)
+        _check(bolt_read_pages(self._h, first, count, _np_ptr(out)), "bolt_read_pages")
+        return out
+
+    def trace(self, cap: int = 1 << 24) -> np.ndarray:
+        out = np.zeros(cap, dtype=np.uint32)
+        n = ctypes.c_uint64()
+        _check(bolt_read_trace(self._h, _np_ptr(out), cap, ctypes.byref(n)), "bolt_read_trace")
+        if n.value > cap:
+            raise BoltError(BOLT_E_ARG, f"trace overflow ({n.value} > {cap})")
+        return out[:n.value].copy()
+
+    def profile(self, reset: bool = True) -> dict:
+        p = bolt_profile_t()
+        _check(bolt_read_profile(self._h, ctypes.byref(p), int(reset)), "bolt_read_profile")
+        out = {"launches": int(p.launches)}
+        for c, name in enumerate(PROF_NAMES):
+            out[name] = {"spans": int(p.spans[c]), "ms": float(p.ms[c])}
+        return out
+
+    def loads(self) -> np.ndarray:
+        out = np.zeros(self.info()["B"], dtype=np.uint8)
+        _check(bolt_read_loads(self._h, _np_ptr(out)), "bolt_read_loads")
+        return out
+
+    def rowcounts(self) -> np.ndarray:
+        out = np.zeros(self.info()["rows"], dtype=np.uint8)
+        _check(bolt_read_rowcounts(self._h, _np_ptr(out)), "bolt_read_rowcounts")
+        return out

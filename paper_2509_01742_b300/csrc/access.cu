@@ -1,0 +1,540 @@
+// access.cu -- batched oblivious access (Alg. 1 over a batch of operations,
+// with the module order of Sec. 4.1: KS -> VAC -> exec -> write-back -> RMP).
+//
+// One batch of n <= BOLT_MAX_BATCH operations, operation i with global
+// sequence number t0 + i:
+//   k_stage     per op: sort element (key, i); PRF pairs for DUMMY and REMAP,
+//               position-map rows PRF(PM, key)
+//   sort        (key, i) ascending (bitonic, sort.cu)
+//   k_group     one CTA: leader (first op on the key), previous writer of each
+//               op, last writer of each key group, by prefix-max scans
+//   k_lookup    warp per op: leaders scan their d rows of the position map
+//               (ballot over the R slots of each row); hit -> stored pair,
+//               otherwise the DUMMY pair; host bins enter a page hash table
+//   k_pages     one CTA: distinct pages in first-read order, read/write trace
+//   k_gather    warp per distinct page: zero-copy 16-byte reads of the pinned
+//               host page, ChaCha20 decryption (quad-cooperative key stream)
+//   k_find      warp per op: find_remove of each hit (page scan by ballot, or
+//               the value store), load and position-map bookkeeping
+//   k_exec      per op: Get/Put/Delete semantics in op order per key
+//   k_evict     warp per distinct page: remaining tuples + stash items bound
+//               for the page, ordered by key, dummy-padded, version + 1,
+//               encrypted, written back to the host page
+//   k_remap_*   P2C remap of every key present after the batch, in rounds of
+//               W_r operation slots decided on round-start loads
+#include "bolt_internal.cuh"
+#include "batch.cuh"
+
+namespace bdev {
+
+__global__ void k_stage(MapDev m, BatchDev b, uint32_t n, uint32_t n_sort, uint64_t t0) {
+  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_sort) return;
+  if (i >= n) {
+    b.sortbuf[i] = make_ulonglong2(~0ull, ~0ull);
+    return;
+  }
+  const uint64_t key = b.keys[i];
+  b.sortbuf[i] = make_ulonglong2(key, i);
+  uint32_t p1, p2;
+  prf_pair(m, DOM_DUMMY, t0 + i, p1, p2);
+  b.pair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
+  prf_pair(m, DOM_REMAP, t0 + i, p1, p2);
+  b.rpair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
+  uint32_t rows[4];
+  prf_rows(m, key, rows);
+  *reinterpret_cast<uint4*>(b.rows + 4 * (uint64_t)i) = make_uint4(rows[0], rows[1], rows[2], rows[3]);
+}
+
+// ---------------------------------------------------------------------------
+// grouping: prefix-max scans over the sorted (key, op) sequence
+__device__ __forceinline__ int32_t block_excl_max(int32_t v, int32_t* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = max(x, y);
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int32_t w = lane < (int)(blockDim.x >> 5) ? sh[lane] : -1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w = max(w, y);
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  int32_t prev_warps = wid > 0 ? sh[wid - 1] : -1;
+  int32_t excl = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane == 0) excl = -1;
+  excl = max(excl, prev_warps);
+  __syncthreads();
+  return excl;
+}
+
+constexpr int GROUP_THREADS = 1024;
+
+__global__ void __launch_bounds__(GROUP_THREADS) k_group(BatchDev b, uint32_t n) {
+  __shared__ int32_t sh[32];
+  const uint32_t per = (n + GROUP_THREADS - 1) / GROUP_THREADS;
+  const uint32_t lo = threadIdx.x * per;
+  const uint32_t hi = min(n, lo + per);
+  // local maxima of head positions and writer positions
+  int32_t hmax = -1, wmax = -1;
+  for (uint32_t s = lo; s < hi; s++) {
+    const ulonglong2 e = b.sortbuf[s];
+    const bool head = s == 0 || b.sortbuf[s - 1].x != e.x;
+    if (head) hmax = (int32_t)s;
+    if (b.ops[e.y] != OP_GET) wmax = (int32_t)s;
+  }
+  int32_t hcar = block_excl_max(hmax, sh);
+  int32_t wcar = block_excl_max(wmax, sh);
+  for (uint32_t s = lo; s < hi; s++) {
+    const ulonglong2 e = b.sortbuf[s];
+    const uint32_t i = (uint32_t)e.y;
+    const bool head = s == 0 || b.sortbuf[s - 1].x != e.x;
+    if (head) hcar = (int32_t)s;
+    const uint32_t lead = (uint32_t)b.sortbuf[hcar].y;
+    // previous writer in the same group (strictly before s)
+    b.prevw[i] = wcar >= hcar ? (uint32_t)b.sortbuf[wcar].y : NONE32;
+    b.leader[i] = lead;
+    if (b.ops[i] != OP_GET) wcar = (int32_t)s;
+    const bool last = s + 1 == n || b.sortbuf[s + 1].x != e.x;
+    if (last) b.lastw[lead] = wcar >= hcar ? (uint32_t)b.sortbuf[wcar].y : NONE32;
+  }
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ht_hash(uint32_t page, uint32_t mask) {
+  return (page * 0x9E3779B1u) & mask;
+}
+
+__device__ __forceinline__ void ht_insert(const BatchDev& b, uint32_t page, uint32_t pos) {
+  uint32_t h = ht_hash(page, b.ht_mask);
+  for (uint32_t probe = 0; probe <= b.ht_mask; probe++) {
+    uint32_t old = atomicCAS(b.ht_key + h, NONE32, page);
+    if (old == NONE32 || old == page) {
+      atomicMin(b.ht_min + h, pos);
+      b.pos_slot[pos] = h;
+      return;
+    }
+    h = (h + 1) & b.ht_mask;
+  }
+}
+
+// warp per op
+__global__ void k_lookup(MapDev m, BatchDev b, uint32_t n) {
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  uint32_t found = NONE32;
+  if (b.leader[i] == i) {
+    const uint64_t key = b.keys[i];
+    const uint4 rows = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
+    const uint32_t rr[4] = {rows.x, rows.y, rows.z, rows.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      bool match = false;
+      uint64_t idx = (uint64_t)rr[j] * m.R + lane;
+      if (lane < (int)m.R)
+        match = meta_loc(m.pm_meta[idx]) != LOC_EMPTY && m.pm_key[idx] == key;
+      uint32_t bal = __ballot_sync(0xffffffffu, match);
+      if (bal && found == NONE32) found = (uint32_t)((uint64_t)rr[j] * m.R + (__ffs(bal) - 1));
+    }
+  }
+  if (lane == 0) {
+    b.hit[i] = found;
+    if (found != NONE32) b.pair[i] = m.pm_bins[found];
+  }
+  __syncwarp();
+  if (lane < 2) {
+    const uint64_t pr = b.pair[i];
+    const uint32_t p = lane == 0 ? (uint32_t)pr : (uint32_t)(pr >> 32);
+    const uint32_t pos = 2 * i + lane;
+    if (p >= m.K) {
+      const uint32_t q = (uint32_t)(p - m.K);
+      b.pos_page[pos] = q;
+      ht_insert(b, q, pos);
+    } else {
+      b.pos_page[pos] = NONE32;
+    }
+  }
+}
+
+// one CTA: distinct pages in first-read order and the host-access trace
+constexpr int PAGES_THREADS = 1024;
+
+__global__ void __launch_bounds__(PAGES_THREADS) k_pages(MapDev m, BatchDev b, uint32_t n) {
+  __shared__ uint32_t sh[32];
+  const uint32_t np = 2 * n;
+  const uint32_t per = (np + PAGES_THREADS - 1) / PAGES_THREADS;
+  const uint32_t lo = threadIdx.x * per, hi = min(np, lo + per);
+  uint32_t nvalid = 0, nfirst = 0;
+  for (uint32_t p = lo; p < hi; p++) {
+    const uint32_t q = b.pos_page[p];
+    if (q == NONE32) continue;
+    nvalid++;
+    if (b.ht_min[b.pos_slot[p]] == p) nfirst++;
+  }
+  uint32_t tot_valid, tot_first;
+  uint32_t rbase = block_excl_scan(nvalid, sh, tot_valid);
+  uint32_t dbase = block_excl_scan(nfirst, sh, tot_first);
+  const uint64_t tbase = m.trace_on ? *m.trace_len : 0;
+  for (uint32_t p = lo; p < hi; p++) {
+    const uint32_t q = b.pos_page[p];
+    if (q == NONE32) continue;
+    if (m.trace_on && tbase + rbase < m.trace_cap) m.trace[tbase + rbase] = q;
+    rbase++;
+    const uint32_t slot = b.pos_slot[p];
+    if (b.ht_min[slot] == p) {
+      b.dpage[dbase] = q;
+      b.ht_d[slot] = dbase;
+      const uint64_t w = tbase + tot_valid + dbase;
+      if (m.trace_on && w < m.trace_cap) m.trace[w] = q | 0x80000000u;
+      dbase++;
+    }
+  }
+  __syncthreads();
+  for (uint32_t p = lo; p < hi; p++) {
+    const uint32_t q = b.pos_page[p];
+    b.pos_d[p] = q == NONE32 ? NONE32 : b.ht_d[b.pos_slot[p]];
+  }
+  if (threadIdx.x == 0) {
+    *b.dcount = tot_first;
+    if (m.trace_on) *m.trace_len = tbase + tot_valid + tot_first;
+  }
+}
+
+// warp per distinct page: read from the pinned host page and decrypt
+__global__ void k_gather(MapDev m, BatchDev b) {
+  const uint32_t d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (d >= *b.dcount) return;
+  const uint64_t q = b.dpage[d];
+  const uint64_t v = m.version[q];
+  const uint8_t* src = m.pages + q * m.page_bytes;
+  uint8_t* dst = b.dbuf + (uint64_t)d * m.page_bytes;
+  for (uint32_t c = 0; c < m.page_bytes; c += 512) {
+    const uint32_t off = c + 16 * lane;
+    uint4 x = make_uint4(0, 0, 0, 0);
+    if (off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
+    const uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)v,
+                                 (uint32_t)(v >> 32));
+    if (off < m.page_bytes) {
+      x.x ^= ks.x; x.y ^= ks.y; x.z ^= ks.z; x.w ^= ks.w;
+      *reinterpret_cast<uint4*>(dst + off) = x;
+    }
+  }
+  if (lane == 0) b.removed[d] = 0;
+}
+
+__device__ __forceinline__ void ring_push(const MapDev& m, uint32_t slot) {
+  unsigned long long pos = atomicAdd(m.ring_ctr + 1, 1ull);
+  m.ring[pos % m.vs_cap] = slot;
+}
+
+// warp per op: find_remove for hits (Alg. 1 lines 6 and 9)
+__global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n || b.leader[i] != i) return;
+  const uint32_t slot = b.hit[i];
+  if (slot == NONE32) {
+    if (lane == 0) b.init_present[i] = 0;
+    return;
+  }
+  const uint32_t meta = m.pm_meta[slot];
+  const uint64_t pr = b.pair[i];
+  const uint32_t which = meta_which(meta);
+  const uint32_t bin = which ? (uint32_t)(pr >> 32) : (uint32_t)pr;
+  uint8_t* out = b.init_val + (uint64_t)i * m.vb;
+  const uint32_t nw = m.vb / 8;
+  if (meta_loc(meta) == LOC_HOST) {
+    const uint32_t d = b.pos_d[2 * i + which];
+    if (d == NONE32) {
+      if (lane == 0) set_err(m, ERR_NOTFOUND);
+      return;
+    }
+    const uint8_t* pg = b.dbuf + (uint64_t)d * m.page_bytes;
+    const uint64_t bitmap = *reinterpret_cast<const uint64_t*>(pg);
+    const uint64_t key = b.keys[i];
+    bool match = false;
+    if (lane < (int)m.lmax && ((bitmap >> lane) & 1))
+      match = *reinterpret_cast<const uint64_t*>(pg + 16 + (size_t)lane * m.rec) == key;
+    const uint32_t bal = __ballot_sync(0xffffffffu, match);
+    if (!bal) {
+      if (lane == 0) set_err(m, ERR_NOTFOUND);
+      return;
+    }
+    const int s = __ffs(bal) - 1;
+    const uint64_t* val = reinterpret_cast<const uint64_t*>(pg + 16 + (size_t)s * m.rec + 8);
+    for (uint32_t w = lane; w < nw; w += 32) reinterpret_cast<uint64_t*>(out)[w] = val[w];
+    if (lane == 0) atomicOr(reinterpret_cast<unsigned long long*>(b.removed + d), 1ull << s);
+  } else {
+    const uint32_t vs = meta_ptr(meta);
+    const uint64_t* val = reinterpret_cast<const uint64_t*>(m.vs_val + (uint64_t)vs * m.vb);
+    for (uint32_t w = lane; w < nw; w += 32) reinterpret_cast<uint64_t*>(out)[w] = val[w];
+    __syncwarp();
+    if (lane == 0) {
+      m.vs_live[vs] = 0;
+      ring_push(m, vs);
+    }
+  }
+  if (lane == 0) {
+    b.init_present[i] = 1;
+    byte_dec(m.load, bin);
+    const uint32_t lw = b.lastw[i];
+    if (lw != NONE32 && b.ops[lw] == OP_DEL) {  // deleted: free the map slot
+      m.pm_meta[slot] = 0;
+      byte_dec(m.rowcnt, slot / m.R);
+    }
+  }
+}
+
+// thread per op: Get/Put/Delete semantics (Alg. 1 line 12)
+__global__ void k_exec(MapDev m, BatchDev b, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t nw = m.vb / 8;
+  const uint32_t w = b.prevw[i];
+  bool present;
+  const uint64_t* src;
+  if (w != NONE32) {
+    present = b.ops[w] == OP_PUT;
+    src = reinterpret_cast<const uint64_t*>(b.vin + (uint64_t)w * m.vb);
+  } else {
+    const uint32_t l = b.leader[i];
+    present = b.init_present[l] != 0;
+    src = reinterpret_cast<const uint64_t*>(b.init_val + (uint64_t)l * m.vb);
+  }
+  b.status[i] = present;
+  uint64_t* out = reinterpret_cast<uint64_t*>(b.vout + (uint64_t)i * m.vb);
+  const bool give = b.ops[i] == OP_GET && present;
+  for (uint32_t k = 0; k < nw; k++) out[k] = give ? src[k] : 0;
+  if (b.leader[i] == i) {
+    const uint32_t lw = b.lastw[i];
+    bool fp;
+    const uint64_t* fs;
+    if (lw != NONE32) {
+      fp = b.ops[lw] == OP_PUT;
+      fs = reinterpret_cast<const uint64_t*>(b.vin + (uint64_t)lw * m.vb);
+    } else {
+      fp = b.init_present[i] != 0;
+      fs = reinterpret_cast<const uint64_t*>(b.init_val + (uint64_t)i * m.vb);
+    }
+    b.fpres[i] = fp;
+    uint64_t* rv = reinterpret_cast<uint64_t*>(b.rval + (uint64_t)i * m.vb);
+    if (fp)
+      for (uint32_t k = 0; k < nw; k++) rv[k] = fs[k];
+  }
+}
+
+// warp per distinct page: write-back with eviction (Alg. 1 line 10)
+__global__ void k_evict(MapDev m, BatchDev b, uint32_t warps_per_block) {
+  extern __shared__ __align__(16) uint8_t sbuf[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t d = blockIdx.x * warps_per_block + wid;
+  if (d >= *b.dcount) return;
+  uint8_t* plain = sbuf + (size_t)wid * (m.page_bytes + 32 * 16);
+  ulonglong2* items = reinterpret_cast<ulonglong2*>(plain + m.page_bytes);
+  const uint64_t q = b.dpage[d];
+  const uint8_t* old = b.dbuf + (uint64_t)d * m.page_bytes;
+  const uint64_t bitmap = *reinterpret_cast<const uint64_t*>(old);
+  const uint64_t removed = b.removed[d];
+  // remaining page tuples (source tag: slot index) and live stash items bound
+  // for this page (source tag: 1 << 31 | value-store slot)
+  const bool pv = lane < (int)m.lmax && ((bitmap >> lane) & 1) && !((removed >> lane) & 1);
+  const uint32_t rc = byte_get(m.revcnt, q);
+  uint32_t vs = NONE32;
+  bool sv = false;
+  if (lane < (int)rc && lane < (int)m.lmax) {
+    vs = m.rev[q * m.lmax + lane];
+    sv = m.vs_live[vs] != 0;
+  }
+  const uint32_t pmask = __ballot_sync(0xffffffffu, pv);
+  const uint32_t smask = __ballot_sync(0xffffffffu, sv);
+  const uint32_t below = (1u << lane) - 1u;
+  const uint32_t np = __popc(pmask), tot = np + __popc(smask);
+  if (tot > m.lmax) {  // cannot happen while every load is <= lmax
+    if (lane == 0) set_err(m, ERR_PAGE);
+    return;
+  }
+  if (pv)
+    items[__popc(pmask & below)] =
+        make_ulonglong2(*reinterpret_cast<const uint64_t*>(old + 16 + (size_t)lane * m.rec), lane);
+  if (sv) items[np + __popc(smask & below)] = make_ulonglong2(m.vs_key[vs], (1ull << 31) | vs);
+  __syncwarp();
+  uint64_t key = ~0ull;
+  uint32_t src = NONE32;
+  if (lane < (int)tot) {
+    key = items[lane].x;
+    src = (uint32_t)items[lane].y;
+  }
+  warp_sort_by_key(key, src);
+  for (uint32_t o = 16 * lane; o < m.page_bytes; o += 512)
+    *reinterpret_cast<uint4*>(plain + o) = make_uint4(0, 0, 0, 0);
+  __syncwarp();
+  if (lane == 0) *reinterpret_cast<uint64_t*>(plain) = tot >= 64 ? ~0ull : ((1ull << tot) - 1);
+  if (lane < (int)tot) {
+    uint8_t* slot = plain + 16 + (size_t)lane * m.rec;
+    *reinterpret_cast<uint64_t*>(slot) = key;
+    const uint64_t* val =
+        (src >> 31) ? reinterpret_cast<const uint64_t*>(m.vs_val + (uint64_t)(src & 0x7fffffffu) * m.vb)
+                    : reinterpret_cast<const uint64_t*>(old + 16 + (size_t)src * m.rec + 8);
+    for (uint32_t w = 0; w < m.vb / 8; w++) reinterpret_cast<uint64_t*>(slot + 8)[w] = val[w];
+  }
+  __syncwarp();
+  const uint64_t ver = m.version[q] + 1;
+  page_encrypt_store(m, plain, q, ver);
+  __syncwarp();
+  if (lane == 0) {
+    m.version[q] = ver;
+    const uint32_t sh = (uint32_t)(q & 3) * 8;
+    atomicAnd(m.revcnt + (q >> 2), ~(0xffu << sh));
+  }
+  if (sv) {  // evicted stash item now lives in the page
+    const uint32_t pmi = m.vs_pm[vs];
+    m.pm_meta[pmi] = meta_make(LOC_HOST, meta_which(m.pm_meta[pmi]), 0);
+    m.vs_live[vs] = 0;
+    ring_push(m, vs);
+  }
+}
+
+// P2C remap, decide on round-start loads (Alg. 1 lines 13-14)
+__global__ void k_remap_decide(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
+  const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi || b.leader[i] != i || !b.fpres[i]) return;
+  const uint64_t pr = b.rpair[i];
+  const uint32_t p1 = (uint32_t)pr, p2 = (uint32_t)(pr >> 32);
+  b.rdest[i] = byte_get(m.load, p1) <= byte_get(m.load, p2) ? p1 : p2;
+  if (b.hit[i] == NONE32) {
+    const uint4 rows = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
+    const uint32_t rr[4] = {rows.x, rows.y, rows.z, rows.w};
+    b.rrow[i] = pick_row(m, rr);
+  }
+}
+
+__global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
+  const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi || b.leader[i] != i || !b.fpres[i]) return;
+  const uint32_t dest = b.rdest[i];
+  if (byte_inc(m.load, dest) + 1 > m.lmax) {
+    set_err(m, ERR_LOAD);
+    return;
+  }
+  const uint64_t pr = b.rpair[i];
+  const uint32_t which = dest == (uint32_t)(pr >> 32) ? 1u : 0u;
+  const unsigned long long pos = atomicAdd(m.ring_ctr, 1ull);
+  if (pos >= m.ring_ctr[1]) {
+    set_err(m, ERR_VS);
+    return;
+  }
+  const uint32_t vs = m.ring[pos % m.vs_cap];
+  const bool hbm = dest < m.K;
+  const uint32_t meta = meta_make(hbm ? LOC_HBM : LOC_STASH, which, vs);
+  uint32_t slot = b.hit[i];
+  const uint64_t key = b.keys[i];
+  if (slot == NONE32) {
+    const uint32_t row = b.rrow[i];
+    if (byte_inc(m.rowcnt, row) + 1 > m.R) {
+      set_err(m, ERR_ROW);
+      return;
+    }
+    for (uint32_t s = 0; s < m.R; s++) {
+      const uint64_t idx = (uint64_t)row * m.R + s;
+      if (atomicCAS(m.pm_meta + idx, 0u, meta) == 0u) {
+        slot = (uint32_t)idx;
+        break;
+      }
+    }
+    if (slot == NONE32) {
+      set_err(m, ERR_ROW);
+      return;
+    }
+    m.pm_key[slot] = key;
+  } else {
+    m.pm_meta[slot] = meta;
+  }
+  m.pm_bins[slot] = pr;
+  m.vs_key[vs] = key;
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(b.rval + (uint64_t)i * m.vb);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(m.vs_val + (uint64_t)vs * m.vb);
+  for (uint32_t w = 0; w < m.vb / 8; w++) dst[w] = src[w];
+  m.vs_pm[vs] = slot;
+  m.vs_live[vs] = 1;
+  if (!hbm) {
+    const uint64_t q = dest - m.K;
+    const uint32_t r = byte_inc(m.revcnt, q);
+    if (r >= m.lmax) {
+      set_err(m, ERR_REV);
+      return;
+    }
+    m.rev[q * m.lmax + r] = vs;
+  }
+}
+
+__global__ void k_clear_table(BatchDev b) {
+  for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h <= b.ht_mask;
+       h += gridDim.x * blockDim.x) {
+    b.ht_key[h] = NONE32;
+    b.ht_min[h] = NONE32;
+  }
+}
+
+cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
+                          cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  uint32_t n_sort = 512;
+  while (n_sort < n) n_sort <<= 1;
+  if (n_sort > 512 && n_sort < 4096) n_sort = 4096;
+  ProfSpan whole(P_ACCESS, st);
+  k_clear_table<<<64, 256, 0, st>>>(b);
+  k_stage<<<(n_sort + 255) / 256, 256, 0, st>>>(m, b, n, n_sort, t0);
+  count_launch(2);
+  cudaError_t e;
+  {
+    ProfSpan ps(P_GROUP, st);
+    e = sort_pairs(b.sortbuf, n_sort, st);
+    if (e != cudaSuccess) return e;
+    k_group<<<1, GROUP_THREADS, 0, st>>>(b, n);
+    count_launch();
+  }
+  const uint32_t warp_blocks = (n * 32 + 255) / 256;
+  k_lookup<<<warp_blocks, 256, 0, st>>>(m, b, n);
+  k_pages<<<1, PAGES_THREADS, 0, st>>>(m, b, n);
+  count_launch(2);
+  const uint32_t dmax = 2 * n;  // distinct pages are at most two per op
+  {
+    ProfSpan ps(P_GATHER, st);
+    k_gather<<<(dmax * 32 + 255) / 256, 256, 0, st>>>(m, b);
+    count_launch();
+  }
+  k_find<<<warp_blocks, 256, 0, st>>>(m, b, n);
+  k_exec<<<(n + 255) / 256, 256, 0, st>>>(m, b, n);
+  count_launch(2);
+  uint32_t wpb = 4;
+  size_t smem = (size_t)wpb * (m.page_bytes + 32 * 16);
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_evict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  {
+    ProfSpan ps(P_EVICT, st);
+    k_evict<<<(dmax + wpb - 1) / wpb, wpb * 32, smem, st>>>(m, b, wpb);
+    count_launch();
+  }
+  for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+    const uint32_t hi = (uint32_t)(lo + m.Wr < n ? lo + m.Wr : n);
+    const uint32_t g = (hi - (uint32_t)lo + 255) / 256;
+    k_remap_decide<<<g, 256, 0, st>>>(m, b, (uint32_t)lo, hi);
+    k_remap_apply<<<g, 256, 0, st>>>(m, b, (uint32_t)lo, hi);
+    count_launch(2);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bdev

@@ -1,0 +1,49 @@
+// batch.cuh -- device buffers of one access batch (capacity BOLT_MAX_BATCH).
+#pragma once
+#include "bolt_internal.cuh"
+
+namespace bdev {
+
+struct BatchDev {
+  // staged inputs / outputs
+  uint8_t* ops;        // [cap]
+  uint64_t* keys;      // [cap]
+  uint8_t* vin;        // [cap * vb]
+  uint8_t* vout;       // [cap * vb]
+  uint8_t* status;     // [cap]
+  // grouping
+  ulonglong2* sortbuf; // [sort_cap] (key, op index)
+  uint32_t* leader;    // [cap] first op on the same key
+  uint32_t* prevw;     // [cap] previous PUT/DEL on the same key, or NONE
+  uint32_t* lastw;     // [cap] (leaders) last PUT/DEL of the key group, or NONE
+  // key search
+  uint64_t* pair;      // [cap] bins read by the op: stored pair or DUMMY pair
+  uint64_t* rpair;     // [cap] REMAP pair
+  uint32_t* rows;      // [4 * cap] position-map rows
+  uint32_t* hit;       // [cap] position-map slot of a leader hit, or NONE
+  // pages read by the batch
+  uint32_t* pos_page;  // [2 cap] host page of read position 2i + j, or NONE
+  uint32_t* pos_slot;  // [2 cap] hash-table slot of that page
+  uint32_t* pos_d;     // [2 cap] distinct-page index of that page
+  uint32_t* ht_key;    // [ht_mask + 1] page hash table
+  uint32_t* ht_min;    // [ht_mask + 1] first read position of the page
+  uint32_t* ht_d;      // [ht_mask + 1] distinct-page index
+  uint32_t ht_mask, pad0;
+  uint32_t* dpage;     // [2 cap] distinct pages in first-read order
+  uint32_t* dcount;    // [1]
+  uint8_t* dbuf;       // [2 cap * page_bytes] decrypted pages
+  uint64_t* removed;   // [2 cap] slots taken out by find_remove
+  // values
+  uint8_t* init_val;   // [cap * vb] value found for a leader hit
+  uint8_t* init_present;  // [cap]
+  uint8_t* rval;       // [cap * vb] value to re-place (leaders)
+  uint8_t* fpres;      // [cap] key present after the batch (leaders)
+  uint32_t* rdest;     // [cap] P2C destination
+  uint32_t* rrow;      // [cap] position-map row for a new key
+};
+
+cudaError_t sort_pairs(ulonglong2* data, uint32_t n_pow2, cudaStream_t st);
+cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
+                          cudaStream_t st);
+
+}  // namespace bdev

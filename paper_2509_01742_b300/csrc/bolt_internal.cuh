@@ -1,0 +1,354 @@
+// bolt_internal.cuh -- device-side types and primitives of the B300 BOLT map.
+//
+// Shared by the build, sort and access translation units.  Nothing here is
+// shared with the CPU oracle: every primitive is written afresh for the GPU.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/bolt.h"
+
+namespace bdev {
+
+// ---------------------------------------------------------------------------
+// Error bits set by kernels in the device error word (Sec. 3.3: a capacity
+// bound may be exceeded with probability 1/O(N); that is reported, not
+// silently absorbed).
+enum : uint32_t {
+  ERR_LOAD = 1u << 0,      // a bin load went above lmax (Claim 3.2)
+  ERR_ROW = 1u << 1,       // a position-map row went above R (Sec. 4.2)
+  ERR_VS = 1u << 2,        // value store (HBM bins + stash) full (Claims 3.3/3.4)
+  ERR_REV = 1u << 3,       // reverse-index list over lmax entries
+  ERR_NOTFOUND = 1u << 4,  // a position-map hit was not found where it points
+  ERR_PAGE = 1u << 5,      // a page held more than lmax tuples
+  ERR_TIMEOUT = 1u << 6,   // a bounded device wait gave up
+  ERR_OVERFLOW_MASK = ERR_LOAD | ERR_ROW | ERR_VS | ERR_REV | ERR_PAGE,
+};
+
+// position-map slot metadata: bits 0-1 location, bit 2 which-bin, bits 3-31
+// value-store slot (Sec. 4.2: flag bit for HBM vs stash, index pointer)
+enum : uint32_t { LOC_EMPTY = 0, LOC_HOST = 1, LOC_HBM = 2, LOC_STASH = 3 };
+__host__ __device__ __forceinline__ uint32_t meta_make(uint32_t loc, uint32_t which,
+                                                       uint32_t ptr) {
+  return loc | (which << 2) | (ptr << 3);
+}
+__host__ __device__ __forceinline__ uint32_t meta_loc(uint32_t m) { return m & 3u; }
+__host__ __device__ __forceinline__ uint32_t meta_which(uint32_t m) { return (m >> 2) & 1u; }
+__host__ __device__ __forceinline__ uint32_t meta_ptr(uint32_t m) { return m >> 3; }
+
+enum : uint32_t { DOM_INIT = 1, DOM_PM = 2, DOM_REMAP = 3, DOM_DUMMY = 4 };
+enum : uint8_t { OP_GET = 0, OP_PUT = 1, OP_DEL = 2 };
+constexpr uint32_t NONE32 = 0xffffffffu;
+
+// Map parameters and device pointers, passed by value to every kernel.
+struct MapDev {
+  // sizing (Sec. 3.3, Sec. 4.2)
+  uint64_t N, B, K, M, rows, Wr, vs_cap;
+  uint32_t R, lmax, vb, rec, page_bytes, pad0;
+  uint32_t kprf[8], kenc[8];
+  // state in HBM
+  uint32_t* load;      // packed u8 bin loads, B bytes (4 per word)
+  uint32_t* rowcnt;    // packed u8 position-map row counts
+  uint64_t* pm_key;    // [rows*R]
+  uint64_t* pm_bins;   // [rows*R] b1 | b2 << 32
+  uint32_t* pm_meta;   // [rows*R]
+  uint64_t* vs_key;    // [vs_cap] value store = HBM bins + stash
+  uint8_t* vs_val;     // [vs_cap * vb]
+  uint32_t* vs_pm;     // [vs_cap] owning position-map slot
+  uint8_t* vs_live;    // [vs_cap]
+  uint32_t* ring;      // [vs_cap] free value-store slots
+  unsigned long long* ring_ctr;  // [0] head (pops), [1] tail (pushes)
+  uint32_t* rev;       // [M * lmax] reverse index: stash slots bound for page q
+  uint32_t* revcnt;    // packed u8 counts, M bytes
+  uint64_t* version;   // [M] page write counters (cipher nonces)
+  uint8_t* pages;      // device alias of the pinned host pages [M * page_bytes]
+  uint32_t* err;       // error word
+  uint32_t* trace;     // host-access trace (optional)
+  unsigned long long* trace_len;
+  uint64_t trace_cap;
+  uint32_t trace_on, pad1;
+};
+
+// ---------------------------------------------------------------------------
+// Packed byte counters: 4 counters per 32-bit word, updated with word atomics.
+__device__ __forceinline__ uint32_t byte_get(const uint32_t* w, uint64_t i) {
+  return reinterpret_cast<const uint8_t*>(w)[i];
+}
+__device__ __forceinline__ uint32_t byte_inc(uint32_t* w, uint64_t i) {
+  uint32_t sh = (uint32_t)(i & 3) * 8;
+  return (atomicAdd(w + (i >> 2), 1u << sh) >> sh) & 0xffu;  // old value
+}
+__device__ __forceinline__ void byte_dec(uint32_t* w, uint64_t i) {
+  uint32_t sh = (uint32_t)(i & 3) * 8;
+  atomicSub(w + (i >> 2), 1u << sh);
+}
+
+__device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) { return __umul64hi(a, b); }
+
+// ---------------------------------------------------------------------------
+// ChaCha20 block function (RFC 8439): 16-word state = 4 constant words,
+// 8 key words, block counter, 3 nonce words; 10 double rounds of column then
+// diagonal quarter rounds; output = final state + input state.
+
+#define BOLT_QR(a, b, c, d)             \
+  a += b; d ^= a; d = __funnelshift_l(d, d, 16); \
+  c += d; b ^= c; b = __funnelshift_l(b, b, 12); \
+  a += b; d ^= a; d = __funnelshift_l(d, d, 8);  \
+  c += d; b ^= c; b = __funnelshift_l(b, b, 7);
+
+__device__ __forceinline__ void chacha_block(const uint32_t* key, uint32_t counter, uint32_t n0,
+                                             uint32_t n1, uint32_t n2, uint32_t out[16]) {
+  uint32_t x0 = 0x61707865u, x1 = 0x3320646eu, x2 = 0x79622d32u, x3 = 0x6b206574u;
+  uint32_t x4 = key[0], x5 = key[1], x6 = key[2], x7 = key[3];
+  uint32_t x8 = key[4], x9 = key[5], x10 = key[6], x11 = key[7];
+  uint32_t x12 = counter, x13 = n0, x14 = n1, x15 = n2;
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    BOLT_QR(x0, x4, x8, x12);
+    BOLT_QR(x1, x5, x9, x13);
+    BOLT_QR(x2, x6, x10, x14);
+    BOLT_QR(x3, x7, x11, x15);
+    BOLT_QR(x0, x5, x10, x15);
+    BOLT_QR(x1, x6, x11, x12);
+    BOLT_QR(x2, x7, x8, x13);
+    BOLT_QR(x3, x4, x9, x14);
+  }
+  out[0] = x0 + 0x61707865u; out[1] = x1 + 0x3320646eu;
+  out[2] = x2 + 0x79622d32u; out[3] = x3 + 0x6b206574u;
+  out[4] = x4 + key[0]; out[5] = x5 + key[1]; out[6] = x6 + key[2]; out[7] = x7 + key[3];
+  out[8] = x8 + key[4]; out[9] = x9 + key[5]; out[10] = x10 + key[6]; out[11] = x11 + key[7];
+  out[12] = x12 + counter; out[13] = x13 + n0; out[14] = x14 + n1; out[15] = x15 + n2;
+}
+
+// Four lanes compute one block together: lane g (= lane & 3) holds column g
+// of the state (words g, 4+g, 8+g, 12+g).  Column rounds are lane-local;
+// diagonal rounds rotate rows 1-3 across the quad with shuffles.  Returns
+// words 4g..4g+3 of the block, i.e. key-stream bytes [16g, 16g+16).  All 32
+// lanes of the warp must call it (full-mask shuffles).
+__device__ __forceinline__ uint4 chacha_quad(const uint32_t* key, uint32_t counter, uint32_t n0,
+                                             uint32_t n1, uint32_t n2) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane & 3;
+  const int base = lane & ~3;
+  const uint32_t c_const = g == 0 ? 0x61707865u : g == 1 ? 0x3320646eu
+                         : g == 2 ? 0x79622d32u : 0x6b206574u;
+  const uint32_t ib = g == 0 ? key[0] : g == 1 ? key[1] : g == 2 ? key[2] : key[3];
+  const uint32_t ic = g == 0 ? key[4] : g == 1 ? key[5] : g == 2 ? key[6] : key[7];
+  const uint32_t id = g == 0 ? counter : g == 1 ? n0 : g == 2 ? n1 : n2;
+  uint32_t a = c_const, b = ib, c = ic, d = id;
+  const int s1 = base | ((g + 1) & 3), s2 = base | ((g + 2) & 3), s3 = base | ((g + 3) & 3);
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    BOLT_QR(a, b, c, d);
+    b = __shfl_sync(0xffffffffu, b, s1);
+    c = __shfl_sync(0xffffffffu, c, s2);
+    d = __shfl_sync(0xffffffffu, d, s3);
+    BOLT_QR(a, b, c, d);
+    b = __shfl_sync(0xffffffffu, b, s3);
+    c = __shfl_sync(0xffffffffu, c, s2);
+    d = __shfl_sync(0xffffffffu, d, s1);
+  }
+  a += c_const; b += ib; c += ic; d += id;
+  // Transpose the quad: this lane needs row g of every column k (word 4g+k).
+  // In round r it receives from lane (g + r) & 3 that lane's row g, which the
+  // sender selects as its row (own index - r) & 3.
+  uint32_t v[4];
+#pragma unroll
+  for (int r = 0; r < 4; r++) {
+    const int want = (g - r) & 3;
+    const uint32_t send = want == 0 ? a : want == 1 ? b : want == 2 ? c : d;
+    v[r] = __shfl_sync(0xffffffffu, send, base | ((g + r) & 3));
+  }
+  // v[r] is column (g + r) & 3, i.e. word 4g + ((g + r) & 3); word 4g + k is
+  // v[(k - g) & 3]
+  const int r0 = (0 - g) & 3, r1 = (1 - g) & 3, r2 = (2 - g) & 3, r3 = (3 - g) & 3;
+  auto pick = [&](int r) { return r == 0 ? v[0] : r == 1 ? v[1] : r == 2 ? v[2] : v[3]; };
+  return make_uint4(pick(r0), pick(r1), pick(r2), pick(r3));
+}
+
+// PRF(dom, x) = ChaCha20(K_prf, counter 0, nonce = dom || x)
+__device__ __forceinline__ void prf(const MapDev& m, uint32_t dom, uint64_t x, uint32_t w[16]) {
+  chacha_block(m.kprf, 0, dom, (uint32_t)x, (uint32_t)(x >> 32), w);
+}
+
+// ordered pair of distinct bins (the random remap of Sec. 3.2)
+__device__ __forceinline__ void prf_pair(const MapDev& m, uint32_t dom, uint64_t x, uint32_t& b1,
+                                         uint32_t& b2) {
+  uint32_t w[16];
+  prf(m, dom, x, w);
+  uint64_t r0 = (uint64_t)w[0] | ((uint64_t)w[1] << 32);
+  uint64_t r1 = (uint64_t)w[2] | ((uint64_t)w[3] << 32);
+  uint64_t f = mulhi64(r0, m.B);
+  uint64_t s = mulhi64(r1, m.B - 1);
+  s += (s >= f);
+  b1 = (uint32_t)f;
+  b2 = (uint32_t)s;
+}
+
+// d = 4 candidate position-map rows of a key (Sec. 4.2)
+__device__ __forceinline__ void prf_rows(const MapDev& m, uint64_t key, uint32_t rows[4]) {
+  uint32_t w[16];
+  prf(m, DOM_PM, key, w);
+#pragma unroll
+  for (int j = 0; j < 4; j++)
+    rows[j] = (uint32_t)mulhi64((uint64_t)w[2 * j] | ((uint64_t)w[2 * j + 1] << 32), m.rows);
+}
+
+// first choice with the fewest occupants, lowest index on ties
+__device__ __forceinline__ uint32_t pick_row(const MapDev& m, const uint32_t rows[4]) {
+  uint32_t best = rows[0], bc = byte_get(m.rowcnt, rows[0]);
+#pragma unroll
+  for (int j = 1; j < 4; j++) {
+    uint32_t c = byte_get(m.rowcnt, rows[j]);
+    if (c < bc) { best = rows[j]; bc = c; }
+  }
+  return best;
+}
+
+__device__ __forceinline__ void set_err(const MapDev& m, uint32_t bits) { atomicOr(m.err, bits); }
+
+// Block-wide exclusive sum (blockDim.x a multiple of 32, <= 1024); `sh`
+// holds 32 words of shared memory; `total` receives the block total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sh, uint32_t& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  total = sh[(blockDim.x >> 5) - 1];
+  uint32_t excl = x - v + (wid > 0 ? sh[wid - 1] : 0);
+  __syncthreads();
+  return excl;
+}
+
+// --- warp-level ordering of up to 32 (key, source) items ------------------
+// ascending by key; lanes without an item carry key ~0 and sort last
+__device__ __forceinline__ void warp_sort_by_key(uint64_t& key, uint32_t& src) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      uint64_t ok = __shfl_xor_sync(0xffffffffu, key, j);
+      uint32_t os = __shfl_xor_sync(0xffffffffu, src, j);
+      bool asc = (lane & k) == 0;
+      bool lower = (lane & j) == 0;
+      bool take = lower == asc ? (ok < key) : (ok > key);
+      if (take) {
+        key = ok;
+        src = os;
+      }
+    }
+  }
+}
+
+// Encrypt the plaintext page in shared memory and store it to the host page:
+// lane L handles bytes [16L, 16L+16) of each 512-byte chunk; the four lanes of
+// a quad compute the chunk's ChaCha20 block together.
+__device__ __forceinline__ void page_encrypt_store(const MapDev& m, const uint8_t* plain,
+                                                   uint64_t q, uint64_t version) {
+  const int lane = threadIdx.x & 31;
+  uint8_t* dst = m.pages + q * m.page_bytes;
+  for (uint32_t c = 0; c < m.page_bytes; c += 512) {
+    uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)version,
+                           (uint32_t)(version >> 32));
+    uint32_t off = c + 16 * lane;
+    if (off < m.page_bytes) {
+      uint4 p = *reinterpret_cast<const uint4*>(plain + off);
+      p.x ^= ks.x; p.y ^= ks.y; p.z ^= ks.z; p.w ^= ks.w;
+      *reinterpret_cast<uint4*>(dst + off) = p;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Profiling: per-kernel-class durations from CUDA events recorded on the
+// launching stream, and a count of every kernel launch.  The runtime points
+// g_prof at the handle's profiler for the duration of an ABI call.
+enum ProfClass : int {
+  P_SORT_GLOBAL = 0,  // bitonic steps with stride >= tile (HBM passes)
+  P_SORT_TILE = 1,    // bitonic in-tile steps (shared memory)
+  P_PAGE_BUILD = 2,   // build: page gather + encrypt + host store
+  P_P2C = 3,          // build: all P2C / position-map rounds
+  P_KEYCHECK = 4,     // build: key-uniqueness check
+  P_ACCESS = 5,       // one whole access batch
+  P_GATHER = 6,       // access: page read + decrypt
+  P_EVICT = 7,        // access: write-back with eviction
+  P_BUILD = 8,        // one whole build
+  P_GROUP = 9,        // access: batch grouping sort + scans
+  P_NCLASS = 10
+};
+
+struct Prof {
+  bool on = false;
+  uint64_t launches = 0;
+  struct Span { int cls; cudaEvent_t a, b; };
+  std::vector<Span> pending;
+  double ms[P_NCLASS] = {};
+  uint64_t count[P_NCLASS] = {};
+};
+extern Prof* g_prof;
+
+inline void count_launch(uint64_t n = 1) {
+  if (g_prof) g_prof->launches += n;
+}
+
+struct ProfSpan {
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  ProfSpan(int c, cudaStream_t s) : cls(c), st(s) {
+    if (g_prof && g_prof->on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+  }
+  ~ProfSpan() {
+    if (!a) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) == cudaSuccess) {
+      cudaEventRecord(b, st);
+      g_prof->pending.push_back({cls, a, b});
+    } else {
+      cudaEventDestroy(a);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// host-side launchers (defined in the .cu files)
+
+// build.cu
+cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
+                         struct BuildScratch& s, cudaStream_t st);
+
+// sort.cu: ascending bitonic sort of n_pow2 uint64 tags in place
+cudaError_t sort_tags_u64(uint64_t* tags, uint64_t n_pow2, int log_tile, cudaStream_t st);
+
+struct BuildScratch {
+  uint64_t cap = 0;        // records the buffers hold
+  uint64_t tag_cap = 0;    // tag buffer elements (power of two)
+  uint64_t* tags = nullptr;
+  uint64_t* bins = nullptr;   // per record b1 | b2 << 32
+  uint32_t* dest = nullptr;   // per record destination bin
+  uint32_t* prow = nullptr;   // per record chosen position-map row
+  uint32_t* page_off = nullptr;  // [M + 1] exclusive prefix of page loads
+  uint32_t* block_sums = nullptr;
+  uint64_t block_cap = 0;
+  unsigned long long* counters = nullptr;  // [0] value-store fill
+};
+
+}  // namespace bdev

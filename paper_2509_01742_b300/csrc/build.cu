@@ -1,0 +1,260 @@
+// build.cu -- the oblivious build (Sec. 4.2 "Fast data initialization",
+// performed on the device instead of by the data owner).
+//
+// Steps (all on the launching stream):
+//   1. rounds of W_r records: record i draws the pair PRF(INIT, i) and its
+//      d = 4 position-map rows PRF(PM, key); it picks the less-loaded bin
+//      (P2C, first choice on ties) and the least-occupied row (lowest index on
+//      ties) against the counts at the start of the round (decide kernel);
+//      then the counts are bumped with atomics, the position-map entry is
+//      written and HBM-bin records take a value-store slot (apply kernel);
+//   2. exclusive prefix sum of the host-page loads -> each page's run start;
+//   3. tag = (page << 32 | record) for host-bin records, all-ones otherwise;
+//      the tags are sorted by the bitonic network (sort.cu), which groups the
+//      records page by page;
+//   4. one warp per page gathers its run, orders it by key, pads it with zero
+//      dummy slots to lmax, encrypts it (ChaCha20, nonce = page || version 0)
+//      and writes it to the pinned host page with 16-byte coalesced stores;
+//   5. the free-slot ring receives every value-store slot not taken in 1.
+#include "bolt_internal.cuh"
+
+namespace bdev {
+
+__global__ void k_build_decide(MapDev m, const uint64_t* __restrict__ keys, uint64_t lo,
+                               uint64_t hi, uint64_t* __restrict__ bins,
+                               uint32_t* __restrict__ dest, uint32_t* __restrict__ prow) {
+  uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi) return;
+  uint32_t b1, b2;
+  prf_pair(m, DOM_INIT, i, b1, b2);
+  uint32_t l1 = byte_get(m.load, b1), l2 = byte_get(m.load, b2);
+  uint32_t rows[4];
+  prf_rows(m, keys[i], rows);
+  bins[i] = (uint64_t)b1 | ((uint64_t)b2 << 32);
+  dest[i] = l1 <= l2 ? b1 : b2;
+  prow[i] = pick_row(m, rows);
+}
+
+__global__ void k_build_apply(MapDev m, const uint64_t* __restrict__ keys,
+                              const uint8_t* __restrict__ vals, uint64_t lo, uint64_t hi,
+                              const uint64_t* __restrict__ bins, const uint32_t* __restrict__ dest,
+                              const uint32_t* __restrict__ prow, unsigned long long* vs_fill) {
+  uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi) return;
+  const uint32_t d = dest[i];
+  if (byte_inc(m.load, d) + 1 > m.lmax) {
+    set_err(m, ERR_LOAD);
+    return;
+  }
+  const uint32_t row = prow[i];
+  const uint32_t slot = byte_inc(m.rowcnt, row);
+  if (slot >= m.R) {
+    set_err(m, ERR_ROW);
+    return;
+  }
+  const uint64_t pmi = (uint64_t)row * m.R + slot;
+  const uint64_t bb = bins[i];
+  const uint32_t which = d == (uint32_t)(bb >> 32) ? 1u : 0u;
+  uint32_t meta = meta_make(LOC_HOST, which, 0);
+  if (d < m.K) {
+    unsigned long long vs = atomicAdd(vs_fill, 1ull);
+    if (vs >= m.vs_cap) {
+      set_err(m, ERR_VS);
+      return;
+    }
+    m.vs_key[vs] = keys[i];
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(vals + i * m.vb);
+    uint64_t* dst = reinterpret_cast<uint64_t*>(m.vs_val + vs * m.vb);
+    for (uint32_t w = 0; w < m.vb / 8; w++) dst[w] = src[w];
+    m.vs_pm[vs] = (uint32_t)pmi;
+    m.vs_live[vs] = 1;
+    meta = meta_make(LOC_HBM, which, (uint32_t)vs);
+  }
+  m.pm_key[pmi] = keys[i];
+  m.pm_bins[pmi] = bb;
+  m.pm_meta[pmi] = meta;
+}
+
+// tags: host-bin records -> (page << 32 | i); HBM-bin records and padding -> ~0
+__global__ void k_build_tags(MapDev m, const uint32_t* __restrict__ dest, uint64_t n,
+                             uint64_t n_pow2, uint64_t* __restrict__ tags) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pow2;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t t = ~0ull;
+    if (i < n) {
+      uint32_t d = dest[i];
+      if (d >= m.K) t = ((uint64_t)(d - m.K) << 32) | i;
+    }
+    tags[i] = t;
+  }
+}
+
+// --- exclusive prefix sum of the M page loads (u8) -> u32 run starts ------
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_ITEMS = 8;  // 8192 pages per block
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_sums(MapDev m, uint32_t* block_sums) {
+  __shared__ uint32_t sh[32];
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN_BLOCK * SCAN_ITEMS;
+  uint32_t s = 0;
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    uint64_t q = base + (uint64_t)threadIdx.x * SCAN_ITEMS + k;
+    if (q < m.M) s += byte_get(m.load, m.K + q);
+  }
+  uint32_t total;
+  block_excl_scan(s, sh, total);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// single CTA: exclusive scan of the block sums in place
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_top(uint32_t* block_sums, uint32_t nb) {
+  __shared__ uint32_t sh[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t lo = 0; lo < nb; lo += SCAN_BLOCK) {
+    uint32_t i = lo + threadIdx.x;
+    uint32_t v = i < nb ? block_sums[i] : 0;
+    uint32_t total;
+    uint32_t e = block_excl_scan(v, sh, total);
+    if (i < nb) block_sums[i] = carry + e;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_fill(MapDev m, const uint32_t* block_sums,
+                                                          uint32_t* page_off) {
+  __shared__ uint32_t sh[32];
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN_BLOCK * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS], s = 0;
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    uint64_t q = base + (uint64_t)threadIdx.x * SCAN_ITEMS + k;
+    v[k] = q < m.M ? byte_get(m.load, m.K + q) : 0;
+    s += v[k];
+  }
+  uint32_t total;
+  uint32_t e = block_excl_scan(s, sh, total) + block_sums[blockIdx.x];
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    uint64_t q = base + (uint64_t)threadIdx.x * SCAN_ITEMS + k;
+    if (q <= m.M) page_off[q] = e;  // page_off[M] = total host records
+    e += v[k];
+  }
+}
+
+// One warp per host page: gather its run of sorted tags, order by key, pad
+// with zero dummies, encrypt under version 0, store.
+__global__ void k_page_build(MapDev m, const uint64_t* __restrict__ keys,
+                             const uint8_t* __restrict__ vals, const uint64_t* __restrict__ tags,
+                             const uint32_t* __restrict__ page_off, uint32_t warps_per_block) {
+  extern __shared__ __align__(16) uint8_t sbuf[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint8_t* plain = sbuf + (size_t)wid * m.page_bytes;
+  const uint64_t stride = (uint64_t)gridDim.x * warps_per_block;
+  for (uint64_t q = (uint64_t)blockIdx.x * warps_per_block + wid; q < m.M; q += stride) {
+    const uint32_t cnt = byte_get(m.load, m.K + q);
+    const uint32_t off = page_off[q];
+    uint64_t key = ~0ull;
+    uint32_t src = NONE32;
+    if (lane < (int)cnt) {
+      uint64_t t = tags[off + lane];
+      if ((t >> 32) != q) {
+        set_err(m, ERR_PAGE);  // counts and sorted tags disagree
+      } else {
+        src = (uint32_t)t;
+        key = keys[src];
+      }
+    }
+    if (cnt > 32 || cnt > m.lmax) set_err(m, ERR_PAGE);
+    warp_sort_by_key(key, src);
+    for (uint32_t o = 16 * lane; o < m.page_bytes; o += 512)
+      *reinterpret_cast<uint4*>(plain + o) = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+    if (lane == 0) {
+      uint64_t bitmap = cnt >= 64 ? ~0ull : ((1ull << cnt) - 1);
+      *reinterpret_cast<uint64_t*>(plain) = bitmap;
+    }
+    if (lane < (int)cnt && lane < (int)m.lmax && src != NONE32) {
+      uint8_t* slot = plain + 16 + (size_t)lane * m.rec;
+      *reinterpret_cast<uint64_t*>(slot) = key;
+      const uint64_t* vsrc = reinterpret_cast<const uint64_t*>(vals + (uint64_t)src * m.vb);
+      for (uint32_t w = 0; w < m.vb / 8; w++)
+        reinterpret_cast<uint64_t*>(slot + 8)[w] = vsrc[w];
+    }
+    __syncwarp();
+    page_encrypt_store(m, plain, q, 0);
+    __syncwarp();
+  }
+}
+
+__global__ void k_ring_fill(MapDev m, const unsigned long long* vs_fill) {
+  const uint64_t used = *vs_fill < m.vs_cap ? *vs_fill : m.vs_cap;
+  const uint64_t nfree = m.vs_cap - used;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nfree;
+       j += (uint64_t)gridDim.x * blockDim.x)
+    m.ring[j] = (uint32_t)(used + j);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    m.ring_ctr[0] = 0;
+    m.ring_ctr[1] = nfree;
+  }
+}
+
+static int sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
+                         BuildScratch& s, cudaStream_t st) {
+  const int sms = sm_count();
+  cudaMemsetAsync(s.counters, 0, 2 * sizeof(unsigned long long), st);
+  // 1. P2C + position map, round by round
+  {
+    ProfSpan ps(P_P2C, st);
+    for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+      uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
+      unsigned g = (unsigned)((hi - lo + 255) / 256);
+      k_build_decide<<<g, 256, 0, st>>>(m, keys, lo, hi, s.bins, s.dest, s.prow);
+      k_build_apply<<<g, 256, 0, st>>>(m, keys, vals, lo, hi, s.bins, s.dest, s.prow,
+                                        s.counters);
+      count_launch(2);
+    }
+  }
+  // 2. page run starts
+  const uint32_t nblocks = (uint32_t)((m.M + 1 + SCAN_BLOCK * SCAN_ITEMS - 1) /
+                                      (SCAN_BLOCK * SCAN_ITEMS));
+  k_scan_sums<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums);
+  k_scan_top<<<1, SCAN_BLOCK, 0, st>>>(s.block_sums, nblocks);
+  k_scan_fill<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums, s.page_off);
+  // 3. tags + bitonic sort
+  k_build_tags<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.tag_cap, s.tags);
+  count_launch(4);
+  cudaError_t e = sort_tags_u64(s.tags, s.tag_cap, 13, st);
+  if (e != cudaSuccess) return e;
+  // 4. pages
+  uint32_t wpb = (uint32_t)(65536 / m.page_bytes);
+  wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;
+  size_t smem = (size_t)wpb * m.page_bytes;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_page_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  uint64_t blocks = (m.M + wpb - 1) / wpb;
+  uint64_t cap = (uint64_t)sms * 32;
+  {
+    ProfSpan ps(P_PAGE_BUILD, st);
+    k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
+        m, keys, vals, s.tags, s.page_off, wpb);
+    count_launch();
+  }
+  // 5. free ring
+  k_ring_fill<<<sms * 4, 256, 0, st>>>(m, s.counters);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace bdev

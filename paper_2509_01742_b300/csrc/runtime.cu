@@ -1,0 +1,724 @@
+// runtime.cu -- host runtime behind the C ABI of include/bolt.h.
+//
+// Owns the planner (Sec. 3.3 sizing and the alpha policy of "Parameters
+// selection"), every device allocation, the pinned device-mapped host pages
+// (Sec. 4.1 step 1: the host provisions pinned memory the accelerator reaches
+// directly), the batch staging buffers, and the error / poison state.  All
+// arithmetic of the method runs in the kernels of build.cu, sort.cu and
+// access.cu; this file only plans, allocates, copies and launches.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "batch.cuh"
+#include "bolt_internal.cuh"
+
+using namespace bdev;
+
+namespace bdev {
+Prof* g_prof = nullptr;
+}
+
+namespace {
+
+constexpr uint32_t MAXB = BOLT_MAX_BATCH;
+
+struct Plan {
+  bolt_info_t info;
+};
+
+// Claim 3.2: lmax = c + ceil(log2 log2 N) + 1 (constant 1 in the O-term, as
+// in Sec. 3.3); Claims 3.3 / 3.4 with constant 1; position map of
+// ceil(N/16) rows holding 16 + ceil(log2 log2 N / log2 d) keys (Sec. 4.2).
+int plan_sizes(uint64_t N, uint32_t c, double alpha, uint32_t vb, bolt_info_t* o) {
+  if (N < 64 || c < 1 || alpha < 0.0 || alpha >= 1.0) return BOLT_E_ARG;
+  std::memset(o, 0, sizeof *o);
+  const double llg = std::log2(std::log2((double)N));
+  o->N = N;
+  o->c = c;
+  o->d = 4;
+  o->key_bytes = 8;
+  o->val_bytes = vb;
+  o->lmax = c + (uint32_t)std::ceil(llg) + 1;
+  o->R = 16 + (uint32_t)std::ceil(llg / 2.0);
+  o->rows = (N + 15) / 16;
+  o->B = (N + c - 1) / c;
+  o->alpha = alpha;
+  o->K = (uint64_t)std::floor(alpha * (double)o->B);
+  o->M = o->B - o->K;
+  if (o->M < 2 || o->lmax > 32 || o->R > 32) return BOLT_E_ARG;
+  const double lnN = std::log((double)N);
+  o->beta1 = (double)o->K * c + o->lmax * std::sqrt((double)o->K * lnN);
+  o->beta2 = (1.0 + alpha) * (double)o->M / 2.0 + o->lmax * std::sqrt((double)o->M * lnN);
+  // Claims 3.3/3.4 bound one-at-a-time access; one batch can add up to a
+  // batch of remapped keys to the stash before their pages are read again.
+  o->vs_cap = (uint64_t)std::ceil(o->beta1 + o->beta2) + (N < MAXB ? N : MAXB);
+  o->round_width = o->B / 256 > 0 ? o->B / 256 : 1;
+  o->rec_bytes = 8 + vb;
+  o->page_bytes = (16 + o->lmax * o->rec_bytes + 63) / 64 * 64;
+  if (o->vs_cap >= (1ull << 29) || o->rows * o->R >= (1ull << 32)) return BOLT_E_ARG;
+  return BOLT_OK;
+}
+
+}  // namespace
+
+struct bolt {
+  uint64_t N = 0;
+  uint32_t vb = 0;
+  uint64_t hbm_budget = 0;
+  double alpha_override = -1.0;
+  uint32_t c = 8;
+  uint32_t batch_width = MAXB;
+  uint64_t trace_cap = 1ull << 22;
+  bool trace_on = false;
+  bool check_keys = true;
+  bolt_info_t info{};
+
+  MapDev m{};
+  BatchDev b{};
+  BuildScratch bs{};
+  cudaStream_t st = nullptr;
+  uint8_t* pages_host = nullptr;
+  std::vector<void*> dev_allocs;  // state + batch buffers (freed by free_state)
+
+  // host-pointer staging
+  uint64_t* in_keys = nullptr;
+  uint8_t* in_vals = nullptr;
+  uint64_t in_cap = 0;
+  uint8_t* h_ops = nullptr;
+  uint64_t* h_keys = nullptr;
+  uint8_t* h_vin = nullptr;
+  uint8_t* h_vout = nullptr;
+  uint8_t* h_status = nullptr;
+  uint32_t* h_err = nullptr;
+  uint32_t* d_kdf = nullptr;
+  uint32_t* d_flag = nullptr;
+
+  uint64_t t = 0, batches = 0;
+  bool allocated = false, initialized = false, poisoned = false;
+  Prof prof;
+  cudaStream_t last_st = nullptr;  // stream of the last enqueued work
+};
+
+namespace {
+// points the kernel-side profiler at the handle for one ABI call
+struct ProfScope {
+  explicit ProfScope(bolt* h) { g_prof = &h->prof; }
+  ~ProfScope() { g_prof = nullptr; }
+};
+}  // namespace
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return BOLT_OK;
+  if (e == cudaErrorMemoryAllocation) return BOLT_E_NOMEM;
+  return BOLT_E_CUDA;
+}
+
+// wait for the handle's own stream and for the caller stream it last used
+cudaError_t sync_all(bolt* h) {
+  cudaError_t e = cudaSuccess;
+  if (h->last_st && h->last_st != h->st) e = cudaStreamSynchronize(h->last_st);
+  if (h->st) {
+    cudaError_t e2 = cudaStreamSynchronize(h->st);
+    if (e == cudaSuccess) e = e2;
+  }
+  return e;
+}
+
+template <typename T>
+int dalloc(bolt* h, T** p, uint64_t count) {
+  void* ptr = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e);
+  h->dev_allocs.push_back(ptr);
+  *p = static_cast<T*>(ptr);
+  return BOLT_OK;
+}
+
+void free_build_scratch(bolt* h) {
+  BuildScratch& s = h->bs;
+  cudaFree(s.tags); cudaFree(s.bins); cudaFree(s.dest); cudaFree(s.prow);
+  cudaFree(s.page_off); cudaFree(s.block_sums); cudaFree(s.counters);
+  s = BuildScratch{};
+  cudaFree(h->in_keys); cudaFree(h->in_vals);
+  h->in_keys = nullptr; h->in_vals = nullptr; h->in_cap = 0;
+}
+
+void free_state(bolt* h) {
+  sync_all(h);
+  h->last_st = nullptr;
+  for (void* p : h->dev_allocs) cudaFree(p);
+  h->dev_allocs.clear();
+  if (h->pages_host) cudaFreeHost(h->pages_host);
+  h->pages_host = nullptr;
+  free_build_scratch(h);
+  h->m = MapDev{};
+  h->b = BatchDev{};
+  h->allocated = false;
+  h->initialized = false;
+}
+
+int choose_plan(bolt* h, bolt_info_t* o) {
+  if (h->alpha_override >= 0.0) return plan_sizes(h->N, h->c, h->alpha_override, h->vb, o);
+  static const double grid[] = {0.2, 0.1, 0.05, 0.01, 0.0};
+  for (double a : grid) {
+    int rc = plan_sizes(h->N, h->c, a, h->vb, o);
+    if (rc) return rc;
+    if ((double)o->vs_cap * (double)(8 + h->vb) <= (double)h->hbm_budget) return BOLT_OK;
+  }
+  return BOLT_E_NOMEM;
+}
+
+int alloc_state(bolt* h) {
+  int rc = choose_plan(h, &h->info);
+  if (rc) return rc;
+  const bolt_info_t& I = h->info;
+  MapDev& m = h->m;
+  m.N = I.N; m.B = I.B; m.K = I.K; m.M = I.M; m.rows = I.rows; m.Wr = I.round_width;
+  m.vs_cap = I.vs_cap; m.R = I.R; m.lmax = I.lmax; m.vb = I.val_bytes; m.rec = I.rec_bytes;
+  m.page_bytes = I.page_bytes;
+  const uint64_t slots = I.rows * I.R;
+#define TRY(x) do { int r_ = (x); if (r_) { free_state(h); return r_; } } while (0)
+  TRY(dalloc(h, &m.load, I.B / 4 + 2));
+  TRY(dalloc(h, &m.rowcnt, I.rows / 4 + 2));
+  TRY(dalloc(h, &m.pm_key, slots));
+  TRY(dalloc(h, &m.pm_bins, slots));
+  TRY(dalloc(h, &m.pm_meta, slots));
+  TRY(dalloc(h, &m.vs_key, I.vs_cap));
+  TRY(dalloc(h, &m.vs_val, I.vs_cap * I.val_bytes));
+  TRY(dalloc(h, &m.vs_pm, I.vs_cap));
+  TRY(dalloc(h, &m.vs_live, I.vs_cap));
+  TRY(dalloc(h, &m.ring, I.vs_cap));
+  TRY(dalloc(h, &m.ring_ctr, 2));
+  TRY(dalloc(h, &m.rev, I.M * I.lmax));
+  TRY(dalloc(h, &m.revcnt, I.M / 4 + 2));
+  TRY(dalloc(h, &m.version, I.M));
+  TRY(dalloc(h, &m.err, 1));
+  TRY(dalloc(h, &m.trace, h->trace_cap));
+  TRY(dalloc(h, &m.trace_len, 1));
+  m.trace_cap = h->trace_cap;
+  m.trace_on = h->trace_on ? 1 : 0;
+  void* hp = nullptr;
+  cudaError_t e = cudaHostAlloc(&hp, I.M * I.page_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+  if (e != cudaSuccess) { free_state(h); return BOLT_E_NOMEM; }
+  h->pages_host = static_cast<uint8_t*>(hp);
+  void* dp = nullptr;
+  e = cudaHostGetDevicePointer(&dp, hp, 0);
+  if (e != cudaSuccess) { free_state(h); return BOLT_E_CUDA; }
+  m.pages = static_cast<uint8_t*>(dp);
+  // batch buffers
+  BatchDev& b = h->b;
+  const uint64_t vb = I.val_bytes;
+  TRY(dalloc(h, &b.ops, MAXB));
+  TRY(dalloc(h, &b.keys, MAXB));
+  TRY(dalloc(h, &b.vin, MAXB * vb));
+  TRY(dalloc(h, &b.vout, MAXB * vb));
+  TRY(dalloc(h, &b.status, MAXB));
+  TRY(dalloc(h, &b.sortbuf, MAXB));
+  TRY(dalloc(h, &b.leader, MAXB));
+  TRY(dalloc(h, &b.prevw, MAXB));
+  TRY(dalloc(h, &b.lastw, MAXB));
+  TRY(dalloc(h, &b.pair, MAXB));
+  TRY(dalloc(h, &b.rpair, MAXB));
+  TRY(dalloc(h, &b.rows, 4ull * MAXB));
+  TRY(dalloc(h, &b.hit, MAXB));
+  TRY(dalloc(h, &b.pos_page, 2ull * MAXB));
+  TRY(dalloc(h, &b.pos_slot, 2ull * MAXB));
+  TRY(dalloc(h, &b.pos_d, 2ull * MAXB));
+  const uint32_t ht = 4 * MAXB;
+  b.ht_mask = ht - 1;
+  TRY(dalloc(h, &b.ht_key, ht));
+  TRY(dalloc(h, &b.ht_min, ht));
+  TRY(dalloc(h, &b.ht_d, ht));
+  TRY(dalloc(h, &b.dpage, 2ull * MAXB));
+  TRY(dalloc(h, &b.dcount, 1));
+  TRY(dalloc(h, &b.dbuf, 2ull * MAXB * I.page_bytes));
+  TRY(dalloc(h, &b.removed, 2ull * MAXB));
+  TRY(dalloc(h, &b.init_val, MAXB * vb));
+  TRY(dalloc(h, &b.init_present, MAXB));
+  TRY(dalloc(h, &b.rval, MAXB * vb));
+  TRY(dalloc(h, &b.fpres, MAXB));
+  TRY(dalloc(h, &b.rdest, MAXB));
+  TRY(dalloc(h, &b.rrow, MAXB));
+  TRY(dalloc(h, &h->d_kdf, 16));
+  TRY(dalloc(h, &h->d_flag, 1));
+#undef TRY
+  h->allocated = true;
+  return BOLT_OK;
+}
+
+int grow_build_scratch(bolt* h, uint64_t n) {
+  BuildScratch& s = h->bs;
+  uint64_t tag_cap = 8192;
+  while (tag_cap < n) tag_cap <<= 1;
+  const uint64_t nblocks = (h->info.M + 1 + 8192 - 1) / 8192 + 1;
+  if (s.cap >= n && s.tag_cap >= tag_cap && s.block_cap >= nblocks && s.page_off) return BOLT_OK;
+  cudaStreamSynchronize(h->st);
+  cudaFree(s.tags); cudaFree(s.bins); cudaFree(s.dest); cudaFree(s.prow);
+  cudaFree(s.page_off); cudaFree(s.block_sums); cudaFree(s.counters);
+  s = BuildScratch{};
+  const uint64_t cap = n > 0 ? n : 1;
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMalloc(&s.tags, tag_cap * sizeof(uint64_t));
+  e = e ? e : cudaMalloc(&s.bins, cap * sizeof(uint64_t));
+  e = e ? e : cudaMalloc(&s.dest, cap * sizeof(uint32_t));
+  e = e ? e : cudaMalloc(&s.prow, cap * sizeof(uint32_t));
+  e = e ? e : cudaMalloc(&s.page_off, (h->info.M + 1) * sizeof(uint32_t));
+  e = e ? e : cudaMalloc(&s.block_sums, nblocks * sizeof(uint32_t));
+  e = e ? e : cudaMalloc(&s.counters, 2 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    cudaFree(s.tags); cudaFree(s.bins); cudaFree(s.dest); cudaFree(s.prow);
+    cudaFree(s.page_off); cudaFree(s.block_sums); cudaFree(s.counters);
+    s = BuildScratch{};
+    return cuda_fail(e);
+  }
+  s.cap = cap;
+  s.tag_cap = tag_cap;
+  s.block_cap = nblocks;
+  return BOLT_OK;
+}
+
+// KDF: ChaCha20 block under the 256-bit key seed || 0^192, nonce "BOLT" || 0;
+// words 0-7 -> K_prf, words 8-15 -> K_enc.
+__global__ void k_kdf(uint64_t seed, uint32_t* out) {
+  const uint32_t key[8] = {(uint32_t)seed, (uint32_t)(seed >> 32), 0, 0, 0, 0, 0, 0};
+  uint32_t w[16];
+  chacha_block(key, 0, 0x544c4f42u, 0, 0, w);
+  for (int i = 0; i < 16; i++) out[i] = w[i];
+}
+
+// keys must be distinct (Sec. 2.1): sort a copy, flag equal neighbours
+__global__ void k_copy_keys(const uint64_t* keys, uint64_t n, uint64_t n_pow2, uint64_t* out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pow2;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = i < n ? keys[i] : ~0ull;
+}
+__global__ void k_adjacent_equal(const uint64_t* sorted, uint64_t n, uint32_t* flag) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    if (sorted[i] == sorted[i - 1]) *flag = 1;
+}
+
+int sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+int read_err(bolt* h, uint32_t* out) {
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  cudaError_t e = cudaMemcpyAsync(h->h_err, h->m.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return BOLT_E_CUDA;
+  *out = *h->h_err;
+  return BOLT_OK;
+}
+
+int err_to_rc(uint32_t err) {
+  if (err & ERR_OVERFLOW_MASK) return BOLT_E_OVERFLOW;
+  if (err & ERR_TIMEOUT) return BOLT_E_TIMEOUT;
+  if (err) return BOLT_E_INTERNAL;
+  return BOLT_OK;
+}
+
+int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n, uint64_t seed,
+              cudaStream_t st) {
+  MapDev& m = h->m;
+  const bolt_info_t& I = h->info;
+  int rc = grow_build_scratch(h, n);
+  if (rc) return rc;
+  h->initialized = false;
+  h->poisoned = false;
+  ProfSpan whole(P_BUILD, st);
+  const int sms = sm_count();
+  // reset the map state
+  cudaMemsetAsync(m.load, 0, (I.B / 4 + 2) * 4, st);
+  cudaMemsetAsync(m.rowcnt, 0, (I.rows / 4 + 2) * 4, st);
+  cudaMemsetAsync(m.pm_meta, 0, I.rows * I.R * 4, st);
+  cudaMemsetAsync(m.vs_live, 0, I.vs_cap, st);
+  cudaMemsetAsync(m.revcnt, 0, (I.M / 4 + 2) * 4, st);
+  cudaMemsetAsync(m.version, 0, I.M * 8, st);
+  cudaMemsetAsync(m.err, 0, 4, st);
+  cudaMemsetAsync(m.trace_len, 0, 8, st);
+  // keys -> K_prf, K_enc
+  k_kdf<<<1, 1, 0, st>>>(seed, h->d_kdf);
+  count_launch();
+  uint32_t kw[16];
+  cudaError_t e = cudaMemcpyAsync(kw, h->d_kdf, sizeof kw, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return BOLT_E_CUDA;
+  for (int i = 0; i < 8; i++) {
+    m.kprf[i] = kw[i];
+    m.kenc[i] = kw[8 + i];
+  }
+  if (h->check_keys && n > 1) {
+    ProfSpan ps(P_KEYCHECK, st);
+    k_copy_keys<<<sms * 8, 256, 0, st>>>(d_keys, n, h->bs.tag_cap, h->bs.tags);
+    count_launch(2);
+    e = sort_tags_u64(h->bs.tags, h->bs.tag_cap, 13, st);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+    cudaMemsetAsync(h->d_flag, 0, 4, st);
+    k_adjacent_equal<<<sms * 8, 256, 0, st>>>(h->bs.tags, n, h->d_flag);
+    uint32_t flag = 0;
+    e = cudaMemcpyAsync(&flag, h->d_flag, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+    if (flag) return BOLT_E_DUPKEY;
+  }
+  e = launch_build(m, d_keys, d_vals, n, h->bs, st);
+  if (e != cudaSuccess) return BOLT_E_CUDA;
+  uint32_t err = 0;
+  h->last_st = st;
+  rc = read_err(h, &err);
+  if (rc) return rc;
+  rc = err_to_rc(err);
+  if (rc) {
+    h->poisoned = true;
+    return rc;
+  }
+  h->t = 0;
+  h->batches = 0;
+  h->initialized = true;
+  return BOLT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bolt_strerror(int code) {
+  switch (code) {
+    case BOLT_OK: return "ok";
+    case BOLT_E_ARG: return "invalid argument";
+    case BOLT_E_NOMEM: return "out of device or pinned host memory (or HBM budget too small)";
+    case BOLT_E_OVERFLOW: return "capacity bound exceeded (map poisoned until re-init)";
+    case BOLT_E_STATE: return "map not initialised or poisoned";
+    case BOLT_E_DUPKEY: return "duplicate keys in bolt_init";
+    case BOLT_E_CUDA: return "CUDA runtime error";
+    case BOLT_E_TIMEOUT: return "bounded device wait timed out";
+    case BOLT_E_INTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+  }
+}
+
+int bolt_plan(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm_budget,
+              double alpha, uint32_t c, bolt_info_t* out) {
+  if (!out || key_bytes != 8 || val_bytes < 8 || val_bytes % 8 || val_bytes > 504 || N < 64 ||
+      N > (1ull << 31) || c < 1 || c > 24)
+    return BOLT_E_ARG;
+  bolt tmp;
+  tmp.N = N;
+  tmp.vb = val_bytes;
+  tmp.hbm_budget = hbm_budget;
+  tmp.alpha_override = alpha;
+  tmp.c = c;
+  return choose_plan(&tmp, out);
+}
+
+int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm_budget,
+                bolt_t** out) {
+  if (!out || key_bytes != 8 || val_bytes < 8 || val_bytes % 8 || val_bytes > 504 || N < 64 ||
+      N > (1ull << 31))
+    return BOLT_E_ARG;
+  *out = nullptr;
+  bolt* h = new (std::nothrow) bolt();
+  if (!h) return BOLT_E_NOMEM;
+  h->N = N;
+  h->vb = val_bytes;
+  h->hbm_budget = hbm_budget;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete h;
+    return BOLT_E_CUDA;
+  }
+  void* p = nullptr;
+  e = cudaHostAlloc(&p, MAXB * (1 + 8 + 2 * (uint64_t)val_bytes + 1) + 64, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(h->st);
+    delete h;
+    return BOLT_E_NOMEM;
+  }
+  uint8_t* q = static_cast<uint8_t*>(p);
+  h->h_keys = reinterpret_cast<uint64_t*>(q); q += MAXB * 8;
+  h->h_vin = q; q += (uint64_t)MAXB * val_bytes;
+  h->h_vout = q; q += (uint64_t)MAXB * val_bytes;
+  h->h_ops = q; q += MAXB;
+  h->h_status = q; q += MAXB;
+  h->h_err = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
+  int rc = alloc_state(h);
+  if (rc) {
+    cudaFreeHost(h->h_keys);
+    cudaStreamDestroy(h->st);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return BOLT_OK;
+}
+
+int bolt_destroy(bolt_t* h) {
+  if (!h) return BOLT_OK;
+  free_state(h);
+  if (h->h_keys) cudaFreeHost(h->h_keys);
+  if (h->st) cudaStreamDestroy(h->st);
+  delete h;
+  return BOLT_OK;
+}
+
+int bolt_set_param(bolt_t* h, int which, double v) {
+  if (!h) return BOLT_E_ARG;
+  switch (which) {
+    case BOLT_PARAM_ALPHA:
+      if (!(v >= 0.0 && v < 1.0)) return BOLT_E_ARG;
+      h->alpha_override = v;
+      break;
+    case BOLT_PARAM_C:
+      if (!(v >= 1.0 && v <= 24.0)) return BOLT_E_ARG;
+      h->c = (uint32_t)v;
+      break;
+    case BOLT_PARAM_TRACE:
+      h->trace_on = v != 0.0;
+      h->m.trace_on = h->trace_on ? 1 : 0;
+      return BOLT_OK;
+    case BOLT_PARAM_BATCH:
+      if (!(v >= 1.0 && v <= (double)MAXB)) return BOLT_E_ARG;
+      h->batch_width = (uint32_t)v;
+      return BOLT_OK;
+    case BOLT_PARAM_TRACE_CAP:
+      if (!(v >= 1.0 && v <= (double)(1ull << 32))) return BOLT_E_ARG;
+      h->trace_cap = (uint64_t)v;
+      break;
+    case BOLT_PARAM_CHECK_KEYS:
+      h->check_keys = v != 0.0;
+      return BOLT_OK;
+    case BOLT_PARAM_PROFILE:
+      h->prof.on = v != 0.0;
+      return BOLT_OK;
+    default:
+      return BOLT_E_ARG;
+  }
+  free_state(h);
+  return alloc_state(h);
+}
+
+int bolt_get_info(const bolt_t* h, bolt_info_t* out) {
+  if (!h || !out) return BOLT_E_ARG;
+  *out = h->info;
+  return BOLT_OK;
+}
+
+int bolt_init_device(bolt_t* h, const void* d_keys, const void* d_vals, uint64_t n, uint64_t seed,
+                     void* stream) {
+  if (!h || !h->allocated || n > h->N || (n && (!d_keys || !d_vals))) return BOLT_E_ARG;
+  ProfScope prof_scope(h);
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
+  return init_impl(h, static_cast<const uint64_t*>(d_keys), static_cast<const uint8_t*>(d_vals), n,
+                   seed, st);
+}
+
+int bolt_init(bolt_t* h, const void* keys, const void* vals, uint64_t n, uint64_t seed) {
+  if (!h || !h->allocated || n > h->N || (n && (!keys || !vals))) return BOLT_E_ARG;
+  ProfScope prof_scope(h);
+  const uint64_t cap = n > 0 ? n : 1;
+  if (h->in_cap < cap) {
+    cudaFree(h->in_keys);
+    cudaFree(h->in_vals);
+    h->in_keys = nullptr;
+    h->in_vals = nullptr;
+    h->in_cap = 0;
+    cudaError_t e = cudaMalloc(&h->in_keys, cap * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&h->in_vals, cap * h->vb);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->in_cap = cap;
+  }
+  if (n) {
+    cudaError_t e = cudaMemcpyAsync(h->in_keys, keys, n * 8, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->in_vals, vals, n * h->vb, cudaMemcpyHostToDevice, h->st);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+  }
+  return init_impl(h, h->in_keys, h->in_vals, n, seed, h->st);
+}
+
+int bolt_sync(bolt_t* h) {
+  if (!h) return BOLT_E_ARG;
+  uint32_t err = 0;
+  int rc = read_err(h, &err);
+  if (rc) return rc;
+  rc = err_to_rc(err);
+  if (rc) h->poisoned = true;
+  return rc;
+}
+
+int bolt_access_device(bolt_t* h, const uint8_t* d_ops, const void* d_keys, const void* d_vals_in,
+                       void* d_vals_out, uint8_t* d_status, uint64_t n, void* stream) {
+  if (!h) return BOLT_E_ARG;
+  if (!h->initialized || h->poisoned) return BOLT_E_STATE;
+  if (n == 0) return BOLT_OK;
+  if (n > MAXB || !d_ops || !d_keys || !d_vals_in || !d_vals_out) return BOLT_E_ARG;
+  ProfScope prof_scope(h);
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
+  BatchDev b = h->b;
+  b.ops = const_cast<uint8_t*>(d_ops);
+  b.keys = static_cast<uint64_t*>(const_cast<void*>(d_keys));
+  b.vin = static_cast<uint8_t*>(const_cast<void*>(d_vals_in));
+  b.vout = static_cast<uint8_t*>(d_vals_out);
+  if (d_status) b.status = d_status;
+  if (h->last_st != st) {
+    // order this batch after work the handle left on another stream
+    if (h->last_st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+    h->last_st = st;
+  }
+  cudaError_t e = launch_access(h->m, b, (uint32_t)n, h->t, st);
+  if (e != cudaSuccess) return BOLT_E_CUDA;
+  h->t += n;
+  h->batches++;
+  return BOLT_OK;
+}
+
+int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* vals_in,
+                void* vals_out, uint8_t* status_out, uint64_t n) {
+  if (!h) return BOLT_E_ARG;
+  if (!h->initialized || h->poisoned) return BOLT_E_STATE;
+  if (n == 0) return BOLT_OK;
+  if (!ops || !keys || !vals_in || !vals_out) return BOLT_E_ARG;
+  for (uint64_t i = 0; i < n; i++)
+    if (ops[i] > BOLT_DEL) return BOLT_E_ARG;
+  ProfScope prof_scope(h);
+  const uint64_t vb = h->vb;
+  const uint8_t* kin = static_cast<const uint8_t*>(keys);
+  const uint8_t* vin = static_cast<const uint8_t*>(vals_in);
+  uint8_t* vout = static_cast<uint8_t*>(vals_out);
+  if (h->last_st != h->st) {
+    if (h->last_st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+    h->last_st = h->st;
+  }
+  for (uint64_t lo = 0; lo < n; lo += h->batch_width) {
+    const uint64_t cnt = n - lo < h->batch_width ? n - lo : h->batch_width;
+    std::memcpy(h->h_ops, ops + lo, cnt);
+    std::memcpy(h->h_keys, kin + lo * 8, cnt * 8);
+    std::memcpy(h->h_vin, vin + lo * vb, cnt * vb);
+    cudaError_t e = cudaMemcpyAsync(h->b.ops, h->h_ops, cnt, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->b.keys, h->h_keys, cnt * 8, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->b.vin, h->h_vin, cnt * vb, cudaMemcpyHostToDevice, h->st);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+    e = launch_access(h->m, h->b, (uint32_t)cnt, h->t, h->st);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+    h->t += cnt;
+    h->batches++;
+    e = cudaMemcpyAsync(h->h_vout, h->b.vout, cnt * vb, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->h_status, h->b.status, cnt, cudaMemcpyDeviceToHost, h->st);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+    int rc = bolt_sync(h);
+    if (rc) return rc;
+    std::memcpy(vout + lo * vb, h->h_vout, cnt * vb);
+    if (status_out) std::memcpy(status_out + lo, h->h_status, cnt);
+  }
+  return BOLT_OK;
+}
+
+int bolt_read_pages(bolt_t* h, uint64_t first, uint64_t count, void* dst) {
+  if (!h || !h->allocated || !dst || first > h->info.M || count > h->info.M - first)
+    return BOLT_E_ARG;
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  std::memcpy(dst, h->pages_host + first * h->info.page_bytes, count * h->info.page_bytes);
+  return BOLT_OK;
+}
+
+int bolt_read_trace(bolt_t* h, uint32_t* dst, uint64_t cap, uint64_t* len) {
+  if (!h || !h->allocated || !len || (cap && !dst)) return BOLT_E_ARG;
+  unsigned long long tl = 0;
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  cudaError_t e = cudaMemcpyAsync(&tl, h->m.trace_len, 8, cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return BOLT_E_CUDA;
+  uint64_t stored = tl < h->m.trace_cap ? tl : h->m.trace_cap;
+  uint64_t ncopy = stored < cap ? stored : cap;
+  if (ncopy) {
+    e = cudaMemcpy(dst, h->m.trace, ncopy * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+  }
+  *len = tl;  // may exceed the capacity: entries beyond it were dropped
+  cudaMemsetAsync(h->m.trace_len, 0, 8, h->st);
+  if (cudaStreamSynchronize(h->st) != cudaSuccess) return BOLT_E_CUDA;
+  return BOLT_OK;
+}
+
+int bolt_read_loads(bolt_t* h, uint8_t* dst) {
+  if (!h || !h->allocated || !dst) return BOLT_E_ARG;
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  return cudaMemcpy(dst, h->m.load, h->info.B, cudaMemcpyDeviceToHost) == cudaSuccess
+             ? BOLT_OK : BOLT_E_CUDA;
+}
+
+int bolt_read_rowcounts(bolt_t* h, uint8_t* dst) {
+  if (!h || !h->allocated || !dst) return BOLT_E_ARG;
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  return cudaMemcpy(dst, h->m.rowcnt, h->info.rows, cudaMemcpyDeviceToHost) == cudaSuccess
+             ? BOLT_OK : BOLT_E_CUDA;
+}
+
+int bolt_read_profile(bolt_t* h, bolt_profile_t* out, int reset) {
+  if (!h || !out) return BOLT_E_ARG;
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  Prof& p = h->prof;
+  for (const Prof::Span& s : p.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(s.b) == cudaSuccess && cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) {
+      p.ms[s.cls] += ms;
+      p.count[s.cls] += 1;
+    }
+    cudaEventDestroy(s.a);
+    cudaEventDestroy(s.b);
+  }
+  p.pending.clear();
+  std::memset(out, 0, sizeof *out);
+  out->launches = p.launches;
+  for (int c = 0; c < BOLT_PROF_CLASSES && c < P_NCLASS; c++) {
+    out->spans[c] = p.count[c];
+    out->ms[c] = p.ms[c];
+  }
+  if (reset) {
+    p.launches = 0;
+    for (int c = 0; c < P_NCLASS; c++) {
+      p.ms[c] = 0.0;
+      p.count[c] = 0;
+    }
+  }
+  return BOLT_OK;
+}
+
+int bolt_get_stats(bolt_t* h, bolt_stats_t* out) {
+  if (!h || !out) return BOLT_E_ARG;
+  std::memset(out, 0, sizeof *out);
+  out->ops = h->t;
+  out->batches = h->batches;
+  if (!h->allocated) return BOLT_OK;
+  const bolt_info_t& I = h->info;
+  std::vector<uint8_t> loads(I.B), rows(I.rows), rc(I.M);
+  if (bolt_read_loads(h, loads.data()) || bolt_read_rowcounts(h, rows.data())) return BOLT_E_CUDA;
+  if (cudaMemcpy(rc.data(), h->m.revcnt, I.M, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BOLT_E_CUDA;
+  for (uint64_t b = 0; b < I.B; b++) {
+    if (b < I.K) out->n_hbm += loads[b];
+    if (loads[b] > out->max_load) out->max_load = loads[b];
+  }
+  for (uint64_t r = 0; r < I.rows; r++)
+    if (rows[r] > out->max_row) out->max_row = rows[r];
+  for (uint64_t q = 0; q < I.M; q++) out->n_stash += rc[q];
+  unsigned long long tl = 0;
+  cudaMemcpy(&tl, h->m.trace_len, 8, cudaMemcpyDeviceToHost);
+  out->trace_len = tl;
+  return BOLT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+"""The C-ABI library loads, exports every entry point its header declares,
+and its host-only planner agrees with the oracle's sizing (no GPU needed)."""
+import os
+import re
+
+import pytest
+
+from oracle import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "bolt.h")).read()
+    return sorted(set(re.findall(r"BOLT_API\s+(?:const\s+)?\w+\*?\s+(bolt_\w+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2509_01742_b300 import bolt as B
+    names = _declared()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(B._lib, name), name
+    assert sorted(B.EXPORTED) == names
+
+
+def test_strerror_and_codes():
+    from paper_2509_01742_b300 import bolt as B
+    assert B.bolt_strerror(B.BOLT_OK) == b"ok"
+    assert b"poisoned" in B.bolt_strerror(B.BOLT_E_OVERFLOW)
+    assert (B.BOLT_E_ARG, B.BOLT_E_NOMEM, B.BOLT_E_OVERFLOW, B.BOLT_E_STATE, B.BOLT_E_DUPKEY) == \
+        (O.E_ARG, O.E_NOMEM, O.E_OVERFLOW, O.E_STATE, O.E_DUPKEY)
+
+
+@pytest.mark.parametrize("N,vb,alpha,c", [
+    (1 << 16, 8, 0.2, 8), (1 << 24, 56, 0.2, 8), (1 << 28, 24, 0.2, 8), (1 << 30, 56, 0.1, 8),
+    (10**6, 8, 0.2, 8), (1 << 20, 8, 0.01, 16), (1 << 12, 24, 0.0, 8), (64, 8, 0.5, 8)])
+def test_planner_matches_oracle(N, vb, alpha, c):
+    from paper_2509_01742_b300 import bolt as B
+    assert B.plan(N, vb, alpha=alpha, c=c) == O.sizing(N, c, alpha, vb)
+
+
+def test_budget_policy_matches_oracle():
+    from paper_2509_01742_b300 import bolt as B
+    # the configured budgets: 2 GB at N=2^24 (56 B values), 16 GB at N=2^30
+    assert B.plan(1 << 24, 56, hbm_budget=2 * 10**9)["alpha"] == 0.2
+    assert B.plan(1 << 30, 56, hbm_budget=16 * 10**9)["alpha"] == 0.1
+    for budget in (10**5, 10**6, 10**7, 10**9):
+        try:
+            mine = B.plan(1 << 20, 8, hbm_budget=budget)
+        except B.BoltError as e:
+            assert e.rc == B.BOLT_E_NOMEM
+            mine = None
+        o = O.OracleMap.__new__(O.OracleMap)
+        try:
+            O.OracleMap.__init__(o, 1 << 20, 8, hbm_budget=budget)
+            theirs = o.info()
+            o.close()
+        except O.OracleError:
+            theirs = None
+        assert mine == theirs
+
+
+def test_bad_arguments_rejected_on_host():
+    from paper_2509_01742_b300 import bolt as B
+    for args in [(32, 8), (1 << 16, 12), (1 << 16, 0), (1 << 16, 512)]:
+        with pytest.raises(B.BoltError):
+            B.plan(*args)

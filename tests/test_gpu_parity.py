@@ -1,0 +1,210 @@
+"""CUDA path vs the CPU oracle, element by element (needs a B300).
+
+Every comparison is exact: the map's outputs are bytes and integers, so the
+bar is bit-exact equality of values, status flags, page ciphertexts, page
+versions, bin loads, position-map row counts and the host-access trace.
+Inputs are seeded and synthetic (paper_2509_01742_b300.workload).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_01742_b300 import workload as W
+from tests.dict_model import DictModel
+
+pytestmark = pytest.mark.gpu
+
+B = pytest.importorskip("paper_2509_01742_b300.bolt")
+
+
+def _pair(N, vb, batch=None, alpha=None, c=None, budget=2**64 - 1):
+    o = O.OracleMap(N, vb, hbm_budget=budget, alpha=alpha, c=c, batch=batch)
+    g = B.BoltMap(N, vb, hbm_budget=budget, alpha=alpha, c=c, trace=True, batch=batch)
+    assert o.info() == g.info()
+    return o, g
+
+
+def _assert_state_equal(o, g, what=""):
+    assert np.array_equal(o.pages(), g.pages()), f"page ciphertexts differ {what}"
+    assert np.array_equal(o.loads(), g.loads()), f"bin loads differ {what}"
+    assert np.array_equal(o.rowcounts().astype(np.uint8), g.rowcounts()), f"pm rows differ {what}"
+    assert np.array_equal(o.trace(), g.trace()), f"host trace differs {what}"
+
+
+def _run_batch(o, g, ops, keys, vin, what=""):
+    rc_o, vo, so = o.access(ops, keys, vin)
+    rc_g, vg, sg = g.access(ops, keys, vin)
+    assert rc_o == rc_g == 0, (rc_o, rc_g)
+    assert np.array_equal(so, sg), f"status differs {what}"
+    assert np.array_equal(vo, vg), f"values differ {what}"
+    return vg, sg
+
+
+def test_build_parity_small_config():
+    """N=2^16 records of 16 B (8 B key + 8 B value): the build's pages,
+    loads and position-map rows equal the oracle's."""
+    N = 1 << 16
+    o, g = _pair(N, 8)
+    keys, vals = W.records(N, 8, 0x5EED0001)
+    assert o.init(keys, vals, 42) == 0
+    assert g.init(keys, vals, 42) == 0
+    _assert_state_equal(o, g, "after build")
+    o.close(); g.close()
+
+
+def test_access_parity_small_config():
+    """N=2^16, then 4096 accesses (50% GET / 50% PUT, 10% absent keys,
+    uniform) in one batch, then more batches with deletes and duplicates."""
+    N = 1 << 16
+    o, g = _pair(N, 8)
+    keys, vals = W.records(N, 8, 0x5EED0001)
+    assert o.init(keys, vals, 42) == 0 and g.init(keys, vals, 42) == 0
+    model = DictModel(keys, vals)
+    ops, k, vin = W.op_stream(N, 4096, 8, 0x5EED0101, get_frac=0.5, absent_frac=0.1)
+    vg, sg = _run_batch(o, g, ops, k, vin, "batch 0")
+    ev, es = model.apply(ops, k, vin, 8)
+    assert np.array_equal(vg, ev) and np.array_equal(sg, es)
+    _assert_state_equal(o, g, "after batch 0")
+    for rep in range(3):
+        ops, k, vin = W.op_stream(N, 3000, 8, 0x5EED0200 + rep, get_frac=0.4, del_frac=0.2,
+                                  absent_frac=0.2)
+        k[::7] = k[1]  # a hot key repeated inside the batch
+        vg, sg = _run_batch(o, g, ops, k, vin, f"batch {rep + 1}")
+        ev, es = model.apply(ops, k, vin, 8)
+        assert np.array_equal(vg, ev) and np.array_equal(sg, es)
+        _assert_state_equal(o, g, f"after batch {rep + 1}")
+    o.close(); g.close()
+
+
+@pytest.mark.parametrize("batch", [1, 7, 333])
+def test_access_parity_batch_widths(batch):
+    """Small batches (one op per batch is Alg. 1) on a 2^12 map, 24 B values."""
+    N = 1 << 12
+    o, g = _pair(N, 24, batch=batch)
+    keys, vals = W.records(3500, 24, 7)
+    assert o.init(keys, vals, 9) == 0 and g.init(keys, vals, 9) == 0
+    _assert_state_equal(o, g, "after build")
+    for rep in range(2):
+        ops, k, vin = W.op_stream(3500, 700, 24, 40 + rep, get_frac=0.5, del_frac=0.1,
+                                  absent_frac=0.2)
+        _run_batch(o, g, ops, k, vin, f"rep {rep}")
+        _assert_state_equal(o, g, f"rep {rep}")
+    o.close(); g.close()
+
+
+def test_access_parity_multi_tile_batch_zipf():
+    """A 20000-op batch (multi-tile grouping sort) with Zipf(0.99) keys, 56 B
+    values, 70% GET / 30% PUT -- the skewed configuration's shape."""
+    N = 1 << 15
+    o, g = _pair(N, 56)
+    keys, vals = W.records(N, 56, 11)
+    assert o.init(keys, vals, 3) == 0 and g.init(keys, vals, 3) == 0
+    ops, k, vin = W.op_stream(N, 20000, 56, 12, get_frac=0.7, zipf_theta=0.99)
+    assert len(np.unique(k)) < 15000  # heavy duplication
+    _run_batch(o, g, ops, k, vin, "zipf")
+    _assert_state_equal(o, g, "zipf")
+    o.close(); g.close()
+
+
+def test_access_parity_max_batch_zipf():
+    """One full 65536-op batch (Zipf 0.99, 70/30) on a 2^20 map."""
+    N = 1 << 20
+    o, g = _pair(N, 56)
+    keys, vals = W.records(N, 56, 14)
+    assert o.init(keys, vals, 3) == 0 and g.init(keys, vals, 3) == 0
+    ops, k, vin = W.op_stream(N, 65536, 56, 13, get_frac=0.7, zipf_theta=0.99)
+    _run_batch(o, g, ops, k, vin, "zipf 65536")
+    _assert_state_equal(o, g, "zipf 65536")
+    o.close(); g.close()
+
+
+def test_batch_wider_than_map():
+    """A 65536-op batch on a 2^15 map (the batch remaps a quarter of all keys
+    at once; the value store's batch headroom absorbs it)."""
+    N = 1 << 15
+    o, g = _pair(N, 56)
+    keys, vals = W.records(N, 56, 11)
+    assert o.init(keys, vals, 3) == 0 and g.init(keys, vals, 3) == 0
+    ops, k, vin = W.op_stream(N, 65536, 56, 13, get_frac=0.7, zipf_theta=0.99)
+    _run_batch(o, g, ops, k, vin, "65536 on 2^15")
+    _assert_state_equal(o, g, "65536 on 2^15")
+    o.close(); g.close()
+
+
+def test_alpha_zero_and_large_alpha():
+    """Edge settings: no HBM bins (alpha = 0) and alpha = 0.5."""
+    for alpha in (0.0, 0.5):
+        N = 1 << 12
+        o, g = _pair(N, 8, alpha=alpha)
+        keys, vals = W.records(N, 8, 5)
+        assert o.init(keys, vals, 1) == 0 and g.init(keys, vals, 1) == 0
+        _assert_state_equal(o, g, f"alpha {alpha} build")
+        ops, k, vin = W.op_stream(N, 2048, 8, 6, del_frac=0.1, absent_frac=0.1)
+        _run_batch(o, g, ops, k, vin, f"alpha {alpha}")
+        _assert_state_equal(o, g, f"alpha {alpha}")
+        o.close(); g.close()
+
+
+def test_empty_and_partial_init():
+    """n = 0 records (every page a dummy page) and n < N."""
+    N = 1 << 12
+    for n in (0, 1000):
+        o, g = _pair(N, 8)
+        keys, vals = W.records(n, 8, 2)
+        assert o.init(keys, vals, 5) == 0 and g.init(keys, vals, 5) == 0
+        _assert_state_equal(o, g, f"n={n}")
+        ops, k, vin = W.op_stream(max(n, 1), 500, 8, 3, get_frac=0.3, absent_frac=0.5)
+        _run_batch(o, g, ops, k, vin, f"n={n}")
+        _assert_state_equal(o, g, f"n={n} access")
+        o.close(); g.close()
+
+
+def test_overflow_and_dupkey_match_oracle():
+    o, g = _pair(64, 8)
+    k = np.array([5, 6, 5], dtype=np.uint64)
+    v = np.zeros((3, 8), np.uint8)
+    assert o.init(k, v, 1) == O.E_DUPKEY and g.init(k, v, 1) == B.BOLT_E_DUPKEY
+    keys, vals = W.records(60, 8, 1)
+    assert o.init(keys, vals, 1) == 0 and g.init(keys, vals, 1) == 0
+    newk = W.key_of(np.arange(1000, 1400))
+    for lo in range(0, 400, 50):
+        ops = np.ones(50, np.uint8)
+        vin = np.ones((50, 8), np.uint8)
+        rc_o, _, _ = o.access(ops, newk[lo:lo + 50], vin)
+        rc_g, _, _ = g.access(ops, newk[lo:lo + 50], vin)
+        assert rc_o == rc_g
+        if rc_o:
+            break
+    assert rc_g == B.BOLT_E_OVERFLOW
+    rc, _, _ = g.access(np.zeros(1, np.uint8), keys[:1], np.zeros((1, 8), np.uint8))
+    assert rc == B.BOLT_E_STATE
+    assert g.init(keys, vals, 2) == 0
+    o.close(); g.close()
+
+
+def test_device_pointer_path_matches_host_path():
+    """bolt_init_device / bolt_access_device on torch tensors give the same
+    outputs and pages as the host-pointer calls."""
+    import torch
+    N = 1 << 14
+    keys, vals = W.records(N, 24, 21)
+    ops, k, vin = W.op_stream(N, 4096, 24, 22, del_frac=0.1, absent_frac=0.1)
+    h = B.BoltMap(N, 24)
+    assert h.init(keys, vals, 77) == 0
+    rc, vh, sh = h.access(ops, k, vin)
+    assert rc == 0
+    d = B.BoltMap(N, 24)
+    tk = torch.from_numpy(keys.view(np.int64)).cuda()
+    tv = torch.from_numpy(vals).cuda()
+    assert d.init_device(tk, tv, 77) == 0
+    t_ops = torch.from_numpy(ops).cuda()
+    t_k = torch.from_numpy(k.view(np.int64)).cuda()
+    t_vin = torch.from_numpy(vin).cuda()
+    t_out = torch.zeros((4096, 24), dtype=torch.uint8, device="cuda")
+    t_st = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    assert d.access_device(t_ops, t_k, t_vin, t_out, t_st) == 0
+    assert d.sync() == 0
+    assert np.array_equal(t_out.cpu().numpy(), vh)
+    assert np.array_equal(t_st.cpu().numpy(), sh)
+    assert np.array_equal(h.pages(), d.pages())
+    h.close(); d.close()
