@@ -146,6 +146,30 @@ BOLT_API int bolt_init_device(bolt_t* h, const void* d_keys, const void* d_vals,
                      uint64_t seed, void* stream);
 
 /*
+ * bolt_init_device_noalloc -- bolt_init_device that allocates no memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they (re)build a map -- for example a
+ * serving loop that re-keys maps in place and must not stall other streams
+ * (cudaMalloc/cudaFree can synchronize the device), or a process whose device
+ * memory is owned by another allocator or a fixed arena.  bolt_init_device
+ * grows its build scratch with cudaMalloc when n exceeds what it holds; this
+ * variant instead uses one fixed scratch array compiled into the library
+ * (about 7 MB, held on every GPU that loads the library until the process
+ * exits), so it calls no cudaMalloc, cudaFree or other allocating routine.
+ *   limits   n <= 2^18 records and a map of at most 2^18 host pages (M);
+ *            larger sizes return BOLT_E_ARG before any work is enqueued;
+ *   set-up   the first call on each device looks up the array's device
+ *            address (cudaGetSymbolAddress) with that device current; make
+ *            that first call before any stream capture;
+ *   sharing  every call on a device, from any handle, uses the same array:
+ *            the call clears what must start at zero, but calls whose work
+ *            overlaps on the GPU race on it, so serialise them (one stream,
+ *            or wait for the previous call to return);
+ * Arguments, results and errors are those of bolt_init_device. */
+BOLT_API int bolt_init_device_noalloc(bolt_t* h, const void* d_keys, const void* d_vals,
+                                      uint64_t n, uint64_t seed, void* stream);
+
+/*
  * bolt_access -- a batch of n oblivious Get/Put/Delete operations (Alg. 1,
  * applied to a batch; a batch of one is Alg. 1).  Per batch every operation
  * reads the host pages of both bins of its pair (stored pair for the first

@@ -68,6 +68,7 @@ _SIGS = {
     "bolt_set_param": ([_P, _i, ctypes.c_double], _i),
     "bolt_init": ([_P, _P, _P, _u64, _u64], _i),
     "bolt_init_device": ([_P, _P, _P, _u64, _u64, _P], _i),
+    "bolt_init_device_noalloc": ([_P, _P, _P, _u64, _u64, _P], _i),
     "bolt_access": ([_P, _P, _P, _P, _P, _P, _u64], _i),
     "bolt_access_device": ([_P, _P, _P, _P, _P, _P, _u64, _P], _i),
     "bolt_sync": ([_P], _i),

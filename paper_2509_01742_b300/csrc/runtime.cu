@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "batch.cuh"
@@ -327,12 +328,13 @@ int err_to_rc(uint32_t err) {
   return BOLT_OK;
 }
 
+// The build on the device.  `bs` must hold at least n records, a tag buffer
+// of a power of two >= max(n, 8192) entries and M + 1 page offsets.
 int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n, uint64_t seed,
-              cudaStream_t st) {
+              cudaStream_t st, BuildScratch& bs) {
   MapDev& m = h->m;
   const bolt_info_t& I = h->info;
-  int rc = grow_build_scratch(h, n);
-  if (rc) return rc;
+  int rc = BOLT_OK;
   h->initialized = false;
   h->poisoned = false;
   ProfSpan whole(P_BUILD, st);
@@ -359,19 +361,19 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
   }
   if (h->check_keys && n > 1) {
     ProfSpan ps(P_KEYCHECK, st);
-    k_copy_keys<<<sms * 8, 256, 0, st>>>(d_keys, n, h->bs.tag_cap, h->bs.tags);
+    k_copy_keys<<<sms * 8, 256, 0, st>>>(d_keys, n, bs.tag_cap, bs.tags);
     count_launch(2);
-    e = sort_tags_u64(h->bs.tags, h->bs.tag_cap, 13, st);
+    e = sort_tags_u64(bs.tags, bs.tag_cap, 13, st);
     if (e != cudaSuccess) return BOLT_E_CUDA;
     cudaMemsetAsync(h->d_flag, 0, 4, st);
-    k_adjacent_equal<<<sms * 8, 256, 0, st>>>(h->bs.tags, n, h->d_flag);
+    k_adjacent_equal<<<sms * 8, 256, 0, st>>>(bs.tags, n, h->d_flag);
     uint32_t flag = 0;
     e = cudaMemcpyAsync(&flag, h->d_flag, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return BOLT_E_CUDA;
     if (flag) return BOLT_E_DUPKEY;
   }
-  e = launch_build(m, d_keys, d_vals, n, h->bs, st);
+  e = launch_build(m, d_keys, d_vals, n, bs, st);
   if (e != cudaSuccess) return BOLT_E_CUDA;
   uint32_t err = 0;
   h->last_st = st;
@@ -518,8 +520,10 @@ int bolt_init_device(bolt_t* h, const void* d_keys, const void* d_vals, uint64_t
   if (!h || !h->allocated || n > h->N || (n && (!d_keys || !d_vals))) return BOLT_E_ARG;
   ProfScope prof_scope(h);
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
+  int rc = grow_build_scratch(h, n);
+  if (rc) return rc;
   return init_impl(h, static_cast<const uint64_t*>(d_keys), static_cast<const uint8_t*>(d_vals), n,
-                   seed, st);
+                   seed, st, h->bs);
 }
 
 int bolt_init(bolt_t* h, const void* keys, const void* vals, uint64_t n, uint64_t seed) {
@@ -543,7 +547,9 @@ int bolt_init(bolt_t* h, const void* keys, const void* vals, uint64_t n, uint64_
       e = cudaMemcpyAsync(h->in_vals, vals, n * h->vb, cudaMemcpyHostToDevice, h->st);
     if (e != cudaSuccess) return BOLT_E_CUDA;
   }
-  return init_impl(h, h->in_keys, h->in_vals, n, seed, h->st);
+  int rc = grow_build_scratch(h, n);
+  if (rc) return rc;
+  return init_impl(h, h->in_keys, h->in_vals, n, seed, h->st, h->bs);
 }
 
 int bolt_sync(bolt_t* h) {
@@ -722,3 +728,80 @@ int bolt_get_stats(bolt_t* h, bolt_stats_t* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// bolt_init_device_noalloc: the device build with its scratch in a
+// file-scope device array instead of memory the handle allocates.
+//
+// Layout of the array (offsets 256-byte aligned), for at most
+// NOALLOC_MAX_RECORDS records and NOALLOC_MAX_PAGES host pages:
+//   tags   u64[NOALLOC_MAX_RECORDS]   (tag buffer, a power of two >= 8192)
+//   bins   u64[NOALLOC_MAX_RECORDS]
+//   dest   u32[NOALLOC_MAX_RECORDS]
+//   prow   u32[NOALLOC_MAX_RECORDS]
+//   page_off u32[NOALLOC_MAX_PAGES + 1]
+//   block_sums u32[64], counters u64[2]
+namespace {
+
+constexpr uint64_t NOALLOC_MAX_RECORDS = 1ull << 18;
+constexpr uint64_t NOALLOC_MAX_PAGES = 1ull << 18;
+constexpr uint64_t NA_OFF_TAGS = 0;
+constexpr uint64_t NA_OFF_BINS = NA_OFF_TAGS + NOALLOC_MAX_RECORDS * 8;
+constexpr uint64_t NA_OFF_DEST = NA_OFF_BINS + NOALLOC_MAX_RECORDS * 8;
+constexpr uint64_t NA_OFF_PROW = NA_OFF_DEST + NOALLOC_MAX_RECORDS * 4;
+constexpr uint64_t NA_OFF_PAGE = NA_OFF_PROW + NOALLOC_MAX_RECORDS * 4;
+constexpr uint64_t NA_OFF_BSUM = NA_OFF_PAGE + ((NOALLOC_MAX_PAGES + 1) * 4 + 255) / 256 * 256;
+constexpr uint64_t NA_BSUM_CAP = 64;
+constexpr uint64_t NA_OFF_CTR = NA_OFF_BSUM + 256;
+constexpr uint64_t NA_BYTES = NA_OFF_CTR + 256;
+static_assert(NOALLOC_MAX_RECORDS >= 8192, "tag buffer must hold one sort tile");
+static_assert((NOALLOC_MAX_PAGES + 1 + 8191) / 8192 + 1 <= NA_BSUM_CAP, "block sums");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NA_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the name is only a host-side stand-in in host code).
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) return BOLT_E_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return BOLT_E_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  return BOLT_OK;
+}
+
+}  // namespace
+
+extern "C" int bolt_init_device_noalloc(bolt_t* h, const void* d_keys, const void* d_vals,
+                                        uint64_t n, uint64_t seed, void* stream) {
+  if (!h || !h->allocated || n > h->N || (n && (!d_keys || !d_vals))) return BOLT_E_ARG;
+  if (n > NOALLOC_MAX_RECORDS || h->info.M > NOALLOC_MAX_PAGES) return BOLT_E_ARG;
+  unsigned char* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (rc) return rc;
+  BuildScratch s{};
+  s.cap = NOALLOC_MAX_RECORDS;
+  s.tag_cap = 8192;
+  while (s.tag_cap < n) s.tag_cap <<= 1;
+  s.tags = reinterpret_cast<uint64_t*>(base + NA_OFF_TAGS);
+  s.bins = reinterpret_cast<uint64_t*>(base + NA_OFF_BINS);
+  s.dest = reinterpret_cast<uint32_t*>(base + NA_OFF_DEST);
+  s.prow = reinterpret_cast<uint32_t*>(base + NA_OFF_PROW);
+  s.page_off = reinterpret_cast<uint32_t*>(base + NA_OFF_PAGE);
+  s.block_sums = reinterpret_cast<uint32_t*>(base + NA_OFF_BSUM);
+  s.block_cap = NA_BSUM_CAP;
+  s.counters = reinterpret_cast<unsigned long long*>(base + NA_OFF_CTR);
+  ProfScope prof_scope(h);
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
+  return init_impl(h, static_cast<const uint64_t*>(d_keys), static_cast<const uint8_t*>(d_vals), n,
+                   seed, st, s);
+}
