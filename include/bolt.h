@@ -78,6 +78,8 @@ typedef struct bolt bolt_t;
 #define BOLT_PARAM_TRACE_CAP 6 /* trace capacity in entries (default 1<<22) */
 #define BOLT_PARAM_CHECK_KEYS 7 /* 1 = bolt_init verifies key uniqueness (default) */
 #define BOLT_PARAM_PROFILE 8 /* 1 = time kernel classes with CUDA events */
+#define BOLT_PARAM_BATCH_CAP 9 /* capacity of the device batch buffers, 1..BOLT_MAX_BATCH
+                                  (default BOLT_MAX_BATCH); reallocates, drops contents */
 
 /* derived parameters (Sec. 3.3 sizing, Sec. 4.2 position map) */
 typedef struct {
@@ -191,7 +193,7 @@ BOLT_API int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const 
                 void* vals_out, uint8_t* status_out, uint64_t n);
 
 /* bolt_access_device -- bolt_access with DEVICE pointers (status may be
- * NULL), enqueued on `stream`; n <= BOLT_MAX_BATCH is one batch.  Returns
+ * NULL), enqueued on `stream`; n <= the batch capacity is one batch.  Returns
  * after enqueueing; the overflow check of this batch is reported by the next
  * call on the handle or by bolt_sync. */
 BOLT_API int bolt_access_device(bolt_t* h, const uint8_t* d_ops, const void* d_keys,
@@ -228,9 +230,11 @@ BOLT_API int bolt_read_rowcounts(bolt_t* h, uint8_t* dst);
  *   4 build key-uniqueness check          5 whole access batch
  *   6 access page read + decrypt          7 access write-back + eviction
  *   8 whole build                         9 access grouping sort + scans
+ *  10 key check: bitonic global steps    11 key check: bitonic in-tile steps
+ *  12 access: written pages copied to the host (side stream)
  * ms[c] sums the event-timed durations of the spans[c] launches (or phases)
  * of class c; launches counts every kernel the library launched. */
-#define BOLT_PROF_CLASSES 10
+#define BOLT_PROF_CLASSES 13
 typedef struct {
   uint64_t launches;
   uint64_t spans[BOLT_PROF_CLASSES];

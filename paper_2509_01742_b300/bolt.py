@@ -22,9 +22,11 @@ BOLT_GET, BOLT_PUT, BOLT_DEL = 0, 1, 2
 BOLT_MAX_BATCH = 65536
 BOLT_PARAM_ALPHA, BOLT_PARAM_C, BOLT_PARAM_TRACE, BOLT_PARAM_BATCH = 1, 2, 4, 5
 BOLT_PARAM_TRACE_CAP, BOLT_PARAM_CHECK_KEYS, BOLT_PARAM_PROFILE = 6, 7, 8
-BOLT_PROF_CLASSES = 10
+BOLT_PARAM_BATCH_CAP = 9
+BOLT_PROF_CLASSES = 13
 PROF_NAMES = ("sort_global", "sort_tile", "page_build", "p2c_rounds", "key_check",
-              "access_batch", "gather", "evict", "build", "group")
+              "access_batch", "gather", "evict", "build", "group", "ksort_global",
+              "ksort_tile", "flush")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -57,8 +59,8 @@ class bolt_stats_t(ctypes.Structure):
 
 
 class bolt_profile_t(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64), ("spans", ctypes.c_uint64 * 10),
-                ("ms", ctypes.c_double * 10)]
+    _fields_ = [("launches", ctypes.c_uint64), ("spans", ctypes.c_uint64 * 13),
+                ("ms", ctypes.c_double * 13)]
 
 
 _P, _u64, _u32, _i = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int

@@ -27,15 +27,31 @@
 
 namespace bdev {
 
+__device__ __forceinline__ uint32_t key_hash(uint64_t k, uint32_t mask) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  return (uint32_t)k & mask;
+}
+
+// per op: PRF pairs and rows, and the op's grouping key.  Equal keys share a
+// hash-table slot (claimed by the first op to reach it), so sorting
+// (slot << 16 | op) lists every key's ops together, in op order.
 __global__ void k_stage(MapDev m, BatchDev b, uint32_t n, uint32_t n_sort, uint64_t t0) {
   uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_sort) return;
   if (i >= n) {
-    b.sortbuf[i] = make_ulonglong2(~0ull, ~0ull);
+    b.skeys[i] = ~0ull;
     return;
   }
   const uint64_t key = b.keys[i];
-  b.sortbuf[i] = make_ulonglong2(key, i);
+  uint32_t h = key_hash(key, b.kt_mask);
+  for (uint32_t probe = 0; probe <= b.kt_mask; probe++) {
+    const uint32_t old = atomicCAS(b.kt_own + h, 0u, i + 1);
+    if (old == 0 || b.keys[old - 1] == key) break;
+    h = (h + 1) & b.kt_mask;
+  }
+  b.skeys[i] = ((uint64_t)h << 16) | i;
   uint32_t p1, p2;
   prf_pair(m, DOM_DUMMY, t0 + i, p1, p2);
   b.pair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
@@ -78,33 +94,37 @@ __device__ __forceinline__ int32_t block_excl_max(int32_t v, int32_t* sh) {
 
 constexpr int GROUP_THREADS = 1024;
 
+// grouping keys sort as (slot << 16 | op): a group is a run of equal slots
+__device__ __forceinline__ uint32_t g_slot(uint64_t sk) { return (uint32_t)(sk >> 16); }
+__device__ __forceinline__ uint32_t g_op(uint64_t sk) { return (uint32_t)(sk & 0xffffu); }
+
 __global__ void __launch_bounds__(GROUP_THREADS) k_group(BatchDev b, uint32_t n) {
   __shared__ int32_t sh[32];
   const uint32_t per = (n + GROUP_THREADS - 1) / GROUP_THREADS;
   const uint32_t lo = threadIdx.x * per;
   const uint32_t hi = min(n, lo + per);
-  // local maxima of head positions and writer positions
+  // local maxima of group-head positions and writer positions
   int32_t hmax = -1, wmax = -1;
   for (uint32_t s = lo; s < hi; s++) {
-    const ulonglong2 e = b.sortbuf[s];
-    const bool head = s == 0 || b.sortbuf[s - 1].x != e.x;
+    const uint64_t e = b.skeys[s];
+    const bool head = s == 0 || g_slot(b.skeys[s - 1]) != g_slot(e);
     if (head) hmax = (int32_t)s;
-    if (b.ops[e.y] != OP_GET) wmax = (int32_t)s;
+    if (b.ops[g_op(e)] != OP_GET) wmax = (int32_t)s;
   }
   int32_t hcar = block_excl_max(hmax, sh);
   int32_t wcar = block_excl_max(wmax, sh);
   for (uint32_t s = lo; s < hi; s++) {
-    const ulonglong2 e = b.sortbuf[s];
-    const uint32_t i = (uint32_t)e.y;
-    const bool head = s == 0 || b.sortbuf[s - 1].x != e.x;
+    const uint64_t e = b.skeys[s];
+    const uint32_t i = g_op(e);
+    const bool head = s == 0 || g_slot(b.skeys[s - 1]) != g_slot(e);
     if (head) hcar = (int32_t)s;
-    const uint32_t lead = (uint32_t)b.sortbuf[hcar].y;
+    const uint32_t lead = g_op(b.skeys[hcar]);
     // previous writer in the same group (strictly before s)
-    b.prevw[i] = wcar >= hcar ? (uint32_t)b.sortbuf[wcar].y : NONE32;
+    b.prevw[i] = wcar >= hcar ? g_op(b.skeys[wcar]) : NONE32;
     b.leader[i] = lead;
     if (b.ops[i] != OP_GET) wcar = (int32_t)s;
-    const bool last = s + 1 == n || b.sortbuf[s + 1].x != e.x;
-    if (last) b.lastw[lead] = wcar >= hcar ? (uint32_t)b.sortbuf[wcar].y : NONE32;
+    const bool last = s + 1 == n || g_slot(b.skeys[s + 1]) != g_slot(e);
+    if (last) b.lastw[lead] = wcar >= hcar ? g_op(b.skeys[wcar]) : NONE32;
   }
 }
 
@@ -209,19 +229,40 @@ __global__ void __launch_bounds__(PAGES_THREADS) k_pages(MapDev m, BatchDev b, u
   }
 }
 
-// warp per distinct page: read from the pinned host page and decrypt
+// page q in the previous batch's write set? -> its distinct index, else NONE
+__device__ __forceinline__ uint32_t prev_written(const BatchDev& b, uint32_t q) {
+  if (!b.prev_valid) return NONE32;
+  uint32_t h = ht_hash(q, b.prev_ht_mask);
+  for (uint32_t probe = 0; probe <= b.prev_ht_mask; probe++) {
+    const uint32_t k = b.prev_ht_key[h];
+    if (k == q) return b.prev_ht_d[h];
+    if (k == NONE32) return NONE32;
+    h = (h + 1) & b.prev_ht_mask;
+  }
+  return NONE32;
+}
+
+// warp per distinct page: read the page (host, or the previous batch's
+// not-yet-flushed ciphertext) and decrypt it
 __global__ void k_gather(MapDev m, BatchDev b) {
   const uint32_t d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (d >= *b.dcount) return;
   const uint64_t q = b.dpage[d];
   const uint64_t v = m.version[q];
-  const uint8_t* src = m.pages + q * m.page_bytes;
+  const uint8_t* host = m.pages + q * m.page_bytes;
+  // the first host read is issued before the previous-batch lookup resolves;
+  // a page the previous batch wrote (rare) is taken from its ciphertext copy
+  uint4 first = make_uint4(0, 0, 0, 0);
+  if (16 * lane < m.page_bytes) first = *reinterpret_cast<const uint4*>(host + 16 * lane);
+  const uint32_t pd = prev_written(b, (uint32_t)q);
   uint8_t* dst = b.dbuf + (uint64_t)d * m.page_bytes;
   for (uint32_t c = 0; c < m.page_bytes; c += 512) {
     const uint32_t off = c + 16 * lane;
-    uint4 x = make_uint4(0, 0, 0, 0);
-    if (off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
+    uint4 x = first;
+    if (c > 0 && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(host + off);
+    if (pd != NONE32 && off < m.page_bytes)
+      x = *reinterpret_cast<const uint4*>(b.prev_dbuf + (uint64_t)pd * m.page_bytes + off);
     const uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)v,
                                  (uint32_t)(v >> 32));
     if (off < m.page_bytes) {
@@ -230,6 +271,17 @@ __global__ void k_gather(MapDev m, BatchDev b) {
     }
   }
   if (lane == 0) b.removed[d] = 0;
+}
+
+// warp per written page: copy the ciphertext from dbuf to the host page
+__global__ void k_flush(MapDev m, BatchDev b) {
+  const uint32_t d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (d >= *b.dcount) return;
+  const uint64_t q = b.dpage[d];
+  const uint4* src = reinterpret_cast<const uint4*>(b.dbuf + (uint64_t)d * m.page_bytes);
+  uint4* dst = reinterpret_cast<uint4*>(m.pages + q * m.page_bytes);
+  for (uint32_t c = lane; c < m.page_bytes / 16; c += 32) dst[c] = src[c];
 }
 
 __device__ __forceinline__ void ring_push(const MapDev& m, uint32_t slot) {
@@ -389,7 +441,9 @@ __global__ void k_evict(MapDev m, BatchDev b, uint32_t warps_per_block) {
   }
   __syncwarp();
   const uint64_t ver = m.version[q] + 1;
-  page_encrypt_store(m, plain, q, ver);
+  // the old plaintext in dbuf is no longer read: the ciphertext replaces it
+  // and k_flush copies it to the host page
+  page_encrypt_to(m, plain, b.dbuf + (uint64_t)d * m.page_bytes, q, ver);
   __syncwarp();
   if (lane == 0) {
     m.version[q] = ver;
@@ -482,11 +536,12 @@ __global__ void k_clear_table(BatchDev b) {
        h += gridDim.x * blockDim.x) {
     b.ht_key[h] = NONE32;
     b.ht_min[h] = NONE32;
+    if (h <= b.kt_mask) b.kt_own[h] = 0;
   }
 }
 
 cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
-                          cudaStream_t st) {
+                          cudaStream_t st, const FlushCtx& fc) {
   if (n == 0) return cudaSuccess;
   uint32_t n_sort = 512;
   while (n_sort < n) n_sort <<= 1;
@@ -498,7 +553,7 @@ cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64
   cudaError_t e;
   {
     ProfSpan ps(P_GROUP, st);
-    e = sort_pairs(b.sortbuf, n_sort, st);
+    e = sort_batch_keys(b.skeys, n_sort, st);
     if (e != cudaSuccess) return e;
     k_group<<<1, GROUP_THREADS, 0, st>>>(b, n);
     count_launch();
@@ -527,6 +582,15 @@ cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64
     k_evict<<<(dmax + wpb - 1) / wpb, wpb * 32, smem, st>>>(m, b, wpb);
     count_launch();
   }
+  // the host write-back overlaps the rest of this batch and the next one
+  cudaEventRecord(fc.ev_evicted, st);
+  cudaStreamWaitEvent(fc.flush_st, fc.ev_evicted, 0);
+  {
+    ProfSpan ps(P_FLUSH, fc.flush_st);
+    k_flush<<<(dmax * 32 + 255) / 256, 256, 0, fc.flush_st>>>(m, b);
+    count_launch();
+  }
+  cudaEventRecord(fc.ev_flushed, fc.flush_st);
   for (uint64_t lo = 0; lo < n; lo += m.Wr) {
     const uint32_t hi = (uint32_t)(lo + m.Wr < n ? lo + m.Wr : n);
     const uint32_t g = (hi - (uint32_t)lo + 255) / 256;

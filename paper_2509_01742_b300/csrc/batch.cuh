@@ -12,7 +12,9 @@ struct BatchDev {
   uint8_t* vout;       // [cap * vb]
   uint8_t* status;     // [cap]
   // grouping
-  ulonglong2* sortbuf; // [sort_cap] (key, op index)
+  uint64_t* skeys;     // [cap] grouping keys: key slot << 16 | op index
+  uint32_t* kt_own;    // [kt_mask + 1] key hash table: owner op + 1, or 0
+  uint32_t kt_mask, pad1;
   uint32_t* leader;    // [cap] first op on the same key
   uint32_t* prevw;     // [cap] previous PUT/DEL on the same key, or NONE
   uint32_t* lastw;     // [cap] (leaders) last PUT/DEL of the key group, or NONE
@@ -31,8 +33,15 @@ struct BatchDev {
   uint32_t ht_mask, pad0;
   uint32_t* dpage;     // [2 cap] distinct pages in first-read order
   uint32_t* dcount;    // [1]
-  uint8_t* dbuf;       // [2 cap * page_bytes] decrypted pages
+  uint8_t* dbuf;       // [2 cap * page_bytes] decrypted pages, then the
+                       // ciphertexts written back (flushed to the host later)
   uint64_t* removed;   // [2 cap] slots taken out by find_remove
+  // the previous batch's written pages, until its flush has landed: a page it
+  // wrote is read from prev_dbuf (ciphertext) instead of the host
+  const uint32_t* prev_ht_key;
+  const uint32_t* prev_ht_d;
+  const uint8_t* prev_dbuf;
+  uint32_t prev_ht_mask, prev_valid;
   // values
   uint8_t* init_val;   // [cap * vb] value found for a leader hit
   uint8_t* init_present;  // [cap]
@@ -42,8 +51,17 @@ struct BatchDev {
   uint32_t* rrow;      // [cap] position-map row for a new key
 };
 
-cudaError_t sort_pairs(ulonglong2* data, uint32_t n_pow2, cudaStream_t st);
+cudaError_t sort_batch_keys(uint64_t* keys, uint32_t n_pow2, cudaStream_t st);
+// Host page write-back runs on `flush_st` after `ev_evicted` (recorded on st
+// once the batch's ciphertexts are in dbuf); `ev_flushed` is recorded on
+// flush_st when the batch's pages are in host memory.
+struct FlushCtx {
+  cudaStream_t flush_st;
+  cudaEvent_t ev_evicted;
+  cudaEvent_t ev_flushed;
+};
+
 cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
-                          cudaStream_t st);
+                          cudaStream_t st, const FlushCtx& fc);
 
 }  // namespace bdev

@@ -258,13 +258,12 @@ __device__ __forceinline__ void warp_sort_by_key(uint64_t& key, uint32_t& src) {
   }
 }
 
-// Encrypt the plaintext page in shared memory and store it to the host page:
-// lane L handles bytes [16L, 16L+16) of each 512-byte chunk; the four lanes of
-// a quad compute the chunk's ChaCha20 block together.
-__device__ __forceinline__ void page_encrypt_store(const MapDev& m, const uint8_t* plain,
-                                                   uint64_t q, uint64_t version) {
+// Encrypt a plaintext page (shared memory) into dst (page_bytes): lane L
+// handles bytes [16L, 16L+16) of each 512-byte chunk; the four lanes of a
+// quad compute the chunk's ChaCha20 block together.
+__device__ __forceinline__ void page_encrypt_to(const MapDev& m, const uint8_t* plain,
+                                                uint8_t* dst, uint64_t q, uint64_t version) {
   const int lane = threadIdx.x & 31;
-  uint8_t* dst = m.pages + q * m.page_bytes;
   for (uint32_t c = 0; c < m.page_bytes; c += 512) {
     uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)version,
                            (uint32_t)(version >> 32));
@@ -275,6 +274,12 @@ __device__ __forceinline__ void page_encrypt_store(const MapDev& m, const uint8_
       *reinterpret_cast<uint4*>(dst + off) = p;
     }
   }
+}
+
+// ... straight into host page q
+__device__ __forceinline__ void page_encrypt_store(const MapDev& m, const uint8_t* plain,
+                                                   uint64_t q, uint64_t version) {
+  page_encrypt_to(m, plain, m.pages + q * m.page_bytes, q, version);
 }
 
 // ---------------------------------------------------------------------------
@@ -292,7 +297,10 @@ enum ProfClass : int {
   P_EVICT = 7,        // access: write-back with eviction
   P_BUILD = 8,        // one whole build
   P_GROUP = 9,        // access: batch grouping sort + scans
-  P_NCLASS = 10
+  P_KSORT_GLOBAL = 10,  // key-uniqueness check: bitonic global steps
+  P_KSORT_TILE = 11,    // key-uniqueness check: bitonic in-tile steps
+  P_FLUSH = 12,         // access: written pages copied to the host
+  P_NCLASS = 13
 };
 
 struct Prof {
@@ -335,8 +343,10 @@ struct ProfSpan {
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
                          struct BuildScratch& s, cudaStream_t st);
 
-// sort.cu: ascending bitonic sort of n_pow2 uint64 tags in place
-cudaError_t sort_tags_u64(uint64_t* tags, uint64_t n_pow2, int log_tile, cudaStream_t st);
+// sort.cu: ascending bitonic sort of n_pow2 uint64 tags in place; the
+// passes are profiled under the given classes
+cudaError_t sort_tags_u64(uint64_t* tags, uint64_t n_pow2, int log_tile, cudaStream_t st,
+                          int cls_global = P_SORT_GLOBAL, int cls_tile = P_SORT_TILE);
 
 struct BuildScratch {
   uint64_t cap = 0;        // records the buffers hold
@@ -345,6 +355,10 @@ struct BuildScratch {
   uint64_t* bins = nullptr;   // per record b1 | b2 << 32
   uint32_t* dest = nullptr;   // per record destination bin
   uint32_t* prow = nullptr;   // per record chosen position-map row
+  uint4* rows4 = nullptr;     // per record position-map candidate rows (optional:
+                              // without it the rounds compute them inline)
+  uint64_t* keysort = nullptr;  // key-uniqueness sort buffer [tag_cap] (optional:
+                                // without it the check reuses `tags` in line)
   uint32_t* page_off = nullptr;  // [M + 1] exclusive prefix of page loads
   uint32_t* block_sums = nullptr;
   uint64_t block_cap = 0;

@@ -20,17 +20,42 @@
 
 namespace bdev {
 
+// every record's pair PRF(INIT, i) and candidate rows PRF(PM, key), computed
+// once at full occupancy so the rounds only touch counters
+__global__ void k_build_prf(MapDev m, const uint64_t* __restrict__ keys, uint64_t n,
+                            uint64_t* __restrict__ bins, uint4* __restrict__ rows4) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t b1, b2;
+    prf_pair(m, DOM_INIT, i, b1, b2);
+    bins[i] = (uint64_t)b1 | ((uint64_t)b2 << 32);
+    uint32_t rows[4];
+    prf_rows(m, keys[i], rows);
+    rows4[i] = make_uint4(rows[0], rows[1], rows[2], rows[3]);
+  }
+}
+
+// decide on round-start counts: P2C bin (first choice on ties) and d-choice
+// row (lowest index on ties)
 __global__ void k_build_decide(MapDev m, const uint64_t* __restrict__ keys, uint64_t lo,
                                uint64_t hi, uint64_t* __restrict__ bins,
-                               uint32_t* __restrict__ dest, uint32_t* __restrict__ prow) {
+                               const uint4* __restrict__ rows4, uint32_t* __restrict__ dest,
+                               uint32_t* __restrict__ prow) {
   uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= hi) return;
-  uint32_t b1, b2;
-  prf_pair(m, DOM_INIT, i, b1, b2);
-  uint32_t l1 = byte_get(m.load, b1), l2 = byte_get(m.load, b2);
-  uint32_t rows[4];
-  prf_rows(m, keys[i], rows);
-  bins[i] = (uint64_t)b1 | ((uint64_t)b2 << 32);
+  uint32_t b1, b2, rows[4];
+  if (rows4) {
+    const uint64_t bb = bins[i];
+    b1 = (uint32_t)bb;
+    b2 = (uint32_t)(bb >> 32);
+    const uint4 r4 = rows4[i];
+    rows[0] = r4.x; rows[1] = r4.y; rows[2] = r4.z; rows[3] = r4.w;
+  } else {
+    prf_pair(m, DOM_INIT, i, b1, b2);
+    bins[i] = (uint64_t)b1 | ((uint64_t)b2 << 32);
+    prf_rows(m, keys[i], rows);
+  }
+  const uint32_t l1 = byte_get(m.load, b1), l2 = byte_get(m.load, b2);
   dest[i] = l1 <= l2 ? b1 : b2;
   prow[i] = pick_row(m, rows);
 }
@@ -214,10 +239,14 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   // 1. P2C + position map, round by round
   {
     ProfSpan ps(P_P2C, st);
+    if (s.rows4 && n) {
+      k_build_prf<<<sms * 16, 256, 0, st>>>(m, keys, n, s.bins, s.rows4);
+      count_launch();
+    }
     for (uint64_t lo = 0; lo < n; lo += m.Wr) {
       uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
       unsigned g = (unsigned)((hi - lo + 255) / 256);
-      k_build_decide<<<g, 256, 0, st>>>(m, keys, lo, hi, s.bins, s.dest, s.prow);
+      k_build_decide<<<g, 256, 0, st>>>(m, keys, lo, hi, s.bins, s.rows4, s.dest, s.prow);
       k_build_apply<<<g, 256, 0, st>>>(m, keys, vals, lo, hi, s.bins, s.dest, s.prow,
                                         s.counters);
       count_launch(2);

@@ -72,6 +72,7 @@ struct bolt {
   double alpha_override = -1.0;
   uint32_t c = 8;
   uint32_t batch_width = MAXB;
+  uint32_t cap_batch = MAXB;  // capacity of the batch buffers (ops per batch)
   uint64_t trace_cap = 1ull << 22;
   bool trace_on = false;
   bool check_keys = true;
@@ -101,6 +102,22 @@ struct bolt {
   bool allocated = false, initialized = false, poisoned = false;
   Prof prof;
   cudaStream_t last_st = nullptr;  // stream of the last enqueued work
+  cudaStream_t st2 = nullptr;      // side stream (key-uniqueness check)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // access batches alternate between two buffer slots; a slot's written pages
+  // reach the host on st_fl while the next batch runs
+  cudaStream_t st_fl = nullptr;
+  cudaEvent_t ev_evicted[2] = {nullptr, nullptr}, ev_flushed[2] = {nullptr, nullptr};
+  bool flush_pending[2] = {false, false};
+  int slot = 0;
+  bool prev_valid = false;
+  uint32_t slot_ht_mask[2] = {0, 0};
+  uint32_t* s_ht_key[2] = {nullptr, nullptr};
+  uint32_t* s_ht_min[2] = {nullptr, nullptr};
+  uint32_t* s_ht_d[2] = {nullptr, nullptr};
+  uint32_t* s_dpage[2] = {nullptr, nullptr};
+  uint32_t* s_dcount[2] = {nullptr, nullptr};
+  uint8_t* s_dbuf[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -123,8 +140,9 @@ int cuda_fail(cudaError_t e) {
 cudaError_t sync_all(bolt* h) {
   cudaError_t e = cudaSuccess;
   if (h->last_st && h->last_st != h->st) e = cudaStreamSynchronize(h->last_st);
-  if (h->st) {
-    cudaError_t e2 = cudaStreamSynchronize(h->st);
+  for (cudaStream_t s : {h->st, h->st2, h->st_fl}) {
+    if (!s) continue;
+    cudaError_t e2 = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = e2;
   }
   return e;
@@ -145,6 +163,7 @@ void free_build_scratch(bolt* h) {
   BuildScratch& s = h->bs;
   cudaFree(s.tags); cudaFree(s.bins); cudaFree(s.dest); cudaFree(s.prow);
   cudaFree(s.page_off); cudaFree(s.block_sums); cudaFree(s.counters);
+  cudaFree(s.rows4); cudaFree(s.keysort);
   s = BuildScratch{};
   cudaFree(h->in_keys); cudaFree(h->in_vals);
   h->in_keys = nullptr; h->in_vals = nullptr; h->in_cap = 0;
@@ -160,8 +179,30 @@ void free_state(bolt* h) {
   free_build_scratch(h);
   h->m = MapDev{};
   h->b = BatchDev{};
+  for (int s = 0; s < 2; s++) {
+    h->flush_pending[s] = false;
+    h->s_ht_key[s] = h->s_ht_min[s] = h->s_ht_d[s] = h->s_dpage[s] = h->s_dcount[s] = nullptr;
+    h->s_dbuf[s] = nullptr;
+  }
+  h->prev_valid = false;
+  h->slot = 0;
   h->allocated = false;
   h->initialized = false;
+}
+
+// streams and events of a handle (any of them may be null)
+void destroy_streams(bolt* h) {
+  for (cudaEvent_t* ev : {&h->ev_fork, &h->ev_join, &h->ev_evicted[0], &h->ev_evicted[1],
+                          &h->ev_flushed[0], &h->ev_flushed[1]})
+    if (*ev) {
+      cudaEventDestroy(*ev);
+      *ev = nullptr;
+    }
+  for (cudaStream_t* s : {&h->st_fl, &h->st2, &h->st})
+    if (*s) {
+      cudaStreamDestroy(*s);
+      *s = nullptr;
+    }
 }
 
 int choose_plan(bolt* h, bolt_info_t* o) {
@@ -212,40 +253,48 @@ int alloc_state(bolt* h) {
   e = cudaHostGetDevicePointer(&dp, hp, 0);
   if (e != cudaSuccess) { free_state(h); return BOLT_E_CUDA; }
   m.pages = static_cast<uint8_t*>(dp);
-  // batch buffers
+  // batch buffers, for batches of up to cap_batch operations
   BatchDev& b = h->b;
   const uint64_t vb = I.val_bytes;
-  TRY(dalloc(h, &b.ops, MAXB));
-  TRY(dalloc(h, &b.keys, MAXB));
-  TRY(dalloc(h, &b.vin, MAXB * vb));
-  TRY(dalloc(h, &b.vout, MAXB * vb));
-  TRY(dalloc(h, &b.status, MAXB));
-  TRY(dalloc(h, &b.sortbuf, MAXB));
-  TRY(dalloc(h, &b.leader, MAXB));
-  TRY(dalloc(h, &b.prevw, MAXB));
-  TRY(dalloc(h, &b.lastw, MAXB));
-  TRY(dalloc(h, &b.pair, MAXB));
-  TRY(dalloc(h, &b.rpair, MAXB));
-  TRY(dalloc(h, &b.rows, 4ull * MAXB));
-  TRY(dalloc(h, &b.hit, MAXB));
-  TRY(dalloc(h, &b.pos_page, 2ull * MAXB));
-  TRY(dalloc(h, &b.pos_slot, 2ull * MAXB));
-  TRY(dalloc(h, &b.pos_d, 2ull * MAXB));
-  const uint32_t ht = 4 * MAXB;
+  const uint64_t cap = h->cap_batch;
+  uint64_t cap2 = 1;
+  while (cap2 < cap) cap2 <<= 1;
+  const uint64_t sort_cap = cap2 <= 512 ? 512 : (cap2 < 4096 ? 4096 : cap2);
+  TRY(dalloc(h, &b.ops, cap));
+  TRY(dalloc(h, &b.keys, cap));
+  TRY(dalloc(h, &b.vin, cap * vb));
+  TRY(dalloc(h, &b.vout, cap * vb));
+  TRY(dalloc(h, &b.status, cap));
+  TRY(dalloc(h, &b.skeys, sort_cap));
+  b.kt_mask = (uint32_t)(2 * cap2 < 128 ? 127 : 2 * cap2 - 1);
+  TRY(dalloc(h, &b.kt_own, (uint64_t)b.kt_mask + 1));
+  TRY(dalloc(h, &b.leader, cap));
+  TRY(dalloc(h, &b.prevw, cap));
+  TRY(dalloc(h, &b.lastw, cap));
+  TRY(dalloc(h, &b.pair, cap));
+  TRY(dalloc(h, &b.rpair, cap));
+  TRY(dalloc(h, &b.rows, 4 * cap));
+  TRY(dalloc(h, &b.hit, cap));
+  TRY(dalloc(h, &b.pos_page, 2 * cap));
+  TRY(dalloc(h, &b.pos_slot, 2 * cap));
+  TRY(dalloc(h, &b.pos_d, 2 * cap));
+  const uint32_t ht = (uint32_t)(4 * cap2 < 256 ? 256 : 4 * cap2);
   b.ht_mask = ht - 1;
-  TRY(dalloc(h, &b.ht_key, ht));
-  TRY(dalloc(h, &b.ht_min, ht));
-  TRY(dalloc(h, &b.ht_d, ht));
-  TRY(dalloc(h, &b.dpage, 2ull * MAXB));
-  TRY(dalloc(h, &b.dcount, 1));
-  TRY(dalloc(h, &b.dbuf, 2ull * MAXB * I.page_bytes));
-  TRY(dalloc(h, &b.removed, 2ull * MAXB));
-  TRY(dalloc(h, &b.init_val, MAXB * vb));
-  TRY(dalloc(h, &b.init_present, MAXB));
-  TRY(dalloc(h, &b.rval, MAXB * vb));
-  TRY(dalloc(h, &b.fpres, MAXB));
-  TRY(dalloc(h, &b.rdest, MAXB));
-  TRY(dalloc(h, &b.rrow, MAXB));
+  for (int s = 0; s < 2; s++) {
+    TRY(dalloc(h, &h->s_ht_key[s], ht));
+    TRY(dalloc(h, &h->s_ht_min[s], ht));
+    TRY(dalloc(h, &h->s_ht_d[s], ht));
+    TRY(dalloc(h, &h->s_dpage[s], 2 * cap));
+    TRY(dalloc(h, &h->s_dcount[s], 1));
+    TRY(dalloc(h, &h->s_dbuf[s], 2 * cap * I.page_bytes));
+  }
+  TRY(dalloc(h, &b.removed, 2 * cap));
+  TRY(dalloc(h, &b.init_val, cap * vb));
+  TRY(dalloc(h, &b.init_present, cap));
+  TRY(dalloc(h, &b.rval, cap * vb));
+  TRY(dalloc(h, &b.fpres, cap));
+  TRY(dalloc(h, &b.rdest, cap));
+  TRY(dalloc(h, &b.rrow, cap));
   TRY(dalloc(h, &h->d_kdf, 16));
   TRY(dalloc(h, &h->d_flag, 1));
 #undef TRY
@@ -259,13 +308,16 @@ int grow_build_scratch(bolt* h, uint64_t n) {
   while (tag_cap < n) tag_cap <<= 1;
   const uint64_t nblocks = (h->info.M + 1 + 8192 - 1) / 8192 + 1;
   if (s.cap >= n && s.tag_cap >= tag_cap && s.block_cap >= nblocks && s.page_off) return BOLT_OK;
-  cudaStreamSynchronize(h->st);
+  sync_all(h);
   cudaFree(s.tags); cudaFree(s.bins); cudaFree(s.dest); cudaFree(s.prow);
   cudaFree(s.page_off); cudaFree(s.block_sums); cudaFree(s.counters);
+  cudaFree(s.rows4); cudaFree(s.keysort);
   s = BuildScratch{};
   const uint64_t cap = n > 0 ? n : 1;
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMalloc(&s.tags, tag_cap * sizeof(uint64_t));
+  e = e ? e : cudaMalloc(&s.keysort, tag_cap * sizeof(uint64_t));
+  e = e ? e : cudaMalloc(&s.rows4, cap * sizeof(uint4));
   e = e ? e : cudaMalloc(&s.bins, cap * sizeof(uint64_t));
   e = e ? e : cudaMalloc(&s.dest, cap * sizeof(uint32_t));
   e = e ? e : cudaMalloc(&s.prow, cap * sizeof(uint32_t));
@@ -275,6 +327,7 @@ int grow_build_scratch(bolt* h, uint64_t n) {
   if (e != cudaSuccess) {
     cudaFree(s.tags); cudaFree(s.bins); cudaFree(s.dest); cudaFree(s.prow);
     cudaFree(s.page_off); cudaFree(s.block_sums); cudaFree(s.counters);
+    cudaFree(s.rows4); cudaFree(s.keysort);
     s = BuildScratch{};
     return cuda_fail(e);
   }
@@ -330,8 +383,56 @@ int err_to_rc(uint32_t err) {
 
 // The build on the device.  `bs` must hold at least n records, a tag buffer
 // of a power of two >= max(n, 8192) entries and M + 1 page offsets.
+// One access batch on stream st: picks the buffer slot, waits for the flush
+// that last used it, sizes the batch hash tables to n, links the previous
+// batch's written pages, launches, and flips the slot.
+cudaError_t access_batch(bolt* h, BatchDev b, uint32_t n, cudaStream_t st) {
+  const int s = h->slot, ps = s ^ 1;
+  if (h->flush_pending[s]) {
+    cudaError_t e = cudaStreamWaitEvent(st, h->ev_flushed[s], 0);
+    if (e != cudaSuccess) return e;
+  }
+  uint32_t ht = 256, kt = 128;
+  while (ht < 4 * n) ht <<= 1;
+  while (kt < 2 * n) kt <<= 1;
+  b.ht_mask = ht - 1;
+  b.kt_mask = kt - 1;
+  b.ht_key = h->s_ht_key[s];
+  b.ht_min = h->s_ht_min[s];
+  b.ht_d = h->s_ht_d[s];
+  b.dpage = h->s_dpage[s];
+  b.dcount = h->s_dcount[s];
+  b.dbuf = h->s_dbuf[s];
+  b.prev_valid = h->prev_valid ? 1u : 0u;
+  b.prev_ht_key = h->s_ht_key[ps];
+  b.prev_ht_d = h->s_ht_d[ps];
+  b.prev_dbuf = h->s_dbuf[ps];
+  b.prev_ht_mask = h->slot_ht_mask[ps];
+  FlushCtx fc{h->st_fl, h->ev_evicted[s], h->ev_flushed[s]};
+  cudaError_t e = launch_access(h->m, b, n, h->t, st, fc);
+  if (e != cudaSuccess) return e;
+  h->flush_pending[s] = true;
+  h->slot_ht_mask[s] = b.ht_mask;
+  h->prev_valid = true;
+  h->slot = ps;
+  return cudaSuccess;
+}
+
+// Order stream st after every pending page flush and forget the previous
+// batch (a build rewrites every page).
+void drain_flushes(bolt* h, cudaStream_t st) {
+  for (int s = 0; s < 2; s++)
+    if (h->flush_pending[s]) {
+      cudaStreamWaitEvent(st, h->ev_flushed[s], 0);
+      h->flush_pending[s] = false;
+    }
+  h->prev_valid = false;
+  h->slot = 0;
+}
+
 int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n, uint64_t seed,
               cudaStream_t st, BuildScratch& bs) {
+  drain_flushes(h, st);
   MapDev& m = h->m;
   const bolt_info_t& I = h->info;
   int rc = BOLT_OK;
@@ -359,26 +460,42 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     m.kprf[i] = kw[i];
     m.kenc[i] = kw[8 + i];
   }
-  if (h->check_keys && n > 1) {
-    ProfSpan ps(P_KEYCHECK, st);
-    k_copy_keys<<<sms * 8, 256, 0, st>>>(d_keys, n, bs.tag_cap, bs.tags);
-    count_launch(2);
-    e = sort_tags_u64(bs.tags, bs.tag_cap, 13, st);
-    if (e != cudaSuccess) return BOLT_E_CUDA;
+  // key uniqueness (Sec. 2.1): sort a copy of the keys, flag equal
+  // neighbours.  With a buffer of its own it runs on the side stream,
+  // overlapping the latency-bound P2C rounds of the build.
+  const bool check = h->check_keys && n > 1;
+  const bool side = check && bs.keysort && h->st2;
+  if (check) {
     cudaMemsetAsync(h->d_flag, 0, 4, st);
-    k_adjacent_equal<<<sms * 8, 256, 0, st>>>(bs.tags, n, h->d_flag);
-    uint32_t flag = 0;
-    e = cudaMemcpyAsync(&flag, h->d_flag, 4, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaStream_t ks = st;
+    uint64_t* kbuf = bs.tags;
+    if (side) {
+      cudaEventRecord(h->ev_fork, st);
+      cudaStreamWaitEvent(h->st2, h->ev_fork, 0);
+      ks = h->st2;
+      kbuf = bs.keysort;
+    }
+    ProfSpan ps(P_KEYCHECK, ks);
+    k_copy_keys<<<sms * 8, 256, 0, ks>>>(d_keys, n, bs.tag_cap, kbuf);
+    count_launch();
+    e = sort_tags_u64(kbuf, bs.tag_cap, 13, ks, P_KSORT_GLOBAL, P_KSORT_TILE);
     if (e != cudaSuccess) return BOLT_E_CUDA;
-    if (flag) return BOLT_E_DUPKEY;
+    k_adjacent_equal<<<sms * 8, 256, 0, ks>>>(kbuf, n, h->d_flag);
+    count_launch();
+    if (side) cudaEventRecord(h->ev_join, h->st2);
   }
   e = launch_build(m, d_keys, d_vals, n, bs, st);
   if (e != cudaSuccess) return BOLT_E_CUDA;
+  if (side) cudaStreamWaitEvent(st, h->ev_join, 0);
   uint32_t err = 0;
   h->last_st = st;
   rc = read_err(h, &err);
   if (rc) return rc;
+  if (check) {
+    uint32_t flag = 0;
+    if (cudaMemcpy(&flag, h->d_flag, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return BOLT_E_CUDA;
+    if (flag) return BOLT_E_DUPKEY;
+  }
   rc = err_to_rc(err);
   if (rc) {
     h->poisoned = true;
@@ -435,14 +552,23 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   h->vb = val_bytes;
   h->hbm_budget = hbm_budget;
   cudaError_t e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_fl, cudaStreamNonBlocking);
+  for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+    e = cudaEventCreateWithFlags(&h->ev_evicted[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_flushed[s], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
+    destroy_streams(h);
     delete h;
     return BOLT_E_CUDA;
   }
   void* p = nullptr;
   e = cudaHostAlloc(&p, MAXB * (1 + 8 + 2 * (uint64_t)val_bytes + 1) + 64, cudaHostAllocDefault);
   if (e != cudaSuccess) {
-    cudaStreamDestroy(h->st);
+    destroy_streams(h);
     delete h;
     return BOLT_E_NOMEM;
   }
@@ -456,7 +582,7 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   int rc = alloc_state(h);
   if (rc) {
     cudaFreeHost(h->h_keys);
-    cudaStreamDestroy(h->st);
+    destroy_streams(h);
     delete h;
     return rc;
   }
@@ -468,7 +594,7 @@ int bolt_destroy(bolt_t* h) {
   if (!h) return BOLT_OK;
   free_state(h);
   if (h->h_keys) cudaFreeHost(h->h_keys);
-  if (h->st) cudaStreamDestroy(h->st);
+  destroy_streams(h);
   delete h;
   return BOLT_OK;
 }
@@ -489,9 +615,14 @@ int bolt_set_param(bolt_t* h, int which, double v) {
       h->m.trace_on = h->trace_on ? 1 : 0;
       return BOLT_OK;
     case BOLT_PARAM_BATCH:
-      if (!(v >= 1.0 && v <= (double)MAXB)) return BOLT_E_ARG;
+      if (!(v >= 1.0 && v <= (double)h->cap_batch)) return BOLT_E_ARG;
       h->batch_width = (uint32_t)v;
       return BOLT_OK;
+    case BOLT_PARAM_BATCH_CAP:
+      if (!(v >= 1.0 && v <= (double)MAXB)) return BOLT_E_ARG;
+      h->cap_batch = (uint32_t)v;
+      if (h->batch_width > h->cap_batch) h->batch_width = h->cap_batch;
+      break;
     case BOLT_PARAM_TRACE_CAP:
       if (!(v >= 1.0 && v <= (double)(1ull << 32))) return BOLT_E_ARG;
       h->trace_cap = (uint64_t)v;
@@ -567,7 +698,7 @@ int bolt_access_device(bolt_t* h, const uint8_t* d_ops, const void* d_keys, cons
   if (!h) return BOLT_E_ARG;
   if (!h->initialized || h->poisoned) return BOLT_E_STATE;
   if (n == 0) return BOLT_OK;
-  if (n > MAXB || !d_ops || !d_keys || !d_vals_in || !d_vals_out) return BOLT_E_ARG;
+  if (n > h->cap_batch || !d_ops || !d_keys || !d_vals_in || !d_vals_out) return BOLT_E_ARG;
   ProfScope prof_scope(h);
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
   BatchDev b = h->b;
@@ -581,7 +712,7 @@ int bolt_access_device(bolt_t* h, const uint8_t* d_ops, const void* d_keys, cons
     if (h->last_st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
     h->last_st = st;
   }
-  cudaError_t e = launch_access(h->m, b, (uint32_t)n, h->t, st);
+  cudaError_t e = access_batch(h, b, (uint32_t)n, st);
   if (e != cudaSuccess) return BOLT_E_CUDA;
   h->t += n;
   h->batches++;
@@ -616,7 +747,7 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h->b.vin, h->h_vin, cnt * vb, cudaMemcpyHostToDevice, h->st);
     if (e != cudaSuccess) return BOLT_E_CUDA;
-    e = launch_access(h->m, h->b, (uint32_t)cnt, h->t, h->st);
+    e = access_batch(h, h->b, (uint32_t)cnt, h->st);
     if (e != cudaSuccess) return BOLT_E_CUDA;
     h->t += cnt;
     h->batches++;

@@ -208,3 +208,36 @@ def test_device_pointer_path_matches_host_path():
     assert np.array_equal(t_st.cpu().numpy(), sh)
     assert np.array_equal(h.pages(), d.pages())
     h.close(); d.close()
+
+
+def test_device_batches_back_to_back_match_oracle():
+    """Twenty device-path batches enqueued without a host sync in between on
+    a 2^12 map: consecutive batches often touch the same pages while the
+    previous batch's write-back is still in flight.  Outputs, pages, loads
+    and the trace equal the oracle's with the same batch partition."""
+    import torch
+    N, vb, bw = 1 << 12, 8, 300
+    o, g = _pair(N, vb)
+    keys, vals = W.records(3000, vb, 31)
+    assert o.init(keys, vals, 8) == 0 and g.init(keys, vals, 8) == 0
+    ops, k, vin = W.op_stream(3000, 20 * bw, vb, 32, get_frac=0.5, del_frac=0.1,
+                              absent_frac=0.2)
+    t_ops = torch.from_numpy(ops).cuda()
+    t_k = torch.from_numpy(k.view(np.int64)).cuda()
+    t_vin = torch.from_numpy(vin).cuda()
+    t_out = torch.zeros((len(ops), vb), dtype=torch.uint8, device="cuda")
+    t_st = torch.zeros(len(ops), dtype=torch.uint8, device="cuda")
+    for lo in range(0, len(ops), bw):
+        sl = slice(lo, lo + bw)
+        assert g.access_device(t_ops[sl], t_k[sl], t_vin[sl], t_out[sl], t_st[sl]) == 0
+    assert g.sync() == 0
+    vo_all, so_all = [], []
+    for lo in range(0, len(ops), bw):
+        rc, vo, so = o.access(ops[lo:lo + bw], k[lo:lo + bw], vin[lo:lo + bw])
+        assert rc == 0
+        vo_all.append(vo)
+        so_all.append(so)
+    assert np.array_equal(np.concatenate(vo_all), t_out.cpu().numpy())
+    assert np.array_equal(np.concatenate(so_all), t_st.cpu().numpy())
+    _assert_state_equal(o, g, "back-to-back device batches")
+    o.close(); g.close()
