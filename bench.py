@@ -493,15 +493,137 @@ def run_sweep(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args) -> None:
+    """Serving: 64 maps with N log-uniform in [2^12, 2^26] (32 B records),
+    admitted under a 120 GB HBM budget; Poisson request arrivals, request
+    sizes log-uniform in 1..4096 ops, 70% GET / 30% PUT, Zipf(0.99) keys per
+    map.  Saturation throughput is measured closed-loop (every request queued
+    at once); then open-loop at 0.5x and 0.8x of it: p50 / p99 latency from
+    arrival to completed batch, and accesses/s."""
+    import threading
+    import torch
+    from paper_2509_01742_b300 import bolt as B
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(0x5EED0005)
+    n_maps, vb, max_batch = args.maps, VAL_BYTES, 4096
+    log_ns = rng.uniform(12, 26, n_maps)
+    Ns = [int(2 ** x) for x in log_ns]
+    srv = B.BoltServer(hbm_budget=120 * 10**9, max_batch=max_batch)
+    t0 = time.perf_counter()
+    mids = []
+    for j, N in enumerate(Ns):
+        keys, vals = make_records_vb(N, vb, SEED_DATA + j)
+        mids.append(srv.add_map(N, vb, keys, vals, SEED_MAP + j))
+    while any(srv.map_state(m) == 0 for m in mids):
+        time.sleep(0.05)
+    assert all(srv.map_state(m) == 1 for m in mids)
+    build_s = time.perf_counter() - t0
+    zipfs = {}
+
+    def gen_requests(count, seed):
+        g = np.random.default_rng(seed)
+        out = []
+        for _ in range(count):
+            j = int(g.integers(0, n_maps))
+            n = int(np.exp(g.uniform(0, np.log(max_batch))))
+            N = Ns[j]
+            if N not in zipfs:
+                zipfs[N] = W.Zipf(N, 0.99)
+            ranks = zipfs[N].sample(g, n)
+            keys = W.key_of(W.mix64(ranks) % np.uint64(N))
+            ops = (g.random(n) >= 0.7).astype(np.uint8)  # 70% GET (0), 30% PUT (1)
+            vin = g.integers(0, 256, size=(n, vb), dtype=np.uint8)
+            out.append((j, ops, keys, vin))
+        return out
+
+    def run(reqs, rate_ops=None):
+        """Submit requests (at Poisson times for the given op rate, or all at
+        once), wait for all; returns (latencies_us, ops, seconds)."""
+        ids = [None] * len(reqs)
+        lat = [0.0] * len(reqs)
+        done_ev = threading.Event()
+
+        def waiter():
+            for i in range(len(reqs)):
+                while ids[i] is None:
+                    time.sleep(0)
+                j, ops, _, _ = reqs[i]
+                rc, _, _, info = srv.wait(ids[i], len(ops), mids[j], timeout_ms=600000)
+                assert rc == 0, rc
+                lat[i] = (info.done_us - info.submit_us, info.submit_us, info.done_us)
+            done_ev.set()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        total = sum(len(r[1]) for r in reqs)
+        g = np.random.default_rng(7)
+        mean_n = total / len(reqs)
+        start = time.perf_counter()
+        t_next = start
+        for i, (j, ops, keys, vin) in enumerate(reqs):
+            if rate_ops:
+                t_next += g.exponential(mean_n / rate_ops)
+                while time.perf_counter() < t_next:
+                    pass
+            ids[i] = srv.submit(mids[j], ops, keys, vin)
+        done_ev.wait()
+        th.join()
+        first = min(x[1] for x in lat)
+        last = max(x[2] for x in lat)
+        return np.array([x[0] for x in lat]), total, (last - first) * 1e-6
+
+    warm = gen_requests(200, 1)
+    run(warm)
+    sat_reqs = gen_requests(args.requests, 2)
+    lat, ops, secs = run(sat_reqs)
+    sat = ops / secs
+    levels = []
+    for frac, seed in ((0.5, 3), (0.8, 4)):
+        reqs = gen_requests(args.requests, seed)
+        lat, ops, secs = run(reqs, rate_ops=frac * sat)
+        levels.append({"offered_fraction": frac, "offered_accesses_per_s": round(frac * sat, 1),
+                       "accesses_per_s": round(ops / secs, 1),
+                       "p50_us": round(float(np.percentile(lat, 50)), 1),
+                       "p99_us": round(float(np.percentile(lat, 99)), 1),
+                       "requests": len(reqs)})
+    st = srv.stats()
+    line = {"metric": "served p50/p99 latency and accesses/s", "unit": "accesses/s",
+            "value": round(sat, 1), "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"{n_maps} maps, N log-uniform in [2^12, 2^26] "
+                                   "(32 B records), 120 GB HBM budget, Poisson arrivals, "
+                                   "request size log-uniform 1..4096, 70% GET / 30% PUT, "
+                                   "Zipf(0.99) keys", "records": int(sum(Ns)),
+                       "max_batch": max_batch},
+            "saturation": {"accesses_per_s": round(sat, 1), "requests": len(sat_reqs)},
+            "levels": levels, "build_s": round(build_s, 2),
+            "batches": st["batches"], "hbm_used_bytes": st["used"]}
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
+def make_records_vb(n: int, vb: int, seed: int):
+    keys = np.empty(n, dtype=np.uint64)
+    for lo in range(0, n, 1 << 24):
+        hi = min(n, lo + (1 << 24))
+        keys[lo:hi] = W.key_of(np.arange(lo, hi, dtype=np.uint64))
+    rng = np.random.default_rng(seed)
+    vals = np.frombuffer(rng.bytes(n * vb), dtype=np.uint8).reshape(n, vb)
+    return keys, vals
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("bolt", "reference"), default="bolt")
-    ap.add_argument("--config", choices=("headline", "zipf", "w1"), default="headline",
+    ap.add_argument("--config", choices=("headline", "zipf", "w1", "serve"), default="headline",
                     help="headline: the JSON line above; zipf: batch-width sweep on the "
-                         "skewed 2^24 x 64 B map; w1: one access per call vs batches of 4096")
+                         "skewed 2^24 x 64 B map; w1: one access per call vs batches of 4096; "
+                         "serve: 64 maps behind the continuous-batching server")
+    ap.add_argument("--maps", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=6000)
     ap.add_argument("--log-n", type=int, default=LOG_N)
     ap.add_argument("--accesses", type=int, default=N_ACCESS)
     ap.add_argument("--no-e2e", action="store_true")
@@ -511,6 +633,8 @@ def main():
         print("note: at least 3 warm-up steps are required for a valid number", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "serve":
+        run_serve(args)
     elif args.config != "headline":
         run_sweep(args)
     else:

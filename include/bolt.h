@@ -245,6 +245,104 @@ typedef struct {
  * events into *out; reset != 0 clears the accumulated profile. */
 BOLT_API int bolt_read_profile(bolt_t* h, bolt_profile_t* out, int reset);
 
+/* Autotuner results (bolt_autotune). */
+#define BOLT_TUNE_WIDTHS 6
+typedef struct {
+  uint32_t sort_log_tile;      /* bitonic tile picked: 2^12 or 2^13 elements */
+  uint32_t batch_width;        /* access batch width picked for bolt_access */
+  double sort_ms[2];           /* sort time of a tag-sized array, tile 2^12 / 2^13 */
+  uint32_t widths[BOLT_TUNE_WIDTHS];
+  double width_us[BOLT_TUNE_WIDTHS];  /* device time per batch at each width
+                                         (0: not measured, above the capacity) */
+} bolt_tune_t;
+
+/* bolt_autotune -- pick performance knobs by measuring them on this device:
+ * the bitonic tile of later builds (a tag-sized scratch array is sorted with
+ * each tile; allocates it) and, when a sample of present keys is given, the
+ * batch width bolt_access splits host calls into: Get batches of 64..65536
+ * ops over the sample, the highest accesses/s whose device time per batch is
+ * at most max_batch_us (<= 0: no bound).  The knobs change no result.  The
+ * tuning Gets are real accesses: they remap their keys (contents unchanged,
+ * layout and trace advanced).  Errors as bolt_access. */
+BOLT_API int bolt_autotune(bolt_t* h, const void* sample_keys, uint64_t n_sample,
+                           double max_batch_us, bolt_tune_t* out);
+
+/* bolt_trim -- release the build scratch (tags, PRF tables, staging); the
+ * next bolt_init allocates it again. */
+BOLT_API int bolt_trim(bolt_t* h);
+
+/* bolt_footprint -- device bytes the handle holds: resident state and batch
+ * buffers, and build scratch (including the host-pointer staging copy). */
+BOLT_API int bolt_footprint(const bolt_t* h, uint64_t* resident_bytes, uint64_t* scratch_bytes);
+
+/* bolt_plan_bytes -- host-only estimate of the same two figures for a map of
+ * capacity N (budget policy for alpha, c = 8, default trace capacity) with
+ * batch buffers for batch_cap ops and a build of n_init records. */
+BOLT_API int bolt_plan_bytes(uint64_t N, uint32_t val_bytes, uint64_t hbm_budget,
+                             uint32_t batch_cap, uint64_t n_init, uint64_t* resident_bytes,
+                             uint64_t* build_bytes);
+
+/* ------------------------------------------------------------------------
+ * Serving many maps (continuous batching).  The paper serves one command
+ * stream on one device; this layer keeps many maps resident and batches
+ * their requests as they arrive.
+ *
+ * A server owns a set of maps and a scheduler thread.  Maps are admitted, in
+ * the order they were added, while their planned device footprint (state,
+ * batch buffers, build scratch) fits `hbm_budget`; the rest wait until a
+ * removed map frees memory.  A request is up to `max_batch` Get/Put/Delete
+ * ops on one map; requests queue per map, and whenever a map has no batch on
+ * the GPU the scheduler packs its queued requests (arrival order, at most
+ * max_batch ops) into one access batch on the map's stream, so batches of
+ * different maps overlap on the device.  Each batch is one bolt access batch:
+ * a request's values and status do not depend on the requests it shares a
+ * batch with; the per-map batch log reproduces ciphertexts and the trace.
+ * All server calls are thread-safe; results are returned by bolt_server_wait.
+ * ------------------------------------------------------------------------ */
+typedef struct bolt_server bolt_server_t;
+
+typedef struct {
+  uint64_t id;
+  uint32_t map, n;
+  int rc;                      /* BOLT_OK or the batch's error */
+  double submit_us, start_us, done_us;  /* microseconds since server creation:
+                                           arrival, batch enqueue, batch done */
+} bolt_req_info_t;
+
+typedef struct {
+  uint64_t budget, used;       /* HBM budget and planned bytes of admitted maps */
+  uint64_t batches, ops;       /* completed batches and operations */
+  uint32_t maps_pending, maps_ready;
+  uint64_t queued;             /* requests waiting for a batch */
+} bolt_server_stats_t;
+
+BOLT_API int bolt_server_create(uint64_t hbm_budget, uint32_t max_batch, bolt_server_t** out);
+/* add a map of capacity N built from n (key, value) records (HOST pointers,
+ * copied); BOLT_E_NOMEM if its footprint alone exceeds the budget */
+BOLT_API int bolt_server_add_map(bolt_server_t* s, uint64_t N, uint32_t val_bytes,
+                                 const void* keys, const void* vals, uint64_t n, uint64_t seed,
+                                 uint32_t* map_id);
+/* 0 pending admission, 1 ready, 2 removed, or the map's error code */
+BOLT_API int bolt_server_map_state(bolt_server_t* s, uint32_t map_id);
+/* remove once its queued requests are served; frees its memory */
+BOLT_API int bolt_server_remove_map(bolt_server_t* s, uint32_t map_id);
+/* queue a request (HOST pointers, copied): n <= max_batch ops */
+BOLT_API int bolt_server_submit(bolt_server_t* s, uint32_t map_id, const uint8_t* ops,
+                                const void* keys, const void* vals_in, uint32_t n,
+                                uint64_t* req_id);
+/* wait for a request (timeout_ms < 0: forever), copy its outputs (HOST,
+ * n * val_bytes and n bytes, either may be NULL) and its timestamps, and
+ * release it; returns its result code or BOLT_E_TIMEOUT */
+BOLT_API int bolt_server_wait(bolt_server_t* s, uint64_t req_id, void* vals_out,
+                              uint8_t* status_out, bolt_req_info_t* info, int timeout_ms);
+/* sizes of the batches run on a map so far (copy up to cap, *count = all) */
+BOLT_API int bolt_server_map_batches(bolt_server_t* s, uint32_t map_id, uint32_t* sizes,
+                                     uint64_t cap, uint64_t* count);
+/* the handle of a ready map, for inspection while the server is quiescent */
+BOLT_API int bolt_server_map_handle(bolt_server_t* s, uint32_t map_id, bolt_t** out);
+BOLT_API int bolt_server_stats(bolt_server_t* s, bolt_server_stats_t* out);
+BOLT_API int bolt_server_destroy(bolt_server_t* s);
+
 /* bolt_strerror -- static description of an error code. */
 BOLT_API const char* bolt_strerror(int code);
 

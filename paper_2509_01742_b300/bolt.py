@@ -63,6 +63,28 @@ class bolt_profile_t(ctypes.Structure):
                 ("ms", ctypes.c_double * 13)]
 
 
+class bolt_tune_t(ctypes.Structure):
+    _fields_ = [("sort_log_tile", ctypes.c_uint32), ("batch_width", ctypes.c_uint32),
+                ("sort_ms", ctypes.c_double * 2), ("widths", ctypes.c_uint32 * 6),
+                ("width_us", ctypes.c_double * 6)]
+
+
+class bolt_req_info_t(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("map", ctypes.c_uint32), ("n", ctypes.c_uint32),
+                ("rc", ctypes.c_int), ("submit_us", ctypes.c_double),
+                ("start_us", ctypes.c_double), ("done_us", ctypes.c_double)]
+
+
+class bolt_server_stats_t(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_uint64), ("used", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("ops", ctypes.c_uint64),
+                ("maps_pending", ctypes.c_uint32), ("maps_ready", ctypes.c_uint32),
+                ("queued", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _P, _u64, _u32, _i = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
 _SIGS = {
     "bolt_create": ([_u64, _u32, _u32, _u64, ctypes.POINTER(_P)], _i),
@@ -82,6 +104,21 @@ _SIGS = {
     "bolt_read_loads": ([_P, _P], _i),
     "bolt_read_rowcounts": ([_P, _P], _i),
     "bolt_read_profile": ([_P, ctypes.POINTER(bolt_profile_t), _i], _i),
+    "bolt_trim": ([_P], _i),
+    "bolt_autotune": ([_P, _P, _u64, ctypes.c_double, ctypes.POINTER(bolt_tune_t)], _i),
+    "bolt_footprint": ([_P, ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i),
+    "bolt_plan_bytes": ([_u64, _u32, _u64, _u32, _u64, ctypes.POINTER(_u64),
+                         ctypes.POINTER(_u64)], _i),
+    "bolt_server_create": ([_u64, _u32, ctypes.POINTER(_P)], _i),
+    "bolt_server_add_map": ([_P, _u64, _u32, _P, _P, _u64, _u64, ctypes.POINTER(_u32)], _i),
+    "bolt_server_map_state": ([_P, _u32], _i),
+    "bolt_server_remove_map": ([_P, _u32], _i),
+    "bolt_server_submit": ([_P, _u32, _P, _P, _P, _u32, ctypes.POINTER(_u64)], _i),
+    "bolt_server_wait": ([_P, _u64, _P, _P, ctypes.POINTER(bolt_req_info_t), _i], _i),
+    "bolt_server_map_batches": ([_P, _u32, _P, _u64, ctypes.POINTER(_u64)], _i),
+    "bolt_server_map_handle": ([_P, _u32, ctypes.POINTER(_P)], _i),
+    "bolt_server_stats": ([_P, ctypes.POINTER(bolt_server_stats_t)], _i),
+    "bolt_server_destroy": ([_P], _i),
     "bolt_strerror": ([_i], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -221,6 +258,23 @@ class BoltMap:
             out[name] = {"spans": int(p.spans[c]), "ms": float(p.ms[c])}
         return out
 
+    def autotune(self, sample_keys=None, max_batch_us: float = 0.0) -> dict:
+        t = bolt_tune_t()
+        if sample_keys is not None:
+            sk = np.ascontiguousarray(sample_keys, dtype=np.uint64)
+            rc = bolt_autotune(self._h, _np_ptr(sk), len(sk), max_batch_us, ctypes.byref(t))
+        else:
+            rc = bolt_autotune(self._h, None, 0, max_batch_us, ctypes.byref(t))
+        _check(rc, "bolt_autotune")
+        return {"sort_log_tile": t.sort_log_tile, "batch_width": t.batch_width,
+                "sort_ms": list(t.sort_ms), "widths": list(t.widths),
+                "width_us": list(t.width_us)}
+
+    def footprint(self):
+        r, s = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(bolt_footprint(self._h, ctypes.byref(r), ctypes.byref(s)), "bolt_footprint")
+        return r.value, s.value
+
     def loads(self) -> np.ndarray:
         out = np.zeros(self.info()["B"], dtype=np.uint8)
         _check(bolt_read_loads(self._h, _np_ptr(out)), "bolt_read_loads")
@@ -230,3 +284,87 @@ class BoltMap:
         out = np.zeros(self.info()["rows"], dtype=np.uint8)
         _check(bolt_read_rowcounts(self._h, _np_ptr(out)), "bolt_read_rowcounts")
         return out
+
+
+def plan_bytes(N: int, val_bytes: int, batch_cap: int = BOLT_MAX_BATCH, n_init: int = 0,
+               hbm_budget: int = 2**64 - 1):
+    r, s = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(bolt_plan_bytes(N, val_bytes, hbm_budget, batch_cap, n_init, ctypes.byref(r),
+                           ctypes.byref(s)), "bolt_plan_bytes")
+    return r.value, s.value
+
+
+class BoltServer:
+    """Continuous-batching server over many maps (bolt_server_* calls)."""
+
+    def __init__(self, hbm_budget: int, max_batch: int = 4096):
+        self._s = ctypes.c_void_p()
+        _check(bolt_server_create(hbm_budget, max_batch, ctypes.byref(self._s)),
+               "bolt_server_create")
+        self.max_batch = max_batch
+        self.vb = {}
+
+    def close(self):
+        if self._s:
+            bolt_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_map(self, N: int, val_bytes: int, keys, vals, seed: int) -> int:
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        vals = np.ascontiguousarray(vals, dtype=np.uint8)
+        mid = ctypes.c_uint32()
+        _check(bolt_server_add_map(self._s, N, val_bytes, _np_ptr(keys), _np_ptr(vals),
+                                   len(keys), seed, ctypes.byref(mid)), "bolt_server_add_map")
+        self.vb[mid.value] = val_bytes
+        return mid.value
+
+    def map_state(self, mid: int) -> int:
+        return bolt_server_map_state(self._s, mid)
+
+    def remove_map(self, mid: int):
+        _check(bolt_server_remove_map(self._s, mid), "bolt_server_remove_map")
+
+    def submit(self, mid: int, ops, keys, vals_in) -> int:
+        ops = np.ascontiguousarray(ops, dtype=np.uint8)
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        vin = np.ascontiguousarray(vals_in, dtype=np.uint8)
+        rid = ctypes.c_uint64()
+        _check(bolt_server_submit(self._s, mid, _np_ptr(ops), _np_ptr(keys), _np_ptr(vin),
+                                  len(ops), ctypes.byref(rid)), "bolt_server_submit")
+        return rid.value
+
+    def wait(self, rid: int, n: int, mid: int, timeout_ms: int = -1):
+        vout = np.zeros((n, self.vb[mid]), dtype=np.uint8)
+        status = np.zeros(n, dtype=np.uint8)
+        info = bolt_req_info_t()
+        rc = bolt_server_wait(self._s, rid, _np_ptr(vout), _np_ptr(status), ctypes.byref(info),
+                              timeout_ms)
+        return rc, vout, status, info
+
+    def batches(self, mid: int) -> np.ndarray:
+        cnt = ctypes.c_uint64()
+        _check(bolt_server_map_batches(self._s, mid, None, 0, ctypes.byref(cnt)), "batches")
+        out = np.zeros(max(1, cnt.value), dtype=np.uint32)
+        _check(bolt_server_map_batches(self._s, mid, _np_ptr(out), cnt.value, ctypes.byref(cnt)),
+               "batches")
+        return out[:cnt.value]
+
+    def map_pages(self, mid: int) -> np.ndarray:
+        h = ctypes.c_void_p()
+        _check(bolt_server_map_handle(self._s, mid, ctypes.byref(h)), "bolt_server_map_handle")
+        o = bolt_info_t()
+        _check(bolt_get_info(h, ctypes.byref(o)), "bolt_get_info")
+        out = np.zeros((o.M, o.page_bytes), dtype=np.uint8)
+        _check(bolt_read_pages(h, 0, o.M, _np_ptr(out)), "bolt_read_pages")
+        return out
+
+    def stats(self) -> dict:
+        s = bolt_server_stats_t()
+        _check(bolt_server_stats(self._s, ctypes.byref(s)), "bolt_server_stats")
+        return s.as_dict()

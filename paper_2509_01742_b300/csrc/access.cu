@@ -37,29 +37,44 @@ __device__ __forceinline__ uint32_t key_hash(uint64_t k, uint32_t mask) {
 // per op: PRF pairs and rows, and the op's grouping key.  Equal keys share a
 // hash-table slot (claimed by the first op to reach it), so sorting
 // (slot << 16 | op) lists every key's ops together, in op order.
-__global__ void k_stage(MapDev m, BatchDev b, uint32_t n, uint32_t n_sort, uint64_t t0) {
-  uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+// Batches of at most 4096 ops pack (slot << 12 | op) into 32 bits (slot <
+// 8192); larger ones use (slot << 16 | op) in 64 bits.
+__global__ void k_stage(MapDev m, BatchDev b, uint32_t n, uint32_t n_sort, uint64_t t0,
+                        int keys32) {
+  // three threads per op: 0 = grouping key + DUMMY pair, 1 = REMAP pair,
+  // 2 = position-map rows (one ChaCha20 block each)
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t i = tid / 3, kind = tid % 3;
   if (i >= n_sort) return;
   if (i >= n) {
-    b.skeys[i] = ~0ull;
+    if (kind == 0) {
+      if (keys32) reinterpret_cast<uint32_t*>(b.skeys)[i] = ~0u;
+      else b.skeys[i] = ~0ull;
+    }
     return;
   }
   const uint64_t key = b.keys[i];
-  uint32_t h = key_hash(key, b.kt_mask);
-  for (uint32_t probe = 0; probe <= b.kt_mask; probe++) {
-    const uint32_t old = atomicCAS(b.kt_own + h, 0u, i + 1);
-    if (old == 0 || b.keys[old - 1] == key) break;
-    h = (h + 1) & b.kt_mask;
-  }
-  b.skeys[i] = ((uint64_t)h << 16) | i;
   uint32_t p1, p2;
-  prf_pair(m, DOM_DUMMY, t0 + i, p1, p2);
-  b.pair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
-  prf_pair(m, DOM_REMAP, t0 + i, p1, p2);
-  b.rpair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
-  uint32_t rows[4];
-  prf_rows(m, key, rows);
-  *reinterpret_cast<uint4*>(b.rows + 4 * (uint64_t)i) = make_uint4(rows[0], rows[1], rows[2], rows[3]);
+  if (kind == 0) {
+    uint32_t h = key_hash(key, b.kt_mask);
+    for (uint32_t probe = 0; probe <= b.kt_mask; probe++) {
+      const uint32_t old = atomicCAS(b.kt_own + h, 0u, i + 1);
+      if (old == 0 || b.keys[old - 1] == key) break;
+      h = (h + 1) & b.kt_mask;
+    }
+    if (keys32) reinterpret_cast<uint32_t*>(b.skeys)[i] = (h << 12) | i;
+    else b.skeys[i] = ((uint64_t)h << 16) | i;
+    prf_pair(m, DOM_DUMMY, t0 + i, p1, p2);
+    b.pair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
+  } else if (kind == 1) {
+    prf_pair(m, DOM_REMAP, t0 + i, p1, p2);
+    b.rpair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
+  } else {
+    uint32_t rows[4];
+    prf_rows(m, key, rows);
+    *reinterpret_cast<uint4*>(b.rows + 4 * (uint64_t)i) =
+        make_uint4(rows[0], rows[1], rows[2], rows[3]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -94,11 +109,20 @@ __device__ __forceinline__ int32_t block_excl_max(int32_t v, int32_t* sh) {
 
 constexpr int GROUP_THREADS = 1024;
 
-// grouping keys sort as (slot << 16 | op): a group is a run of equal slots
-__device__ __forceinline__ uint32_t g_slot(uint64_t sk) { return (uint32_t)(sk >> 16); }
-__device__ __forceinline__ uint32_t g_op(uint64_t sk) { return (uint32_t)(sk & 0xffffu); }
+// grouping keys sort as (slot << SHIFT | op): a group is a run of equal slots
+template <typename K>
+struct GroupKey {
+  static constexpr int SHIFT = sizeof(K) == 4 ? 12 : 16;
+  static __device__ __forceinline__ uint32_t slot(K k) { return (uint32_t)(k >> SHIFT); }
+  static __device__ __forceinline__ uint32_t op(K k) {
+    return (uint32_t)(k & (((K)1 << SHIFT) - 1));
+  }
+};
 
+template <typename K>
 __global__ void __launch_bounds__(GROUP_THREADS) k_group(BatchDev b, uint32_t n) {
+  using G = GroupKey<K>;
+  const K* sk = reinterpret_cast<const K*>(b.skeys);
   __shared__ int32_t sh[32];
   const uint32_t per = (n + GROUP_THREADS - 1) / GROUP_THREADS;
   const uint32_t lo = threadIdx.x * per;
@@ -106,25 +130,25 @@ __global__ void __launch_bounds__(GROUP_THREADS) k_group(BatchDev b, uint32_t n)
   // local maxima of group-head positions and writer positions
   int32_t hmax = -1, wmax = -1;
   for (uint32_t s = lo; s < hi; s++) {
-    const uint64_t e = b.skeys[s];
-    const bool head = s == 0 || g_slot(b.skeys[s - 1]) != g_slot(e);
+    const K e = sk[s];
+    const bool head = s == 0 || G::slot(sk[s - 1]) != G::slot(e);
     if (head) hmax = (int32_t)s;
-    if (b.ops[g_op(e)] != OP_GET) wmax = (int32_t)s;
+    if (b.ops[G::op(e)] != OP_GET) wmax = (int32_t)s;
   }
   int32_t hcar = block_excl_max(hmax, sh);
   int32_t wcar = block_excl_max(wmax, sh);
   for (uint32_t s = lo; s < hi; s++) {
-    const uint64_t e = b.skeys[s];
-    const uint32_t i = g_op(e);
-    const bool head = s == 0 || g_slot(b.skeys[s - 1]) != g_slot(e);
+    const K e = sk[s];
+    const uint32_t i = G::op(e);
+    const bool head = s == 0 || G::slot(sk[s - 1]) != G::slot(e);
     if (head) hcar = (int32_t)s;
-    const uint32_t lead = g_op(b.skeys[hcar]);
+    const uint32_t lead = G::op(sk[hcar]);
     // previous writer in the same group (strictly before s)
-    b.prevw[i] = wcar >= hcar ? g_op(b.skeys[wcar]) : NONE32;
+    b.prevw[i] = wcar >= hcar ? G::op(sk[wcar]) : NONE32;
     b.leader[i] = lead;
     if (b.ops[i] != OP_GET) wcar = (int32_t)s;
-    const bool last = s + 1 == n || g_slot(b.skeys[s + 1]) != g_slot(e);
-    if (last) b.lastw[lead] = wcar >= hcar ? g_op(b.skeys[wcar]) : NONE32;
+    const bool last = s + 1 == n || G::slot(sk[s + 1]) != G::slot(e);
+    if (last) b.lastw[lead] = wcar >= hcar ? G::op(sk[wcar]) : NONE32;
   }
 }
 
@@ -185,47 +209,92 @@ __global__ void k_lookup(MapDev m, BatchDev b, uint32_t n) {
   }
 }
 
-// one CTA: distinct pages in first-read order and the host-access trace
-constexpr int PAGES_THREADS = 1024;
+// Distinct pages in first-read order and the host-access trace, in three
+// passes over the 2n read positions: per-block counts of valid reads and of
+// first reads, one scan of the block counts, then ranks and outputs.
+constexpr int PAGES_BLOCK = 256;
 
-__global__ void __launch_bounds__(PAGES_THREADS) k_pages(MapDev m, BatchDev b, uint32_t n) {
+__device__ __forceinline__ void pos_flags(const BatchDev& b, uint32_t p, uint32_t np, bool& valid,
+                                          bool& first, uint32_t& q, uint32_t& slot) {
+  valid = first = false;
+  q = NONE32;
+  slot = 0;
+  if (p >= np) return;
+  q = b.pos_page[p];
+  if (q == NONE32) return;
+  valid = true;
+  slot = b.pos_slot[p];
+  first = b.ht_min[slot] == p;
+}
+
+__global__ void __launch_bounds__(PAGES_BLOCK) k_pages_count(BatchDev b, uint32_t np,
+                                                             uint32_t* block_cnt) {
   __shared__ uint32_t sh[32];
-  const uint32_t np = 2 * n;
-  const uint32_t per = (np + PAGES_THREADS - 1) / PAGES_THREADS;
-  const uint32_t lo = threadIdx.x * per, hi = min(np, lo + per);
-  uint32_t nvalid = 0, nfirst = 0;
-  for (uint32_t p = lo; p < hi; p++) {
-    const uint32_t q = b.pos_page[p];
-    if (q == NONE32) continue;
-    nvalid++;
-    if (b.ht_min[b.pos_slot[p]] == p) nfirst++;
+  const uint32_t p = blockIdx.x * PAGES_BLOCK + threadIdx.x;
+  bool valid, first;
+  uint32_t q, slot;
+  pos_flags(b, p, np, valid, first, q, slot);
+  uint32_t tv, tf;
+  block_excl_scan(valid ? 1u : 0u, sh, tv);
+  block_excl_scan(first ? 1u : 0u, sh, tf);
+  if (threadIdx.x == 0) {
+    block_cnt[2 * blockIdx.x] = tv;
+    block_cnt[2 * blockIdx.x + 1] = tf;
   }
-  uint32_t tot_valid, tot_first;
-  uint32_t rbase = block_excl_scan(nvalid, sh, tot_valid);
-  uint32_t dbase = block_excl_scan(nfirst, sh, tot_first);
-  const uint64_t tbase = m.trace_on ? *m.trace_len : 0;
-  for (uint32_t p = lo; p < hi; p++) {
-    const uint32_t q = b.pos_page[p];
-    if (q == NONE32) continue;
-    if (m.trace_on && tbase + rbase < m.trace_cap) m.trace[tbase + rbase] = q;
-    rbase++;
-    const uint32_t slot = b.pos_slot[p];
-    if (b.ht_min[slot] == p) {
-      b.dpage[dbase] = q;
-      b.ht_d[slot] = dbase;
-      const uint64_t w = tbase + tot_valid + dbase;
-      if (m.trace_on && w < m.trace_cap) m.trace[w] = q | 0x80000000u;
-      dbase++;
-    }
-  }
+}
+
+// one block: exclusive scan of the per-block (valid, first) counts in place
+__global__ void __launch_bounds__(1024) k_pages_scan(MapDev m, BatchDev b, uint32_t nblocks,
+                                                     uint32_t* block_cnt) {
+  __shared__ uint32_t sh[32];
+  __shared__ uint32_t carry_v, carry_f;
+  if (threadIdx.x == 0) carry_v = carry_f = 0;
   __syncthreads();
-  for (uint32_t p = lo; p < hi; p++) {
-    const uint32_t q = b.pos_page[p];
-    b.pos_d[p] = q == NONE32 ? NONE32 : b.ht_d[b.pos_slot[p]];
+  for (uint32_t lo = 0; lo < nblocks; lo += 1024) {
+    const uint32_t i = lo + threadIdx.x;
+    const uint32_t v = i < nblocks ? block_cnt[2 * i] : 0;
+    const uint32_t f = i < nblocks ? block_cnt[2 * i + 1] : 0;
+    uint32_t tv, tf;
+    const uint32_t ev = block_excl_scan(v, sh, tv);
+    const uint32_t ef = block_excl_scan(f, sh, tf);
+    if (i < nblocks) {
+      block_cnt[2 * i] = carry_v + ev;
+      block_cnt[2 * i + 1] = carry_f + ef;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      carry_v += tv;
+      carry_f += tf;
+    }
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
-    *b.dcount = tot_first;
-    if (m.trace_on) *m.trace_len = tbase + tot_valid + tot_first;
+    *b.dcount = carry_f;
+    const uint64_t tbase = m.trace_on ? *m.trace_len : 0;
+    b.trace_base[0] = tbase;
+    b.trace_base[1] = carry_v;
+    if (m.trace_on) *m.trace_len = tbase + carry_v + carry_f;
+  }
+}
+
+__global__ void __launch_bounds__(PAGES_BLOCK) k_pages_emit(MapDev m, BatchDev b, uint32_t np,
+                                                            const uint32_t* block_cnt) {
+  __shared__ uint32_t sh[32];
+  const uint32_t p = blockIdx.x * PAGES_BLOCK + threadIdx.x;
+  bool valid, first;
+  uint32_t q, slot;
+  pos_flags(b, p, np, valid, first, q, slot);
+  uint32_t tv, tf;
+  const uint32_t rv = block_excl_scan(valid ? 1u : 0u, sh, tv) + block_cnt[2 * blockIdx.x];
+  const uint32_t d = block_excl_scan(first ? 1u : 0u, sh, tf) + block_cnt[2 * blockIdx.x + 1];
+  if (!valid) return;
+  const uint64_t tbase = b.trace_base[0], tot_valid = b.trace_base[1];
+  if (m.trace_on && tbase + rv < m.trace_cap) m.trace[tbase + rv] = q;
+  if (first) {
+    b.dpage[d] = q;
+    b.ht_d[slot] = d;
+    const uint64_t w = tbase + tot_valid + d;
+    if (m.trace_on && w < m.trace_cap) m.trace[w] = q | 0x80000000u;
   }
 }
 
@@ -306,7 +375,8 @@ __global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
   uint8_t* out = b.init_val + (uint64_t)i * m.vb;
   const uint32_t nw = m.vb / 8;
   if (meta_loc(meta) == LOC_HOST) {
-    const uint32_t d = b.pos_d[2 * i + which];
+    const uint32_t pos = 2 * i + which;
+    const uint32_t d = b.pos_page[pos] == NONE32 ? NONE32 : b.ht_d[b.pos_slot[pos]];
     if (d == NONE32) {
       if (lane == 0) set_err(m, ERR_NOTFOUND);
       return;
@@ -472,14 +542,11 @@ __global__ void k_remap_decide(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
   }
 }
 
-__global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
-  const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= hi || b.leader[i] != i || !b.fpres[i]) return;
-  const uint32_t dest = b.rdest[i];
-  if (byte_inc(m.load, dest) + 1 > m.lmax) {
-    set_err(m, ERR_LOAD);
-    return;
-  }
+// place leader i in its new bin: a value-store slot from the ring, the
+// position-map entry (a free slot of the chosen row for a new key), and the
+// reverse-index entry for a stash item; the counts are already bumped
+__device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, uint32_t i,
+                                            uint32_t dest) {
   const uint64_t pr = b.rpair[i];
   const uint32_t which = dest == (uint32_t)(pr >> 32) ? 1u : 0u;
   const unsigned long long pos = atomicAdd(m.ring_ctr, 1ull);
@@ -494,10 +561,6 @@ __global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
   const uint64_t key = b.keys[i];
   if (slot == NONE32) {
     const uint32_t row = b.rrow[i];
-    if (byte_inc(m.rowcnt, row) + 1 > m.R) {
-      set_err(m, ERR_ROW);
-      return;
-    }
     for (uint32_t s = 0; s < m.R; s++) {
       const uint64_t idx = (uint64_t)row * m.R + s;
       if (atomicCAS(m.pm_meta + idx, 0u, meta) == 0u) {
@@ -531,6 +594,86 @@ __global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
   }
 }
 
+__global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
+  const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi || b.leader[i] != i || !b.fpres[i]) return;
+  const uint32_t dest = b.rdest[i];
+  if (byte_inc(m.load, dest) + 1 > m.lmax) {
+    set_err(m, ERR_LOAD);
+    return;
+  }
+  if (b.hit[i] == NONE32 && byte_inc(m.rowcnt, b.rrow[i]) + 1 > m.R) {
+    set_err(m, ERR_ROW);
+    return;
+  }
+  remap_place(m, b, i, dest);
+}
+
+// Small maps (B <= 2^17 bins, <= 2^16 rows): every P2C round of the batch in
+// one CTA, on shared-memory copies of the bin loads and row counts (same
+// round-start decisions and counts as the launch-per-round path); the
+// placement work then runs in parallel in k_remap_rest.
+constexpr uint32_t REMAP_SMEM_MAX_BINS = 1u << 17;
+constexpr uint32_t REMAP_SMEM_MAX_ROWS = 1u << 16;
+
+__device__ __forceinline__ uint32_t sbyte_get(const uint32_t* w, uint32_t i) {
+  return (w[i >> 2] >> ((i & 3) * 8)) & 0xffu;
+}
+__device__ __forceinline__ uint32_t sbyte_inc(uint32_t* w, uint32_t i) {
+  const uint32_t sh = (i & 3) * 8;
+  return (atomicAdd(w + (i >> 2), 1u << sh) >> sh) & 0xffu;
+}
+
+__global__ void __launch_bounds__(1024) k_remap_smem(MapDev m, BatchDev b, uint32_t n) {
+  extern __shared__ uint32_t rsm[];
+  const uint32_t lw = (uint32_t)(m.B + 3) / 4, rw = (uint32_t)(m.rows + 3) / 4;
+  uint32_t* sload = rsm;
+  uint32_t* srow = rsm + lw;
+  for (uint32_t w = threadIdx.x; w < lw; w += blockDim.x) sload[w] = m.load[w];
+  for (uint32_t w = threadIdx.x; w < rw; w += blockDim.x) srow[w] = m.rowcnt[w];
+  __syncthreads();
+  uint32_t err = 0;
+  for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+    const uint32_t hi = (uint32_t)(lo + m.Wr < n ? lo + m.Wr : n);
+    for (uint32_t i = (uint32_t)lo + threadIdx.x; i < hi; i += blockDim.x) {
+      if (b.leader[i] != i || !b.fpres[i]) continue;
+      const uint64_t pr = b.rpair[i];
+      const uint32_t p1 = (uint32_t)pr, p2 = (uint32_t)(pr >> 32);
+      b.rdest[i] = sbyte_get(sload, p1) <= sbyte_get(sload, p2) ? p1 : p2;
+      if (b.hit[i] == NONE32) {
+        const uint4 r4 = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
+        const uint32_t rows[4] = {r4.x, r4.y, r4.z, r4.w};
+        uint32_t best = rows[0], bc = sbyte_get(srow, rows[0]);
+#pragma unroll
+        for (int j = 1; j < 4; j++) {
+          const uint32_t c = sbyte_get(srow, rows[j]);
+          if (c < bc) {
+            best = rows[j];
+            bc = c;
+          }
+        }
+        b.rrow[i] = best;
+      }
+    }
+    __syncthreads();
+    for (uint32_t i = (uint32_t)lo + threadIdx.x; i < hi; i += blockDim.x) {
+      if (b.leader[i] != i || !b.fpres[i]) continue;
+      if (sbyte_inc(sload, b.rdest[i]) + 1 > m.lmax) err |= ERR_LOAD;
+      if (b.hit[i] == NONE32 && sbyte_inc(srow, b.rrow[i]) + 1 > m.R) err |= ERR_ROW;
+    }
+    __syncthreads();
+  }
+  if (err) set_err(m, err);
+  for (uint32_t w = threadIdx.x; w < lw; w += blockDim.x) m.load[w] = sload[w];
+  for (uint32_t w = threadIdx.x; w < rw; w += blockDim.x) m.rowcnt[w] = srow[w];
+}
+
+__global__ void k_remap_rest(MapDev m, BatchDev b, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || b.leader[i] != i || !b.fpres[i]) return;
+  remap_place(m, b, i, b.rdest[i]);
+}
+
 __global__ void k_clear_table(BatchDev b) {
   for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h <= b.ht_mask;
        h += gridDim.x * blockDim.x) {
@@ -548,20 +691,33 @@ cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64
   if (n_sort > 512 && n_sort < 4096) n_sort = 4096;
   ProfSpan whole(P_ACCESS, st);
   k_clear_table<<<64, 256, 0, st>>>(b);
-  k_stage<<<(n_sort + 255) / 256, 256, 0, st>>>(m, b, n, n_sort, t0);
+  const int keys32 = n_sort <= 4096;
+  k_stage<<<(3 * n_sort + 255) / 256, 256, 0, st>>>(m, b, n, n_sort, t0, keys32);
   count_launch(2);
   cudaError_t e;
   {
     ProfSpan ps(P_GROUP, st);
-    e = sort_batch_keys(b.skeys, n_sort, st);
-    if (e != cudaSuccess) return e;
-    k_group<<<1, GROUP_THREADS, 0, st>>>(b, n);
+    if (keys32) {
+      e = sort_batch_keys32(reinterpret_cast<uint32_t*>(b.skeys), n_sort, st);
+      if (e != cudaSuccess) return e;
+      k_group<uint32_t><<<1, GROUP_THREADS, 0, st>>>(b, n);
+    } else {
+      e = sort_batch_keys(b.skeys, n_sort, st);
+      if (e != cudaSuccess) return e;
+      k_group<uint64_t><<<1, GROUP_THREADS, 0, st>>>(b, n);
+    }
     count_launch();
   }
   const uint32_t warp_blocks = (n * 32 + 255) / 256;
   k_lookup<<<warp_blocks, 256, 0, st>>>(m, b, n);
-  k_pages<<<1, PAGES_THREADS, 0, st>>>(m, b, n);
-  count_launch(2);
+  {
+    const uint32_t np = 2 * n;
+    const uint32_t nblk = (np + PAGES_BLOCK - 1) / PAGES_BLOCK;
+    k_pages_count<<<nblk, PAGES_BLOCK, 0, st>>>(b, np, b.block_cnt);
+    k_pages_scan<<<1, 1024, 0, st>>>(m, b, nblk, b.block_cnt);
+    k_pages_emit<<<nblk, PAGES_BLOCK, 0, st>>>(m, b, np, b.block_cnt);
+    count_launch(4);
+  }
   const uint32_t dmax = 2 * n;  // distinct pages are at most two per op
   {
     ProfSpan ps(P_GATHER, st);
@@ -591,12 +747,27 @@ cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64
     count_launch();
   }
   cudaEventRecord(fc.ev_flushed, fc.flush_st);
-  for (uint64_t lo = 0; lo < n; lo += m.Wr) {
-    const uint32_t hi = (uint32_t)(lo + m.Wr < n ? lo + m.Wr : n);
-    const uint32_t g = (hi - (uint32_t)lo + 255) / 256;
-    k_remap_decide<<<g, 256, 0, st>>>(m, b, (uint32_t)lo, hi);
-    k_remap_apply<<<g, 256, 0, st>>>(m, b, (uint32_t)lo, hi);
+  // P2C remap: one round -> a decide and an apply launch; many rounds on a
+  // small map -> all rounds in one CTA on shared-memory counts
+  const uint64_t rounds = (n + m.Wr - 1) / m.Wr;
+  const size_t rsmem = ((m.B + 3) / 4 + (m.rows + 3) / 4) * 4;
+  if (rounds > 1 && m.B <= REMAP_SMEM_MAX_BINS && m.rows <= REMAP_SMEM_MAX_ROWS) {
+    if (rsmem > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_remap_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)rsmem);
+      if (e != cudaSuccess) return e;
+    }
+    k_remap_smem<<<1, 1024, rsmem, st>>>(m, b, n);
+    k_remap_rest<<<(n + 255) / 256, 256, 0, st>>>(m, b, n);
     count_launch(2);
+  } else {
+    for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+      const uint32_t hi = (uint32_t)(lo + m.Wr < n ? lo + m.Wr : n);
+      const uint32_t g = (hi - (uint32_t)lo + 255) / 256;
+      k_remap_decide<<<g, 256, 0, st>>>(m, b, (uint32_t)lo, hi);
+      k_remap_apply<<<g, 256, 0, st>>>(m, b, (uint32_t)lo, hi);
+      count_launch(2);
+    }
   }
   return cudaGetLastError();
 }

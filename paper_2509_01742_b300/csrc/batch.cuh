@@ -26,7 +26,8 @@ struct BatchDev {
   // pages read by the batch
   uint32_t* pos_page;  // [2 cap] host page of read position 2i + j, or NONE
   uint32_t* pos_slot;  // [2 cap] hash-table slot of that page
-  uint32_t* pos_d;     // [2 cap] distinct-page index of that page
+  uint32_t* block_cnt; // [2 * blocks] per-block (valid, first) read counts, then offsets
+  unsigned long long* trace_base;  // [2] trace offset of the batch, its read count
   uint32_t* ht_key;    // [ht_mask + 1] page hash table
   uint32_t* ht_min;    // [ht_mask + 1] first read position of the page
   uint32_t* ht_d;      // [ht_mask + 1] distinct-page index
@@ -52,6 +53,7 @@ struct BatchDev {
 };
 
 cudaError_t sort_batch_keys(uint64_t* keys, uint32_t n_pow2, cudaStream_t st);
+cudaError_t sort_batch_keys32(uint32_t* keys, uint32_t n_pow2, cudaStream_t st);
 // Host page write-back runs on `flush_st` after `ev_evicted` (recorded on st
 // once the batch's ciphertexts are in dbuf); `ev_flushed` is recorded on
 // flush_st when the batch's pages are in host memory.

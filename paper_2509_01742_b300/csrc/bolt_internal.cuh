@@ -311,7 +311,7 @@ struct Prof {
   double ms[P_NCLASS] = {};
   uint64_t count[P_NCLASS] = {};
 };
-extern Prof* g_prof;
+extern thread_local Prof* g_prof;
 
 inline void count_launch(uint64_t n = 1) {
   if (g_prof) g_prof->launches += n;
@@ -341,7 +341,8 @@ struct ProfSpan {
 
 // build.cu
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
-                         struct BuildScratch& s, cudaStream_t st);
+                         struct BuildScratch& s, cudaStream_t st,
+                         cudaEvent_t sorted_ev = nullptr);  // recorded after the tag sort
 
 // sort.cu: ascending bitonic sort of n_pow2 uint64 tags in place; the
 // passes are profiled under the given classes
@@ -362,6 +363,7 @@ struct BuildScratch {
   uint32_t* page_off = nullptr;  // [M + 1] exclusive prefix of page loads
   uint32_t* block_sums = nullptr;
   uint64_t block_cap = 0;
+  int log_tile = 13;          // bitonic tile (2^log_tile elements), chosen by the autotuner
   unsigned long long* counters = nullptr;  // [0] value-store fill
 };
 

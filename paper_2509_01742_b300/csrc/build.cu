@@ -60,18 +60,16 @@ __global__ void k_build_decide(MapDev m, const uint64_t* __restrict__ keys, uint
   prow[i] = pick_row(m, rows);
 }
 
-__global__ void k_build_apply(MapDev m, const uint64_t* __restrict__ keys,
-                              const uint8_t* __restrict__ vals, uint64_t lo, uint64_t hi,
-                              const uint64_t* __restrict__ bins, const uint32_t* __restrict__ dest,
-                              const uint32_t* __restrict__ prow, unsigned long long* vs_fill) {
-  uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= hi) return;
-  const uint32_t d = dest[i];
+// bump the counts of record i's choices, write its position-map entry, give
+// an HBM-bin record a value-store slot
+__device__ __forceinline__ void build_apply_one(const MapDev& m, const uint64_t* __restrict__ keys,
+                                                const uint8_t* __restrict__ vals, uint64_t i,
+                                                const uint64_t* __restrict__ bins, uint32_t d,
+                                                uint32_t row, unsigned long long* vs_fill) {
   if (byte_inc(m.load, d) + 1 > m.lmax) {
     set_err(m, ERR_LOAD);
     return;
   }
-  const uint32_t row = prow[i];
   const uint32_t slot = byte_inc(m.rowcnt, row);
   if (slot >= m.R) {
     set_err(m, ERR_ROW);
@@ -98,6 +96,147 @@ __global__ void k_build_apply(MapDev m, const uint64_t* __restrict__ keys,
   m.pm_key[pmi] = keys[i];
   m.pm_bins[pmi] = bb;
   m.pm_meta[pmi] = meta;
+}
+
+__global__ void k_build_apply(MapDev m, const uint64_t* __restrict__ keys,
+                              const uint8_t* __restrict__ vals, uint64_t lo, uint64_t hi,
+                              const uint64_t* __restrict__ bins, const uint32_t* __restrict__ dest,
+                              const uint32_t* __restrict__ prow, unsigned long long* vs_fill) {
+  uint64_t i = lo + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= hi) return;
+  build_apply_one(m, keys, vals, i, bins, dest[i], prow[i], vs_fill);
+}
+
+// --- all rounds in one persistent kernel ------------------------------------
+// A software grid barrier separates the decide and apply phases of every
+// round.  All blocks are co-resident (cooperative launch).  Every wait is
+// bounded: a block that gives up sets ERR_TIMEOUT and leaves the kernel, so
+// the others give up at their next barrier too and the kernel always ends.
+constexpr uint32_t BAR_SPIN_LIMIT = 1u << 22;  // x ~256 ns sleep: about one second
+// a record's claimed position-map row and slot packed in one word (rows <
+// 2^27 for N <= 2^31, slots < R <= 32); NONE32 marks a record that overflowed
+constexpr uint32_t PROW_SLOT_SHIFT = 27;
+constexpr uint32_t PROW_ROW_MASK = (1u << PROW_SLOT_SHIFT) - 1;
+
+__device__ __forceinline__ bool grid_barrier(const MapDev& m, unsigned int* bar) {
+  // bar[0]: arrivals, bar[1]: generation
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u);
+    ok = 1;
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      uint32_t it = 0;
+      while (*gen == g) {
+        if (++it > BAR_SPIN_LIMIT) {
+          ok = 0;
+          set_err(m, ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// round-start counts must come from L2, not from a line this SM cached in an
+// earlier round of the same kernel
+__device__ __forceinline__ uint32_t byte_get_l2(const uint32_t* w, uint64_t i) {
+  return (__ldcg(w + (i >> 2)) >> ((uint32_t)(i & 3) * 8)) & 0xffu;
+}
+
+__global__ void __launch_bounds__(256) k_build_rounds(MapDev m, const uint64_t* __restrict__ keys,
+                                                      const uint8_t* __restrict__ vals, uint64_t n,
+                                                      const uint64_t* __restrict__ bins,
+                                                      const uint4* __restrict__ rows4,
+                                                      uint32_t* __restrict__ dest,
+                                                      uint32_t* __restrict__ prow,
+                                                      unsigned long long* vs_fill,
+                                                      unsigned int* bar) {
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+    const uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
+    for (uint64_t i = lo + tid; i < hi; i += nthreads) {
+      const uint64_t bb = bins[i];
+      const uint32_t b1 = (uint32_t)bb, b2 = (uint32_t)(bb >> 32);
+      const uint32_t l1 = byte_get_l2(m.load, b1), l2 = byte_get_l2(m.load, b2);
+      dest[i] = l1 <= l2 ? b1 : b2;
+      const uint4 r4 = rows4[i];
+      const uint32_t rows[4] = {r4.x, r4.y, r4.z, r4.w};
+      uint32_t best = rows[0], bc = byte_get_l2(m.rowcnt, rows[0]);
+#pragma unroll
+      for (int j = 1; j < 4; j++) {
+        const uint32_t c = byte_get_l2(m.rowcnt, rows[j]);
+        if (c < bc) {
+          best = rows[j];
+          bc = c;
+        }
+      }
+      prow[i] = best;
+    }
+    if (!grid_barrier(m, bar)) return;
+    // only the order-dependent part happens between the barriers: the
+    // counts; the entry is written later by k_build_place
+    for (uint64_t i = lo + tid; i < hi; i += nthreads) {
+      const uint32_t row = prow[i];
+      uint32_t tag = NONE32;
+      if (byte_inc(m.load, dest[i]) + 1 > m.lmax) {
+        set_err(m, ERR_LOAD);
+      } else {
+        const uint32_t slot = byte_inc(m.rowcnt, row);
+        if (slot >= m.R) set_err(m, ERR_ROW);
+        else tag = row | (slot << PROW_SLOT_SHIFT);
+      }
+      prow[i] = tag;
+    }
+    if (!grid_barrier(m, bar)) return;
+  }
+}
+
+// write every record's position-map entry (row and slot claimed in the
+// rounds) and give HBM-bin records a value-store slot
+__global__ void k_build_place(MapDev m, const uint64_t* __restrict__ keys,
+                              const uint8_t* __restrict__ vals, uint64_t n,
+                              const uint64_t* __restrict__ bins, const uint32_t* __restrict__ dest,
+                              const uint32_t* __restrict__ prow, unsigned long long* vs_fill) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t tag = prow[i];
+    if (tag == NONE32) continue;
+    const uint64_t pmi = (uint64_t)(tag & PROW_ROW_MASK) * m.R + (tag >> PROW_SLOT_SHIFT);
+    const uint32_t d = dest[i];
+    const uint64_t bb = bins[i];
+    const uint32_t which = d == (uint32_t)(bb >> 32) ? 1u : 0u;
+    uint32_t meta = meta_make(LOC_HOST, which, 0);
+    if (d < m.K) {
+      const unsigned long long vs = atomicAdd(vs_fill, 1ull);
+      if (vs >= m.vs_cap) {
+        set_err(m, ERR_VS);
+        continue;
+      }
+      m.vs_key[vs] = keys[i];
+      const uint64_t* src = reinterpret_cast<const uint64_t*>(vals + i * m.vb);
+      uint64_t* dst = reinterpret_cast<uint64_t*>(m.vs_val + vs * m.vb);
+      for (uint32_t w = 0; w < m.vb / 8; w++) dst[w] = src[w];
+      m.vs_pm[vs] = (uint32_t)pmi;
+      m.vs_live[vs] = 1;
+      meta = meta_make(LOC_HBM, which, (uint32_t)vs);
+    }
+    m.pm_key[pmi] = keys[i];
+    m.pm_bins[pmi] = bb;
+    m.pm_meta[pmi] = meta;
+  }
 }
 
 // tags: host-bin records -> (page << 32 | i); HBM-bin records and padding -> ~0
@@ -233,17 +372,47 @@ static int sm_count() {
 }
 
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
-                         BuildScratch& s, cudaStream_t st) {
+                         BuildScratch& s, cudaStream_t st, cudaEvent_t sorted_ev) {
   const int sms = sm_count();
   cudaMemsetAsync(s.counters, 0, 2 * sizeof(unsigned long long), st);
   // 1. P2C + position map, round by round
   {
     ProfSpan ps(P_P2C, st);
+    bool done = false;
     if (s.rows4 && n) {
       k_build_prf<<<sms * 16, 256, 0, st>>>(m, keys, n, s.bins, s.rows4);
       count_launch();
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_rounds, 256, 0) ==
+              cudaSuccess && per_sm > 0) {
+        unsigned int* bar = reinterpret_cast<unsigned int*>(s.counters + 1);
+        cudaMemsetAsync(bar, 0, 8, st);
+        // about one record per thread per round; a small round needs few blocks
+        const uint64_t want = (m.Wr + 255) / 256;
+        const uint64_t cap = (uint64_t)sms * (per_sm < 4 ? per_sm : 4);
+        const unsigned int blocks = (unsigned int)(want < cap ? want : cap);
+        const uint64_t* kp = keys;
+        const uint8_t* vp = vals;
+        uint64_t nn = n;
+        const uint64_t* bp = s.bins;
+        const uint4* rp = s.rows4;
+        uint32_t* dp = s.dest;
+        uint32_t* pp = s.prow;
+        unsigned long long* fp = s.counters;
+        MapDev mm = m;
+        void* args[] = {&mm, &kp, &vp, &nn, &bp, &rp, &dp, &pp, &fp, &bar};
+        if (cudaLaunchCooperativeKernel((const void*)k_build_rounds, dim3(blocks), dim3(256), args,
+                                        0, st) == cudaSuccess) {
+          k_build_place<<<sms * 16, 256, 0, st>>>(m, keys, vals, n, s.bins, s.dest, s.prow,
+                                                  s.counters);
+          count_launch(2);
+          done = true;
+        } else {
+          cudaGetLastError();  // clear; fall back to one launch pair per round
+        }
+      }
     }
-    for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+    for (uint64_t lo = 0; !done && lo < n; lo += m.Wr) {
       uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
       unsigned g = (unsigned)((hi - lo + 255) / 256);
       k_build_decide<<<g, 256, 0, st>>>(m, keys, lo, hi, s.bins, s.rows4, s.dest, s.prow);
@@ -261,8 +430,9 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   // 3. tags + bitonic sort
   k_build_tags<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.tag_cap, s.tags);
   count_launch(4);
-  cudaError_t e = sort_tags_u64(s.tags, s.tag_cap, 13, st);
+  cudaError_t e = sort_tags_u64(s.tags, s.tag_cap, s.log_tile, st);
   if (e != cudaSuccess) return e;
+  if (sorted_ev) cudaEventRecord(sorted_ev, st);
   // 4. pages
   uint32_t wpb = (uint32_t)(65536 / m.page_bytes);
   wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;

@@ -1,0 +1,90 @@
+// handle.h -- the map handle behind the C ABI (shared by runtime.cu and
+// serve.cu; not part of the public interface).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "batch.cuh"
+#include "bolt_internal.cuh"
+
+constexpr uint32_t MAXB = BOLT_MAX_BATCH;
+
+struct bolt {
+  uint64_t dev_bytes = 0;     // device bytes of the resident state + batch buffers
+  uint64_t scratch_bytes = 0; // device bytes of the build scratch
+  int sort_log_tile = 13;      // bitonic tile chosen by bolt_autotune
+  uint64_t N = 0;
+  uint32_t vb = 0;
+  uint64_t hbm_budget = 0;
+  double alpha_override = -1.0;
+  uint32_t c = 8;
+  uint32_t batch_width = MAXB;
+  uint32_t cap_batch = MAXB;  // capacity of the batch buffers (ops per batch)
+  uint64_t trace_cap = 1ull << 22;
+  bool trace_on = false;
+  bool check_keys = true;
+  bolt_info_t info{};
+
+  bdev::MapDev m{};
+  bdev::BatchDev b{};
+  bdev::BuildScratch bs{};
+  cudaStream_t st = nullptr;
+  uint8_t* pages_host = nullptr;
+  std::vector<void*> dev_allocs;  // state + batch buffers (freed by free_state)
+
+  // host-pointer staging
+  uint64_t* in_keys = nullptr;
+  uint8_t* in_vals = nullptr;
+  uint64_t in_cap = 0;
+  uint8_t* h_ops = nullptr;
+  uint64_t* h_keys = nullptr;
+  uint8_t* h_vin = nullptr;
+  uint8_t* h_vout = nullptr;
+  uint8_t* h_status = nullptr;
+  uint32_t* h_err = nullptr;
+  uint32_t* d_kdf = nullptr;
+  uint32_t* d_flag = nullptr;
+
+  uint64_t t = 0, batches = 0;
+  bool allocated = false, initialized = false, poisoned = false;
+  bdev::Prof prof;
+  cudaStream_t last_st = nullptr;  // stream of the last enqueued work
+  cudaStream_t st2 = nullptr;      // side stream (key-uniqueness check)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // access batches alternate between two buffer slots; a slot's written pages
+  // reach the host on st_fl while the next batch runs
+  cudaStream_t st_fl = nullptr;
+  cudaEvent_t ev_evicted[2] = {nullptr, nullptr}, ev_flushed[2] = {nullptr, nullptr};
+  bool flush_pending[2] = {false, false};
+  int slot = 0;
+  bool prev_valid = false;
+  uint32_t slot_ht_mask[2] = {0, 0};
+  uint32_t* s_ht_key[2] = {nullptr, nullptr};
+  uint32_t* s_ht_min[2] = {nullptr, nullptr};
+  uint32_t* s_ht_d[2] = {nullptr, nullptr};
+  uint32_t* s_dpage[2] = {nullptr, nullptr};
+  uint32_t* s_dcount[2] = {nullptr, nullptr};
+  uint8_t* s_dbuf[2] = {nullptr, nullptr};
+};
+
+
+// points the kernel-side profiler at the handle for one ABI call
+struct ProfScope {
+  explicit ProfScope(bolt* h) { bdev::g_prof = &h->prof; }
+  ~ProfScope() { bdev::g_prof = nullptr; }
+};
+
+namespace brt {
+// one access batch of n <= cap_batch ops whose inputs are already in the
+// handle's device batch buffers, enqueued on st (outputs in h->b.vout/status)
+cudaError_t enqueue_batch(bolt* h, uint32_t n, cudaStream_t st);
+// BOLT_OK / BOLT_E_* for a device error word
+int err_rc(uint32_t err);
+// wait for every stream of the handle
+cudaError_t sync_handle(bolt* h);
+// device bytes the planner expects a map to hold resident, and its build
+// scratch for n records
+uint64_t resident_estimate(const bolt_info_t& I, uint64_t cap_batch, uint64_t trace_cap);
+uint64_t build_estimate(const bolt_info_t& I, uint64_t n);
+}  // namespace brt

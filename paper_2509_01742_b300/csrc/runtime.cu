@@ -13,18 +13,16 @@
 #include <mutex>
 #include <vector>
 
-#include "batch.cuh"
-#include "bolt_internal.cuh"
+#include "handle.h"
 
 using namespace bdev;
 
 namespace bdev {
-Prof* g_prof = nullptr;
+thread_local Prof* g_prof = nullptr;
 }
 
 namespace {
 
-constexpr uint32_t MAXB = BOLT_MAX_BATCH;
 
 struct Plan {
   bolt_info_t info;
@@ -65,68 +63,6 @@ int plan_sizes(uint64_t N, uint32_t c, double alpha, uint32_t vb, bolt_info_t* o
 
 }  // namespace
 
-struct bolt {
-  uint64_t N = 0;
-  uint32_t vb = 0;
-  uint64_t hbm_budget = 0;
-  double alpha_override = -1.0;
-  uint32_t c = 8;
-  uint32_t batch_width = MAXB;
-  uint32_t cap_batch = MAXB;  // capacity of the batch buffers (ops per batch)
-  uint64_t trace_cap = 1ull << 22;
-  bool trace_on = false;
-  bool check_keys = true;
-  bolt_info_t info{};
-
-  MapDev m{};
-  BatchDev b{};
-  BuildScratch bs{};
-  cudaStream_t st = nullptr;
-  uint8_t* pages_host = nullptr;
-  std::vector<void*> dev_allocs;  // state + batch buffers (freed by free_state)
-
-  // host-pointer staging
-  uint64_t* in_keys = nullptr;
-  uint8_t* in_vals = nullptr;
-  uint64_t in_cap = 0;
-  uint8_t* h_ops = nullptr;
-  uint64_t* h_keys = nullptr;
-  uint8_t* h_vin = nullptr;
-  uint8_t* h_vout = nullptr;
-  uint8_t* h_status = nullptr;
-  uint32_t* h_err = nullptr;
-  uint32_t* d_kdf = nullptr;
-  uint32_t* d_flag = nullptr;
-
-  uint64_t t = 0, batches = 0;
-  bool allocated = false, initialized = false, poisoned = false;
-  Prof prof;
-  cudaStream_t last_st = nullptr;  // stream of the last enqueued work
-  cudaStream_t st2 = nullptr;      // side stream (key-uniqueness check)
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  // access batches alternate between two buffer slots; a slot's written pages
-  // reach the host on st_fl while the next batch runs
-  cudaStream_t st_fl = nullptr;
-  cudaEvent_t ev_evicted[2] = {nullptr, nullptr}, ev_flushed[2] = {nullptr, nullptr};
-  bool flush_pending[2] = {false, false};
-  int slot = 0;
-  bool prev_valid = false;
-  uint32_t slot_ht_mask[2] = {0, 0};
-  uint32_t* s_ht_key[2] = {nullptr, nullptr};
-  uint32_t* s_ht_min[2] = {nullptr, nullptr};
-  uint32_t* s_ht_d[2] = {nullptr, nullptr};
-  uint32_t* s_dpage[2] = {nullptr, nullptr};
-  uint32_t* s_dcount[2] = {nullptr, nullptr};
-  uint8_t* s_dbuf[2] = {nullptr, nullptr};
-};
-
-namespace {
-// points the kernel-side profiler at the handle for one ABI call
-struct ProfScope {
-  explicit ProfScope(bolt* h) { g_prof = &h->prof; }
-  ~ProfScope() { g_prof = nullptr; }
-};
-}  // namespace
 
 namespace {
 
@@ -155,6 +91,7 @@ int dalloc(bolt* h, T** p, uint64_t count) {
   cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
   if (e != cudaSuccess) return cuda_fail(e);
   h->dev_allocs.push_back(ptr);
+  h->dev_bytes += count * sizeof(T);
   *p = static_cast<T*>(ptr);
   return BOLT_OK;
 }
@@ -167,6 +104,7 @@ void free_build_scratch(bolt* h) {
   s = BuildScratch{};
   cudaFree(h->in_keys); cudaFree(h->in_vals);
   h->in_keys = nullptr; h->in_vals = nullptr; h->in_cap = 0;
+  h->scratch_bytes = 0;
 }
 
 void free_state(bolt* h) {
@@ -174,6 +112,7 @@ void free_state(bolt* h) {
   h->last_st = nullptr;
   for (void* p : h->dev_allocs) cudaFree(p);
   h->dev_allocs.clear();
+  h->dev_bytes = 0;
   if (h->pages_host) cudaFreeHost(h->pages_host);
   h->pages_host = nullptr;
   free_build_scratch(h);
@@ -277,7 +216,8 @@ int alloc_state(bolt* h) {
   TRY(dalloc(h, &b.hit, cap));
   TRY(dalloc(h, &b.pos_page, 2 * cap));
   TRY(dalloc(h, &b.pos_slot, 2 * cap));
-  TRY(dalloc(h, &b.pos_d, 2 * cap));
+  TRY(dalloc(h, &b.block_cnt, 2 * ((2 * cap + 255) / 256) + 2));
+  TRY(dalloc(h, &b.trace_base, 2));
   const uint32_t ht = (uint32_t)(4 * cap2 < 256 ? 256 : 4 * cap2);
   b.ht_mask = ht - 1;
   for (int s = 0; s < 2; s++) {
@@ -334,6 +274,7 @@ int grow_build_scratch(bolt* h, uint64_t n) {
   s.cap = cap;
   s.tag_cap = tag_cap;
   s.block_cap = nblocks;
+  h->scratch_bytes = tag_cap * 16 + cap * (16 + 8 + 4 + 4) + (h->info.M + 1) * 4 + nblocks * 4 + 16;
   return BOLT_OK;
 }
 
@@ -460,32 +401,35 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     m.kprf[i] = kw[i];
     m.kenc[i] = kw[8 + i];
   }
+  bs.log_tile = h->sort_log_tile;
   // key uniqueness (Sec. 2.1): sort a copy of the keys, flag equal
-  // neighbours.  With a buffer of its own it runs on the side stream,
-  // overlapping the latency-bound P2C rounds of the build.
+  // neighbours.  With a buffer of its own it runs on the side stream during
+  // the page build, which is bound by the host link, not by HBM or the SMs.
   const bool check = h->check_keys && n > 1;
   const bool side = check && bs.keysort && h->st2;
-  if (check) {
-    cudaMemsetAsync(h->d_flag, 0, 4, st);
-    cudaStream_t ks = st;
-    uint64_t* kbuf = bs.tags;
-    if (side) {
-      cudaEventRecord(h->ev_fork, st);
-      cudaStreamWaitEvent(h->st2, h->ev_fork, 0);
-      ks = h->st2;
-      kbuf = bs.keysort;
-    }
+  if (check) cudaMemsetAsync(h->d_flag, 0, 4, st);
+  auto key_check = [&](cudaStream_t ks, uint64_t* kbuf) -> cudaError_t {
     ProfSpan ps(P_KEYCHECK, ks);
     k_copy_keys<<<sms * 8, 256, 0, ks>>>(d_keys, n, bs.tag_cap, kbuf);
     count_launch();
-    e = sort_tags_u64(kbuf, bs.tag_cap, 13, ks, P_KSORT_GLOBAL, P_KSORT_TILE);
-    if (e != cudaSuccess) return BOLT_E_CUDA;
+    cudaError_t ke = sort_tags_u64(kbuf, bs.tag_cap, bs.log_tile, ks, P_KSORT_GLOBAL, P_KSORT_TILE);
+    if (ke != cudaSuccess) return ke;
     k_adjacent_equal<<<sms * 8, 256, 0, ks>>>(kbuf, n, h->d_flag);
     count_launch();
-    if (side) cudaEventRecord(h->ev_join, h->st2);
+    return cudaGetLastError();
+  };
+  if (check && !side) {
+    e = key_check(st, bs.tags);  // in line, before the build reuses `tags`
+    if (e != cudaSuccess) return BOLT_E_CUDA;
   }
-  e = launch_build(m, d_keys, d_vals, n, bs, st);
+  e = launch_build(m, d_keys, d_vals, n, bs, st, side ? h->ev_fork : nullptr);
   if (e != cudaSuccess) return BOLT_E_CUDA;
+  if (side) {
+    cudaStreamWaitEvent(h->st2, h->ev_fork, 0);
+    e = key_check(h->st2, bs.keysort);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+    cudaEventRecord(h->ev_join, h->st2);
+  }
   if (side) cudaStreamWaitEvent(st, h->ev_join, 0);
   uint32_t err = 0;
   h->last_st = st;
@@ -935,4 +879,184 @@ extern "C" int bolt_init_device_noalloc(bolt_t* h, const void* d_keys, const voi
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
   return init_impl(h, static_cast<const uint64_t*>(d_keys), static_cast<const uint8_t*>(d_vals), n,
                    seed, st, s);
+}
+
+// ---------------------------------------------------------------------------
+// internal entry points for the serving layer (serve.cu)
+namespace brt {
+
+cudaError_t enqueue_batch(bolt* h, uint32_t n, cudaStream_t st) {
+  if (h->last_st != st) {
+    if (h->last_st) {
+      cudaError_t e = sync_all(h);
+      if (e != cudaSuccess) return e;
+    }
+    h->last_st = st;
+  }
+  cudaError_t e = access_batch(h, h->b, n, st);
+  if (e != cudaSuccess) return e;
+  h->t += n;
+  h->batches++;
+  return cudaSuccess;
+}
+
+int err_rc(uint32_t err) { return err_to_rc(err); }
+
+cudaError_t sync_handle(bolt* h) { return sync_all(h); }
+
+uint64_t resident_estimate(const bolt_info_t& I, uint64_t cap, uint64_t trace_cap) {
+  const uint64_t slots = I.rows * I.R, vb = I.val_bytes;
+  uint64_t b = 4 * (I.B / 4 + 2) + 4 * (I.rows / 4 + 2) + slots * (8 + 8 + 4) +
+               I.vs_cap * (8 + vb + 4 + 1 + 4) + 16 + I.M * I.lmax * 4 + 4 * (I.M / 4 + 2) +
+               I.M * 8 + 4 + trace_cap * 4 + 8;
+  uint64_t cap2 = 1;
+  while (cap2 < cap) cap2 <<= 1;
+  const uint64_t sort_cap = cap2 <= 512 ? 512 : (cap2 < 4096 ? 4096 : cap2);
+  const uint64_t kt = 2 * cap2 < 128 ? 128 : 2 * cap2;
+  const uint64_t ht = 4 * cap2 < 256 ? 256 : 4 * cap2;
+  b += cap * (1 + 8 + 2 * vb + 1) + sort_cap * 8 + kt * 4 + cap * 12 + cap * 16 + cap * 16 +
+       cap * 4 + 2 * cap * 8 + (2 * ((2 * cap + 255) / 256) + 2) * 4 + 16;
+  b += 2 * (ht * 12 + 2 * cap * 4 + 4 + 2 * cap * I.page_bytes);
+  b += 2 * cap * 8 + cap * vb + cap + cap * vb + cap + cap * 8 + 16 * 4 + 4;
+  return b;
+}
+
+uint64_t build_estimate(const bolt_info_t& I, uint64_t n) {
+  const uint64_t cap = n > 0 ? n : 1;
+  uint64_t tag_cap = 8192;
+  while (tag_cap < n) tag_cap <<= 1;
+  const uint64_t nblocks = (I.M + 1 + 8192 - 1) / 8192 + 1;
+  return tag_cap * 16 + cap * (16 + 8 + 4 + 4) + (I.M + 1) * 4 + nblocks * 4 + 16 +
+         cap * (8 + (uint64_t)I.val_bytes);  // + the host-pointer staging copy
+}
+
+}  // namespace brt
+
+extern "C" int bolt_trim(bolt_t* h) {
+  if (!h) return BOLT_E_ARG;
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  free_build_scratch(h);
+  return BOLT_OK;
+}
+
+extern "C" int bolt_footprint(const bolt_t* h, uint64_t* resident_bytes, uint64_t* scratch_bytes) {
+  if (!h) return BOLT_E_ARG;
+  if (resident_bytes) *resident_bytes = h->dev_bytes;
+  if (scratch_bytes) *scratch_bytes = h->scratch_bytes + h->in_cap * (8 + (uint64_t)h->vb);
+  return BOLT_OK;
+}
+
+extern "C" int bolt_plan_bytes(uint64_t N, uint32_t val_bytes, uint64_t hbm_budget,
+                               uint32_t batch_cap, uint64_t n_init, uint64_t* resident_bytes,
+                               uint64_t* build_bytes) {
+  bolt_info_t I;
+  int rc = bolt_plan(N, 8, val_bytes, hbm_budget, -1.0, 8, &I);
+  if (rc) return rc;
+  if (batch_cap < 1 || batch_cap > MAXB || n_init > N) return BOLT_E_ARG;
+  if (resident_bytes) *resident_bytes = brt::resident_estimate(I, batch_cap, 1ull << 22);
+  if (build_bytes) *build_bytes = brt::build_estimate(I, n_init);
+  return BOLT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: performance knobs only (nothing it picks changes a result, a
+// ciphertext or the trace of later calls, except through the accesses it
+// runs itself)
+namespace {
+
+__global__ void k_fill_tags(uint64_t* t, uint64_t n, uint64_t salt) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t x = (i + salt) * 0x9E3779B97F4A7C15ull;
+    x ^= x >> 29;
+    t[i] = x * 0xBF58476D1CE4E5B9ull;
+  }
+}
+
+}  // namespace
+
+extern "C" int bolt_autotune(bolt_t* h, const void* sample_keys, uint64_t n_sample,
+                             double max_batch_us, bolt_tune_t* out) {
+  if (!h || !out || !h->allocated) return BOLT_E_ARG;
+  if (!h->initialized || h->poisoned) return BOLT_E_STATE;
+  std::memset(out, 0, sizeof *out);
+  ProfScope prof_scope(h);
+  cudaStream_t st = h->st;
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return BOLT_E_CUDA;
+  // 1. bitonic tile: sort a scratch array the size of this map's tag buffer
+  uint64_t n = 8192;
+  while (n < h->N) n <<= 1;
+  uint64_t* tags = nullptr;
+  int rc = BOLT_OK;
+  if (cudaMalloc(&tags, n * 8) != cudaSuccess) {
+    rc = BOLT_E_NOMEM;
+  } else {
+    const int tiles[2] = {12, 13};
+    double best = 1e30;
+    for (int k = 0; k < 2; k++) {
+      float ms = 0;
+      for (int rep = 0; rep < 2; rep++) {  // the first run warms up
+        k_fill_tags<<<256, 256, 0, st>>>(tags, n, (uint64_t)rep);
+        cudaEventRecord(a, st);
+        sort_tags_u64(tags, n, tiles[k], st);
+        cudaEventRecord(b, st);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+      }
+      out->sort_ms[k] = ms;
+      if (ms < best) {
+        best = ms;
+        out->sort_log_tile = (uint32_t)tiles[k];
+      }
+    }
+    cudaFree(tags);
+    h->sort_log_tile = (int)out->sort_log_tile;
+  }
+  // 2. access batch width: Get batches over the caller's key sample
+  if (rc == BOLT_OK && sample_keys && n_sample) {
+    const uint32_t cand[BOLT_TUNE_WIDTHS] = {64, 256, 1024, 4096, 16384, 65536};
+    double best_rate = 0;
+    out->batch_width = 1;
+    const uint64_t* keys = static_cast<const uint64_t*>(sample_keys);
+    for (int k = 0; k < BOLT_TUNE_WIDTHS && rc == BOLT_OK; k++) {
+      const uint32_t w = cand[k];
+      out->widths[k] = w;
+      if (w > h->cap_batch) continue;
+      const int reps = 3;
+      float ms = 0;
+      for (int rep = 0; rep <= reps && rc == BOLT_OK; rep++) {
+        for (uint32_t i = 0; i < w; i++) {
+          h->h_keys[i] = keys[(rep * (uint64_t)w + i) % n_sample];
+          h->h_ops[i] = BOLT_GET;
+        }
+        std::memset(h->h_vin, 0, (uint64_t)w * h->vb);
+        cudaMemcpyAsync(h->b.ops, h->h_ops, w, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(h->b.keys, h->h_keys, (uint64_t)w * 8, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(h->b.vin, h->h_vin, (uint64_t)w * h->vb, cudaMemcpyHostToDevice, st);
+        if (rep == 1) cudaEventRecord(a, st);  // rep 0 warms up
+        if (access_batch(h, h->b, w, st) != cudaSuccess) rc = BOLT_E_CUDA;
+        h->t += w;
+        h->batches++;
+      }
+      cudaEventRecord(b, st);
+      cudaEventSynchronize(b);
+      cudaEventElapsedTime(&ms, a, b);
+      const double us = ms * 1e3 / reps;
+      out->width_us[k] = us;
+      const double rate = w / (us * 1e-6);
+      if ((max_batch_us <= 0 || us <= max_batch_us) && rate > best_rate) {
+        best_rate = rate;
+        out->batch_width = w;
+      }
+    }
+    uint32_t err = 0;
+    if (rc == BOLT_OK && (rc = read_err(h, &err)) == BOLT_OK) rc = err_to_rc(err);
+    if (rc == BOLT_OK) h->batch_width = out->batch_width;
+    else if (rc == BOLT_E_OVERFLOW) h->poisoned = true;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
 }

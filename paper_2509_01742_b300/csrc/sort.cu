@@ -29,19 +29,18 @@
 
 namespace bdev {
 
-__device__ __forceinline__ void cx(uint64_t& a, uint64_t& b, bool asc) {
+template <typename T>
+__device__ __forceinline__ void cx(T& a, T& b, bool asc) {
   // ascending: (min, max); descending: (max, min)
-  const bool lt = a < b;
-  const uint64_t lo = lt ? a : b, hi = lt ? b : a;
+  const T lo = min(a, b), hi = max(a, b);
   a = asc ? lo : hi;
   b = asc ? hi : lo;
 }
 
 // compare-exchange with a compile-time direction
-template <bool ASC>
-__device__ __forceinline__ void cxd(uint64_t& a, uint64_t& b) {
-  const bool lt = a < b;
-  const uint64_t lo = lt ? a : b, hi = lt ? b : a;
+template <bool ASC, typename T>
+__device__ __forceinline__ void cxd(T& a, T& b) {
+  const T lo = min(a, b), hi = max(a, b);
   a = ASC ? lo : hi;
   b = ASC ? hi : lo;
 }
@@ -54,34 +53,51 @@ __device__ __forceinline__ uint32_t win_idx(uint32_t t, uint32_t r) {
   return ((t >> W) << (W + 4)) | (r << W) | (t & ((1u << W) - 1u));
 }
 
-template <int W>
-__device__ __forceinline__ void ld_smem(const uint64_t* sm, uint64_t v[16]) {
+template <int W, typename T>
+__device__ __forceinline__ void ld_smem(const T* sm, T v[16]) {
   const uint32_t t = threadIdx.x;
 #pragma unroll
   for (int r = 0; r < 16; r++) v[r] = sm[pad_idx(win_idx<W>(t, r))];
 }
 
-template <int W>
-__device__ __forceinline__ void st_smem(uint64_t* sm, const uint64_t v[16]) {
+template <int W, typename T>
+__device__ __forceinline__ void st_smem(T* sm, const T v[16]) {
   const uint32_t t = threadIdx.x;
 #pragma unroll
   for (int r = 0; r < 16; r++) sm[pad_idx(win_idx<W>(t, r))] = v[r];
 }
 
-// steps for stride bits BHI..BLO (inside the window [W, W+3]), one direction
-template <int W, int BHI, int BLO>
-__device__ __forceinline__ void steps_uniform(uint64_t v[16], bool asc) {
+// 16 consecutive elements per thread, moved as 16-byte vectors
+template <typename T>
+__device__ __forceinline__ void ld16(const T* g, T v[16]) {
+  const uint4* in = reinterpret_cast<const uint4*>(g);
+  constexpr int PER = 16 / sizeof(T);
 #pragma unroll
-  for (int b = BHI; b >= BLO; b--) {
-    const int rb = b - W;
+  for (int k = 0; k < 16 / PER; k++) {
+    const uint4 x = in[k];
+    const T* e = reinterpret_cast<const T*>(&x);
 #pragma unroll
-    for (int r = 0; r < 16; r++)
-      if (!(r & (1 << rb))) cx(v[r], v[r | (1 << rb)], asc);
+    for (int j = 0; j < PER; j++) v[k * PER + j] = e[j];
   }
 }
 
-template <int W, int BHI, int BLO, bool ASC>
-__device__ __forceinline__ void steps_dir(uint64_t v[16]) {
+template <typename T>
+__device__ __forceinline__ void st16(T* g, const T v[16]) {
+  uint4* out = reinterpret_cast<uint4*>(g);
+  constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+  for (int k = 0; k < 16 / PER; k++) {
+    uint4 x;
+    T* e = reinterpret_cast<T*>(&x);
+#pragma unroll
+    for (int j = 0; j < PER; j++) e[j] = v[k * PER + j];
+    out[k] = x;
+  }
+}
+
+// steps for stride bits BHI..BLO (inside the window [W, W+3]), one direction
+template <int W, int BHI, int BLO, bool ASC, typename T>
+__device__ __forceinline__ void steps_dir(T v[16]) {
 #pragma unroll
   for (int b = BHI; b >= BLO; b--) {
     const int rb = b - W;
@@ -91,10 +107,21 @@ __device__ __forceinline__ void steps_dir(uint64_t v[16]) {
   }
 }
 
+template <int W, int BHI, int BLO, typename T>
+__device__ __forceinline__ void steps_uniform(T v[16], bool asc) {
+#pragma unroll
+  for (int b = BHI; b >= BLO; b--) {
+    const int rb = b - W;
+#pragma unroll
+    for (int r = 0; r < 16; r++)
+      if (!(r & (1 << rb))) cx(v[r], v[r | (1 << rb)], asc);
+  }
+}
+
 // steps for stride bits BHI..BLO of stage S < LT: a pair is ascending when
 // bit S of its local index is 0
-template <int W, int BHI, int BLO, int S>
-__device__ __forceinline__ void steps_stage(uint64_t v[16]) {
+template <int W, int BHI, int BLO, int S, typename T>
+__device__ __forceinline__ void steps_stage(T v[16]) {
   const bool thread_asc = ((win_idx<W>(threadIdx.x, 0) >> S) & 1) == 0;
 #pragma unroll
   for (int b = BHI; b >= BLO; b--) {
@@ -102,8 +129,12 @@ __device__ __forceinline__ void steps_stage(uint64_t v[16]) {
 #pragma unroll
     for (int r = 0; r < 16; r++) {
       if (r & (1 << rb)) continue;
-      const bool asc = (S >= W && S < W + 4) ? (((r >> (S - W)) & 1) == 0) : thread_asc;
-      cx(v[r], v[r | (1 << rb)], asc);
+      if (S >= W && S < W + 4) {
+        if (((r >> (S - W)) & 1) == 0) cxd<true>(v[r], v[r | (1 << rb)]);
+        else cxd<false>(v[r], v[r | (1 << rb)]);
+      } else {
+        cx(v[r], v[r | (1 << rb)], thread_asc);
+      }
     }
   }
 }
@@ -115,8 +146,8 @@ struct Win {
 };
 
 // Merge pass, chunk of bits HI..max(HI-3,0); registers arrive in window CURW.
-template <int LT, int HI, int CURW, bool ASC>
-__device__ __forceinline__ void merge_chunks(uint64_t* sm, uint64_t v[16], uint64_t* gout) {
+template <int LT, int HI, int CURW, bool ASC, typename T>
+__device__ __forceinline__ void merge_chunks(T* sm, T v[16], T* gout) {
   constexpr int LO = HI - 3 > 0 ? HI - 3 : 0;
   constexpr int W = Win<LT, LO>::value;
   if constexpr (CURW != W) {
@@ -130,19 +161,16 @@ __device__ __forceinline__ void merge_chunks(uint64_t* sm, uint64_t v[16], uint6
     merge_chunks<LT, LO - 1, W, ASC>(sm, v, gout);
   } else {
     static_assert(W == 0, "the last window starts at bit 0");
-    // a thread's registers are 16 consecutive elements: 16-byte vector stores
-    ulonglong2* o = reinterpret_cast<ulonglong2*>(gout + 16 * (uint64_t)threadIdx.x);
-#pragma unroll
-    for (int r = 0; r < 8; r++) o[r] = make_ulonglong2(v[2 * r], v[2 * r + 1]);
+    // a thread's registers are 16 consecutive elements
+    st16(gout + 16 * (uint64_t)threadIdx.x, v);
   }
 }
 
 // Full in-tile sort, chunk of bits HI..max(HI-3,0) of stage S; registers
 // arrive in window CURW.  Stage LT's direction is the tile's (bit LT of the
 // global index).
-template <int LT, int S, int HI, int CURW>
-__device__ __forceinline__ void full_chunks(uint64_t* sm, uint64_t v[16], bool tile_asc,
-                                            uint64_t* gout) {
+template <int LT, int S, int HI, int CURW, typename T>
+__device__ __forceinline__ void full_chunks(T* sm, T v[16], bool tile_asc, T* gout) {
   constexpr int LO = HI - 3 > 0 ? HI - 3 : 0;
   constexpr int W = Win<LT, LO>::value;
   if constexpr (CURW != W) {
@@ -162,41 +190,32 @@ __device__ __forceinline__ void full_chunks(uint64_t* sm, uint64_t v[16], bool t
     full_chunks<LT, S + 1, S, W>(sm, v, tile_asc, gout);
   } else {
     static_assert(W == 0, "the last window starts at bit 0");
-    ulonglong2* o = reinterpret_cast<ulonglong2*>(gout + 16 * (uint64_t)threadIdx.x);
-#pragma unroll
-    for (int r = 0; r < 8; r++) o[r] = make_ulonglong2(v[2 * r], v[2 * r + 1]);
+    st16(gout + 16 * (uint64_t)threadIdx.x, v);
   }
 }
 
 // Stages 1..LT of each tile (sorts tiles into alternating directions).
-template <int LT>
-__global__ void __launch_bounds__(1 << (LT - 4)) k_sort_tile_full(uint64_t* data) {
+template <int LT, typename T>
+__global__ void __launch_bounds__(1 << (LT - 4)) k_sort_tile_full(T* data) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw);
+  T* sm = reinterpret_cast<T*>(smem_raw);
   const uint64_t base = (uint64_t)blockIdx.x << LT;
-  uint64_t* g = data + base;
-  uint64_t v[16];
-  // window 0: 16 consecutive elements per thread, 16-byte vector loads
-  const ulonglong2* in = reinterpret_cast<const ulonglong2*>(g + 16 * (uint64_t)threadIdx.x);
-#pragma unroll
-  for (int r = 0; r < 8; r++) {
-    const ulonglong2 x = in[r];
-    v[2 * r] = x.x;
-    v[2 * r + 1] = x.y;
-  }
+  T* g = data + base;
+  T v[16];
+  ld16(g + 16 * (uint64_t)threadIdx.x, v);
   full_chunks<LT, 1, 0, 0>(sm, v, ((base >> LT) & 1) == 0, g);
 }
 
 // The in-tile steps (bits LT-1..0) of stage s_merge > LT: one direction per
 // tile.  Two CTAs per SM overlap one tile's loads with another's compute.
-template <int LT>
-__global__ void __launch_bounds__(1 << (LT - 4), 2) k_sort_tile_merge(uint64_t* data, int s_merge) {
+template <int LT, typename T>
+__global__ void __launch_bounds__(1 << (LT - 4), 2) k_sort_tile_merge(T* data, int s_merge) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint64_t* sm = reinterpret_cast<uint64_t*>(smem_raw);
+  T* sm = reinterpret_cast<T*>(smem_raw);
   const uint64_t base = (uint64_t)blockIdx.x << LT;
-  uint64_t* g = data + base;
+  T* g = data + base;
   const uint32_t t = threadIdx.x;
-  uint64_t v[16];
+  T v[16];
   // window LT-4: thread t takes elements t + r * 2^(LT-4): coalesced loads
 #pragma unroll
   for (int r = 0; r < 16; r++) v[r] = g[win_idx<LT - 4>(t, r)];
@@ -253,9 +272,9 @@ __global__ void __launch_bounds__(256, 2) k_sort_global_u64(uint64_t* data, uint
   }
 }
 
-template <int LT>
+template <int LT, typename T = uint64_t>
 static size_t tile_smem() {
-  return (size_t)((1u << LT) + (1u << LT) / 16) * sizeof(uint64_t);
+  return (size_t)((1u << LT) + (1u << LT) / 16) * sizeof(T);
 }
 
 template <int LT>
@@ -263,10 +282,10 @@ static cudaError_t sort_u64_lt(uint64_t* tags, uint64_t n, cudaStream_t st,
                                int cls_global = P_SORT_GLOBAL, int cls_tile = P_SORT_TILE) {
   const size_t smem = tile_smem<LT>();
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_sort_tile_full<LT>,
+    cudaError_t e = cudaFuncSetAttribute(k_sort_tile_full<LT, uint64_t>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_sort_tile_merge<LT>,
+      e = cudaFuncSetAttribute(k_sort_tile_merge<LT, uint64_t>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -274,7 +293,7 @@ static cudaError_t sort_u64_lt(uint64_t* tags, uint64_t n, cudaStream_t st,
   const int nt = 1 << (LT - 4);
   {
     ProfSpan ps(cls_tile, st);
-    k_sort_tile_full<LT><<<(unsigned)tiles, nt, smem, st>>>(tags);
+    k_sort_tile_full<LT, uint64_t><<<(unsigned)tiles, nt, smem, st>>>(tags);
     count_launch();
   }
   int logn = 0;
@@ -299,7 +318,7 @@ static cudaError_t sort_u64_lt(uint64_t* tags, uint64_t n, cudaStream_t st,
       }
     }
     ProfSpan ps(cls_tile, st);
-    k_sort_tile_merge<LT><<<(unsigned)tiles, nt, smem, st>>>(tags, s);
+    k_sort_tile_merge<LT, uint64_t><<<(unsigned)tiles, nt, smem, st>>>(tags, s);
     count_launch();
   }
   return cudaGetLastError();
@@ -313,6 +332,19 @@ cudaError_t sort_tags_u64(uint64_t* tags, uint64_t n, int log_tile, cudaStream_t
   if (log_tile == 12 && n >= (1ull << 12)) return sort_u64_lt<12>(tags, n, st, cls_global, cls_tile);
   if (log_tile == 9 && n >= (1ull << 9)) return sort_u64_lt<9>(tags, n, st, cls_global, cls_tile);
   return cudaErrorInvalidValue;
+}
+
+// batch grouping keys packed in 32 bits: one tile of n = 512 or 4096 keys
+cudaError_t sort_batch_keys32(uint32_t* keys, uint32_t n, cudaStream_t st) {
+  if (n == 512) {
+    k_sort_tile_full<9, uint32_t><<<1, 32, tile_smem<9, uint32_t>(), st>>>(keys);
+  } else if (n == 4096) {
+    k_sort_tile_full<12, uint32_t><<<1, 256, tile_smem<12, uint32_t>(), st>>>(keys);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
 }
 
 // batch grouping keys, n a power of two in [512, 65536]

@@ -241,3 +241,42 @@ def test_device_batches_back_to_back_match_oracle():
     assert np.array_equal(np.concatenate(so_all), t_st.cpu().numpy())
     _assert_state_equal(o, g, "back-to-back device batches")
     o.close(); g.close()
+
+
+def test_autotune_keeps_results():
+    """bolt_autotune picks a tile and a batch width by measurement; the map's
+    contents are unchanged (its tuning Gets only remap keys) and later builds
+    with the picked tile still match the oracle."""
+    N, vb = 1 << 16, 8
+    keys, vals = W.records(N, vb, 41)
+    g = B.BoltMap(N, vb)
+    assert g.init(keys, vals, 5) == 0
+    t = g.autotune(sample_keys=keys[:20000], max_batch_us=0)
+    assert t["sort_log_tile"] in (12, 13) and t["batch_width"] in (64, 256, 1024, 4096, 16384, 65536)
+    assert all(x > 0 for x in t["sort_ms"])
+    model = DictModel(keys, vals)
+    ops, k, vin = W.op_stream(N, 5000, vb, 42, del_frac=0.1, absent_frac=0.1)
+    rc, vout, st = g.access(ops, k, vin)
+    ev, es = model.apply(ops, k, vin, vb)
+    assert rc == 0 and np.array_equal(vout, ev) and np.array_equal(st, es)
+    o = O.OracleMap(N, vb)
+    assert o.init(keys, vals, 6) == 0 and g.init(keys, vals, 6) == 0  # tuned tile
+    assert np.array_equal(o.pages(), g.pages())
+    o.close(); g.close()
+
+
+def test_large_config_scaled_replica():
+    """The 2^30-record, 64 B, 16 GB-budget configuration (alpha = 0.1 under
+    that budget) on a scaled replica the oracle can run: N = 2^22, alpha 0.1,
+    Zipf(0.99) keys, 90% GET / 10% PUT, batches of 4096."""
+    N, vb = 1 << 22, 56
+    o, g = _pair(N, vb, alpha=0.1)
+    keys, vals = W.records(N, vb, 0x5EED0004)
+    assert o.init(keys, vals, 99) == 0 and g.init(keys, vals, 99) == 0
+    assert np.array_equal(o.pages(), g.pages())
+    for rep in range(4):
+        ops, k, vin = W.op_stream(N, 4096, vb, 0x5EED0104 + rep, get_frac=0.9,
+                                  zipf_theta=0.99)
+        _run_batch(o, g, ops, k, vin, f"replica batch {rep}")
+    _assert_state_equal(o, g, "scaled replica")
+    o.close(); g.close()

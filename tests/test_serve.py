@@ -1,0 +1,132 @@
+"""The continuous-batching server: admission by HBM budget, results that do
+not depend on how requests were batched or interleaved, and an oracle replay
+of each map's logged batch partition that reproduces its page ciphertexts."""
+import threading
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_01742_b300 import workload as W
+from tests.dict_model import DictModel
+
+pytestmark = pytest.mark.gpu
+
+B = pytest.importorskip("paper_2509_01742_b300.bolt")
+
+
+def _requests(n_records, count, vb, seed, max_n):
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(count):
+        n = int(np.exp(rng.uniform(0, np.log(max_n))))
+        ops, k, vin = W.op_stream(n_records, max(1, n), vb, seed * 1000 + r, get_frac=0.6,
+                                  del_frac=0.1, absent_frac=0.15,
+                                  zipf_theta=0.99 if r % 2 else None)
+        out.append((ops, k, vin))
+    return out
+
+
+def test_mixed_results_equal_alone_and_oracle_replay():
+    vb = 24
+    sizes = [1 << 12, 1 << 13, 1 << 15, 1 << 16]
+    srv = B.BoltServer(hbm_budget=8 << 30, max_batch=1024)
+    maps, data, reqs = [], [], []
+    for j, N in enumerate(sizes):
+        keys, vals = W.records(N * 3 // 4, vb, 500 + j)
+        maps.append(srv.add_map(N, vb, keys, vals, 77 + j))
+        data.append((N, keys, vals))
+        reqs.append(_requests(N * 3 // 4, 40, vb, 600 + j, 700))
+    # submit interleaved from two client threads while batches run
+    order = [(j, r) for r in range(40) for j in range(len(sizes))]
+    ids = {}
+    lock = threading.Lock()
+
+    def client(part):
+        for j, r in part:
+            ops, k, vin = reqs[j][r]
+            rid = srv.submit(maps[j], ops, k, vin)
+            with lock:
+                ids[(j, r)] = rid
+    # one thread per map keeps each map's arrival order
+    threads = [threading.Thread(target=client, args=([x for x in order if x[0] == j],))
+               for j in range(len(sizes))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    got = {}
+    for (j, r), rid in ids.items():
+        rc, vout, st, info = srv.wait(rid, len(reqs[j][r][0]), maps[j], timeout_ms=120000)
+        assert rc == 0, rc
+        assert info.done_us >= info.start_us >= info.submit_us
+        got[(j, r)] = (vout, st)
+    for j, (N, keys, vals) in enumerate(data):
+        # alone: the same requests through a plain dict, one after another
+        model = DictModel(keys, vals)
+        for r in range(40):
+            ops, k, vin = reqs[j][r]
+            ev, es = model.apply(ops, k, vin, vb)
+            assert np.array_equal(got[(j, r)][0], ev) and np.array_equal(got[(j, r)][1], es)
+        # oracle replay of the logged batch partition reproduces the pages
+        sizes_log = srv.batches(maps[j])
+        allops = np.concatenate([reqs[j][r][0] for r in range(40)])
+        allk = np.concatenate([reqs[j][r][1] for r in range(40)])
+        allv = np.concatenate([reqs[j][r][2] for r in range(40)])
+        assert sizes_log.sum() == len(allops)
+        o = O.OracleMap(N, vb)
+        assert o.init(keys, vals, 77 + j) == 0
+        lo = 0
+        for s in sizes_log:
+            rc, _, _ = o.access(allops[lo:lo + s], allk[lo:lo + s], allv[lo:lo + s])
+            assert rc == 0
+            lo += s
+        assert np.array_equal(o.pages(), srv.map_pages(maps[j]))
+        o.close()
+    st = srv.stats()
+    assert st["maps_ready"] == len(sizes) and st["queued"] == 0
+    srv.close()
+
+
+def test_admission_by_budget():
+    import time
+    vb, N = 24, 1 << 16
+    keys, vals = W.records(N // 2, vb, 5)
+    # a server map's planned resident footprint, as the server accounts it
+    probe = B.BoltServer(hbm_budget=1 << 40, max_batch=512)
+    pid = probe.add_map(N, vb, keys, vals, 1)
+    t0 = time.time()
+    while probe.map_state(pid) == 0 and time.time() - t0 < 60:
+        time.sleep(0.01)
+    res = probe.stats()["used"]
+    probe.close()
+    _, build = B.plan_bytes(N, vb, batch_cap=512, n_init=N // 2)
+    # room for two maps (plus one build) but not three
+    srv = B.BoltServer(hbm_budget=2 * res + build + (res // 2), max_batch=512)
+    ids = [srv.add_map(N, vb, keys, vals, 10 + j) for j in range(3)]
+    ops, k, vin = W.op_stream(N // 2, 100, vb, 6)
+    r0 = srv.submit(ids[0], ops, k, vin)
+    assert srv.wait(r0, 100, ids[0], timeout_ms=60000)[0] == 0
+    t0 = time.time()
+    while srv.map_state(ids[1]) == 0 and time.time() - t0 < 60:
+        time.sleep(0.01)
+    assert srv.map_state(ids[0]) == 1 and srv.map_state(ids[1]) == 1
+    time.sleep(0.2)
+    assert srv.map_state(ids[2]) == 0  # pending: does not fit
+    assert srv.stats()["maps_pending"] == 1
+    r2 = srv.submit(ids[2], ops, k, vin)  # queued until admitted
+    srv.remove_map(ids[0])
+    rc, vout, st, info = srv.wait(r2, 100, ids[2], timeout_ms=60000)
+    assert rc == 0 and srv.map_state(ids[2]) == 1 and srv.map_state(ids[0]) == 2
+    with pytest.raises(B.BoltError):
+        srv.submit(ids[0], ops, k, vin)  # removed
+    srv.close()
+
+
+def test_footprint_estimate_matches_allocation():
+    for N, vb in [(1 << 14, 8), (1 << 16, 24)]:
+        m = B.BoltMap(N, vb)
+        res, _ = m.footprint()
+        est, _ = B.plan_bytes(N, vb)
+        assert res == est, (N, vb, res, est)
+        m.close()
