@@ -44,17 +44,26 @@ BATCH = 4096
 SEED_DATA = 0x5EED0003
 SEED_OPS = 0x5EED0103
 SEED_MAP = 0x5EED0203
-CONFIG = {
-    "workload": "N=2^28 records x 32 B (8 B uint64 key + 24 B value), oblivious build, then "
-                "2^22 uniform accesses to existing keys (50% GET / 50% PUT) in batches of 4096",
-    "records": 1 << LOG_N,
-    "record_bytes": 8 + VAL_BYTES,
-    "accesses_per_step": N_ACCESS,
-    "batch": BATCH,
-    "c": 8,
-    "alpha": 0.2,
-    "l2": "inputs larger than L2 (8 GiB records, 5.9 GiB position map, 13.7 GiB host pages)",
-}
+def config_for(log_n: int, n_acc: int) -> dict:
+    """The workload description of a headline-shaped run (N = 2^log_n)."""
+    N = 1 << log_n
+    tag_gib = 8 * N / 2**30
+    return {
+        "workload": f"N=2^{log_n} records x 32 B (8 B uint64 key + 24 B value), oblivious build, "
+                    f"then {n_acc} uniform accesses to existing keys (50% GET / 50% PUT) in "
+                    f"batches of {BATCH}",
+        "records": N,
+        "record_bytes": 8 + VAL_BYTES,
+        "accesses_per_step": n_acc,
+        "batch": BATCH,
+        "c": 8,
+        "alpha": 0.2,
+        "l2": (f"inputs larger than L2 ({N * 32 / 2**30:.3g} GiB records, {tag_gib:.3g} GiB of "
+               "sort tags, pages and position map larger still)"),
+    }
+
+
+CONFIG = config_for(LOG_N, N_ACCESS)
 
 
 def aggregate(local: dict, world: int, group=None) -> dict:
@@ -262,6 +271,7 @@ def run_bolt(args) -> None:
 
     m = B.BoltMap(N, VAL_BYTES)
     m.set_param(B.BOLT_PARAM_PROFILE, 1)
+    m.set_param(B.BOLT_PARAM_LOOKAHEAD, args.lookahead)
     info = m.info()
     nb = (n_acc + BATCH - 1) // BATCH
 
@@ -272,11 +282,9 @@ def run_bolt(args) -> None:
         assert rc == 0, rc
         if events:
             events[1].record(stream)
-        for b in range(nb):
-            lo, hi = b * BATCH, min(n_acc, (b + 1) * BATCH)
-            rc = m.access_device(d_ops[lo:hi], d_akeys[lo:hi], d_avin[lo:hi], d_vout[lo:hi],
-                                 d_status[lo:hi], stream=stream)
-            assert rc == 0, rc
+        rc = m.access_device_batches(d_ops, d_akeys, d_avin, d_vout, d_status, BATCH,
+                                     stream=stream)
+        assert rc == 0, rc
         if events:
             events[2].record(stream)
 
@@ -403,7 +411,7 @@ def run_bolt(args) -> None:
         "vs_baseline": None,
         "dtype": "u8/u64 (integer; ChaCha20 ARX)",
         "data": "synthetic (seeded; keys = bijective mix of the record index, random values)",
-        "config": CONFIG,
+        "config": dict(config_for(args.log_n, n_acc), lookahead=bool(args.lookahead)),
         "build": {"value": round(agg["records"] / agg["build_s"] / 1e6, 2), "unit": "Mrec/s",
                   "ms_per_build": round(build_s / args.steps * 1e3, 2)},
         "roofline": roofline,
@@ -428,7 +436,7 @@ def run_sweep(args) -> None:
     """Batch-width sweep on the skewed workload: N = 2^24 records of 64 B
     (8 B key + 56 B value), a 2 GB HBM budget (alpha = 0.2), Zipf(0.99) keys,
     70% GET / 30% PUT; accesses/s for batch widths 1, 4, 16, ..., 65536 (one
-    bolt_access_device call per batch).  Also one access per call vs batches of
+    bolt_access_device_batches call over all the batches of a width).  Also one access per call vs batches of
     4096 on the headline map when --config w1 is given."""
     import torch
     from paper_2509_01742_b300 import bolt as B
@@ -470,10 +478,8 @@ def run_sweep(args) -> None:
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
         a.record(stream)
-        for k in range(nb):
-            lo = k * w
-            assert m.access_device(d_ops[lo:lo + w], d_akeys[lo:lo + w], d_avin[lo:lo + w],
-                                   d_vout[lo:lo + w], d_st[lo:lo + w], stream=stream) == 0
+        assert m.access_device_batches(d_ops[:count], d_akeys[:count], d_avin[:count],
+                                       d_vout[:count], d_st[:count], w, stream=stream) == 0
         b.record(stream)
         b.synchronize()
         wall = time.perf_counter() - t0
@@ -628,6 +634,8 @@ def main():
     ap.add_argument("--accesses", type=int, default=N_ACCESS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--lookahead", type=int, default=0,
+                    help="1 = read each batch's pages while the previous batch runs")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "bolt" and args.config == "headline":
         print("note: at least 3 warm-up steps are required for a valid number", file=sys.stderr)

@@ -80,6 +80,9 @@ typedef struct bolt bolt_t;
 #define BOLT_PARAM_PROFILE 8 /* 1 = time kernel classes with CUDA events */
 #define BOLT_PARAM_BATCH_CAP 9 /* capacity of the device batch buffers, 1..BOLT_MAX_BATCH
                                   (default BOLT_MAX_BATCH); reallocates, drops contents */
+#define BOLT_PARAM_LOOKAHEAD 10 /* 1 = bolt_access_device_batches reads a batch's
+                                   pages while the previous batch runs (default 0);
+                                   results are the same either way */
 
 /* derived parameters (Sec. 3.3 sizing, Sec. 4.2 position map) */
 typedef struct {
@@ -200,6 +203,21 @@ BOLT_API int bolt_access_device(bolt_t* h, const uint8_t* d_ops, const void* d_k
                        const void* d_vals_in, void* d_vals_out, uint8_t* d_status,
                        uint64_t n, void* stream);
 
+/* bolt_access_device_batches -- ceil(n / width) consecutive access batches
+ * (Sec. 4, Algorithm 2 per batch) over DEVICE arrays of n ops: batch j takes
+ * ops [j*width, min(n, (j+1)*width)); the result equals one
+ * bolt_access_device call per slice, in order.  width 0 means the handle's
+ * batch width (BOLT_PARAM_BATCH); width <= the batch capacity.  All five
+ * arrays are required (d_status holds n bytes).  Each batch's preparation
+ * (grouping, DUMMY/REMAP pairs, position-map rows) runs on an internal stream
+ * ahead of the previous batch's main part.  Enqueued on `stream`; the inputs
+ * must be ready in `stream` order at the call; errors are reported as for
+ * bolt_access_device. */
+BOLT_API int bolt_access_device_batches(bolt_t* h, const uint8_t* d_ops, const void* d_keys,
+                                        const void* d_vals_in, void* d_vals_out,
+                                        uint8_t* d_status, uint64_t n, uint32_t width,
+                                        void* stream);
+
 /* bolt_sync -- wait for the handle's enqueued work and report its error. */
 BOLT_API int bolt_sync(bolt_t* h);
 
@@ -232,9 +250,10 @@ BOLT_API int bolt_read_rowcounts(bolt_t* h, uint8_t* dst);
  *   8 whole build                         9 access grouping sort + scans
  *  10 key check: bitonic global steps    11 key check: bitonic in-tile steps
  *  12 access: written pages copied to the host (side stream)
+ *  13 access: lookahead position-map search + page reads (side stream)
  * ms[c] sums the event-timed durations of the spans[c] launches (or phases)
  * of class c; launches counts every kernel the library launched. */
-#define BOLT_PROF_CLASSES 13
+#define BOLT_PROF_CLASSES 14
 typedef struct {
   uint64_t launches;
   uint64_t spans[BOLT_PROF_CLASSES];

@@ -22,11 +22,11 @@ BOLT_GET, BOLT_PUT, BOLT_DEL = 0, 1, 2
 BOLT_MAX_BATCH = 65536
 BOLT_PARAM_ALPHA, BOLT_PARAM_C, BOLT_PARAM_TRACE, BOLT_PARAM_BATCH = 1, 2, 4, 5
 BOLT_PARAM_TRACE_CAP, BOLT_PARAM_CHECK_KEYS, BOLT_PARAM_PROFILE = 6, 7, 8
-BOLT_PARAM_BATCH_CAP = 9
-BOLT_PROF_CLASSES = 13
+BOLT_PARAM_BATCH_CAP, BOLT_PARAM_LOOKAHEAD = 9, 10
+BOLT_PROF_CLASSES = 14
 PROF_NAMES = ("sort_global", "sort_tile", "page_build", "p2c_rounds", "key_check",
               "access_batch", "gather", "evict", "build", "group", "ksort_global",
-              "ksort_tile", "flush")
+              "ksort_tile", "flush", "ahead")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -59,8 +59,8 @@ class bolt_stats_t(ctypes.Structure):
 
 
 class bolt_profile_t(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_uint64), ("spans", ctypes.c_uint64 * 13),
-                ("ms", ctypes.c_double * 13)]
+    _fields_ = [("launches", ctypes.c_uint64), ("spans", ctypes.c_uint64 * BOLT_PROF_CLASSES),
+                ("ms", ctypes.c_double * BOLT_PROF_CLASSES)]
 
 
 class bolt_tune_t(ctypes.Structure):
@@ -95,6 +95,7 @@ _SIGS = {
     "bolt_init_device_noalloc": ([_P, _P, _P, _u64, _u64, _P], _i),
     "bolt_access": ([_P, _P, _P, _P, _P, _P, _u64], _i),
     "bolt_access_device": ([_P, _P, _P, _P, _P, _P, _u64, _P], _i),
+    "bolt_access_device_batches": ([_P, _P, _P, _P, _P, _P, _u64, ctypes.c_uint32, _P], _i),
     "bolt_sync": ([_P], _i),
     "bolt_destroy": ([_P], _i),
     "bolt_get_info": ([_P, ctypes.POINTER(bolt_info_t)], _i),
@@ -230,6 +231,17 @@ class BoltMap:
                                   ctypes.c_void_p(keys.data_ptr()),
                                   ctypes.c_void_p(vals_in.data_ptr()),
                                   ctypes.c_void_p(vals_out.data_ptr()), st, ops.numel(), s)
+
+    def access_device_batches(self, ops, keys, vals_in, vals_out, status, width: int = 0,
+                              stream=None) -> int:
+        """Consecutive batches of `width` ops over device tensors (one call)."""
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        return bolt_access_device_batches(self._h, ctypes.c_void_p(ops.data_ptr()),
+                                          ctypes.c_void_p(keys.data_ptr()),
+                                          ctypes.c_void_p(vals_in.data_ptr()),
+                                          ctypes.c_void_p(vals_out.data_ptr()),
+                                          ctypes.c_void_p(status.data_ptr()), ops.numel(),
+                                          width, s)
 
     def sync(self) -> int:
         return bolt_sync(self._h)

@@ -170,6 +170,23 @@ __device__ __forceinline__ void ht_insert(const BatchDev& b, uint32_t page, uint
   }
 }
 
+// the warp scans the key's d = 4 rows, R slots each (ballot per row)
+__device__ __forceinline__ uint32_t pm_search(const MapDev& m, const BatchDev& b, uint32_t i,
+                                              uint64_t key, int lane) {
+  uint32_t found = NONE32;
+  const uint4 rows = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
+  const uint32_t rr[4] = {rows.x, rows.y, rows.z, rows.w};
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    bool match = false;
+    const uint64_t idx = (uint64_t)rr[j] * m.R + lane;
+    if (lane < (int)m.R) match = meta_loc(m.pm_meta[idx]) != LOC_EMPTY && m.pm_key[idx] == key;
+    const uint32_t bal = __ballot_sync(0xffffffffu, match);
+    if (bal && found == NONE32) found = (uint32_t)((uint64_t)rr[j] * m.R + (__ffs(bal) - 1));
+  }
+  return found;
+}
+
 // warp per op
 __global__ void k_lookup(MapDev m, BatchDev b, uint32_t n) {
   const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -178,17 +195,20 @@ __global__ void k_lookup(MapDev m, BatchDev b, uint32_t n) {
   uint32_t found = NONE32;
   if (b.leader[i] == i) {
     const uint64_t key = b.keys[i];
-    const uint4 rows = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
-    const uint32_t rr[4] = {rows.x, rows.y, rows.z, rows.w};
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      bool match = false;
-      uint64_t idx = (uint64_t)rr[j] * m.R + lane;
-      if (lane < (int)m.R)
-        match = meta_loc(m.pm_meta[idx]) != LOC_EMPTY && m.pm_key[idx] == key;
-      uint32_t bal = __ballot_sync(0xffffffffu, match);
-      if (bal && found == NONE32) found = (uint32_t)((uint64_t)rr[j] * m.R + (__ffs(bal) - 1));
+    bool scan = true;
+    if (b.la_on && b.done[i]) {
+      // searched ahead: a miss stands (the key is not in the previous batch,
+      // so nothing inserted it since); a hit is re-checked, since the search
+      // may have seen a slot that the previous batch was re-using
+      const uint32_t hs = b.hit[i];
+      if (hs == NONE32) {
+        scan = false;
+      } else if (meta_loc(m.pm_meta[hs]) != LOC_EMPTY && m.pm_key[hs] == key) {
+        found = hs;
+        scan = false;
+      }
     }
+    if (scan) found = pm_search(m, b, i, key, lane);
   }
   if (lane == 0) {
     b.hit[i] = found;
@@ -205,6 +225,136 @@ __global__ void k_lookup(MapDev m, BatchDev b, uint32_t n) {
       ht_insert(b, q, pos);
     } else {
       b.pos_page[pos] = NONE32;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// lookahead
+constexpr uint32_t PREV_UNKNOWN = 0xFFFFFFFEu;
+
+// the previous batch's op owning the key's slot in its key table; NONE32 if
+// the key is not in the previous batch
+__device__ __forceinline__ uint32_t prev_owner(const BatchDev& b, uint64_t key) {
+  uint32_t h = key_hash(key, b.prev_kt_mask);
+  for (uint32_t probe = 0; probe <= b.prev_kt_mask; probe++) {
+    const uint32_t own = b.prev_kt_own[h];
+    if (own == 0) return NONE32;
+    if (b.prev_keys[own - 1] == key) return own - 1;
+    h = (h + 1) & b.prev_kt_mask;
+  }
+  return PREV_UNKNOWN;
+}
+
+__device__ __forceinline__ void la_insert(const BatchDev& b, uint32_t q) {
+  uint32_t h = ht_hash(q, b.ht_mask);
+  for (uint32_t probe = 0; probe <= b.ht_mask; probe++) {
+    const uint32_t old = atomicCAS(b.la_key + h, NONE32, q);
+    if (old == NONE32) {
+      const uint32_t e = atomicAdd(b.la_count, 1u);
+      b.la_idx[h] = e;
+      b.la_list[e] = q;
+      return;
+    }
+    if (old == q) return;
+    h = (h + 1) & b.ht_mask;
+  }
+}
+
+__device__ __forceinline__ uint32_t la_find(const BatchDev& b, uint32_t q) {
+  uint32_t h = ht_hash(q, b.ht_mask);
+  for (uint32_t probe = 0; probe <= b.ht_mask; probe++) {
+    const uint32_t k = b.la_key[h];
+    if (k == q) return b.la_idx[h];
+    if (k == NONE32) return NONE32;
+    h = (h + 1) & b.ht_mask;
+  }
+  return NONE32;
+}
+
+__global__ void k_clear_la(BatchDev b) {
+  for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h <= b.ht_mask;
+       h += gridDim.x * blockDim.x)
+    b.la_key[h] = NONE32;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *b.la_count = 0;
+}
+
+// warp per op: leaders whose key the previous batch does not touch search the
+// position map now (the previous batch changes no slot of such a key: it
+// removes, deletes and re-places only its own keys, and its eviction changes
+// only the location field of an occupied slot).  A leader whose key the
+// previous batch touches gets the bins that batch re-maps it to (its
+// leader's REMAP pair) if the key is present after it, else its DUMMY pair.
+// Then the page of every read position whose bin is known is queued for
+// reading ahead.  What is found here only decides which pages are read
+// ahead: the main lookup re-checks hits and searches for the other leaders.
+__global__ void k_ahead_lookup(MapDev m, BatchDev b, uint32_t n) {
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  bool known = true;
+  uint64_t pr = b.pair[i];
+  if (b.leader[i] == i) {
+    const uint64_t key = b.keys[i];
+    const uint32_t o = prev_owner(b, key);
+    if (o == NONE32) {
+      const uint32_t found = pm_search(m, b, i, key, lane);
+      if (found != NONE32) pr = m.pm_bins[found];
+      if (lane == 0) {
+        b.hit[i] = found;
+        b.done[i] = 1;
+        b.pres[i] = found != NONE32 ? 1 : 0;
+      }
+    } else {
+      uint32_t after = 2;
+      uint32_t lead = 0;
+      if (o != PREV_UNKNOWN) {
+        lead = b.prev_leader[o];
+        const uint32_t lw = b.prev_lastw[lead];
+        after = lw != NONE32 ? (b.prev_ops[lw] == OP_PUT ? 1u : 0u) : b.prev_pres[lead];
+      }
+      if (after == 1) pr = b.prev_rpair[lead];
+      known = after != 2;
+      if (lane == 0) {
+        b.done[i] = 0;
+        b.pres[i] = (uint8_t)after;
+      }
+    }
+  }
+  if (known && lane < 2) {
+    const uint32_t p = lane == 0 ? (uint32_t)pr : (uint32_t)(pr >> 32);
+    if (p >= m.K) la_insert(b, (uint32_t)(p - m.K));
+  }
+}
+
+// Host-page copies that run while other kernels of the access path run use
+// few warps, one 512-byte chunk in flight per warp: pending host reads and
+// writes slow down every random HBM access on the device roughly in
+// proportion to how many are outstanding, while a few hundred in flight
+// already keep the host link near its random-page rate.
+constexpr uint32_t LINK_WARPS = 192;
+constexpr uint32_t COPY_BLOCK = 128;
+constexpr uint32_t LINK_BLOCKS = LINK_WARPS * 32 / COPY_BLOCK;
+
+// the pages queued ahead, one 512-byte chunk per warp step: host read +
+// decryption into la_buf.  Pages the previous batch rewrites may be read torn
+// here; the main gather takes those from the previous batch's ciphertexts.
+__global__ void __launch_bounds__(COPY_BLOCK) k_ahead_gather(MapDev m, BatchDev b) {
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t nch = (m.page_bytes + 511) / 512;
+  const uint32_t items = *b.la_count * nch;
+  for (uint32_t it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nw) {
+    const uint32_t e = it / nch, c = (it % nch) * 512, off = c + 16 * lane;
+    const uint64_t q = b.la_list[e];
+    uint4 x = make_uint4(0, 0, 0, 0);
+    if (off < m.page_bytes) x = *reinterpret_cast<const uint4*>(m.pages + q * m.page_bytes + off);
+    const uint64_t v = m.version[q];
+    const uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)v,
+                                 (uint32_t)(v >> 32));
+    if (off < m.page_bytes) {
+      x.x ^= ks.x; x.y ^= ks.y; x.z ^= ks.z; x.w ^= ks.w;
+      *reinterpret_cast<uint4*>(b.la_buf + (uint64_t)e * m.page_bytes + off) = x;
     }
   }
 }
@@ -298,6 +448,55 @@ __global__ void __launch_bounds__(PAGES_BLOCK) k_pages_emit(MapDev m, BatchDev b
   }
 }
 
+// Batches of up to 4096 ops (8192 read positions): the three passes in one
+// CTA, each thread over 8 consecutive positions.
+constexpr uint32_t PAGES_SMALL_MAX = 8192;
+
+__global__ void __launch_bounds__(1024) k_pages_small(MapDev m, BatchDev b, uint32_t np) {
+  __shared__ uint32_t sh[32];
+  __shared__ unsigned long long s_tbase;
+  const uint32_t per = (np + 1023) / 1024;
+  const uint32_t lo = threadIdx.x * per;
+  uint32_t qs[8], slots[8], flags = 0, cv = 0, cf = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < 8; k++) {
+    bool valid = false, first = false;
+    qs[k] = NONE32;
+    slots[k] = 0;
+    if (k < per) pos_flags(b, lo + k, np, valid, first, qs[k], slots[k]);
+    cv += valid;
+    cf += first;
+    flags |= (valid ? 1u : 0u) << (2 * k);
+    flags |= (first ? 1u : 0u) << (2 * k + 1);
+  }
+  uint32_t tv, tf;
+  uint32_t rv = block_excl_scan(cv, sh, tv);
+  uint32_t d = block_excl_scan(cf, sh, tf);
+  if (threadIdx.x == 0) {
+    const uint64_t tbase = m.trace_on ? *m.trace_len : 0;
+    s_tbase = tbase;
+    *b.dcount = tf;
+    b.trace_base[0] = tbase;
+    b.trace_base[1] = tv;
+    if (m.trace_on) *m.trace_len = tbase + tv + tf;
+  }
+  __syncthreads();
+  const uint64_t tbase = s_tbase;
+#pragma unroll
+  for (uint32_t k = 0; k < 8; k++) {
+    if (!((flags >> (2 * k)) & 1u)) continue;
+    if (m.trace_on && tbase + rv < m.trace_cap) m.trace[tbase + rv] = qs[k];
+    rv++;
+    if ((flags >> (2 * k + 1)) & 1u) {
+      b.dpage[d] = qs[k];
+      b.ht_d[slots[k]] = d;
+      const uint64_t w = tbase + tv + d;
+      if (m.trace_on && w < m.trace_cap) m.trace[w] = qs[k] | 0x80000000u;
+      d++;
+    }
+  }
+}
+
 // page q in the previous batch's write set? -> its distinct index, else NONE
 __device__ __forceinline__ uint32_t prev_written(const BatchDev& b, uint32_t q) {
   if (!b.prev_valid) return NONE32;
@@ -318,20 +517,40 @@ __global__ void k_gather(MapDev m, BatchDev b) {
   const int lane = threadIdx.x & 31;
   if (d >= *b.dcount) return;
   const uint64_t q = b.dpage[d];
-  const uint64_t v = m.version[q];
-  const uint8_t* host = m.pages + q * m.page_bytes;
-  // the first host read is issued before the previous-batch lookup resolves;
-  // a page the previous batch wrote (rare) is taken from its ciphertext copy
-  uint4 first = make_uint4(0, 0, 0, 0);
-  if (16 * lane < m.page_bytes) first = *reinterpret_cast<const uint4*>(host + 16 * lane);
-  const uint32_t pd = prev_written(b, (uint32_t)q);
   uint8_t* dst = b.dbuf + (uint64_t)d * m.page_bytes;
+  const uint8_t* host = m.pages + q * m.page_bytes;
+  uint32_t pd = NONE32;
+  uint4 first = make_uint4(0, 0, 0, 0);
+  if (b.la_on) {
+    // a page the previous batch wrote comes from its ciphertext copy; else a
+    // page read ahead is copied; else it is read from the host now
+    pd = prev_written(b, (uint32_t)q);
+    if (pd == NONE32) {
+      const uint32_t e = la_find(b, (uint32_t)q);
+      if (e != NONE32) {
+        const uint4* src = reinterpret_cast<const uint4*>(b.la_buf + (uint64_t)e * m.page_bytes);
+        for (uint32_t c = lane; c < m.page_bytes / 16; c += 32)
+          reinterpret_cast<uint4*>(dst)[c] = src[c];
+        if (lane == 0) b.removed[d] = 0;
+        return;
+      }
+      if (16 * lane < m.page_bytes) first = *reinterpret_cast<const uint4*>(host + 16 * lane);
+    }
+  } else {
+    // the first host read is issued before the previous-batch lookup
+    // resolves; a page the previous batch wrote (rare) is taken from its
+    // ciphertext copy
+    if (16 * lane < m.page_bytes) first = *reinterpret_cast<const uint4*>(host + 16 * lane);
+    pd = prev_written(b, (uint32_t)q);
+  }
+  const uint64_t v = m.version[q];
   for (uint32_t c = 0; c < m.page_bytes; c += 512) {
     const uint32_t off = c + 16 * lane;
     uint4 x = first;
-    if (c > 0 && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(host + off);
     if (pd != NONE32 && off < m.page_bytes)
       x = *reinterpret_cast<const uint4*>(b.prev_dbuf + (uint64_t)pd * m.page_bytes + off);
+    else if (c > 0 && off < m.page_bytes)
+      x = *reinterpret_cast<const uint4*>(host + off);
     const uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)v,
                                  (uint32_t)(v >> 32));
     if (off < m.page_bytes) {
@@ -342,15 +561,21 @@ __global__ void k_gather(MapDev m, BatchDev b) {
   if (lane == 0) b.removed[d] = 0;
 }
 
-// warp per written page: copy the ciphertext from dbuf to the host page
-__global__ void k_flush(MapDev m, BatchDev b) {
-  const uint32_t d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// the written pages, one 512-byte chunk per warp step: copy the ciphertexts
+// from dbuf to the host pages (few warps: runs beside the next batch)
+__global__ void __launch_bounds__(COPY_BLOCK) k_flush(MapDev m, BatchDev b) {
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (d >= *b.dcount) return;
-  const uint64_t q = b.dpage[d];
-  const uint4* src = reinterpret_cast<const uint4*>(b.dbuf + (uint64_t)d * m.page_bytes);
-  uint4* dst = reinterpret_cast<uint4*>(m.pages + q * m.page_bytes);
-  for (uint32_t c = lane; c < m.page_bytes / 16; c += 32) dst[c] = src[c];
+  const uint32_t nch = (m.page_bytes + 511) / 512;
+  const uint32_t items = *b.dcount * nch;
+  for (uint32_t it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nw) {
+    const uint32_t off = (it % nch) * 512 + 16 * lane;
+    if (off < m.page_bytes) {
+      const uint64_t q = b.dpage[it / nch];
+      *reinterpret_cast<uint4*>(m.pages + q * m.page_bytes + off) =
+          *reinterpret_cast<const uint4*>(b.dbuf + (uint64_t)(it / nch) * m.page_bytes + off);
+    }
+  }
 }
 
 __device__ __forceinline__ void ring_push(const MapDev& m, uint32_t slot) {
@@ -360,6 +585,14 @@ __device__ __forceinline__ void ring_push(const MapDev& m, uint32_t slot) {
 
 // warp per op: find_remove for hits (Alg. 1 lines 6 and 9)
 __global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
+  // the previous batch's page table was last read by this batch's gather:
+  // return the entries it used to NONE for the batch after this one
+  if (b.clr_ht_key)
+    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h <= b.clr_mask;
+         h += gridDim.x * blockDim.x) {
+      b.clr_ht_key[h] = NONE32;
+      b.clr_ht_min[h] = NONE32;
+    }
   const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= n || b.leader[i] != i) return;
@@ -668,29 +901,104 @@ __global__ void __launch_bounds__(1024) k_remap_smem(MapDev m, BatchDev b, uint3
   for (uint32_t w = threadIdx.x; w < rw; w += blockDim.x) m.rowcnt[w] = srow[w];
 }
 
+// Batches of at most 4 x 1024 ops: every thread loads its (up to) four ops
+// into registers once, so a round costs two barriers and shared-memory work
+// only (the rounds of a small map are many and short).
+constexpr int REMAP_REG_OPS = 4;
+
+__global__ void __launch_bounds__(1024) k_remap_smem_reg(MapDev m, BatchDev b, uint32_t n) {
+  extern __shared__ uint32_t rsm[];
+  const uint32_t lw = (uint32_t)(m.B + 3) / 4, rw = (uint32_t)(m.rows + 3) / 4;
+  uint32_t* sload = rsm;
+  uint32_t* srow = rsm + lw;
+  for (uint32_t w = threadIdx.x; w < lw; w += blockDim.x) sload[w] = m.load[w];
+  for (uint32_t w = threadIdx.x; w < rw; w += blockDim.x) srow[w] = m.rowcnt[w];
+  uint32_t op[REMAP_REG_OPS], p1[REMAP_REG_OPS], p2[REMAP_REG_OPS], dest[REMAP_REG_OPS];
+  uint4 rows[REMAP_REG_OPS];
+  uint32_t row[REMAP_REG_OPS];
+  bool act[REMAP_REG_OPS], fresh[REMAP_REG_OPS];
+#pragma unroll
+  for (int k = 0; k < REMAP_REG_OPS; k++) {
+    op[k] = threadIdx.x + k * blockDim.x;
+    act[k] = op[k] < n && b.leader[op[k]] == op[k] && b.fpres[op[k]];
+    fresh[k] = false;
+    dest[k] = row[k] = 0;
+    if (act[k]) {
+      const uint64_t pr = b.rpair[op[k]];
+      p1[k] = (uint32_t)pr;
+      p2[k] = (uint32_t)(pr >> 32);
+      fresh[k] = b.hit[op[k]] == NONE32;
+      if (fresh[k]) rows[k] = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)op[k]);
+    }
+  }
+  __syncthreads();
+  uint32_t err = 0;
+  for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+    const uint64_t hi = lo + m.Wr;
+#pragma unroll
+    for (int k = 0; k < REMAP_REG_OPS; k++) {
+      if (!act[k] || op[k] < lo || op[k] >= hi) continue;
+      dest[k] = sbyte_get(sload, p1[k]) <= sbyte_get(sload, p2[k]) ? p1[k] : p2[k];
+      if (fresh[k]) {
+        const uint32_t rr[4] = {rows[k].x, rows[k].y, rows[k].z, rows[k].w};
+        uint32_t best = rr[0], bc = sbyte_get(srow, rr[0]);
+#pragma unroll
+        for (int j = 1; j < 4; j++) {
+          const uint32_t c = sbyte_get(srow, rr[j]);
+          if (c < bc) {
+            best = rr[j];
+            bc = c;
+          }
+        }
+        row[k] = best;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < REMAP_REG_OPS; k++) {
+      if (!act[k] || op[k] < lo || op[k] >= hi) continue;
+      if (sbyte_inc(sload, dest[k]) + 1 > m.lmax) err |= ERR_LOAD;
+      if (fresh[k] && sbyte_inc(srow, row[k]) + 1 > m.R) err |= ERR_ROW;
+    }
+    __syncthreads();
+  }
+  if (err) set_err(m, err);
+#pragma unroll
+  for (int k = 0; k < REMAP_REG_OPS; k++)
+    if (act[k]) {
+      b.rdest[op[k]] = dest[k];
+      if (fresh[k]) b.rrow[op[k]] = row[k];
+    }
+  for (uint32_t w = threadIdx.x; w < lw; w += blockDim.x) m.load[w] = sload[w];
+  for (uint32_t w = threadIdx.x; w < rw; w += blockDim.x) m.rowcnt[w] = srow[w];
+}
+
 __global__ void k_remap_rest(MapDev m, BatchDev b, uint32_t n) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n || b.leader[i] != i || !b.fpres[i]) return;
   remap_place(m, b, i, b.rdest[i]);
 }
 
-__global__ void k_clear_table(BatchDev b) {
-  for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h <= b.ht_mask;
+__global__ void k_clear_keys(BatchDev b, uint32_t n) {
+  for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h <= b.kt_mask;
        h += gridDim.x * blockDim.x) {
-    b.ht_key[h] = NONE32;
-    b.ht_min[h] = NONE32;
-    if (h <= b.kt_mask) b.kt_own[h] = 0;
+    b.kt_own[h] = 0;
+    if (h < n) b.pres[h] = 2;
   }
 }
 
-cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
-                          cudaStream_t st, const FlushCtx& fc) {
+
+// The batch's preparation depends only on its own inputs: the grouping keys
+// (key hash table), the DUMMY / REMAP pairs and position-map rows, the
+// grouping sort and scan.  It may run on its own stream, ahead of the
+// previous batch's main part.
+cudaError_t launch_prep(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
+                        cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   uint32_t n_sort = 512;
   while (n_sort < n) n_sort <<= 1;
   if (n_sort > 512 && n_sort < 4096) n_sort = 4096;
-  ProfSpan whole(P_ACCESS, st);
-  k_clear_table<<<64, 256, 0, st>>>(b);
+  k_clear_keys<<<32, 256, 0, st>>>(b, n);
   const int keys32 = n_sort <= 4096;
   k_stage<<<(3 * n_sort + 255) / 256, 256, 0, st>>>(m, b, n, n_sort, t0, keys32);
   count_launch(2);
@@ -708,15 +1016,42 @@ cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64
     }
     count_launch();
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ahead(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  ProfSpan ps(P_AHEAD, st);
+  k_clear_la<<<64, 256, 0, st>>>(b);
+  const uint32_t warp_blocks = (n * 32 + 255) / 256;
+  k_ahead_lookup<<<warp_blocks, 256, 0, st>>>(m, b, n);
+  k_ahead_gather<<<LINK_BLOCKS, COPY_BLOCK, 0, st>>>(m, b);
+  count_launch(3);
+  return cudaGetLastError();
+}
+
+// The part that reads and changes the map: lookup, page reads, find_remove,
+// exec, write-back, remap.
+cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st,
+                        const FlushCtx& fc) {
+  if (n == 0) return cudaSuccess;
+  cudaError_t e;
+  ProfSpan whole(P_ACCESS, st);
   const uint32_t warp_blocks = (n * 32 + 255) / 256;
   k_lookup<<<warp_blocks, 256, 0, st>>>(m, b, n);
+  count_launch();
   {
     const uint32_t np = 2 * n;
-    const uint32_t nblk = (np + PAGES_BLOCK - 1) / PAGES_BLOCK;
-    k_pages_count<<<nblk, PAGES_BLOCK, 0, st>>>(b, np, b.block_cnt);
-    k_pages_scan<<<1, 1024, 0, st>>>(m, b, nblk, b.block_cnt);
-    k_pages_emit<<<nblk, PAGES_BLOCK, 0, st>>>(m, b, np, b.block_cnt);
-    count_launch(4);
+    if (np <= PAGES_SMALL_MAX) {
+      k_pages_small<<<1, 1024, 0, st>>>(m, b, np);
+      count_launch();
+    } else {
+      const uint32_t nblk = (np + PAGES_BLOCK - 1) / PAGES_BLOCK;
+      k_pages_count<<<nblk, PAGES_BLOCK, 0, st>>>(b, np, b.block_cnt);
+      k_pages_scan<<<1, 1024, 0, st>>>(m, b, nblk, b.block_cnt);
+      k_pages_emit<<<nblk, PAGES_BLOCK, 0, st>>>(m, b, np, b.block_cnt);
+      count_launch(3);
+    }
   }
   const uint32_t dmax = 2 * n;  // distinct pages are at most two per op
   {
@@ -743,7 +1078,7 @@ cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64
   cudaStreamWaitEvent(fc.flush_st, fc.ev_evicted, 0);
   {
     ProfSpan ps(P_FLUSH, fc.flush_st);
-    k_flush<<<(dmax * 32 + 255) / 256, 256, 0, fc.flush_st>>>(m, b);
+    k_flush<<<LINK_BLOCKS, COPY_BLOCK, 0, fc.flush_st>>>(m, b);
     count_launch();
   }
   cudaEventRecord(fc.ev_flushed, fc.flush_st);
@@ -752,12 +1087,14 @@ cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64
   const uint64_t rounds = (n + m.Wr - 1) / m.Wr;
   const size_t rsmem = ((m.B + 3) / 4 + (m.rows + 3) / 4) * 4;
   if (rounds > 1 && m.B <= REMAP_SMEM_MAX_BINS && m.rows <= REMAP_SMEM_MAX_ROWS) {
+    const bool reg = n <= REMAP_REG_OPS * 1024;
     if (rsmem > 48 * 1024) {
-      e = cudaFuncSetAttribute(k_remap_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)rsmem);
+      e = cudaFuncSetAttribute(reg ? (const void*)k_remap_smem_reg : (const void*)k_remap_smem,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
       if (e != cudaSuccess) return e;
     }
-    k_remap_smem<<<1, 1024, rsmem, st>>>(m, b, n);
+    if (reg) k_remap_smem_reg<<<1, 1024, rsmem, st>>>(m, b, n);
+    else k_remap_smem<<<1, 1024, rsmem, st>>>(m, b, n);
     k_remap_rest<<<(n + 255) / 256, 256, 0, st>>>(m, b, n);
     count_launch(2);
   } else {

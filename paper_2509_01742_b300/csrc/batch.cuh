@@ -43,6 +43,11 @@ struct BatchDev {
   const uint32_t* prev_ht_d;
   const uint8_t* prev_dbuf;
   uint32_t prev_ht_mask, prev_valid;
+  // the previous batch's page table, cleared by this batch once read (the
+  // entries up to clr_mask; none when clr_ht_key is null)
+  uint32_t* clr_ht_key;
+  uint32_t* clr_ht_min;
+  uint32_t clr_mask, pad3;
   // values
   uint8_t* init_val;   // [cap * vb] value found for a leader hit
   uint8_t* init_present;  // [cap]
@@ -50,6 +55,30 @@ struct BatchDev {
   uint8_t* fpres;      // [cap] key present after the batch (leaders)
   uint32_t* rdest;     // [cap] P2C destination
   uint32_t* rrow;      // [cap] position-map row for a new key
+  // lookahead: while the previous batch runs, leaders whose key is not in it
+  // search the position map, and the pages of every read position whose bin
+  // is then known are read and decrypted ahead
+  uint32_t la_on, la_pad;
+  uint8_t* done;       // [cap] leader searched ahead (its hit is in hit[])
+  uint32_t* la_key;    // [ht_mask + 1] page read ahead, or NONE
+  uint32_t* la_idx;    // [ht_mask + 1] its row in la_buf
+  uint32_t* la_list;   // [2 cap] pages read ahead, in claim order
+  uint32_t* la_count;  // [1]
+  uint8_t* la_buf;     // [2 cap * page_bytes] their plaintexts
+  uint8_t* pres;       // [cap] (leaders) key present before the batch as
+                       // seen ahead: 0 no, 1 yes, 2 not known
+  // the previous batch: key table, keys, ops, grouping, REMAP pairs and
+  // presence seen ahead (a key it touches is re-mapped to its leader's REMAP
+  // pair when present after it, so the bins this batch reads for the key are
+  // known before the previous batch ends)
+  const uint32_t* prev_kt_own;
+  const uint64_t* prev_keys;
+  const uint8_t* prev_ops;
+  const uint32_t* prev_leader;
+  const uint32_t* prev_lastw;
+  const uint64_t* prev_rpair;
+  const uint8_t* prev_pres;
+  uint32_t prev_kt_mask, pad2;
 };
 
 cudaError_t sort_batch_keys(uint64_t* keys, uint32_t n_pow2, cudaStream_t st);
@@ -63,7 +92,13 @@ struct FlushCtx {
   cudaEvent_t ev_flushed;
 };
 
-cudaError_t launch_access(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
-                          cudaStream_t st, const FlushCtx& fc);
+cudaError_t launch_prep(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
+                        cudaStream_t st);
+cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st,
+                        const FlushCtx& fc);
+// The lookahead part of a batch (b.la_on = 1), after its preparation: may
+// run while the previous batch's main part runs, once the flush two batches
+// back has landed.
+cudaError_t launch_ahead(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st);
 
 }  // namespace bdev

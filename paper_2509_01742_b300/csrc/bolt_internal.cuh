@@ -300,7 +300,8 @@ enum ProfClass : int {
   P_KSORT_GLOBAL = 10,  // key-uniqueness check: bitonic global steps
   P_KSORT_TILE = 11,    // key-uniqueness check: bitonic in-tile steps
   P_FLUSH = 12,         // access: written pages copied to the host
-  P_NCLASS = 13
+  P_AHEAD = 13,         // access: lookahead search + page reads (side stream)
+  P_NCLASS = 14
 };
 
 struct Prof {

@@ -24,6 +24,7 @@ struct bolt {
   uint64_t trace_cap = 1ull << 22;
   bool trace_on = false;
   bool check_keys = true;
+  bool lookahead = false;     // BOLT_PARAM_LOOKAHEAD
   bolt_info_t info{};
 
   bdev::MapDev m{};
@@ -66,6 +67,30 @@ struct bolt {
   uint32_t* s_dpage[2] = {nullptr, nullptr};
   uint32_t* s_dcount[2] = {nullptr, nullptr};
   uint8_t* s_dbuf[2] = {nullptr, nullptr};
+  // per-slot outputs of a batch's preparation (grouping, PRF pairs, rows)
+  // and lookahead (position-map hits, pages read ahead), so that the next
+  // batch's preparation and lookahead can run on st_prep while this batch's
+  // main part runs
+  struct PrepSet {
+    uint64_t* skeys = nullptr;
+    uint32_t* kt_own = nullptr;
+    uint32_t* leader = nullptr;
+    uint32_t* prevw = nullptr;
+    uint32_t* lastw = nullptr;
+    uint64_t* pair = nullptr;
+    uint64_t* rpair = nullptr;
+    uint32_t* rows = nullptr;
+    uint32_t* hit = nullptr;
+    uint8_t* done = nullptr;
+    uint8_t* pres = nullptr;
+    uint32_t* la_key = nullptr;
+    uint32_t* la_idx = nullptr;
+    uint32_t* la_list = nullptr;
+    uint32_t* la_count = nullptr;
+    uint8_t* la_buf = nullptr;
+  } s_prep[2];
+  cudaStream_t st_prep = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_prep[2] = {nullptr, nullptr}, ev_pfree[2] = {nullptr, nullptr};
 };
 
 

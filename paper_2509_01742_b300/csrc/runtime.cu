@@ -76,7 +76,7 @@ int cuda_fail(cudaError_t e) {
 cudaError_t sync_all(bolt* h) {
   cudaError_t e = cudaSuccess;
   if (h->last_st && h->last_st != h->st) e = cudaStreamSynchronize(h->last_st);
-  for (cudaStream_t s : {h->st, h->st2, h->st_fl}) {
+  for (cudaStream_t s : {h->st, h->st2, h->st_fl, h->st_prep}) {
     if (!s) continue;
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = e2;
@@ -132,12 +132,13 @@ void free_state(bolt* h) {
 // streams and events of a handle (any of them may be null)
 void destroy_streams(bolt* h) {
   for (cudaEvent_t* ev : {&h->ev_fork, &h->ev_join, &h->ev_evicted[0], &h->ev_evicted[1],
-                          &h->ev_flushed[0], &h->ev_flushed[1]})
+                          &h->ev_flushed[0], &h->ev_flushed[1], &h->ev_in, &h->ev_prep[0],
+                          &h->ev_prep[1], &h->ev_pfree[0], &h->ev_pfree[1]})
     if (*ev) {
       cudaEventDestroy(*ev);
       *ev = nullptr;
     }
-  for (cudaStream_t* s : {&h->st_fl, &h->st2, &h->st})
+  for (cudaStream_t* s : {&h->st_prep, &h->st_fl, &h->st2, &h->st})
     if (*s) {
       cudaStreamDestroy(*s);
       *s = nullptr;
@@ -204,22 +205,32 @@ int alloc_state(bolt* h) {
   TRY(dalloc(h, &b.vin, cap * vb));
   TRY(dalloc(h, &b.vout, cap * vb));
   TRY(dalloc(h, &b.status, cap));
-  TRY(dalloc(h, &b.skeys, sort_cap));
   b.kt_mask = (uint32_t)(2 * cap2 < 128 ? 127 : 2 * cap2 - 1);
-  TRY(dalloc(h, &b.kt_own, (uint64_t)b.kt_mask + 1));
-  TRY(dalloc(h, &b.leader, cap));
-  TRY(dalloc(h, &b.prevw, cap));
-  TRY(dalloc(h, &b.lastw, cap));
-  TRY(dalloc(h, &b.pair, cap));
-  TRY(dalloc(h, &b.rpair, cap));
-  TRY(dalloc(h, &b.rows, 4 * cap));
-  TRY(dalloc(h, &b.hit, cap));
+  const uint32_t ht = (uint32_t)(4 * cap2 < 256 ? 256 : 4 * cap2);
+  b.ht_mask = ht - 1;
+  for (int s = 0; s < 2; s++) {
+    bolt::PrepSet& ps = h->s_prep[s];
+    TRY(dalloc(h, &ps.skeys, sort_cap));
+    TRY(dalloc(h, &ps.kt_own, (uint64_t)b.kt_mask + 1));
+    TRY(dalloc(h, &ps.leader, cap));
+    TRY(dalloc(h, &ps.prevw, cap));
+    TRY(dalloc(h, &ps.lastw, cap));
+    TRY(dalloc(h, &ps.pair, cap));
+    TRY(dalloc(h, &ps.rpair, cap));
+    TRY(dalloc(h, &ps.rows, 4 * cap));
+    TRY(dalloc(h, &ps.hit, cap));
+    TRY(dalloc(h, &ps.done, cap));
+    TRY(dalloc(h, &ps.pres, cap));
+    TRY(dalloc(h, &ps.la_key, ht));
+    TRY(dalloc(h, &ps.la_idx, ht));
+    TRY(dalloc(h, &ps.la_list, 2 * cap));
+    TRY(dalloc(h, &ps.la_count, 1));
+    TRY(dalloc(h, &ps.la_buf, 2 * cap * I.page_bytes));
+  }
   TRY(dalloc(h, &b.pos_page, 2 * cap));
   TRY(dalloc(h, &b.pos_slot, 2 * cap));
   TRY(dalloc(h, &b.block_cnt, 2 * ((2 * cap + 255) / 256) + 2));
   TRY(dalloc(h, &b.trace_base, 2));
-  const uint32_t ht = (uint32_t)(4 * cap2 < 256 ? 256 : 4 * cap2);
-  b.ht_mask = ht - 1;
   for (int s = 0; s < 2; s++) {
     TRY(dalloc(h, &h->s_ht_key[s], ht));
     TRY(dalloc(h, &h->s_ht_min[s], ht));
@@ -324,20 +335,34 @@ int err_to_rc(uint32_t err) {
 
 // The build on the device.  `bs` must hold at least n records, a tag buffer
 // of a power of two >= max(n, 8192) entries and M + 1 page offsets.
-// One access batch on stream st: picks the buffer slot, waits for the flush
-// that last used it, sizes the batch hash tables to n, links the previous
-// batch's written pages, launches, and flips the slot.
-cudaError_t access_batch(bolt* h, BatchDev b, uint32_t n, cudaStream_t st) {
-  const int s = h->slot, ps = s ^ 1;
-  if (h->flush_pending[s]) {
-    cudaError_t e = cudaStreamWaitEvent(st, h->ev_flushed[s], 0);
-    if (e != cudaSuccess) return e;
-  }
+// The view of slot s of the batch buffers for a batch of n ops: the slot's
+// preparation outputs, page hash table and page buffers, table sizes for n,
+// and the previous batch's written pages (the other slot).
+BatchDev slot_view(bolt* h, BatchDev b, uint32_t n, int s) {
+  const int ps = s ^ 1;
   uint32_t ht = 256, kt = 128;
   while (ht < 4 * n) ht <<= 1;
   while (kt < 2 * n) kt <<= 1;
   b.ht_mask = ht - 1;
   b.kt_mask = kt - 1;
+  const bolt::PrepSet& p = h->s_prep[s];
+  b.skeys = p.skeys;
+  b.kt_own = p.kt_own;
+  b.leader = p.leader;
+  b.prevw = p.prevw;
+  b.lastw = p.lastw;
+  b.pair = p.pair;
+  b.rpair = p.rpair;
+  b.rows = p.rows;
+  b.hit = p.hit;
+  b.done = p.done;
+  b.pres = p.pres;
+  b.la_key = p.la_key;
+  b.la_idx = p.la_idx;
+  b.la_list = p.la_list;
+  b.la_count = p.la_count;
+  b.la_buf = p.la_buf;
+  b.la_on = 0;
   b.ht_key = h->s_ht_key[s];
   b.ht_min = h->s_ht_min[s];
   b.ht_d = h->s_ht_d[s];
@@ -349,24 +374,139 @@ cudaError_t access_batch(bolt* h, BatchDev b, uint32_t n, cudaStream_t st) {
   b.prev_ht_d = h->s_ht_d[ps];
   b.prev_dbuf = h->s_dbuf[ps];
   b.prev_ht_mask = h->slot_ht_mask[ps];
+  b.clr_ht_key = h->prev_valid ? h->s_ht_key[ps] : nullptr;
+  b.clr_ht_min = h->s_ht_min[ps];
+  b.clr_mask = h->slot_ht_mask[ps];
+  return b;
+}
+
+// The main part of a batch in the current slot, on stream st, once its
+// preparation has been enqueued (on st, or on st_prep with st waiting for it):
+// waits for the flush that last used the slot, launches, flips the slot.
+cudaError_t main_batch(bolt* h, const BatchDev& b, uint32_t n, cudaStream_t st) {
+  const int s = h->slot;
+  if (h->flush_pending[s]) {
+    cudaError_t e = cudaStreamWaitEvent(st, h->ev_flushed[s], 0);
+    if (e != cudaSuccess) return e;
+  }
   FlushCtx fc{h->st_fl, h->ev_evicted[s], h->ev_flushed[s]};
-  cudaError_t e = launch_access(h->m, b, n, h->t, st, fc);
+  cudaError_t e = launch_main(h->m, b, n, st, fc);
   if (e != cudaSuccess) return e;
   h->flush_pending[s] = true;
   h->slot_ht_mask[s] = b.ht_mask;
   h->prev_valid = true;
-  h->slot = ps;
+  h->slot = s ^ 1;
   return cudaSuccess;
+}
+
+// One access batch, preparation and main part, on stream st.
+cudaError_t access_batch(bolt* h, BatchDev b, uint32_t n, cudaStream_t st) {
+  const BatchDev v = slot_view(h, b, n, h->slot);
+  cudaError_t e = launch_prep(h->m, v, n, h->t, st);
+  if (e != cudaSuccess) return e;
+  return main_batch(h, v, n, st);
+}
+
+// ceil(n / w) batches of w ops (the last one ragged) over device arrays, in
+// order, on stream st -- the same result as one access_batch per slice.  The
+// preparation of batch j + 1 depends only on its own inputs, and its
+// lookahead only on state that batch j does not change, so both run on
+// st_prep while batch j's main part runs on st; slot s's buffers are reused
+// two batches later, after ev_pfree[s] (recorded once the main part that
+// read them is done).
+cudaError_t access_batches(bolt* h, BatchDev b, uint64_t n, uint32_t w, cudaStream_t st) {
+  const uint64_t nb = (n + w - 1) / w;
+  auto slice = [&](uint64_t j, uint32_t& cnt) {
+    BatchDev x = b;
+    const uint64_t lo = j * w;
+    cnt = (uint32_t)(n - lo < w ? n - lo : w);
+    x.ops = b.ops + lo;
+    x.keys = b.keys + lo;
+    x.vin = b.vin + lo * h->vb;
+    x.vout = b.vout + lo * h->vb;
+    x.status = b.status + lo;
+    return x;
+  };
+  if (nb == 1) {
+    uint32_t cnt = 0;
+    const BatchDev x = slice(0, cnt);
+    cudaError_t e = access_batch(h, x, cnt, st);
+    if (e == cudaSuccess) {
+      h->t += cnt;
+      h->batches++;
+    }
+    return e;
+  }
+  // the inputs are ready once the caller's earlier work on st is done
+  cudaError_t e = cudaEventRecord(h->ev_in, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st_prep, h->ev_in, 0);
+  if (e != cudaSuccess) return e;
+  const uint64_t t_start = h->t;
+  auto prep = [&](uint64_t j, int s) -> cudaError_t {
+    uint32_t cnt = 0;
+    const BatchDev x = slice(j, cnt);
+    BatchDev v = slot_view(h, x, cnt, s);
+    if (j >= 2) {
+      cudaError_t pe = cudaStreamWaitEvent(h->st_prep, h->ev_pfree[s], 0);
+      if (pe != cudaSuccess) return pe;
+    }
+    cudaError_t pe = launch_prep(h->m, v, cnt, t_start + j * w, h->st_prep);
+    if (pe == cudaSuccess && h->lookahead && j >= 1) {
+      // lookahead against batch j - 1 (its key table is in the other slot);
+      // host pages are current once the flush two batches back has landed
+      uint32_t pc = 0;
+      const BatchDev px = slice(j - 1, pc);
+      uint32_t kt = 128;
+      while (kt < 2 * pc) kt <<= 1;
+      const bolt::PrepSet& pp = h->s_prep[s ^ 1];
+      v.la_on = 1;
+      v.prev_kt_own = pp.kt_own;
+      v.prev_keys = px.keys;
+      v.prev_ops = px.ops;
+      v.prev_leader = pp.leader;
+      v.prev_lastw = pp.lastw;
+      v.prev_rpair = pp.rpair;
+      v.prev_pres = pp.pres;
+      v.prev_kt_mask = kt - 1;
+      if (h->flush_pending[s]) pe = cudaStreamWaitEvent(h->st_prep, h->ev_flushed[s], 0);
+      if (pe == cudaSuccess) pe = launch_ahead(h->m, v, cnt, h->st_prep);
+    }
+    if (pe == cudaSuccess) pe = cudaEventRecord(h->ev_prep[s], h->st_prep);
+    return pe;
+  };
+  e = prep(0, h->slot);
+  for (uint64_t j = 0; j < nb && e == cudaSuccess; j++) {
+    const int s = h->slot;
+    if (j + 1 < nb) e = prep(j + 1, s ^ 1);
+    if (e != cudaSuccess) break;
+    e = cudaStreamWaitEvent(st, h->ev_prep[s], 0);
+    if (e != cudaSuccess) break;
+    uint32_t cnt = 0;
+    const BatchDev x = slice(j, cnt);
+    BatchDev v = slot_view(h, x, cnt, s);
+    v.la_on = h->lookahead && j >= 1 ? 1u : 0u;
+    e = main_batch(h, v, cnt, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_pfree[s], st);
+    if (e == cudaSuccess) {
+      h->t += cnt;
+      h->batches++;
+    }
+  }
+  return e;
 }
 
 // Order stream st after every pending page flush and forget the previous
 // batch (a build rewrites every page).
 void drain_flushes(bolt* h, cudaStream_t st) {
-  for (int s = 0; s < 2; s++)
+  for (int s = 0; s < 2; s++) {
     if (h->flush_pending[s]) {
       cudaStreamWaitEvent(st, h->ev_flushed[s], 0);
       h->flush_pending[s] = false;
     }
+    // both page tables start empty (a batch clears its predecessor's table)
+    cudaMemsetAsync(h->s_ht_key[s], 0xff, ((uint64_t)h->b.ht_mask + 1) * 4, st);
+    cudaMemsetAsync(h->s_ht_min[s], 0xff, ((uint64_t)h->b.ht_mask + 1) * 4, st);
+  }
   h->prev_valid = false;
   h->slot = 0;
 }
@@ -500,9 +640,13 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_fl, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_prep, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
   for (int s = 0; s < 2 && e == cudaSuccess; s++) {
     e = cudaEventCreateWithFlags(&h->ev_evicted[s], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_flushed[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_prep[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pfree[s], cudaEventDisableTiming);
   }
   if (e != cudaSuccess) {
     destroy_streams(h);
@@ -561,6 +705,9 @@ int bolt_set_param(bolt_t* h, int which, double v) {
     case BOLT_PARAM_BATCH:
       if (!(v >= 1.0 && v <= (double)h->cap_batch)) return BOLT_E_ARG;
       h->batch_width = (uint32_t)v;
+      return BOLT_OK;
+    case BOLT_PARAM_LOOKAHEAD:
+      h->lookahead = v != 0.0;
       return BOLT_OK;
     case BOLT_PARAM_BATCH_CAP:
       if (!(v >= 1.0 && v <= (double)MAXB)) return BOLT_E_ARG;
@@ -661,6 +808,30 @@ int bolt_access_device(bolt_t* h, const uint8_t* d_ops, const void* d_keys, cons
   h->t += n;
   h->batches++;
   return BOLT_OK;
+}
+
+int bolt_access_device_batches(bolt_t* h, const uint8_t* d_ops, const void* d_keys,
+                               const void* d_vals_in, void* d_vals_out, uint8_t* d_status,
+                               uint64_t n, uint32_t width, void* stream) {
+  if (!h) return BOLT_E_ARG;
+  if (!h->initialized || h->poisoned) return BOLT_E_STATE;
+  if (n == 0) return BOLT_OK;
+  if (width == 0) width = h->batch_width;
+  if (width > h->cap_batch || !d_ops || !d_keys || !d_vals_in || !d_vals_out || !d_status)
+    return BOLT_E_ARG;
+  ProfScope prof_scope(h);
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
+  BatchDev b = h->b;
+  b.ops = const_cast<uint8_t*>(d_ops);
+  b.keys = static_cast<uint64_t*>(const_cast<void*>(d_keys));
+  b.vin = static_cast<uint8_t*>(const_cast<void*>(d_vals_in));
+  b.vout = static_cast<uint8_t*>(d_vals_out);
+  b.status = d_status;
+  if (h->last_st != st) {
+    if (h->last_st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+    h->last_st = st;
+  }
+  return access_batches(h, b, n, width, st) == cudaSuccess ? BOLT_OK : BOLT_E_CUDA;
 }
 
 int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* vals_in,
@@ -914,8 +1085,9 @@ uint64_t resident_estimate(const bolt_info_t& I, uint64_t cap, uint64_t trace_ca
   const uint64_t sort_cap = cap2 <= 512 ? 512 : (cap2 < 4096 ? 4096 : cap2);
   const uint64_t kt = 2 * cap2 < 128 ? 128 : 2 * cap2;
   const uint64_t ht = 4 * cap2 < 256 ? 256 : 4 * cap2;
-  b += cap * (1 + 8 + 2 * vb + 1) + sort_cap * 8 + kt * 4 + cap * 12 + cap * 16 + cap * 16 +
-       cap * 4 + 2 * cap * 8 + (2 * ((2 * cap + 255) / 256) + 2) * 4 + 16;
+  b += cap * (1 + 8 + 2 * vb + 1) + 2 * cap * 8 + (2 * ((2 * cap + 255) / 256) + 2) * 4 + 16;
+  b += 2 * (sort_cap * 8 + kt * 4 + cap * 12 + cap * 16 + cap * 16 + cap * 4 + 2 * cap + ht * 8 +
+            2 * cap * 4 + 4 + 2 * cap * I.page_bytes);
   b += 2 * (ht * 12 + 2 * cap * 4 + 4 + 2 * cap * I.page_bytes);
   b += 2 * cap * 8 + cap * vb + cap + cap * vb + cap + cap * 8 + 16 * 4 + 4;
   return b;

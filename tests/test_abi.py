@@ -66,3 +66,40 @@ def test_bad_arguments_rejected_on_host():
     for args in [(32, 8), (1 << 16, 12), (1 << 16, 0), (1 << 16, 512)]:
         with pytest.raises(B.BoltError):
             B.plan(*args)
+
+
+def test_binding_layouts_match_header(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets that a C
+    compiler gives the header's declaration, and every #define constant the
+    binding repeats has the header's value."""
+    import ctypes
+    import subprocess
+    from paper_2509_01742_b300 import bolt as B
+    structs = ["bolt_info_t", "bolt_stats_t", "bolt_profile_t", "bolt_tune_t",
+               "bolt_req_info_t", "bolt_server_stats_t"]
+    lines = ['#include <stdio.h>', '#include "bolt.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'printf("{s} %zu\\n", sizeof({s}));')
+        for name, _ in getattr(B, s)._fields_:
+            lines.append(f'printf("{s}.{name} %zu\\n", offsetof({s}, {name}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-include",
+                    "stddef.h", str(src), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([str(exe)], check=True, capture_output=True,
+                              text=True).stdout.split("\n") if line)
+    for s in structs:
+        cls = getattr(B, s)
+        assert int(got[s]) == ctypes.sizeof(cls), s
+        for name, _ in cls._fields_:
+            assert int(got[f"{s}.{name}"]) == getattr(cls, name).offset, f"{s}.{name}"
+    text = open(os.path.join(ROOT, "include", "bolt.h")).read()
+    defines = dict(re.findall(r"#define\s+(BOLT_\w+)\s+(-?\d+)", text))
+    assert defines, "no numeric #define found"
+    for name, value in defines.items():
+        if hasattr(B, name):
+            assert getattr(B, name) == int(value), name
+    assert int(defines["BOLT_PROF_CLASSES"]) == len(B.PROF_NAMES)

@@ -243,6 +243,52 @@ def test_device_batches_back_to_back_match_oracle():
     o.close(); g.close()
 
 
+@pytest.mark.parametrize("lookahead", [0, 1])
+def test_device_batches_call_matches_oracle(lookahead):
+    """bolt_access_device_batches (the next batch's preparation, and with
+    lookahead its position-map search and page reads, run ahead on an
+    internal stream) over 21 batches of width 300 with a ragged tail of 123,
+    then one plain device batch, then batches of width 1000 on a caller
+    stream: outputs and state equal the oracle's with the same batch
+    partition.  Keys repeat across consecutive batches (3000 keys), so
+    predicted bins, re-checked hits and pages rewritten by the previous batch
+    are all exercised."""
+    import torch
+    N, vb = 1 << 12, 8
+    o, g = _pair(N, vb)
+    g.set_param(B.BOLT_PARAM_LOOKAHEAD, lookahead)
+    keys, vals = W.records(3000, vb, 41)
+    assert o.init(keys, vals, 9) == 0 and g.init(keys, vals, 9) == 0
+    n1, n2, n3 = 20 * 300 + 123, 257, 3500
+    ops, k, vin = W.op_stream(3000, n1 + n2 + n3, vb, 42, get_frac=0.5, del_frac=0.1,
+                              absent_frac=0.2)
+    t_ops = torch.from_numpy(ops).cuda()
+    t_k = torch.from_numpy(k.view(np.int64)).cuda()
+    t_vin = torch.from_numpy(vin).cuda()
+    t_out = torch.zeros((len(ops), vb), dtype=torch.uint8, device="cuda")
+    t_st = torch.zeros(len(ops), dtype=torch.uint8, device="cuda")
+    a, b, c = slice(0, n1), slice(n1, n1 + n2), slice(n1 + n2, n1 + n2 + n3)
+    assert g.access_device_batches(t_ops[a], t_k[a], t_vin[a], t_out[a], t_st[a], 300) == 0
+    assert g.access_device(t_ops[b], t_k[b], t_vin[b], t_out[b], t_st[b]) == 0
+    side = torch.cuda.Stream()
+    assert g.access_device_batches(t_ops[c], t_k[c], t_vin[c], t_out[c], t_st[c], 1000,
+                                   stream=side) == 0
+    assert g.sync() == 0
+    parts = [(lo, min(n1, lo + 300)) for lo in range(0, n1, 300)] + [(n1, n1 + n2)]
+    parts += [(lo, min(n1 + n2 + n3, lo + 1000)) for lo in range(n1 + n2, n1 + n2 + n3, 1000)]
+    vo_all, so_all = [], []
+    for lo, hi in parts:
+        rc, vo, so = o.access(ops[lo:hi], k[lo:hi], vin[lo:hi])
+        assert rc == 0
+        vo_all.append(vo)
+        so_all.append(so)
+    assert np.array_equal(np.concatenate(so_all), t_st.cpu().numpy())
+    assert np.array_equal(np.concatenate(vo_all), t_out.cpu().numpy())
+    _assert_state_equal(o, g, "pipelined device batches")
+    assert g.stats()["batches"] == len(parts)
+    o.close(); g.close()
+
+
 def test_autotune_keeps_results():
     """bolt_autotune picks a tile and a batch width by measurement; the map's
     contents are unchanged (its tuning Gets only remap keys) and later builds
