@@ -251,9 +251,12 @@ BOLT_API int bolt_read_rowcounts(bolt_t* h, uint8_t* dst);
  *  10 key check: bitonic global steps    11 key check: bitonic in-tile steps
  *  12 access: written pages copied to the host (side stream)
  *  13 access: lookahead position-map search + page reads (side stream)
+ *  14 access: position-map search        15 access: distinct pages + trace
+ *  16 access: find_remove + semantics    17 access: P2C remap
+ *  18 access: PRF pairs, rows, grouping keys
  * ms[c] sums the event-timed durations of the spans[c] launches (or phases)
  * of class c; launches counts every kernel the library launched. */
-#define BOLT_PROF_CLASSES 14
+#define BOLT_PROF_CLASSES 19
 typedef struct {
   uint64_t launches;
   uint64_t spans[BOLT_PROF_CLASSES];

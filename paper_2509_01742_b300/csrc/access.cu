@@ -10,14 +10,18 @@
 //               op, last writer of each key group, by prefix-max scans
 //   k_lookup    warp per op: leaders scan their d rows of the position map
 //               (ballot over the R slots of each row); hit -> stored pair,
-//               otherwise the DUMMY pair; host bins enter a page hash table
-//   k_pages     one CTA: distinct pages in first-read order, read/write trace
-//   k_gather    warp per distinct page: zero-copy 16-byte reads of the pinned
-//               host page, ChaCha20 decryption (quad-cooperative key stream)
+//               otherwise the DUMMY pair; host bins enter a page hash table,
+//               and the position claiming a page's slot reads it (zero-copy
+//               16-byte loads of the pinned host page) and decrypts it
+//               (quad-cooperative ChaCha20 key stream) into the slot's buffer
+//   k_pages     (trace on) read/write trace, distinct pages in first-read
+//               order
 //   k_find      warp per op: find_remove of each hit (page scan by ballot, or
 //               the value store), load and position-map bookkeeping
-//   k_exec      per op: Get/Put/Delete semantics in op order per key
-//   k_evict     warp per distinct page: remaining tuples + stash items bound
+//   k_exec_evict  blocks of warps per page: write-back (below); other blocks
+//               per op: Get/Put/Delete semantics in op order per key, and the
+//               P2C decision when the remap is one round
+//   (evict)     warp per distinct page: remaining tuples + stash items bound
 //               for the page, ordered by key, dummy-padded, version + 1,
 //               encrypted, written back to the host page
 //   k_remap_*   P2C remap of every key present after the batch, in rounds of
@@ -32,6 +36,20 @@ __device__ __forceinline__ uint32_t key_hash(uint64_t k, uint32_t mask) {
   k *= 0xff51afd7ed558ccdull;
   k ^= k >> 33;
   return (uint32_t)k & mask;
+}
+
+// SMs of the current device (queried once per device)
+static int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int v = 148;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = v > 0 ? v : 148;
+  }
+  return cached[dev];
 }
 
 // per op: PRF pairs and rows, and the op's grouping key.  Equal keys share a
@@ -124,7 +142,7 @@ __global__ void __launch_bounds__(GROUP_THREADS) k_group(BatchDev b, uint32_t n)
   using G = GroupKey<K>;
   const K* sk = reinterpret_cast<const K*>(b.skeys);
   __shared__ int32_t sh[32];
-  const uint32_t per = (n + GROUP_THREADS - 1) / GROUP_THREADS;
+  const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
   const uint32_t lo = threadIdx.x * per;
   const uint32_t hi = min(n, lo + per);
   // local maxima of group-head positions and writer positions
@@ -157,17 +175,20 @@ __device__ __forceinline__ uint32_t ht_hash(uint32_t page, uint32_t mask) {
   return (page * 0x9E3779B1u) & mask;
 }
 
-__device__ __forceinline__ void ht_insert(const BatchDev& b, uint32_t page, uint32_t pos) {
+// page into the batch's page table; returns the slot if this call claimed
+// it (the caller then reads the page), NONE32 if the page was already there
+__device__ __forceinline__ uint32_t ht_insert(const BatchDev& b, uint32_t page, uint32_t pos) {
   uint32_t h = ht_hash(page, b.ht_mask);
   for (uint32_t probe = 0; probe <= b.ht_mask; probe++) {
     uint32_t old = atomicCAS(b.ht_key + h, NONE32, page);
     if (old == NONE32 || old == page) {
       atomicMin(b.ht_min + h, pos);
       b.pos_slot[pos] = h;
-      return;
+      return old == NONE32 ? h : NONE32;
     }
     h = (h + 1) & b.ht_mask;
   }
+  return NONE32;
 }
 
 // the warp scans the key's d = 4 rows, R slots each (ballot per row)
@@ -185,48 +206,6 @@ __device__ __forceinline__ uint32_t pm_search(const MapDev& m, const BatchDev& b
     if (bal && found == NONE32) found = (uint32_t)((uint64_t)rr[j] * m.R + (__ffs(bal) - 1));
   }
   return found;
-}
-
-// warp per op
-__global__ void k_lookup(MapDev m, BatchDev b, uint32_t n) {
-  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  uint32_t found = NONE32;
-  if (b.leader[i] == i) {
-    const uint64_t key = b.keys[i];
-    bool scan = true;
-    if (b.la_on && b.done[i]) {
-      // searched ahead: a miss stands (the key is not in the previous batch,
-      // so nothing inserted it since); a hit is re-checked, since the search
-      // may have seen a slot that the previous batch was re-using
-      const uint32_t hs = b.hit[i];
-      if (hs == NONE32) {
-        scan = false;
-      } else if (meta_loc(m.pm_meta[hs]) != LOC_EMPTY && m.pm_key[hs] == key) {
-        found = hs;
-        scan = false;
-      }
-    }
-    if (scan) found = pm_search(m, b, i, key, lane);
-  }
-  if (lane == 0) {
-    b.hit[i] = found;
-    if (found != NONE32) b.pair[i] = m.pm_bins[found];
-  }
-  __syncwarp();
-  if (lane < 2) {
-    const uint64_t pr = b.pair[i];
-    const uint32_t p = lane == 0 ? (uint32_t)pr : (uint32_t)(pr >> 32);
-    const uint32_t pos = 2 * i + lane;
-    if (p >= m.K) {
-      const uint32_t q = (uint32_t)(p - m.K);
-      b.pos_page[pos] = q;
-      ht_insert(b, q, pos);
-    } else {
-      b.pos_page[pos] = NONE32;
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -335,6 +314,17 @@ __global__ void k_ahead_lookup(MapDev m, BatchDev b, uint32_t n) {
 constexpr uint32_t LINK_WARPS = 192;
 constexpr uint32_t COPY_BLOCK = 128;
 constexpr uint32_t LINK_BLOCKS = LINK_WARPS * 32 / COPY_BLOCK;
+// The write-back of batch k has until batch k + 2 starts and runs beside
+// batch k + 1, whose random HBM accesses and page reads it slows in
+// proportion to its writes in flight: as few warps as keep it inside about
+// one batch time.  A warp writes a page per ~1.2 us, a 4096-op batch (~6.5 k
+// host pages at N = 2^28) takes ~220 us, so about one warp per 160 read
+// positions (2 per op), between 16 and 192 warps.
+__host__ __device__ __forceinline__ uint32_t flush_blocks(uint32_t n) {
+  uint32_t w = 2 * n / 160;
+  w = w < 16 ? 16 : (w > 192 ? 192 : w);
+  return (w * 32 + COPY_BLOCK - 1) / COPY_BLOCK;
+}
 
 // the pages queued ahead, one 512-byte chunk per warp step: host read +
 // decryption into la_buf.  Pages the previous batch rewrites may be read torn
@@ -359,9 +349,11 @@ __global__ void __launch_bounds__(COPY_BLOCK) k_ahead_gather(MapDev m, BatchDev 
   }
 }
 
-// Distinct pages in first-read order and the host-access trace, in three
-// passes over the 2n read positions: per-block counts of valid reads and of
-// first reads, one scan of the block counts, then ranks and outputs.
+// The host-access trace (parity runs): every read position's page in
+// position order, then each distinct page once, in first-read order, as a
+// write.  Three passes over the 2n read positions: per-block counts of valid
+// reads and of first reads, one scan of the block counts, then ranks and
+// outputs.
 constexpr int PAGES_BLOCK = 256;
 
 __device__ __forceinline__ void pos_flags(const BatchDev& b, uint32_t p, uint32_t np, bool& valid,
@@ -419,7 +411,6 @@ __global__ void __launch_bounds__(1024) k_pages_scan(MapDev m, BatchDev b, uint3
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    *b.dcount = carry_f;
     const uint64_t tbase = m.trace_on ? *m.trace_len : 0;
     b.trace_base[0] = tbase;
     b.trace_base[1] = carry_v;
@@ -441,8 +432,6 @@ __global__ void __launch_bounds__(PAGES_BLOCK) k_pages_emit(MapDev m, BatchDev b
   const uint64_t tbase = b.trace_base[0], tot_valid = b.trace_base[1];
   if (m.trace_on && tbase + rv < m.trace_cap) m.trace[tbase + rv] = q;
   if (first) {
-    b.dpage[d] = q;
-    b.ht_d[slot] = d;
     const uint64_t w = tbase + tot_valid + d;
     if (m.trace_on && w < m.trace_cap) m.trace[w] = q | 0x80000000u;
   }
@@ -475,7 +464,6 @@ __global__ void __launch_bounds__(1024) k_pages_small(MapDev m, BatchDev b, uint
   if (threadIdx.x == 0) {
     const uint64_t tbase = m.trace_on ? *m.trace_len : 0;
     s_tbase = tbase;
-    *b.dcount = tf;
     b.trace_base[0] = tbase;
     b.trace_base[1] = tv;
     if (m.trace_on) *m.trace_len = tbase + tv + tf;
@@ -488,8 +476,6 @@ __global__ void __launch_bounds__(1024) k_pages_small(MapDev m, BatchDev b, uint
     if (m.trace_on && tbase + rv < m.trace_cap) m.trace[tbase + rv] = qs[k];
     rv++;
     if ((flags >> (2 * k + 1)) & 1u) {
-      b.dpage[d] = qs[k];
-      b.ht_d[slots[k]] = d;
       const uint64_t w = tbase + tv + d;
       if (m.trace_on && w < m.trace_cap) m.trace[w] = qs[k] | 0x80000000u;
       d++;
@@ -497,84 +483,170 @@ __global__ void __launch_bounds__(1024) k_pages_small(MapDev m, BatchDev b, uint
   }
 }
 
-// page q in the previous batch's write set? -> its distinct index, else NONE
+// page q in the previous batch's write set? -> its slot there, else NONE
 __device__ __forceinline__ uint32_t prev_written(const BatchDev& b, uint32_t q) {
   if (!b.prev_valid) return NONE32;
   uint32_t h = ht_hash(q, b.prev_ht_mask);
   for (uint32_t probe = 0; probe <= b.prev_ht_mask; probe++) {
     const uint32_t k = b.prev_ht_key[h];
-    if (k == q) return b.prev_ht_d[h];
+    if (k == q) return h;
     if (k == NONE32) return NONE32;
     h = (h + 1) & b.prev_ht_mask;
   }
   return NONE32;
 }
 
-// warp per distinct page: read the page (host, or the previous batch's
-// not-yet-flushed ciphertext) and decrypt it
-__global__ void k_gather(MapDev m, BatchDev b) {
-  const uint32_t d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (d >= *b.dcount) return;
-  const uint64_t q = b.dpage[d];
-  uint8_t* dst = b.dbuf + (uint64_t)d * m.page_bytes;
-  const uint8_t* host = m.pages + q * m.page_bytes;
-  uint32_t pd = NONE32;
-  uint4 first = make_uint4(0, 0, 0, 0);
-  if (b.la_on) {
-    // a page the previous batch wrote comes from its ciphertext copy; else a
-    // page read ahead is copied; else it is read from the host now
-    pd = prev_written(b, (uint32_t)q);
-    if (pd == NONE32) {
-      const uint32_t e = la_find(b, (uint32_t)q);
-      if (e != NONE32) {
-        const uint4* src = reinterpret_cast<const uint4*>(b.la_buf + (uint64_t)e * m.page_bytes);
-        for (uint32_t c = lane; c < m.page_bytes / 16; c += 32)
-          reinterpret_cast<uint4*>(dst)[c] = src[c];
-        if (lane == 0) b.removed[d] = 0;
-        return;
-      }
-      if (16 * lane < m.page_bytes) first = *reinterpret_cast<const uint4*>(host + 16 * lane);
-    }
-  } else {
-    // the first host read is issued before the previous-batch lookup
-    // resolves; a page the previous batch wrote (rare) is taken from its
-    // ciphertext copy
-    if (16 * lane < m.page_bytes) first = *reinterpret_cast<const uint4*>(host + 16 * lane);
-    pd = prev_written(b, (uint32_t)q);
-  }
-  const uint64_t v = m.version[q];
+// Where a claimed page comes from: the host page (ciphertext), the previous
+// batch's not-yet-flushed ciphertext, or a plaintext read ahead.
+enum : int { SRC_NONE = 0, SRC_HOST = 1, SRC_PREV = 2, SRC_PLAIN = 3 };
+
+// the rest of a page whose first 16 bytes per lane are in `first`: decrypt
+// (unless already plaintext) into the slot's buffer
+__device__ __forceinline__ void page_in(const MapDev& m, const BatchDev& b, uint32_t slot,
+                                        uint64_t q, int kind, const uint8_t* src, uint4 first,
+                                        int lane) {
+  uint8_t* dst = b.dbuf + (uint64_t)slot * m.page_bytes;
+  const uint64_t v = kind == SRC_PLAIN ? 0 : m.version[q];
   for (uint32_t c = 0; c < m.page_bytes; c += 512) {
     const uint32_t off = c + 16 * lane;
     uint4 x = first;
-    if (pd != NONE32 && off < m.page_bytes)
-      x = *reinterpret_cast<const uint4*>(b.prev_dbuf + (uint64_t)pd * m.page_bytes + off);
-    else if (c > 0 && off < m.page_bytes)
-      x = *reinterpret_cast<const uint4*>(host + off);
-    const uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)v,
-                                 (uint32_t)(v >> 32));
-    if (off < m.page_bytes) {
+    if (c > 0 && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
+    if (kind != SRC_PLAIN) {
+      const uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)v,
+                                   (uint32_t)(v >> 32));
       x.x ^= ks.x; x.y ^= ks.y; x.z ^= ks.z; x.w ^= ks.w;
-      *reinterpret_cast<uint4*>(dst + off) = x;
     }
+    if (off < m.page_bytes) *reinterpret_cast<uint4*>(dst + off) = x;
   }
-  if (lane == 0) b.removed[d] = 0;
+  if (lane == 0) b.removed[slot] = 0;
 }
 
-// the written pages, one 512-byte chunk per warp step: copy the ciphertexts
-// from dbuf to the host pages (few warps: runs beside the next batch)
+// warp per op (Alg. 1 lines 2-5 over a batch): leaders search the position
+// map -- a hit reads the stored pair, a miss and every non-leader the DUMMY
+// pair -- and the two bins' host pages enter the batch's page table.  The
+// position that claims a page's slot reads the page at once into the slot's
+// buffer: from the previous batch's ciphertext if that batch wrote it
+// (its host copy may still be in flight), from the plaintext read ahead
+// (lookahead), else from the host.  With lookahead, a leader searched ahead
+// keeps a miss and re-checks a hit (a slot the previous batch was re-using
+// could have looked like a match), the others search now.
+__device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, uint32_t i,
+                                          int lane) {
+  uint32_t found = NONE32;
+  if (b.leader[i] == i) {
+    const uint64_t key = b.keys[i];
+    bool scan = true;
+    if (b.la_on && b.done[i]) {
+      const uint32_t hs = b.hit[i];
+      if (hs == NONE32) {
+        scan = false;
+      } else if (meta_loc(m.pm_meta[hs]) != LOC_EMPTY && m.pm_key[hs] == key) {
+        found = hs;
+        scan = false;
+      }
+    }
+    if (scan) found = pm_search(m, b, i, key, lane);
+  }
+  if (lane == 0) {
+    b.hit[i] = found;
+    if (found != NONE32) b.pair[i] = m.pm_bins[found];
+  }
+  __syncwarp();
+  uint32_t q = NONE32, claim = NONE32;
+  if (lane < 2) {
+    const uint64_t pr = b.pair[i];
+    const uint32_t p = lane == 0 ? (uint32_t)pr : (uint32_t)(pr >> 32);
+    const uint32_t pos = 2 * i + lane;
+    if (p >= m.K) {
+      q = (uint32_t)(p - m.K);
+      b.pos_page[pos] = q;
+      claim = ht_insert(b, q, pos);
+      if (claim != NONE32) {
+        const uint32_t e = atomicAdd(b.dcount, 1u);
+        b.dslot[e] = claim;
+        b.dpage[e] = q;
+      }
+    } else {
+      b.pos_page[pos] = NONE32;
+    }
+  }
+  uint32_t sl[2], qs[2];
+  int kind[2];
+  const uint8_t* src[2];
+  uint4 x[2];
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    sl[k] = __shfl_sync(0xffffffffu, claim, k);
+    qs[k] = __shfl_sync(0xffffffffu, q, k);
+    kind[k] = sl[k] == NONE32 ? SRC_NONE : SRC_HOST;
+    src[k] = m.pages + (uint64_t)qs[k] * m.page_bytes;
+    if (kind[k] != SRC_NONE && b.la_on) {
+      const uint32_t pd = prev_written(b, qs[k]);
+      if (pd != NONE32) {
+        kind[k] = SRC_PREV;
+        src[k] = b.prev_dbuf + (uint64_t)pd * m.page_bytes;
+      } else {
+        const uint32_t e = la_find(b, qs[k]);
+        if (e != NONE32) {
+          kind[k] = SRC_PLAIN;
+          src[k] = b.la_buf + (uint64_t)e * m.page_bytes;
+        }
+      }
+    }
+  }
+  // first 16 bytes per lane of both pages in flight before either is used;
+  // without lookahead the host reads are issued before the previous-batch
+  // check resolves (a page the previous batch wrote is rare)
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    x[k] = make_uint4(0, 0, 0, 0);
+    if (kind[k] != SRC_NONE && 16 * lane < m.page_bytes)
+      x[k] = *reinterpret_cast<const uint4*>(src[k] + 16 * lane);
+  }
+  if (!b.la_on) {
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      if (kind[k] == SRC_NONE) continue;
+      const uint32_t pd = prev_written(b, qs[k]);
+      if (pd != NONE32) {
+        kind[k] = SRC_PREV;
+        src[k] = b.prev_dbuf + (uint64_t)pd * m.page_bytes;
+        if (16 * lane < m.page_bytes) x[k] = *reinterpret_cast<const uint4*>(src[k] + 16 * lane);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 2; k++)
+    if (kind[k] != SRC_NONE) page_in(m, b, sl[k], qs[k], kind[k], src[k], x[k], lane);
+}
+
+// ops over at most LOOKUP_BLOCKS_PER_SM blocks per SM: a warp waiting on host
+// reads holds its registers, and the next batch's preparation (one-CTA
+// kernels on another stream) must still find room beside it
+constexpr uint32_t LOOKUP_BLOCKS_PER_SM = 2;
+
+__global__ void __launch_bounds__(256) k_lookup(MapDev m, BatchDev b, uint32_t n) {
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw)
+    lookup_op(m, b, i, lane);
+}
+
+// the written pages (the batch's page list), one 512-byte chunk per warp
+// step: copy the ciphertexts from dbuf to the host pages (few warps: runs
+// beside the next batch)
 __global__ void __launch_bounds__(COPY_BLOCK) k_flush(MapDev m, BatchDev b) {
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t nch = (m.page_bytes + 511) / 512;
   const uint32_t items = *b.dcount * nch;
   for (uint32_t it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nw) {
-    const uint32_t off = (it % nch) * 512 + 16 * lane;
-    if (off < m.page_bytes) {
-      const uint64_t q = b.dpage[it / nch];
+    const uint32_t e = it / nch, off = (it % nch) * 512 + 16 * lane;
+    const uint32_t slot = b.dslot[e];
+    const uint64_t q = b.dpage[e];
+    if (off < m.page_bytes)
       *reinterpret_cast<uint4*>(m.pages + q * m.page_bytes + off) =
-          *reinterpret_cast<const uint4*>(b.dbuf + (uint64_t)(it / nch) * m.page_bytes + off);
-    }
+          *reinterpret_cast<const uint4*>(b.dbuf + (uint64_t)slot * m.page_bytes + off);
   }
 }
 
@@ -609,7 +681,7 @@ __global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
   const uint32_t nw = m.vb / 8;
   if (meta_loc(meta) == LOC_HOST) {
     const uint32_t pos = 2 * i + which;
-    const uint32_t d = b.pos_page[pos] == NONE32 ? NONE32 : b.ht_d[b.pos_slot[pos]];
+    const uint32_t d = b.pos_page[pos] == NONE32 ? NONE32 : b.pos_slot[pos];
     if (d == NONE32) {
       if (lane == 0) set_err(m, ERR_NOTFOUND);
       return;
@@ -651,9 +723,20 @@ __global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
 }
 
 // thread per op: Get/Put/Delete semantics (Alg. 1 line 12)
-__global__ void k_exec(MapDev m, BatchDev b, uint32_t n) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+// P2C decision for leader i on the round-start loads (Alg. 1 lines 13-14):
+// the less loaded of its REMAP pair, and for a new key the position-map row
+__device__ __forceinline__ void decide_op(const MapDev& m, const BatchDev& b, uint32_t i) {
+  const uint64_t pr = b.rpair[i];
+  const uint32_t p1 = (uint32_t)pr, p2 = (uint32_t)(pr >> 32);
+  b.rdest[i] = byte_get(m.load, p1) <= byte_get(m.load, p2) ? p1 : p2;
+  if (b.hit[i] == NONE32) {
+    const uint4 rows = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
+    const uint32_t rr[4] = {rows.x, rows.y, rows.z, rows.w};
+    b.rrow[i] = pick_row(m, rr);
+  }
+}
+
+__device__ __forceinline__ void exec_op(const MapDev& m, const BatchDev& b, uint32_t i) {
   const uint32_t nw = m.vb / 8;
   const uint32_t w = b.prevw[i];
   bool present;
@@ -688,15 +771,16 @@ __global__ void k_exec(MapDev m, BatchDev b, uint32_t n) {
   }
 }
 
-// warp per distinct page: write-back with eviction (Alg. 1 line 10)
-__global__ void k_evict(MapDev m, BatchDev b, uint32_t warps_per_block) {
-  extern __shared__ __align__(16) uint8_t sbuf[];
+// warp per page of the batch: write-back with eviction (Alg. 1 line 10)
+__device__ __forceinline__ void evict_page(const MapDev& m, const BatchDev& b, uint32_t block,
+                                           uint8_t* sbuf) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t d = blockIdx.x * warps_per_block + wid;
-  if (d >= *b.dcount) return;
+  const uint32_t e = block * (blockDim.x >> 5) + wid;
+  if (e >= *b.dcount) return;
   uint8_t* plain = sbuf + (size_t)wid * (m.page_bytes + 32 * 16);
   ulonglong2* items = reinterpret_cast<ulonglong2*>(plain + m.page_bytes);
-  const uint64_t q = b.dpage[d];
+  const uint32_t d = b.dslot[e];
+  const uint64_t q = b.dpage[e];
   const uint8_t* old = b.dbuf + (uint64_t)d * m.page_bytes;
   const uint64_t bitmap = *reinterpret_cast<const uint64_t*>(old);
   const uint64_t removed = b.removed[d];
@@ -761,18 +845,32 @@ __global__ void k_evict(MapDev m, BatchDev b, uint32_t warps_per_block) {
   }
 }
 
+// The first blocks run the ops' semantics (thread per op) and, when the
+// batch's remap is one round, the leaders' P2C decisions; the last
+// evict_blocks write the pages back (warp per page).  Exec and the decisions
+// need only find_remove's results, and eviction changes no bin load or row
+// count, so the two run side by side.
+constexpr uint32_t EVICT_WARPS_PER_BLOCK = 4;
+
+__global__ void __launch_bounds__(EVICT_WARPS_PER_BLOCK * 32)
+    k_exec_evict(MapDev m, BatchDev b, uint32_t n, uint32_t evict_blocks, int decide) {
+  extern __shared__ __align__(16) uint8_t sbuf[];
+  const uint32_t exec_blocks = gridDim.x - evict_blocks;
+  if (blockIdx.x >= exec_blocks) {
+    evict_page(m, b, blockIdx.x - exec_blocks, sbuf);
+    return;
+  }
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  exec_op(m, b, i);
+  if (decide && b.leader[i] == i && b.fpres[i]) decide_op(m, b, i);
+}
+
 // P2C remap, decide on round-start loads (Alg. 1 lines 13-14)
 __global__ void k_remap_decide(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
   const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= hi || b.leader[i] != i || !b.fpres[i]) return;
-  const uint64_t pr = b.rpair[i];
-  const uint32_t p1 = (uint32_t)pr, p2 = (uint32_t)(pr >> 32);
-  b.rdest[i] = byte_get(m.load, p1) <= byte_get(m.load, p2) ? p1 : p2;
-  if (b.hit[i] == NONE32) {
-    const uint4 rows = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
-    const uint32_t rr[4] = {rows.x, rows.y, rows.z, rows.w};
-    b.rrow[i] = pick_row(m, rr);
-  }
+  decide_op(m, b, i);
 }
 
 // place leader i in its new bin: a value-store slot from the ring, the
@@ -998,21 +1096,24 @@ cudaError_t launch_prep(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t
   uint32_t n_sort = 512;
   while (n_sort < n) n_sort <<= 1;
   if (n_sort > 512 && n_sort < 4096) n_sort = 4096;
-  k_clear_keys<<<32, 256, 0, st>>>(b, n);
   const int keys32 = n_sort <= 4096;
-  k_stage<<<(3 * n_sort + 255) / 256, 256, 0, st>>>(m, b, n, n_sort, t0, keys32);
-  count_launch(2);
+  {
+    ProfSpan ps(P_STAGE, st);
+    k_clear_keys<<<32, 256, 0, st>>>(b, n);
+    k_stage<<<(3 * n_sort + 255) / 256, 256, 0, st>>>(m, b, n, n_sort, t0, keys32);
+    count_launch(2);
+  }
   cudaError_t e;
   {
     ProfSpan ps(P_GROUP, st);
     if (keys32) {
       e = sort_batch_keys32(reinterpret_cast<uint32_t*>(b.skeys), n_sort, st);
       if (e != cudaSuccess) return e;
-      k_group<uint32_t><<<1, GROUP_THREADS, 0, st>>>(b, n);
+      k_group<uint32_t><<<1, n <= 8192 ? 256 : GROUP_THREADS, 0, st>>>(b, n);
     } else {
       e = sort_batch_keys(b.skeys, n_sort, st);
       if (e != cudaSuccess) return e;
-      k_group<uint64_t><<<1, GROUP_THREADS, 0, st>>>(b, n);
+      k_group<uint64_t><<<1, n <= 8192 ? 256 : GROUP_THREADS, 0, st>>>(b, n);
     }
     count_launch();
   }
@@ -1038,9 +1139,17 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
   cudaError_t e;
   ProfSpan whole(P_ACCESS, st);
   const uint32_t warp_blocks = (n * 32 + 255) / 256;
-  k_lookup<<<warp_blocks, 256, 0, st>>>(m, b, n);
-  count_launch();
+  e = cudaMemsetAsync(b.dcount, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
   {
+    // position-map search fused with the page reads
+    ProfSpan ps(P_GATHER, st);
+    const uint32_t lb = LOOKUP_BLOCKS_PER_SM * (uint32_t)num_sms();
+    k_lookup<<<warp_blocks < lb ? warp_blocks : lb, 256, 0, st>>>(m, b, n);
+    count_launch();
+  }
+  if (m.trace_on) {
+    ProfSpan ps(P_PAGES, st);
     const uint32_t np = 2 * n;
     if (np <= PAGES_SMALL_MAX) {
       k_pages_small<<<1, 1024, 0, st>>>(m, b, np);
@@ -1053,24 +1162,30 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
       count_launch(3);
     }
   }
-  const uint32_t dmax = 2 * n;  // distinct pages are at most two per op
   {
-    ProfSpan ps(P_GATHER, st);
-    k_gather<<<(dmax * 32 + 255) / 256, 256, 0, st>>>(m, b);
+    ProfSpan ps(P_FINDEXEC, st);
+    k_find<<<warp_blocks, 256, 0, st>>>(m, b, n);
     count_launch();
   }
-  k_find<<<warp_blocks, 256, 0, st>>>(m, b, n);
-  k_exec<<<(n + 255) / 256, 256, 0, st>>>(m, b, n);
-  count_launch(2);
-  uint32_t wpb = 4;
-  size_t smem = (size_t)wpb * (m.page_bytes + 32 * 16);
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_evict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  // P2C remap: one round -> the decisions run with exec, then one apply
+  // launch; many rounds on a small map -> all rounds in one CTA on
+  // shared-memory counts; otherwise a decide and an apply launch per round
+  const uint64_t rounds = (n + m.Wr - 1) / m.Wr;
+  const bool smem_remap = rounds > 1 && m.B <= REMAP_SMEM_MAX_BINS && m.rows <= REMAP_SMEM_MAX_ROWS;
+  const int fused_decide = rounds == 1 ? 1 : 0;
   {
     ProfSpan ps(P_EVICT, st);
-    k_evict<<<(dmax + wpb - 1) / wpb, wpb * 32, smem, st>>>(m, b, wpb);
+    const uint32_t wpb = EVICT_WARPS_PER_BLOCK;
+    const size_t smem = (size_t)wpb * (m.page_bytes + 32 * 16);
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(k_exec_evict, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    const uint32_t evict_blocks = (2 * n + wpb - 1) / wpb;
+    const uint32_t exec_blocks = (n + wpb * 32 - 1) / (wpb * 32);
+    k_exec_evict<<<evict_blocks + exec_blocks, wpb * 32, smem, st>>>(m, b, n, evict_blocks,
+                                                                     fused_decide);
     count_launch();
   }
   // the host write-back overlaps the rest of this batch and the next one
@@ -1078,15 +1193,16 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
   cudaStreamWaitEvent(fc.flush_st, fc.ev_evicted, 0);
   {
     ProfSpan ps(P_FLUSH, fc.flush_st);
-    k_flush<<<LINK_BLOCKS, COPY_BLOCK, 0, fc.flush_st>>>(m, b);
+    k_flush<<<flush_blocks(n), COPY_BLOCK, 0, fc.flush_st>>>(m, b);
     count_launch();
   }
   cudaEventRecord(fc.ev_flushed, fc.flush_st);
-  // P2C remap: one round -> a decide and an apply launch; many rounds on a
-  // small map -> all rounds in one CTA on shared-memory counts
-  const uint64_t rounds = (n + m.Wr - 1) / m.Wr;
+  ProfSpan prs(P_REMAP, st);
   const size_t rsmem = ((m.B + 3) / 4 + (m.rows + 3) / 4) * 4;
-  if (rounds > 1 && m.B <= REMAP_SMEM_MAX_BINS && m.rows <= REMAP_SMEM_MAX_ROWS) {
+  if (fused_decide) {
+    k_remap_apply<<<(n + 255) / 256, 256, 0, st>>>(m, b, 0, n);
+    count_launch();
+  } else if (smem_remap) {
     const bool reg = n <= REMAP_REG_OPS * 1024;
     if (rsmem > 48 * 1024) {
       e = cudaFuncSetAttribute(reg ? (const void*)k_remap_smem_reg : (const void*)k_remap_smem,

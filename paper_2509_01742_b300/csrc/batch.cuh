@@ -28,19 +28,21 @@ struct BatchDev {
   uint32_t* pos_slot;  // [2 cap] hash-table slot of that page
   uint32_t* block_cnt; // [2 * blocks] per-block (valid, first) read counts, then offsets
   unsigned long long* trace_base;  // [2] trace offset of the batch, its read count
-  uint32_t* ht_key;    // [ht_mask + 1] page hash table
+  uint32_t* ht_key;    // [ht_mask + 1] page hash table: host page, or NONE
   uint32_t* ht_min;    // [ht_mask + 1] first read position of the page
-  uint32_t* ht_d;      // [ht_mask + 1] distinct-page index
   uint32_t ht_mask, pad0;
-  uint32_t* dpage;     // [2 cap] distinct pages in first-read order
+  uint8_t* dbuf;       // [(ht_mask + 1) * page_bytes] per page-table slot: the
+                       // decrypted page, then the ciphertext written back
+                       // (flushed to the host later)
+  uint64_t* removed;   // [ht_mask + 1] page slots taken out by find_remove
+  uint32_t* dslot;     // [2 cap] page-table slots holding a page, claim order
+  uint32_t* dpage;     // [2 cap] their pages (the write-back reads these: the
+                       // table itself is cleared by the next batch)
   uint32_t* dcount;    // [1]
-  uint8_t* dbuf;       // [2 cap * page_bytes] decrypted pages, then the
-                       // ciphertexts written back (flushed to the host later)
-  uint64_t* removed;   // [2 cap] slots taken out by find_remove
   // the previous batch's written pages, until its flush has landed: a page it
-  // wrote is read from prev_dbuf (ciphertext) instead of the host
+  // wrote is read from prev_dbuf (ciphertext, at its slot in prev_ht_key)
+  // instead of the host
   const uint32_t* prev_ht_key;
-  const uint32_t* prev_ht_d;
   const uint8_t* prev_dbuf;
   uint32_t prev_ht_mask, prev_valid;
   // the previous batch's page table, cleared by this batch once read (the

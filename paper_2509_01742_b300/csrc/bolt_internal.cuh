@@ -301,7 +301,12 @@ enum ProfClass : int {
   P_KSORT_TILE = 11,    // key-uniqueness check: bitonic in-tile steps
   P_FLUSH = 12,         // access: written pages copied to the host
   P_AHEAD = 13,         // access: lookahead search + page reads (side stream)
-  P_NCLASS = 14
+  P_LOOKUP = 14,        // access: position-map search
+  P_PAGES = 15,         // access: distinct pages, trace
+  P_FINDEXEC = 16,      // access: find_remove + Get/Put/Delete semantics
+  P_REMAP = 17,         // access: P2C remap
+  P_STAGE = 18,         // access: PRF pairs, rows, grouping keys
+  P_NCLASS = 19
 };
 
 struct Prof {

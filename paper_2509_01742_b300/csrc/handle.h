@@ -44,6 +44,18 @@ struct bolt {
   uint8_t* h_vout = nullptr;
   uint8_t* h_status = nullptr;
   uint32_t* h_err = nullptr;
+  // bolt_access moves chunks of ops through two alternating sets of pinned
+  // staging (set 0 is h_ops ... h_status) and device I/O buffers (set 0 is
+  // b.ops ... b.status), so that one chunk's host copies overlap another's
+  // batches
+  struct IoSet {
+    uint8_t* ops = nullptr;
+    uint64_t* keys = nullptr;
+    uint8_t* vin = nullptr;
+    uint8_t* vout = nullptr;
+    uint8_t* status = nullptr;
+  } h_io[2], d_io2;
+  cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_d2h[2] = {nullptr, nullptr};
   uint32_t* d_kdf = nullptr;
   uint32_t* d_flag = nullptr;
 
@@ -63,10 +75,10 @@ struct bolt {
   uint32_t slot_ht_mask[2] = {0, 0};
   uint32_t* s_ht_key[2] = {nullptr, nullptr};
   uint32_t* s_ht_min[2] = {nullptr, nullptr};
-  uint32_t* s_ht_d[2] = {nullptr, nullptr};
+  uint8_t* s_dbuf[2] = {nullptr, nullptr};
+  uint32_t* s_dslot[2] = {nullptr, nullptr};
   uint32_t* s_dpage[2] = {nullptr, nullptr};
   uint32_t* s_dcount[2] = {nullptr, nullptr};
-  uint8_t* s_dbuf[2] = {nullptr, nullptr};
   // per-slot outputs of a batch's preparation (grouping, PRF pairs, rows)
   // and lookahead (position-map hits, pages read ahead), so that the next
   // batch's preparation and lookahead can run on st_prep while this batch's

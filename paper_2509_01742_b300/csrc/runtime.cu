@@ -120,7 +120,7 @@ void free_state(bolt* h) {
   h->b = BatchDev{};
   for (int s = 0; s < 2; s++) {
     h->flush_pending[s] = false;
-    h->s_ht_key[s] = h->s_ht_min[s] = h->s_ht_d[s] = h->s_dpage[s] = h->s_dcount[s] = nullptr;
+    h->s_ht_key[s] = h->s_ht_min[s] = h->s_dslot[s] = h->s_dpage[s] = h->s_dcount[s] = nullptr;
     h->s_dbuf[s] = nullptr;
   }
   h->prev_valid = false;
@@ -133,7 +133,8 @@ void free_state(bolt* h) {
 void destroy_streams(bolt* h) {
   for (cudaEvent_t* ev : {&h->ev_fork, &h->ev_join, &h->ev_evicted[0], &h->ev_evicted[1],
                           &h->ev_flushed[0], &h->ev_flushed[1], &h->ev_in, &h->ev_prep[0],
-                          &h->ev_prep[1], &h->ev_pfree[0], &h->ev_pfree[1]})
+                          &h->ev_prep[1], &h->ev_pfree[0], &h->ev_pfree[1], &h->ev_h2d[0],
+                          &h->ev_h2d[1], &h->ev_d2h[0], &h->ev_d2h[1]})
     if (*ev) {
       cudaEventDestroy(*ev);
       *ev = nullptr;
@@ -205,6 +206,11 @@ int alloc_state(bolt* h) {
   TRY(dalloc(h, &b.vin, cap * vb));
   TRY(dalloc(h, &b.vout, cap * vb));
   TRY(dalloc(h, &b.status, cap));
+  TRY(dalloc(h, &h->d_io2.ops, cap));
+  TRY(dalloc(h, &h->d_io2.keys, cap));
+  TRY(dalloc(h, &h->d_io2.vin, cap * vb));
+  TRY(dalloc(h, &h->d_io2.vout, cap * vb));
+  TRY(dalloc(h, &h->d_io2.status, cap));
   b.kt_mask = (uint32_t)(2 * cap2 < 128 ? 127 : 2 * cap2 - 1);
   const uint32_t ht = (uint32_t)(4 * cap2 < 256 ? 256 : 4 * cap2);
   b.ht_mask = ht - 1;
@@ -234,12 +240,12 @@ int alloc_state(bolt* h) {
   for (int s = 0; s < 2; s++) {
     TRY(dalloc(h, &h->s_ht_key[s], ht));
     TRY(dalloc(h, &h->s_ht_min[s], ht));
-    TRY(dalloc(h, &h->s_ht_d[s], ht));
+    TRY(dalloc(h, &h->s_dbuf[s], (uint64_t)ht * I.page_bytes));
+    TRY(dalloc(h, &h->s_dslot[s], 2 * cap));
     TRY(dalloc(h, &h->s_dpage[s], 2 * cap));
     TRY(dalloc(h, &h->s_dcount[s], 1));
-    TRY(dalloc(h, &h->s_dbuf[s], 2 * cap * I.page_bytes));
   }
-  TRY(dalloc(h, &b.removed, 2 * cap));
+  TRY(dalloc(h, &b.removed, ht));
   TRY(dalloc(h, &b.init_val, cap * vb));
   TRY(dalloc(h, &b.init_present, cap));
   TRY(dalloc(h, &b.rval, cap * vb));
@@ -365,13 +371,12 @@ BatchDev slot_view(bolt* h, BatchDev b, uint32_t n, int s) {
   b.la_on = 0;
   b.ht_key = h->s_ht_key[s];
   b.ht_min = h->s_ht_min[s];
-  b.ht_d = h->s_ht_d[s];
+  b.dbuf = h->s_dbuf[s];
+  b.dslot = h->s_dslot[s];
   b.dpage = h->s_dpage[s];
   b.dcount = h->s_dcount[s];
-  b.dbuf = h->s_dbuf[s];
   b.prev_valid = h->prev_valid ? 1u : 0u;
   b.prev_ht_key = h->s_ht_key[ps];
-  b.prev_ht_d = h->s_ht_d[ps];
   b.prev_dbuf = h->s_dbuf[ps];
   b.prev_ht_mask = h->slot_ht_mask[ps];
   b.clr_ht_key = h->prev_valid ? h->s_ht_key[ps] : nullptr;
@@ -643,6 +648,10 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_prep, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
   for (int s = 0; s < 2 && e == cudaSuccess; s++) {
+    e = cudaEventCreateWithFlags(&h->ev_h2d[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_d2h[s], cudaEventDisableTiming);
+  }
+  for (int s = 0; s < 2 && e == cudaSuccess; s++) {
     e = cudaEventCreateWithFlags(&h->ev_evicted[s], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_flushed[s], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_prep[s], cudaEventDisableTiming);
@@ -654,18 +663,27 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
     return BOLT_E_CUDA;
   }
   void* p = nullptr;
-  e = cudaHostAlloc(&p, MAXB * (1 + 8 + 2 * (uint64_t)val_bytes + 1) + 64, cudaHostAllocDefault);
+  const uint64_t set_bytes = MAXB * (1 + 8 + 2 * (uint64_t)val_bytes + 1);
+  e = cudaHostAlloc(&p, 2 * set_bytes + 64, cudaHostAllocDefault);
   if (e != cudaSuccess) {
     destroy_streams(h);
     delete h;
     return BOLT_E_NOMEM;
   }
   uint8_t* q = static_cast<uint8_t*>(p);
-  h->h_keys = reinterpret_cast<uint64_t*>(q); q += MAXB * 8;
-  h->h_vin = q; q += (uint64_t)MAXB * val_bytes;
-  h->h_vout = q; q += (uint64_t)MAXB * val_bytes;
-  h->h_ops = q; q += MAXB;
-  h->h_status = q; q += MAXB;
+  for (int s = 0; s < 2; s++) {
+    bolt::IoSet& io = h->h_io[s];
+    io.keys = reinterpret_cast<uint64_t*>(q); q += MAXB * 8;
+    io.vin = q; q += (uint64_t)MAXB * val_bytes;
+    io.vout = q; q += (uint64_t)MAXB * val_bytes;
+    io.ops = q; q += MAXB;
+    io.status = q; q += MAXB;
+  }
+  h->h_keys = h->h_io[0].keys;
+  h->h_vin = h->h_io[0].vin;
+  h->h_vout = h->h_io[0].vout;
+  h->h_ops = h->h_io[0].ops;
+  h->h_status = h->h_io[0].status;
   h->h_err = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
   int rc = alloc_state(h);
   if (rc) {
@@ -834,6 +852,20 @@ int bolt_access_device_batches(bolt_t* h, const uint8_t* d_ops, const void* d_ke
   return access_batches(h, b, n, width, st) == cudaSuccess ? BOLT_OK : BOLT_E_CUDA;
 }
 
+static bool host_pinned(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// Chunks of up to cap_batch ops (whole batches of batch_width), alternating
+// between two device I/O sets; each chunk is one access_batches call.  Pinned
+// caller arrays are copied directly; pageable ones through pinned staging,
+// the next chunk's inputs staged and the previous chunk's outputs copied out
+// while a chunk runs.
 int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* vals_in,
                 void* vals_out, uint8_t* status_out, uint64_t n) {
   if (!h) return BOLT_E_ARG;
@@ -847,35 +879,80 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
   const uint8_t* kin = static_cast<const uint8_t*>(keys);
   const uint8_t* vin = static_cast<const uint8_t*>(vals_in);
   uint8_t* vout = static_cast<uint8_t*>(vals_out);
-  if (h->last_st != h->st) {
+  cudaStream_t st = h->st;
+  if (h->last_st != st) {
     if (h->last_st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
-    h->last_st = h->st;
+    h->last_st = st;
   }
-  for (uint64_t lo = 0; lo < n; lo += h->batch_width) {
-    const uint64_t cnt = n - lo < h->batch_width ? n - lo : h->batch_width;
-    std::memcpy(h->h_ops, ops + lo, cnt);
-    std::memcpy(h->h_keys, kin + lo * 8, cnt * 8);
-    std::memcpy(h->h_vin, vin + lo * vb, cnt * vb);
-    cudaError_t e = cudaMemcpyAsync(h->b.ops, h->h_ops, cnt, cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(h->b.keys, h->h_keys, cnt * 8, cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(h->b.vin, h->h_vin, cnt * vb, cudaMemcpyHostToDevice, h->st);
-    if (e != cudaSuccess) return BOLT_E_CUDA;
-    e = access_batch(h, h->b, (uint32_t)cnt, h->st);
-    if (e != cudaSuccess) return BOLT_E_CUDA;
-    h->t += cnt;
-    h->batches++;
-    e = cudaMemcpyAsync(h->h_vout, h->b.vout, cnt * vb, cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(h->h_status, h->b.status, cnt, cudaMemcpyDeviceToHost, h->st);
-    if (e != cudaSuccess) return BOLT_E_CUDA;
-    int rc = bolt_sync(h);
+  const uint32_t w = h->batch_width;
+  const uint64_t chunk = (uint64_t)(h->cap_batch / w) * w;
+  const bool pin_in = host_pinned(ops) && host_pinned(keys) && host_pinned(vals_in);
+  const bool pin_out = host_pinned(vals_out) && (!status_out || host_pinned(status_out));
+  const bolt::IoSet dev[2] = {{h->b.ops, h->b.keys, h->b.vin, h->b.vout, h->b.status}, h->d_io2};
+  bool pending[2] = {false, false};
+  uint64_t plo[2] = {0, 0}, pcnt[2] = {0, 0};
+  auto copy_out = [&](int s) -> int {
+    if (!pending[s]) return BOLT_OK;
+    pending[s] = false;
+    if (cudaEventSynchronize(h->ev_d2h[s]) != cudaSuccess) return BOLT_E_CUDA;
+    std::memcpy(vout + plo[s] * vb, h->h_io[s].vout, pcnt[s] * vb);
+    if (status_out) std::memcpy(status_out + plo[s], h->h_io[s].status, pcnt[s]);
+    return BOLT_OK;
+  };
+  cudaError_t e = cudaSuccess;
+  int k = 0;
+  for (uint64_t lo = 0; lo < n && e == cudaSuccess; lo += chunk, k ^= 1) {
+    const uint64_t cnt = n - lo < chunk ? n - lo : chunk;
+    const bolt::IoSet& d = dev[k];
+    const bolt::IoSet& hs = h->h_io[k];
+    const uint8_t* src_ops = ops + lo;
+    const void* src_keys = kin + lo * 8;
+    const uint8_t* src_vin = vin + lo * vb;
+    if (!pin_in) {
+      // the staging set was last read by the copy two chunks back
+      if (cudaEventSynchronize(h->ev_h2d[k]) != cudaSuccess) return BOLT_E_CUDA;
+      std::memcpy(hs.ops, src_ops, cnt);
+      std::memcpy(hs.keys, src_keys, cnt * 8);
+      std::memcpy(hs.vin, src_vin, cnt * vb);
+      src_ops = hs.ops;
+      src_keys = hs.keys;
+      src_vin = hs.vin;
+    }
+    e = cudaMemcpyAsync(d.ops, src_ops, cnt, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.keys, src_keys, cnt * 8, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.vin, src_vin, cnt * vb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_h2d[k], st);
+    if (e != cudaSuccess) break;
+    BatchDev b = h->b;
+    b.ops = d.ops;
+    b.keys = d.keys;
+    b.vin = d.vin;
+    b.vout = d.vout;
+    b.status = d.status;
+    e = access_batches(h, b, cnt, w, st);
+    if (e != cudaSuccess) break;
+    uint8_t* dst_vout = pin_out ? vout + lo * vb : hs.vout;
+    uint8_t* dst_st = pin_out && status_out ? status_out + lo : hs.status;
+    e = cudaMemcpyAsync(dst_vout, d.vout, cnt * vb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && (status_out || !pin_out))
+      e = cudaMemcpyAsync(dst_st, d.status, cnt, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_d2h[k], st);
+    if (e != cudaSuccess) break;
+    if (!pin_out) {
+      // the previous chunk's outputs, while this one runs
+      int rc = copy_out(k ^ 1);
+      if (rc) return rc;
+      pending[k] = true;
+      plo[k] = lo;
+      pcnt[k] = cnt;
+    }
+  }
+  if (e != cudaSuccess) return BOLT_E_CUDA;
+  for (int s = 0; s < 2; s++) {
+    int rc = copy_out(s ^ k);
     if (rc) return rc;
-    std::memcpy(vout + lo * vb, h->h_vout, cnt * vb);
-    if (status_out) std::memcpy(status_out + lo, h->h_status, cnt);
   }
-  return BOLT_OK;
+  return bolt_sync(h);
 }
 
 int bolt_read_pages(bolt_t* h, uint64_t first, uint64_t count, void* dst) {
@@ -1085,11 +1162,11 @@ uint64_t resident_estimate(const bolt_info_t& I, uint64_t cap, uint64_t trace_ca
   const uint64_t sort_cap = cap2 <= 512 ? 512 : (cap2 < 4096 ? 4096 : cap2);
   const uint64_t kt = 2 * cap2 < 128 ? 128 : 2 * cap2;
   const uint64_t ht = 4 * cap2 < 256 ? 256 : 4 * cap2;
-  b += cap * (1 + 8 + 2 * vb + 1) + 2 * cap * 8 + (2 * ((2 * cap + 255) / 256) + 2) * 4 + 16;
+  b += 2 * cap * (1 + 8 + 2 * vb + 1) + 2 * cap * 8 + (2 * ((2 * cap + 255) / 256) + 2) * 4 + 16;
   b += 2 * (sort_cap * 8 + kt * 4 + cap * 12 + cap * 16 + cap * 16 + cap * 4 + 2 * cap + ht * 8 +
             2 * cap * 4 + 4 + 2 * cap * I.page_bytes);
-  b += 2 * (ht * 12 + 2 * cap * 4 + 4 + 2 * cap * I.page_bytes);
-  b += 2 * cap * 8 + cap * vb + cap + cap * vb + cap + cap * 8 + 16 * 4 + 4;
+  b += 2 * (ht * 8 + ht * I.page_bytes + 2 * cap * 8 + 4);
+  b += ht * 8 + cap * vb + cap + cap * vb + cap + cap * 8 + 16 * 4 + 4;
   return b;
 }
 

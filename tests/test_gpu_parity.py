@@ -289,6 +289,43 @@ def test_device_batches_call_matches_oracle(lookahead):
     o.close(); g.close()
 
 
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_call_over_many_chunks_matches_oracle(pinned):
+    """bolt_access over 5000 ops with batch capacity 1000 and batch width
+    300: chunks of 900 ops alternate between two device I/O sets (pageable
+    arrays through pinned staging, pinned arrays copied directly), each chunk
+    a pipelined run of batches.  Outputs and state equal the oracle's with
+    batches of 300."""
+    import ctypes
+    import torch
+    N, vb, bw = 1 << 14, 16, 300
+    o = O.OracleMap(N, vb, batch=bw)
+    g = B.BoltMap(N, vb, trace=True)
+    g.set_param(B.BOLT_PARAM_BATCH_CAP, 1000)
+    g.set_param(B.BOLT_PARAM_BATCH, bw)
+    keys, vals = W.records(12000, vb, 51)
+    assert o.init(keys, vals, 5) == 0 and g.init(keys, vals, 5) == 0
+    ops, k, vin = W.op_stream(12000, 5000, vb, 52, get_frac=0.5, del_frac=0.1, absent_frac=0.1)
+    rc_o, vo, so = o.access(ops, k, vin)
+    assert rc_o == 0
+    if pinned:
+        t = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+             for a in (ops, k.view(np.int64), vin)]
+        out = torch.zeros((len(ops), vb), dtype=torch.uint8).pin_memory()
+        st = torch.zeros(len(ops), dtype=torch.uint8).pin_memory()
+        rc = B.bolt_access(g.handle, *[ctypes.c_void_p(x.data_ptr()) for x in (*t, out, st)],
+                           len(ops))
+        vg, sg = out.numpy(), st.numpy()
+    else:
+        rc, vg, sg = g.access(ops, k, vin)
+    assert rc == 0
+    assert np.array_equal(so, sg)
+    assert np.array_equal(vo, vg)
+    _assert_state_equal(o, g, "chunked host call")
+    assert g.stats()["batches"] == (5000 + bw - 1) // bw
+    o.close(); g.close()
+
+
 def test_autotune_keeps_results():
     """bolt_autotune picks a tile and a batch width by measurement; the map's
     contents are unchanged (its tuning Gets only remap keys) and later builds
