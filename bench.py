@@ -400,6 +400,23 @@ def run_bolt(args) -> None:
                "d2h_bytes_per_step": n_acc * (VAL_BYTES + 1),
                "build_mrec_s": round(N * e2e_steps / eb / 1e6, 2), "steps": e2e_steps}
 
+    # the access path's roofline: host pages touched per second against the
+    # zero-copy random-page rate of this map's own store (read + write back)
+    per_op = 2.0 * info["M"] / info["B"]  # expected host pages read per op
+    probe = m.probe_link(int(round(per_op * BATCH)), 50)
+    acc_rate = agg["accesses"] / agg["access_s"]
+    touch = acc_rate * per_op
+    access_link = {"bound": "host link (random 512-byte pages: each batch's reads beside "
+                            "the previous batch's write-back)",
+                   "achieved_pages_per_s": round(touch, 1),
+                   "peak_pages_per_s": round(probe["pipelined_pages_per_s"], 1),
+                   "frac": round(touch / probe["pipelined_pages_per_s"], 4),
+                   "read_only_pages_per_s": round(probe["read_pages_per_s"], 1),
+                   "pages_per_op": round(per_op, 4),
+                   "unit_note": "a page = one 512-byte read and one 512-byte write",
+                   "peak_source": "bolt_probe_link on this map's pinned page store (one "
+                                  "batch's worth of pages per launch, no compute)"}
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -425,6 +442,7 @@ def run_bolt(args) -> None:
         "build": {"value": round(agg["records"] / agg["build_s"] / 1e6, 2), "unit": "Mrec/s",
                   "ms_per_build": round(build_s / args.steps * 1e3, 2)},
         "roofline": roofline,
+        "access_link": access_link,
         "link": {"h2d_gbs": link.get("h2d"), "d2h_gbs": link.get("d2h"),
                  "gather_ms_per_batch": round(gat["ms"] / max(1, gat["spans"]), 4),
                  "evict_ms_per_batch": round(ev["ms"] / max(1, ev["spans"]), 4),

@@ -297,6 +297,23 @@ BOLT_API int bolt_trim(bolt_t* h);
  * buffers, and build scratch (including the host-pointer staging copy). */
 BOLT_API int bolt_footprint(const bolt_t* h, uint64_t* resident_bytes, uint64_t* scratch_bytes);
 
+/* bolt_probe_link -- measure the host link as the access path uses it, on
+ * this map's own pinned page store, through zero-copy 16-byte loads and
+ * stores (warp per 512-byte page, full width), CUDA-event timed on the
+ * handle's stream over `launches` launches of `pages` random pages each:
+ *   *read_pages_per_s       random pages read per second;
+ *   *pipelined_pages_per_s  pages per second when each launch reads a random
+ *                           set and writes back the set the previous launch
+ *                           read (one page read + one page written each) --
+ *                           the access path's batch reads beside the
+ *                           previous batch's write-back, with no compute.
+ * Written pages get their own bytes back, so the map is unchanged; waits for
+ * the handle's work first and allocates 2 * pages * page_bytes of device
+ * scratch for the call.  pages <= 2^22.  No counterpart in the paper: it is
+ * the access path's roofline denominator.  BOLT_E_STATE before bolt_init. */
+BOLT_API int bolt_probe_link(bolt_t* h, uint32_t pages, uint32_t launches,
+                             double* read_pages_per_s, double* pipelined_pages_per_s);
+
 /* bolt_plan_bytes -- host-only estimate of the same two figures for a map of
  * capacity N (budget policy for alpha, c = 8, default trace capacity) with
  * batch buffers for batch_cap ops and a build of n_init records. */

@@ -98,6 +98,8 @@ _SIGS = {
     "bolt_access_device": ([_P, _P, _P, _P, _P, _P, _u64, _P], _i),
     "bolt_access_device_batches": ([_P, _P, _P, _P, _P, _P, _u64, ctypes.c_uint32, _P], _i),
     "bolt_sync": ([_P], _i),
+    "bolt_probe_link": ([_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(ctypes.c_double)], _i),
     "bolt_destroy": ([_P], _i),
     "bolt_get_info": ([_P, ctypes.POINTER(bolt_info_t)], _i),
     "bolt_get_stats": ([_P, ctypes.POINTER(bolt_stats_t)], _i),
@@ -246,6 +248,14 @@ class BoltMap:
 
     def sync(self) -> int:
         return bolt_sync(self._h)
+
+    def probe_link(self, pages: int, launches: int = 50) -> dict:
+        """Random-page zero-copy read rate, and the read + previous-set write-back
+        rate, over this map's own pinned pages."""
+        r, w = ctypes.c_double(), ctypes.c_double()
+        _check(bolt_probe_link(self._h, pages, launches, ctypes.byref(r), ctypes.byref(w)),
+               "bolt_probe_link")
+        return {"read_pages_per_s": r.value, "pipelined_pages_per_s": w.value}
 
     # --- inspection ----------------------------------------------------------
     def pages(self, first: int = 0, count=None) -> np.ndarray:

@@ -1195,6 +1195,85 @@ extern "C" int bolt_footprint(const bolt_t* h, uint64_t* resident_bytes, uint64_
   return BOLT_OK;
 }
 
+namespace {
+__device__ __forceinline__ uint64_t probe_page(uint32_t w, uint32_t salt, uint64_t M) {
+  uint64_t x = ((uint64_t)salt << 32) ^ w;
+  x ^= x >> 33; x *= 0xff51afd7ed558ccdull; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ull; x ^= x >> 33;
+  return x % M;
+}
+// warps [0, reads): read random page set `salt_r` into buf_r (warp per page);
+// warps [reads, reads + writes): write buf_w back to the pages of set
+// `salt_w`, which the previous launch read into it (so their bytes do not
+// change) -- the access path's pattern of one batch's page reads beside the
+// previous batch's write-back
+__global__ void k_probe_link(const MapDev m, uint32_t reads, uint32_t writes, uint32_t salt_r,
+                             uint32_t salt_w, uint8_t* buf_r, const uint8_t* buf_w) {
+  const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const uint32_t nu4 = m.page_bytes / 16;
+  if (w < reads) {
+    const uint4* pg = reinterpret_cast<const uint4*>(m.pages + probe_page(w, salt_r, m.M) * m.page_bytes);
+    uint4* dst = reinterpret_cast<uint4*>(buf_r + (uint64_t)w * m.page_bytes);
+    for (uint32_t c = lane; c < nu4; c += 32) dst[c] = pg[c];
+  } else if (w < reads + writes) {
+    const uint32_t k = w - reads;
+    uint4* pg = reinterpret_cast<uint4*>(m.pages + probe_page(k, salt_w, m.M) * m.page_bytes);
+    const uint4* src = reinterpret_cast<const uint4*>(buf_w + (uint64_t)k * m.page_bytes);
+    for (uint32_t c = lane; c < nu4; c += 32) pg[c] = src[c];
+  }
+}
+}  // namespace
+
+extern "C" int bolt_probe_link(bolt_t* h, uint32_t pages, uint32_t launches,
+                               double* read_pages_per_s, double* pipelined_pages_per_s) {
+  if (!h || pages == 0 || launches == 0 || !read_pages_per_s || !pipelined_pages_per_s)
+    return BOLT_E_ARG;
+  if (!h->initialized) return BOLT_E_STATE;
+  if (h->info.M == 0 || pages > (1u << 22)) return BOLT_E_ARG;
+  // nothing of the handle may be in flight: a page write-back racing the
+  // probe's writes could be overwritten with older bytes
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  const uint64_t pb = h->info.page_bytes;
+  uint8_t* buf = nullptr;
+  if (cudaMalloc(&buf, 2 * (uint64_t)pages * pb) != cudaSuccess) {
+    cudaGetLastError();
+    return BOLT_E_NOMEM;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  double rate[2] = {0, 0};
+  const uint32_t salt0 = 0x51ED0000u + (uint32_t)(h->batches & 0xffff) * 131u;
+  for (int pipelined = 0; pipelined < 2 && e == cudaSuccess; pipelined++) {
+    uint32_t salt = salt0 + (uint32_t)pipelined * 0x10000u;
+    const uint32_t wr = pipelined ? pages : 0;
+    const uint32_t blocks = (uint32_t)(((uint64_t)(pages + wr) * 32 + 255) / 256);
+    // launch 0 reads the first set (nothing to write back yet); launch i
+    // reads set i into buffer i % 2 and writes set i - 1 back from the other
+    k_probe_link<<<(pages * 32 + 255) / 256, 256, 0, h->st>>>(h->m, pages, 0, salt, 0, buf,
+                                                              buf + pages * pb);
+    e = cudaEventRecord(a, h->st);
+    for (uint32_t i = 1; i <= launches && e == cudaSuccess; i++) {
+      uint8_t* br = buf + (uint64_t)(i & 1) * pages * pb;
+      const uint8_t* bw = buf + (uint64_t)((i - 1) & 1) * pages * pb;
+      k_probe_link<<<blocks, 256, 0, h->st>>>(h->m, pages, wr, salt + i, salt + i - 1, br, bw);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b, h->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && ms > 0) rate[pipelined] = (double)pages * launches / (ms * 1e-3);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(buf);
+  if (e != cudaSuccess) return BOLT_E_CUDA;
+  *read_pages_per_s = rate[0];
+  *pipelined_pages_per_s = rate[1];
+  return BOLT_OK;
+}
+
 extern "C" int bolt_plan_bytes(uint64_t N, uint32_t val_bytes, uint64_t hbm_budget,
                                uint32_t batch_cap, uint64_t n_init, uint64_t* resident_bytes,
                                uint64_t* build_bytes) {

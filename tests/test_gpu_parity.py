@@ -363,3 +363,21 @@ def test_large_config_scaled_replica():
         _run_batch(o, g, ops, k, vin, f"replica batch {rep}")
     _assert_state_equal(o, g, "scaled replica")
     o.close(); g.close()
+
+
+def test_link_probe_leaves_pages_unchanged():
+    """bolt_probe_link reads random pages of the map's own store and writes
+    earlier-read pages back: rates are positive and every page ciphertext is
+    unchanged, so the map still matches the oracle afterwards."""
+    N, vb = 1 << 14, 8
+    o, g = _pair(N, vb)
+    keys, vals = W.records(N, vb, 61)
+    assert o.init(keys, vals, 3) == 0 and g.init(keys, vals, 3) == 0
+    before = g.pages().copy()
+    r = g.probe_link(512, launches=5)
+    assert r["read_pages_per_s"] > 0 and r["pipelined_pages_per_s"] > 0
+    assert np.array_equal(before, g.pages())
+    ops, k, vin = W.op_stream(N, 2048, vb, 62, get_frac=0.5)
+    _run_batch(o, g, ops, k, vin, "after the probe")
+    _assert_state_equal(o, g, "after the probe")
+    o.close(); g.close()
