@@ -639,6 +639,121 @@ def run_serve(args) -> None:
     srv.close()
 
 
+def host_mem_available() -> int:
+    """MemAvailable of this host in bytes (0 if unknown)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def run_big(args) -> None:
+    """The largest configuration: N = 2^30 records of 64 B (8 B key + 56 B
+    value) under a 16 GB HBM budget (alpha = 0.1: ~120.8 M host pages of
+    960 B, ~116 GB of pinned host memory), built from keys and values
+    generated on the device; then 2^24 Zipf(0.99) accesses, 90% GET / 10%
+    PUT, in batches of 4096 (a 2^20-op warm-up pass first).  The sampled GETs
+    are checked against the initial values and the stream's own PUTs.  Skips
+    (prints a "skipped" line) when the host cannot pin the page store."""
+    import torch
+    from paper_2509_01742_b300 import bolt as B
+
+    torch.cuda.set_device(0)
+    log_n = args.big_log_n
+    N, vb, budget = 1 << log_n, 56, 16 * 10**9
+    info = B.plan(N, vb, budget)
+    pinned = info["M"] * info["page_bytes"]
+    avail = host_mem_available()
+    config = {"workload": f"N=2^{log_n} records x 64 B (8 B key + 56 B value), 16 GB HBM budget, "
+                          "inputs generated on the device; 2^24 Zipf(0.99) accesses, 90% GET / "
+                          "10% PUT, batches of 4096",
+              "records": N, "alpha": info["alpha"], "pinned_page_bytes": pinned}
+    line = {"metric": "oblivious accesses/s and build Mrec/s, largest map", "unit": "accesses/s",
+            "higher_is_better": True, "n_gpus": 1, "data": "synthetic", "config": config}
+    if not avail or pinned + (24 << 30) > avail:
+        line["skipped"] = f"host memory: {pinned / 2**30:.1f} GiB of pinned pages needed, " \
+                          f"{avail / 2**30:.1f} GiB available"
+        print(json.dumps(line), flush=True)
+        return
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        d_keys = W.key_of_torch(torch.arange(N, device="cuda", dtype=torch.int64))
+        d_vals = torch.empty((N, vb), dtype=torch.uint8, device="cuda")
+        g = torch.Generator(device="cuda")
+        g.manual_seed(SEED_DATA + 4)
+        for lo in range(0, N, 1 << 26):
+            hi = min(N, lo + (1 << 26))
+            d_vals[lo:hi] = torch.randint(0, 256, (hi - lo, vb), dtype=torch.uint8,
+                                          device="cuda", generator=g)
+    torch.cuda.synchronize()
+    n_warm, n_ops = 1 << 20, 1 << 24
+    ops, akeys, avin, aidx = W.op_stream(N, n_warm + n_ops, vb, SEED_OPS + 4, get_frac=0.9,
+                                         zipf_theta=0.99, return_index=True)
+    d_ops = torch.from_numpy(ops).cuda()
+    d_akeys = torch.from_numpy(akeys.view(np.int64)).cuda()
+    d_avin = torch.from_numpy(avin).cuda()
+    d_vout = torch.empty((n_warm + n_ops, vb), dtype=torch.uint8, device="cuda")
+    d_st = torch.empty(n_warm + n_ops, dtype=torch.uint8, device="cuda")
+    t0 = time.perf_counter()
+    m = B.BoltMap(N, vb, hbm_budget=budget)
+    alloc_s = time.perf_counter() - t0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
+    assert m.init_device(d_keys, d_vals, SEED_MAP + 4, stream=stream) == 0
+    ev[1].record(stream)
+    assert m.access_device_batches(d_ops[:n_warm], d_akeys[:n_warm], d_avin[:n_warm],
+                                   d_vout[:n_warm], d_st[:n_warm], BATCH, stream=stream) == 0
+    ev[2].record(stream)
+    with ClockSampler(0) as clk:
+        assert m.access_device_batches(d_ops[n_warm:], d_akeys[n_warm:], d_avin[n_warm:],
+                                       d_vout[n_warm:], d_st[n_warm:], BATCH,
+                                       stream=stream) == 0
+        ev[3].record(stream)
+        ev[3].synchronize()
+    assert m.sync() == 0
+    build_s = ev[0].elapsed_time(ev[1]) * 1e-3
+    acc_s = ev[2].elapsed_time(ev[3]) * 1e-3
+    # check: every key exists; a sample of GETs returns the last PUT before it
+    # in the stream, else the record's initial value
+    st = d_st.cpu().numpy()
+    assert st.all(), "every accessed key exists"
+    rng = np.random.default_rng(5)
+    gets = np.flatnonzero(ops == W.GET)
+    sample = np.sort(rng.choice(gets, size=min(20000, len(gets)), replace=False))
+    T = np.uint64(len(ops))
+    puts = np.flatnonzero(ops == W.PUT).astype(np.uint64)
+    put_key = np.sort(aidx[puts] * T + puts)
+    q = aidx[sample] * T + sample.astype(np.uint64)
+    j = np.searchsorted(put_key, q) - 1
+    has = (j >= 0) & (put_key[np.maximum(j, 0)] // T == aidx[sample])
+    last_put = (put_key[np.maximum(j, 0)] % T).astype(np.int64)
+    init_vals = d_vals[torch.from_numpy(aidx[sample].astype(np.int64)).cuda()].cpu().numpy()
+    expect = np.where(has[:, None], avin[last_put], init_vals)
+    got = d_vout[torch.from_numpy(sample.astype(np.int64)).cuda()].cpu().numpy()
+    assert np.array_equal(got, expect), "sampled GETs match the stream"
+    per_op = 2.0 * info["M"] / info["B"]
+    probe = m.probe_link(int(round(per_op * BATCH)), 20)
+    rate = n_ops / acc_s
+    line.update({
+        "value": round(rate, 1),
+        "build": {"value": round(N / build_s / 1e6, 2), "unit": "Mrec/s",
+                  "ms_per_build": round(build_s * 1e3, 1),
+                  "pinned_alloc_s": round(alloc_s, 1)},
+        "access_link": {"achieved_pages_per_s": round(rate * per_op, 1),
+                        "peak_pages_per_s": round(probe["pipelined_pages_per_s"], 1),
+                        "frac": round(rate * per_op / probe["pipelined_pages_per_s"], 4),
+                        "pages_per_op": round(per_op, 4), "page_bytes": info["page_bytes"]},
+        "checked_gets": int(len(sample)),
+        "clocks": clk.summary(),
+    })
+    m.close()
+    print(json.dumps(line), flush=True)
+
+
 def make_records_vb(n: int, vb: int, seed: int):
     keys = np.empty(n, dtype=np.uint64)
     for lo in range(0, n, 1 << 24):
@@ -655,10 +770,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("bolt", "reference"), default="bolt")
-    ap.add_argument("--config", choices=("headline", "zipf", "w1", "serve"), default="headline",
+    ap.add_argument("--config", choices=("headline", "zipf", "w1", "serve", "big"),
+                    default="headline",
                     help="headline: the JSON line above; zipf: batch-width sweep on the "
                          "skewed 2^24 x 64 B map; w1: one access per call vs batches of 4096; "
-                         "serve: 64 maps behind the continuous-batching server")
+                         "serve: 64 maps behind the continuous-batching server; big: the "
+                         "2^30 x 64 B map under a 16 GB budget")
+    ap.add_argument("--big-log-n", type=int, default=30)
     ap.add_argument("--maps", type=int, default=64)
     ap.add_argument("--requests", type=int, default=6000)
     ap.add_argument("--log-n", type=int, default=LOG_N)
@@ -674,6 +792,8 @@ def main():
         run_reference(args)
     elif args.config == "serve":
         run_serve(args)
+    elif args.config == "big":
+        run_big(args)
     elif args.config != "headline":
         run_sweep(args)
     else:

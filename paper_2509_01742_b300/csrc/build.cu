@@ -205,27 +205,41 @@ __global__ void __launch_bounds__(256) k_build_rounds(MapDev m, const uint64_t* 
 }
 
 // write every record's position-map entry (row and slot claimed in the
-// rounds) and give HBM-bin records a value-store slot
+// rounds) and give HBM-bin records a value-store slot.  The slots come from
+// one counter, taken once per warp for all its HBM-bin records (which slot a
+// record gets is never observable: the value store lives in HBM).
 __global__ void k_build_place(MapDev m, const uint64_t* __restrict__ keys,
                               const uint8_t* __restrict__ vals, uint64_t n,
                               const uint64_t* __restrict__ bins, const uint32_t* __restrict__ dest,
                               const uint32_t* __restrict__ prow, unsigned long long* vs_fill) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t tag = prow[i];
+  const int lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
+       base += stride) {
+    const uint64_t i = base + lane;
+    uint32_t tag = NONE32, d = 0;
+    if (i < n) {
+      tag = prow[i];
+      d = dest[i];
+    }
+    const bool hbm = tag != NONE32 && d < m.K;
+    const uint32_t hmask = __ballot_sync(0xffffffffu, hbm);
+    unsigned long long vbase = 0;
+    if (lane == 0 && hmask) vbase = atomicAdd(vs_fill, (unsigned long long)__popc(hmask));
+    vbase = __shfl_sync(0xffffffffu, vbase, 0);
     if (tag == NONE32) continue;
     const uint64_t pmi = (uint64_t)(tag & PROW_ROW_MASK) * m.R + (tag >> PROW_SLOT_SHIFT);
-    const uint32_t d = dest[i];
     const uint64_t bb = bins[i];
     const uint32_t which = d == (uint32_t)(bb >> 32) ? 1u : 0u;
     uint32_t meta = meta_make(LOC_HOST, which, 0);
-    if (d < m.K) {
-      const unsigned long long vs = atomicAdd(vs_fill, 1ull);
+    const uint64_t key = keys[i];
+    if (hbm) {
+      const unsigned long long vs = vbase + __popc(hmask & ((1u << lane) - 1u));
       if (vs >= m.vs_cap) {
         set_err(m, ERR_VS);
         continue;
       }
-      m.vs_key[vs] = keys[i];
+      m.vs_key[vs] = key;
       const uint64_t* src = reinterpret_cast<const uint64_t*>(vals + i * m.vb);
       uint64_t* dst = reinterpret_cast<uint64_t*>(m.vs_val + vs * m.vb);
       for (uint32_t w = 0; w < m.vb / 8; w++) dst[w] = src[w];
@@ -233,7 +247,7 @@ __global__ void k_build_place(MapDev m, const uint64_t* __restrict__ keys,
       m.vs_live[vs] = 1;
       meta = meta_make(LOC_HBM, which, (uint32_t)vs);
     }
-    m.pm_key[pmi] = keys[i];
+    m.pm_key[pmi] = key;
     m.pm_bins[pmi] = bb;
     m.pm_meta[pmi] = meta;
   }

@@ -35,6 +35,23 @@ def key_of(index: np.ndarray) -> np.ndarray:
     return mix64(np.asarray(index, dtype=np.uint64) ^ _KEY_SALT)
 
 
+def _s64(c: int) -> int:
+    return c - (1 << 64) if c >= (1 << 63) else c
+
+
+def key_of_torch(index):
+    """key_of for an integer torch tensor on any device: the same 64 bits, as
+    int64 (right shifts are made logical by masking the sign-extended bits)."""
+    import torch
+    x = index.to(torch.int64) ^ _s64(int(_KEY_SALT))
+    x = x ^ ((x >> 30) & ((1 << 34) - 1))
+    x = x * _s64(int(_M1))
+    x = x ^ ((x >> 27) & ((1 << 37) - 1))
+    x = x * _s64(int(_M2))
+    x = x ^ ((x >> 31) & ((1 << 33) - 1))
+    return x
+
+
 def records(n: int, val_bytes: int, seed: int):
     """n distinct keys (uint64) and n random values (uint8[n, val_bytes])."""
     rng = np.random.default_rng(seed)
@@ -69,14 +86,15 @@ class Zipf:
 
 
 def op_stream(n_records: int, n_ops: int, val_bytes: int, seed: int, get_frac=0.5,
-              del_frac=0.0, absent_frac=0.0, zipf_theta=None):
+              del_frac=0.0, absent_frac=0.0, zipf_theta=None, return_index=False):
     """An operation stream over an n_records map.
 
     Returns (ops uint8[n], keys uint64[n], vals_in uint8[n, val_bytes]).
     Keys are existing records drawn uniformly or Zipf-skewed (popular ranks are
     scattered over the key space by the mixer), with `absent_frac` of them
     replaced by keys that were never inserted; ops are GET with probability
-    `get_frac`, DEL with `del_frac`, else PUT.
+    `get_frac`, DEL with `del_frac`, else PUT.  With return_index, the record
+    index of each op's key (key = key_of(index)) is returned fourth.
     """
     rng = np.random.default_rng(seed)
     if zipf_theta is None:
@@ -92,4 +110,6 @@ def op_stream(n_records: int, n_ops: int, val_bytes: int, seed: int, get_frac=0.
     ops = np.where(u < get_frac, GET, np.where(u < get_frac + del_frac, DEL, PUT))
     ops = ops.astype(np.uint8)
     vals = rng.integers(0, 256, size=(n_ops, val_bytes), dtype=np.uint8)
+    if return_index:
+        return ops, keys, vals, idx
     return ops, keys, vals
