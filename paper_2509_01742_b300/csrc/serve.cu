@@ -12,7 +12,9 @@
 //     while the map is busy ride the next batch, and batches of different maps
 //     run concurrently on the device;
 //   - a completed batch (CUDA event) returns each request's values and
-//     status, timestamped, to the client.
+//     status, timestamped, to the client;
+//   - a small pool of dispatch threads enqueues the packed batches, so the
+//     host cost of enqueueing does not serialise the maps.
 // Each batch is exactly one bolt access batch (Alg. 1 over a batch), so a
 // request's results do not depend on what it was batched with; the per-map
 // log of batch sizes lets a replay reproduce ciphertexts and the trace.
@@ -59,6 +61,7 @@ struct Map {
   bolt* h = nullptr;
   std::deque<Request*> queue;
   std::vector<Request*> inflight;
+  std::atomic<bool> dispatched{false};  // the in-flight batch's done_ev is recorded
   bool remove_requested = false;
   cudaEvent_t done_ev = nullptr;
   // pinned staging of one batch
@@ -79,6 +82,12 @@ struct bolt_server {
   std::mutex mu;
   std::condition_variable work_cv, done_cv;
   std::thread worker;
+  // dispatch workers: enqueueing a batch (staging copies and about twenty
+  // stream operations) takes tens of microseconds of host time, so several
+  // threads enqueue the batches of different maps at once
+  std::vector<std::thread> dispatchers;
+  std::deque<std::pair<Map*, std::vector<Request*>>> jobs;  // guarded by mu
+  std::condition_variable job_cv;
   std::atomic<bool> stop{false};
   std::atomic<uint64_t> work_seq{0};  // bumped by every submit / add / remove
   uint64_t next_id = 1;
@@ -94,6 +103,7 @@ struct bolt_server {
 namespace {
 
 constexpr uint64_t SERVER_TRACE_CAP = 1024;
+constexpr int SERVER_DISPATCHERS = 4;
 
 void free_map_device(Map* m) {
   if (m->h) {
@@ -136,8 +146,9 @@ int build_map(bolt_server* s, Map* m) {
   return BOLT_OK;
 }
 
-// pack queued requests into one batch and enqueue it (scheduler thread,
-// lock not held; touches only the map's staging and its handle)
+// copy a packed batch's requests into the map's staging and enqueue the batch
+// (a dispatch worker, lock not held; touches only the map's staging and its
+// handle, and a map has at most one batch in flight)
 cudaError_t dispatch(bolt_server* s, Map* m, const std::vector<Request*>& reqs, uint32_t* n_out) {
   bolt* h = m->h;
   const uint64_t vb = m->vb;
@@ -206,7 +217,9 @@ void scheduler(bolt_server* s) {
     // 1. completions
     for (size_t i = 0; i < s->maps.size(); i++) {
       Map* m = s->maps[i];
-      if (!m->inflight.empty() && cudaEventQuery(m->done_ev) == cudaSuccess) {
+      if (!m->inflight.empty() && m->dispatched.load() &&
+          cudaEventQuery(m->done_ev) == cudaSuccess) {
+        m->dispatched.store(false);
         complete(s, m);
         progress = true;
       }
@@ -270,19 +283,10 @@ void scheduler(bolt_server* s) {
         n += m->queue.front()->n;
         m->queue.pop_front();
       }
-      lock.unlock();
-      uint32_t packed = 0;
-      const cudaError_t e = dispatch(s, m, reqs, &packed);
-      lock.lock();
       m->inflight = reqs;
-      m->batch_log.push_back(packed);
-      if (e != cudaSuccess) {
-        // the batch never ran: fail its requests now
-        m->error = BOLT_E_CUDA;
-        *m->h_err = 0;
-        complete(s, m);
-        s->done_cv.notify_all();
-      }
+      m->dispatched.store(false);
+      s->jobs.emplace_back(m, std::move(reqs));
+      s->job_cv.notify_one();
       progress = true;
     }
     if (progress) continue;
@@ -302,10 +306,39 @@ void scheduler(bolt_server* s) {
       if (s->stop.load() || s->work_seq.load() != seq) break;
       bool any = false;
       for (Map* m : busy_maps)
-        if (cudaEventQuery(m->done_ev) == cudaSuccess) any = true;
+        if (m->dispatched.load() && cudaEventQuery(m->done_ev) == cudaSuccess) any = true;
       if (any) break;
       std::this_thread::yield();
     }
+  }
+}
+
+// dispatch worker: enqueue the batches the scheduler packed
+void dispatcher(bolt_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lock(s->mu);
+  for (;;) {
+    s->job_cv.wait(lock, [&] { return s->stop.load() || !s->jobs.empty(); });
+    if (s->jobs.empty()) return;  // stopping
+    auto job = std::move(s->jobs.front());
+    s->jobs.pop_front();
+    Map* m = job.first;
+    lock.unlock();
+    uint32_t packed = 0;
+    const cudaError_t e = dispatch(s, m, job.second, &packed);
+    lock.lock();
+    m->batch_log.push_back(packed);
+    if (e != cudaSuccess) {
+      // the batch never ran: fail its requests now
+      m->error = BOLT_E_CUDA;
+      *m->h_err = 0;
+      complete(s, m);
+      s->done_cv.notify_all();
+    } else {
+      m->dispatched.store(true);
+    }
+    s->work_seq.fetch_add(1);
+    s->work_cv.notify_all();
   }
 }
 
@@ -325,6 +358,7 @@ int bolt_server_create(uint64_t hbm_budget, uint32_t max_batch, bolt_server_t** 
   s->max_batch = max_batch;
   cudaGetDevice(&s->device);
   s->worker = std::thread(scheduler, s);
+  for (int i = 0; i < SERVER_DISPATCHERS; i++) s->dispatchers.emplace_back(dispatcher, s);
   *out = s;
   return BOLT_OK;
 }
@@ -482,7 +516,10 @@ int bolt_server_destroy(bolt_server_t* s) {
     s->stop.store(true);
   }
   s->work_cv.notify_all();
+  s->job_cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  for (std::thread& t : s->dispatchers)
+    if (t.joinable()) t.join();
   for (Map* m : s->maps) {
     if (m->h) brt::sync_handle(m->h);
     for (Request* r : m->queue) (void)r;
