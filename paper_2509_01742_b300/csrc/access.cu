@@ -52,6 +52,32 @@ static int num_sms() {
   return cached[dev];
 }
 
+// Programmatic dependent launch for the batch's main chain: a kernel
+// launched with launch_dependent() may be scheduled while its predecessor on
+// the stream finishes; it must pass dep_wait() before touching anything the
+// predecessor wrote (a no-op when launched normally).  dep_trigger() lets the
+// successor be scheduled once every block of this kernel has reached it.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... Params, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(Params...), unsigned grid, unsigned block,
+                                    size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Params>(args)...);
+}
+
 // per op: PRF pairs and rows, and the op's grouping key.  Equal keys share a
 // hash-table slot (claimed by the first op to reach it), so sorting
 // (slot << 16 | op) lists every key's ops together, in op order.
@@ -630,6 +656,7 @@ __global__ void __launch_bounds__(256) k_lookup(MapDev m, BatchDev b, uint32_t n
   const int lane = threadIdx.x & 31;
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw)
     lookup_op(m, b, i, lane);
+  dep_trigger();
 }
 
 // the written pages (the batch's page list), one 512-byte chunk per warp
@@ -657,6 +684,7 @@ __device__ __forceinline__ void ring_push(const MapDev& m, uint32_t slot) {
 
 // warp per op: find_remove for hits (Alg. 1 lines 6 and 9)
 __global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
+  dep_wait();
   // the previous batch's page table was last read by this batch's gather:
   // return the entries it used to NONE for the batch after this one
   if (b.clr_ht_key)
@@ -855,6 +883,7 @@ constexpr uint32_t EVICT_WARPS_PER_BLOCK = 4;
 __global__ void __launch_bounds__(EVICT_WARPS_PER_BLOCK * 32)
     k_exec_evict(MapDev m, BatchDev b, uint32_t n, uint32_t evict_blocks, int decide) {
   extern __shared__ __align__(16) uint8_t sbuf[];
+  dep_wait();
   const uint32_t exec_blocks = gridDim.x - evict_blocks;
   if (blockIdx.x >= exec_blocks) {
     evict_page(m, b, blockIdx.x - exec_blocks, sbuf);
@@ -926,6 +955,7 @@ __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, 
 }
 
 __global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
+  dep_wait();
   const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= hi || b.leader[i] != i || !b.fpres[i]) return;
   const uint32_t dest = b.rdest[i];
@@ -1164,7 +1194,8 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
   }
   {
     ProfSpan ps(P_FINDEXEC, st);
-    k_find<<<warp_blocks, 256, 0, st>>>(m, b, n);
+    e = launch_dependent(k_find, warp_blocks, 256, 0, st, m, b, n);
+    if (e != cudaSuccess) return e;
     count_launch();
   }
   // P2C remap: one round -> the decisions run with exec, then one apply
@@ -1184,8 +1215,9 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
     }
     const uint32_t evict_blocks = (2 * n + wpb - 1) / wpb;
     const uint32_t exec_blocks = (n + wpb * 32 - 1) / (wpb * 32);
-    k_exec_evict<<<evict_blocks + exec_blocks, wpb * 32, smem, st>>>(m, b, n, evict_blocks,
-                                                                     fused_decide);
+    e = launch_dependent(k_exec_evict, evict_blocks + exec_blocks, wpb * 32, smem, st, m, b, n,
+                         evict_blocks, fused_decide);
+    if (e != cudaSuccess) return e;
     count_launch();
   }
   // the host write-back overlaps the rest of this batch and the next one
@@ -1200,7 +1232,8 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
   ProfSpan prs(P_REMAP, st);
   const size_t rsmem = ((m.B + 3) / 4 + (m.rows + 3) / 4) * 4;
   if (fused_decide) {
-    k_remap_apply<<<(n + 255) / 256, 256, 0, st>>>(m, b, 0, n);
+    e = launch_dependent(k_remap_apply, (n + 255) / 256, 256, 0, st, m, b, 0u, n);
+    if (e != cudaSuccess) return e;
     count_launch();
   } else if (smem_remap) {
     const bool reg = n <= REMAP_REG_OPS * 1024;
