@@ -865,11 +865,18 @@ __device__ __forceinline__ void evict_page(const MapDev& m, const BatchDev& b, u
     const uint32_t sh = (uint32_t)(q & 3) * 8;
     atomicAnd(m.revcnt + (q >> 2), ~(0xffu << sh));
   }
-  if (sv) {  // evicted stash item now lives in the page
+  // evicted stash items now live in the page; their value-store slots go
+  // back to the free ring (one tail bump per warp)
+  const uint32_t smask2 = __ballot_sync(0xffffffffu, sv);
+  unsigned long long tail = 0;
+  if (smask2 && lane == __ffs(smask2) - 1)
+    tail = atomicAdd(m.ring_ctr + 1, (unsigned long long)__popc(smask2));
+  tail = __shfl_sync(0xffffffffu, tail, smask2 ? __ffs(smask2) - 1 : 0);
+  if (sv) {
     const uint32_t pmi = m.vs_pm[vs];
     m.pm_meta[pmi] = meta_make(LOC_HOST, meta_which(m.pm_meta[pmi]), 0);
     m.vs_live[vs] = 0;
-    ring_push(m, vs);
+    m.ring[(tail + __popc(smask2 & below)) % m.vs_cap] = vs;
   }
 }
 
@@ -905,11 +912,22 @@ __global__ void k_remap_decide(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
 // place leader i in its new bin: a value-store slot from the ring, the
 // position-map entry (a free slot of the chosen row for a new key), and the
 // reverse-index entry for a stash item; the counts are already bumped
+// One counter hands out ring positions to every lane of the warp that places
+// an item (one atomic per warp): returns this lane's position, or ~0 when the
+// lane does not take one.  All 32 lanes must call it.
+__device__ __forceinline__ unsigned long long ring_take(const MapDev& m, bool take) {
+  const uint32_t mask = __ballot_sync(0xffffffffu, take);
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (mask && lane == __ffs(mask) - 1) base = atomicAdd(m.ring_ctr, (unsigned long long)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, mask ? __ffs(mask) - 1 : 0);
+  return take ? base + __popc(mask & ((1u << lane) - 1u)) : ~0ull;
+}
+
 __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, uint32_t i,
-                                            uint32_t dest) {
+                                            uint32_t dest, unsigned long long pos) {
   const uint64_t pr = b.rpair[i];
   const uint32_t which = dest == (uint32_t)(pr >> 32) ? 1u : 0u;
-  const unsigned long long pos = atomicAdd(m.ring_ctr, 1ull);
   if (pos >= m.ring_ctr[1]) {
     set_err(m, ERR_VS);
     return;
@@ -957,17 +975,20 @@ __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, 
 __global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
   dep_wait();
   const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= hi || b.leader[i] != i || !b.fpres[i]) return;
-  const uint32_t dest = b.rdest[i];
-  if (byte_inc(m.load, dest) + 1 > m.lmax) {
-    set_err(m, ERR_LOAD);
-    return;
+  bool go = i < hi && b.leader[i] == i && b.fpres[i];
+  uint32_t dest = 0;
+  if (go) {
+    dest = b.rdest[i];
+    if (byte_inc(m.load, dest) + 1 > m.lmax) {
+      set_err(m, ERR_LOAD);
+      go = false;
+    } else if (b.hit[i] == NONE32 && byte_inc(m.rowcnt, b.rrow[i]) + 1 > m.R) {
+      set_err(m, ERR_ROW);
+      go = false;
+    }
   }
-  if (b.hit[i] == NONE32 && byte_inc(m.rowcnt, b.rrow[i]) + 1 > m.R) {
-    set_err(m, ERR_ROW);
-    return;
-  }
-  remap_place(m, b, i, dest);
+  const unsigned long long pos = ring_take(m, go);
+  if (go) remap_place(m, b, i, dest, pos);
 }
 
 // Small maps (B <= 2^17 bins, <= 2^16 rows): every P2C round of the batch in
@@ -1103,8 +1124,9 @@ __global__ void __launch_bounds__(1024) k_remap_smem_reg(MapDev m, BatchDev b, u
 
 __global__ void k_remap_rest(MapDev m, BatchDev b, uint32_t n) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || b.leader[i] != i || !b.fpres[i]) return;
-  remap_place(m, b, i, b.rdest[i]);
+  const bool go = i < n && b.leader[i] == i && b.fpres[i];
+  const unsigned long long pos = ring_take(m, go);
+  if (go) remap_place(m, b, i, b.rdest[i], pos);
 }
 
 __global__ void k_clear_keys(BatchDev b, uint32_t n) {
