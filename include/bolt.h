@@ -246,12 +246,13 @@ BOLT_API int bolt_read_rowcounts(bolt_t* h, uint8_t* dst);
  *   0 bitonic global steps (HBM passes)   1 bitonic in-tile steps
  *   2 build page gather/encrypt/store     3 build P2C + position-map rounds
  *   4 build key-uniqueness check          5 whole access batch
- *   6 access page read + decrypt          7 access write-back + eviction
+ *   6 access position-map search + page read + decrypt
+ *   7 access write-back + eviction (with exec)
  *   8 whole build                         9 access grouping sort + scans
  *  10 key check: bitonic global steps    11 key check: bitonic in-tile steps
  *  12 access: written pages copied to the host (side stream)
  *  13 access: lookahead position-map search + page reads (side stream)
- *  14 access: position-map search        15 access: distinct pages + trace
+ *  14 (unused: the search runs in class 6) 15 access: distinct pages + trace
  *  16 access: find_remove + semantics    17 access: P2C remap
  *  18 access: PRF pairs, rows, grouping keys
  * ms[c] sums the event-timed durations of the spans[c] launches (or phases)

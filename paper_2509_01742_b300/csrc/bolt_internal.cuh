@@ -293,7 +293,7 @@ enum ProfClass : int {
   P_P2C = 3,          // build: all P2C / position-map rounds
   P_KEYCHECK = 4,     // build: key-uniqueness check
   P_ACCESS = 5,       // one whole access batch
-  P_GATHER = 6,       // access: page read + decrypt
+  P_GATHER = 6,       // access: position-map search + page reads + decrypt
   P_EVICT = 7,        // access: write-back with eviction
   P_BUILD = 8,        // one whole build
   P_GROUP = 9,        // access: batch grouping sort + scans
@@ -301,7 +301,7 @@ enum ProfClass : int {
   P_KSORT_TILE = 11,    // key-uniqueness check: bitonic in-tile steps
   P_FLUSH = 12,         // access: written pages copied to the host
   P_AHEAD = 13,         // access: lookahead search + page reads (side stream)
-  P_LOOKUP = 14,        // access: position-map search
+  P_LOOKUP = 14,        // (unused: the search is fused with the page reads, P_GATHER)
   P_PAGES = 15,         // access: distinct pages, trace
   P_FINDEXEC = 16,      // access: find_remove + Get/Put/Delete semantics
   P_REMAP = 17,         // access: P2C remap
