@@ -421,6 +421,17 @@ static void page_store(omap_t* m, uint64_t q, tuple_t* t, uint32_t cnt, uint64_t
   free(buf);
 }
 
+void oracle_kdf(uint64_t seed, uint32_t kprf[8], uint32_t kenc[8]) {
+  derive_keys(seed, kprf, kenc);
+}
+
+void oracle_page_decrypt(const uint32_t kenc[8], uint64_t q, uint64_t version,
+                         const uint8_t* in, uint8_t* out, uint64_t page_bytes) {
+  uint32_t nonce[3] = {(uint32_t)q, (uint32_t)version, (uint32_t)(version >> 32)};
+  if (out != in) memmove(out, in, page_bytes);
+  oracle_chacha20_xor(kenc, 0, nonce, out, page_bytes);
+}
+
 int oracle_decrypt_page(const omap_t* m, uint64_t q, uint8_t* out) {
   if (!m || !m->initialized || q >= m->p.M) return ORC_E_ARG;
   memcpy(out, m->pages + q * m->p.page_bytes, m->p.page_bytes);

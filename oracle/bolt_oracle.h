@@ -108,6 +108,13 @@ int oracle_sizing(uint64_t N, uint32_t c, double alpha, uint32_t val_bytes,
                   oracle_info_t* out);
 int oracle_pair(const uint32_t kprf[8], uint32_t dom, uint64_t x, uint64_t B,
                 uint32_t* b1, uint32_t* b2);
+/* the two working keys derived from a seed, as bolt_init derives them */
+void oracle_kdf(uint64_t seed, uint32_t kprf[8], uint32_t kenc[8]);
+/* decrypt one page ciphertext of page_bytes taken from page q at `version`
+ * under K_enc (in and out may alias) -- for checking sampled pages of maps
+ * too large to rebuild here */
+void oracle_page_decrypt(const uint32_t kenc[8], uint64_t q, uint64_t version,
+                         const uint8_t* in, uint8_t* out, uint64_t page_bytes);
 
 #ifdef __cplusplus
 }

@@ -92,6 +92,10 @@ def lib():
         L.oracle_chacha20_xor.restype = None
         L.oracle_sizing.argtypes = [u64, u32, ctypes.c_double, u32, ctypes.POINTER(Info)]
         L.oracle_pair.argtypes = [P, u32, u64, u64, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        L.oracle_kdf.argtypes = [u64, P, P]
+        L.oracle_kdf.restype = None
+        L.oracle_page_decrypt.argtypes = [P, u64, u64, P, P, u64]
+        L.oracle_page_decrypt.restype = None
         _lib = L
     return _lib
 
@@ -122,6 +126,23 @@ def sizing(N: int, c: int, alpha: float, val_bytes: int) -> dict:
     if rc:
         raise ValueError(f"oracle_sizing rc={rc}")
     return o.as_dict()
+
+
+def kdf(seed: int):
+    """(K_prf, K_enc) derived from a map seed, 8 uint32 words each."""
+    kprf = np.zeros(8, dtype=np.uint32)
+    kenc = np.zeros(8, dtype=np.uint32)
+    lib().oracle_kdf(seed, _ptr(kprf), _ptr(kenc))
+    return kprf, kenc
+
+
+def page_decrypt(kenc_words, q: int, version: int, ciphertext: np.ndarray) -> np.ndarray:
+    """Plaintext of page q's ciphertext at `version` under K_enc."""
+    k = np.ascontiguousarray(kenc_words, dtype=np.uint32)
+    c = np.ascontiguousarray(ciphertext, dtype=np.uint8)
+    out = np.empty_like(c)
+    lib().oracle_page_decrypt(_ptr(k), q, version, _ptr(c), _ptr(out), c.size)
+    return out
 
 
 def pair(kprf_words, dom: int, x: int, B: int):

@@ -420,3 +420,20 @@ def test_dupkey_and_overflow_poison():
     assert rc2 == O.E_STATE
     assert m.init(keys, vals, 2) == 0  # re-init clears the poison
     m.close()
+
+
+def test_standalone_kdf_and_page_codec_match_a_built_map():
+    """oracle.kdf / oracle.page_decrypt (used to check sampled pages of maps
+    too large for the oracle to build) agree with an oracle map's own keys and
+    page decryption."""
+    N, vb, seed = 1 << 10, 8, 0x1234567
+    keys, vals = W.records(N, vb, 3)
+    o = O.OracleMap(N, vb)
+    assert o.init(keys, vals, seed) == 0
+    kprf, kenc = O.kdf(seed)
+    k2 = o.keys()
+    assert np.array_equal(kprf, k2[0]) and np.array_equal(kenc, k2[1])
+    pages = o.pages()
+    for q in (0, 1, o.info()["M"] - 1):
+        assert np.array_equal(O.page_decrypt(kenc, q, 0, pages[q]), o.decrypt_page(q))
+    o.close()
