@@ -208,6 +208,8 @@ class BoltMap:
     def init(self, keys: np.ndarray, vals: np.ndarray, seed: int) -> int:
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
         vals = np.ascontiguousarray(vals, dtype=np.uint8)
+        if vals.size != len(keys) * self.vb:
+            raise ValueError(f"{len(keys)} keys need {len(keys) * self.vb} value bytes")
         return bolt_init(self._h, _np_ptr(keys), _np_ptr(vals), len(keys), seed)
 
     def access(self, ops, keys, vals_in):
@@ -215,6 +217,8 @@ class BoltMap:
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
         vin = np.ascontiguousarray(vals_in, dtype=np.uint8)
         n = len(ops)
+        if len(keys) != n or vin.size != n * self.vb:
+            raise ValueError(f"array sizes do not match {n} ops of {self.vb}-byte values")
         vout = np.zeros((n, self.vb), dtype=np.uint8)
         status = np.zeros(n, dtype=np.uint8)
         rc = bolt_access(self._h, _np_ptr(ops), _np_ptr(keys), _np_ptr(vin), _np_ptr(vout),
@@ -223,11 +227,29 @@ class BoltMap:
 
     # --- device-pointer calls (torch CUDA tensors) --------------------------
     def init_device(self, keys, vals, seed: int, stream=None) -> int:
+        if keys.element_size() != 8 or vals.element_size() != 1 or \
+                vals.numel() != keys.numel() * self.vb:
+            raise ValueError("keys must be 8-byte, values uint8 of n * val_bytes")
         s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
         return bolt_init_device(self._h, ctypes.c_void_p(keys.data_ptr()),
                                 ctypes.c_void_p(vals.data_ptr()), keys.numel(), seed, s)
 
+    def _check_io(self, ops, keys, vals_in, vals_out, status):
+        n = ops.numel()
+        vb = self.vb
+        if keys.numel() != n or vals_in.numel() != n * vb or vals_out.numel() != n * vb or \
+                (status is not None and status.numel() != n):
+            raise ValueError(f"array sizes do not match {n} ops of {vb}-byte values")
+        if ops.element_size() != 1 or keys.element_size() != 8 or \
+                vals_in.element_size() != 1 or vals_out.element_size() != 1 or \
+                (status is not None and status.element_size() != 1):
+            raise ValueError("ops, values and status are bytes; keys are 8-byte integers")
+        for t in (ops, keys, vals_in, vals_out) + ((status,) if status is not None else ()):
+            if not t.is_contiguous():
+                raise ValueError("arrays must be contiguous")
+
     def access_device(self, ops, keys, vals_in, vals_out, status=None, stream=None) -> int:
+        self._check_io(ops, keys, vals_in, vals_out, status)
         s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
         st = ctypes.c_void_p(status.data_ptr()) if status is not None else ctypes.c_void_p(0)
         return bolt_access_device(self._h, ctypes.c_void_p(ops.data_ptr()),
@@ -238,6 +260,7 @@ class BoltMap:
     def access_device_batches(self, ops, keys, vals_in, vals_out, status, width: int = 0,
                               stream=None) -> int:
         """Consecutive batches of `width` ops over device tensors (one call)."""
+        self._check_io(ops, keys, vals_in, vals_out, status)
         s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
         return bolt_access_device_batches(self._h, ctypes.c_void_p(ops.data_ptr()),
                                           ctypes.c_void_p(keys.data_ptr()),

@@ -84,7 +84,8 @@ def test_full_size_headline_map_sampled():
 
     # Get / Put in the benchmark's launch configuration
     n = 2 * batch
-    gidx = idx[:batch]
+    gidx = rng.choice(N, size=batch, replace=False).astype(np.uint64)
+    gvals = d_vals[torch.from_numpy(gidx.astype(np.int64)).cuda()].cpu().numpy()
     pidx = rng.choice(N, size=batch, replace=False).astype(np.uint64)
     newv = rng.integers(0, 256, size=(batch, vb), dtype=np.uint8)
     ops = np.concatenate([np.zeros(batch, np.uint8), np.ones(batch, np.uint8)])
@@ -96,7 +97,7 @@ def test_full_size_headline_map_sampled():
     assert m.access_device_batches(t[0], t[1], t[2], out, st, batch) == 0
     assert m.sync() == 0
     assert st.cpu().numpy().all()
-    assert np.array_equal(out[:batch].cpu().numpy(), vals[:batch])
+    assert np.array_equal(out[:batch].cpu().numpy(), gvals)
     assert not out[batch:].cpu().numpy().any()  # PUT responses are zero
     # the new values are read back
     ops2 = np.zeros(batch, np.uint8)
