@@ -44,7 +44,7 @@ BATCH = 4096
 SEED_DATA = 0x5EED0003
 SEED_OPS = 0x5EED0103
 SEED_MAP = 0x5EED0203
-def config_for(log_n: int, n_acc: int) -> dict:
+def config_for(log_n: int, n_acc: int, lookahead: bool = False) -> dict:
     """The workload description of a headline-shaped run (N = 2^log_n)."""
     N = 1 << log_n
     tag_gib = 8 * N / 2**30
@@ -60,6 +60,7 @@ def config_for(log_n: int, n_acc: int) -> dict:
         "alpha": 0.2,
         "l2": (f"inputs larger than L2 ({N * 32 / 2**30:.3g} GiB records, {tag_gib:.3g} GiB of "
                "sort tags, pages and position map larger still)"),
+        "lookahead": lookahead,
     }
 
 
@@ -438,7 +439,7 @@ def run_bolt(args) -> None:
         "vs_baseline": None,
         "dtype": "u8/u64 (integer; ChaCha20 ARX)",
         "data": "synthetic (seeded; keys = bijective mix of the record index, random values)",
-        "config": dict(config_for(args.log_n, n_acc), lookahead=bool(args.lookahead)),
+        "config": config_for(args.log_n, n_acc, bool(args.lookahead)),
         "build": {"value": round(agg["records"] / agg["build_s"] / 1e6, 2), "unit": "Mrec/s",
                   "ms_per_build": round(build_s / args.steps * 1e3, 2)},
         "roofline": roofline,
