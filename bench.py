@@ -44,7 +44,7 @@ BATCH = 4096
 SEED_DATA = 0x5EED0003
 SEED_OPS = 0x5EED0103
 SEED_MAP = 0x5EED0203
-def config_for(log_n: int, n_acc: int, lookahead: bool = False) -> dict:
+def config_for(log_n: int, n_acc: int, lookahead: float = 0.0) -> dict:
     """The workload description of a headline-shaped run (N = 2^log_n)."""
     N = 1 << log_n
     tag_gib = 8 * N / 2**30
@@ -439,7 +439,7 @@ def run_bolt(args) -> None:
         "vs_baseline": None,
         "dtype": "u8/u64 (integer; ChaCha20 ARX)",
         "data": "synthetic (seeded; keys = bijective mix of the record index, random values)",
-        "config": config_for(args.log_n, n_acc, bool(args.lookahead)),
+        "config": config_for(args.log_n, n_acc, args.lookahead),
         "build": {"value": round(agg["records"] / agg["build_s"] / 1e6, 2), "unit": "Mrec/s",
                   "ms_per_build": round(build_s / args.steps * 1e3, 2)},
         "roofline": roofline,
@@ -784,8 +784,9 @@ def main():
     ap.add_argument("--accesses", type=int, default=N_ACCESS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--lookahead", type=int, default=0,
-                    help="1 = read each batch's pages while the previous batch runs")
+    ap.add_argument("--lookahead", type=float, default=0.0,
+                    help="share of each batch's pages read while the previous batch "
+                         "finishes (0 = off)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "bolt" and args.config == "headline":
         print("note: at least 3 warm-up steps are required for a valid number", file=sys.stderr)

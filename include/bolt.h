@@ -80,9 +80,10 @@ typedef struct bolt bolt_t;
 #define BOLT_PARAM_PROFILE 8 /* 1 = time kernel classes with CUDA events */
 #define BOLT_PARAM_BATCH_CAP 9 /* capacity of the device batch buffers, 1..BOLT_MAX_BATCH
                                   (default BOLT_MAX_BATCH); reallocates, drops contents */
-#define BOLT_PARAM_LOOKAHEAD 10 /* 1 = bolt_access_device_batches reads a batch's
-                                   pages while the previous batch runs (default 0);
-                                   results are the same either way */
+#define BOLT_PARAM_LOOKAHEAD 10 /* share in [0, 1] of each batch's predicted host pages
+                                   that bolt_access_device_batches reads ahead, while
+                                   the previous batch finishes (default 0 = off);
+                                   results are the same for every value */
 
 /* derived parameters (Sec. 3.3 sizing, Sec. 4.2 position map) */
 typedef struct {

@@ -270,7 +270,10 @@ __device__ __forceinline__ uint32_t la_find(const BatchDev& b, uint32_t q) {
   uint32_t h = ht_hash(q, b.ht_mask);
   for (uint32_t probe = 0; probe <= b.ht_mask; probe++) {
     const uint32_t k = b.la_key[h];
-    if (k == q) return b.la_idx[h];
+    if (k == q) {
+      const uint32_t e = b.la_idx[h];
+      return e < b.la_limit ? e : NONE32;  // queued beyond the limit: not read
+    }
     if (k == NONE32) return NONE32;
     h = (h + 1) & b.ht_mask;
   }
@@ -346,8 +349,8 @@ constexpr uint32_t LINK_BLOCKS = LINK_WARPS * 32 / COPY_BLOCK;
 // one batch time.  A warp writes a page per ~1.2 us, a 4096-op batch (~6.5 k
 // host pages at N = 2^28) takes ~220 us, so about one warp per 160 read
 // positions (2 per op), between 16 and 192 warps.
-__host__ __device__ __forceinline__ uint32_t flush_blocks(uint32_t n) {
-  uint32_t w = 2 * n / 160;
+__host__ __device__ __forceinline__ uint32_t flush_blocks(uint32_t n, int fast) {
+  uint32_t w = 2 * n / (fast ? 80 : 160);
   w = w < 16 ? 16 : (w > 192 ? 192 : w);
   return (w * 32 + COPY_BLOCK - 1) / COPY_BLOCK;
 }
@@ -355,11 +358,13 @@ __host__ __device__ __forceinline__ uint32_t flush_blocks(uint32_t n) {
 // the pages queued ahead, one 512-byte chunk per warp step: host read +
 // decryption into la_buf.  Pages the previous batch rewrites may be read torn
 // here; the main gather takes those from the previous batch's ciphertexts.
-__global__ void __launch_bounds__(COPY_BLOCK) k_ahead_gather(MapDev m, BatchDev b) {
+__global__ void __launch_bounds__(COPY_BLOCK) k_ahead_gather(MapDev m, BatchDev b,
+                                                             uint32_t limit) {
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   const uint32_t nch = (m.page_bytes + 511) / 512;
-  const uint32_t items = *b.la_count * nch;
+  const uint32_t cnt = *b.la_count;
+  const uint32_t items = (cnt < limit ? cnt : limit) * nch;
   for (uint32_t it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nw) {
     const uint32_t e = it / nch, c = (it % nch) * 512, off = c + 16 * lane;
     const uint64_t q = b.la_list[e];
@@ -1172,14 +1177,22 @@ cudaError_t launch_prep(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_ahead(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st) {
+cudaError_t launch_ahead_lookup(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   ProfSpan ps(P_AHEAD, st);
   k_clear_la<<<64, 256, 0, st>>>(b);
   const uint32_t warp_blocks = (n * 32 + 255) / 256;
   k_ahead_lookup<<<warp_blocks, 256, 0, st>>>(m, b, n);
-  k_ahead_gather<<<LINK_BLOCKS, COPY_BLOCK, 0, st>>>(m, b);
-  count_launch(3);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ahead_gather(const MapDev& m, const BatchDev& b, uint32_t limit,
+                                cudaStream_t st) {
+  if (limit == 0) return cudaSuccess;
+  ProfSpan ps(P_AHEAD, st);
+  k_ahead_gather<<<LINK_BLOCKS, COPY_BLOCK, 0, st>>>(m, b, limit);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -1214,6 +1227,7 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
       count_launch(3);
     }
   }
+  if (fc.ev_looked) cudaEventRecord(fc.ev_looked, st);
   {
     ProfSpan ps(P_FINDEXEC, st);
     e = launch_dependent(k_find, warp_blocks, 256, 0, st, m, b, n);
@@ -1247,7 +1261,7 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
   cudaStreamWaitEvent(fc.flush_st, fc.ev_evicted, 0);
   {
     ProfSpan ps(P_FLUSH, fc.flush_st);
-    k_flush<<<flush_blocks(n), COPY_BLOCK, 0, fc.flush_st>>>(m, b);
+    k_flush<<<flush_blocks(n, fc.fast_flush), COPY_BLOCK, 0, fc.flush_st>>>(m, b);
     count_launch();
   }
   cudaEventRecord(fc.ev_flushed, fc.flush_st);

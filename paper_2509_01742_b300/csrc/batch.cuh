@@ -60,7 +60,7 @@ struct BatchDev {
   // lookahead: while the previous batch runs, leaders whose key is not in it
   // search the position map, and the pages of every read position whose bin
   // is then known are read and decrypted ahead
-  uint32_t la_on, la_pad;
+  uint32_t la_on, la_limit;  // la_limit: queued pages read ahead (the first ones)
   uint8_t* done;       // [cap] leader searched ahead (its hit is in hit[])
   uint32_t* la_key;    // [ht_mask + 1] page read ahead, or NONE
   uint32_t* la_idx;    // [ht_mask + 1] its row in la_buf
@@ -92,15 +92,23 @@ struct FlushCtx {
   cudaStream_t flush_st;
   cudaEvent_t ev_evicted;
   cudaEvent_t ev_flushed;
+  cudaEvent_t ev_looked;   // recorded on st once the batch's page reads are done
+  int fast_flush;          // 1: the write-back may use twice the warps
 };
 
 cudaError_t launch_prep(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
                         cudaStream_t st);
 cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st,
                         const FlushCtx& fc);
-// The lookahead part of a batch (b.la_on = 1), after its preparation: may
-// run while the previous batch's main part runs, once the flush two batches
-// back has landed.
-cudaError_t launch_ahead(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st);
+// The lookahead part of a batch (b.la_on = 1), after its preparation:
+// launch_ahead_lookup searches the position map for the leaders whose key
+// the previous batch does not touch and queues the pages it can predict; it
+// may run while the previous batch's main part runs.  launch_ahead_gather
+// reads and decrypts the first `limit` queued pages; it runs once the
+// previous batch's own page reads are done and the flush two batches back
+// has landed.
+cudaError_t launch_ahead_lookup(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st);
+cudaError_t launch_ahead_gather(const MapDev& m, const BatchDev& b, uint32_t limit,
+                                cudaStream_t st);
 
 }  // namespace bdev

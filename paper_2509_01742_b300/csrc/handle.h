@@ -24,7 +24,7 @@ struct bolt {
   uint64_t trace_cap = 1ull << 22;
   bool trace_on = false;
   bool check_keys = true;
-  bool lookahead = false;     // BOLT_PARAM_LOOKAHEAD
+  double la_frac = 0.0;       // BOLT_PARAM_LOOKAHEAD: share of a batch's pages read ahead
   bolt_info_t info{};
 
   bdev::MapDev m{};
@@ -103,6 +103,7 @@ struct bolt {
   } s_prep[2];
   cudaStream_t st_prep = nullptr;
   cudaEvent_t ev_in = nullptr, ev_prep[2] = {nullptr, nullptr}, ev_pfree[2] = {nullptr, nullptr};
+  cudaEvent_t ev_looked[2] = {nullptr, nullptr};  // a slot's batch finished its page reads
 };
 
 

@@ -134,7 +134,8 @@ void destroy_streams(bolt* h) {
   for (cudaEvent_t* ev : {&h->ev_fork, &h->ev_join, &h->ev_evicted[0], &h->ev_evicted[1],
                           &h->ev_flushed[0], &h->ev_flushed[1], &h->ev_in, &h->ev_prep[0],
                           &h->ev_prep[1], &h->ev_pfree[0], &h->ev_pfree[1], &h->ev_h2d[0],
-                          &h->ev_h2d[1], &h->ev_d2h[0], &h->ev_d2h[1]})
+                          &h->ev_h2d[1], &h->ev_d2h[0], &h->ev_d2h[1], &h->ev_looked[0],
+                          &h->ev_looked[1]})
     if (*ev) {
       cudaEventDestroy(*ev);
       *ev = nullptr;
@@ -369,6 +370,7 @@ BatchDev slot_view(bolt* h, BatchDev b, uint32_t n, int s) {
   b.la_count = p.la_count;
   b.la_buf = p.la_buf;
   b.la_on = 0;
+  b.la_limit = 0;
   b.ht_key = h->s_ht_key[s];
   b.ht_min = h->s_ht_min[s];
   b.dbuf = h->s_dbuf[s];
@@ -388,13 +390,15 @@ BatchDev slot_view(bolt* h, BatchDev b, uint32_t n, int s) {
 // The main part of a batch in the current slot, on stream st, once its
 // preparation has been enqueued (on st, or on st_prep with st waiting for it):
 // waits for the flush that last used the slot, launches, flips the slot.
-cudaError_t main_batch(bolt* h, const BatchDev& b, uint32_t n, cudaStream_t st) {
+cudaError_t main_batch(bolt* h, const BatchDev& b, uint32_t n, cudaStream_t st,
+                       bool lookahead = false) {
   const int s = h->slot;
   if (h->flush_pending[s]) {
     cudaError_t e = cudaStreamWaitEvent(st, h->ev_flushed[s], 0);
     if (e != cudaSuccess) return e;
   }
-  FlushCtx fc{h->st_fl, h->ev_evicted[s], h->ev_flushed[s]};
+  FlushCtx fc{h->st_fl, h->ev_evicted[s], h->ev_flushed[s],
+              lookahead ? h->ev_looked[s] : nullptr, lookahead ? 1 : 0};
   cudaError_t e = launch_main(h->m, b, n, st, fc);
   if (e != cudaSuccess) return e;
   h->flush_pending[s] = true;
@@ -447,6 +451,10 @@ cudaError_t access_batches(bolt* h, BatchDev b, uint64_t n, uint32_t w, cudaStre
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->st_prep, h->ev_in, 0);
   if (e != cudaSuccess) return e;
   const uint64_t t_start = h->t;
+  const bool la = h->la_frac > 0.0;
+  auto la_limit = [&](uint32_t cnt) {
+    return (uint32_t)(h->la_frac * 2.0 * cnt + 0.5);
+  };
   auto prep = [&](uint64_t j, int s) -> cudaError_t {
     uint32_t cnt = 0;
     const BatchDev x = slice(j, cnt);
@@ -456,15 +464,18 @@ cudaError_t access_batches(bolt* h, BatchDev b, uint64_t n, uint32_t w, cudaStre
       if (pe != cudaSuccess) return pe;
     }
     cudaError_t pe = launch_prep(h->m, v, cnt, t_start + j * w, h->st_prep);
-    if (pe == cudaSuccess && h->lookahead && j >= 1) {
-      // lookahead against batch j - 1 (its key table is in the other slot);
-      // host pages are current once the flush two batches back has landed
+    if (pe == cudaSuccess && la && j >= 1) {
+      // lookahead against batch j - 1 (its key table is in the other slot):
+      // the position-map search runs at once; the page reads wait until
+      // batch j - 1's own page reads are done (they then overlap its
+      // find/exec/evict/remap) and the flush two batches back has landed
       uint32_t pc = 0;
       const BatchDev px = slice(j - 1, pc);
       uint32_t kt = 128;
       while (kt < 2 * pc) kt <<= 1;
       const bolt::PrepSet& pp = h->s_prep[s ^ 1];
       v.la_on = 1;
+      v.la_limit = la_limit(cnt);
       v.prev_kt_own = pp.kt_own;
       v.prev_keys = px.keys;
       v.prev_ops = px.ops;
@@ -473,29 +484,34 @@ cudaError_t access_batches(bolt* h, BatchDev b, uint64_t n, uint32_t w, cudaStre
       v.prev_rpair = pp.rpair;
       v.prev_pres = pp.pres;
       v.prev_kt_mask = kt - 1;
-      if (h->flush_pending[s]) pe = cudaStreamWaitEvent(h->st_prep, h->ev_flushed[s], 0);
-      if (pe == cudaSuccess) pe = launch_ahead(h->m, v, cnt, h->st_prep);
+      pe = launch_ahead_lookup(h->m, v, cnt, h->st_prep);
+      if (pe == cudaSuccess) pe = cudaStreamWaitEvent(h->st_prep, h->ev_looked[s ^ 1], 0);
+      if (pe == cudaSuccess && h->flush_pending[s])
+        pe = cudaStreamWaitEvent(h->st_prep, h->ev_flushed[s], 0);
+      if (pe == cudaSuccess) pe = launch_ahead_gather(h->m, v, v.la_limit, h->st_prep);
     }
     if (pe == cudaSuccess) pe = cudaEventRecord(h->ev_prep[s], h->st_prep);
     return pe;
   };
+  // batch j's main part is enqueued before batch j + 1's preparation, so that
+  // the lookahead's wait binds to batch j's page reads (the streams still run
+  // the two side by side)
   e = prep(0, h->slot);
   for (uint64_t j = 0; j < nb && e == cudaSuccess; j++) {
     const int s = h->slot;
-    if (j + 1 < nb) e = prep(j + 1, s ^ 1);
-    if (e != cudaSuccess) break;
     e = cudaStreamWaitEvent(st, h->ev_prep[s], 0);
     if (e != cudaSuccess) break;
     uint32_t cnt = 0;
     const BatchDev x = slice(j, cnt);
     BatchDev v = slot_view(h, x, cnt, s);
-    v.la_on = h->lookahead && j >= 1 ? 1u : 0u;
-    e = main_batch(h, v, cnt, st);
+    v.la_on = la && j >= 1 ? 1u : 0u;
+    v.la_limit = la_limit(cnt);
+    e = main_batch(h, v, cnt, st, la);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_pfree[s], st);
-    if (e == cudaSuccess) {
-      h->t += cnt;
-      h->batches++;
-    }
+    if (e != cudaSuccess) break;
+    h->t += cnt;
+    h->batches++;
+    if (j + 1 < nb) e = prep(j + 1, s ^ 1);
   }
   return e;
 }
@@ -648,7 +664,8 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_prep, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
   for (int s = 0; s < 2 && e == cudaSuccess; s++) {
-    e = cudaEventCreateWithFlags(&h->ev_h2d[s], cudaEventDisableTiming);
+    e = cudaEventCreateWithFlags(&h->ev_looked[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_h2d[s], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_d2h[s], cudaEventDisableTiming);
   }
   for (int s = 0; s < 2 && e == cudaSuccess; s++) {
@@ -725,7 +742,8 @@ int bolt_set_param(bolt_t* h, int which, double v) {
       h->batch_width = (uint32_t)v;
       return BOLT_OK;
     case BOLT_PARAM_LOOKAHEAD:
-      h->lookahead = v != 0.0;
+      if (!(v >= 0.0 && v <= 1.0)) return BOLT_E_ARG;
+      h->la_frac = v;
       return BOLT_OK;
     case BOLT_PARAM_BATCH_CAP:
       if (!(v >= 1.0 && v <= (double)MAXB)) return BOLT_E_ARG;

@@ -243,7 +243,7 @@ def test_device_batches_back_to_back_match_oracle():
     o.close(); g.close()
 
 
-@pytest.mark.parametrize("lookahead", [0, 1])
+@pytest.mark.parametrize("lookahead", [0, 0.3, 1])
 def test_device_batches_call_matches_oracle(lookahead):
     """bolt_access_device_batches (the next batch's preparation, and with
     lookahead its position-map search and page reads, run ahead on an
