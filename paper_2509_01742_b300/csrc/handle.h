@@ -56,6 +56,7 @@ struct bolt {
     uint8_t* status = nullptr;
   } h_io[2], d_io2;
   cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_d2h[2] = {nullptr, nullptr};
+  cudaEvent_t ev_ioready[2] = {nullptr, nullptr};  // a chunk's batches are done
   uint32_t* d_kdf = nullptr;
   uint32_t* d_flag = nullptr;
 
@@ -102,6 +103,7 @@ struct bolt {
     uint8_t* la_buf = nullptr;
   } s_prep[2];
   cudaStream_t st_prep = nullptr;
+  cudaStream_t st_out = nullptr;  // bolt_access: device-to-host result copies
   cudaEvent_t ev_in = nullptr, ev_prep[2] = {nullptr, nullptr}, ev_pfree[2] = {nullptr, nullptr};
   cudaEvent_t ev_looked[2] = {nullptr, nullptr};  // a slot's batch finished its page reads
 };

@@ -76,7 +76,7 @@ int cuda_fail(cudaError_t e) {
 cudaError_t sync_all(bolt* h) {
   cudaError_t e = cudaSuccess;
   if (h->last_st && h->last_st != h->st) e = cudaStreamSynchronize(h->last_st);
-  for (cudaStream_t s : {h->st, h->st2, h->st_fl, h->st_prep}) {
+  for (cudaStream_t s : {h->st, h->st2, h->st_fl, h->st_prep, h->st_out}) {
     if (!s) continue;
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = e2;
@@ -135,12 +135,12 @@ void destroy_streams(bolt* h) {
                           &h->ev_flushed[0], &h->ev_flushed[1], &h->ev_in, &h->ev_prep[0],
                           &h->ev_prep[1], &h->ev_pfree[0], &h->ev_pfree[1], &h->ev_h2d[0],
                           &h->ev_h2d[1], &h->ev_d2h[0], &h->ev_d2h[1], &h->ev_looked[0],
-                          &h->ev_looked[1]})
+                          &h->ev_looked[1], &h->ev_ioready[0], &h->ev_ioready[1]})
     if (*ev) {
       cudaEventDestroy(*ev);
       *ev = nullptr;
     }
-  for (cudaStream_t* s : {&h->st_prep, &h->st_fl, &h->st2, &h->st})
+  for (cudaStream_t* s : {&h->st_out, &h->st_prep, &h->st_fl, &h->st2, &h->st})
     if (*s) {
       cudaStreamDestroy(*s);
       *s = nullptr;
@@ -662,9 +662,11 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_fl, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_prep, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_out, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
   for (int s = 0; s < 2 && e == cudaSuccess; s++) {
     e = cudaEventCreateWithFlags(&h->ev_looked[s], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_ioready[s], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_h2d[s], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_d2h[s], cudaEventDisableTiming);
   }
@@ -890,14 +892,19 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
   if (!h->initialized || h->poisoned) return BOLT_E_STATE;
   if (n == 0) return BOLT_OK;
   if (!ops || !keys || !vals_in || !vals_out) return BOLT_E_ARG;
-  for (uint64_t i = 0; i < n; i++)
-    if (ops[i] > BOLT_DEL) return BOLT_E_ARG;
+  uint8_t bad = 0;
+  for (uint64_t i = 0; i < n; i++) bad |= (uint8_t)(ops[i] > BOLT_DEL);
+  if (bad) return BOLT_E_ARG;
   ProfScope prof_scope(h);
   const uint64_t vb = h->vb;
   const uint8_t* kin = static_cast<const uint8_t*>(keys);
   const uint8_t* vin = static_cast<const uint8_t*>(vals_in);
   uint8_t* vout = static_cast<uint8_t*>(vals_out);
   cudaStream_t st = h->st;
+  // host<->device copies run beside the batches on st: inputs on st2 (idle
+  // outside bolt_init), outputs on st_out, so chunk k + 1's inputs arrive and
+  // chunk k - 1's outputs leave while chunk k runs
+  cudaStream_t cs = h->st2, co = h->st_out;
   if (h->last_st != st) {
     if (h->last_st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
     h->last_st = st;
@@ -936,10 +943,13 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
       src_keys = hs.keys;
       src_vin = hs.vin;
     }
-    e = cudaMemcpyAsync(d.ops, src_ops, cnt, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d.keys, src_keys, cnt * 8, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d.vin, src_vin, cnt * vb, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaEventRecord(h->ev_h2d[k], st);
+    // the device set was last used by chunk k - 2: its batches and output copy
+    e = lo >= 2 * chunk ? cudaStreamWaitEvent(cs, h->ev_d2h[k], 0) : cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.ops, src_ops, cnt, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.keys, src_keys, cnt * 8, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d.vin, src_vin, cnt * vb, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_h2d[k], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_h2d[k], 0);
     if (e != cudaSuccess) break;
     BatchDev b = h->b;
     b.ops = d.ops;
@@ -948,13 +958,15 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
     b.vout = d.vout;
     b.status = d.status;
     e = access_batches(h, b, cnt, w, st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_ioready[k], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(co, h->ev_ioready[k], 0);
     if (e != cudaSuccess) break;
     uint8_t* dst_vout = pin_out ? vout + lo * vb : hs.vout;
     uint8_t* dst_st = pin_out && status_out ? status_out + lo : hs.status;
-    e = cudaMemcpyAsync(dst_vout, d.vout, cnt * vb, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(dst_vout, d.vout, cnt * vb, cudaMemcpyDeviceToHost, co);
     if (e == cudaSuccess && (status_out || !pin_out))
-      e = cudaMemcpyAsync(dst_st, d.status, cnt, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaEventRecord(h->ev_d2h[k], st);
+      e = cudaMemcpyAsync(dst_st, d.status, cnt, cudaMemcpyDeviceToHost, co);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_d2h[k], co);
     if (e != cudaSuccess) break;
     if (!pin_out) {
       // the previous chunk's outputs, while this one runs
