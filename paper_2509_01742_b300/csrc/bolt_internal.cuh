@@ -348,7 +348,7 @@ struct ProfSpan {
 // build.cu
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
                          struct BuildScratch& s, cudaStream_t st,
-                         cudaEvent_t sorted_ev = nullptr);  // recorded after the tag sort
+                         cudaEvent_t tags_wait = nullptr);  // waited on before the tags are written
 
 // sort.cu: ascending bitonic sort of n_pow2 uint64 tags in place; the
 // passes are profiled under the given classes

@@ -386,7 +386,7 @@ static int sm_count() {
 }
 
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
-                         BuildScratch& s, cudaStream_t st, cudaEvent_t sorted_ev) {
+                         BuildScratch& s, cudaStream_t st, cudaEvent_t tags_wait) {
   const int sms = sm_count();
   cudaMemsetAsync(s.counters, 0, 2 * sizeof(unsigned long long), st);
   // 1. P2C + position map, round by round
@@ -441,12 +441,12 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   k_scan_sums<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums);
   k_scan_top<<<1, SCAN_BLOCK, 0, st>>>(s.block_sums, nblocks);
   k_scan_fill<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums, s.page_off);
-  // 3. tags + bitonic sort
+  // 3. tags + bitonic sort (the tag buffer may have been lent out until now)
+  if (tags_wait) cudaStreamWaitEvent(st, tags_wait, 0);
   k_build_tags<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.tag_cap, s.tags);
   count_launch(4);
   cudaError_t e = sort_tags_u64(s.tags, s.tag_cap, s.log_tile, st);
   if (e != cudaSuccess) return e;
-  if (sorted_ev) cudaEventRecord(sorted_ev, st);
   // 4. pages
   uint32_t wpb = (uint32_t)(65536 / m.page_bytes);
   wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;

@@ -311,6 +311,40 @@ __global__ void k_copy_keys(const uint64_t* keys, uint64_t n, uint64_t n_pow2, u
        i += (uint64_t)gridDim.x * blockDim.x)
     out[i] = i < n ? keys[i] : ~0ull;
 }
+// keys must be distinct (Sec. 2.1), hashed variant: every key goes into an
+// open-addressing table of 2 * half slots (two buffers of `half`) by
+// compare-and-swap; a key met twice raises the flag.  A slot holds key ^ SALT
+// (0 = empty); the one key equal to SALT is counted apart in *salt_count.
+constexpr uint64_t DUP_SALT = 0x9E3779B97F4A7C15ull;
+__global__ void k_dup_insert(const uint64_t* keys, uint64_t n, uint64_t* t0, uint64_t* t1,
+                             uint64_t half, uint32_t* flag, unsigned long long* salt_count) {
+  const uint64_t mask = 2 * half - 1;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t k = keys[i];
+    const uint64_t e = k ^ DUP_SALT;
+    if (e == 0) {
+      if (atomicAdd(salt_count, 1ull) > 0) *flag = 1;
+      continue;
+    }
+    uint64_t h = k;
+    h ^= h >> 33; h *= 0xff51afd7ed558ccdull; h ^= h >> 33; h *= 0xc4ceb9fe1a85ec53ull;
+    h ^= h >> 33;
+    h &= mask;
+    for (uint64_t probe = 0; probe <= mask; probe++) {
+      unsigned long long* slot =
+          reinterpret_cast<unsigned long long*>(h < half ? t0 + h : t1 + (h - half));
+      const unsigned long long old = atomicCAS(slot, 0ull, (unsigned long long)e);
+      if (old == 0) break;
+      if (old == e) {
+        *flag = 1;
+        break;
+      }
+      h = (h + 1) & mask;
+    }
+  }
+}
+
 __global__ void k_adjacent_equal(const uint64_t* sorted, uint64_t n, uint32_t* flag) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n;
        i += (uint64_t)gridDim.x * blockDim.x)
@@ -563,9 +597,9 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     m.kenc[i] = kw[8 + i];
   }
   bs.log_tile = h->sort_log_tile;
-  // key uniqueness (Sec. 2.1): sort a copy of the keys, flag equal
-  // neighbours.  With a buffer of its own it runs on the side stream during
-  // the page build, which is bound by the host link, not by HBM or the SMs.
+  // key uniqueness (Sec. 2.1).  With the key-sort buffer available it is a
+  // hashed check on the side stream (below); otherwise a sorted copy of the
+  // keys in line, flagging equal neighbours.
   const bool check = h->check_keys && n > 1;
   const bool side = check && bs.keysort && h->st2;
   if (check) cudaMemsetAsync(h->d_flag, 0, 4, st);
@@ -583,15 +617,26 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     e = key_check(st, bs.tags);  // in line, before the build reuses `tags`
     if (e != cudaSuccess) return BOLT_E_CUDA;
   }
-  e = launch_build(m, d_keys, d_vals, n, bs, st, side ? h->ev_fork : nullptr);
-  if (e != cudaSuccess) return BOLT_E_CUDA;
   if (side) {
+    // hashed check on the side stream beside the PRF and P2C phases (bound by
+    // the ALU and by round latency, while this is random atomics in HBM); its
+    // table is the key-sort buffer plus the tag buffer, which the build
+    // writes only after the P2C rounds.  Beside the page build it would be
+    // slowed several times by the page stores in flight to the host.
+    ProfSpan ps(P_KEYCHECK, h->st2);
+    unsigned long long* salt_count = reinterpret_cast<unsigned long long*>(h->d_kdf + 2);
+    cudaEventRecord(h->ev_fork, st);
     cudaStreamWaitEvent(h->st2, h->ev_fork, 0);
-    e = key_check(h->st2, bs.keysort);
-    if (e != cudaSuccess) return BOLT_E_CUDA;
+    cudaMemsetAsync(bs.keysort, 0, bs.tag_cap * sizeof(uint64_t), h->st2);
+    cudaMemsetAsync(bs.tags, 0, bs.tag_cap * sizeof(uint64_t), h->st2);
+    cudaMemsetAsync(salt_count, 0, sizeof(unsigned long long), h->st2);
+    k_dup_insert<<<sms * 8, 256, 0, h->st2>>>(d_keys, n, bs.keysort, bs.tags, bs.tag_cap,
+                                               h->d_flag, salt_count);
+    count_launch();
     cudaEventRecord(h->ev_join, h->st2);
   }
-  if (side) cudaStreamWaitEvent(st, h->ev_join, 0);
+  e = launch_build(m, d_keys, d_vals, n, bs, st, side ? h->ev_join : nullptr);
+  if (e != cudaSuccess) return BOLT_E_CUDA;
   uint32_t err = 0;
   h->last_st = st;
   rc = read_err(h, &err);
