@@ -348,7 +348,8 @@ struct ProfSpan {
 // build.cu
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
                          struct BuildScratch& s, cudaStream_t st,
-                         cudaEvent_t tags_wait = nullptr);  // waited on before the tags are written
+                         cudaEvent_t tags_wait,  // waited on before the tags are written
+                         cudaStream_t side, cudaEvent_t side_fork, cudaEvent_t side_join);
 
 // sort.cu: ascending bitonic sort of n_pow2 uint64 tags in place; the
 // passes are profiled under the given classes

@@ -386,10 +386,12 @@ static int sm_count() {
 }
 
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
-                         BuildScratch& s, cudaStream_t st, cudaEvent_t tags_wait) {
+                         BuildScratch& s, cudaStream_t st, cudaEvent_t tags_wait,
+                         cudaStream_t side, cudaEvent_t side_fork, cudaEvent_t side_join) {
   const int sms = sm_count();
   cudaMemsetAsync(s.counters, 0, 2 * sizeof(unsigned long long), st);
   // 1. P2C + position map, round by round
+  bool deferred_place = false;
   {
     ProfSpan ps(P_P2C, st);
     bool done = false;
@@ -417,10 +419,9 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
         void* args[] = {&mm, &kp, &vp, &nn, &bp, &rp, &dp, &pp, &fp, &bar};
         if (cudaLaunchCooperativeKernel((const void*)k_build_rounds, dim3(blocks), dim3(256), args,
                                         0, st) == cudaSuccess) {
-          k_build_place<<<sms * 16, 256, 0, st>>>(m, keys, vals, n, s.bins, s.dest, s.prow,
-                                                  s.counters);
-          count_launch(2);
+          count_launch();
           done = true;
+          deferred_place = true;
         } else {
           cudaGetLastError();  // clear; fall back to one launch pair per round
         }
@@ -447,6 +448,23 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   count_launch(4);
   cudaError_t e = sort_tags_u64(s.tags, s.tag_cap, s.log_tile, st);
   if (e != cudaSuccess) return e;
+  // The position-map entries and HBM residents (k_build_place) are read by
+  // none of the steps that follow, so after the rounds kernel they are
+  // written on the side stream beside the page build, which is bound by the
+  // host link; the free ring needs their count and follows them.
+  if (deferred_place) {
+    cudaEventRecord(side_fork, st);
+    cudaStreamWaitEvent(side, side_fork, 0);
+    {
+      ProfSpan ps(P_P2C, side);
+      k_build_place<<<sms * 16, 256, 0, side>>>(m, keys, vals, n, s.bins, s.dest, s.prow,
+                                                 s.counters);
+      count_launch();
+    }
+    k_ring_fill<<<sms * 4, 256, 0, side>>>(m, s.counters);
+    count_launch();
+    cudaEventRecord(side_join, side);
+  }
   // 4. pages
   uint32_t wpb = (uint32_t)(65536 / m.page_bytes);
   wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;
@@ -465,8 +483,12 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
     count_launch();
   }
   // 5. free ring
-  k_ring_fill<<<sms * 4, 256, 0, st>>>(m, s.counters);
-  count_launch();
+  if (deferred_place) {
+    cudaStreamWaitEvent(st, side_join, 0);
+  } else {
+    k_ring_fill<<<sms * 4, 256, 0, st>>>(m, s.counters);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 

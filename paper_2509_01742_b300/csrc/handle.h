@@ -66,6 +66,7 @@ struct bolt {
   cudaStream_t last_st = nullptr;  // stream of the last enqueued work
   cudaStream_t st2 = nullptr;      // side stream (key-uniqueness check)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_pfork = nullptr, ev_pjoin = nullptr;  // build: placement on the side stream
   // access batches alternate between two buffer slots; a slot's written pages
   // reach the host on st_fl while the next batch runs
   cudaStream_t st_fl = nullptr;

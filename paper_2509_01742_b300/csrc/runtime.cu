@@ -135,7 +135,8 @@ void destroy_streams(bolt* h) {
                           &h->ev_flushed[0], &h->ev_flushed[1], &h->ev_in, &h->ev_prep[0],
                           &h->ev_prep[1], &h->ev_pfree[0], &h->ev_pfree[1], &h->ev_h2d[0],
                           &h->ev_h2d[1], &h->ev_d2h[0], &h->ev_d2h[1], &h->ev_looked[0],
-                          &h->ev_looked[1], &h->ev_ioready[0], &h->ev_ioready[1]})
+                          &h->ev_looked[1], &h->ev_ioready[0], &h->ev_ioready[1],
+                          &h->ev_pfork, &h->ev_pjoin})
     if (*ev) {
       cudaEventDestroy(*ev);
       *ev = nullptr;
@@ -635,7 +636,8 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     count_launch();
     cudaEventRecord(h->ev_join, h->st2);
   }
-  e = launch_build(m, d_keys, d_vals, n, bs, st, side ? h->ev_join : nullptr);
+  e = launch_build(m, d_keys, d_vals, n, bs, st, side ? h->ev_join : nullptr, h->st2,
+                   h->ev_pfork, h->ev_pjoin);
   if (e != cudaSuccess) return BOLT_E_CUDA;
   uint32_t err = 0;
   h->last_st = st;
@@ -705,6 +707,8 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pfork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_pjoin, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_fl, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_prep, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_out, cudaStreamNonBlocking);
