@@ -349,7 +349,10 @@ struct ProfSpan {
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
                          struct BuildScratch& s, cudaStream_t st,
                          cudaEvent_t tags_wait,  // waited on before the tags are written
-                         cudaStream_t side, cudaEvent_t side_fork, cudaEvent_t side_join);
+                         cudaStream_t side, cudaEvent_t side_fork, cudaEvent_t side_join,
+                         // pages built in HBM chunks and copied to the host on
+                         // copy_st (null: straight to the host); two events each
+                         cudaStream_t copy_st, cudaEvent_t* ev_built, cudaEvent_t* ev_copied);
 
 // sort.cu: ascending bitonic sort of n_pow2 uint64 tags in place; the
 // passes are profiled under the given classes

@@ -323,14 +323,18 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_fill(MapDev m, const uint32
 
 // One warp per host page: gather its run of sorted tags, order by key, pad
 // with zero dummies, encrypt under version 0, store.
+// Pages [q0, q1); each ciphertext goes to out + (q - q0) * page_bytes in HBM
+// when `out` is given (the copy engine moves the chunk to the host), else
+// straight to the host page.
 __global__ void k_page_build(MapDev m, const uint64_t* __restrict__ keys,
                              const uint8_t* __restrict__ vals, const uint64_t* __restrict__ tags,
-                             const uint32_t* __restrict__ page_off, uint32_t warps_per_block) {
+                             const uint32_t* __restrict__ page_off, uint32_t warps_per_block,
+                             uint64_t q0, uint64_t q1, uint8_t* out) {
   extern __shared__ __align__(16) uint8_t sbuf[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint8_t* plain = sbuf + (size_t)wid * m.page_bytes;
   const uint64_t stride = (uint64_t)gridDim.x * warps_per_block;
-  for (uint64_t q = (uint64_t)blockIdx.x * warps_per_block + wid; q < m.M; q += stride) {
+  for (uint64_t q = q0 + (uint64_t)blockIdx.x * warps_per_block + wid; q < q1; q += stride) {
     const uint32_t cnt = byte_get(m.load, m.K + q);
     const uint32_t off = page_off[q];
     uint64_t key = ~0ull;
@@ -361,7 +365,8 @@ __global__ void k_page_build(MapDev m, const uint64_t* __restrict__ keys,
         reinterpret_cast<uint64_t*>(slot + 8)[w] = vsrc[w];
     }
     __syncwarp();
-    page_encrypt_store(m, plain, q, 0);
+    page_encrypt_to(m, plain, out ? out + (q - q0) * m.page_bytes : m.pages + q * m.page_bytes, q,
+                    0);
     __syncwarp();
   }
 }
@@ -387,7 +392,8 @@ static int sm_count() {
 
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
                          BuildScratch& s, cudaStream_t st, cudaEvent_t tags_wait,
-                         cudaStream_t side, cudaEvent_t side_fork, cudaEvent_t side_join) {
+                         cudaStream_t side, cudaEvent_t side_fork, cudaEvent_t side_join,
+                         cudaStream_t copy_st, cudaEvent_t* ev_built, cudaEvent_t* ev_copied) {
   const int sms = sm_count();
   cudaMemsetAsync(s.counters, 0, 2 * sizeof(unsigned long long), st);
   // 1. P2C + position map, round by round
@@ -474,13 +480,43 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
                              (int)smem);
     if (e != cudaSuccess) return e;
   }
-  uint64_t blocks = (m.M + wpb - 1) / wpb;
-  uint64_t cap = (uint64_t)sms * 32;
+  const uint64_t cap = (uint64_t)sms * 32;
+  // With the candidate-row buffer free (it is read only by the rounds), pages
+  // are built into two halves of it in chunks and the copy engine moves each
+  // chunk to the host (pinned copies run faster than zero-copy stores, and
+  // hold no SM-side requests in flight); otherwise straight to the host.
+  const uint64_t stage_bytes = s.rows4 ? s.cap * sizeof(uint4) : 0;
+  const uint64_t chunk = stage_bytes / 2 / m.page_bytes;
+  const bool staged = copy_st && chunk >= (1u << 14);
   {
     ProfSpan ps(P_PAGE_BUILD, st);
-    k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
-        m, keys, vals, s.tags, s.page_off, wpb);
-    count_launch();
+    if (!staged) {
+      const uint64_t blocks = (m.M + wpb - 1) / wpb;
+      k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
+          m, keys, vals, s.tags, s.page_off, wpb, 0, m.M, nullptr);
+      count_launch();
+    } else {
+      uint8_t* stage = reinterpret_cast<uint8_t*>(s.rows4);
+      uint64_t c = 0;
+      for (uint64_t q0 = 0; q0 < m.M; q0 += chunk, c++) {
+        const uint64_t q1 = q0 + chunk < m.M ? q0 + chunk : m.M;
+        const int k = (int)(c & 1);
+        uint8_t* buf = stage + (uint64_t)k * chunk * m.page_bytes;
+        if (c >= 2) cudaStreamWaitEvent(st, ev_copied[k], 0);
+        const uint64_t blocks = (q1 - q0 + wpb - 1) / wpb;
+        k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
+            m, keys, vals, s.tags, s.page_off, wpb, q0, q1, buf);
+        count_launch();
+        cudaEventRecord(ev_built[k], st);
+        cudaStreamWaitEvent(copy_st, ev_built[k], 0);
+        e = cudaMemcpyAsync(m.pages + q0 * m.page_bytes, buf, (q1 - q0) * m.page_bytes,
+                            cudaMemcpyDefault, copy_st);
+        if (e != cudaSuccess) return e;
+        cudaEventRecord(ev_copied[k], copy_st);
+      }
+      // every chunk is on the host once the last copy on copy_st is done
+      if (c) cudaStreamWaitEvent(st, ev_copied[(c - 1) & 1], 0);
+    }
   }
   // 5. free ring
   if (deferred_place) {

@@ -636,8 +636,10 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     count_launch();
     cudaEventRecord(h->ev_join, h->st2);
   }
+  // the build's page chunks travel to the host on the write-back stream,
+  // with its two events (no write-back is pending during a build)
   e = launch_build(m, d_keys, d_vals, n, bs, st, side ? h->ev_join : nullptr, h->st2,
-                   h->ev_pfork, h->ev_pjoin);
+                   h->ev_pfork, h->ev_pjoin, h->st_fl, h->ev_evicted, h->ev_flushed);
   if (e != cudaSuccess) return BOLT_E_CUDA;
   uint32_t err = 0;
   h->last_st = st;
