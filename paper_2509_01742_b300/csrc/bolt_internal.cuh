@@ -366,10 +366,13 @@ struct BuildScratch {
   uint64_t* bins = nullptr;   // per record b1 | b2 << 32
   uint32_t* dest = nullptr;   // per record destination bin
   uint32_t* prow = nullptr;   // per record chosen position-map row
-  uint4* rows4 = nullptr;     // per record position-map candidate rows (optional:
-                              // without it the rounds compute them inline)
-  uint64_t* keysort = nullptr;  // key-uniqueness sort buffer [tag_cap] (optional:
-                                // without it the check reuses `tags` in line)
+  uint4* rows4 = nullptr;     // per record position-map candidate rows, then (after
+                              // the rounds) the two staging halves of the page build
+                              // (optional: without it the rounds compute the rows
+                              // inline and pages are stored straight to the host)
+  uint64_t* keysort = nullptr;  // [tag_cap] with `tags`, the key-uniqueness hash table
+                                // (optional: without it the check sorts a copy of the
+                                // keys in `tags`, in line)
   uint32_t* page_off = nullptr;  // [M + 1] exclusive prefix of page loads
   uint32_t* block_sums = nullptr;
   uint64_t block_cap = 0;
