@@ -370,9 +370,9 @@ struct BuildScratch {
                               // the rounds) the two staging halves of the page build
                               // (optional: without it the rounds compute the rows
                               // inline and pages are stored straight to the host)
-  uint64_t* keysort = nullptr;  // [tag_cap] with `tags`, the key-uniqueness hash table
-                                // (optional: without it the check sorts a copy of the
-                                // keys in `tags`, in line)
+  uint64_t* keysort = nullptr;  // [2 tag_cap] the key-uniqueness hash table (optional:
+                                // without it the check sorts a copy of the keys in
+                                // `tags`, in line)
   uint32_t* page_off = nullptr;  // [M + 1] exclusive prefix of page loads
   uint32_t* block_sums = nullptr;
   uint64_t block_cap = 0;

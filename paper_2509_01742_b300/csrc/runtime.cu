@@ -275,7 +275,7 @@ int grow_build_scratch(bolt* h, uint64_t n) {
   const uint64_t cap = n > 0 ? n : 1;
   cudaError_t e = cudaSuccess;
   e = e ? e : cudaMalloc(&s.tags, tag_cap * sizeof(uint64_t));
-  e = e ? e : cudaMalloc(&s.keysort, tag_cap * sizeof(uint64_t));
+  e = e ? e : cudaMalloc(&s.keysort, 2 * tag_cap * sizeof(uint64_t));
   e = e ? e : cudaMalloc(&s.rows4, cap * sizeof(uint4));
   e = e ? e : cudaMalloc(&s.bins, cap * sizeof(uint64_t));
   e = e ? e : cudaMalloc(&s.dest, cap * sizeof(uint32_t));
@@ -293,7 +293,7 @@ int grow_build_scratch(bolt* h, uint64_t n) {
   s.cap = cap;
   s.tag_cap = tag_cap;
   s.block_cap = nblocks;
-  h->scratch_bytes = tag_cap * 16 + cap * (16 + 8 + 4 + 4) + (h->info.M + 1) * 4 + nblocks * 4 + 16;
+  h->scratch_bytes = tag_cap * 24 + cap * (16 + 8 + 4 + 4) + (h->info.M + 1) * 4 + nblocks * 4 + 16;
   return BOLT_OK;
 }
 
@@ -618,29 +618,23 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     e = key_check(st, bs.tags);  // in line, before the build reuses `tags`
     if (e != cudaSuccess) return BOLT_E_CUDA;
   }
+  e = launch_build(m, d_keys, d_vals, n, bs, st, nullptr, h->st2, h->ev_pfork, h->ev_pjoin,
+                   h->st_fl, h->ev_evicted, h->ev_flushed);
+  if (e != cudaSuccess) return BOLT_E_CUDA;
   if (side) {
-    // hashed check on the side stream beside the PRF and P2C phases (bound by
-    // the ALU and by round latency, while this is random atomics in HBM); its
-    // table is the key-sort buffer plus the tag buffer, which the build
-    // writes only after the P2C rounds.  Beside the page build it would be
-    // slowed several times by the page stores in flight to the host.
+    // hashed check on the side stream after the placement, both beside the
+    // page build (its kernel waits on the copy engine; its host traffic goes
+    // through the copy engine, not through the SMs), in a table of its own
     ProfSpan ps(P_KEYCHECK, h->st2);
     unsigned long long* salt_count = reinterpret_cast<unsigned long long*>(h->d_kdf + 2);
-    cudaEventRecord(h->ev_fork, st);
-    cudaStreamWaitEvent(h->st2, h->ev_fork, 0);
-    cudaMemsetAsync(bs.keysort, 0, bs.tag_cap * sizeof(uint64_t), h->st2);
-    cudaMemsetAsync(bs.tags, 0, bs.tag_cap * sizeof(uint64_t), h->st2);
+    cudaMemsetAsync(bs.keysort, 0, 2 * bs.tag_cap * sizeof(uint64_t), h->st2);
     cudaMemsetAsync(salt_count, 0, sizeof(unsigned long long), h->st2);
-    k_dup_insert<<<sms * 8, 256, 0, h->st2>>>(d_keys, n, bs.keysort, bs.tags, bs.tag_cap,
-                                               h->d_flag, salt_count);
+    k_dup_insert<<<sms * 8, 256, 0, h->st2>>>(d_keys, n, bs.keysort, bs.keysort + bs.tag_cap,
+                                               bs.tag_cap, h->d_flag, salt_count);
     count_launch();
     cudaEventRecord(h->ev_join, h->st2);
+    cudaStreamWaitEvent(st, h->ev_join, 0);
   }
-  // the build's page chunks travel to the host on the write-back stream,
-  // with its two events (no write-back is pending during a build)
-  e = launch_build(m, d_keys, d_vals, n, bs, st, side ? h->ev_join : nullptr, h->st2,
-                   h->ev_pfork, h->ev_pjoin, h->st_fl, h->ev_evicted, h->ev_flushed);
-  if (e != cudaSuccess) return BOLT_E_CUDA;
   uint32_t err = 0;
   h->last_st = st;
   rc = read_err(h, &err);
@@ -1256,7 +1250,7 @@ uint64_t build_estimate(const bolt_info_t& I, uint64_t n) {
   uint64_t tag_cap = 8192;
   while (tag_cap < n) tag_cap <<= 1;
   const uint64_t nblocks = (I.M + 1 + 8192 - 1) / 8192 + 1;
-  return tag_cap * 16 + cap * (16 + 8 + 4 + 4) + (I.M + 1) * 4 + nblocks * 4 + 16 +
+  return tag_cap * 24 + cap * (16 + 8 + 4 + 4) + (I.M + 1) * 4 + nblocks * 4 + 16 +
          cap * (8 + (uint64_t)I.val_bytes);  // + the host-pointer staging copy
 }
 
