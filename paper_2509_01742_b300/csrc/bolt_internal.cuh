@@ -348,7 +348,8 @@ struct ProfSpan {
 // build.cu
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
                          struct BuildScratch& s, cudaStream_t st,
-                         cudaEvent_t tags_wait,  // waited on before the tags are written
+                         cudaEvent_t vals_wait,  // the values are on the device (or null);
+                                                 // `side` is already ordered after them
                          cudaStream_t side, cudaEvent_t side_fork, cudaEvent_t side_join,
                          // pages built in HBM chunks and copied to the host on
                          // copy_st (null: straight to the host); two events each

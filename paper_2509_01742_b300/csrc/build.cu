@@ -391,7 +391,7 @@ static int sm_count() {
 }
 
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
-                         BuildScratch& s, cudaStream_t st, cudaEvent_t tags_wait,
+                         BuildScratch& s, cudaStream_t st, cudaEvent_t vals_wait,
                          cudaStream_t side, cudaEvent_t side_fork, cudaEvent_t side_join,
                          cudaStream_t copy_st, cudaEvent_t* ev_built, cudaEvent_t* ev_copied) {
   const int sms = sm_count();
@@ -433,6 +433,7 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
         }
       }
     }
+    if (!done && vals_wait) cudaStreamWaitEvent(st, vals_wait, 0);
     for (uint64_t lo = 0; !done && lo < n; lo += m.Wr) {
       uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
       unsigned g = (unsigned)((hi - lo + 255) / 256);
@@ -448,8 +449,7 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   k_scan_sums<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums);
   k_scan_top<<<1, SCAN_BLOCK, 0, st>>>(s.block_sums, nblocks);
   k_scan_fill<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums, s.page_off);
-  // 3. tags + bitonic sort (the tag buffer may have been lent out until now)
-  if (tags_wait) cudaStreamWaitEvent(st, tags_wait, 0);
+  // 3. tags + bitonic sort
   k_build_tags<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.tag_cap, s.tags);
   count_launch(4);
   cudaError_t e = sort_tags_u64(s.tags, s.tag_cap, s.log_tile, st);
@@ -471,7 +471,8 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
     count_launch();
     cudaEventRecord(side_join, side);
   }
-  // 4. pages
+  // 4. pages (they read the values)
+  if (vals_wait) cudaStreamWaitEvent(st, vals_wait, 0);
   uint32_t wpb = (uint32_t)(65536 / m.page_bytes);
   wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;
   size_t smem = (size_t)wpb * m.page_bytes;

@@ -568,7 +568,10 @@ void drain_flushes(bolt* h, cudaStream_t st) {
 }
 
 int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n, uint64_t seed,
-              cudaStream_t st, BuildScratch& bs) {
+              cudaStream_t st, BuildScratch& bs, cudaEvent_t vals_ready = nullptr) {
+  // work the handle left on another stream (a caller stream of the access
+  // calls) finishes before the build resets the map
+  if (h->last_st && h->last_st != st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
   drain_flushes(h, st);
   MapDev& m = h->m;
   const bolt_info_t& I = h->info;
@@ -618,7 +621,7 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     e = key_check(st, bs.tags);  // in line, before the build reuses `tags`
     if (e != cudaSuccess) return BOLT_E_CUDA;
   }
-  e = launch_build(m, d_keys, d_vals, n, bs, st, nullptr, h->st2, h->ev_pfork, h->ev_pjoin,
+  e = launch_build(m, d_keys, d_vals, n, bs, st, vals_ready, h->st2, h->ev_pfork, h->ev_pjoin,
                    h->st_fl, h->ev_evicted, h->ev_flushed);
   if (e != cudaSuccess) return BOLT_E_CUDA;
   if (side) {
@@ -846,15 +849,19 @@ int bolt_init(bolt_t* h, const void* keys, const void* vals, uint64_t n, uint64_
     if (e != cudaSuccess) return cuda_fail(e);
     h->in_cap = cap;
   }
-  if (n) {
-    cudaError_t e = cudaMemcpyAsync(h->in_keys, keys, n * 8, cudaMemcpyHostToDevice, h->st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(h->in_vals, vals, n * h->vb, cudaMemcpyHostToDevice, h->st);
-    if (e != cudaSuccess) return BOLT_E_CUDA;
-  }
   int rc = grow_build_scratch(h, n);
   if (rc) return rc;
-  return init_impl(h, h->in_keys, h->in_vals, n, seed, h->st, h->bs);
+  if (h->last_st && h->last_st != h->st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  if (n) {
+    // keys first (the PRF phase reads them); the values, read only by the
+    // placement and the page build, arrive on the side stream meanwhile
+    cudaError_t e = cudaMemcpyAsync(h->in_keys, keys, n * 8, cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->in_vals, vals, n * h->vb, cudaMemcpyHostToDevice, h->st2);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_in, h->st2);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+  }
+  return init_impl(h, h->in_keys, h->in_vals, n, seed, h->st, h->bs, n ? h->ev_in : nullptr);
 }
 
 int bolt_sync(bolt_t* h) {
