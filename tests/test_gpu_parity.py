@@ -159,6 +159,28 @@ def test_empty_and_partial_init():
         o.close(); g.close()
 
 
+@pytest.mark.parametrize("case", ["far_apart", "salt_key", "distinct_with_salt_key"])
+def test_duplicate_keys_detected_at_scale(case):
+    """The build's key-uniqueness check (a hashed table on the side stream)
+    on 2^17 keys: a duplicate pair far apart, the key that the table encodes
+    as its empty value given twice, and that key given once among distinct
+    keys (no false alarm)."""
+    N = 1 << 17
+    keys, vals = W.records(N, 8, 71)
+    salt = np.uint64(0x9E3779B97F4A7C15)
+    if case == "far_apart":
+        keys[N - 1] = keys[3]
+    elif case == "salt_key":
+        keys[10] = salt
+        keys[N - 5] = salt
+    else:
+        keys[10] = salt
+    g = B.BoltMap(N, 8)
+    rc = g.init(keys, vals, 3)
+    assert rc == (0 if case == "distinct_with_salt_key" else B.BOLT_E_DUPKEY)
+    g.close()
+
+
 def test_overflow_and_dupkey_match_oracle():
     o, g = _pair(64, 8)
     k = np.array([5, 6, 5], dtype=np.uint64)
