@@ -437,3 +437,62 @@ def test_standalone_kdf_and_page_codec_match_a_built_map():
     for q in (0, 1, o.info()["M"] - 1):
         assert np.array_equal(O.page_decrypt(kenc, q, 0, pages[q]), o.decrypt_page(q))
     o.close()
+
+
+def _chacha_ref(key_words, nonce_words, length, counter=0):
+    """Keystream of the `cryptography` package's ChaCha20 (RFC 7539 block
+    layout: 32-bit little-endian counter followed by a 96-bit nonce)."""
+    from cryptography.hazmat.primitives.ciphers import Cipher, algorithms
+    key = np.asarray(key_words, dtype="<u4").tobytes()
+    nonce = np.asarray(nonce_words, dtype="<u4").tobytes()
+    enc = Cipher(algorithms.ChaCha20(key, counter.to_bytes(4, "little") + nonce),
+                 mode=None).encryptor()
+    return np.frombuffer(enc.update(bytes(length)), dtype=np.uint8)
+
+
+def test_keys_and_page_cipher_match_cryptography():
+    """The working keys and every page ciphertext, rebuilt with a third-party
+    ChaCha20 from their definitions: K_prf || K_enc is the first key-stream
+    block under the 64-bit seed (little-endian, zero-extended to 256 bits)
+    and the nonce "BOLT"; page q at version v is its plaintext XOR the key
+    stream under K_enc and the nonce (q, v) from block 0 (Sec. 4.1 step 3
+    encryption; Sec. 4.2 page contents).  The plaintext decoded this way
+    holds exactly the init records that P2C put in the page, and after one
+    batch every page it wrote decrypts under its bumped version."""
+    N, vb, seed = 1 << 11, 8, 0x0123456789ABCDEF
+    keys, vals = W.records(N, vb, 8)
+    m = O.OracleMap(N, vb)
+    assert m.init(keys, vals, seed) == 0
+    info = m.info()
+    kprf, kenc = m.keys()
+    blk = _chacha_ref([seed & 0xFFFFFFFF, seed >> 32, 0, 0, 0, 0, 0, 0],
+                      [int.from_bytes(b"BOLT", "little"), 0, 0], 64).view("<u4")
+    assert np.array_equal(kprf, blk[:8]) and np.array_equal(kenc, blk[8:])
+
+    M, P = info["M"], info["page_bytes"]
+    val_of = {int(k): vals[i].tobytes() for i, k in enumerate(keys)}
+
+    def decrypt(q, v):
+        ks = _chacha_ref(kenc, [q, v & 0xFFFFFFFF, v >> 32], P)
+        return m.pages()[q] ^ ks
+
+    seen = 0
+    for q in range(M):
+        pk, pv = decode_page(decrypt(q, 0), info)
+        assert [val_of[k] for k in pk] == pv
+        seen += len(pk)
+    assert seen == m.stats()["n_host"]
+
+    rng = np.random.default_rng(3)
+    idx = rng.choice(N, 64, replace=False)
+    ops = np.full(64, 1, dtype=np.uint8)  # PUT
+    vin = rng.integers(0, 256, (64, vb), dtype=np.uint8)
+    m.trace()
+    assert m.access(ops, keys[idx], vin)[0] == 0
+    written = [int(e) & 0x7FFFFFFF for e in m.trace() if int(e) & 0x80000000]
+    ver = m.versions()
+    assert written and all(ver[q] == 1 for q in written)
+    assert sum(int(v) for v in ver) == len(written)
+    for q in written:
+        decode_page(decrypt(q, 1), info)
+    m.close()
