@@ -581,16 +581,23 @@ def run_serve(args) -> None:
         ids = [None] * len(reqs)
         lat = [0.0] * len(reqs)
         done_ev = threading.Event()
+        failed = []
 
         def waiter():
-            for i in range(len(reqs)):
-                while ids[i] is None:
-                    time.sleep(0)
-                j, ops, _, _ = reqs[i]
-                rc, _, _, info = srv.wait(ids[i], len(ops), mids[j], timeout_ms=600000)
-                assert rc == 0, rc
-                lat[i] = (info.done_us - info.submit_us, info.submit_us, info.done_us)
-            done_ev.set()
+            try:
+                for i in range(len(reqs)):
+                    while ids[i] is None:
+                        time.sleep(0)
+                    j, ops, _, _ = reqs[i]
+                    rc, _, _, info = srv.wait(ids[i], len(ops), mids[j], timeout_ms=60000)
+                    if rc != 0:
+                        why = B.bolt_strerror(rc).decode()
+                        raise RuntimeError(f"request {i} on map {j}: {why} ({rc})")
+                    lat[i] = (info.done_us - info.submit_us, info.submit_us, info.done_us)
+            except BaseException as exc:  # reported by the submitting thread
+                failed.append(exc)
+            finally:
+                done_ev.set()
 
         th = threading.Thread(target=waiter)
         th.start()
@@ -605,8 +612,12 @@ def run_serve(args) -> None:
                 while time.perf_counter() < t_next:
                     pass
             ids[i] = srv.submit(mids[j], ops, keys, vin)
+            if failed:
+                break
         done_ev.wait()
         th.join()
+        if failed:
+            raise failed[0]
         first = min(x[1] for x in lat)
         last = max(x[2] for x in lat)
         return np.array([x[0] for x in lat]), total, (last - first) * 1e-6

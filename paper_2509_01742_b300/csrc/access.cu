@@ -1244,11 +1244,8 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
     ProfSpan ps(P_EVICT, st);
     const uint32_t wpb = EVICT_WARPS_PER_BLOCK;
     const size_t smem = (size_t)wpb * (m.page_bytes + 32 * 16);
-    if (smem > 48 * 1024) {
-      e = cudaFuncSetAttribute(k_exec_evict, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e != cudaSuccess) return e;
-    }
+    e = raise_smem_limit((const void*)k_exec_evict, smem);
+    if (e != cudaSuccess) return e;
     const uint32_t evict_blocks = (2 * n + wpb - 1) / wpb;
     const uint32_t exec_blocks = (n + wpb * 32 - 1) / (wpb * 32);
     e = launch_dependent(k_exec_evict, evict_blocks + exec_blocks, wpb * 32, smem, st, m, b, n,
@@ -1273,11 +1270,8 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
     count_launch();
   } else if (smem_remap) {
     const bool reg = n <= REMAP_REG_OPS * 1024;
-    if (rsmem > 48 * 1024) {
-      e = cudaFuncSetAttribute(reg ? (const void*)k_remap_smem_reg : (const void*)k_remap_smem,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsmem);
-      if (e != cudaSuccess) return e;
-    }
+    e = raise_smem_limit(reg ? (const void*)k_remap_smem_reg : (const void*)k_remap_smem, rsmem);
+    if (e != cudaSuccess) return e;
     if (reg) k_remap_smem_reg<<<1, 1024, rsmem, st>>>(m, b, n);
     else k_remap_smem<<<1, 1024, rsmem, st>>>(m, b, n);
     k_remap_rest<<<(n + 255) / 256, 256, 0, st>>>(m, b, n);

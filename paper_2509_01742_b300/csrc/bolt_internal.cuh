@@ -319,6 +319,13 @@ struct Prof {
 };
 extern thread_local Prof* g_prof;
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  The limit is a per-kernel attribute shared by every host
+// thread, so it is only ever raised (under a lock): a launch of the same
+// kernel for another map, enqueued by another thread, never finds its size
+// above a limit that was lowered meanwhile.
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
+
 inline void count_launch(uint64_t n = 1) {
   if (g_prof) g_prof->launches += n;
 }

@@ -476,11 +476,8 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   uint32_t wpb = (uint32_t)(65536 / m.page_bytes);
   wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;
   size_t smem = (size_t)wpb * m.page_bytes;
-  if (smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_page_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  e = raise_smem_limit((const void*)k_page_build, smem);
+  if (e != cudaSuccess) return e;
   const uint64_t cap = (uint64_t)sms * 32;
   // With the candidate-row buffer free (it is read only by the rounds), pages
   // are built into two halves of it in chunks and the copy engine moves each

@@ -47,14 +47,16 @@ struct bolt {
   // bolt_access moves chunks of ops through two alternating sets of pinned
   // staging (set 0 is h_ops ... h_status) and device I/O buffers (set 0 is
   // b.ops ... b.status), so that one chunk's host copies overlap another's
-  // batches
+  // batches.  Each set is one block: an input part keys | vin | ops of
+  // cap * (9 + vb) bytes from `keys`, and an output part vout | status of
+  // cap * (vb + 1) bytes from `vout` (see io_packed).
   struct IoSet {
     uint8_t* ops = nullptr;
     uint64_t* keys = nullptr;
     uint8_t* vin = nullptr;
     uint8_t* vout = nullptr;
     uint8_t* status = nullptr;
-  } h_io[2], d_io2;
+  } h_io[2], d_io[2];
   cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_d2h[2] = {nullptr, nullptr};
   cudaEvent_t ev_ioready[2] = {nullptr, nullptr};  // a chunk's batches are done
   uint32_t* d_kdf = nullptr;
@@ -110,6 +112,22 @@ struct bolt {
 };
 
 
+// n ops packed back to back from the start of an I/O set's two parts --
+// inputs keys[n] | vin[n * vb] | ops[n], outputs vout[n * vb] | status[n] --
+// so that a batch's inputs and its results each cross the link in one copy
+struct IoPacked {
+  uint64_t* keys;
+  uint8_t* vin;
+  uint8_t* ops;
+  uint8_t* vout;
+  uint8_t* status;
+  uint64_t in_bytes, out_bytes;
+};
+inline IoPacked io_packed(const bolt::IoSet& s, uint64_t n, uint64_t vb) {
+  uint8_t* in = reinterpret_cast<uint8_t*>(s.keys);
+  return {s.keys, in + n * 8, in + n * (8 + vb), s.vout, s.vout + n * vb, n * (9 + vb), n * (vb + 1)};
+}
+
 // points the kernel-side profiler at the handle for one ABI call
 struct ProfScope {
   explicit ProfScope(bolt* h) { bdev::g_prof = &h->prof; }
@@ -120,6 +138,8 @@ namespace brt {
 // one access batch of n <= cap_batch ops whose inputs are already in the
 // handle's device batch buffers, enqueued on st (outputs in h->b.vout/status)
 cudaError_t enqueue_batch(bolt* h, uint32_t n, cudaStream_t st);
+// the same, with its inputs and outputs packed in I/O set 0 (io_packed)
+cudaError_t enqueue_batch_packed(bolt* h, uint32_t n, cudaStream_t st);
 // BOLT_OK / BOLT_E_* for a device error word
 int err_rc(uint32_t err);
 // wait for every stream of the handle

@@ -19,7 +19,32 @@ using namespace bdev;
 
 namespace bdev {
 thread_local Prof* g_prof = nullptr;
+
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  struct Limit {
+    const void* kernel;
+    int device;
+    size_t bytes;
+  };
+  static std::mutex mu;
+  static std::vector<Limit> limits;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (Limit& l : limits)
+    if (l.kernel == kernel && l.device == dev) {
+      if (l.bytes >= bytes) return cudaSuccess;
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e == cudaSuccess) l.bytes = bytes;
+      return e;
+    }
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) limits.push_back({kernel, dev, bytes});
+  return e;
 }
+}  // namespace bdev
 
 namespace {
 
@@ -203,16 +228,24 @@ int alloc_state(bolt* h) {
   uint64_t cap2 = 1;
   while (cap2 < cap) cap2 <<= 1;
   const uint64_t sort_cap = cap2 <= 512 ? 512 : (cap2 < 4096 ? 4096 : cap2);
-  TRY(dalloc(h, &b.ops, cap));
-  TRY(dalloc(h, &b.keys, cap));
-  TRY(dalloc(h, &b.vin, cap * vb));
-  TRY(dalloc(h, &b.vout, cap * vb));
-  TRY(dalloc(h, &b.status, cap));
-  TRY(dalloc(h, &h->d_io2.ops, cap));
-  TRY(dalloc(h, &h->d_io2.keys, cap));
-  TRY(dalloc(h, &h->d_io2.vin, cap * vb));
-  TRY(dalloc(h, &h->d_io2.vout, cap * vb));
-  TRY(dalloc(h, &h->d_io2.status, cap));
+  // two I/O sets, one block each: inputs keys | vin | ops, then (from a
+  // 256-byte boundary) outputs vout | status; set 0 is the batch's own
+  const uint64_t io_in = (cap * (9 + vb) + 255) / 256 * 256;
+  for (int s = 0; s < 2; s++) {
+    uint8_t* blk = nullptr;
+    TRY(dalloc(h, &blk, io_in + cap * (vb + 1)));
+    bolt::IoSet& d = h->d_io[s];
+    d.keys = reinterpret_cast<uint64_t*>(blk);
+    d.vin = blk + cap * 8;
+    d.ops = blk + cap * (8 + vb);
+    d.vout = blk + io_in;
+    d.status = blk + io_in + cap * vb;
+  }
+  b.ops = h->d_io[0].ops;
+  b.keys = h->d_io[0].keys;
+  b.vin = h->d_io[0].vin;
+  b.vout = h->d_io[0].vout;
+  b.status = h->d_io[0].status;
   b.kt_mask = (uint32_t)(2 * cap2 < 128 ? 127 : 2 * cap2 - 1);
   const uint32_t ht = (uint32_t)(4 * cap2 < 256 ? 256 : 4 * cap2);
   b.ht_mask = ht - 1;
@@ -737,13 +770,14 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
     delete h;
     return BOLT_E_NOMEM;
   }
+  // the same two parts as a device I/O set (MAXB is a multiple of 8)
   uint8_t* q = static_cast<uint8_t*>(p);
   for (int s = 0; s < 2; s++) {
     bolt::IoSet& io = h->h_io[s];
     io.keys = reinterpret_cast<uint64_t*>(q); q += MAXB * 8;
     io.vin = q; q += (uint64_t)MAXB * val_bytes;
-    io.vout = q; q += (uint64_t)MAXB * val_bytes;
     io.ops = q; q += MAXB;
+    io.vout = q; q += (uint64_t)MAXB * val_bytes;
     io.status = q; q += MAXB;
   }
   h->h_keys = h->h_io[0].keys;
@@ -934,10 +968,15 @@ static bool host_pinned(const void* p) {
 }
 
 // Chunks of up to cap_batch ops (whole batches of batch_width), alternating
-// between two device I/O sets; each chunk is one access_batches call.  Pinned
-// caller arrays are copied directly; pageable ones through pinned staging,
-// the next chunk's inputs staged and the previous chunk's outputs copied out
-// while a chunk runs.
+// between two device I/O sets; each chunk is one access_batches call.  A
+// chunk whose arrays are pageable, or small, is packed through pinned
+// staging so that its inputs and its results each cross the link in one copy
+// (io_packed); large pinned caller arrays are copied directly.  With several
+// chunks the next chunk's inputs are staged and the previous chunk's results
+// copied out while a chunk runs; a single chunk keeps every copy on the
+// batch stream.
+constexpr uint64_t PACK_MAX_BYTES = 64 << 10;
+
 int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* vals_in,
                 void* vals_out, uint8_t* status_out, uint64_t n) {
   if (!h) return BOLT_E_ARG;
@@ -953,81 +992,93 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
   const uint8_t* vin = static_cast<const uint8_t*>(vals_in);
   uint8_t* vout = static_cast<uint8_t*>(vals_out);
   cudaStream_t st = h->st;
-  // host<->device copies run beside the batches on st: inputs on st2 (idle
-  // outside bolt_init), outputs on st_out, so chunk k + 1's inputs arrive and
-  // chunk k - 1's outputs leave while chunk k runs
-  cudaStream_t cs = h->st2, co = h->st_out;
   if (h->last_st != st) {
     if (h->last_st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
     h->last_st = st;
   }
   const uint32_t w = h->batch_width;
   const uint64_t chunk = (uint64_t)(h->cap_batch / w) * w;
-  const bool pin_in = host_pinned(ops) && host_pinned(keys) && host_pinned(vals_in);
-  const bool pin_out = host_pinned(vals_out) && (!status_out || host_pinned(status_out));
-  const bolt::IoSet dev[2] = {{h->b.ops, h->b.keys, h->b.vin, h->b.vout, h->b.status}, h->d_io2};
+  const bool single = n <= chunk;
+  // several chunks: host<->device copies run beside the batches on st --
+  // inputs on st2 (idle outside bolt_init), outputs on st_out -- so chunk
+  // k + 1's inputs arrive and chunk k - 1's outputs leave while chunk k runs
+  cudaStream_t cs = single ? st : h->st2, co = single ? st : h->st_out;
+  // whether the caller's arrays can feed the copy engine directly (only
+  // asked where a chunk is too large to pack)
+  const bool pin_in = n * (9 + vb) > PACK_MAX_BYTES && host_pinned(ops) && host_pinned(keys) &&
+                      host_pinned(vals_in);
+  const bool pin_out = n * (vb + 1) > PACK_MAX_BYTES && host_pinned(vals_out) &&
+                       (!status_out || host_pinned(status_out));
   bool pending[2] = {false, false};
   uint64_t plo[2] = {0, 0}, pcnt[2] = {0, 0};
+  // a packed chunk's results, from staging to the caller's arrays
   auto copy_out = [&](int s) -> int {
     if (!pending[s]) return BOLT_OK;
     pending[s] = false;
     if (cudaEventSynchronize(h->ev_d2h[s]) != cudaSuccess) return BOLT_E_CUDA;
-    std::memcpy(vout + plo[s] * vb, h->h_io[s].vout, pcnt[s] * vb);
-    if (status_out) std::memcpy(status_out + plo[s], h->h_io[s].status, pcnt[s]);
+    const IoPacked hp = io_packed(h->h_io[s], pcnt[s], vb);
+    std::memcpy(vout + plo[s] * vb, hp.vout, pcnt[s] * vb);
+    if (status_out) std::memcpy(status_out + plo[s], hp.status, pcnt[s]);
     return BOLT_OK;
   };
   cudaError_t e = cudaSuccess;
   int k = 0;
   for (uint64_t lo = 0; lo < n && e == cudaSuccess; lo += chunk, k ^= 1) {
     const uint64_t cnt = n - lo < chunk ? n - lo : chunk;
-    const bolt::IoSet& d = dev[k];
-    const bolt::IoSet& hs = h->h_io[k];
-    const uint8_t* src_ops = ops + lo;
-    const void* src_keys = kin + lo * 8;
-    const uint8_t* src_vin = vin + lo * vb;
-    if (!pin_in) {
-      // the staging set was last read by the copy two chunks back
-      if (cudaEventSynchronize(h->ev_h2d[k]) != cudaSuccess) return BOLT_E_CUDA;
-      std::memcpy(hs.ops, src_ops, cnt);
-      std::memcpy(hs.keys, src_keys, cnt * 8);
-      std::memcpy(hs.vin, src_vin, cnt * vb);
-      src_ops = hs.ops;
-      src_keys = hs.keys;
-      src_vin = hs.vin;
-    }
+    const bolt::IoSet& d = h->d_io[k];
+    const IoPacked dp = io_packed(d, cnt, vb);
+    const bool pack_in = !pin_in || cnt * (9 + vb) <= PACK_MAX_BYTES;
+    const bool pack_out = !pin_out || cnt * (vb + 1) <= PACK_MAX_BYTES;
+    BatchDev b = h->b;
     // the device set was last used by chunk k - 2: its batches and output copy
     e = lo >= 2 * chunk ? cudaStreamWaitEvent(cs, h->ev_d2h[k], 0) : cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d.ops, src_ops, cnt, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d.keys, src_keys, cnt * 8, cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d.vin, src_vin, cnt * vb, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) break;
+    if (pack_in) {
+      // the staging set was last read by the copy two chunks back
+      if (cudaEventSynchronize(h->ev_h2d[k]) != cudaSuccess) return BOLT_E_CUDA;
+      const IoPacked hp = io_packed(h->h_io[k], cnt, vb);
+      std::memcpy(hp.keys, kin + lo * 8, cnt * 8);
+      std::memcpy(hp.vin, vin + lo * vb, cnt * vb);
+      std::memcpy(hp.ops, ops + lo, cnt);
+      e = cudaMemcpyAsync(dp.keys, hp.keys, dp.in_bytes, cudaMemcpyHostToDevice, cs);
+      b.ops = dp.ops;
+      b.keys = dp.keys;
+      b.vin = dp.vin;
+    } else {
+      e = cudaMemcpyAsync(d.ops, ops + lo, cnt, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d.keys, kin + lo * 8, cnt * 8, cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d.vin, vin + lo * vb, cnt * vb, cudaMemcpyHostToDevice, cs);
+      b.ops = d.ops;
+      b.keys = d.keys;
+      b.vin = d.vin;
+    }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_h2d[k], cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, h->ev_h2d[k], 0);
+    if (e == cudaSuccess && cs != st) e = cudaStreamWaitEvent(st, h->ev_h2d[k], 0);
     if (e != cudaSuccess) break;
-    BatchDev b = h->b;
-    b.ops = d.ops;
-    b.keys = d.keys;
-    b.vin = d.vin;
-    b.vout = d.vout;
-    b.status = d.status;
+    b.vout = pack_out ? dp.vout : d.vout;
+    b.status = pack_out ? dp.status : d.status;
     e = access_batches(h, b, cnt, w, st);
-    if (e == cudaSuccess) e = cudaEventRecord(h->ev_ioready[k], st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(co, h->ev_ioready[k], 0);
+    if (e == cudaSuccess && co != st) {
+      e = cudaEventRecord(h->ev_ioready[k], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(co, h->ev_ioready[k], 0);
+    }
     if (e != cudaSuccess) break;
-    uint8_t* dst_vout = pin_out ? vout + lo * vb : hs.vout;
-    uint8_t* dst_st = pin_out && status_out ? status_out + lo : hs.status;
-    e = cudaMemcpyAsync(dst_vout, d.vout, cnt * vb, cudaMemcpyDeviceToHost, co);
-    if (e == cudaSuccess && (status_out || !pin_out))
-      e = cudaMemcpyAsync(dst_st, d.status, cnt, cudaMemcpyDeviceToHost, co);
+    if (pack_out) {
+      const IoPacked hp = io_packed(h->h_io[k], cnt, vb);
+      e = cudaMemcpyAsync(hp.vout, dp.vout, dp.out_bytes, cudaMemcpyDeviceToHost, co);
+    } else {
+      e = cudaMemcpyAsync(vout + lo * vb, d.vout, cnt * vb, cudaMemcpyDeviceToHost, co);
+      if (e == cudaSuccess && status_out)
+        e = cudaMemcpyAsync(status_out + lo, d.status, cnt, cudaMemcpyDeviceToHost, co);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_d2h[k], co);
     if (e != cudaSuccess) break;
-    if (!pin_out) {
-      // the previous chunk's outputs, while this one runs
-      int rc = copy_out(k ^ 1);
-      if (rc) return rc;
-      pending[k] = true;
-      plo[k] = lo;
-      pcnt[k] = cnt;
-    }
+    // the previous chunk's results, while this one runs
+    int rc = copy_out(k ^ 1);
+    if (rc) return rc;
+    pending[k] = pack_out;
+    plo[k] = lo;
+    pcnt[k] = cnt;
   }
   if (e != cudaSuccess) return BOLT_E_CUDA;
   for (int s = 0; s < 2; s++) {
@@ -1230,6 +1281,19 @@ cudaError_t enqueue_batch(bolt* h, uint32_t n, cudaStream_t st) {
   return cudaSuccess;
 }
 
+cudaError_t enqueue_batch_packed(bolt* h, uint32_t n, cudaStream_t st) {
+  const IoPacked dp = io_packed(h->d_io[0], n, h->vb);
+  BatchDev saved = h->b;
+  h->b.ops = dp.ops;
+  h->b.keys = dp.keys;
+  h->b.vin = dp.vin;
+  h->b.vout = dp.vout;
+  h->b.status = dp.status;
+  cudaError_t e = enqueue_batch(h, n, st);
+  h->b = saved;
+  return e;
+}
+
 int err_rc(uint32_t err) { return err_to_rc(err); }
 
 cudaError_t sync_handle(bolt* h) { return sync_all(h); }
@@ -1244,7 +1308,8 @@ uint64_t resident_estimate(const bolt_info_t& I, uint64_t cap, uint64_t trace_ca
   const uint64_t sort_cap = cap2 <= 512 ? 512 : (cap2 < 4096 ? 4096 : cap2);
   const uint64_t kt = 2 * cap2 < 128 ? 128 : 2 * cap2;
   const uint64_t ht = 4 * cap2 < 256 ? 256 : 4 * cap2;
-  b += 2 * cap * (1 + 8 + 2 * vb + 1) + 2 * cap * 8 + (2 * ((2 * cap + 255) / 256) + 2) * 4 + 16;
+  b += 2 * ((cap * (9 + vb) + 255) / 256 * 256 + cap * (vb + 1)) + 2 * cap * 8 +
+       (2 * ((2 * cap + 255) / 256) + 2) * 4 + 16;
   b += 2 * (sort_cap * 8 + kt * 4 + cap * 12 + cap * 16 + cap * 16 + cap * 4 + 2 * cap + ht * 8 +
             2 * cap * 4 + 4 + 2 * cap * I.page_bytes);
   b += 2 * (ht * 8 + ht * I.page_bytes + 2 * cap * 8 + 4);

@@ -66,8 +66,8 @@ struct Map {
   cudaEvent_t done_ev = nullptr;
   // pinned staging of one batch
   uint8_t* h_buf = nullptr;
-  uint8_t *h_ops = nullptr, *h_vin = nullptr, *h_vout = nullptr, *h_status = nullptr;
-  uint64_t* h_keys = nullptr;
+  bolt::IoSet io;              // the input and output parts of h_buf
+  IoPacked packed{};           // the in-flight batch's layout in them
   uint32_t* h_err = nullptr;
   std::vector<uint32_t> batch_log;
 };
@@ -129,16 +129,16 @@ int build_map(bolt_server* s, Map* m) {
   if (rc) return rc;
   rc = bolt_trim(h);
   if (rc) return rc;
+  // staging laid out like the handle's device I/O set 0: an input part and an
+  // output part, each filled back to back for the batch's n ops (io_packed)
   const uint64_t cap = s->max_batch, vb = m->vb;
-  const uint64_t bytes = cap * (1 + 8 + 2 * vb + 1) + 64;
+  const uint64_t in_bytes = (cap * (9 + vb) + 63) / 64 * 64;
+  const uint64_t bytes = in_bytes + cap * (vb + 1) + 64;
   if (cudaHostAlloc(reinterpret_cast<void**>(&m->h_buf), bytes, cudaHostAllocDefault) != cudaSuccess)
     return BOLT_E_NOMEM;
-  uint8_t* q = m->h_buf;
-  m->h_keys = reinterpret_cast<uint64_t*>(q); q += cap * 8;
-  m->h_vin = q; q += cap * vb;
-  m->h_vout = q; q += cap * vb;
-  m->h_ops = q; q += cap;
-  m->h_status = q; q += cap;
+  m->io.keys = reinterpret_cast<uint64_t*>(m->h_buf);
+  m->io.vout = m->h_buf + in_bytes;
+  uint8_t* q = m->io.vout + cap * (vb + 1);
   m->h_err = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
   if (cudaEventCreateWithFlags(&m->done_ev, cudaEventDisableTiming) != cudaSuccess) return BOLT_E_CUDA;
   std::vector<uint64_t>().swap(m->init_keys);
@@ -153,23 +153,25 @@ cudaError_t dispatch(bolt_server* s, Map* m, const std::vector<Request*>& reqs, 
   bolt* h = m->h;
   const uint64_t vb = m->vb;
   uint32_t n = 0;
+  for (Request* r : reqs) n += r->n;
+  const IoPacked hp = io_packed(m->io, n, vb);
   const double t_start = s->now_us();
+  uint32_t off = 0;
   for (Request* r : reqs) {
-    std::memcpy(m->h_ops + n, r->ops.data(), r->n);
-    std::memcpy(m->h_keys + n, r->keys.data(), (uint64_t)r->n * 8);
-    std::memcpy(m->h_vin + (uint64_t)n * vb, r->vin.data(), (uint64_t)r->n * vb);
+    std::memcpy(hp.ops + off, r->ops.data(), r->n);
+    std::memcpy(hp.keys + off, r->keys.data(), (uint64_t)r->n * 8);
+    std::memcpy(hp.vin + (uint64_t)off * vb, r->vin.data(), (uint64_t)r->n * vb);
     r->t_start = t_start;
-    n += r->n;
+    off += r->n;
   }
   *n_out = n;
+  m->packed = hp;
   cudaStream_t st = h->st;
   ProfScope prof_scope(h);
-  cudaError_t e = cudaMemcpyAsync(h->b.ops, m->h_ops, n, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->b.keys, m->h_keys, (uint64_t)n * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->b.vin, m->h_vin, (uint64_t)n * vb, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = brt::enqueue_batch(h, n, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_vout, h->b.vout, (uint64_t)n * vb, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_status, h->b.status, n, cudaMemcpyDeviceToHost, st);
+  const IoPacked dp = io_packed(h->d_io[0], n, vb);
+  cudaError_t e = cudaMemcpyAsync(dp.keys, hp.keys, hp.in_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = brt::enqueue_batch_packed(h, n, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hp.vout, dp.vout, hp.out_bytes, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_err, h->m.err, 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaEventRecord(m->done_ev, st);
   return e;
@@ -186,8 +188,8 @@ void complete(bolt_server* s, Map* m) {
   const double t_done = s->now_us();
   uint32_t off = 0;
   for (Request* r : m->inflight) {
-    r->vout.assign(m->h_vout + (uint64_t)off * vb, m->h_vout + (uint64_t)(off + r->n) * vb);
-    r->status.assign(m->h_status + off, m->h_status + off + r->n);
+    r->vout.assign(m->packed.vout + (uint64_t)off * vb, m->packed.vout + (uint64_t)(off + r->n) * vb);
+    r->status.assign(m->packed.status + off, m->packed.status + off + r->n);
     r->rc = rc;
     r->t_done = t_done;
     r->done = true;

@@ -281,12 +281,9 @@ template <int LT>
 static cudaError_t sort_u64_lt(uint64_t* tags, uint64_t n, cudaStream_t st,
                                int cls_global = P_SORT_GLOBAL, int cls_tile = P_SORT_TILE) {
   const size_t smem = tile_smem<LT>();
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_sort_tile_full<LT, uint64_t>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_sort_tile_merge<LT, uint64_t>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = raise_smem_limit((const void*)k_sort_tile_full<LT, uint64_t>, smem);
+    if (e == cudaSuccess) e = raise_smem_limit((const void*)k_sort_tile_merge<LT, uint64_t>, smem);
     if (e != cudaSuccess) return e;
   }
   const uint64_t tiles = n >> LT;

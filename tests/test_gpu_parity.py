@@ -311,19 +311,26 @@ def test_device_batches_call_matches_oracle(lookahead):
     o.close(); g.close()
 
 
-@pytest.mark.parametrize("pinned", [False, True])
-def test_host_call_over_many_chunks_matches_oracle(pinned):
-    """bolt_access over 5000 ops with batch capacity 1000 and batch width
-    300: chunks of 900 ops alternate between two device I/O sets (pageable
-    arrays through pinned staging, pinned arrays copied directly), each chunk
-    a pipelined run of batches.  Outputs and state equal the oracle's with
-    batches of 300."""
+@pytest.mark.parametrize("pinned,cap,bw,with_status", [
+    (False, 1000, 300, True),   # pageable: every chunk packed through staging
+    (True, 1000, 300, True),    # pinned but small chunks: packed as well
+    (True, 4000, 1300, True),   # pinned 3900-op chunk copied directly, ragged 1100 packed
+    (True, 4000, 1300, False),  # the same without a status array
+    (False, 4000, 1300, True),  # pageable large chunks
+])
+def test_host_call_over_many_chunks_matches_oracle(pinned, cap, bw, with_status):
+    """bolt_access over 5000 ops with a batch capacity below the call:
+    chunks of whole batches alternate between two device I/O sets, each
+    chunk a pipelined run of batches.  Pageable or small chunks cross the
+    link packed (one copy per direction through pinned staging), large
+    pinned ones are copied directly from and to the caller's arrays.
+    Outputs and state equal the oracle's with the same batch width."""
     import ctypes
     import torch
-    N, vb, bw = 1 << 14, 16, 300
+    N, vb = 1 << 14, 16
     o = O.OracleMap(N, vb, batch=bw)
     g = B.BoltMap(N, vb, trace=True)
-    g.set_param(B.BOLT_PARAM_BATCH_CAP, 1000)
+    g.set_param(B.BOLT_PARAM_BATCH_CAP, cap)
     g.set_param(B.BOLT_PARAM_BATCH, bw)
     keys, vals = W.records(12000, vb, 51)
     assert o.init(keys, vals, 5) == 0 and g.init(keys, vals, 5) == 0
@@ -335,13 +342,17 @@ def test_host_call_over_many_chunks_matches_oracle(pinned):
              for a in (ops, k.view(np.int64), vin)]
         out = torch.zeros((len(ops), vb), dtype=torch.uint8).pin_memory()
         st = torch.zeros(len(ops), dtype=torch.uint8).pin_memory()
-        rc = B.bolt_access(g.handle, *[ctypes.c_void_p(x.data_ptr()) for x in (*t, out, st)],
-                           len(ops))
+        ptrs = [ctypes.c_void_p(x.data_ptr()) for x in (*t, out)]
+        ptrs.append(ctypes.c_void_p(st.data_ptr() if with_status else 0))
+        rc = B.bolt_access(g.handle, *ptrs, len(ops))
         vg, sg = out.numpy(), st.numpy()
     else:
         rc, vg, sg = g.access(ops, k, vin)
     assert rc == 0
-    assert np.array_equal(so, sg)
+    if with_status:
+        assert np.array_equal(so, sg)
+    else:
+        assert not sg.any()
     assert np.array_equal(vo, vg)
     _assert_state_equal(o, g, "chunked host call")
     assert g.stats()["batches"] == (5000 + bw - 1) // bw
