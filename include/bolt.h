@@ -190,7 +190,10 @@ BOLT_API int bolt_init_device_noalloc(bolt_t* h, const void* d_keys, const void*
  *   status_out HOST, n bytes or NULL: 1 if the key was present before the op;
  * n may exceed BOLT_MAX_BATCH: the call is split into batches of the
  * configured width.  Results never depend on the batch partition; page
- * ciphertexts and the trace do.  Synchronous.
+ * ciphertexts and the trace do.  Synchronous.  Copies: the call moves chunks
+ * of up to the batch capacity; a chunk of pageable (or, up to 64 KiB, any)
+ * arrays is packed into the handle's pinned staging and crosses the link in
+ * one copy each way, larger pinned arrays are copied directly.
  * Errors: BOLT_E_ARG, BOLT_E_STATE, BOLT_E_OVERFLOW, BOLT_E_CUDA.
  */
 BOLT_API int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* vals_in,
