@@ -434,6 +434,12 @@ int bolt_server_submit(bolt_server_t* s, uint32_t map_id, const uint8_t* ops, co
   r->keys.assign(static_cast<const uint64_t*>(keys), static_cast<const uint64_t*>(keys) + n);
   r->vin.assign(static_cast<const uint8_t*>(vals_in), static_cast<const uint8_t*>(vals_in) + (uint64_t)n * vb);
   lock.lock();
+  // the map may have been removed while the request was copied: a request
+  // queued on it now would never be served
+  if (m->state == MAP_REMOVED || m->remove_requested) {
+    delete r;
+    return BOLT_E_STATE;
+  }
   r->id = s->next_id++;
   r->t_submit = s->now_us();
   s->requests[r->id] = r;
@@ -524,8 +530,7 @@ int bolt_server_destroy(bolt_server_t* s) {
     if (t.joinable()) t.join();
   for (Map* m : s->maps) {
     if (m->h) brt::sync_handle(m->h);
-    for (Request* r : m->queue) (void)r;
-    free_map_device(m);
+    free_map_device(m);  // queued requests are freed with s->requests below
     delete m;
   }
   for (auto& kv : s->requests) delete kv.second;
