@@ -496,3 +496,36 @@ def test_keys_and_page_cipher_match_cryptography():
     for q in written:
         decode_page(decrypt(q, 1), info)
     m.close()
+
+
+def test_init_position_map_rows_brute_force():
+    """Position-map placement at init (Sec. 4.2, d = 4 choices): a key's
+    candidate rows are four 64-bit words of PRF(K_prf, PM, key), each scaled
+    to [0, rows) by its high product, recomputed here with a third-party
+    ChaCha20; every key goes to its least-occupied candidate on the counts
+    at the start of its P2C round (W_r records, Sec. 3.3), the first of equal
+    candidates on ties.  The recount equals the oracle's row occupancies and
+    no row exceeds R."""
+    N = 1 << 16
+    keys, vals = W.records(N, 8, 13)
+    m = O.OracleMap(N, 8)
+    assert m.init(keys, vals, 99) == 0
+    info = m.info()
+    kprf, _ = m.keys()
+    rows, Wr = info["rows"], info["round_width"]
+    assert Wr > 1
+    cand = np.empty((N, 4), dtype=np.int64)
+    for i, k in enumerate(keys):
+        k = int(k)
+        w = _chacha_ref(kprf, [DOM_PM, k & 0xFFFFFFFF, k >> 32], 64).view("<u4")
+        for j in range(4):
+            r = int(w[2 * j]) | (int(w[2 * j + 1]) << 32)
+            cand[i, j] = (r * rows) >> 64
+    cnt = np.zeros(rows, dtype=np.int64)
+    for lo in range(0, N, Wr):
+        c = cand[lo:lo + Wr]
+        pick = c[np.arange(len(c)), np.argmin(cnt[c], axis=1)]  # argmin: first of ties
+        np.add.at(cnt, pick, 1)
+    assert np.array_equal(cnt, m.rowcounts().astype(np.int64))
+    assert cnt.max() <= info["R"]
+    m.close()
