@@ -529,3 +529,24 @@ def test_init_position_map_rows_brute_force():
     assert np.array_equal(cnt, m.rowcounts().astype(np.int64))
     assert cnt.max() <= info["R"]
     m.close()
+
+
+def test_pair_from_independent_prf():
+    """The bin pair of (domain, x): PRF block under K_prf with the nonce
+    (domain, x); the first bin scales its first 64-bit word to [0, B), the
+    second scales the next word to [0, B - 1) and skips the first (Sec. 3.2,
+    two distinct uniformly random bins), recomputed with a third-party
+    ChaCha20 for all four domains, B = 2 and large B."""
+    rng = np.random.default_rng(17)
+    kprf, _ = O.kdf(0xC0FFEE)
+    for B in (2, 3, 8192, (1 << 25) + 7):
+        for dom in (DOM_INIT, DOM_PM, DOM_REMAP, DOM_DUMMY):
+            for x in [0, 1, (1 << 64) - 1] + [int(v) for v in rng.integers(0, 2**63, 5)]:
+                w = _chacha_ref(kprf, [dom, x & 0xFFFFFFFF, x >> 32], 64).view("<u4")
+                r0 = int(w[0]) | (int(w[1]) << 32)
+                r1 = int(w[2]) | (int(w[3]) << 32)
+                first = (r0 * B) >> 64
+                second = (r1 * (B - 1)) >> 64
+                second += second >= first
+                assert O.pair(kprf, dom, x, B) == (first, second)
+                assert first != second and 0 <= first < B and 0 <= second < B
