@@ -216,15 +216,17 @@ void scheduler(bolt_server* s) {
     const uint64_t seq = s->work_seq.load();
     std::unique_lock<std::mutex> lock(s->mu);
     bool progress = false;
-    // 1. completions
+    // 1. completions (a batch whose event reports an error completes with
+    //    BOLT_E_CUDA rather than never)
     for (size_t i = 0; i < s->maps.size(); i++) {
       Map* m = s->maps[i];
-      if (!m->inflight.empty() && m->dispatched.load() &&
-          cudaEventQuery(m->done_ev) == cudaSuccess) {
-        m->dispatched.store(false);
-        complete(s, m);
-        progress = true;
-      }
+      if (m->inflight.empty() || !m->dispatched.load()) continue;
+      const cudaError_t q = cudaEventQuery(m->done_ev);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) m->error = BOLT_E_CUDA;
+      m->dispatched.store(false);
+      complete(s, m);
+      progress = true;
     }
     if (progress) s->done_cv.notify_all();
     // 2. removals of idle maps (the lock is dropped inside these loops: index
@@ -308,7 +310,7 @@ void scheduler(bolt_server* s) {
       if (s->stop.load() || s->work_seq.load() != seq) break;
       bool any = false;
       for (Map* m : busy_maps)
-        if (m->dispatched.load() && cudaEventQuery(m->done_ev) == cudaSuccess) any = true;
+        if (m->dispatched.load() && cudaEventQuery(m->done_ev) != cudaErrorNotReady) any = true;
       if (any) break;
       std::this_thread::yield();
     }
