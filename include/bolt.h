@@ -84,6 +84,12 @@ typedef struct bolt bolt_t;
                                    that bolt_access_device_batches reads ahead, while
                                    the previous batch finishes (default 0 = off);
                                    results are the same for every value */
+#define BOLT_PARAM_DEFER_FLUSH 11 /* 1 = between the batches of one call, a batch's host
+                                     write-back starts once the next batch's page reads
+                                     are done; 2 = the same with twice the write-back
+                                     warps; 0 = right after its eviction (default: the
+                                     fastest here); results, pages and trace are the
+                                     same for all */
 
 /* derived parameters (Sec. 3.3 sizing, Sec. 4.2 position map) */
 typedef struct {

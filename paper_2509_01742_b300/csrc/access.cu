@@ -1228,6 +1228,18 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
     }
   }
   if (fc.ev_looked) cudaEventRecord(fc.ev_looked, st);
+  if (fc.prev) {
+    // the previous batch's write-back, now that this batch's page reads
+    // (which took the pages it rewrote from its ciphertexts) are done
+    e = cudaEventRecord(fc.ev_reads_done, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(fc.flush_st, fc.ev_reads_done, 0);
+    if (e != cudaSuccess) return e;
+    ProfSpan ps(P_FLUSH, fc.flush_st);
+    k_flush<<<flush_blocks(fc.prev_n, fc.prev_fast), COPY_BLOCK, 0, fc.flush_st>>>(m, *fc.prev);
+    count_launch();
+    e = cudaEventRecord(fc.prev_flushed, fc.flush_st);
+    if (e != cudaSuccess) return e;
+  }
   {
     ProfSpan ps(P_FINDEXEC, st);
     e = launch_dependent(k_find, warp_blocks, 256, 0, st, m, b, n);
@@ -1255,13 +1267,15 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
   }
   // the host write-back overlaps the rest of this batch and the next one
   cudaEventRecord(fc.ev_evicted, st);
-  cudaStreamWaitEvent(fc.flush_st, fc.ev_evicted, 0);
-  {
-    ProfSpan ps(P_FLUSH, fc.flush_st);
-    k_flush<<<flush_blocks(n, fc.fast_flush), COPY_BLOCK, 0, fc.flush_st>>>(m, b);
-    count_launch();
+  if (!fc.defer_own) {
+    cudaStreamWaitEvent(fc.flush_st, fc.ev_evicted, 0);
+    {
+      ProfSpan ps(P_FLUSH, fc.flush_st);
+      k_flush<<<flush_blocks(n, fc.fast_flush), COPY_BLOCK, 0, fc.flush_st>>>(m, b);
+      count_launch();
+    }
+    cudaEventRecord(fc.ev_flushed, fc.flush_st);
   }
-  cudaEventRecord(fc.ev_flushed, fc.flush_st);
   ProfSpan prs(P_REMAP, st);
   const size_t rsmem = ((m.B + 3) / 4 + (m.rows + 3) / 4) * 4;
   if (fused_decide) {

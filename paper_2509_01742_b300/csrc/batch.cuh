@@ -87,13 +87,22 @@ cudaError_t sort_batch_keys(uint64_t* keys, uint32_t n_pow2, cudaStream_t st);
 cudaError_t sort_batch_keys32(uint32_t* keys, uint32_t n_pow2, cudaStream_t st);
 // Host page write-back runs on `flush_st` after `ev_evicted` (recorded on st
 // once the batch's ciphertexts are in dbuf); `ev_flushed` is recorded on
-// flush_st when the batch's pages are in host memory.
+// flush_st when the batch's pages are in host memory.  With `defer_own` the
+// batch's write-back is not enqueued here: the next batch's launch_main
+// enqueues it (as `prev`) once that batch's own page reads are done, so the
+// writes fill the link while that batch finds, executes and remaps.
 struct FlushCtx {
   cudaStream_t flush_st;
   cudaEvent_t ev_evicted;
   cudaEvent_t ev_flushed;
   cudaEvent_t ev_looked;   // recorded on st once the batch's page reads are done
   int fast_flush;          // 1: the write-back may use twice the warps
+  int defer_own;           // 1: leave this batch's write-back to the next batch
+  const BatchDev* prev;    // a deferred write-back to enqueue after the page reads
+  uint32_t prev_n;         // its batch's op count (sizes its grid)
+  int prev_fast;           // 1: that write-back uses twice the warps
+  cudaEvent_t prev_flushed;  // recorded on flush_st when it has landed
+  cudaEvent_t ev_reads_done; // scratch event: this batch's page reads are done
 };
 
 cudaError_t launch_prep(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,

@@ -25,6 +25,7 @@ struct bolt {
   bool trace_on = false;
   bool check_keys = true;
   double la_frac = 0.0;       // BOLT_PARAM_LOOKAHEAD: share of a batch's pages read ahead
+  int defer_flush = 0;        // BOLT_PARAM_DEFER_FLUSH: write-back after the next batch's reads
   bolt_info_t info{};
 
   bdev::MapDev m{};
@@ -109,6 +110,12 @@ struct bolt {
   cudaStream_t st_out = nullptr;  // bolt_access: device-to-host result copies
   cudaEvent_t ev_in = nullptr, ev_prep[2] = {nullptr, nullptr}, ev_pfree[2] = {nullptr, nullptr};
   cudaEvent_t ev_looked[2] = {nullptr, nullptr};  // a slot's batch finished its page reads
+  // a batch whose write-back waits for the next batch's page reads (only
+  // between the batches of one call; every call ends with none deferred)
+  bool deferred = false;
+  bdev::BatchDev deferred_b{};
+  uint32_t deferred_n = 0;
+  cudaEvent_t ev_reads_done = nullptr;
 };
 
 

@@ -149,6 +149,7 @@ void free_state(bolt* h) {
     h->s_dbuf[s] = nullptr;
   }
   h->prev_valid = false;
+  h->deferred = false;
   h->slot = 0;
   h->allocated = false;
   h->initialized = false;
@@ -161,7 +162,7 @@ void destroy_streams(bolt* h) {
                           &h->ev_prep[1], &h->ev_pfree[0], &h->ev_pfree[1], &h->ev_h2d[0],
                           &h->ev_h2d[1], &h->ev_d2h[0], &h->ev_d2h[1], &h->ev_looked[0],
                           &h->ev_looked[1], &h->ev_ioready[0], &h->ev_ioready[1],
-                          &h->ev_pfork, &h->ev_pjoin})
+                          &h->ev_pfork, &h->ev_pjoin, &h->ev_reads_done})
     if (*ev) {
       cudaEventDestroy(*ev);
       *ev = nullptr;
@@ -459,7 +460,7 @@ BatchDev slot_view(bolt* h, BatchDev b, uint32_t n, int s) {
 // preparation has been enqueued (on st, or on st_prep with st waiting for it):
 // waits for the flush that last used the slot, launches, flips the slot.
 cudaError_t main_batch(bolt* h, const BatchDev& b, uint32_t n, cudaStream_t st,
-                       bool lookahead = false) {
+                       bool lookahead = false, bool defer_own = false) {
   const int s = h->slot;
   if (h->flush_pending[s]) {
     cudaError_t e = cudaStreamWaitEvent(st, h->ev_flushed[s], 0);
@@ -467,8 +468,22 @@ cudaError_t main_batch(bolt* h, const BatchDev& b, uint32_t n, cudaStream_t st,
   }
   FlushCtx fc{h->st_fl, h->ev_evicted[s], h->ev_flushed[s],
               lookahead ? h->ev_looked[s] : nullptr, lookahead ? 1 : 0};
+  fc.defer_own = defer_own ? 1 : 0;
+  if (h->deferred) {
+    // the previous batch (the other slot) left its write-back to this one
+    fc.prev = &h->deferred_b;
+    fc.prev_n = h->deferred_n;
+    fc.prev_fast = h->defer_flush >= 2 ? 1 : 0;
+    fc.prev_flushed = h->ev_flushed[s ^ 1];
+    fc.ev_reads_done = h->ev_reads_done;
+  }
   cudaError_t e = launch_main(h->m, b, n, st, fc);
   if (e != cudaSuccess) return e;
+  h->deferred = defer_own;
+  if (defer_own) {
+    h->deferred_b = b;
+    h->deferred_n = n;
+  }
   h->flush_pending[s] = true;
   h->slot_ht_mask[s] = b.ht_mask;
   h->prev_valid = true;
@@ -574,7 +589,10 @@ cudaError_t access_batches(bolt* h, BatchDev b, uint64_t n, uint32_t w, cudaStre
     BatchDev v = slot_view(h, x, cnt, s);
     v.la_on = la && j >= 1 ? 1u : 0u;
     v.la_limit = la_limit(cnt);
-    e = main_batch(h, v, cnt, st, la);
+    // with BOLT_PARAM_DEFER_FLUSH every batch but the last leaves its
+    // write-back to the next one (not with the lookahead, whose page reads
+    // wait for the write-backs)
+    e = main_batch(h, v, cnt, st, la, h->defer_flush > 0 && !la && j + 1 < nb);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_pfree[s], st);
     if (e != cudaSuccess) break;
     h->t += cnt;
@@ -587,6 +605,7 @@ cudaError_t access_batches(bolt* h, BatchDev b, uint64_t n, uint32_t w, cudaStre
 // Order stream st after every pending page flush and forget the previous
 // batch (a build rewrites every page).
 void drain_flushes(bolt* h, cudaStream_t st) {
+  h->deferred = false;  // a write-back never enqueued: the build rewrites every page
   for (int s = 0; s < 2; s++) {
     if (h->flush_pending[s]) {
       cudaStreamWaitEvent(st, h->ev_flushed[s], 0);
@@ -745,6 +764,7 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_prep, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->st_out, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_reads_done, cudaEventDisableTiming);
   for (int s = 0; s < 2 && e == cudaSuccess; s++) {
     e = cudaEventCreateWithFlags(&h->ev_looked[s], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_ioready[s], cudaEventDisableTiming);
@@ -828,6 +848,10 @@ int bolt_set_param(bolt_t* h, int which, double v) {
     case BOLT_PARAM_LOOKAHEAD:
       if (!(v >= 0.0 && v <= 1.0)) return BOLT_E_ARG;
       h->la_frac = v;
+      return BOLT_OK;
+    case BOLT_PARAM_DEFER_FLUSH:
+      if (!(v == 0.0 || v == 1.0 || v == 2.0)) return BOLT_E_ARG;
+      h->defer_flush = (int)v;
       return BOLT_OK;
     case BOLT_PARAM_BATCH_CAP:
       if (!(v >= 1.0 && v <= (double)MAXB)) return BOLT_E_ARG;

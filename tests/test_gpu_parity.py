@@ -265,11 +265,13 @@ def test_device_batches_back_to_back_match_oracle():
     o.close(); g.close()
 
 
-@pytest.mark.parametrize("lookahead", [0, 0.3, 1])
-def test_device_batches_call_matches_oracle(lookahead):
+@pytest.mark.parametrize("lookahead,defer", [(0, 0), (0, 1), (0, 2), (0.3, 1), (1, 1)])
+def test_device_batches_call_matches_oracle(lookahead, defer):
     """bolt_access_device_batches (the next batch's preparation, and with
     lookahead its position-map search and page reads, run ahead on an
-    internal stream) over 21 batches of width 300 with a ragged tail of 123,
+    internal stream; without lookahead each batch's host write-back either
+    follows its eviction or waits for the next batch's page reads) over 21
+    batches of width 300 with a ragged tail of 123,
     then one plain device batch, then batches of width 1000 on a caller
     stream: outputs and state equal the oracle's with the same batch
     partition.  Keys repeat across consecutive batches (3000 keys), so
@@ -279,6 +281,7 @@ def test_device_batches_call_matches_oracle(lookahead):
     N, vb = 1 << 12, 8
     o, g = _pair(N, vb)
     g.set_param(B.BOLT_PARAM_LOOKAHEAD, lookahead)
+    g.set_param(B.BOLT_PARAM_DEFER_FLUSH, defer)
     keys, vals = W.records(3000, vb, 41)
     assert o.init(keys, vals, 9) == 0 and g.init(keys, vals, 9) == 0
     n1, n2, n3 = 20 * 300 + 123, 257, 3500
