@@ -550,3 +550,52 @@ def test_pair_from_independent_prf():
                 second += second >= first
                 assert O.pair(kprf, dom, x, B) == (first, second)
                 assert first != second and 0 <= first < B and 0 <= second < B
+
+
+@pytest.mark.parametrize("N", [1 << 12, 1 << 16])
+def test_per_access_block_counts(N):
+    """The fixed block set of one access (Sec. 4.3 overhead claim: constant
+    rounds and O(1) + O(log2 log2 N) bandwidth per access; Alg. 1):
+    with one operation per batch every access reads at most two host pages
+    (the host bins of its pair, in pair order) and writes back exactly the
+    distinct pages it read; every page is page_bytes long with
+    lmax = c + ceil(log2 log2 N) + 1 slots, and a key's position-map search
+    covers d = 4 rows of R = 16 + ceil(log2 log2 N / log2 d) slots -- the O(1)
+    + O(log log N) bound.  Over 3000 accesses of a Zipf-skewed mix with
+    deletes and misses the mean number of page reads per access is 2(1 - alpha)
+    within sampling error."""
+    m = O.OracleMap(N, 8, batch=1)
+    keys, vals = W.records(N // 2, 8, 21)
+    assert m.init(keys, vals, 6) == 0
+    info = m.info()
+    llg = math.ceil(math.log2(math.log2(N)))
+    assert info["lmax"] == info["c"] + llg + 1
+    assert info["R"] == 16 + math.ceil(math.log2(math.log2(N)) / 2)
+    assert info["page_bytes"] == (16 + info["lmax"] * info["rec_bytes"] + 63) // 64 * 64
+    ops, k, vin = W.op_stream(N // 2, 3000, 8, 22, get_frac=0.5, del_frac=0.1,
+                              absent_frac=0.1, zipf_theta=0.99)
+    m.trace()
+    assert m.access(ops, k, vin)[0] == 0
+    tr = [int(e) for e in m.trace()]
+    reads_per_access, i = [], 0
+    while i < len(tr):
+        reads = []
+        while i < len(tr) and not tr[i] & 0x80000000:
+            reads.append(tr[i])
+            i += 1
+        writes = []
+        while i < len(tr) and tr[i] & 0x80000000:
+            writes.append(tr[i] & 0x7FFFFFFF)
+            i += 1
+        assert 1 <= len(reads) <= 2
+        assert writes == list(dict.fromkeys(reads))
+        assert all(q < info["M"] for q in reads)
+        reads_per_access.append(len(reads))
+    # accesses whose two bins are both HBM bins leave no trace entry
+    n_host = len(reads_per_access)
+    assert n_host <= 3000
+    mean = sum(reads_per_access) / 3000
+    alpha = info["K"] / info["B"]
+    expect = 2 * (1 - alpha)
+    assert abs(mean - expect) < 5 * math.sqrt(2 * alpha * (1 - alpha) / 3000) + 0.01
+    m.close()
