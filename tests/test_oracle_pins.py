@@ -599,3 +599,52 @@ def test_per_access_block_counts(N):
     expect = 2 * (1 - alpha)
     assert abs(mean - expect) < 5 * math.sqrt(2 * alpha * (1 - alpha) / 3000) + 0.01
     m.close()
+
+
+@pytest.mark.parametrize("batch", [1, 64])
+def test_host_residents_sit_in_a_bin_of_their_current_pair(batch):
+    """After a run of batches every record found in host page q has bin K + q
+    in its current pair: the INIT pair of its input index if no batch touched
+    it, else the REMAP pair drawn at the global sequence number of the first
+    operation on it in the last batch that touched it (Alg. 1 remap; Sec. 3.2
+    pairs; batch leaders).  Pairs come from the PRF definition recomputed here
+    with a third-party ChaCha20, pages from the oracle's ciphertexts decrypted
+    the same way."""
+    N = 1 << 12
+    keys, vals = W.records(N // 2, 8, 31)
+    m = O.OracleMap(N, 8, batch=batch)
+    assert m.init(keys, vals, 12) == 0
+    info = m.info()
+    kprf, kenc = m.keys()
+    K, B, P = info["K"], info["B"], info["page_bytes"]
+    n_ops = 2048
+    ops, k, vin = W.op_stream(N // 2, n_ops, 8, 32, get_frac=0.6, zipf_theta=0.9)
+    assert m.access(ops, k, vin)[0] == 0
+
+    def pair(dom, x):
+        w = _chacha_ref(kprf, [dom, x & 0xFFFFFFFF, x >> 32], 64).view("<u4")
+        first = ((int(w[0]) | (int(w[1]) << 32)) * B) >> 64
+        second = ((int(w[2]) | (int(w[3]) << 32)) * (B - 1)) >> 64
+        return first, second + (second >= first)
+
+    index = {int(x): i for i, x in enumerate(keys)}
+    leader_t = {}
+    for lo in range(0, n_ops, batch):
+        seen = set()
+        for t in range(lo, min(n_ops, lo + batch)):
+            kk = int(k[t])
+            if kk not in seen:
+                seen.add(kk)
+                leader_t[kk] = t
+    ver = m.versions()
+    checked = 0
+    for q in range(info["M"]):
+        v = int(ver[q])
+        plain = m.pages()[q] ^ _chacha_ref(kenc, [q, v & 0xFFFFFFFF, v >> 32], P)
+        pk, _ = decode_page(plain, info)
+        for kk in pk:
+            cur = pair(DOM_REMAP, leader_t[kk]) if kk in leader_t else pair(DOM_INIT, index[kk])
+            assert K + q in cur, (q, kk)
+            checked += 1
+    assert checked > N // 4
+    m.close()
