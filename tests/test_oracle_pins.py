@@ -648,3 +648,54 @@ def test_host_residents_sit_in_a_bin_of_their_current_pair(batch):
             checked += 1
     assert checked > N // 4
     m.close()
+
+
+def test_remap_p2c_choice_one_op_at_a_time():
+    """P2C at access time, checked op by op on the bin loads (Alg. 1 remap;
+    Sec. 3.1 P2C with ties to the first bin): an op on a present key removes
+    it from one bin of its current pair; if the key is present afterwards it
+    goes to the less loaded bin of the REMAP pair drawn at the op's sequence
+    number, on the loads after that removal, the first bin on ties.  A Get or
+    Delete of an absent key changes no load.  Pairs are recomputed with a
+    third-party ChaCha20; presence follows a plain dict."""
+    N = 1 << 12
+    keys, vals = W.records(N // 2, 8, 41)
+    m = O.OracleMap(N, 8, batch=1)
+    assert m.init(keys, vals, 14) == 0
+    info = m.info()
+    kprf, _ = m.keys()
+    B = info["B"]
+
+    def pair(dom, x):
+        w = _chacha_ref(kprf, [dom, x & 0xFFFFFFFF, x >> 32], 64).view("<u4")
+        first = ((int(w[0]) | (int(w[1]) << 32)) * B) >> 64
+        second = ((int(w[2]) | (int(w[3]) << 32)) * (B - 1)) >> 64
+        return first, second + (second >= first)
+
+    cur = {int(x): pair(DOM_INIT, i) for i, x in enumerate(keys)}
+    ops, k, vin = W.op_stream(N // 2, 600, 8, 42, get_frac=0.4, del_frac=0.2,
+                              absent_frac=0.2)
+    before = m.loads().astype(np.int64)
+    for t in range(len(ops)):
+        assert m.access(ops[t:t + 1], k[t:t + 1], vin[t:t + 1])[0] == 0
+        after = m.loads().astype(np.int64)
+        kk, op = int(k[t]), int(ops[t])
+        present_after = op == W.PUT or (op == W.GET and kk in cur)
+        olds = cur[kk] if kk in cur else (None,)
+        ok = False
+        for old in olds:
+            mid = before.copy()
+            if old is not None:
+                mid[old] -= 1
+            expect = mid.copy()
+            if present_after:
+                r1, r2 = pair(DOM_REMAP, t)
+                expect[r1 if mid[r1] <= mid[r2] else r2] += 1
+            ok |= np.array_equal(expect, after)
+        assert ok, (t, op, kk in cur)
+        if present_after:
+            cur[kk] = pair(DOM_REMAP, t)
+        else:
+            cur.pop(kk, None)
+        before = after
+    m.close()
