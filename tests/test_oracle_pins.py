@@ -699,3 +699,70 @@ def test_remap_p2c_choice_one_op_at_a_time():
             cur.pop(kk, None)
         before = after
     m.close()
+
+
+def test_written_pages_hold_exactly_their_bin():
+    """Eviction and write-back checked op by op (Alg. 1: read both pages,
+    remove the key, evict the stash items bound for the pages, write them
+    back; the remapped key then waits in the stash or the HBM store): after
+    each single-op batch, every page the trace shows written holds exactly
+    the present keys whose bin is that page, except the op's own key if it
+    was just remapped there, each with its current value.  Bins are tracked
+    from the INIT P2C rounds and the REMAP rule, pairs recomputed with a
+    third-party ChaCha20, values from a plain dict."""
+    N = 1 << 12
+    keys, vals = W.records(N // 2, 8, 51)
+    m = O.OracleMap(N, 8, batch=1)
+    assert m.init(keys, vals, 15) == 0
+    info = m.info()
+    kprf, kenc = m.keys()
+    B, K, Wr, P = info["B"], info["K"], info["round_width"], info["page_bytes"]
+
+    def pair(dom, x):
+        w = _chacha_ref(kprf, [dom, x & 0xFFFFFFFF, x >> 32], 64).view("<u4")
+        first = ((int(w[0]) | (int(w[1]) << 32)) * B) >> 64
+        second = ((int(w[2]) | (int(w[3]) << 32)) * (B - 1)) >> 64
+        return first, second + (second >= first)
+
+    # bins after init: round-synchronous P2C on round-start loads
+    load = np.zeros(B, dtype=np.int64)
+    bin_of = {}
+    for lo in range(0, len(keys), Wr):
+        chosen = []
+        for i in range(lo, min(len(keys), lo + Wr)):
+            a, b = pair(DOM_INIT, i)
+            chosen.append((int(keys[i]), a if load[a] <= load[b] else b))
+        for kk, d in chosen:
+            bin_of[kk] = d
+            load[d] += 1
+    assert np.array_equal(load, m.loads().astype(np.int64))
+    value = {int(x): vals[i].tobytes() for i, x in enumerate(keys)}
+    ops, k, vin = W.op_stream(N // 2, 400, 8, 52, get_frac=0.4, del_frac=0.2,
+                              absent_frac=0.2)
+    m.trace()
+    for t in range(len(ops)):
+        assert m.access(ops[t:t + 1], k[t:t + 1], vin[t:t + 1])[0] == 0
+        kk, op = int(k[t]), int(ops[t])
+        if kk in bin_of:
+            load[bin_of.pop(kk)] -= 1
+        if op == W.PUT:
+            value[kk] = vin[t].tobytes()
+        elif op == W.DEL:
+            value.pop(kk, None)
+        if kk in value:
+            r1, r2 = pair(DOM_REMAP, t)
+            bin_of[kk] = r1 if load[r1] <= load[r2] else r2
+            load[bin_of[kk]] += 1
+        assert np.array_equal(load, m.loads().astype(np.int64)), t
+        ver = m.versions()
+        for e in m.trace():
+            if not int(e) & 0x80000000:
+                continue
+            q = int(e) & 0x7FFFFFFF
+            v = int(ver[q])
+            plain = m.pages()[q] ^ _chacha_ref(kenc, [q, v & 0xFFFFFFFF, v >> 32], P)
+            pk, pv = decode_page(plain, info)
+            expect = sorted(x for x, d in bin_of.items() if d == K + q and x != kk)
+            assert pk == expect, (t, q)
+            assert pv == [value[x] for x in pk]
+    m.close()
