@@ -702,12 +702,14 @@ def test_remap_p2c_choice_one_op_at_a_time():
 
 
 def test_written_pages_hold_exactly_their_bin():
-    """Eviction and write-back checked op by op (Alg. 1: read both pages,
+    """Trace, eviction and write-back checked op by op (Alg. 1: read both pages,
     remove the key, evict the stash items bound for the pages, write them
     back; the remapped key then waits in the stash or the HBM store): after
     each single-op batch, every page the trace shows written holds exactly
     the present keys whose bin is that page, except the op's own key if it
-    was just remapped there, each with its current value.  Bins are tracked
+    was just remapped there, each with its current value; the trace itself is
+    the host bins of the key's stored pair (a DUMMY pair at the op's sequence
+    number for an absent key), then each page once as a write.  Bins are tracked
     from the INIT P2C rounds and the REMAP rule, pairs recomputed with a
     third-party ChaCha20, values from a plain dict."""
     N = 1 << 12
@@ -726,11 +728,12 @@ def test_written_pages_hold_exactly_their_bin():
 
     # bins after init: round-synchronous P2C on round-start loads
     load = np.zeros(B, dtype=np.int64)
-    bin_of = {}
+    bin_of, pair_of = {}, {}
     for lo in range(0, len(keys), Wr):
         chosen = []
         for i in range(lo, min(len(keys), lo + Wr)):
             a, b = pair(DOM_INIT, i)
+            pair_of[int(keys[i])] = (a, b)
             chosen.append((int(keys[i]), a if load[a] <= load[b] else b))
         for kk, d in chosen:
             bin_of[kk] = d
@@ -743,6 +746,12 @@ def test_written_pages_hold_exactly_their_bin():
     for t in range(len(ops)):
         assert m.access(ops[t:t + 1], k[t:t + 1], vin[t:t + 1])[0] == 0
         kk, op = int(k[t]), int(ops[t])
+        # the trace: the host bins of the stored pair (a DUMMY pair for an
+        # absent key), then each page once as a write
+        read_pair = pair_of[kk] if kk in bin_of else pair(DOM_DUMMY, t)
+        reads = [p - K for p in read_pair if p >= K]
+        trace = m.trace()
+        assert [int(e) for e in trace] == reads + [q | 0x80000000 for q in dict.fromkeys(reads)]
         if kk in bin_of:
             load[bin_of.pop(kk)] -= 1
         if op == W.PUT:
@@ -751,11 +760,12 @@ def test_written_pages_hold_exactly_their_bin():
             value.pop(kk, None)
         if kk in value:
             r1, r2 = pair(DOM_REMAP, t)
+            pair_of[kk] = (r1, r2)
             bin_of[kk] = r1 if load[r1] <= load[r2] else r2
             load[bin_of[kk]] += 1
         assert np.array_equal(load, m.loads().astype(np.int64)), t
         ver = m.versions()
-        for e in m.trace():
+        for e in trace:
             if not int(e) & 0x80000000:
                 continue
             q = int(e) & 0x7FFFFFFF
