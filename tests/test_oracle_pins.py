@@ -776,3 +776,95 @@ def test_written_pages_hold_exactly_their_bin():
             assert pk == expect, (t, q)
             assert pv == [value[x] for x in pk]
     m.close()
+
+
+@pytest.mark.parametrize("width", [37, 64, 4096])
+def test_batches_follow_the_stated_semantics(width):
+    """Batches of several ops against an independent model of the batch
+    reading of Alg. 1 (grouping by key; the first op on a present key reads
+    its stored pair, misses and repeats read a DUMMY pair at their sequence
+    number; every read page is written once, in first-read order, holding
+    the keys of its bin after the batch's removals; keys present afterwards
+    are remapped by P2C in rounds of W_r op slots decided on round-start
+    loads, ties to the first bin).  Checked per batch: the trace, the bin
+    loads and every written page (keys and values), at N = 2^16 where a
+    round holds 32 op slots (batches of 4096 make keys of one round compete
+    for bins, so deciding a round's keys one after another fails).  Pairs
+    come from a third-party ChaCha20."""
+    N = 1 << 16
+    keys, vals = W.records(N // 2, 8, 61)
+    m = O.OracleMap(N, 8, batch=width)
+    assert m.init(keys, vals, 16) == 0
+    info = m.info()
+    kprf, kenc = m.keys()
+    B, K, Wr, P = info["B"], info["K"], info["round_width"], info["page_bytes"]
+    assert Wr == 32
+
+    def pair(dom, x):
+        w = _chacha_ref(kprf, [dom, x & 0xFFFFFFFF, x >> 32], 64).view("<u4")
+        first = ((int(w[0]) | (int(w[1]) << 32)) * B) >> 64
+        second = ((int(w[2]) | (int(w[3]) << 32)) * (B - 1)) >> 64
+        return first, second + (second >= first)
+
+    load = np.zeros(B, dtype=np.int64)
+    bin_of, pair_of = {}, {}
+    for lo in range(0, len(keys), Wr):
+        chosen = []
+        for i in range(lo, min(len(keys), lo + Wr)):
+            p = pair(DOM_INIT, i)
+            pair_of[int(keys[i])] = p
+            chosen.append((int(keys[i]), p[0] if load[p[0]] <= load[p[1]] else p[1]))
+        for kk, d in chosen:
+            bin_of[kk] = d
+            load[d] += 1
+    value = {int(x): vals[i].tobytes() for i, x in enumerate(keys)}
+    n_ops = min(8 * width, 3 * 4096)
+    ops, k, vin = W.op_stream(N // 2, n_ops, 8, 62, get_frac=0.4, del_frac=0.2,
+                              absent_frac=0.15, zipf_theta=1.1)
+    m.trace()
+    for t0 in range(0, n_ops, width):
+        n = min(width, n_ops - t0)
+        assert m.access(ops[t0:t0 + n], k[t0:t0 + n], vin[t0:t0 + n])[0] == 0
+        bk = [int(x) for x in k[t0:t0 + n]]
+        first = {}
+        for i, kk in enumerate(bk):
+            first.setdefault(kk, i)
+        reads = []
+        for i, kk in enumerate(bk):
+            p = pair_of[kk] if first[kk] == i and kk in bin_of else pair(DOM_DUMMY, t0 + i)
+            reads += [b - K for b in p if b >= K]
+        written = list(dict.fromkeys(reads))
+        trace = [int(e) for e in m.trace()]
+        assert trace == reads + [q | 0x80000000 for q in written]
+        for kk in first:
+            if kk in bin_of:
+                load[bin_of.pop(kk)] -= 1
+        for i, kk in enumerate(bk):
+            if ops[t0 + i] == W.PUT:
+                value[kk] = vin[t0 + i].tobytes()
+            elif ops[t0 + i] == W.DEL:
+                value.pop(kk, None)
+        ver = m.versions()
+        pages = m.pages()
+        by_page = {}
+        for x, d in bin_of.items():
+            if d >= K:
+                by_page.setdefault(d - K, []).append(x)
+        for q in written:
+            v = int(ver[q])
+            plain = pages[q] ^ _chacha_ref(kenc, [q, v & 0xFFFFFFFF, v >> 32], P)
+            pk, pv = decode_page(plain, info)
+            assert pk == sorted(by_page.get(q, [])), (t0, q)
+            assert pv == [value[x] for x in pk]
+        for lo in range(0, n, Wr):
+            chosen = []
+            for i in range(lo, min(n, lo + Wr)):
+                kk = bk[i]
+                if first[kk] == i and kk in value:
+                    p = pair(DOM_REMAP, t0 + i)
+                    chosen.append((kk, p, p[0] if load[p[0]] <= load[p[1]] else p[1]))
+            for kk, p, d in chosen:
+                pair_of[kk], bin_of[kk] = p, d
+                load[d] += 1
+        assert np.array_equal(load, m.loads().astype(np.int64)), t0
+    m.close()
