@@ -115,7 +115,13 @@ typedef struct {
  * bolt_create -- plan a map of capacity N records (Sec. 3.3 sizing) and
  * allocate its device state and its M pinned, device-mapped host pages.
  *   N           capacity in records, 64 <= N <= 2^31;
- *   key_bytes   must be 8 (keys are uint64, little-endian in pages);
+ *   key_bytes   8 (keys are uint64) or 4 (keys are uint32): the width of the
+ *               keys the host-pointer calls (bolt_init, bolt_access,
+ *               bolt_autotune) take; the map zero-extends 4-byte keys and
+ *               holds every key as a uint64 (an 8-byte little-endian key
+ *               field in each page slot, so page_bytes does not depend on
+ *               it); the device-pointer calls and the server take uint64
+ *               keys for either width;
  *   val_bytes   value size, a multiple of 8 in [8, 504];
  *   hbm_budget  bytes the value store (HBM bins + stash, Claims 3.3/3.4) may
  *               use; alpha is the largest of {0.2, 0.1, 0.05, 0.01, 0} that

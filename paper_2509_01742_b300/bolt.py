@@ -151,9 +151,10 @@ def _np_ptr(a: np.ndarray):
 
 
 def plan(N: int, val_bytes: int, hbm_budget: int = 2**64 - 1, alpha: float = -1.0,
-         c: int = 8) -> dict:
+         c: int = 8, key_bytes: int = 8) -> dict:
     o = bolt_info_t()
-    _check(bolt_plan(N, 8, val_bytes, hbm_budget, alpha, c, ctypes.byref(o)), "bolt_plan")
+    _check(bolt_plan(N, key_bytes, val_bytes, hbm_budget, alpha, c, ctypes.byref(o)),
+           "bolt_plan")
     return o.as_dict()
 
 
@@ -161,10 +162,13 @@ class BoltMap:
     """One oblivious map handle (owns its device state and pinned pages)."""
 
     def __init__(self, N: int, val_bytes: int, hbm_budget: int = 2**64 - 1, alpha=None,
-                 c=None, trace: bool = False, batch=None, check_keys=None):
+                 c=None, trace: bool = False, batch=None, check_keys=None, key_bytes: int = 8):
         self._h = ctypes.c_void_p()
-        _check(bolt_create(N, 8, val_bytes, hbm_budget, ctypes.byref(self._h)), "bolt_create")
+        _check(bolt_create(N, key_bytes, val_bytes, hbm_budget, ctypes.byref(self._h)),
+               "bolt_create")
         self.vb = val_bytes
+        # host-pointer calls take keys of this width (device calls take uint64)
+        self._kdt = np.uint32 if key_bytes == 4 else np.uint64
         if c is not None:
             self.set_param(BOLT_PARAM_C, c)
         if alpha is not None:
@@ -175,6 +179,13 @@ class BoltMap:
             self.set_param(BOLT_PARAM_BATCH, batch)
         if check_keys is not None:
             self.set_param(BOLT_PARAM_CHECK_KEYS, int(check_keys))
+
+    def _keys(self, keys):
+        keys = np.asarray(keys)
+        if self._kdt is np.uint32 and keys.dtype.itemsize > 4 and keys.size and \
+                int(keys.max()) > 0xFFFFFFFF:
+            raise ValueError("a map of 4-byte keys takes keys below 2^32")
+        return np.ascontiguousarray(keys, dtype=self._kdt)
 
     def set_param(self, which: int, value: float):
         _check(bolt_set_param(self._h, which, float(value)), "bolt_set_param")
@@ -206,7 +217,7 @@ class BoltMap:
 
     # --- host-pointer calls ------------------------------------------------
     def init(self, keys: np.ndarray, vals: np.ndarray, seed: int) -> int:
-        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        keys = self._keys(keys)
         vals = np.ascontiguousarray(vals, dtype=np.uint8)
         if vals.size != len(keys) * self.vb:
             raise ValueError(f"{len(keys)} keys need {len(keys) * self.vb} value bytes")
@@ -214,7 +225,7 @@ class BoltMap:
 
     def access(self, ops, keys, vals_in):
         ops = np.ascontiguousarray(ops, dtype=np.uint8)
-        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        keys = self._keys(keys)
         vin = np.ascontiguousarray(vals_in, dtype=np.uint8)
         n = len(ops)
         if len(keys) != n or vin.size != n * self.vb:
@@ -307,7 +318,7 @@ class BoltMap:
     def autotune(self, sample_keys=None, max_batch_us: float = 0.0) -> dict:
         t = bolt_tune_t()
         if sample_keys is not None:
-            sk = np.ascontiguousarray(sample_keys, dtype=np.uint64)
+            sk = self._keys(sample_keys)
             rc = bolt_autotune(self._h, _np_ptr(sk), len(sk), max_batch_us, ctypes.byref(t))
         else:
             rc = bolt_autotune(self._h, None, 0, max_batch_us, ctypes.byref(t))

@@ -16,6 +16,7 @@ struct bolt {
   int sort_log_tile = 13;      // bitonic tile chosen by bolt_autotune
   uint64_t N = 0;
   uint32_t vb = 0;
+  uint32_t kb = 8;            // key bytes at the host-pointer boundary (4 or 8)
   uint64_t hbm_budget = 0;
   double alpha_override = -1.0;
   uint32_t c = 8;

@@ -188,6 +188,7 @@ int choose_plan(bolt* h, bolt_info_t* o) {
 int alloc_state(bolt* h) {
   int rc = choose_plan(h, &h->info);
   if (rc) return rc;
+  h->info.key_bytes = h->kb;
   const bolt_info_t& I = h->info;
   MapDev& m = h->m;
   m.N = I.N; m.B = I.B; m.K = I.K; m.M = I.M; m.rows = I.rows; m.Wr = I.round_width;
@@ -731,8 +732,8 @@ const char* bolt_strerror(int code) {
 
 int bolt_plan(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm_budget,
               double alpha, uint32_t c, bolt_info_t* out) {
-  if (!out || key_bytes != 8 || val_bytes < 8 || val_bytes % 8 || val_bytes > 504 || N < 64 ||
-      N > (1ull << 31) || c < 1 || c > 24)
+  if (!out || (key_bytes != 8 && key_bytes != 4) || val_bytes < 8 || val_bytes % 8 ||
+      val_bytes > 504 || N < 64 || N > (1ull << 31) || c < 1 || c > 24)
     return BOLT_E_ARG;
   bolt tmp;
   tmp.N = N;
@@ -740,18 +741,21 @@ int bolt_plan(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm_b
   tmp.hbm_budget = hbm_budget;
   tmp.alpha_override = alpha;
   tmp.c = c;
-  return choose_plan(&tmp, out);
+  int rc = choose_plan(&tmp, out);
+  if (rc == BOLT_OK) out->key_bytes = key_bytes;
+  return rc;
 }
 
 int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm_budget,
                 bolt_t** out) {
-  if (!out || key_bytes != 8 || val_bytes < 8 || val_bytes % 8 || val_bytes > 504 || N < 64 ||
-      N > (1ull << 31))
+  if (!out || (key_bytes != 8 && key_bytes != 4) || val_bytes < 8 || val_bytes % 8 ||
+      val_bytes > 504 || N < 64 || N > (1ull << 31))
     return BOLT_E_ARG;
   *out = nullptr;
   bolt* h = new (std::nothrow) bolt();
   if (!h) return BOLT_E_NOMEM;
   h->N = N;
+  h->kb = key_bytes;
   h->vb = val_bytes;
   h->hbm_budget = hbm_budget;
   cudaError_t e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
@@ -910,6 +914,14 @@ int bolt_init(bolt_t* h, const void* keys, const void* vals, uint64_t n, uint64_
   int rc = grow_build_scratch(h, n);
   if (rc) return rc;
   if (h->last_st && h->last_st != h->st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  // 4-byte keys are zero-extended: the map holds every key as a uint64
+  std::vector<uint64_t> wide;
+  if (n && h->kb == 4) {
+    wide.resize(n);
+    const uint32_t* k32 = static_cast<const uint32_t*>(keys);
+    for (uint64_t i = 0; i < n; i++) wide[i] = k32[i];
+    keys = wide.data();
+  }
   if (n) {
     // keys first (the PRF phase reads them); the values, read only by the
     // placement and the page build, arrive on the side stream meanwhile
@@ -1029,8 +1041,8 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
   cudaStream_t cs = single ? st : h->st2, co = single ? st : h->st_out;
   // whether the caller's arrays can feed the copy engine directly (only
   // asked where a chunk is too large to pack)
-  const bool pin_in = n * (9 + vb) > PACK_MAX_BYTES && host_pinned(ops) && host_pinned(keys) &&
-                      host_pinned(vals_in);
+  const bool pin_in = h->kb == 8 && n * (9 + vb) > PACK_MAX_BYTES && host_pinned(ops) &&
+                      host_pinned(keys) && host_pinned(vals_in);
   const bool pin_out = n * (vb + 1) > PACK_MAX_BYTES && host_pinned(vals_out) &&
                        (!status_out || host_pinned(status_out));
   bool pending[2] = {false, false};
@@ -1061,7 +1073,13 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
       // the staging set was last read by the copy two chunks back
       if (cudaEventSynchronize(h->ev_h2d[k]) != cudaSuccess) return BOLT_E_CUDA;
       const IoPacked hp = io_packed(h->h_io[k], cnt, vb);
-      std::memcpy(hp.keys, kin + lo * 8, cnt * 8);
+      if (h->kb == 4) {
+        // zero-extended into the uint64 keys the map holds
+        const uint32_t* k32 = reinterpret_cast<const uint32_t*>(kin) + lo;
+        for (uint64_t i = 0; i < cnt; i++) hp.keys[i] = k32[i];
+      } else {
+        std::memcpy(hp.keys, kin + lo * 8, cnt * 8);
+      }
       std::memcpy(hp.vin, vin + lo * vb, cnt * vb);
       std::memcpy(hp.ops, ops + lo, cnt);
       e = cudaMemcpyAsync(dp.keys, hp.keys, dp.in_bytes, cudaMemcpyHostToDevice, cs);
@@ -1105,11 +1123,16 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
     pcnt[k] = cnt;
   }
   if (e != cudaSuccess) return BOLT_E_CUDA;
+  // the error word rides behind the last batch on st, so one wait covers it
+  e = cudaMemcpyAsync(h->h_err, h->m.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   for (int s = 0; s < 2; s++) {
     int rc = copy_out(s ^ k);
     if (rc) return rc;
   }
-  return bolt_sync(h);
+  if (sync_all(h) != cudaSuccess || e != cudaSuccess) return BOLT_E_CUDA;
+  const int rc = err_to_rc(*h->h_err);
+  if (rc) h->poisoned = true;
+  return rc;
 }
 
 int bolt_read_pages(bolt_t* h, uint64_t first, uint64_t count, void* dst) {
@@ -1518,7 +1541,11 @@ extern "C" int bolt_autotune(bolt_t* h, const void* sample_keys, uint64_t n_samp
     const uint32_t cand[BOLT_TUNE_WIDTHS] = {64, 256, 1024, 4096, 16384, 65536};
     double best_rate = 0;
     out->batch_width = 1;
-    const uint64_t* keys = static_cast<const uint64_t*>(sample_keys);
+    // sample keys are key_bytes wide (4-byte keys zero-extended)
+    auto sample = [&](uint64_t j) -> uint64_t {
+      return h->kb == 4 ? static_cast<const uint32_t*>(sample_keys)[j]
+                        : static_cast<const uint64_t*>(sample_keys)[j];
+    };
     for (int k = 0; k < BOLT_TUNE_WIDTHS && rc == BOLT_OK; k++) {
       const uint32_t w = cand[k];
       out->widths[k] = w;
@@ -1527,7 +1554,7 @@ extern "C" int bolt_autotune(bolt_t* h, const void* sample_keys, uint64_t n_samp
       float ms = 0;
       for (int rep = 0; rep <= reps && rc == BOLT_OK; rep++) {
         for (uint32_t i = 0; i < w; i++) {
-          h->h_keys[i] = keys[(rep * (uint64_t)w + i) % n_sample];
+          h->h_keys[i] = sample((rep * (uint64_t)w + i) % n_sample);
           h->h_ops[i] = BOLT_GET;
         }
         std::memset(h->h_vin, 0, (uint64_t)w * h->vb);

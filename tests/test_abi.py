@@ -66,6 +66,20 @@ def test_bad_arguments_rejected_on_host():
     for args in [(32, 8), (1 << 16, 12), (1 << 16, 0), (1 << 16, 512)]:
         with pytest.raises(B.BoltError):
             B.plan(*args)
+    for kb in (0, 2, 5, 16):
+        with pytest.raises(B.BoltError):
+            B.plan(1 << 16, 8, key_bytes=kb)
+
+
+def test_four_byte_keys_plan_like_eight_byte_keys():
+    """A map of 4-byte keys holds them zero-extended: the same sizing, pages
+    and records as 8-byte keys, only the reported key width differs."""
+    from paper_2509_01742_b300 import bolt as B
+    for N, vb in [(10**6, 8), (1 << 20, 24)]:
+        four, eight = B.plan(N, vb, key_bytes=4), B.plan(N, vb, key_bytes=8)
+        assert four["key_bytes"] == 4 and eight["key_bytes"] == 8
+        four.pop("key_bytes"), eight.pop("key_bytes")
+        assert four == eight
 
 
 def test_binding_layouts_match_header(tmp_path):

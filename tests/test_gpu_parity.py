@@ -362,6 +362,46 @@ def test_host_call_over_many_chunks_matches_oracle(pinned, cap, bw, with_status)
     o.close(); g.close()
 
 
+def test_four_byte_keys_match_the_oracle_on_widened_keys():
+    """A map created with 4-byte keys takes uint32 keys at its host-pointer
+    calls and holds them zero-extended: build, a single-chunk call and a
+    chunked call (batch capacity 1000, width 300) give the same values,
+    status, pages, loads, rows and trace as the oracle on the same keys as
+    uint64."""
+    N, vb = 1 << 14, 8
+    o = O.OracleMap(N, vb, batch=300)
+    g = B.BoltMap(N, vb, trace=True, key_bytes=4)
+    assert g.info()["key_bytes"] == 4
+    rng = np.random.default_rng(71)
+    k32 = rng.choice(2**32, size=13000, replace=False).astype(np.uint32)
+    keys32 = k32[:12000]
+    _, vals = W.records(12000, vb, 72)
+    assert o.init(keys32.astype(np.uint64), vals, 73) == 0
+    assert g.init(keys32, vals, 73) == 0
+    _assert_state_equal(o, g, "after init")
+    g.set_param(B.BOLT_PARAM_BATCH, 300)
+    for n, cap in [(300, None), (5000, 1000)]:
+        if cap:
+            g.set_param(B.BOLT_PARAM_BATCH_CAP, cap)
+            g.set_param(B.BOLT_PARAM_BATCH, 300)
+            g.set_param(B.BOLT_PARAM_TRACE, 1)
+            assert g.init(keys32, vals, 73) == 0
+            o.close()
+            o = O.OracleMap(N, vb, batch=300)
+            assert o.init(keys32.astype(np.uint64), vals, 73) == 0
+        idx = rng.integers(0, 13000, n)  # indices >= 12000 are absent keys
+        ops = rng.integers(0, 3, n).astype(np.uint8)
+        vin = rng.integers(0, 256, (n, vb), dtype=np.uint8)
+        rc_o, vo, so = o.access(ops, k32[idx].astype(np.uint64), vin)
+        rc_g, vg, sg = g.access(ops, k32[idx], vin)
+        assert rc_o == rc_g == 0
+        assert np.array_equal(so, sg) and np.array_equal(vo, vg)
+        _assert_state_equal(o, g, f"after {n} ops")
+    with pytest.raises(ValueError):
+        g.access(ops[:1], np.array([1 << 40], dtype=np.uint64), vin[:1])
+    o.close(); g.close()
+
+
 def test_autotune_keeps_results():
     """bolt_autotune picks a tile and a batch width by measurement; the map's
     contents are unchanged (its tuning Gets only remap keys) and later builds
