@@ -868,3 +868,49 @@ def test_batches_follow_the_stated_semantics(width):
                 load[d] += 1
         assert np.array_equal(load, m.loads().astype(np.int64)), t0
     m.close()
+
+
+def test_position_map_rows_one_op_at_a_time():
+    """Position-map occupancy op by op (Sec. 4.2 d-choice at insertion; a
+    delete frees the key's slot): with one op per batch a Put of an absent
+    key adds one to the least-occupied of its four candidate rows (the
+    first of equal ones), a Delete of a present key frees its row's slot,
+    and every other op leaves the rows unchanged.  Candidate rows come from
+    the PRF recomputed with a third-party ChaCha20; rows of the init keys
+    from the init placement rule."""
+    N = 1 << 12
+    keys, vals = W.records(N // 2, 8, 81)
+    m = O.OracleMap(N, 8, batch=1)
+    assert m.init(keys, vals, 18) == 0
+    info = m.info()
+    kprf, _ = m.keys()
+    rows, Wr = info["rows"], info["round_width"]
+
+    def cand(kk):
+        w = _chacha_ref(kprf, [DOM_PM, kk & 0xFFFFFFFF, kk >> 32], 64).view("<u4")
+        return [((int(w[2 * j]) | (int(w[2 * j + 1]) << 32)) * rows) >> 64 for j in range(4)]
+
+    cnt = np.zeros(rows, dtype=np.int64)
+    row_of = {}
+    for lo in range(0, len(keys), Wr):
+        chosen = []
+        for i in range(lo, min(len(keys), lo + Wr)):
+            c = cand(int(keys[i]))
+            chosen.append((int(keys[i]), c[int(np.argmin(cnt[c]))]))
+        for kk, r in chosen:
+            row_of[kk] = r
+            cnt[r] += 1
+    assert np.array_equal(cnt, m.rowcounts().astype(np.int64))
+    ops, k, vin = W.op_stream(N // 2, 800, 8, 82, get_frac=0.3, del_frac=0.3,
+                              absent_frac=0.3)
+    for t in range(len(ops)):
+        assert m.access(ops[t:t + 1], k[t:t + 1], vin[t:t + 1])[0] == 0
+        kk, op = int(k[t]), int(ops[t])
+        if op == W.PUT and kk not in row_of:
+            c = cand(kk)
+            row_of[kk] = c[int(np.argmin(cnt[c]))]
+            cnt[row_of[kk]] += 1
+        elif op == W.DEL and kk in row_of:
+            cnt[row_of.pop(kk)] -= 1
+        assert np.array_equal(cnt, m.rowcounts().astype(np.int64)), t
+    m.close()
