@@ -22,26 +22,32 @@ thread_local Prof* g_prof = nullptr;
 
 cudaError_t raise_smem_limit(const void* kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
+  // a fixed table (no host allocation: the allocation-free build uses this)
   struct Limit {
     const void* kernel;
     int device;
     size_t bytes;
   };
+  constexpr int MAX_LIMITS = 256;
   static std::mutex mu;
-  static std::vector<Limit> limits;
+  static Limit limits[MAX_LIMITS];
+  static int n_limits = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(mu);
-  for (Limit& l : limits)
+  for (int i = 0; i < n_limits; i++) {
+    Limit& l = limits[i];
     if (l.kernel == kernel && l.device == dev) {
       if (l.bytes >= bytes) return cudaSuccess;
       e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e == cudaSuccess) l.bytes = bytes;
       return e;
     }
+  }
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) limits.push_back({kernel, dev, bytes});
+  // past the table's end the attribute is still set (under the lock) each time
+  if (e == cudaSuccess && n_limits < MAX_LIMITS) limits[n_limits++] = {kernel, dev, bytes};
   return e;
 }
 }  // namespace bdev
