@@ -71,8 +71,9 @@ typedef struct bolt bolt_t;
 /* bolt_set_param ids */
 #define BOLT_PARAM_ALPHA 1  /* HBM-bin ratio alpha in [0,1) overriding the
                                budget policy; before bolt_init */
-#define BOLT_PARAM_C 2      /* average bin load c (default 8, Sec. 5.1);
-                               before bolt_init */
+#define BOLT_PARAM_C 2      /* average bin load c in [1, 32] (default 8, Sec. 5.1);
+                               before bolt_init; the plan must give lmax <= 32
+                               (one warp lane per page slot) */
 #define BOLT_PARAM_TRACE 4  /* 1 = record the host-access trace (parity runs) */
 #define BOLT_PARAM_BATCH 5  /* operations per batch, 1..BOLT_MAX_BATCH */
 #define BOLT_PARAM_TRACE_CAP 6 /* trace capacity in entries (default 1<<22) */
@@ -90,6 +91,14 @@ typedef struct bolt bolt_t;
                                      warps; 0 = right after its eviction (default: the
                                      fastest here); results, pages and trace are the
                                      same for all */
+#define BOLT_PARAM_SPIN_LIMIT 12 /* iterations (of a ~256 ns sleep) a bounded device wait
+                                    spins before it gives up, 0..2^22 (default 2^22,
+                                    about one second): the build's grid barrier between
+                                    P2C rounds.  A wait that gives up makes bolt_init
+                                    return BOLT_E_TIMEOUT with nothing placed; the
+                                    context stays usable and the next bolt_init
+                                    rebuilds the map.  Small values exist to test that
+                                    path. */
 
 /* derived parameters (Sec. 3.3 sizing, Sec. 4.2 position map) */
 typedef struct {
@@ -183,7 +192,13 @@ BOLT_API int bolt_init_device(bolt_t* h, const void* d_keys, const void* d_vals,
  *            the call clears what must start at zero, but calls whose work
  *            overlaps on the GPU race on it, so serialise them (one stream,
  *            or wait for the previous call to return);
+ *   profile  the call records no BOLT_PARAM_PROFILE spans (recording one
+ *            creates CUDA events and grows a host list);
+ *   memory   the array (BOLT_NOALLOC_SCRATCH_BYTES) is not part of any
+ *            handle's bolt_footprint; the server counts it once against its
+ *            HBM budget;
  * Arguments, results and errors are those of bolt_init_device. */
+#define BOLT_NOALLOC_SCRATCH_BYTES 7340800ull
 BOLT_API int bolt_init_device_noalloc(bolt_t* h, const void* d_keys, const void* d_vals,
                                       uint64_t n, uint64_t seed, void* stream);
 
@@ -220,7 +235,7 @@ BOLT_API int bolt_access_device(bolt_t* h, const uint8_t* d_ops, const void* d_k
                        uint64_t n, void* stream);
 
 /* bolt_access_device_batches -- ceil(n / width) consecutive access batches
- * (Sec. 4, Algorithm 2 per batch) over DEVICE arrays of n ops: batch j takes
+ * (Alg. 1 applied to each batch) over DEVICE arrays of n ops: batch j takes
  * ops [j*width, min(n, (j+1)*width)); the result equals one
  * bolt_access_device call per slice, in order.  width 0 means the handle's
  * batch width (BOLT_PARAM_BATCH); width <= the batch capacity.  All five
@@ -345,8 +360,9 @@ BOLT_API int bolt_plan_bytes(uint64_t N, uint32_t val_bytes, uint64_t hbm_budget
  *
  * A server owns a set of maps and a scheduler thread.  Maps are admitted, in
  * the order they were added, while their planned device footprint (state,
- * batch buffers, build scratch) fits `hbm_budget`; the rest wait until a
- * removed map frees memory.  A request is up to `max_batch` Get/Put/Delete
+ * batch buffers, build scratch) fits `hbm_budget` less the library's fixed
+ * BOLT_NOALLOC_SCRATCH_BYTES array; the rest wait until a removed map frees
+ * memory.  A request is up to `max_batch` Get/Put/Delete
  * ops on one map; requests queue per map, and whenever a map has no batch on
  * the GPU the scheduler packs its queued requests (arrival order, at most
  * max_batch ops) into one access batch on the map's stream, so batches of

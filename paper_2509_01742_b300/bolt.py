@@ -20,9 +20,11 @@ BOLT_OK, BOLT_E_ARG, BOLT_E_NOMEM, BOLT_E_OVERFLOW = 0, -1, -2, -3
 BOLT_E_STATE, BOLT_E_DUPKEY, BOLT_E_CUDA, BOLT_E_TIMEOUT, BOLT_E_INTERNAL = -4, -5, -6, -7, -9
 BOLT_GET, BOLT_PUT, BOLT_DEL = 0, 1, 2
 BOLT_MAX_BATCH = 65536
+BOLT_NOALLOC_SCRATCH_BYTES = 7340800
 BOLT_PARAM_ALPHA, BOLT_PARAM_C, BOLT_PARAM_TRACE, BOLT_PARAM_BATCH = 1, 2, 4, 5
 BOLT_PARAM_TRACE_CAP, BOLT_PARAM_CHECK_KEYS, BOLT_PARAM_PROFILE = 6, 7, 8
 BOLT_PARAM_BATCH_CAP, BOLT_PARAM_LOOKAHEAD, BOLT_PARAM_DEFER_FLUSH = 9, 10, 11
+BOLT_PARAM_SPIN_LIMIT = 12
 BOLT_PROF_CLASSES = 19
 PROF_NAMES = ("sort_global", "sort_tile", "page_build", "p2c_rounds", "key_check",
               "access_batch", "gather", "evict", "build", "group", "ksort_global",
@@ -419,6 +421,25 @@ class BoltServer:
         _check(bolt_get_info(h, ctypes.byref(o)), "bolt_get_info")
         out = np.zeros((o.M, o.page_bytes), dtype=np.uint8)
         _check(bolt_read_pages(h, 0, o.M, _np_ptr(out)), "bolt_read_pages")
+        return out
+
+    def _map_handle(self, mid: int):
+        h = ctypes.c_void_p()
+        _check(bolt_server_map_handle(self._s, mid, ctypes.byref(h)), "bolt_server_map_handle")
+        return h
+
+    def map_stats(self, mid: int) -> dict:
+        """bolt_get_stats of a ready map (the server must be quiescent)."""
+        s = bolt_stats_t()
+        _check(bolt_get_stats(self._map_handle(mid), ctypes.byref(s)), "bolt_get_stats")
+        return s.as_dict()
+
+    def map_loads(self, mid: int) -> np.ndarray:
+        h = self._map_handle(mid)
+        o = bolt_info_t()
+        _check(bolt_get_info(h, ctypes.byref(o)), "bolt_get_info")
+        out = np.zeros(o.B, dtype=np.uint8)
+        _check(bolt_read_loads(h, _np_ptr(out)), "bolt_read_loads")
         return out
 
     def stats(self) -> dict:

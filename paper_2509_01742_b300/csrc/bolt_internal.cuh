@@ -46,7 +46,8 @@ constexpr uint32_t NONE32 = 0xffffffffu;
 struct MapDev {
   // sizing (Sec. 3.3, Sec. 4.2)
   uint64_t N, B, K, M, rows, Wr, vs_cap;
-  uint32_t R, lmax, vb, rec, page_bytes, pad0;
+  uint32_t R, lmax, vb, rec, page_bytes;
+  uint32_t spin_limit;  // iterations a bounded device wait spins before it gives up
   uint32_t kprf[8], kenc[8];
   // state in HBM
   uint32_t* load;      // packed u8 bin loads, B bytes (4 per word)

@@ -110,9 +110,12 @@ __global__ void k_build_apply(MapDev m, const uint64_t* __restrict__ keys,
 // --- all rounds in one persistent kernel ------------------------------------
 // A software grid barrier separates the decide and apply phases of every
 // round.  All blocks are co-resident (cooperative launch).  Every wait is
-// bounded: a block that gives up sets ERR_TIMEOUT and leaves the kernel, so
-// the others give up at their next barrier too and the kernel always ends.
-constexpr uint32_t BAR_SPIN_LIMIT = 1u << 22;  // x ~256 ns sleep: about one second
+// bounded (m.spin_limit iterations of a ~256 ns sleep; the default 2^22 is
+// about one second): a block that gives up sets ERR_TIMEOUT and leaves the
+// kernel, so the others give up at their next barrier too and the kernel
+// always ends.  The steps after the rounds then skip their work (they would
+// read a half-decided placement), and the build returns BOLT_E_TIMEOUT.
+
 // a record's claimed position-map row and slot packed in one word (rows <
 // 2^27 for N <= 2^31, slots < R <= 32); NONE32 marks a record that overflowed
 constexpr uint32_t PROW_SLOT_SHIFT = 27;
@@ -135,7 +138,7 @@ __device__ __forceinline__ bool grid_barrier(const MapDev& m, unsigned int* bar)
     } else {
       uint32_t it = 0;
       while (*gen == g) {
-        if (++it > BAR_SPIN_LIMIT) {
+        if (++it > m.spin_limit) {
           ok = 0;
           set_err(m, ERR_TIMEOUT);
           break;
@@ -214,6 +217,9 @@ __global__ void k_build_place(MapDev m, const uint64_t* __restrict__ keys,
                               const uint32_t* __restrict__ prow, unsigned long long* vs_fill) {
   const int lane = threadIdx.x & 31;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  // rounds that gave up at a barrier leave rows and slots unclaimed (and the
+  // claim words of later rounds unwritten): nothing is placed then
+  if (*(volatile uint32_t*)m.err & ERR_TIMEOUT) return;
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n;
        base += stride) {
     const uint64_t i = base + lane;
@@ -228,6 +234,10 @@ __global__ void k_build_place(MapDev m, const uint64_t* __restrict__ keys,
     if (lane == 0 && hmask) vbase = atomicAdd(vs_fill, (unsigned long long)__popc(hmask));
     vbase = __shfl_sync(0xffffffffu, vbase, 0);
     if (tag == NONE32) continue;
+    if ((tag & PROW_ROW_MASK) >= m.rows || (tag >> PROW_SLOT_SHIFT) >= m.R) {
+      set_err(m, ERR_ROW);  // not a claim the rounds wrote
+      continue;
+    }
     const uint64_t pmi = (uint64_t)(tag & PROW_ROW_MASK) * m.R + (tag >> PROW_SLOT_SHIFT);
     const uint64_t bb = bins[i];
     const uint32_t which = d == (uint32_t)(bb >> 32) ? 1u : 0u;

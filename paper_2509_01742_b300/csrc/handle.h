@@ -27,6 +27,7 @@ struct bolt {
   bool check_keys = true;
   double la_frac = 0.0;       // BOLT_PARAM_LOOKAHEAD: share of a batch's pages read ahead
   int defer_flush = 0;        // BOLT_PARAM_DEFER_FLUSH: write-back after the next batch's reads
+  uint32_t spin_limit = 1u << 22;  // BOLT_PARAM_SPIN_LIMIT: bounded device waits
   bolt_info_t info{};
 
   bdev::MapDev m{};

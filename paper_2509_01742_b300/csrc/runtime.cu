@@ -221,6 +221,7 @@ int alloc_state(bolt* h) {
   TRY(dalloc(h, &m.trace_len, 1));
   m.trace_cap = h->trace_cap;
   m.trace_on = h->trace_on ? 1 : 0;
+  m.spin_limit = h->spin_limit;
   void* hp = nullptr;
   cudaError_t e = cudaHostAlloc(&hp, I.M * I.page_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
   if (e != cudaSuccess) { free_state(h); return BOLT_E_NOMEM; }
@@ -410,8 +411,10 @@ int read_err(bolt* h, uint32_t* out) {
 }
 
 int err_to_rc(uint32_t err) {
-  if (err & ERR_OVERFLOW_MASK) return BOLT_E_OVERFLOW;
+  // a wait that gave up first: the steps after it may have flagged the
+  // half-built state as well
   if (err & ERR_TIMEOUT) return BOLT_E_TIMEOUT;
+  if (err & ERR_OVERFLOW_MASK) return BOLT_E_OVERFLOW;
   if (err) return BOLT_E_INTERNAL;
   return BOLT_OK;
 }
@@ -739,7 +742,7 @@ const char* bolt_strerror(int code) {
 int bolt_plan(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm_budget,
               double alpha, uint32_t c, bolt_info_t* out) {
   if (!out || (key_bytes != 8 && key_bytes != 4) || val_bytes < 8 || val_bytes % 8 ||
-      val_bytes > 504 || N < 64 || N > (1ull << 31) || c < 1 || c > 24)
+      val_bytes > 504 || N < 64 || N > (1ull << 31) || c < 1 || c > 32)
     return BOLT_E_ARG;
   bolt tmp;
   tmp.N = N;
@@ -844,7 +847,7 @@ int bolt_set_param(bolt_t* h, int which, double v) {
       h->alpha_override = v;
       break;
     case BOLT_PARAM_C:
-      if (!(v >= 1.0 && v <= 24.0)) return BOLT_E_ARG;
+      if (!(v >= 1.0 && v <= 32.0)) return BOLT_E_ARG;  // lmax <= 32 is checked by the plan
       h->c = (uint32_t)v;
       break;
     case BOLT_PARAM_TRACE:
@@ -862,6 +865,11 @@ int bolt_set_param(bolt_t* h, int which, double v) {
     case BOLT_PARAM_DEFER_FLUSH:
       if (!(v == 0.0 || v == 1.0 || v == 2.0)) return BOLT_E_ARG;
       h->defer_flush = (int)v;
+      return BOLT_OK;
+    case BOLT_PARAM_SPIN_LIMIT:
+      if (!(v >= 0.0 && v <= (double)(1u << 22))) return BOLT_E_ARG;
+      h->spin_limit = (uint32_t)v;
+      h->m.spin_limit = h->spin_limit;
       return BOLT_OK;
     case BOLT_PARAM_BATCH_CAP:
       if (!(v >= 1.0 && v <= (double)MAXB)) return BOLT_E_ARG;
@@ -1263,6 +1271,7 @@ constexpr uint64_t NA_OFF_BSUM = NA_OFF_PAGE + ((NOALLOC_MAX_PAGES + 1) * 4 + 25
 constexpr uint64_t NA_BSUM_CAP = 64;
 constexpr uint64_t NA_OFF_CTR = NA_OFF_BSUM + 256;
 constexpr uint64_t NA_BYTES = NA_OFF_CTR + 256;
+static_assert(NA_BYTES == BOLT_NOALLOC_SCRATCH_BYTES, "the header states the array's size");
 static_assert(NOALLOC_MAX_RECORDS >= 8192, "tag buffer must hold one sort tile");
 static_assert((NOALLOC_MAX_PAGES + 1 + 8191) / 8192 + 1 <= NA_BSUM_CAP, "block sums");
 
@@ -1309,7 +1318,8 @@ extern "C" int bolt_init_device_noalloc(bolt_t* h, const void* d_keys, const voi
   s.block_sums = reinterpret_cast<uint32_t*>(base + NA_OFF_BSUM);
   s.block_cap = NA_BSUM_CAP;
   s.counters = reinterpret_cast<unsigned long long*>(base + NA_OFF_CTR);
-  ProfScope prof_scope(h);
+  // no ProfScope: the kernel-class profiler creates events and grows a host
+  // vector per span, which this call must not do (its spans are not recorded)
   cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
   return init_impl(h, static_cast<const uint64_t*>(d_keys), static_cast<const uint8_t*>(d_vals), n,
                    seed, st, s);

@@ -359,6 +359,9 @@ int bolt_server_create(uint64_t hbm_budget, uint32_t max_batch, bolt_server_t** 
   bolt_server* s = new (std::nothrow) bolt_server();
   if (!s) return BOLT_E_NOMEM;
   s->budget = hbm_budget;
+  // the library's allocation-free build array is resident on every device
+  // that loaded it: counted once, before any map
+  s->used = BOLT_NOALLOC_SCRATCH_BYTES;
   s->max_batch = max_batch;
   cudaGetDevice(&s->device);
   s->worker = std::thread(scheduler, s);
@@ -382,7 +385,7 @@ int bolt_server_add_map(bolt_server_t* s, uint64_t N, uint32_t val_bytes, const 
   m->init_vals.assign(static_cast<const uint8_t*>(vals), static_cast<const uint8_t*>(vals) + n * val_bytes);
   m->resident = brt::resident_estimate(I, s->max_batch, SERVER_TRACE_CAP);
   m->build = brt::build_estimate(I, n);
-  if (m->resident + m->build > s->budget) {
+  if (m->resident + m->build + BOLT_NOALLOC_SCRATCH_BYTES > s->budget) {
     delete m;
     return BOLT_E_NOMEM;  // could never be admitted
   }

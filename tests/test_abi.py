@@ -40,6 +40,29 @@ def test_planner_matches_oracle(N, vb, alpha, c):
     assert B.plan(N, vb, alpha=alpha, c=c) == O.sizing(N, c, alpha, vb)
 
 
+def test_plan_limits_against_oracle():
+    """The planner takes every sizing the oracle takes that fits the device
+    layout, with the same derived sizes, and rejects the rest: c above 32;
+    lmax = c + ceil(log2 log2 N) + 1 above 32 (the kernels give each page slot
+    a warp lane); a value store of 2^29 slots or more (29-bit slot pointers in
+    a position-map entry); 2^32 position-map slots or more.  The oracle
+    itself accepts lmax up to 64 and has none of the other limits."""
+    from paper_2509_01742_b300 import bolt as B
+    for log_n in (6, 10, 16, 17, 20, 24, 28, 31):
+        N = 1 << log_n
+        for c in (1, 2, 8, 16, 24, 25, 26, 27, 28, 30, 32, 33, 40):
+            theirs = O.sizing(N, c, 0.2, 8)
+            try:
+                mine = B.plan(N, 8, alpha=0.2, c=c)
+            except B.BoltError as e:
+                assert e.rc == B.BOLT_E_ARG
+                assert c > 32 or theirs["lmax"] > 32 or theirs["vs_cap"] >= 1 << 29 or \
+                    theirs["rows"] * theirs["R"] >= 1 << 32, (N, c)
+                continue
+            assert c <= 32 and theirs["lmax"] <= 32 and theirs["vs_cap"] < 1 << 29
+            assert mine == theirs, (N, c)
+
+
 def test_budget_policy_matches_oracle():
     from paper_2509_01742_b300 import bolt as B
     # the configured budgets: 2 GB at N=2^24 (56 B values), 16 GB at N=2^30

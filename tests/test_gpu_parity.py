@@ -17,18 +17,30 @@ pytestmark = pytest.mark.gpu
 B = pytest.importorskip("paper_2509_01742_b300.bolt")
 
 
-def _pair(N, vb, batch=None, alpha=None, c=None, budget=2**64 - 1):
-    o = O.OracleMap(N, vb, hbm_budget=budget, alpha=alpha, c=c, batch=batch)
-    g = B.BoltMap(N, vb, hbm_budget=budget, alpha=alpha, c=c, trace=True, batch=batch)
+def _pair(N, vb, batch=None, alpha=None, c=None, budget=2**64 - 1, trace=True):
+    """An oracle map and a GPU map of the same sizing.  trace=False leaves the
+    GPU map's trace recorder off, as the benchmark and the server run it (the
+    batch's kernel chain is then shorter); the oracle records nothing either."""
+    o = O.OracleMap(N, vb, hbm_budget=budget, alpha=alpha, c=c, batch=batch, trace=trace)
+    g = B.BoltMap(N, vb, hbm_budget=budget, alpha=alpha, c=c, trace=trace, batch=batch)
     assert o.info() == g.info()
     return o, g
 
 
-def _assert_state_equal(o, g, what=""):
+def _assert_state_equal(o, g, what="", trace=True):
+    """Full map state: page ciphertexts (every record's page, value and
+    version), bin loads, position-map row counts, live HBM-store and stash
+    items, and (trace on) the host-access trace."""
     assert np.array_equal(o.pages(), g.pages()), f"page ciphertexts differ {what}"
     assert np.array_equal(o.loads(), g.loads()), f"bin loads differ {what}"
     assert np.array_equal(o.rowcounts().astype(np.uint8), g.rowcounts()), f"pm rows differ {what}"
-    assert np.array_equal(o.trace(), g.trace()), f"host trace differs {what}"
+    so, sg = o.stats(), g.stats()
+    for f in ("n_hbm", "n_stash", "max_load", "max_row"):
+        assert so[f] == sg[f], f"{f} differs {what}: oracle {so[f]}, gpu {sg[f]}"
+    if trace:
+        assert np.array_equal(o.trace(), g.trace()), f"host trace differs {what}"
+    else:
+        assert g.stats()["trace_len"] == 0, f"trace recorded with the recorder off {what}"
 
 
 def _run_batch(o, g, ops, keys, vin, what=""):
@@ -204,6 +216,30 @@ def test_overflow_and_dupkey_match_oracle():
     o.close(); g.close()
 
 
+def test_build_barrier_wait_gives_up_and_map_recovers():
+    """The build's P2C rounds run in one cooperative kernel whose blocks meet at
+    a software grid barrier between the decide and apply phases of each round;
+    every wait there is bounded.  With the bound set to zero iterations a
+    block that finds the barrier still closed gives up at once (N = 2^22: 8
+    blocks, 4096 barriers): bolt_init returns BOLT_E_TIMEOUT, the map refuses
+    accesses (BOLT_E_STATE) but the CUDA context is unharmed, and with the
+    bound restored the next bolt_init builds the map the oracle builds."""
+    N, vb = 1 << 22, 8
+    o, g = _pair(N, vb, trace=False)
+    keys, vals = W.records(N, vb, 33)
+    g.set_param(B.BOLT_PARAM_SPIN_LIMIT, 0)
+    assert g.init(keys, vals, 3) == B.BOLT_E_TIMEOUT
+    rc, _, _ = g.access(np.zeros(1, np.uint8), keys[:1], np.zeros((1, vb), np.uint8))
+    assert rc == B.BOLT_E_STATE
+    g.set_param(B.BOLT_PARAM_SPIN_LIMIT, 1 << 22)
+    assert o.init(keys, vals, 3) == 0 and g.init(keys, vals, 3) == 0
+    _assert_state_equal(o, g, "after the re-init", trace=False)
+    ops, k, vin = W.op_stream(N, 4096, vb, 34, del_frac=0.1, absent_frac=0.1)
+    _run_batch(o, g, ops, k, vin, "after the re-init")
+    _assert_state_equal(o, g, "after a batch", trace=False)
+    o.close(); g.close()
+
+
 def test_device_pointer_path_matches_host_path():
     """bolt_init_device / bolt_access_device on torch tensors give the same
     outputs and pages as the host-pointer calls."""
@@ -232,14 +268,16 @@ def test_device_pointer_path_matches_host_path():
     h.close(); d.close()
 
 
-def test_device_batches_back_to_back_match_oracle():
+@pytest.mark.parametrize("trace", [True, False])
+def test_device_batches_back_to_back_match_oracle(trace):
     """Twenty device-path batches enqueued without a host sync in between on
     a 2^12 map: consecutive batches often touch the same pages while the
     previous batch's write-back is still in flight.  Outputs, pages, loads
-    and the trace equal the oracle's with the same batch partition."""
+    and (recorder on) the trace equal the oracle's with the same batch
+    partition; with the recorder off the kernel chain is the benchmark's."""
     import torch
     N, vb, bw = 1 << 12, 8, 300
-    o, g = _pair(N, vb)
+    o, g = _pair(N, vb, trace=trace)
     keys, vals = W.records(3000, vb, 31)
     assert o.init(keys, vals, 8) == 0 and g.init(keys, vals, 8) == 0
     ops, k, vin = W.op_stream(3000, 20 * bw, vb, 32, get_frac=0.5, del_frac=0.1,
@@ -261,12 +299,16 @@ def test_device_batches_back_to_back_match_oracle():
         so_all.append(so)
     assert np.array_equal(np.concatenate(vo_all), t_out.cpu().numpy())
     assert np.array_equal(np.concatenate(so_all), t_st.cpu().numpy())
-    _assert_state_equal(o, g, "back-to-back device batches")
+    _assert_state_equal(o, g, "back-to-back device batches", trace=trace)
     o.close(); g.close()
 
 
-@pytest.mark.parametrize("lookahead,defer", [(0, 0), (0, 1), (0, 2), (0.3, 1), (1, 1)])
-def test_device_batches_call_matches_oracle(lookahead, defer):
+@pytest.mark.parametrize("lookahead,defer,trace", [
+    (0, 0, True), (0, 1, True), (0, 2, True), (0.3, 1, True), (1, 1, True),
+    # the benchmark's configuration (recorder off, no lookahead, no deferral)
+    # and the other pipelines with the shorter chain
+    (0, 0, False), (0, 1, False), (0.3, 1, False)])
+def test_device_batches_call_matches_oracle(lookahead, defer, trace):
     """bolt_access_device_batches (the next batch's preparation, and with
     lookahead its position-map search and page reads, run ahead on an
     internal stream; without lookahead each batch's host write-back either
@@ -279,7 +321,7 @@ def test_device_batches_call_matches_oracle(lookahead, defer):
     are all exercised."""
     import torch
     N, vb = 1 << 12, 8
-    o, g = _pair(N, vb)
+    o, g = _pair(N, vb, trace=trace)
     g.set_param(B.BOLT_PARAM_LOOKAHEAD, lookahead)
     g.set_param(B.BOLT_PARAM_DEFER_FLUSH, defer)
     keys, vals = W.records(3000, vb, 41)
@@ -309,19 +351,21 @@ def test_device_batches_call_matches_oracle(lookahead, defer):
         so_all.append(so)
     assert np.array_equal(np.concatenate(so_all), t_st.cpu().numpy())
     assert np.array_equal(np.concatenate(vo_all), t_out.cpu().numpy())
-    _assert_state_equal(o, g, "pipelined device batches")
+    _assert_state_equal(o, g, "pipelined device batches", trace=trace)
     assert g.stats()["batches"] == len(parts)
     o.close(); g.close()
 
 
-@pytest.mark.parametrize("pinned,cap,bw,with_status", [
-    (False, 1000, 300, True),   # pageable: every chunk packed through staging
-    (True, 1000, 300, True),    # pinned but small chunks: packed as well
-    (True, 4000, 1300, True),   # pinned 3900-op chunk copied directly, ragged 1100 packed
-    (True, 4000, 1300, False),  # the same without a status array
-    (False, 4000, 1300, True),  # pageable large chunks
+@pytest.mark.parametrize("pinned,cap,bw,with_status,trace", [
+    (False, 1000, 300, True, True),   # pageable: every chunk packed through staging
+    (True, 1000, 300, True, True),    # pinned but small chunks: packed as well
+    (True, 4000, 1300, True, True),   # pinned 3900-op chunk copied directly, ragged 1100 packed
+    (True, 4000, 1300, False, True),  # the same without a status array
+    (False, 4000, 1300, True, True),  # pageable large chunks
+    (False, 1000, 300, True, False),  # recorder off (the end-to-end benchmark's calls)
+    (True, 4000, 1300, True, False),
 ])
-def test_host_call_over_many_chunks_matches_oracle(pinned, cap, bw, with_status):
+def test_host_call_over_many_chunks_matches_oracle(pinned, cap, bw, with_status, trace):
     """bolt_access over 5000 ops with a batch capacity below the call:
     chunks of whole batches alternate between two device I/O sets, each
     chunk a pipelined run of batches.  Pageable or small chunks cross the
@@ -331,8 +375,8 @@ def test_host_call_over_many_chunks_matches_oracle(pinned, cap, bw, with_status)
     import ctypes
     import torch
     N, vb = 1 << 14, 16
-    o = O.OracleMap(N, vb, batch=bw)
-    g = B.BoltMap(N, vb, trace=True)
+    o = O.OracleMap(N, vb, batch=bw, trace=trace)
+    g = B.BoltMap(N, vb, trace=trace)
     g.set_param(B.BOLT_PARAM_BATCH_CAP, cap)
     g.set_param(B.BOLT_PARAM_BATCH, bw)
     keys, vals = W.records(12000, vb, 51)
@@ -357,7 +401,7 @@ def test_host_call_over_many_chunks_matches_oracle(pinned, cap, bw, with_status)
     else:
         assert not sg.any()
     assert np.array_equal(vo, vg)
-    _assert_state_equal(o, g, "chunked host call")
+    _assert_state_equal(o, g, "chunked host call", trace=trace)
     assert g.stats()["batches"] == (5000 + bw - 1) // bw
     o.close(); g.close()
 

@@ -88,6 +88,80 @@ def test_mixed_results_equal_alone_and_oracle_replay():
     srv.close()
 
 
+def test_sixteen_maps_full_batches_match_oracle():
+    """Sixteen maps of N log-uniform in [2^12, 2^20] (32 B records) behind one
+    server with 4096-op batches; requests of log-uniform size 1..4096 (half
+    Zipf(0.99)) arrive from four client threads at once, so batches of
+    different maps overlap on the device and a map's queued requests share
+    batches.  Each request's values and status equal a plain dict applying
+    that map's requests alone, in order; the oracle replaying each map's
+    logged batch partition reproduces its page ciphertexts, bin loads,
+    position-map rows and stash and HBM-store counts."""
+    vb, n_maps, n_req, max_batch = 24, 16, 24, 4096
+    rng = np.random.default_rng(0x5EED0015)
+    sizes = [int(2 ** x) for x in rng.uniform(12, 20, n_maps)]
+    srv = B.BoltServer(hbm_budget=64 << 30, max_batch=max_batch)
+    maps, data, reqs = [], [], []
+    for j, N in enumerate(sizes):
+        keys, vals = W.records(N, vb, 900 + j)
+        maps.append(srv.add_map(N, vb, keys, vals, 1000 + j))
+        data.append((N, keys, vals))
+        reqs.append(_requests(N, n_req, vb, 1100 + j, max_batch))
+    ids = {}
+    lock = threading.Lock()
+
+    def client(part):
+        for j in part:
+            for r in range(n_req):
+                ops, k, vin = reqs[j][r]
+                rid = srv.submit(maps[j], ops, k, vin)
+                with lock:
+                    ids[(j, r)] = rid
+    # four threads, four maps each: a map's requests keep their order
+    threads = [threading.Thread(target=client, args=(list(range(t, n_maps, 4)),))
+               for t in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    got = {}
+    for (j, r), rid in ids.items():
+        rc, vout, st, info = srv.wait(rid, len(reqs[j][r][0]), maps[j], timeout_ms=300000)
+        assert rc == 0, rc
+        got[(j, r)] = (vout, st)
+    shared = 0
+    for j, (N, keys, vals) in enumerate(data):
+        model = DictModel(keys, vals)
+        for r in range(n_req):
+            ops, k, vin = reqs[j][r]
+            ev, es = model.apply(ops, k, vin, vb)
+            assert np.array_equal(got[(j, r)][0], ev) and np.array_equal(got[(j, r)][1], es), \
+                f"map {j} request {r}"
+        log = srv.batches(maps[j])
+        assert log.sum() == sum(len(reqs[j][r][0]) for r in range(n_req))
+        assert log.max() <= max_batch
+        shared += n_req - len(log)
+        allops = np.concatenate([reqs[j][r][0] for r in range(n_req)])
+        allk = np.concatenate([reqs[j][r][1] for r in range(n_req)])
+        allv = np.concatenate([reqs[j][r][2] for r in range(n_req)])
+        o = O.OracleMap(N, vb, trace=False)
+        assert o.init(keys, vals, 1000 + j) == 0
+        lo = 0
+        for s in log:
+            rc, _, _ = o.access(allops[lo:lo + s], allk[lo:lo + s], allv[lo:lo + s])
+            assert rc == 0
+            lo += s
+        assert np.array_equal(o.pages(), srv.map_pages(maps[j])), f"pages of map {j}"
+        st = srv.map_stats(maps[j])
+        so = o.stats()
+        for f in ("n_hbm", "n_stash", "max_load", "max_row"):
+            assert so[f] == st[f], f"map {j}: {f} oracle {so[f]} server {st[f]}"
+        assert np.array_equal(o.loads(), srv.map_loads(maps[j])), f"loads of map {j}"
+        o.close()
+    assert shared > 0, "no two requests of a map ever shared a batch"
+    srv.close()
+
+
 def test_admission_by_budget():
     import time
     vb, N = 24, 1 << 16
@@ -98,11 +172,12 @@ def test_admission_by_budget():
     t0 = time.time()
     while probe.map_state(pid) == 0 and time.time() - t0 < 60:
         time.sleep(0.01)
-    res = probe.stats()["used"]
+    fixed = B.BOLT_NOALLOC_SCRATCH_BYTES  # counted once by every server
+    res = probe.stats()["used"] - fixed
     probe.close()
     _, build = B.plan_bytes(N, vb, batch_cap=512, n_init=N // 2)
     # room for two maps (plus one build) but not three
-    srv = B.BoltServer(hbm_budget=2 * res + build + (res // 2), max_batch=512)
+    srv = B.BoltServer(hbm_budget=fixed + 2 * res + build + (res // 2), max_batch=512)
     ids = [srv.add_map(N, vb, keys, vals, 10 + j) for j in range(3)]
     ops, k, vin = W.op_stream(N // 2, 100, vb, 6)
     r0 = srv.submit(ids[0], ops, k, vin)

@@ -40,6 +40,9 @@ def test_noalloc_build_matches_device_build_twice():
         tv = torch.from_numpy(vals.copy()).cuda()
         assert ref.init_device(tk, tv, seed) == 0
         assert _noalloc_init(nal, tk, tv, seed) == 0
+        # nothing was allocated for the build: this handle never ran
+        # bolt_init or bolt_init_device, so it holds no build scratch
+        assert nal.footprint()[1] == 0
         assert np.array_equal(ref.pages(), nal.pages()), f"pages differ on call {call}"
         assert np.array_equal(ref.loads(), nal.loads()), f"loads differ on call {call}"
         assert np.array_equal(ref.rowcounts(), nal.rowcounts()), f"rows differ on call {call}"
@@ -49,8 +52,42 @@ def test_noalloc_build_matches_device_build_twice():
         assert rc1 == rc2 == 0
         assert np.array_equal(v1, v2) and np.array_equal(s1, s2)
         assert np.array_equal(ref.pages(), nal.pages())
+        assert nal.footprint()[1] == 0
     ref.close()
     nal.close()
+
+
+@pytest.mark.parametrize("case", ["far_apart", "max_key_twice", "max_key_once"])
+def test_noalloc_key_check(case):
+    """The allocation-free build checks key uniqueness (Sec. 2.1) by sorting a
+    copy of the keys, padded with all-ones words, and comparing neighbours:
+    a duplicate pair far apart is found, the all-ones key given twice is
+    found, and given once among distinct keys (equal to the padding) it is
+    not mistaken for a duplicate.  2^17 keys, within the array's limit."""
+    import torch
+    n = 1 << 17
+    keys, vals = W.records(n, 8, 91)
+    top = np.uint64(0xFFFFFFFFFFFFFFFF)
+    if case == "far_apart":
+        keys[n - 1] = keys[2]
+    elif case == "max_key_twice":
+        keys[7] = top
+        keys[n - 3] = top
+    else:
+        keys[n // 2] = top
+    m = B.BoltMap(n, 8)
+    tk = torch.from_numpy(keys.view(np.int64)).cuda()
+    tv = torch.from_numpy(vals.copy()).cuda()
+    rc = _noalloc_init(m, tk, tv, 4)
+    assert rc == (0 if case == "max_key_once" else B.BOLT_E_DUPKEY)
+    assert m.footprint()[1] == 0
+    if rc == 0:
+        # the map built beside the padding value serves its keys
+        ops = np.zeros(64, np.uint8)
+        idx = np.arange(n // 2 - 32, n // 2 + 32)
+        rc2, vout, st = m.access(ops, keys[idx], np.zeros((64, 8), np.uint8))
+        assert rc2 == 0 and st.all() and np.array_equal(vout, vals[idx])
+    m.close()
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
