@@ -117,7 +117,12 @@ typedef struct {
   uint64_t n_hbm, n_stash;     /* live items in the HBM store and the stash */
   uint64_t batches;            /* batches processed since bolt_init */
   uint64_t trace_len;          /* recorded trace entries */
-  uint32_t max_load, max_row;  /* largest bin load / position-map row count */
+  uint32_t max_load, max_row;  /* largest bin load / position-map row count now */
+  /* peaks since bolt_init, the quantities Claims 3.2-3.4 bound (Sec. 3.3
+   * "Dimensions in practice"): the largest HBM-store and stash occupancy at
+   * the end of the build or of any batch, and the largest bin load reached */
+  uint64_t peak_hbm, peak_stash;
+  uint32_t peak_load, pad;
 } bolt_stats_t;
 
 /*
@@ -255,7 +260,11 @@ BOLT_API int bolt_sync(bolt_t* h);
 /* bolt_destroy -- release every allocation of the handle (NULL is a no-op). */
 BOLT_API int bolt_destroy(bolt_t* h);
 
-/* bolt_get_info / bolt_get_stats -- derived parameters and counters. */
+/* bolt_get_info / bolt_get_stats -- derived parameters and counters.  The
+ * occupancy figures come from counters the kernels keep on the device;
+ * bolt_get_stats recounts n_hbm and n_stash from the bin loads and the
+ * reverse index and returns BOLT_E_INTERNAL if the two disagree (not checked
+ * on a poisoned map). */
 BOLT_API int bolt_get_info(const bolt_t* h, bolt_info_t* out);
 BOLT_API int bolt_get_stats(bolt_t* h, bolt_stats_t* out);
 

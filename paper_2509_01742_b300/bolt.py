@@ -55,10 +55,12 @@ class bolt_stats_t(ctypes.Structure):
     _fields_ = [("ops", ctypes.c_uint64), ("n_hbm", ctypes.c_uint64),
                 ("n_stash", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("trace_len", ctypes.c_uint64), ("max_load", ctypes.c_uint32),
-                ("max_row", ctypes.c_uint32)]
+                ("max_row", ctypes.c_uint32), ("peak_hbm", ctypes.c_uint64),
+                ("peak_stash", ctypes.c_uint64), ("peak_load", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "pad"}
 
 
 class bolt_profile_t(ctypes.Structure):

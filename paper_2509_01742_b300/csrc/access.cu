@@ -742,6 +742,7 @@ __global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
     if (lane == 0) {
       m.vs_live[vs] = 0;
       ring_push(m, vs);
+      stat_leave(m, meta_loc(meta) == LOC_HBM, 1);
     }
   }
   if (lane == 0) {
@@ -874,8 +875,10 @@ __device__ __forceinline__ void evict_page(const MapDev& m, const BatchDev& b, u
   // back to the free ring (one tail bump per warp)
   const uint32_t smask2 = __ballot_sync(0xffffffffu, sv);
   unsigned long long tail = 0;
-  if (smask2 && lane == __ffs(smask2) - 1)
+  if (smask2 && lane == __ffs(smask2) - 1) {
     tail = atomicAdd(m.ring_ctr + 1, (unsigned long long)__popc(smask2));
+    stat_leave(m, false, __popc(smask2));
+  }
   tail = __shfl_sync(0xffffffffu, tail, smask2 ? __ffs(smask2) - 1 : 0);
   if (sv) {
     const uint32_t pmi = m.vs_pm[vs];
@@ -981,10 +984,11 @@ __global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
   dep_wait();
   const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
   bool go = i < hi && b.leader[i] == i && b.fpres[i];
-  uint32_t dest = 0;
+  uint32_t dest = 0, new_load = 0;
   if (go) {
     dest = b.rdest[i];
-    if (byte_inc(m.load, dest) + 1 > m.lmax) {
+    new_load = byte_inc(m.load, dest) + 1;
+    if (new_load > m.lmax) {
       set_err(m, ERR_LOAD);
       go = false;
     } else if (b.hit[i] == NONE32 && byte_inc(m.rowcnt, b.rrow[i]) + 1 > m.R) {
@@ -994,6 +998,7 @@ __global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
   }
   const unsigned long long pos = ring_take(m, go);
   if (go) remap_place(m, b, i, dest, pos);
+  stat_place(m, go, dest < m.K, new_load);
 }
 
 // Small maps (B <= 2^17 bins, <= 2^16 rows): every P2C round of the batch in
@@ -1051,6 +1056,12 @@ __global__ void __launch_bounds__(1024) k_remap_smem(MapDev m, BatchDev b, uint3
     __syncthreads();
   }
   if (err) set_err(m, err);
+  // peak load: a bin's final load is the value its last placement reached
+  uint32_t top = 0;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+    if (b.leader[i] == i && b.fpres[i]) top = max(top, sbyte_get(sload, b.rdest[i]));
+  top = __reduce_max_sync(0xffffffffu, top);
+  if ((threadIdx.x & 31) == 0 && top) atomicMax(m.stat + ST_PEAK_LOAD, (unsigned long long)top);
   for (uint32_t w = threadIdx.x; w < lw; w += blockDim.x) m.load[w] = sload[w];
   for (uint32_t w = threadIdx.x; w < rw; w += blockDim.x) m.rowcnt[w] = srow[w];
 }
@@ -1117,12 +1128,16 @@ __global__ void __launch_bounds__(1024) k_remap_smem_reg(MapDev m, BatchDev b, u
     __syncthreads();
   }
   if (err) set_err(m, err);
+  uint32_t top = 0;
 #pragma unroll
   for (int k = 0; k < REMAP_REG_OPS; k++)
     if (act[k]) {
       b.rdest[op[k]] = dest[k];
       if (fresh[k]) b.rrow[op[k]] = row[k];
+      top = max(top, sbyte_get(sload, dest[k]));  // final load of the bin (peak)
     }
+  top = __reduce_max_sync(0xffffffffu, top);
+  if ((threadIdx.x & 31) == 0 && top) atomicMax(m.stat + ST_PEAK_LOAD, (unsigned long long)top);
   for (uint32_t w = threadIdx.x; w < lw; w += blockDim.x) m.load[w] = sload[w];
   for (uint32_t w = threadIdx.x; w < rw; w += blockDim.x) m.rowcnt[w] = srow[w];
 }
@@ -1130,8 +1145,11 @@ __global__ void __launch_bounds__(1024) k_remap_smem_reg(MapDev m, BatchDev b, u
 __global__ void k_remap_rest(MapDev m, BatchDev b, uint32_t n) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool go = i < n && b.leader[i] == i && b.fpres[i];
+  const uint32_t dest = go ? b.rdest[i] : 0;
   const unsigned long long pos = ring_take(m, go);
-  if (go) remap_place(m, b, i, b.rdest[i], pos);
+  if (go) remap_place(m, b, i, dest, pos);
+  // the loads were raised in k_remap_smem(_reg), which took their peak
+  stat_place(m, go, dest < m.K, 0);
 }
 
 __global__ void k_clear_keys(BatchDev b, uint32_t n) {

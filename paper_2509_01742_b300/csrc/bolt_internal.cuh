@@ -66,6 +66,7 @@ struct MapDev {
   uint64_t* version;   // [M] page write counters (cipher nonces)
   uint8_t* pages;      // device alias of the pinned host pages [M * page_bytes]
   uint32_t* err;       // error word
+  unsigned long long* stat;  // [ST_WORDS] occupancy counters and their peaks (below)
   uint32_t* trace;     // host-access trace (optional)
   unsigned long long* trace_len;
   uint64_t trace_cap;
@@ -209,6 +210,42 @@ __device__ __forceinline__ uint32_t pick_row(const MapDev& m, const uint32_t row
 }
 
 __device__ __forceinline__ void set_err(const MapDev& m, uint32_t bits) { atomicOr(m.err, bits); }
+
+// Occupancy statistics (the quantities Claims 3.2-3.4 bound): live items in
+// the HBM store and in the stash, and the largest values seen since the build.
+// The stash and the HBM store only shrink before a batch's remap phase
+// (find_remove, eviction) and only grow in it, so the running maximum taken
+// at every increment of the remap phase is the maximum over end-of-batch
+// values; a bin load only grows by a placement, so its running maximum at
+// every increment is the peak load.
+enum : int { ST_HBM = 0, ST_STASH = 1, ST_PEAK_HBM = 2, ST_PEAK_STASH = 3, ST_PEAK_LOAD = 4,
+             ST_WORDS = 8 };
+
+// A warp's placements of the remap phase: `placed` lanes put one item into
+// the HBM store (hbm) or the stash, a bin reaching `new_load`.  All 32 lanes
+// call; one lane per warp updates the counters.
+__device__ __forceinline__ void stat_place(const MapDev& m, bool placed, bool hbm,
+                                           uint32_t new_load) {
+  const uint32_t hm = __ballot_sync(0xffffffffu, placed && hbm);
+  const uint32_t sm = __ballot_sync(0xffffffffu, placed && !hbm);
+  const uint32_t top = __reduce_max_sync(0xffffffffu, placed ? new_load : 0u);
+  if ((threadIdx.x & 31) == 0) {
+    if (hm) {
+      const unsigned long long c = __popc(hm);
+      atomicMax(m.stat + ST_PEAK_HBM, atomicAdd(m.stat + ST_HBM, c) + c);
+    }
+    if (sm) {
+      const unsigned long long c = __popc(sm);
+      atomicMax(m.stat + ST_PEAK_STASH, atomicAdd(m.stat + ST_STASH, c) + c);
+    }
+    if (top) atomicMax(m.stat + ST_PEAK_LOAD, (unsigned long long)top);
+  }
+}
+
+// items leaving the HBM store (hbm) or the stash
+__device__ __forceinline__ void stat_leave(const MapDev& m, bool hbm, unsigned long long count) {
+  atomicAdd(m.stat + (hbm ? ST_HBM : ST_STASH), 0ull - count);
+}
 
 // Block-wide exclusive sum (blockDim.x a multiple of 32, <= 1024); `sh`
 // holds 32 words of shared memory; `total` receives the block total.

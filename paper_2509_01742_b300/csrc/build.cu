@@ -381,6 +381,10 @@ __global__ void k_page_build(MapDev m, const uint64_t* __restrict__ keys,
   }
 }
 
+// The free ring gets every value-store slot the placement left; the
+// occupancy counters start from the build's HBM residents (an empty stash),
+// and the peak bin load from the largest load the build left (blockDim a
+// multiple of 32).
 __global__ void k_ring_fill(MapDev m, const unsigned long long* vs_fill) {
   const uint64_t used = *vs_fill < m.vs_cap ? *vs_fill : m.vs_cap;
   const uint64_t nfree = m.vs_cap - used;
@@ -390,7 +394,17 @@ __global__ void k_ring_fill(MapDev m, const unsigned long long* vs_fill) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     m.ring_ctr[0] = 0;
     m.ring_ctr[1] = nfree;
+    m.stat[ST_HBM] = used;
+    m.stat[ST_PEAK_HBM] = used;
+    m.stat[ST_STASH] = 0;
+    m.stat[ST_PEAK_STASH] = 0;
   }
+  uint32_t top = 0;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < m.B;
+       b += (uint64_t)gridDim.x * blockDim.x)
+    top = max(top, byte_get(m.load, b));
+  top = __reduce_max_sync(0xffffffffu, top);
+  if ((threadIdx.x & 31) == 0 && top) atomicMax(m.stat + ST_PEAK_LOAD, (unsigned long long)top);
 }
 
 static int sm_count() {

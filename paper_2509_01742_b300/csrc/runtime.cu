@@ -217,6 +217,7 @@ int alloc_state(bolt* h) {
   TRY(dalloc(h, &m.revcnt, I.M / 4 + 2));
   TRY(dalloc(h, &m.version, I.M));
   TRY(dalloc(h, &m.err, 1));
+  TRY(dalloc(h, &m.stat, ST_WORDS));
   TRY(dalloc(h, &m.trace, h->trace_cap));
   TRY(dalloc(h, &m.trace_len, 1));
   m.trace_cap = h->trace_cap;
@@ -650,6 +651,7 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
   cudaMemsetAsync(m.revcnt, 0, (I.M / 4 + 2) * 4, st);
   cudaMemsetAsync(m.version, 0, I.M * 8, st);
   cudaMemsetAsync(m.err, 0, 4, st);
+  cudaMemsetAsync(m.stat, 0, ST_WORDS * 8, st);
   cudaMemsetAsync(m.trace_len, 0, 8, st);
   // keys -> K_prf, K_enc
   k_kdf<<<1, 1, 0, st>>>(seed, h->d_kdf);
@@ -1238,9 +1240,16 @@ int bolt_get_stats(bolt_t* h, bolt_stats_t* out) {
   for (uint64_t r = 0; r < I.rows; r++)
     if (rows[r] > out->max_row) out->max_row = rows[r];
   for (uint64_t q = 0; q < I.M; q++) out->n_stash += rc[q];
-  unsigned long long tl = 0;
-  cudaMemcpy(&tl, h->m.trace_len, 8, cudaMemcpyDeviceToHost);
+  unsigned long long tl = 0, st[ST_WORDS] = {};
+  if (cudaMemcpy(&tl, h->m.trace_len, 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(st, h->m.stat, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return BOLT_E_CUDA;
   out->trace_len = tl;
+  out->peak_hbm = st[ST_PEAK_HBM];
+  out->peak_stash = st[ST_PEAK_STASH];
+  out->peak_load = (uint32_t)st[ST_PEAK_LOAD];
+  if (h->initialized && !h->poisoned && (st[ST_HBM] != out->n_hbm || st[ST_STASH] != out->n_stash))
+    return BOLT_E_INTERNAL;
   return BOLT_OK;
 }
 
@@ -1365,7 +1374,7 @@ uint64_t resident_estimate(const bolt_info_t& I, uint64_t cap, uint64_t trace_ca
   const uint64_t slots = I.rows * I.R, vb = I.val_bytes;
   uint64_t b = 4 * (I.B / 4 + 2) + 4 * (I.rows / 4 + 2) + slots * (8 + 8 + 4) +
                I.vs_cap * (8 + vb + 4 + 1 + 4) + 16 + I.M * I.lmax * 4 + 4 * (I.M / 4 + 2) +
-               I.M * 8 + 4 + trace_cap * 4 + 8;
+               I.M * 8 + 4 + ST_WORDS * 8 + trace_cap * 4 + 8;
   uint64_t cap2 = 1;
   while (cap2 < cap) cap2 <<= 1;
   const uint64_t sort_cap = cap2 <= 512 ? 512 : (cap2 < 4096 ? 4096 : cap2);

@@ -35,7 +35,7 @@ def _assert_state_equal(o, g, what="", trace=True):
     assert np.array_equal(o.loads(), g.loads()), f"bin loads differ {what}"
     assert np.array_equal(o.rowcounts().astype(np.uint8), g.rowcounts()), f"pm rows differ {what}"
     so, sg = o.stats(), g.stats()
-    for f in ("n_hbm", "n_stash", "max_load", "max_row"):
+    for f in ("n_hbm", "n_stash", "max_load", "max_row", "peak_hbm", "peak_stash", "peak_load"):
         assert so[f] == sg[f], f"{f} differs {what}: oracle {so[f]}, gpu {sg[f]}"
     if trace:
         assert np.array_equal(o.trace(), g.trace()), f"host trace differs {what}"

@@ -154,7 +154,8 @@ def test_sixteen_maps_full_batches_match_oracle():
         assert np.array_equal(o.pages(), srv.map_pages(maps[j])), f"pages of map {j}"
         st = srv.map_stats(maps[j])
         so = o.stats()
-        for f in ("n_hbm", "n_stash", "max_load", "max_row"):
+        for f in ("n_hbm", "n_stash", "max_load", "max_row", "peak_hbm", "peak_stash",
+                  "peak_load"):
             assert so[f] == st[f], f"map {j}: {f} oracle {so[f]} server {st[f]}"
         assert np.array_equal(o.loads(), srv.map_loads(maps[j])), f"loads of map {j}"
         o.close()
