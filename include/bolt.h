@@ -91,6 +91,11 @@ typedef struct bolt bolt_t;
                                      warps; 0 = right after its eviction (default: the
                                      fastest here); results, pages and trace are the
                                      same for all */
+#define BOLT_PARAM_FUSED 13 /* 1 = a batch of at most 32 operations runs as one
+                               single-CTA launch that also writes its pages to
+                               the host (default); 0 = the multi-kernel chain
+                               of larger batches for every batch.  Results,
+                               pages and trace are the same for both */
 #define BOLT_PARAM_SPIN_LIMIT 12 /* iterations (of a ~256 ns sleep) a bounded device wait
                                     spins before it gives up, 0..2^22 (default 2^22,
                                     about one second): the build's grid barrier between

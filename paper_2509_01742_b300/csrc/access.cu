@@ -687,20 +687,11 @@ __device__ __forceinline__ void ring_push(const MapDev& m, uint32_t slot) {
   m.ring[pos % m.vs_cap] = slot;
 }
 
-// warp per op: find_remove for hits (Alg. 1 lines 6 and 9)
-__global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
-  dep_wait();
-  // the previous batch's page table was last read by this batch's gather:
-  // return the entries it used to NONE for the batch after this one
-  if (b.clr_ht_key)
-    for (uint32_t h = blockIdx.x * blockDim.x + threadIdx.x; h <= b.clr_mask;
-         h += gridDim.x * blockDim.x) {
-      b.clr_ht_key[h] = NONE32;
-      b.clr_ht_min[h] = NONE32;
-    }
-  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= n || b.leader[i] != i) return;
+// find_remove of op i's hit (Alg. 1 lines 6 and 9), one warp; a no-op for
+// non-leaders
+__device__ __forceinline__ void find_op(const MapDev& m, const BatchDev& b, uint32_t i,
+                                        int lane) {
+  if (b.leader[i] != i) return;
   const uint32_t slot = b.hit[i];
   if (slot == NONE32) {
     if (lane == 0) b.init_present[i] = 0;
@@ -756,6 +747,25 @@ __global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
   }
 }
 
+// the previous batch's page table was last read by this batch's gather:
+// return the entries it used to NONE for the batch after this one
+__device__ __forceinline__ void clear_prev_table(const BatchDev& b, uint32_t tid,
+                                                 uint32_t nthreads) {
+  if (b.clr_ht_key)
+    for (uint32_t h = tid; h <= b.clr_mask; h += nthreads) {
+      b.clr_ht_key[h] = NONE32;
+      b.clr_ht_min[h] = NONE32;
+    }
+}
+
+// warp per op: find_remove for hits
+__global__ void k_find(MapDev m, BatchDev b, uint32_t n) {
+  dep_wait();
+  clear_prev_table(b, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  const uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i < n) find_op(m, b, i, threadIdx.x & 31);
+}
+
 // thread per op: Get/Put/Delete semantics (Alg. 1 line 12)
 // P2C decision for leader i on the round-start loads (Alg. 1 lines 13-14):
 // the less loaded of its REMAP pair, and for a new key the position-map row
@@ -805,13 +815,14 @@ __device__ __forceinline__ void exec_op(const MapDev& m, const BatchDev& b, uint
   }
 }
 
-// warp per page of the batch: write-back with eviction (Alg. 1 line 10)
-__device__ __forceinline__ void evict_page(const MapDev& m, const BatchDev& b, uint32_t block,
-                                           uint8_t* sbuf) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t e = block * (blockDim.x >> 5) + wid;
-  if (e >= *b.dcount) return;
-  uint8_t* plain = sbuf + (size_t)wid * (m.page_bytes + 32 * 16);
+// One warp writes back page e of the batch's page list with eviction (Alg. 1
+// line 10): `plain` is this warp's page_bytes + 512 bytes of shared memory.
+// The ciphertext goes to the page's slot in dbuf (the next batch reads it
+// there while the host copy is in flight) and, with to_host, also straight
+// to the host page.
+__device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, uint32_t e,
+                                          uint8_t* plain, bool to_host) {
+  const int lane = threadIdx.x & 31;
   ulonglong2* items = reinterpret_cast<ulonglong2*>(plain + m.page_bytes);
   const uint32_t d = b.dslot[e];
   const uint64_t q = b.dpage[e];
@@ -863,8 +874,13 @@ __device__ __forceinline__ void evict_page(const MapDev& m, const BatchDev& b, u
   __syncwarp();
   const uint64_t ver = m.version[q] + 1;
   // the old plaintext in dbuf is no longer read: the ciphertext replaces it
-  // and k_flush copies it to the host page
-  page_encrypt_to(m, plain, b.dbuf + (uint64_t)d * m.page_bytes, q, ver);
+  // and k_flush copies it to the host page (or this warp does, below)
+  uint8_t* cipher = b.dbuf + (uint64_t)d * m.page_bytes;
+  page_encrypt_to(m, plain, cipher, q, ver);
+  if (to_host)  // each lane stores the 16-byte pieces it encrypted
+    for (uint32_t o = 16 * lane; o < m.page_bytes; o += 512)
+      *reinterpret_cast<uint4*>(m.pages + q * m.page_bytes + o) =
+          *reinterpret_cast<const uint4*>(cipher + o);
   __syncwarp();
   if (lane == 0) {
     m.version[q] = ver;
@@ -886,6 +902,15 @@ __device__ __forceinline__ void evict_page(const MapDev& m, const BatchDev& b, u
     m.vs_live[vs] = 0;
     m.ring[(tail + __popc(smask2 & below)) % m.vs_cap] = vs;
   }
+}
+
+// warp per page of the batch (block `block` of the eviction blocks)
+__device__ __forceinline__ void evict_page(const MapDev& m, const BatchDev& b, uint32_t block,
+                                           uint8_t* sbuf) {
+  const int wid = threadIdx.x >> 5;
+  const uint32_t e = block * (blockDim.x >> 5) + wid;
+  if (e >= *b.dcount) return;
+  evict_one(m, b, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), false);
 }
 
 // The first blocks run the ops' semantics (thread per op) and, when the
@@ -980,10 +1005,11 @@ __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, 
   }
 }
 
-__global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
-  dep_wait();
-  const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
-  bool go = i < hi && b.leader[i] == i && b.fpres[i];
+// place op i if `go` (a leader whose key is present after the batch, in the
+// current round): bump the counts of its decided bin (and row, for a new
+// key), take a ring slot, write its entries.  All 32 lanes of the warp call.
+__device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& b, uint32_t i,
+                                               bool go) {
   uint32_t dest = 0, new_load = 0;
   if (go) {
     dest = b.rdest[i];
@@ -999,6 +1025,12 @@ __global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
   const unsigned long long pos = ring_take(m, go);
   if (go) remap_place(m, b, i, dest, pos);
   stat_place(m, go, dest < m.K, new_load);
+}
+
+__global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
+  dep_wait();
+  const uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+  remap_apply_op(m, b, i, i < hi && b.leader[i] == i && b.fpres[i]);
 }
 
 // Small maps (B <= 2^17 bins, <= 2^16 rows): every P2C round of the batch in
@@ -1160,6 +1192,175 @@ __global__ void k_clear_keys(BatchDev b, uint32_t n) {
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Small batches in one CTA.  A batch of at most FUSED_MAX_OPS operations (a
+// batch of one is Alg. 1 for one command) runs every step of the chain above
+// in a single launch, with block barriers where the chain has kernel
+// boundaries: the same device functions on the same tables and buffers, so
+// the same results, pages and trace.  Its written pages go to the host from
+// this kernel (no separate write-back launch): a caller issuing one
+// operation at a time pays one launch per operation.
+constexpr uint32_t FUSED_THREADS = 512;
+
+// the P2C decision of op i on round-start counts read from L2: the counts
+// change by atomics between the rounds of this one launch
+__device__ __forceinline__ void decide_op_l2(const MapDev& m, const BatchDev& b, uint32_t i) {
+  auto get = [](const uint32_t* w, uint64_t k) {
+    return (__ldcg(w + (k >> 2)) >> ((uint32_t)(k & 3) * 8)) & 0xffu;
+  };
+  const uint64_t pr = b.rpair[i];
+  const uint32_t p1 = (uint32_t)pr, p2 = (uint32_t)(pr >> 32);
+  b.rdest[i] = get(m.load, p1) <= get(m.load, p2) ? p1 : p2;
+  if (b.hit[i] == NONE32) {
+    const uint4 r4 = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
+    const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+    uint32_t best = rr[0], bc = get(m.rowcnt, rr[0]);
+#pragma unroll
+    for (int j = 1; j < 4; j++) {
+      const uint32_t c = get(m.rowcnt, rr[j]);
+      if (c < bc) {
+        best = rr[j];
+        bc = c;
+      }
+    }
+    b.rrow[i] = best;
+  }
+}
+
+__global__ void __launch_bounds__(FUSED_THREADS)
+    k_fused(MapDev m, BatchDev b, uint32_t n, uint64_t t0, uint32_t evict_warps) {
+  extern __shared__ __align__(16) uint8_t sbuf[];
+  const int lane = threadIdx.x & 31;
+  const uint32_t wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // 1. per op the DUMMY pair, the REMAP pair and the position-map rows (one
+  //    ChaCha20 block each); warp 0 groups the ops by key with n^2 compares:
+  //    leader = first op on the key, previous writer of each op, last writer
+  //    of each key group
+  if (threadIdx.x == 0) *b.dcount = 0;
+  if (b.h_in) {
+    // the inputs straight from the caller's pinned staging (16-byte reads
+    // over the link; both buffers hold the rounded-up tail)
+    const uint32_t words = (n * (9 + m.vb) + 15) / 16;
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x)
+      reinterpret_cast<uint4*>(b.keys)[w] = reinterpret_cast<const uint4*>(b.h_in)[w];
+    __syncthreads();
+  }
+  for (uint32_t tid = threadIdx.x; tid < 3 * n; tid += blockDim.x) {
+    const uint32_t i = tid / 3, kind = tid % 3;
+    uint32_t p1, p2;
+    if (kind == 0) {
+      prf_pair(m, DOM_DUMMY, t0 + i, p1, p2);
+      b.pair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
+    } else if (kind == 1) {
+      prf_pair(m, DOM_REMAP, t0 + i, p1, p2);
+      b.rpair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
+    } else {
+      uint32_t rows[4];
+      prf_rows(m, b.keys[i], rows);
+      *reinterpret_cast<uint4*>(b.rows + 4 * (uint64_t)i) =
+          make_uint4(rows[0], rows[1], rows[2], rows[3]);
+    }
+  }
+  if (wid == 0) {
+    const bool mine = (uint32_t)lane < n;
+    const uint64_t key = mine ? b.keys[lane] : 0;
+    const uint32_t op = mine ? b.ops[lane] : OP_GET;
+    uint32_t lead = lane, prevw = NONE32, lastw = NONE32;
+    for (uint32_t j = 0; j < n; j++) {
+      const uint64_t kj = __shfl_sync(0xffffffffu, key, j);
+      const uint32_t oj = __shfl_sync(0xffffffffu, op, j);
+      if (!mine || kj != key) continue;
+      if (j < (uint32_t)lane) {
+        lead = min(lead, j);
+        if (oj != OP_GET) prevw = j;
+      } else if (oj != OP_GET) {
+        lastw = j;
+      }
+    }
+    if (mine) {
+      b.leader[lane] = lead;
+      b.prevw[lane] = prevw;
+      if (lead == (uint32_t)lane) b.lastw[lane] = lastw;
+    }
+  }
+  __syncthreads();
+  // 2. position-map search and page reads (warp per op)
+  for (uint32_t i = wid; i < n; i += nwarps) lookup_op(m, b, i, lane);
+  __syncthreads();
+  // 3. the host-access trace (every read position in order, then each
+  //    distinct page once as a write); the previous batch's table is cleared
+  if (m.trace_on && wid == 0) {
+    const uint32_t np = 2 * n;
+    bool v0, f0, v1, f1;
+    uint32_t q0, q1, s0, s1;
+    pos_flags(b, lane, np, v0, f0, q0, s0);
+    pos_flags(b, lane + 32, np, v1, f1, q1, s1);
+    const uint32_t bv0 = __ballot_sync(0xffffffffu, v0), bv1 = __ballot_sync(0xffffffffu, v1);
+    const uint32_t bf0 = __ballot_sync(0xffffffffu, f0), bf1 = __ballot_sync(0xffffffffu, f1);
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t tv = __popc(bv0) + __popc(bv1), tf = __popc(bf0) + __popc(bf1);
+    unsigned long long tbase = 0;
+    if (lane == 0) {
+      tbase = *m.trace_len;
+      *m.trace_len = tbase + tv + tf;
+    }
+    tbase = __shfl_sync(0xffffffffu, tbase, 0);
+    auto put = [&](uint64_t at, uint32_t e) {
+      if (at < m.trace_cap) m.trace[at] = e;
+    };
+    if (v0) put(tbase + __popc(bv0 & below), q0);
+    if (v1) put(tbase + __popc(bv0) + __popc(bv1 & below), q1);
+    if (f0) put(tbase + tv + __popc(bf0 & below), q0 | 0x80000000u);
+    if (f1) put(tbase + tv + __popc(bf0) + __popc(bf1 & below), q1 | 0x80000000u);
+  }
+  clear_prev_table(b, threadIdx.x, blockDim.x);
+  // 4. find_remove (warp per op)
+  for (uint32_t i = wid; i < n; i += nwarps) find_op(m, b, i, lane);
+  __syncthreads();
+  // 5. Get/Put/Delete semantics (thread per op), then write-back with
+  //    eviction (warp per page, straight to the host as well)
+  if (threadIdx.x < n) exec_op(m, b, threadIdx.x);
+  const uint32_t nd = *b.dcount;
+  if (wid < evict_warps)
+    for (uint32_t e = wid; e < nd; e += evict_warps)
+      evict_one(m, b, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), true);
+  __syncthreads();
+  // 6. P2C remap in rounds of W_r op slots: decide on round-start counts,
+  //    then place (warp 0, one lane per op)
+  for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+    const uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
+    const uint32_t i = threadIdx.x;
+    const bool act = i >= lo && i < hi && b.leader[i] == i && b.fpres[i];
+    if (act) decide_op_l2(m, b, i);
+    __syncthreads();
+    if (wid == 0) remap_apply_op(m, b, lane, act);
+    __syncthreads();
+  }
+  if (b.h_out) {
+    // results and the error word back to the caller's pinned staging
+    const uint32_t words = (n * (m.vb + 1) + 15) / 16;
+    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x)
+      reinterpret_cast<uint4*>(b.h_out)[w] = reinterpret_cast<const uint4*>(b.vout)[w];
+    if (threadIdx.x == 0) *b.h_err = *(volatile uint32_t*)m.err;
+  }
+}
+
+cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
+                         cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  if (n > FUSED_MAX_OPS) return cudaErrorInvalidValue;
+  ProfSpan whole(P_ACCESS, st);
+  const uint32_t per_warp = m.page_bytes + 32 * 16;
+  uint32_t ew = (200u << 10) / per_warp;
+  ew = ew < 1 ? 1 : (ew > FUSED_THREADS / 32 ? FUSED_THREADS / 32 : ew);
+  const size_t smem = (size_t)ew * per_warp;
+  cudaError_t e = raise_smem_limit((const void*)k_fused, smem);
+  if (e != cudaSuccess) return e;
+  k_fused<<<1, FUSED_THREADS, smem, st>>>(m, b, n, t0, ew);
+  count_launch();
+  return cudaGetLastError();
+}
 
 // The batch's preparation depends only on its own inputs: the grouping keys
 // (key hash table), the DUMMY / REMAP pairs and position-map rows, the

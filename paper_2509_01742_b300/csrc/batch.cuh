@@ -81,6 +81,13 @@ struct BatchDev {
   const uint64_t* prev_rpair;
   const uint8_t* prev_pres;
   uint32_t prev_kt_mask, pad2;
+  // a host-pointer call of one small batch (fused launch only): the packed
+  // inputs keys | vin | ops in pinned host staging, copied by the kernel into
+  // the device inputs above (laid out the same way from `keys`); the packed
+  // results vout | status copied back to h_out, and the error word to h_err
+  const uint8_t* h_in;
+  uint8_t* h_out;
+  uint32_t* h_err;
 };
 
 cudaError_t sort_batch_keys(uint64_t* keys, uint32_t n_pow2, cudaStream_t st);
@@ -107,6 +114,14 @@ struct FlushCtx {
 
 cudaError_t launch_prep(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
                         cudaStream_t st);
+// A whole batch of n <= FUSED_MAX_OPS ops (preparation, main part and the
+// host write-back of its pages) in one single-CTA launch; op i has sequence
+// number t0 + i.  Same tables, buffers, results, pages and trace as
+// launch_prep + launch_main + the write-back.  No write-back of an earlier
+// batch may still be in flight when it starts.
+constexpr uint32_t FUSED_MAX_OPS = 32;
+cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
+                         cudaStream_t st);
 cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st,
                         const FlushCtx& fc);
 // The lookahead part of a batch (b.la_on = 1), after its preparation:

@@ -276,7 +276,9 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sh, ui
 }
 
 // --- warp-level ordering of up to 32 (key, source) items ------------------
-// ascending by key; lanes without an item carry key ~0 and sort last
+// ascending by key; lanes without an item carry src NONE32 (and key ~0) and
+// sort after every item, an item whose key is ~0 included: the order is on
+// (key, src == NONE32)
 __device__ __forceinline__ void warp_sort_by_key(uint64_t& key, uint32_t& src) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -287,7 +289,10 @@ __device__ __forceinline__ void warp_sort_by_key(uint64_t& key, uint32_t& src) {
       uint32_t os = __shfl_xor_sync(0xffffffffu, src, j);
       bool asc = (lane & k) == 0;
       bool lower = (lane & j) == 0;
-      bool take = lower == asc ? (ok < key) : (ok > key);
+      const bool mine_empty = src == NONE32, other_empty = os == NONE32;
+      const bool o_less = ok < key || (ok == key && !other_empty && mine_empty);
+      const bool o_greater = ok > key || (ok == key && other_empty && !mine_empty);
+      bool take = lower == asc ? o_less : o_greater;
       if (take) {
         key = ok;
         src = os;

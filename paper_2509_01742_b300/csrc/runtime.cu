@@ -502,8 +502,30 @@ cudaError_t main_batch(bolt* h, const BatchDev& b, uint32_t n, cudaStream_t st,
   return cudaSuccess;
 }
 
+// A batch of n <= FUSED_MAX_OPS ops as one launch in the current slot.  Its
+// pages reach the host from the kernel itself, so it first orders st after
+// every write-back still in flight (one could be of a page it rewrites) and
+// leaves none pending.
+cudaError_t fused_batch(bolt* h, const BatchDev& b, uint32_t n, uint64_t t0, cudaStream_t st) {
+  const int s = h->slot;
+  for (int k = 0; k < 2; k++)
+    if (h->flush_pending[k]) {
+      cudaError_t e = cudaStreamWaitEvent(st, h->ev_flushed[k], 0);
+      if (e != cudaSuccess) return e;
+      h->flush_pending[k] = false;
+    }
+  const BatchDev v = slot_view(h, b, n, s);
+  cudaError_t e = launch_fused(h->m, v, n, t0, st);
+  if (e != cudaSuccess) return e;
+  h->slot_ht_mask[s] = v.ht_mask;
+  h->prev_valid = true;
+  h->slot = s ^ 1;
+  return cudaSuccess;
+}
+
 // One access batch, preparation and main part, on stream st.
 cudaError_t access_batch(bolt* h, BatchDev b, uint32_t n, cudaStream_t st) {
+  if (h->fused && n <= FUSED_MAX_OPS) return fused_batch(h, b, n, h->t, st);
   const BatchDev v = slot_view(h, b, n, h->slot);
   cudaError_t e = launch_prep(h->m, v, n, h->t, st);
   if (e != cudaSuccess) return e;
@@ -539,6 +561,18 @@ cudaError_t access_batches(bolt* h, BatchDev b, uint64_t n, uint32_t w, cudaStre
       h->batches++;
     }
     return e;
+  }
+  if (h->fused && w <= FUSED_MAX_OPS) {
+    // small batches: one launch each, in order on st
+    for (uint64_t j = 0; j < nb; j++) {
+      uint32_t cnt = 0;
+      const BatchDev x = slice(j, cnt);
+      cudaError_t e = fused_batch(h, x, cnt, h->t, st);
+      if (e != cudaSuccess) return e;
+      h->t += cnt;
+      h->batches++;
+    }
+    return cudaSuccess;
   }
   // the inputs are ready once the caller's earlier work on st is done
   cudaError_t e = cudaEventRecord(h->ev_in, st);
@@ -799,12 +833,19 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   }
   void* p = nullptr;
   const uint64_t set_bytes = MAXB * (1 + 8 + 2 * (uint64_t)val_bytes + 1);
-  e = cudaHostAlloc(&p, 2 * set_bytes + 64, cudaHostAllocDefault);
+  e = cudaHostAlloc(&p, 2 * set_bytes + 64, cudaHostAllocMapped);
+  void* pd = nullptr;
+  if (e == cudaSuccess && cudaHostGetDevicePointer(&pd, p, 0) != cudaSuccess) {
+    cudaFreeHost(p);
+    e = cudaErrorMemoryAllocation;
+  }
   if (e != cudaSuccess) {
     destroy_streams(h);
     delete h;
     return BOLT_E_NOMEM;
   }
+  // the fused small-batch call reads and writes this staging from the device
+  h->io_dev_delta = static_cast<uint8_t*>(pd) - static_cast<uint8_t*>(p);
   // the same two parts as a device I/O set (MAXB is a multiple of 8)
   uint8_t* q = static_cast<uint8_t*>(p);
   for (int s = 0; s < 2; s++) {
@@ -867,6 +908,10 @@ int bolt_set_param(bolt_t* h, int which, double v) {
     case BOLT_PARAM_DEFER_FLUSH:
       if (!(v == 0.0 || v == 1.0 || v == 2.0)) return BOLT_E_ARG;
       h->defer_flush = (int)v;
+      return BOLT_OK;
+    case BOLT_PARAM_FUSED:
+      if (!(v == 0.0 || v == 1.0)) return BOLT_E_ARG;
+      h->fused = v != 0.0;
       return BOLT_OK;
     case BOLT_PARAM_SPIN_LIMIT:
       if (!(v >= 0.0 && v <= (double)(1u << 22))) return BOLT_E_ARG;
@@ -1049,6 +1094,40 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
     h->last_st = st;
   }
   const uint32_t w = h->batch_width;
+  if (h->fused && n <= FUSED_MAX_OPS && n <= w && n <= h->cap_batch) {
+    // one small batch: a single fused launch that reads its inputs from the
+    // pinned staging and writes its results and the error word back there,
+    // so the call is one launch and one stream wait (no copies)
+    const IoPacked hp = io_packed(h->h_io[0], n, vb);
+    const IoPacked dp = io_packed(h->d_io[0], n, vb);
+    if (h->kb == 4) {
+      const uint32_t* k32 = reinterpret_cast<const uint32_t*>(kin);
+      for (uint64_t i = 0; i < n; i++) hp.keys[i] = k32[i];
+    } else {
+      std::memcpy(hp.keys, kin, n * 8);
+    }
+    std::memcpy(hp.vin, vin, n * vb);
+    std::memcpy(hp.ops, ops, n);
+    BatchDev b = h->b;
+    b.ops = dp.ops;
+    b.keys = dp.keys;
+    b.vin = dp.vin;
+    b.vout = dp.vout;
+    b.status = dp.status;
+    b.h_in = reinterpret_cast<const uint8_t*>(hp.keys) + h->io_dev_delta;
+    b.h_out = hp.vout + h->io_dev_delta;
+    b.h_err = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->h_err) + h->io_dev_delta);
+    cudaError_t e = fused_batch(h, b, (uint32_t)n, h->t, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return BOLT_E_CUDA;
+    h->t += n;
+    h->batches++;
+    std::memcpy(vout, hp.vout, n * vb);
+    if (status_out) std::memcpy(status_out, hp.status, n);
+    const int rc = err_to_rc(*h->h_err);
+    if (rc) h->poisoned = true;
+    return rc;
+  }
   const uint64_t chunk = (uint64_t)(h->cap_batch / w) * w;
   const bool single = n <= chunk;
   // several chunks: host<->device copies run beside the batches on st --

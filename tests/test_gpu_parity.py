@@ -88,11 +88,14 @@ def test_access_parity_small_config():
     o.close(); g.close()
 
 
-@pytest.mark.parametrize("batch", [1, 7, 333])
-def test_access_parity_batch_widths(batch):
-    """Small batches (one op per batch is Alg. 1) on a 2^12 map, 24 B values."""
+@pytest.mark.parametrize("batch,fused", [(1, 1), (7, 1), (32, 1), (1, 0), (7, 0), (333, 1)])
+def test_access_parity_batch_widths(batch, fused):
+    """Small batches (one op per batch is Alg. 1) on a 2^12 map, 24 B values,
+    through bolt_access.  Batches of at most 32 ops run as one fused launch
+    (fused = 1) or through the multi-kernel chain (fused = 0)."""
     N = 1 << 12
     o, g = _pair(N, 24, batch=batch)
+    g.set_param(B.BOLT_PARAM_FUSED, fused)
     keys, vals = W.records(3500, 24, 7)
     assert o.init(keys, vals, 9) == 0 and g.init(keys, vals, 9) == 0
     _assert_state_equal(o, g, "after build")
@@ -100,6 +103,112 @@ def test_access_parity_batch_widths(batch):
         ops, k, vin = W.op_stream(3500, 700, 24, 40 + rep, get_frac=0.5, del_frac=0.1,
                                   absent_frac=0.2)
         _run_batch(o, g, ops, k, vin, f"rep {rep}")
+        _assert_state_equal(o, g, f"rep {rep}")
+    o.close(); g.close()
+
+
+@pytest.mark.parametrize("trace", [True, False])
+def test_fused_and_chain_batches_interleaved_match_oracle(trace):
+    """Calls whose batches run as single fused launches (widths 1, 5, 32)
+    between calls that run the multi-kernel chain (widths 33, 300), through
+    bolt_access_device_batches and bolt_access_device without a host sync in
+    between: a fused batch right after a chain batch whose host write-back is
+    still in flight, and a chain batch right after fused ones.  Keys repeat
+    (1500 keys on a 2^12 map), deletes, misses.  Everything equals the oracle
+    with the same batch partition."""
+    import torch
+    N, vb = 1 << 12, 16
+    o, g = _pair(N, vb, trace=trace)
+    keys, vals = W.records(1500, vb, 81)
+    assert o.init(keys, vals, 4) == 0 and g.init(keys, vals, 4) == 0
+    plan = [(64, 1), (300, 300), (40, 5), (330, 33), (96, 32), (1, 1), (600, 300), (7, 1)]
+    total = sum(n for n, _ in plan)
+    ops, k, vin = W.op_stream(1500, total, vb, 82, get_frac=0.4, del_frac=0.15,
+                              absent_frac=0.2)
+    t_ops = torch.from_numpy(ops).cuda()
+    t_k = torch.from_numpy(k.view(np.int64)).cuda()
+    t_vin = torch.from_numpy(vin).cuda()
+    t_out = torch.zeros((total, vb), dtype=torch.uint8, device="cuda")
+    t_st = torch.zeros(total, dtype=torch.uint8, device="cuda")
+    lo = 0
+    vo_all, so_all = [], []
+    for n, w in plan:
+        s = slice(lo, lo + n)
+        if n == w:
+            assert g.access_device(t_ops[s], t_k[s], t_vin[s], t_out[s], t_st[s]) == 0
+        else:
+            assert g.access_device_batches(t_ops[s], t_k[s], t_vin[s], t_out[s], t_st[s], w) == 0
+        for b in range(lo, lo + n, w):
+            e = min(lo + n, b + w)
+            rc, vo, so = o.access(ops[b:e], k[b:e], vin[b:e])
+            assert rc == 0
+            vo_all.append(vo)
+            so_all.append(so)
+        lo += n
+    assert g.sync() == 0
+    assert np.array_equal(np.concatenate(so_all), t_st.cpu().numpy())
+    assert np.array_equal(np.concatenate(vo_all), t_out.cpu().numpy())
+    _assert_state_equal(o, g, "fused and chain batches", trace=trace)
+    o.close(); g.close()
+
+
+@pytest.mark.parametrize("key_bytes,trace", [(8, True), (8, False), (4, False)])
+def test_small_host_calls_match_oracle(key_bytes, trace):
+    """bolt_access calls of 1..32 operations, each one batch: a single fused
+    launch reads the call's inputs from the pinned staging and writes its
+    results back there (no copies).  Interleaved with calls of 33..200 ops in
+    batches of 64 (the chain, copies through the staging).  Values, status
+    and state equal the oracle's with the same batch partition."""
+    N, vb = 1 << 13, 24
+    o = O.OracleMap(N, vb, batch=64, trace=trace)
+    g = B.BoltMap(N, vb, trace=trace, batch=64, key_bytes=key_bytes)
+    rng = np.random.default_rng(101)
+    if key_bytes == 4:
+        keys = rng.choice(2**32, size=6001, replace=False).astype(np.uint64)
+    else:
+        keys = W.key_of(np.arange(6001, dtype=np.uint64))
+    _, vals = W.records(6000, vb, 102)
+    assert o.init(keys[:6000], vals, 7) == 0
+    assert g.init(keys[:6000].astype(np.uint32) if key_bytes == 4 else keys[:6000], vals, 7) == 0
+    for call in range(300):
+        n = int(rng.integers(1, 33)) if call % 10 else int(rng.integers(33, 201))
+        idx = rng.integers(0, 6001, n)  # index 6000 is an absent key
+        ops = rng.integers(0, 3, n).astype(np.uint8)
+        vin = rng.integers(0, 256, (n, vb), dtype=np.uint8)
+        k = keys[idx]
+        rc_o, vo, so = o.access(ops, k, vin)
+        rc_g, vg, sg = g.access(ops, k.astype(np.uint32) if key_bytes == 4 else k, vin)
+        assert rc_o == rc_g == 0
+        assert np.array_equal(so, sg) and np.array_equal(vo, vg), f"call {call}"
+    _assert_state_equal(o, g, "small host calls", trace=trace)
+    o.close(); g.close()
+
+
+@pytest.mark.parametrize("batch", [1, 4096])
+def test_extreme_keys_match_oracle(batch):
+    """Keys at the ends of the key space -- 0, 1, 2^63, 2^64 - 2 and 2^64 - 1
+    (the value the page build's and the eviction's warp sort give an empty
+    lane) -- among random keys: the build places them, Gets return their
+    values, Puts and Deletes change them, in single-op fused launches and in a
+    4096-op chain batch; pages and state equal the oracle's."""
+    N, vb = 1 << 12, 8
+    o, g = _pair(N, vb, batch=batch)
+    keys, vals = W.records(3000, vb, 91)
+    special = np.array([0, 1, 1 << 63, (1 << 64) - 2, (1 << 64) - 1], dtype=np.uint64)
+    keys[[5, 700, 1400, 2100, 2999]] = special
+    assert o.init(keys, vals, 6) == 0 and g.init(keys, vals, 6) == 0
+    _assert_state_equal(o, g, "after build")
+    model = DictModel(keys, vals)
+    rng = np.random.default_rng(92)
+    for rep in range(3):
+        idx = rng.integers(0, 3000, 200)
+        kk = keys[idx]
+        kk[::4] = special[rng.integers(0, 5, len(kk[::4]))]
+        ops = rng.integers(0, 3, len(kk)).astype(np.uint8)
+        vin = rng.integers(0, 256, (len(kk), vb), dtype=np.uint8)
+        vg, sg = _run_batch(o, g, ops, kk, vin, f"rep {rep}")
+        ev, es = model.apply(ops, kk, vin, vb)
+        assert np.array_equal(vg, ev) and np.array_equal(sg, es)
         _assert_state_equal(o, g, f"rep {rep}")
     o.close(); g.close()
 
