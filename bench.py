@@ -177,14 +177,31 @@ def link_bandwidth(torch) -> dict:
     return out
 
 
-def cpu_baseline_sample(seconds_hint: float = 15.0) -> dict:
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    workload: a 2^21-record map of 32 B records, then accesses in batches of
-    4096 from the same op distribution."""
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline_sample(seconds_hint: float = 15.0, multicore: bool = False) -> dict:
+    """The oracle as it stands on a bounded sample of the workload: a
+    2^21-record map of 32 B records, then accesses in batches of 4096 from
+    the same op distribution.  Single-threaded (the oracle proper), or its
+    OpenMP build on every host core (multicore: the same source, its
+    independent loops -- PRF draws, per-round decisions, page decryption and
+    encryption -- spread over the cores; byte-identical results)."""
     from oracle import oracle as O
     n_s = 1 << 21
     keys, vals = make_records(n_s, SEED_DATA)
-    m = O.OracleMap(n_s, VAL_BYTES, trace=False)
+    cores = 1
+    if multicore:
+        cores = O.threads(os.cpu_count() or 1)
+    m = O.OracleMap(n_s, VAL_BYTES, trace=False, omp=multicore)
     t0 = time.perf_counter()
     rc = m.init(keys, vals, SEED_MAP)
     t_build = time.perf_counter() - t0
@@ -199,11 +216,13 @@ def cpu_baseline_sample(seconds_hint: float = 15.0) -> dict:
         done += BATCH
         rep += 1
     m.close()
-    return {"value": round(done / t_acc, 1), "unit": "accesses/s", "cores": 1, "kind": "oracle",
+    return {"value": round(done / t_acc, 1), "unit": "accesses/s", "cores": cores,
+            "kind": "oracle (OpenMP build, all host cores)" if multicore else "oracle",
+            "cpu": cpu_model(),
             "build_mrec_s": round(n_s / t_build / 1e6, 3),
             "sample": f"oracle map of 2^21 x 32 B records (build {t_build:.1f} s), then {done} "
                       f"uniform 50/50 GET/PUT accesses in batches of {BATCH} ({t_acc:.1f} s); "
-                      "single host thread"}
+                      + (f"{cores} host threads" if multicore else "single host thread")}
 
 
 def run_reference(args) -> None:
@@ -501,6 +520,7 @@ def run_bolt(args) -> None:
             dist.destroy_process_group()
         return
     cpu = cpu_baseline_sample() if world == 1 and not args.no_cpu else None
+    cpu_mt = cpu_baseline_sample(8.0, multicore=True) if world == 1 and not args.no_cpu else None
     serving = None
     if world == 1 and not args.no_serve:
         serving = serve_measure(16, 2000, 24.0, (0.5,))
@@ -535,6 +555,7 @@ def run_bolt(args) -> None:
         "clocks": clk.summary(),
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "cpu_baseline_multicore": cpu_mt,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
@@ -855,6 +876,84 @@ def run_big(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_validate(args) -> None:
+    """The paper's dimensional validation (Sec. 3.3 "Dimensions in
+    practice", the table inside Fig. 5) on the device: N = 2^20 records, for
+    c in {8, 16} and alpha in {0.01, 0.2, 0.5}, `--accesses` uniform random
+    accesses (Get on present keys; every access remaps its key) in batches of
+    `--width`; the peak bin load, peak HBM-store occupancy and peak stash
+    occupancy since the build (device counters, bolt_get_stats) beside the
+    analytical bounds and the paper's empirical maxima (bound - printed
+    slack).  The paper accesses one key at a time: at the end of a batch of W
+    the stash also holds that batch's own remapped keys (about W (1 - alpha)
+    of them) that no page read has had a chance to evict yet."""
+    import torch
+    from paper_2509_01742_b300 import bolt as B
+
+    torch.cuda.set_device(0)
+    N, vb, W_ = 1 << 20, 8, args.width
+    slack = {}
+    with open(os.path.join(ROOT, "tests", "golden", "slack_table.txt")) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                metric, c, a, abs_s, _ = ln.split()
+                slack[(metric, int(c), float(a))] = int(abs_s)
+    keys = W.key_of(np.arange(N, dtype=np.uint64))
+    vals = np.zeros((N, vb), dtype=np.uint8)
+    d_keys = torch.from_numpy(keys.view(np.int64)).cuda()
+    d_vals = torch.from_numpy(vals).cuda()
+    chunk = 1 << 22
+    d_ops = torch.zeros(chunk, dtype=torch.uint8, device="cuda")
+    d_vin = torch.zeros((chunk, vb), dtype=torch.uint8, device="cuda")
+    d_out = torch.empty((chunk, vb), dtype=torch.uint8, device="cuda")
+    d_st = torch.empty(chunk, dtype=torch.uint8, device="cuda")
+    gen = torch.Generator(device="cuda")
+    stream = torch.cuda.Stream()
+    rows = []
+    total = int(args.accesses)
+    for c in (8, 16):
+        for alpha in (0.01, 0.2, 0.5):
+            m = B.BoltMap(N, vb, alpha=alpha, c=c)
+            info = m.info()
+            assert m.init_device(d_keys, d_vals, 0x5EED0007, stream=stream) == 0
+            gen.manual_seed(int(c * 1000 + alpha * 100))
+            t0 = time.perf_counter()
+            done = 0
+            while done < total:
+                n = min(chunk, total - done)
+                n -= n % W_ if n > W_ else 0
+                with torch.cuda.stream(stream):
+                    idx = torch.randint(0, N, (n,), device="cuda", generator=gen)
+                    d_k = W.key_of_torch(idx)
+                assert m.access_device_batches(d_ops[:n], d_k, d_vin[:n], d_out[:n], d_st[:n],
+                                               W_, stream=stream) == 0
+                done += n
+            assert m.sync() == 0
+            secs = time.perf_counter() - t0
+            st = m.stats()
+            assert bool(d_st[:n].all()), "every accessed key is present"
+            emp = {k: (b - slack[(k, c, alpha)]) for k, b in
+                   (("binload", info["lmax"]), ("hbm", info["beta1"]), ("stash", info["beta2"]))}
+            rows.append({"c": c, "alpha": alpha, "accesses": done, "seconds": round(secs, 1),
+                         "peak_load": st["peak_load"], "lmax": info["lmax"],
+                         "paper_peak_load": emp["binload"],
+                         "peak_hbm": st["peak_hbm"], "beta1": round(info["beta1"], 1),
+                         "paper_peak_hbm": round(emp["hbm"], 1),
+                         "peak_hbm_vs_paper": round(st["peak_hbm"] / emp["hbm"] - 1, 4),
+                         "peak_stash": st["peak_stash"], "beta2": round(info["beta2"], 1),
+                         "paper_peak_stash": round(emp["stash"], 1),
+                         "peak_stash_vs_paper": round(st["peak_stash"] / emp["stash"] - 1, 4),
+                         "batch_remap_term": round(W_ * (1 - alpha), 1)})
+            print(json.dumps(rows[-1]), flush=True)
+            m.close()
+    line = {"metric": "dimensional validation: peak bin load, HBM store and stash (N=2^20)",
+            "unit": "items", "n_gpus": 1, "data": "synthetic (uniform random accesses)",
+            "config": {"workload": f"N=2^20 records, {total} uniform accesses per setting in "
+                                   f"batches of {W_}, c in {{8,16}}, alpha in {{0.01,0.2,0.5}}"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def make_records_vb(n: int, vb: int, seed: int):
     keys = np.empty(n, dtype=np.uint64)
     for lo in range(0, n, 1 << 24):
@@ -923,7 +1022,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("bolt", "reference"), default="bolt")
-    ap.add_argument("--config", choices=("headline", "zipf", "w1", "serve", "big", "paper"),
+    ap.add_argument("--config", choices=("headline", "zipf", "w1", "serve", "big", "paper",
+                                         "validate"),
                     default="headline",
                     help="headline: the JSON line above; zipf: batch-width sweep on the "
                          "skewed 2^24 x 64 B map; w1: one access per call vs batches of 4096; "
@@ -931,6 +1031,8 @@ def main():
                          "2^30 x 64 B map under a 16 GB budget; paper: the paper's 10^6 x "
                          "(4 B key, 8 B value) workload, one op per call")
     ap.add_argument("--big-log-n", type=int, default=30)
+    ap.add_argument("--width", type=int, default=4096,
+                    help="batch width of --config validate")
     ap.add_argument("--maps", type=int, default=64)
     ap.add_argument("--requests", type=int, default=6000)
     ap.add_argument("--log-n", type=int, default=LOG_N)
@@ -953,6 +1055,8 @@ def main():
         run_big(args)
     elif args.config == "paper":
         run_paper_workload(args)
+    elif args.config == "validate":
+        run_validate(args)
     elif args.config != "headline":
         run_sweep(args)
     else:

@@ -19,6 +19,9 @@
  *   - a page holds its real tuples in ascending key order in the first slots,
  *     a bitmap of occupied slots in its 16-byte header and zero dummies.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "bolt_oracle.h"
 
 #include <math.h>
@@ -501,11 +504,13 @@ int oracle_init(omap_t* m, const uint64_t* keys, const uint8_t* vals, uint64_t n
   int rc = ORC_OK;
   if (!b1 || !b2 || !dest || !prow) { rc = ORC_E_NOMEM; goto out; }
 
+#pragma omp parallel for schedule(static)
   for (uint64_t i = 0; i < n; i++) oracle_pair(m->kprf, DOM_INIT, i, p->B, &b1[i], &b2[i]);
 
   /* P2C and d-choice in rounds of W_r records against round-start loads */
   for (uint64_t lo = 0; lo < n; lo += p->round_width) {
     uint64_t hi = lo + p->round_width < n ? lo + p->round_width : n;
+#pragma omp parallel for schedule(static) if (hi - lo >= 512)
     for (uint64_t i = lo; i < hi; i++) {
       dest[i] = m->load[b1[i]] <= m->load[b2[i]] ? b1[i] : b2[i];
       uint64_t rows[4];
@@ -560,6 +565,7 @@ int oracle_init(omap_t* m, const uint64_t* keys, const uint8_t* vals, uint64_t n
         all[start[q] + fill[q]].val = vals + i * p->val_bytes;
         fill[q]++;
       }
+#pragma omp parallel for schedule(static)
     for (uint64_t q = 0; q < p->M; q++)
       page_store(m, q, all + start[q], (uint32_t)(start[q + 1] - start[q]), 0);
     free(start); free(all); free(fill);
@@ -656,6 +662,7 @@ static int access_batch(omap_t* m, const uint8_t* ops, const uint64_t* keys,
   /* 2. key search (KS): leaders look up the position map; a hit yields the
    *    stored pair, every other operation (miss, duplicate) a fresh random
    *    pair (Alg. 1 line 3, Sec. 4.1 step 3). */
+#pragma omp parallel for schedule(static) if (n >= 64)
   for (uint64_t i = 0; i < n; i++) {
     hit[i] = NO_INDEX;
     if (leader[i] == i) hit[i] = pm_find(m, keys[i]);
@@ -669,7 +676,7 @@ static int access_batch(omap_t* m, const uint8_t* ops, const uint64_t* keys,
 
   /* 3. value access (VAC): read every host bin of every pair, in operation
    *    order, first bin then second (Alg. 1 lines 5-8); decrypt each distinct
-   *    page once. */
+   *    page once (the decryptions are independent of one another). */
   for (uint64_t i = 0; i < n; i++) {
     uint32_t pair[2] = {p1[i], p2[i]};
     for (int j = 0; j < 2; j++) {
@@ -682,14 +689,17 @@ static int access_batch(omap_t* m, const uint8_t* ops, const uint64_t* keys,
       dp[nd].plain = malloc(p->page_bytes);
       if (!dp[nd].plain) { rc = ORC_E_NOMEM; goto out; }
       memcpy(dp[nd].plain, m->pages + q * p->page_bytes, p->page_bytes);
-      page_crypt(m, q, m->version[q], dp[nd].plain);
-      uint64_t bitmap;
-      memcpy(&bitmap, dp[nd].plain, 8);
-      uint32_t cnt = 0;
-      while (cnt < 64 && (bitmap >> cnt) & 1) cnt++;
-      dp[nd].cnt = cnt;
       nd++;
     }
+  }
+#pragma omp parallel for schedule(static) if (nd >= 64)
+  for (uint64_t d = 0; d < nd; d++) {
+    page_crypt(m, dp[d].q, m->version[dp[d].q], dp[d].plain);
+    uint64_t bitmap;
+    memcpy(&bitmap, dp[d].plain, 8);
+    uint32_t cnt = 0;
+    while (cnt < 64 && (bitmap >> cnt) & 1) cnt++;
+    dp[d].cnt = cnt;
   }
 
   /* 4. find_remove (Alg. 1 lines 6 and 9): take each hit key out of the HBM
@@ -754,31 +764,47 @@ static int access_batch(omap_t* m, const uint8_t* ops, const uint64_t* keys,
 
   /* 7. write-back with eviction (Alg. 1 line 10): every distinct page read,
    *    in first-read order, gets its remaining tuples plus every stash item
-   *    bound for it, under a fresh version. */
+   *    bound for it, under a fresh version.  A page's new content depends on
+   *    its own tuples and stash items only, so the pages are built and
+   *    encrypted independently; the bookkeeping that follows (stash items
+   *    leave, slots return to the free ring, trace) runs in page order. */
+  int wb_rc = ORC_OK;
+#pragma omp parallel for schedule(static) if (nd >= 64)
   for (uint64_t d = 0; d < nd; d++) {
     dpage_t* pg = &dp[d];
     uint64_t q = pg->q;
     tuple_t* t = malloc((pg->cnt + p->lmax + 1) * sizeof *t);
     uint32_t cnt = 0;
-    if (!t) { rc = ORC_E_NOMEM; goto out; }
-    for (uint32_t k = 0; k < pg->cnt; k++) {
+    const int nomem = !t;
+    int bad = nomem;
+    for (uint32_t k = 0; !bad && k < pg->cnt; k++) {
       if ((pg->removed >> k) & 1) continue;
       uint8_t* slot = pg->plain + 16 + (uint64_t)k * p->rec_bytes;
       memcpy(&t[cnt].key, slot, 8);
       t[cnt].val = slot + 8;
       cnt++;
     }
-    for (uint32_t r = 0; r < m->revcnt[q]; r++) {
+    for (uint32_t r = 0; !bad && r < m->revcnt[q]; r++) {
       uint64_t vs = m->rev[q * p->lmax + r];
       if (!m->vs_live[vs]) continue; /* taken out by find_remove above */
-      if (cnt >= p->lmax) { free(t); rc = ORC_E_INTERNAL; goto out; }
+      if (cnt >= p->lmax) { bad = 1; break; }
       t[cnt].key = m->vs_key[vs];
       t[cnt].val = m->vs_val + vs * vb;
       cnt++;
     }
-    m->version[q]++;
-    page_store(m, q, t, cnt, m->version[q]);
+    if (!bad) {
+      m->version[q]++;
+      page_store(m, q, t, cnt, m->version[q]);
+    }
     free(t);
+    if (bad) {
+#pragma omp critical
+      wb_rc = nomem ? ORC_E_NOMEM : ORC_E_INTERNAL;
+    }
+  }
+  if (wb_rc) { rc = wb_rc; goto out; }
+  for (uint64_t d = 0; d < nd; d++) {
+    uint64_t q = dp[d].q;
     for (uint32_t r = 0; r < m->revcnt[q]; r++) {
       uint64_t vs = m->rev[q * p->lmax + r];
       if (!m->vs_live[vs]) continue;
@@ -811,6 +837,7 @@ static int access_batch(omap_t* m, const uint8_t* ops, const uint64_t* keys,
       goto out;
     }
     /* decide */
+#pragma omp parallel for schedule(static) if (hi - lo >= 64)
     for (uint64_t i = lo; i < hi; i++) {
       uint64_t k = i - lo;
       if (leader[i] != i) continue;
@@ -903,6 +930,20 @@ int oracle_access(omap_t* m, const uint8_t* ops, const uint64_t* keys,
 }
 
 /* ------------------------------------------------------------------------ */
+
+/* Host threads the loops above may use: the library built with OpenMP runs
+ * its independent loops (PRF draws, per-round decisions, page decryption and
+ * encryption) on up to `n` threads; built without it, it is single-threaded
+ * and this returns 1.  Results do not depend on the thread count. */
+int oracle_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 int oracle_info(const omap_t* m, oracle_info_t* out) {
   if (!m || !out) return ORC_E_ARG;

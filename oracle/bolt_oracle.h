@@ -82,6 +82,8 @@ int oracle_access(omap_t*, const uint8_t* ops, const uint64_t* keys,
 void oracle_destroy(omap_t*);
 
 int oracle_info(const omap_t*, oracle_info_t* out);
+/* threads of the OpenMP build (n > 0 sets them); 1 for the plain build */
+int oracle_threads(int n);
 int oracle_stats(const omap_t*, oracle_stats_t* out);
 /* host-resident encrypted pages, M * page_bytes bytes (read only) */
 const uint8_t* oracle_pages(const omap_t*);

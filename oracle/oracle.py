@@ -15,6 +15,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liboracle.so")
+OMP_LIB_PATH = os.path.join(HERE, "liboracle_omp.so")
 SRC_PATH = os.path.join(HERE, "bolt_oracle.c")
 
 PARAM_ALPHA, PARAM_C, PARAM_NOCRYPT, PARAM_TRACE, PARAM_BATCH = 1, 2, 3, 4, 5
@@ -23,11 +24,16 @@ GET, PUT, DEL = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/liboracle.so with the system C compiler."""
-    if force or not os.path.exists(LIB_PATH) or (
-            os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC_PATH)):
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC",
-                               "-o", LIB_PATH, SRC_PATH, "-lm"])
+    """Compile the oracle with the system C compiler: oracle/liboracle.so
+    (single-threaded, the oracle proper) and oracle/liboracle_omp.so (the
+    same source with OpenMP on: its independent loops run on all host cores,
+    the multi-core CPU baseline)."""
+    hdr = os.path.join(HERE, "bolt_oracle.h")
+    for path, extra in ((LIB_PATH, ["-Wno-unknown-pragmas"]), (OMP_LIB_PATH, ["-fopenmp"])):
+        if force or not os.path.exists(path) or os.path.getmtime(path) < max(
+                os.path.getmtime(SRC_PATH), os.path.getmtime(hdr)):
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-Wall", *extra, "-shared", "-fPIC",
+                                   "-o", path, SRC_PATH, "-lm"])
     return LIB_PATH
 
 
@@ -57,13 +63,29 @@ class Stats(ctypes.Structure):
 
 
 _lib = None
+_omp_lib = None
+
+
+def omp_lib():
+    """The OpenMP build (multi-core CPU baseline): same entry points."""
+    global _omp_lib
+    if _omp_lib is None:
+        lib()
+        _omp_lib = _bind_all(ctypes.CDLL(OMP_LIB_PATH))
+    return _omp_lib
 
 
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(LIB_PATH)
+        _lib = _bind_all(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def _bind_all(L):
+    """ctypes signatures of the oracle's entry points."""
+    if L is not None:
         P, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
         L.oracle_create.argtypes = [u64, u32, u32, u64, ctypes.POINTER(P)]
         L.oracle_set_param.argtypes = [P, i32, ctypes.c_double]
@@ -96,8 +118,8 @@ def lib():
         L.oracle_kdf.restype = None
         L.oracle_page_decrypt.argtypes = [P, u64, u64, P, P, u64]
         L.oracle_page_decrypt.restype = None
-        _lib = L
-    return _lib
+        L.oracle_threads.argtypes = [i32]
+    return L
 
 
 def _ptr(a: np.ndarray):
@@ -154,6 +176,11 @@ def pair(kprf_words, dom: int, x: int, B: int):
     return a.value, b.value
 
 
+def threads(n: int = 0) -> int:
+    """Threads the OpenMP build uses (n > 0 sets them)."""
+    return omp_lib().oracle_threads(n)
+
+
 class OracleError(RuntimeError):
     def __init__(self, rc, what):
         super().__init__(f"{what} failed rc={rc}")
@@ -164,9 +191,12 @@ class OracleMap:
     """One oracle map instance (same call shapes as the product C ABI)."""
 
     def __init__(self, N, val_bytes, hbm_budget=2**64 - 1, key_bytes=8, alpha=None,
-                 c=None, nocrypt=False, trace=True, batch=None):
+                 c=None, nocrypt=False, trace=True, batch=None, omp=False):
+        """omp=True runs the same oracle from its OpenMP build (independent
+        loops on all host cores; results identical to the plain build)."""
+        self._L = omp_lib() if omp else lib()
         self._h = ctypes.c_void_p()
-        rc = lib().oracle_create(N, key_bytes, val_bytes, hbm_budget, ctypes.byref(self._h))
+        rc = self._L.oracle_create(N, key_bytes, val_bytes, hbm_budget, ctypes.byref(self._h))
         if rc:
             raise OracleError(rc, "oracle_create")
         if c is not None:
@@ -182,13 +212,13 @@ class OracleMap:
         self.vb = val_bytes
 
     def set_param(self, which, v):
-        rc = lib().oracle_set_param(self._h, which, float(v))
+        rc = self._L.oracle_set_param(self._h, which, float(v))
         if rc:
             raise OracleError(rc, "oracle_set_param")
 
     def close(self):
         if self._h:
-            lib().oracle_destroy(self._h)
+            self._L.oracle_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):
@@ -200,7 +230,7 @@ class OracleMap:
     def init(self, keys: np.ndarray, vals: np.ndarray, seed: int) -> int:
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
         vals = np.ascontiguousarray(vals, dtype=np.uint8)
-        return lib().oracle_init(self._h, _ptr(keys), _ptr(vals), len(keys), seed)
+        return self._L.oracle_init(self._h, _ptr(keys), _ptr(vals), len(keys), seed)
 
     def access(self, ops, keys, vals_in):
         ops = np.ascontiguousarray(ops, dtype=np.uint8)
@@ -209,53 +239,53 @@ class OracleMap:
         n = len(ops)
         vout = np.zeros((n, self.vb), dtype=np.uint8)
         status = np.zeros(n, dtype=np.uint8)
-        rc = lib().oracle_access(self._h, _ptr(ops), _ptr(keys), _ptr(vin), _ptr(vout),
+        rc = self._L.oracle_access(self._h, _ptr(ops), _ptr(keys), _ptr(vin), _ptr(vout),
                                  _ptr(status), n)
         return rc, vout, status
 
     def info(self) -> dict:
         o = Info()
-        lib().oracle_info(self._h, ctypes.byref(o))
+        self._L.oracle_info(self._h, ctypes.byref(o))
         return o.as_dict()
 
     def stats(self) -> dict:
         s = Stats()
-        lib().oracle_stats(self._h, ctypes.byref(s))
+        self._L.oracle_stats(self._h, ctypes.byref(s))
         return s.as_dict()
 
     def pages(self) -> np.ndarray:
         i = self.info()
         size = i["M"] * i["page_bytes"]
-        addr = lib().oracle_pages(self._h)
+        addr = self._L.oracle_pages(self._h)
         buf = (ctypes.c_uint8 * size).from_address(addr)
         return np.frombuffer(buf, dtype=np.uint8).copy().reshape(i["M"], i["page_bytes"])
 
     def loads(self) -> np.ndarray:
         out = np.zeros(self.info()["B"], dtype=np.uint8)
-        lib().oracle_loads(self._h, _ptr(out))
+        self._L.oracle_loads(self._h, _ptr(out))
         return out
 
     def versions(self) -> np.ndarray:
         out = np.zeros(self.info()["M"], dtype=np.uint64)
-        lib().oracle_versions(self._h, _ptr(out))
+        self._L.oracle_versions(self._h, _ptr(out))
         return out
 
     def rowcounts(self) -> np.ndarray:
         out = np.zeros(self.info()["rows"], dtype=np.uint32)
-        lib().oracle_rowcounts(self._h, _ptr(out))
+        self._L.oracle_rowcounts(self._h, _ptr(out))
         return out
 
     def trace(self, clear=True) -> np.ndarray:
-        n = lib().oracle_trace_len(self._h)
+        n = self._L.oracle_trace_len(self._h)
         out = np.zeros(n, dtype=np.uint32)
-        lib().oracle_trace_copy(self._h, _ptr(out), n)
+        self._L.oracle_trace_copy(self._h, _ptr(out), n)
         if clear:
-            lib().oracle_trace_clear(self._h)
+            self._L.oracle_trace_clear(self._h)
         return out
 
     def decrypt_page(self, q) -> np.ndarray:
         out = np.zeros(self.info()["page_bytes"], dtype=np.uint8)
-        rc = lib().oracle_decrypt_page(self._h, q, _ptr(out))
+        rc = self._L.oracle_decrypt_page(self._h, q, _ptr(out))
         if rc:
             raise OracleError(rc, "oracle_decrypt_page")
         return out
@@ -263,7 +293,7 @@ class OracleMap:
     def keys(self):
         a = np.zeros(8, dtype=np.uint32)
         b = np.zeros(8, dtype=np.uint32)
-        rc = lib().oracle_keys(self._h, _ptr(a), _ptr(b))
+        rc = self._L.oracle_keys(self._h, _ptr(a), _ptr(b))
         if rc:
             raise OracleError(rc, "oracle_keys")
         return a, b

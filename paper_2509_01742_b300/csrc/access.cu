@@ -217,20 +217,37 @@ __device__ __forceinline__ uint32_t ht_insert(const BatchDev& b, uint32_t page, 
   return NONE32;
 }
 
-// the warp scans the key's d = 4 rows, R slots each (ballot per row)
+// The warp scans the key's d = 4 rows, R slots each (a ballot per row; the
+// first row with a match, then its first matching slot).  Every slot's
+// metadata, key and bin pair of all four rows are loaded at once -- one
+// memory round trip instead of two per row -- and *bins receives the pair
+// of the matching slot (all lanes).
 __device__ __forceinline__ uint32_t pm_search(const MapDev& m, const BatchDev& b, uint32_t i,
-                                              uint64_t key, int lane) {
-  uint32_t found = NONE32;
+                                              uint64_t key, int lane, uint64_t* bins) {
   const uint4 rows = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
   const uint32_t rr[4] = {rows.x, rows.y, rows.z, rows.w};
+  const bool in = lane < (int)m.R;
+  uint32_t meta[4];
+  uint64_t k[4], pb[4];
 #pragma unroll
   for (int j = 0; j < 4; j++) {
-    bool match = false;
     const uint64_t idx = (uint64_t)rr[j] * m.R + lane;
-    if (lane < (int)m.R) match = meta_loc(m.pm_meta[idx]) != LOC_EMPTY && m.pm_key[idx] == key;
-    const uint32_t bal = __ballot_sync(0xffffffffu, match);
-    if (bal && found == NONE32) found = (uint32_t)((uint64_t)rr[j] * m.R + (__ffs(bal) - 1));
+    meta[j] = in ? m.pm_meta[idx] : 0u;
+    k[j] = in ? m.pm_key[idx] : 0ull;
+    pb[j] = in ? m.pm_bins[idx] : 0ull;
   }
+  uint32_t found = NONE32;
+  uint64_t fb = 0;
+#pragma unroll
+  for (int j = 3; j >= 0; j--) {  // the lowest matching row wins
+    const uint32_t bal = __ballot_sync(0xffffffffu, meta_loc(meta[j]) != LOC_EMPTY && k[j] == key);
+    if (bal) {
+      const int s = __ffs(bal) - 1;
+      found = (uint32_t)((uint64_t)rr[j] * m.R + s);
+      fb = __shfl_sync(0xffffffffu, pb[j], s);
+    }
+  }
+  *bins = fb;
   return found;
 }
 
@@ -306,8 +323,9 @@ __global__ void k_ahead_lookup(MapDev m, BatchDev b, uint32_t n) {
     const uint64_t key = b.keys[i];
     const uint32_t o = prev_owner(b, key);
     if (o == NONE32) {
-      const uint32_t found = pm_search(m, b, i, key, lane);
-      if (found != NONE32) pr = m.pm_bins[found];
+      uint64_t fb;
+      const uint32_t found = pm_search(m, b, i, key, lane, &fb);
+      if (found != NONE32) pr = fb;
       if (lane == 0) {
         b.hit[i] = found;
         b.done[i] = 1;
@@ -564,6 +582,7 @@ __device__ __forceinline__ void page_in(const MapDev& m, const BatchDev& b, uint
 __device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, uint32_t i,
                                           int lane) {
   uint32_t found = NONE32;
+  uint64_t fb = 0;
   if (b.leader[i] == i) {
     const uint64_t key = b.keys[i];
     bool scan = true;
@@ -573,19 +592,20 @@ __device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, ui
         scan = false;
       } else if (meta_loc(m.pm_meta[hs]) != LOC_EMPTY && m.pm_key[hs] == key) {
         found = hs;
+        fb = m.pm_bins[hs];
         scan = false;
       }
     }
-    if (scan) found = pm_search(m, b, i, key, lane);
+    if (scan) found = pm_search(m, b, i, key, lane, &fb);
   }
+  // a hit reads its stored pair, everything else the DUMMY pair
+  const uint64_t pr = found != NONE32 ? fb : b.pair[i];
   if (lane == 0) {
     b.hit[i] = found;
-    if (found != NONE32) b.pair[i] = m.pm_bins[found];
+    if (found != NONE32) b.pair[i] = pr;
   }
-  __syncwarp();
   uint32_t q = NONE32, claim = NONE32;
   if (lane < 2) {
-    const uint64_t pr = b.pair[i];
     const uint32_t p = lane == 0 ? (uint32_t)pr : (uint32_t)(pr >> 32);
     const uint32_t pos = 2 * i + lane;
     if (p >= m.K) {
@@ -832,12 +852,17 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
   // remaining page tuples (source tag: slot index) and live stash items bound
   // for this page (source tag: 1 << 31 | value-store slot)
   const bool pv = lane < (int)m.lmax && ((bitmap >> lane) & 1) && !((removed >> lane) & 1);
+  // the reverse-index list is read with its count (entries past the count
+  // are not used), then each listed item's live flag and key together
+  const uint32_t rev_e = lane < (int)m.lmax ? m.rev[q * m.lmax + lane] : NONE32;
   const uint32_t rc = byte_get(m.revcnt, q);
-  uint32_t vs = NONE32;
+  const bool listed = lane < (int)rc && lane < (int)m.lmax;
+  const uint32_t vs = listed ? rev_e : NONE32;
+  uint64_t skey = 0;
   bool sv = false;
-  if (lane < (int)rc && lane < (int)m.lmax) {
-    vs = m.rev[q * m.lmax + lane];
+  if (listed) {
     sv = m.vs_live[vs] != 0;
+    skey = m.vs_key[vs];
   }
   const uint32_t pmask = __ballot_sync(0xffffffffu, pv);
   const uint32_t smask = __ballot_sync(0xffffffffu, sv);
@@ -850,7 +875,7 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
   if (pv)
     items[__popc(pmask & below)] =
         make_ulonglong2(*reinterpret_cast<const uint64_t*>(old + 16 + (size_t)lane * m.rec), lane);
-  if (sv) items[np + __popc(smask & below)] = make_ulonglong2(m.vs_key[vs], (1ull << 31) | vs);
+  if (sv) items[np + __popc(smask & below)] = make_ulonglong2(skey, (1ull << 31) | vs);
   __syncwarp();
   uint64_t key = ~0ull;
   uint32_t src = NONE32;
@@ -1234,7 +1259,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   const int lane = threadIdx.x & 31;
   const uint32_t wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   // 1. per op the DUMMY pair, the REMAP pair and the position-map rows (one
-  //    ChaCha20 block each); warp 0 groups the ops by key with n^2 compares:
+  //    ChaCha20 block each); warp 3 groups the ops by key with n^2 compares:
   //    leader = first op on the key, previous writer of each op, last writer
   //    of each key group
   if (threadIdx.x == 0) *b.dcount = 0;
@@ -1246,13 +1271,15 @@ __global__ void __launch_bounds__(FUSED_THREADS)
       reinterpret_cast<uint4*>(b.keys)[w] = reinterpret_cast<const uint4*>(b.h_in)[w];
     __syncthreads();
   }
-  for (uint32_t tid = threadIdx.x; tid < 3 * n; tid += blockDim.x) {
-    const uint32_t i = tid / 3, kind = tid % 3;
+  // (each kind of block in a warp of its own, lane = op, so the three run
+  // side by side instead of as divergent paths of one warp)
+  if (wid < 3 && (uint32_t)lane < n) {
+    const uint32_t i = lane;
     uint32_t p1, p2;
-    if (kind == 0) {
+    if (wid == 0) {
       prf_pair(m, DOM_DUMMY, t0 + i, p1, p2);
       b.pair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
-    } else if (kind == 1) {
+    } else if (wid == 1) {
       prf_pair(m, DOM_REMAP, t0 + i, p1, p2);
       b.rpair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
     } else {
@@ -1262,7 +1289,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
           make_uint4(rows[0], rows[1], rows[2], rows[3]);
     }
   }
-  if (wid == 0) {
+  if (wid == 3) {
     const bool mine = (uint32_t)lane < n;
     const uint64_t key = mine ? b.keys[lane] : 0;
     const uint32_t op = mine ? b.ops[lane] : OP_GET;
@@ -1318,25 +1345,31 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   // 4. find_remove (warp per op)
   for (uint32_t i = wid; i < n; i += nwarps) find_op(m, b, i, lane);
   __syncthreads();
-  // 5. Get/Put/Delete semantics (thread per op), then write-back with
-  //    eviction (warp per page, straight to the host as well)
-  if (threadIdx.x < n) exec_op(m, b, threadIdx.x);
-  const uint32_t nd = *b.dcount;
-  if (wid < evict_warps)
+  // 5. Get/Put/Delete semantics (the last warp, lane per op) beside the
+  //    write-back with eviction (the other warps, warp per page, straight to
+  //    the host as well)
+  if (wid == nwarps - 1) {
+    if ((uint32_t)lane < n) exec_op(m, b, lane);
+  } else if (wid < evict_warps) {
+    const uint32_t nd = *b.dcount;
     for (uint32_t e = wid; e < nd; e += evict_warps)
       evict_one(m, b, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), true);
-  __syncthreads();
-  // 6. P2C remap in rounds of W_r op slots: decide on round-start counts,
-  //    then place (warp 0, one lane per op)
-  for (uint64_t lo = 0; lo < n; lo += m.Wr) {
-    const uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
-    const uint32_t i = threadIdx.x;
-    const bool act = i >= lo && i < hi && b.leader[i] == i && b.fpres[i];
-    if (act) decide_op_l2(m, b, i);
-    __syncthreads();
-    if (wid == 0) remap_apply_op(m, b, lane, act);
-    __syncthreads();
   }
+  __syncthreads();
+  // 6. P2C remap in rounds of W_r op slots (warp 0, lane per op): decide on
+  //    round-start counts, then place
+  if (wid == 0) {
+    for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+      const uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
+      const uint32_t i = lane;
+      const bool act = i >= lo && i < hi && b.leader[i] == i && b.fpres[i];
+      if (act) decide_op_l2(m, b, i);
+      __syncwarp();
+      remap_apply_op(m, b, i, act);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
   if (b.h_out) {
     // results and the error word back to the caller's pinned staging
     const uint32_t words = (n * (m.vb + 1) + 15) / 16;
@@ -1353,7 +1386,8 @@ cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_
   ProfSpan whole(P_ACCESS, st);
   const uint32_t per_warp = m.page_bytes + 32 * 16;
   uint32_t ew = (200u << 10) / per_warp;
-  ew = ew < 1 ? 1 : (ew > FUSED_THREADS / 32 ? FUSED_THREADS / 32 : ew);
+  // (the last warp runs the ops' semantics meanwhile)
+  ew = ew < 1 ? 1 : (ew > FUSED_THREADS / 32 - 1 ? FUSED_THREADS / 32 - 1 : ew);
   const size_t smem = (size_t)ew * per_warp;
   cudaError_t e = raise_smem_limit((const void*)k_fused, smem);
   if (e != cudaSuccess) return e;

@@ -914,3 +914,33 @@ def test_position_map_rows_one_op_at_a_time():
             cnt[row_of.pop(kk)] -= 1
         assert np.array_equal(cnt, m.rowcounts().astype(np.int64)), t
     m.close()
+
+
+@pytest.mark.parametrize("batch", [1, 64, 4096])
+def test_openmp_build_is_byte_identical(batch):
+    """The multi-core CPU baseline is the oracle's own source built with
+    OpenMP (its independent loops -- PRF draws, per-round decisions, page
+    decryption and encryption -- on several threads).  On the same seeded
+    inputs it gives the same pages, trace, loads, rows, statistics, values
+    and status as the single-threaded build, at any thread count."""
+    N, vb = 1 << 14, 24
+    keys, vals = W.records(12000, vb, 61)
+    ops, k, vin = W.op_stream(12000, 6000, vb, 62, get_frac=0.5, del_frac=0.1,
+                              absent_frac=0.1, zipf_theta=0.99)
+    one = O.OracleMap(N, vb, batch=batch)
+    assert one.init(keys, vals, 9) == 0
+    r1 = one.access(ops, k, vin)
+    for nthreads in (2, 7):
+        assert O.threads(nthreads) == nthreads
+        many = O.OracleMap(N, vb, batch=batch, omp=True)
+        assert many.init(keys, vals, 9) == 0
+        r2 = many.access(ops, k, vin)
+        assert r1[0] == r2[0] == 0
+        assert np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+        assert np.array_equal(one.pages(), many.pages())
+        assert np.array_equal(one.loads(), many.loads())
+        assert np.array_equal(one.rowcounts(), many.rowcounts())
+        assert one.stats() == many.stats()
+        assert np.array_equal(one.trace(clear=False), many.trace(clear=False))
+        many.close()
+    one.close()
