@@ -292,6 +292,8 @@ def run_bolt(args) -> None:
     m = B.BoltMap(N, VAL_BYTES)
     m.set_param(B.BOLT_PARAM_PROFILE, 1)
     m.set_param(B.BOLT_PARAM_LOOKAHEAD, args.lookahead)
+    if args.defer is not None:
+        m.set_param(B.BOLT_PARAM_DEFER_FLUSH, args.defer)
     info = m.info()
     nb = (n_acc + BATCH - 1) // BATCH
 
@@ -954,6 +956,74 @@ def run_validate(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_scaling(args) -> None:
+    """The shape of the paper's scaling experiments (Sec. 5.4: entries from
+    10^5 to 10^7 at 8-byte values; values from 8 to 256 bytes): for each map,
+    the device build (init) time, Gets and Puts one operation per batch
+    (Alg. 1, one command at a time; 2000 ops through bolt_access_device_batches
+    of width 1, device time) and in batches of 4096 (2^20 ops), 50% GET / 50%
+    PUT on present keys, uniform.  Keys and values are generated on the
+    device."""
+    import torch
+    from paper_2509_01742_b300 import bolt as B
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    grid = [(n, 8) for n in (10**5, 10**6, 10**7)] + [(10**6, vb) for vb in (32, 128, 256)]
+    rows = []
+    for N, vb in grid:
+        g = torch.Generator(device="cuda")
+        g.manual_seed(N + vb)
+        with torch.cuda.stream(stream):
+            d_keys = W.key_of_torch(torch.arange(N, device="cuda", dtype=torch.int64))
+            d_vals = torch.randint(0, 256, (N, vb), dtype=torch.uint8, device="cuda", generator=g)
+        n_ops = 1 << 20
+        ops, akeys, avin = W.op_stream(N, n_ops, vb, SEED_OPS + N + vb, get_frac=0.5)
+        d_ops = torch.from_numpy(ops).cuda()
+        d_ak = torch.from_numpy(akeys.view(np.int64)).cuda()
+        d_av = torch.from_numpy(avin).cuda()
+        d_out = torch.empty((n_ops, vb), dtype=torch.uint8, device="cuda")
+        d_st = torch.empty(n_ops, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        m = B.BoltMap(N, vb)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        assert m.init_device(d_keys, d_vals, SEED_MAP, stream=stream) == 0  # warm-up build
+        ev[0].record(stream)
+        assert m.init_device(d_keys, d_vals, SEED_MAP, stream=stream) == 0
+        ev[1].record(stream)
+        n1 = 2000
+        assert m.access_device_batches(d_ops[:64], d_ak[:64], d_av[:64], d_out[:64], d_st[:64],
+                                       1, stream=stream) == 0
+        ev[2].record(stream)
+        assert m.access_device_batches(d_ops[:n1], d_ak[:n1], d_av[:n1], d_out[:n1], d_st[:n1],
+                                       1, stream=stream) == 0
+        ev[3].record(stream)
+        ev[4].record(stream)
+        assert m.access_device_batches(d_ops, d_ak, d_av, d_out, d_st, BATCH, stream=stream) == 0
+        ev[5].record(stream)
+        ev[5].synchronize()
+        assert m.sync() == 0
+        assert bool(d_st.all()), "every accessed key is present"
+        info = m.info()
+        rows.append({"N": N, "val_bytes": vb, "alpha": info["alpha"],
+                     "page_bytes": info["page_bytes"],
+                     "init_ms": round(ev[0].elapsed_time(ev[1]), 2),
+                     "init_mrec_s": round(N / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e6, 1),
+                     "w1_accesses_per_s": round(n1 / (ev[2].elapsed_time(ev[3]) * 1e-3), 1),
+                     "w1_us_per_access": round(ev[2].elapsed_time(ev[3]) * 1e3 / n1, 2),
+                     "batched_accesses_per_s": round(n_ops / (ev[4].elapsed_time(ev[5]) * 1e-3), 1)})
+        print(json.dumps(rows[-1]), flush=True)
+        m.close()
+        del d_keys, d_vals, d_ops, d_ak, d_av, d_out, d_st
+        torch.cuda.empty_cache()
+    line = {"metric": "init time and accesses/s vs entries and value size", "unit": "accesses/s",
+            "n_gpus": 1, "data": "synthetic (device-generated keys and values)",
+            "config": {"workload": "N in {1e5, 1e6, 1e7} at 8 B values; values in {8, 32, 128, "
+                                   "256} B at N = 1e6; uniform 50/50 GET/PUT on present keys"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def make_records_vb(n: int, vb: int, seed: int):
     keys = np.empty(n, dtype=np.uint64)
     for lo in range(0, n, 1 << 24):
@@ -1023,7 +1093,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("bolt", "reference"), default="bolt")
     ap.add_argument("--config", choices=("headline", "zipf", "w1", "serve", "big", "paper",
-                                         "validate"),
+                                         "validate", "scaling"),
                     default="headline",
                     help="headline: the JSON line above; zipf: batch-width sweep on the "
                          "skewed 2^24 x 64 B map; w1: one access per call vs batches of 4096; "
@@ -1041,6 +1111,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the bounded serving run of the headline line")
+    ap.add_argument("--defer", type=int, default=None, choices=(0, 1, 2),
+                    help="BOLT_PARAM_DEFER_FLUSH for the headline map (default: the library's, 0)")
     ap.add_argument("--lookahead", type=float, default=0.0,
                     help="share of each batch's pages read while the previous batch "
                          "finishes (0 = off)")
@@ -1057,6 +1129,8 @@ def main():
         run_paper_workload(args)
     elif args.config == "validate":
         run_validate(args)
+    elif args.config == "scaling":
+        run_scaling(args)
     elif args.config != "headline":
         run_sweep(args)
     else:
