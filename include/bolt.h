@@ -213,6 +213,46 @@ BOLT_API int bolt_init_device_noalloc(bolt_t* h, const void* d_keys, const void*
                                       uint64_t n, uint64_t seed, void* stream);
 
 /*
+ * Owner-side build (Sec. 4.2 "Fast data initialization").  The paper's data
+ * owner pre-organizes the records offline -- each record's random bin pair,
+ * its power-of-two-choices bin, its position-map row -- and the device only
+ * loads that layout with sequential reads and writes.  An image holds n
+ * records in bin-major order: bin 0's records, then bin 1's, ... (bins
+ * 0..K-1 are the HBM bins, bin K + q is host page q), ascending record index
+ * within a bin; all arrays on the DEVICE, 8-byte aligned:
+ */
+typedef struct {
+  uint64_t* keys;   /* [n] the records' keys, bin-major */
+  void* vals;       /* [n * val_bytes] their values, the same order */
+  uint64_t* pairs;  /* [n] each record's bin pair b1 | b2 << 32 */
+  uint32_t* rows;   /* [n] its position-map row, bit 31 set when it sits in b2 */
+  uint8_t* counts;  /* [B] records per bin (the bin loads) */
+} bolt_image_t;
+
+/* bolt_prepare_device -- the data owner's preprocessing on a device: builds
+ * the map from n records exactly as bolt_init_device does (same arguments,
+ * results and errors) and writes the placement it made as an image into the
+ * arrays of *out, which the caller allocated on the device (keys n * 8,
+ * vals n * val_bytes, pairs n * 8, rows n * 4, counts B bytes).  The image
+ * depends only on the records, the map's sizing and the seed. */
+BOLT_API int bolt_prepare_device(bolt_t* h, const void* d_keys, const void* d_vals, uint64_t n,
+                                 uint64_t seed, const bolt_image_t* out, void* stream);
+
+/* bolt_init_prepared -- load an image of n records prepared for this map's
+ * sizing under the same seed (by bolt_prepare_device, or by the data owner's
+ * own program): bin loads from the counts, position-map entries and HBM
+ * residents from the records in order, each host page built from its
+ * contiguous run, encrypted (version 0) and stored.  The result is the map
+ * bolt_init builds from the same records and seed (same pages, loads, rows
+ * and later behaviour).  The image is trusted as the paper's data owner is:
+ * the loader checks what keeps it in bounds -- bins and rows in range, counts
+ * covering exactly n records, no count above lmax (BOLT_E_OVERFLOW), no row
+ * above R (BOLT_E_OVERFLOW), HBM-bin records first -- not the keys'
+ * uniqueness.  Synchronous.  Errors: BOLT_E_ARG, BOLT_E_OVERFLOW, BOLT_E_CUDA. */
+BOLT_API int bolt_init_prepared(bolt_t* h, const bolt_image_t* img, uint64_t n, uint64_t seed,
+                                void* stream);
+
+/*
  * bolt_access -- a batch of n oblivious Get/Put/Delete operations (Alg. 1,
  * applied to a batch; a batch of one is Alg. 1).  Per batch every operation
  * reads the host pages of both bins of its pair (stored pair for the first

@@ -472,8 +472,23 @@ static int claim_pm_slot(omap_t* m, uint64_t row, uint64_t* slot) {
   return ORC_E_OVERFLOW;
 }
 
+/* where oracle_init put each record: its pair, its P2C bin, its
+ * position-map row (arrays of n, filled when non-NULL) */
+typedef struct {
+  uint32_t *b1, *b2, *dest;
+  uint64_t* prow;
+} placement_t;
+
+static int init_impl(omap_t* m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
+                     uint64_t seed, placement_t* out);
+
 int oracle_init(omap_t* m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
                 uint64_t seed) {
+  return init_impl(m, keys, vals, n, seed, NULL);
+}
+
+static int init_impl(omap_t* m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
+                     uint64_t seed, placement_t* out) {
   if (!m || n > m->p.N || (n && (!keys || !vals))) return ORC_E_ARG;
   const oracle_info_t* p = &m->p;
   /* keys must be unique (Sec. 2.1) */
@@ -572,9 +587,52 @@ int oracle_init(omap_t* m, const uint64_t* keys, const uint8_t* vals, uint64_t n
   }
   m->peak_hbm = m->n_hbm;
   m->initialized = 1;
+  if (out && n) {
+    memcpy(out->b1, b1, n * sizeof *b1);
+    memcpy(out->b2, b2, n * sizeof *b2);
+    memcpy(out->dest, dest, n * sizeof *dest);
+    memcpy(out->prow, prow, n * sizeof *prow);
+  }
 out:
   free(b1); free(b2); free(dest); free(prow);
   if (rc) m->poisoned = 1;
+  return rc;
+}
+
+/* The data owner's preprocessing (Sec. 4.2 "Fast data initialization"): the
+ * placement oracle_init makes for these records and this seed, as an image
+ * in bin-major order -- bin 0's records, then bin 1's, ... (bins 0..K-1 are
+ * the HBM bins, bin K + q is host page q), ascending record index within a
+ * bin -- with each record's key and value, its pair b1 | b2 << 32, its
+ * position-map row with bit 31 set when it sits in b2, and every bin's
+ * record count.  The map is built as by oracle_init. */
+int oracle_prepare(omap_t* m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
+                   uint64_t seed, uint64_t* img_keys, uint8_t* img_vals, uint64_t* img_pairs,
+                   uint32_t* img_rows, uint8_t* counts) {
+  if (!m || n > m->p.N || (n && (!keys || !vals || !img_keys || !img_vals || !img_pairs ||
+                                 !img_rows)) || !counts)
+    return ORC_E_ARG;
+  placement_t pl = {malloc((n + 1) * 4), malloc((n + 1) * 4), malloc((n + 1) * 4),
+                    malloc((n + 1) * 8)};
+  uint64_t* start = calloc(m->p.B + 1, sizeof *start);
+  int rc = (!pl.b1 || !pl.b2 || !pl.dest || !pl.prow || !start) ? ORC_E_NOMEM
+                                                                 : init_impl(m, keys, vals, n, seed, &pl);
+  if (rc == ORC_OK) {
+    const oracle_info_t* p = &m->p;
+    const uint32_t vb = p->val_bytes;
+    for (uint64_t b = 0; b < p->B; b++) {
+      counts[b] = (uint8_t)m->load[b];
+      start[b + 1] = start[b] + m->load[b];
+    }
+    for (uint64_t i = 0; i < n; i++) {
+      const uint64_t at = start[pl.dest[i]]++;
+      img_keys[at] = keys[i];
+      memcpy(img_vals + at * vb, vals + i * vb, vb);
+      img_pairs[at] = (uint64_t)pl.b1[i] | ((uint64_t)pl.b2[i] << 32);
+      img_rows[at] = (uint32_t)pl.prow[i] | (pl.dest[i] == pl.b2[i] ? 0x80000000u : 0u);
+    }
+  }
+  free(pl.b1); free(pl.b2); free(pl.dest); free(pl.prow); free(start);
   return rc;
 }
 

@@ -76,6 +76,14 @@ int oracle_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes,
 int oracle_set_param(omap_t*, int which, double v);
 int oracle_init(omap_t*, const uint64_t* keys, const uint8_t* vals, uint64_t n,
                 uint64_t seed);
+/* the data owner's image of the placement oracle_init makes (Sec. 4.2 "Fast
+ * data initialization"): records in bin-major order (HBM bins first, then
+ * host pages; ascending record index within a bin) with their keys, values,
+ * pairs (b1 | b2 << 32) and position-map rows (bit 31 set: in b2), and the B
+ * per-bin counts; builds the map as oracle_init does */
+int oracle_prepare(omap_t*, const uint64_t* keys, const uint8_t* vals, uint64_t n,
+                   uint64_t seed, uint64_t* img_keys, uint8_t* img_vals, uint64_t* img_pairs,
+                   uint32_t* img_rows, uint8_t* counts);
 int oracle_access(omap_t*, const uint8_t* ops, const uint64_t* keys,
                   const uint8_t* vals_in, uint8_t* vals_out, uint8_t* status_out,
                   uint64_t n);

@@ -119,6 +119,7 @@ def _bind_all(L):
         L.oracle_page_decrypt.argtypes = [P, u64, u64, P, P, u64]
         L.oracle_page_decrypt.restype = None
         L.oracle_threads.argtypes = [i32]
+        L.oracle_prepare.argtypes = [P, P, P, u64, u64, P, P, P, P, P]
     return L
 
 
@@ -231,6 +232,20 @@ class OracleMap:
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
         vals = np.ascontiguousarray(vals, dtype=np.uint8)
         return self._L.oracle_init(self._h, _ptr(keys), _ptr(vals), len(keys), seed)
+
+    def prepare(self, keys: np.ndarray, vals: np.ndarray, seed: int):
+        """The data owner's bin-major image of this map's placement (and the
+        map built as by init): (rc, dict of keys, vals, pairs, rows, counts)."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        vals = np.ascontiguousarray(vals, dtype=np.uint8)
+        n = len(keys)
+        img = {"keys": np.zeros(n, np.uint64), "vals": np.zeros((n, self.vb), np.uint8),
+               "pairs": np.zeros(n, np.uint64), "rows": np.zeros(n, np.uint32),
+               "counts": np.zeros(self.info()["B"], np.uint8)}
+        rc = self._L.oracle_prepare(self._h, _ptr(keys), _ptr(vals), n, seed, _ptr(img["keys"]),
+                                    _ptr(img["vals"]), _ptr(img["pairs"]), _ptr(img["rows"]),
+                                    _ptr(img["counts"]))
+        return rc, img
 
     def access(self, ops, keys, vals_in):
         ops = np.ascontiguousarray(ops, dtype=np.uint8)

@@ -74,6 +74,11 @@ class bolt_tune_t(ctypes.Structure):
                 ("width_us", ctypes.c_double * 6)]
 
 
+class bolt_image_t(ctypes.Structure):
+    _fields_ = [("keys", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("pairs", ctypes.c_void_p),
+                ("rows", ctypes.c_void_p), ("counts", ctypes.c_void_p)]
+
+
 class bolt_req_info_t(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("map", ctypes.c_uint32), ("n", ctypes.c_uint32),
                 ("rc", ctypes.c_int), ("submit_us", ctypes.c_double),
@@ -98,6 +103,8 @@ _SIGS = {
     "bolt_init": ([_P, _P, _P, _u64, _u64], _i),
     "bolt_init_device": ([_P, _P, _P, _u64, _u64, _P], _i),
     "bolt_init_device_noalloc": ([_P, _P, _P, _u64, _u64, _P], _i),
+    "bolt_prepare_device": ([_P, _P, _P, _u64, _u64, ctypes.POINTER(bolt_image_t), _P], _i),
+    "bolt_init_prepared": ([_P, ctypes.POINTER(bolt_image_t), _u64, _u64, _P], _i),
     "bolt_access": ([_P, _P, _P, _P, _P, _P, _u64], _i),
     "bolt_access_device": ([_P, _P, _P, _P, _P, _P, _u64, _P], _i),
     "bolt_access_device_batches": ([_P, _P, _P, _P, _P, _P, _u64, ctypes.c_uint32, _P], _i),
@@ -248,6 +255,32 @@ class BoltMap:
         s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
         return bolt_init_device(self._h, ctypes.c_void_p(keys.data_ptr()),
                                 ctypes.c_void_p(vals.data_ptr()), keys.numel(), seed, s)
+
+    def _image(self, img: dict):
+        return bolt_image_t(*(ctypes.c_void_p(img[k].data_ptr())
+                              for k in ("keys", "vals", "pairs", "rows", "counts")))
+
+    def prepare_device(self, keys, vals, seed: int, stream=None):
+        """bolt_prepare_device: build the map from device tensors and return
+        (rc, image) with the image's arrays as device tensors (keys, vals,
+        pairs, rows, counts)."""
+        import torch
+        n = keys.numel()
+        img = {"keys": torch.empty(n, dtype=torch.int64, device=keys.device),
+               "vals": torch.empty((n, self.vb), dtype=torch.uint8, device=keys.device),
+               "pairs": torch.empty(n, dtype=torch.int64, device=keys.device),
+               "rows": torch.empty(n, dtype=torch.int32, device=keys.device),
+               "counts": torch.empty(self.info()["B"], dtype=torch.uint8, device=keys.device)}
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        rc = bolt_prepare_device(self._h, ctypes.c_void_p(keys.data_ptr()),
+                                 ctypes.c_void_p(vals.data_ptr()), n, seed,
+                                 ctypes.byref(self._image(img)), s)
+        return rc, img
+
+    def init_prepared(self, img: dict, n: int, seed: int, stream=None) -> int:
+        """bolt_init_prepared from an image of device tensors."""
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else 0)
+        return bolt_init_prepared(self._h, ctypes.byref(self._image(img)), n, seed, s)
 
     def _check_io(self, ops, keys, vals_in, vals_out, status):
         n = ops.numel()

@@ -405,6 +405,19 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
                          // copy_st (null: straight to the host); two events each
                          cudaStream_t copy_st, cudaEvent_t* ev_built, cudaEvent_t* ev_copied);
 
+// build.cu, the data owner's image (Sec. 4.2 "Fast data initialization"):
+// export the placement the last build (still in `s`) made as a bin-major
+// image; load an image into the map (loads, position map, HBM residents,
+// pages, free ring)
+cudaError_t launch_image_export(const MapDev& m, const uint64_t* keys, const uint8_t* vals,
+                                uint64_t n, struct BuildScratch& s, cudaStream_t st,
+                                uint64_t* img_keys, uint8_t* img_vals, uint64_t* img_pairs,
+                                uint32_t* img_rows, uint8_t* img_counts);
+cudaError_t launch_image_load(const MapDev& m, const uint64_t* keys, const uint8_t* vals,
+                              const uint64_t* pairs, const uint32_t* rows, const uint8_t* counts,
+                              uint64_t n, struct BuildScratch& s, cudaStream_t st,
+                              cudaStream_t copy_st, cudaEvent_t* ev_built, cudaEvent_t* ev_copied);
+
 // sort.cu: ascending bitonic sort of n_pow2 uint64 tags in place; the
 // passes are profiled under the given classes
 cudaError_t sort_tags_u64(uint64_t* tags, uint64_t n_pow2, int log_tile, cudaStream_t st,

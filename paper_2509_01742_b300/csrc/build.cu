@@ -336,10 +336,14 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_fill(MapDev m, const uint32
 // Pages [q0, q1); each ciphertext goes to out + (q - q0) * page_bytes in HBM
 // when `out` is given (the copy engine moves the chunk to the host), else
 // straight to the host page.
+// Without tags (a data owner's image, records already in bin-major order)
+// page q's run is records run_base[0] + page_off[q] ... of keys / vals, the
+// first n_rec of them being valid.
 __global__ void k_page_build(MapDev m, const uint64_t* __restrict__ keys,
                              const uint8_t* __restrict__ vals, const uint64_t* __restrict__ tags,
                              const uint32_t* __restrict__ page_off, uint32_t warps_per_block,
-                             uint64_t q0, uint64_t q1, uint8_t* out) {
+                             uint64_t q0, uint64_t q1, uint8_t* out,
+                             const unsigned long long* run_base, uint64_t n_rec) {
   extern __shared__ __align__(16) uint8_t sbuf[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint8_t* plain = sbuf + (size_t)wid * m.page_bytes;
@@ -350,12 +354,22 @@ __global__ void k_page_build(MapDev m, const uint64_t* __restrict__ keys,
     uint64_t key = ~0ull;
     uint32_t src = NONE32;
     if (lane < (int)cnt) {
-      uint64_t t = tags[off + lane];
-      if ((t >> 32) != q) {
-        set_err(m, ERR_PAGE);  // counts and sorted tags disagree
+      if (tags) {
+        uint64_t t = tags[off + lane];
+        if ((t >> 32) != q) {
+          set_err(m, ERR_PAGE);  // counts and sorted tags disagree
+        } else {
+          src = (uint32_t)t;
+          key = keys[src];
+        }
       } else {
-        src = (uint32_t)t;
-        key = keys[src];
+        const uint64_t r = *run_base + off + lane;
+        if (r < n_rec && lane < (int)m.lmax) {
+          src = (uint32_t)r;
+          key = keys[src];
+        } else {
+          set_err(m, ERR_PAGE);  // counts do not fit the image
+        }
       }
     }
     if (cnt > 32 || cnt > m.lmax) set_err(m, ERR_PAGE);
@@ -407,11 +421,166 @@ __global__ void k_ring_fill(MapDev m, const unsigned long long* vs_fill) {
   if ((threadIdx.x & 31) == 0 && top) atomicMax(m.stat + ST_PEAK_LOAD, (unsigned long long)top);
 }
 
+// --- the data owner's image (Sec. 4.2 "Fast data initialization") ---------
+// export: every record tagged (bin << 32 | record) so that sorting groups the
+// records bin by bin, ascending record index within a bin
+__global__ void k_image_tags(const uint32_t* __restrict__ dest, uint64_t n, uint64_t n_pow2,
+                             uint64_t* __restrict__ tags) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pow2;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    tags[i] = i < n ? ((uint64_t)dest[i] << 32) | i : ~0ull;
+}
+
+// export: the sorted records' keys, values, pairs and rows (bit 31: in b2)
+__global__ void k_image_gather(MapDev m, const uint64_t* __restrict__ keys,
+                               const uint8_t* __restrict__ vals, const uint64_t* __restrict__ tags,
+                               const uint64_t* __restrict__ bins, const uint32_t* __restrict__ dest,
+                               const uint32_t* __restrict__ prow, uint64_t n, uint64_t* img_keys,
+                               uint8_t* img_vals, uint64_t* img_pairs, uint32_t* img_rows) {
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)tags[p];
+    const uint64_t bb = bins[i];
+    img_keys[p] = keys[i];
+    const uint64_t* s = reinterpret_cast<const uint64_t*>(vals + (uint64_t)i * m.vb);
+    uint64_t* d = reinterpret_cast<uint64_t*>(img_vals + p * m.vb);
+    for (uint32_t w = 0; w < m.vb / 8; w++) d[w] = s[w];
+    img_pairs[p] = bb;
+    const uint32_t in_b2 = dest[i] == (uint32_t)(bb >> 32) ? 0x80000000u : 0u;
+    img_rows[p] = (prow[i] & PROW_ROW_MASK) | in_b2;
+  }
+}
+
+// load: bin counts above lmax, and the records of the HBM bins (the first of
+// the image) counted into *n_hbm (blockDim a multiple of 32)
+__global__ void k_image_counts(MapDev m, unsigned long long* n_hbm) {
+  uint32_t s = 0;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < m.B;
+       b += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = byte_get(m.load, b);
+    if (c > m.lmax) set_err(m, ERR_LOAD);
+    if (b < m.K) s += c;
+  }
+  s = __reduce_add_sync(0xffffffffu, s);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(n_hbm, (unsigned long long)s);
+}
+
+// load: the counts must cover the n records exactly
+__global__ void k_image_total(MapDev m, const uint32_t* page_off, const unsigned long long* n_hbm,
+                              uint64_t n) {
+  if (*n_hbm + page_off[m.M] != n) set_err(m, ERR_PAGE);
+}
+
+// load: every record's position-map entry (a slot of its row, claimed in any
+// order: which slot holds a key is never observable) and, for the HBM bins'
+// records (the first n_hbm of the image), value-store slot p
+__global__ void k_image_place(MapDev m, const uint64_t* __restrict__ keys,
+                              const uint8_t* __restrict__ vals, const uint64_t* __restrict__ pairs,
+                              const uint32_t* __restrict__ rows, uint64_t n,
+                              const unsigned long long* n_hbm_p) {
+  if (*(volatile uint32_t*)m.err) return;  // counts already wrong
+  const uint64_t n_hbm = *n_hbm_p;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t rw = rows[p];
+    const uint32_t row = rw & 0x7fffffffu, which = rw >> 31;
+    const uint64_t bb = pairs[p];
+    const uint32_t bin = which ? (uint32_t)(bb >> 32) : (uint32_t)bb;
+    const bool hbm = p < n_hbm;
+    if (row >= m.rows || (uint32_t)bb >= m.B || (uint32_t)(bb >> 32) >= m.B ||
+        (bin < m.K) != hbm || (hbm && p >= m.vs_cap)) {
+      set_err(m, ERR_PAGE);  // not an image of this map's sizing
+      continue;
+    }
+    const uint32_t slot = byte_inc(m.rowcnt, row);
+    if (slot >= m.R) {
+      set_err(m, ERR_ROW);
+      continue;
+    }
+    const uint64_t pmi = (uint64_t)row * m.R + slot;
+    uint32_t meta = meta_make(LOC_HOST, which, 0);
+    if (hbm) {
+      m.vs_key[p] = keys[p];
+      const uint64_t* s = reinterpret_cast<const uint64_t*>(vals + p * m.vb);
+      uint64_t* d = reinterpret_cast<uint64_t*>(m.vs_val + p * m.vb);
+      for (uint32_t w = 0; w < m.vb / 8; w++) d[w] = s[w];
+      m.vs_pm[p] = (uint32_t)pmi;
+      m.vs_live[p] = 1;
+      meta = meta_make(LOC_HBM, which, (uint32_t)p);
+    }
+    m.pm_key[pmi] = keys[p];
+    m.pm_bins[pmi] = bb;
+    m.pm_meta[pmi] = meta;
+  }
+}
+
 static int sm_count() {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return sms;
+}
+
+// Every host page: one warp gathers the page's run (from the sorted tags, or
+// a contiguous run of an owner's image when tags is null), orders it by key,
+// pads it, encrypts it under version 0.  With the candidate-row buffer free
+// (it is read only by the rounds), pages are built into two halves of it in
+// chunks and the copy engine moves each chunk to the host (pinned copies run
+// faster than zero-copy stores, and hold no SM-side requests in flight);
+// otherwise straight to the host.
+static cudaError_t build_pages(const MapDev& m, const uint64_t* keys, const uint8_t* vals,
+                               const uint64_t* tags, const unsigned long long* run_base,
+                               uint64_t n_rec, BuildScratch& s, cudaStream_t st,
+                               cudaStream_t copy_st, cudaEvent_t* ev_built, cudaEvent_t* ev_copied) {
+  const int sms = sm_count();
+  uint32_t wpb = (uint32_t)(65536 / m.page_bytes);
+  wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;
+  size_t smem = (size_t)wpb * m.page_bytes;
+  cudaError_t e = raise_smem_limit((const void*)k_page_build, smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t cap = (uint64_t)sms * 32;
+  const uint64_t stage_bytes = s.rows4 ? s.cap * sizeof(uint4) : 0;
+  const uint64_t chunk = stage_bytes / 2 / m.page_bytes;
+  const bool staged = copy_st && chunk >= (1u << 14);
+  ProfSpan ps(P_PAGE_BUILD, st);
+  if (!staged) {
+    const uint64_t blocks = (m.M + wpb - 1) / wpb;
+    k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
+        m, keys, vals, tags, s.page_off, wpb, 0, m.M, nullptr, run_base, n_rec);
+    count_launch();
+    return cudaGetLastError();
+  }
+  uint8_t* stage = reinterpret_cast<uint8_t*>(s.rows4);
+  uint64_t c = 0;
+  for (uint64_t q0 = 0; q0 < m.M; q0 += chunk, c++) {
+    const uint64_t q1 = q0 + chunk < m.M ? q0 + chunk : m.M;
+    const int k = (int)(c & 1);
+    uint8_t* buf = stage + (uint64_t)k * chunk * m.page_bytes;
+    if (c >= 2) cudaStreamWaitEvent(st, ev_copied[k], 0);
+    const uint64_t blocks = (q1 - q0 + wpb - 1) / wpb;
+    k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
+        m, keys, vals, tags, s.page_off, wpb, q0, q1, buf, run_base, n_rec);
+    count_launch();
+    cudaEventRecord(ev_built[k], st);
+    cudaStreamWaitEvent(copy_st, ev_built[k], 0);
+    e = cudaMemcpyAsync(m.pages + q0 * m.page_bytes, buf, (q1 - q0) * m.page_bytes,
+                        cudaMemcpyDefault, copy_st);
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(ev_copied[k], copy_st);
+  }
+  // every chunk is on the host once the last copy on copy_st is done
+  if (c) cudaStreamWaitEvent(st, ev_copied[(c - 1) & 1], 0);
+  return cudaGetLastError();
+}
+
+// the page run starts: exclusive prefix sum of the host pages' loads
+static void scan_page_runs(const MapDev& m, BuildScratch& s, cudaStream_t st) {
+  const uint32_t nblocks = (uint32_t)((m.M + 1 + SCAN_BLOCK * SCAN_ITEMS - 1) /
+                                      (SCAN_BLOCK * SCAN_ITEMS));
+  k_scan_sums<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums);
+  k_scan_top<<<1, SCAN_BLOCK, 0, st>>>(s.block_sums, nblocks);
+  k_scan_fill<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums, s.page_off);
+  count_launch(3);
 }
 
 cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* vals, uint64_t n,
@@ -468,14 +637,10 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
     }
   }
   // 2. page run starts
-  const uint32_t nblocks = (uint32_t)((m.M + 1 + SCAN_BLOCK * SCAN_ITEMS - 1) /
-                                      (SCAN_BLOCK * SCAN_ITEMS));
-  k_scan_sums<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums);
-  k_scan_top<<<1, SCAN_BLOCK, 0, st>>>(s.block_sums, nblocks);
-  k_scan_fill<<<nblocks, SCAN_BLOCK, 0, st>>>(m, s.block_sums, s.page_off);
+  scan_page_runs(m, s, st);
   // 3. tags + bitonic sort
   k_build_tags<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.tag_cap, s.tags);
-  count_launch(4);
+  count_launch();
   cudaError_t e = sort_tags_u64(s.tags, s.tag_cap, s.log_tile, st);
   if (e != cudaSuccess) return e;
   // The position-map entries and HBM residents (k_build_place) are read by
@@ -497,49 +662,8 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   }
   // 4. pages (they read the values)
   if (vals_wait) cudaStreamWaitEvent(st, vals_wait, 0);
-  uint32_t wpb = (uint32_t)(65536 / m.page_bytes);
-  wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;
-  size_t smem = (size_t)wpb * m.page_bytes;
-  e = raise_smem_limit((const void*)k_page_build, smem);
+  e = build_pages(m, keys, vals, s.tags, nullptr, n, s, st, copy_st, ev_built, ev_copied);
   if (e != cudaSuccess) return e;
-  const uint64_t cap = (uint64_t)sms * 32;
-  // With the candidate-row buffer free (it is read only by the rounds), pages
-  // are built into two halves of it in chunks and the copy engine moves each
-  // chunk to the host (pinned copies run faster than zero-copy stores, and
-  // hold no SM-side requests in flight); otherwise straight to the host.
-  const uint64_t stage_bytes = s.rows4 ? s.cap * sizeof(uint4) : 0;
-  const uint64_t chunk = stage_bytes / 2 / m.page_bytes;
-  const bool staged = copy_st && chunk >= (1u << 14);
-  {
-    ProfSpan ps(P_PAGE_BUILD, st);
-    if (!staged) {
-      const uint64_t blocks = (m.M + wpb - 1) / wpb;
-      k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
-          m, keys, vals, s.tags, s.page_off, wpb, 0, m.M, nullptr);
-      count_launch();
-    } else {
-      uint8_t* stage = reinterpret_cast<uint8_t*>(s.rows4);
-      uint64_t c = 0;
-      for (uint64_t q0 = 0; q0 < m.M; q0 += chunk, c++) {
-        const uint64_t q1 = q0 + chunk < m.M ? q0 + chunk : m.M;
-        const int k = (int)(c & 1);
-        uint8_t* buf = stage + (uint64_t)k * chunk * m.page_bytes;
-        if (c >= 2) cudaStreamWaitEvent(st, ev_copied[k], 0);
-        const uint64_t blocks = (q1 - q0 + wpb - 1) / wpb;
-        k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
-            m, keys, vals, s.tags, s.page_off, wpb, q0, q1, buf);
-        count_launch();
-        cudaEventRecord(ev_built[k], st);
-        cudaStreamWaitEvent(copy_st, ev_built[k], 0);
-        e = cudaMemcpyAsync(m.pages + q0 * m.page_bytes, buf, (q1 - q0) * m.page_bytes,
-                            cudaMemcpyDefault, copy_st);
-        if (e != cudaSuccess) return e;
-        cudaEventRecord(ev_copied[k], copy_st);
-      }
-      // every chunk is on the host once the last copy on copy_st is done
-      if (c) cudaStreamWaitEvent(st, ev_copied[(c - 1) & 1], 0);
-    }
-  }
   // 5. free ring
   if (deferred_place) {
     cudaStreamWaitEvent(st, side_join, 0);
@@ -547,6 +671,46 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
     k_ring_fill<<<sms * 4, 256, 0, st>>>(m, s.counters);
     count_launch();
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image_export(const MapDev& m, const uint64_t* keys, const uint8_t* vals,
+                                uint64_t n, BuildScratch& s, cudaStream_t st, uint64_t* img_keys,
+                                uint8_t* img_vals, uint64_t* img_pairs, uint32_t* img_rows,
+                                uint8_t* img_counts) {
+  const int sms = sm_count();
+  cudaError_t e = cudaMemcpyAsync(img_counts, m.load, m.B, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess || n == 0) return e;
+  k_image_tags<<<sms * 8, 256, 0, st>>>(s.dest, n, s.tag_cap, s.tags);
+  count_launch();
+  e = sort_tags_u64(s.tags, s.tag_cap, s.log_tile, st);
+  if (e != cudaSuccess) return e;
+  k_image_gather<<<sms * 8, 256, 0, st>>>(m, keys, vals, s.tags, s.bins, s.dest, s.prow, n,
+                                          img_keys, img_vals, img_pairs, img_rows);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image_load(const MapDev& m, const uint64_t* keys, const uint8_t* vals,
+                              const uint64_t* pairs, const uint32_t* rows, const uint8_t* counts,
+                              uint64_t n, BuildScratch& s, cudaStream_t st, cudaStream_t copy_st,
+                              cudaEvent_t* ev_built, cudaEvent_t* ev_copied) {
+  const int sms = sm_count();
+  ProfSpan ps(P_P2C, st);
+  // bin loads straight from the counts (one byte per bin, as the map packs them)
+  cudaError_t e = cudaMemcpyAsync(m.load, counts, m.B, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return e;
+  unsigned long long* n_hbm = s.counters;
+  cudaMemsetAsync(s.counters, 0, 2 * sizeof(unsigned long long), st);
+  k_image_counts<<<sms * 4, 256, 0, st>>>(m, n_hbm);
+  scan_page_runs(m, s, st);
+  k_image_total<<<1, 1, 0, st>>>(m, s.page_off, n_hbm, n);
+  k_image_place<<<sms * 16, 256, 0, st>>>(m, keys, vals, pairs, rows, n, n_hbm);
+  count_launch(3);
+  e = build_pages(m, keys, vals, nullptr, n_hbm, n, s, st, copy_st, ev_built, ev_copied);
+  if (e != cudaSuccess) return e;
+  k_ring_fill<<<sms * 4, 256, 0, st>>>(m, s.counters);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -664,19 +664,17 @@ void drain_flushes(bolt* h, cudaStream_t st) {
   h->slot = 0;
 }
 
-int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n, uint64_t seed,
-              cudaStream_t st, BuildScratch& bs, cudaEvent_t vals_ready = nullptr) {
+// The start of every build: the handle's earlier work done, the map state
+// reset, the working keys derived from the seed.
+int build_prologue(bolt* h, uint64_t seed, cudaStream_t st) {
   // work the handle left on another stream (a caller stream of the access
   // calls) finishes before the build resets the map
   if (h->last_st && h->last_st != st && sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
   drain_flushes(h, st);
   MapDev& m = h->m;
   const bolt_info_t& I = h->info;
-  int rc = BOLT_OK;
   h->initialized = false;
   h->poisoned = false;
-  ProfSpan whole(P_BUILD, st);
-  const int sms = sm_count();
   // reset the map state
   cudaMemsetAsync(m.load, 0, (I.B / 4 + 2) * 4, st);
   cudaMemsetAsync(m.rowcnt, 0, (I.rows / 4 + 2) * 4, st);
@@ -698,6 +696,39 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     m.kprf[i] = kw[i];
     m.kenc[i] = kw[8 + i];
   }
+  return BOLT_OK;
+}
+
+// The end of every build: the error word (and the key check's flag) read
+// back, the handle poisoned or made ready.
+int build_epilogue(bolt* h, cudaStream_t st, bool check) {
+  uint32_t err = 0;
+  h->last_st = st;
+  int rc = read_err(h, &err);
+  if (rc) return rc;
+  if (check) {
+    uint32_t flag = 0;
+    if (cudaMemcpy(&flag, h->d_flag, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return BOLT_E_CUDA;
+    if (flag) return BOLT_E_DUPKEY;
+  }
+  rc = err_to_rc(err);
+  if (rc) {
+    h->poisoned = true;
+    return rc;
+  }
+  h->t = 0;
+  h->batches = 0;
+  h->initialized = true;
+  return BOLT_OK;
+}
+
+int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n, uint64_t seed,
+              cudaStream_t st, BuildScratch& bs, cudaEvent_t vals_ready = nullptr) {
+  ProfSpan whole(P_BUILD, st);
+  int rc = build_prologue(h, seed, st);
+  if (rc) return rc;
+  MapDev& m = h->m;
+  const int sms = sm_count();
   bs.log_tile = h->sort_log_tile;
   // key uniqueness (Sec. 2.1).  With the key-sort buffer available it is a
   // hashed check on the side stream (below); otherwise a sorted copy of the
@@ -715,6 +746,7 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     count_launch();
     return cudaGetLastError();
   };
+  cudaError_t e = cudaSuccess;
   if (check && !side) {
     e = key_check(st, bs.tags);  // in line, before the build reuses `tags`
     if (e != cudaSuccess) return BOLT_E_CUDA;
@@ -736,24 +768,7 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     cudaEventRecord(h->ev_join, h->st2);
     cudaStreamWaitEvent(st, h->ev_join, 0);
   }
-  uint32_t err = 0;
-  h->last_st = st;
-  rc = read_err(h, &err);
-  if (rc) return rc;
-  if (check) {
-    uint32_t flag = 0;
-    if (cudaMemcpy(&flag, h->d_flag, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return BOLT_E_CUDA;
-    if (flag) return BOLT_E_DUPKEY;
-  }
-  rc = err_to_rc(err);
-  if (rc) {
-    h->poisoned = true;
-    return rc;
-  }
-  h->t = 0;
-  h->batches = 0;
-  h->initialized = true;
-  return BOLT_OK;
+  return build_epilogue(h, st, check);
 }
 
 }  // namespace
@@ -993,6 +1008,43 @@ int bolt_init(bolt_t* h, const void* keys, const void* vals, uint64_t n, uint64_
     if (e != cudaSuccess) return BOLT_E_CUDA;
   }
   return init_impl(h, h->in_keys, h->in_vals, n, seed, h->st, h->bs, n ? h->ev_in : nullptr);
+}
+
+int bolt_prepare_device(bolt_t* h, const void* d_keys, const void* d_vals, uint64_t n,
+                        uint64_t seed, const bolt_image_t* out, void* stream) {
+  if (!h || !h->allocated || !out || !out->counts || n > h->N ||
+      (n && (!out->keys || !out->vals || !out->pairs || !out->rows)))
+    return BOLT_E_ARG;
+  int rc = bolt_init_device(h, d_keys, d_vals, n, seed, stream);
+  if (rc) return rc;
+  ProfScope prof_scope(h);
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
+  // the build's placement is still in its scratch: dest, rows, pairs
+  cudaError_t e = launch_image_export(h->m, static_cast<const uint64_t*>(d_keys),
+                                      static_cast<const uint8_t*>(d_vals), n, h->bs, st, out->keys,
+                                      static_cast<uint8_t*>(out->vals), out->pairs, out->rows,
+                                      out->counts);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? BOLT_OK : BOLT_E_CUDA;
+}
+
+int bolt_init_prepared(bolt_t* h, const bolt_image_t* img, uint64_t n, uint64_t seed,
+                       void* stream) {
+  if (!h || !h->allocated || !img || !img->counts || n > h->N ||
+      (n && (!img->keys || !img->vals || !img->pairs || !img->rows)))
+    return BOLT_E_ARG;
+  ProfScope prof_scope(h);
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->st;
+  int rc = grow_build_scratch(h, n);
+  if (rc) return rc;
+  ProfSpan whole(P_BUILD, st);
+  rc = build_prologue(h, seed, st);
+  if (rc) return rc;
+  cudaError_t e = launch_image_load(h->m, img->keys, static_cast<const uint8_t*>(img->vals),
+                                    img->pairs, img->rows, img->counts, n, h->bs, st, h->st_fl,
+                                    h->ev_evicted, h->ev_flushed);
+  if (e != cudaSuccess) return BOLT_E_CUDA;
+  return build_epilogue(h, st, false);
 }
 
 int bolt_sync(bolt_t* h) {

@@ -112,7 +112,7 @@ def test_binding_layouts_match_header(tmp_path):
     import ctypes
     import subprocess
     from paper_2509_01742_b300 import bolt as B
-    structs = ["bolt_info_t", "bolt_stats_t", "bolt_profile_t", "bolt_tune_t",
+    structs = ["bolt_info_t", "bolt_stats_t", "bolt_profile_t", "bolt_tune_t", "bolt_image_t",
                "bolt_req_info_t", "bolt_server_stats_t"]
     lines = ['#include <stdio.h>', '#include "bolt.h"', "int main(void) {"]
     for s in structs:

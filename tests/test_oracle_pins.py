@@ -944,3 +944,54 @@ def test_openmp_build_is_byte_identical(batch):
         assert np.array_equal(one.trace(clear=False), many.trace(clear=False))
         many.close()
     one.close()
+
+
+def test_owner_image_matches_the_built_map():
+    """The data owner's image (Sec. 4.2 "Fast data initialization"): records
+    in bin-major order (HBM bins first, then host pages; ascending record
+    index within a bin), each with the pair PRF(INIT, i), the bin it sits in,
+    and a position-map row among its d = 4 candidate rows.  Checked against
+    the map the same call builds: per-bin counts equal the bin loads, the rows
+    recount to the position-map row counts, every host page decrypts to
+    exactly its bin's run of the image."""
+    N, vb = 1 << 14, 16
+    keys, vals = W.records(12000, vb, 41)
+    m = O.OracleMap(N, vb)
+    rc, img = m.prepare(keys, vals, 5)
+    assert rc == 0
+    info = m.info()
+    K, B_ = info["K"], info["B"]
+    assert np.array_equal(img["counts"], m.loads())
+    assert int(img["counts"].sum()) == len(keys)
+    idx_of = {int(k): i for i, k in enumerate(keys)}
+    src = np.array([idx_of[int(k)] for k in img["keys"]])
+    assert sorted(src.tolist()) == list(range(len(keys)))  # a permutation
+    assert np.array_equal(img["vals"], vals[src])
+    b1 = (img["pairs"] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    b2 = (img["pairs"] >> np.uint64(32)).astype(np.int64)
+    in_b2 = (img["rows"] >> np.uint32(31)).astype(bool)
+    rows = (img["rows"] & np.uint32(0x7FFFFFFF)).astype(np.int64)
+    bins = np.where(in_b2, b2, b1)
+    assert np.all(np.diff(bins) >= 0), "bin-major order"
+    same = np.diff(bins) == 0
+    assert np.all(np.diff(src)[same] > 0), "ascending record index within a bin"
+    assert np.array_equal(np.bincount(bins, minlength=B_), img["counts"].astype(np.int64))
+    kprf, _ = m.keys()
+    for j in range(0, len(keys), 97):
+        assert O.pair(kprf, 1, int(src[j]), B_) == (b1[j], b2[j])
+        # the row is one of the key's d = 4 candidates PRF(PM, key) (Sec. 4.2)
+        k = int(img["keys"][j])
+        w = O.chacha20_block(kprf, 0, [2, k & 0xFFFFFFFF, k >> 32]).astype(np.uint64)
+        cand = [((int(w[2 * t]) | (int(w[2 * t + 1]) << 32)) * info["rows"]) >> 64 for t in range(4)]
+        assert rows[j] in cand
+    assert np.array_equal(np.bincount(rows, minlength=info["rows"]), m.rowcounts())
+    starts = np.concatenate([[0], np.cumsum(img["counts"].astype(np.int64))])
+    rec = 8 + vb
+    for q in range(0, info["M"], 37):
+        plain = m.decrypt_page(q)
+        cnt = int(img["counts"][K + q])
+        lo = starts[K + q]
+        slots = plain[16:16 + cnt * rec].reshape(cnt, rec)
+        got = slots[:, :8].copy().view(np.uint64)[:, 0]
+        assert np.array_equal(got, np.sort(img["keys"][lo:lo + cnt]))
+    m.close()
