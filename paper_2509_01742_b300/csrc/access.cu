@@ -579,8 +579,30 @@ __device__ __forceinline__ void page_in(const MapDev& m, const BatchDev& b, uint
 // (lookahead), else from the host.  With lookahead, a leader searched ahead
 // keeps a miss and re-checks a hit (a slot the previous batch was re-using
 // could have looked like a match), the others search now.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// While a claimed page's host read is in flight: bring what its eviction will
+// read into L2 -- the reverse-index count and list, then each listed stash
+// item's live flag, key and value (only entries below the count: those past
+// it are stale).  All 32 lanes call.
+__device__ __forceinline__ void prefetch_eviction(const MapDev& m, uint32_t q, bool claimed,
+                                                  int lane) {
+  uint32_t vs = NONE32;
+  if (claimed && lane < (int)m.lmax) {
+    const uint32_t e = m.rev[(uint64_t)q * m.lmax + lane];
+    if (lane < (int)byte_get(m.revcnt, q)) vs = e;
+  }
+  if (vs != NONE32) {
+    prefetch_l2(m.vs_live + vs);
+    prefetch_l2(m.vs_key + vs);
+    prefetch_l2(m.vs_val + (uint64_t)vs * m.vb);
+  }
+}
+
 __device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, uint32_t i,
-                                          int lane) {
+                                          int lane, bool prefetch = false) {
   uint32_t found = NONE32;
   uint64_t fb = 0;
   if (b.leader[i] == i) {
@@ -654,6 +676,9 @@ __device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, ui
     if (kind[k] != SRC_NONE && 16 * lane < m.page_bytes)
       x[k] = *reinterpret_cast<const uint4*>(src[k] + 16 * lane);
   }
+  if (prefetch)
+#pragma unroll
+    for (int k = 0; k < 2; k++) prefetch_eviction(m, qs[k], kind[k] != SRC_NONE, lane);
   if (!b.la_on) {
 #pragma unroll
     for (int k = 0; k < 2; k++) {
@@ -1282,11 +1307,17 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     } else if (wid == 1) {
       prf_pair(m, DOM_REMAP, t0 + i, p1, p2);
       b.rpair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
+      // the remap will read these loads and take a free value-store slot
+      prefetch_l2(m.load + (p1 >> 2));
+      prefetch_l2(m.load + (p2 >> 2));
+      if (i == 0) prefetch_l2(m.ring + (*m.ring_ctr % m.vs_cap));
     } else {
       uint32_t rows[4];
       prf_rows(m, b.keys[i], rows);
       *reinterpret_cast<uint4*>(b.rows + 4 * (uint64_t)i) =
           make_uint4(rows[0], rows[1], rows[2], rows[3]);
+#pragma unroll
+      for (int j = 0; j < 4; j++) prefetch_l2(m.rowcnt + (rows[j] >> 2));
     }
   }
   if (wid == 3) {
@@ -1313,7 +1344,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   }
   __syncthreads();
   // 2. position-map search and page reads (warp per op)
-  for (uint32_t i = wid; i < n; i += nwarps) lookup_op(m, b, i, lane);
+  for (uint32_t i = wid; i < n; i += nwarps) lookup_op(m, b, i, lane, true);
   __syncthreads();
   // 3. the host-access trace (every read position in order, then each
   //    distinct page once as a write); the previous batch's table is cleared
