@@ -416,6 +416,7 @@ cudaError_t launch_image_export(const MapDev& m, const uint64_t* keys, const uin
 cudaError_t launch_image_load(const MapDev& m, const uint64_t* keys, const uint8_t* vals,
                               const uint64_t* pairs, const uint32_t* rows, const uint8_t* counts,
                               uint64_t n, struct BuildScratch& s, cudaStream_t st,
+                              cudaStream_t side, cudaEvent_t side_fork, cudaEvent_t side_join,
                               cudaStream_t copy_st, cudaEvent_t* ev_built, cudaEvent_t* ev_copied);
 
 // sort.cu: ascending bitonic sort of n_pow2 uint64 tags in place; the

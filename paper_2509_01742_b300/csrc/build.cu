@@ -693,10 +693,10 @@ cudaError_t launch_image_export(const MapDev& m, const uint64_t* keys, const uin
 
 cudaError_t launch_image_load(const MapDev& m, const uint64_t* keys, const uint8_t* vals,
                               const uint64_t* pairs, const uint32_t* rows, const uint8_t* counts,
-                              uint64_t n, BuildScratch& s, cudaStream_t st, cudaStream_t copy_st,
+                              uint64_t n, BuildScratch& s, cudaStream_t st, cudaStream_t side,
+                              cudaEvent_t side_fork, cudaEvent_t side_join, cudaStream_t copy_st,
                               cudaEvent_t* ev_built, cudaEvent_t* ev_copied) {
   const int sms = sm_count();
-  ProfSpan ps(P_P2C, st);
   // bin loads straight from the counts (one byte per bin, as the map packs them)
   cudaError_t e = cudaMemcpyAsync(m.load, counts, m.B, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
@@ -705,12 +705,22 @@ cudaError_t launch_image_load(const MapDev& m, const uint64_t* keys, const uint8
   k_image_counts<<<sms * 4, 256, 0, st>>>(m, n_hbm);
   scan_page_runs(m, s, st);
   k_image_total<<<1, 1, 0, st>>>(m, s.page_off, n_hbm, n);
-  k_image_place<<<sms * 16, 256, 0, st>>>(m, keys, vals, pairs, rows, n, n_hbm);
-  count_launch(3);
+  count_launch(2);
+  // the position-map entries, HBM residents and free ring are read by no
+  // step of the page build: they are written on the side stream beside it
+  cudaEventRecord(side_fork, st);
+  cudaStreamWaitEvent(side, side_fork, 0);
+  {
+    ProfSpan ps(P_P2C, side);
+    k_image_place<<<sms * 16, 256, 0, side>>>(m, keys, vals, pairs, rows, n, n_hbm);
+    count_launch();
+  }
+  k_ring_fill<<<sms * 4, 256, 0, side>>>(m, s.counters);
+  count_launch();
+  cudaEventRecord(side_join, side);
   e = build_pages(m, keys, vals, nullptr, n_hbm, n, s, st, copy_st, ev_built, ev_copied);
   if (e != cudaSuccess) return e;
-  k_ring_fill<<<sms * 4, 256, 0, st>>>(m, s.counters);
-  count_launch();
+  cudaStreamWaitEvent(st, side_join, 0);
   return cudaGetLastError();
 }
 

@@ -1041,8 +1041,9 @@ int bolt_init_prepared(bolt_t* h, const bolt_image_t* img, uint64_t n, uint64_t 
   rc = build_prologue(h, seed, st);
   if (rc) return rc;
   cudaError_t e = launch_image_load(h->m, img->keys, static_cast<const uint8_t*>(img->vals),
-                                    img->pairs, img->rows, img->counts, n, h->bs, st, h->st_fl,
-                                    h->ev_evicted, h->ev_flushed);
+                                    img->pairs, img->rows, img->counts, n, h->bs, st, h->st2,
+                                    h->ev_pfork, h->ev_pjoin, h->st_fl, h->ev_evicted,
+                                    h->ev_flushed);
   if (e != cudaSuccess) return BOLT_E_CUDA;
   return build_epilogue(h, st, false);
 }
