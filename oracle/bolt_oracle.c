@@ -29,6 +29,7 @@
 #include <string.h>
 
 #define ORC_E_INTERNAL -9
+#define ORC_E_INTEGRITY -8
 
 enum { LOC_EMPTY = 0, LOC_HOST = 1, LOC_HBM = 2, LOC_STASH = 3 };
 enum { OP_GET = 0, OP_PUT = 1, OP_DEL = 2 };
@@ -41,6 +42,7 @@ struct omap {
   double alpha_override; /* < 0: use the budget policy */
   uint32_t c_param;
   int nocrypt, trace_on;
+  int integrity; /* pages are ChaCha20-Poly1305 sealed (tag in the last 16 bytes) */
   uint64_t batch_width;
 
   int allocated, initialized, poisoned;
@@ -218,7 +220,17 @@ int oracle_sizing(uint64_t N, uint32_t c, double alpha, uint32_t val_bytes,
 
 /* alpha policy (Sec. 3.3 "Parameters selection"): the largest alpha of a
  * fixed grid whose value store (V_hbm + stash) fits the HBM budget. */
+static int choose_alpha_plain(omap_t* m, oracle_info_t* o);
+
+/* the sizing policy, then room for the tag when pages are sealed */
 static int choose_alpha(omap_t* m, oracle_info_t* o) {
+  int rc = choose_alpha_plain(m, o);
+  if (rc == ORC_OK && m->integrity)
+    o->page_bytes = (16 + o->lmax * o->rec_bytes + 16 + 63) / 64 * 64;
+  return rc;
+}
+
+static int choose_alpha_plain(omap_t* m, oracle_info_t* o) {
   if (m->alpha_override >= 0.0)
     return oracle_sizing(m->p.N, m->c_param, m->alpha_override, m->p.val_bytes, o);
   static const double grid[] = {0.2, 0.1, 0.05, 0.01, 0.0};
@@ -291,6 +303,9 @@ int oracle_set_param(omap_t* m, int which, double v) {
       m->c_param = (uint32_t)v;
       break;
     case ORC_PARAM_NOCRYPT: m->nocrypt = v != 0.0; return ORC_OK;
+    case ORC_PARAM_INTEGRITY:
+      m->integrity = v != 0.0;
+      break;
     case ORC_PARAM_TRACE: m->trace_on = v != 0.0; return ORC_OK;
     case ORC_PARAM_BATCH:
       if (v < 1.0 || v > 65536.0) return ORC_E_ARG;
@@ -400,10 +415,126 @@ static int cmp_tuple(const void* a, const void* b) {
   return x < y ? -1 : x > y;
 }
 
-static void page_crypt(const omap_t* m, uint64_t q, uint64_t version, uint8_t* buf) {
+/* Poly1305 one-time authenticator (RFC 8439, Sec. 2.5), written from its
+ * definition: r = key[0..15] with the specified bits cleared, s =
+ * key[16..31]; each 16-byte block of the message (the last one may be short)
+ * with a 1 byte appended is added to the accumulator, which is then
+ * multiplied by r modulo p = 2^130 - 5; the tag is (h + s) mod 2^128.  The
+ * accumulator is kept in three 64-bit limbs, products in 128-bit integers. */
+void oracle_poly1305(const uint8_t key[32], const uint8_t* msg, uint64_t len, uint8_t tag[16]) {
+  typedef unsigned __int128 u128;
+  uint64_t r0, r1, s0, s1;
+  memcpy(&r0, key, 8);
+  memcpy(&r1, key + 8, 8);
+  memcpy(&s0, key + 16, 8);
+  memcpy(&s1, key + 24, 8);
+  r0 &= 0x0ffffffc0fffffffull;
+  r1 &= 0x0ffffffc0ffffffcull;
+  uint64_t h0 = 0, h1 = 0, h2 = 0; /* h = h0 + h1 2^64 + h2 2^128 */
+  for (uint64_t off = 0; off < len; off += 16) {
+    uint8_t blk[17] = {0};
+    const uint64_t n = len - off < 16 ? len - off : 16;
+    memcpy(blk, msg + off, n);
+    blk[n] = 1;
+    uint64_t m0, m1;
+    memcpy(&m0, blk, 8);
+    memcpy(&m1, blk + 8, 8);
+    /* h += block */
+    u128 t = (u128)h0 + m0;
+    h0 = (uint64_t)t;
+    t = (u128)h1 + m1 + (uint64_t)(t >> 64);
+    h1 = (uint64_t)t;
+    h2 += blk[16] + (uint64_t)(t >> 64);
+    /* h *= r: the four 128-bit partial sums of the product */
+    const u128 d0 = (u128)h0 * r0;
+    const u128 d1 = (u128)h0 * r1 + (u128)h1 * r0;
+    const u128 d2 = (u128)h1 * r1 + (u128)h2 * r0;
+    const u128 d3 = (u128)h2 * r1;
+    uint64_t p0 = (uint64_t)d0;
+    u128 c = (d0 >> 64) + d1;
+    uint64_t p1 = (uint64_t)c;
+    c = (c >> 64) + d2;
+    uint64_t p2 = (uint64_t)c;
+    uint64_t p3 = (uint64_t)((c >> 64) + d3);
+    /* mod p: the bits from 2^130 up fold back times 5 (2^130 = 5 mod p) */
+    const u128 hi = ((u128)p3 << 62) | (p2 >> 2);
+    const u128 hi5 = hi * 5;
+    t = (u128)p0 + (uint64_t)hi5;
+    h0 = (uint64_t)t;
+    t = (u128)p1 + (uint64_t)(hi5 >> 64) + (uint64_t)(t >> 64);
+    h1 = (uint64_t)t;
+    h2 = (p2 & 3) + (uint64_t)(t >> 64);
+  }
+  /* full reduction: subtract p while h >= p (h + 5 reaches 2^130) */
+  for (int k = 0; k < 2; k++) {
+    u128 t = (u128)h0 + 5;
+    const uint64_t g0 = (uint64_t)t;
+    t = (u128)h1 + (uint64_t)(t >> 64);
+    const uint64_t g1 = (uint64_t)t;
+    const uint64_t g2 = h2 + (uint64_t)(t >> 64);
+    if (g2 >> 2) {
+      h0 = g0;
+      h1 = g1;
+      h2 = g2 & 3;
+    }
+  }
+  u128 t = (u128)h0 + s0;
+  const uint64_t t0 = (uint64_t)t;
+  const uint64_t t1 = h1 + s1 + (uint64_t)(t >> 64);
+  memcpy(tag, &t0, 8);
+  memcpy(tag + 8, &t1, 8);
+}
+
+/* The page cipher.  Without integrity: ChaCha20 under K_enc, nonce = page q
+ * (u32) || version (u64), counter from 0, over the whole page.  With
+ * integrity (NEXT-4: per-page authentication bound to (page, version)): the
+ * ChaCha20-Poly1305 AEAD of RFC 8439 Sec. 2.8 with the same key and nonce and
+ * no additional data -- the one-time Poly1305 key is the first 32 bytes of
+ * block 0, the page's first page_bytes - 16 bytes are encrypted from block 1,
+ * and the tag over them and their length fills the last 16 bytes. */
+static void aead_tag(const omap_t* m, const uint32_t nonce[3], const uint8_t* ct, uint64_t len,
+                     uint8_t tag[16]) {
+  uint32_t blk[16];
+  oracle_chacha20_block(m->kenc, 0, nonce, blk);
+  uint8_t otk[32];
+  memcpy(otk, blk, 32);
+  uint8_t* mac = malloc(len + 16);
+  memcpy(mac, ct, len);
+  const uint64_t lens[2] = {0, len}; /* no additional data; len is a multiple of 16 */
+  memcpy(mac + len, lens, 16);
+  oracle_poly1305(otk, mac, len + 16, tag);
+  free(mac);
+}
+
+static void page_seal(const omap_t* m, uint64_t q, uint64_t version, uint8_t* buf) {
   if (m->nocrypt) return;
   uint32_t nonce[3] = {(uint32_t)q, (uint32_t)version, (uint32_t)(version >> 32)};
-  oracle_chacha20_xor(m->kenc, 0, nonce, buf, m->p.page_bytes);
+  if (!m->integrity) {
+    oracle_chacha20_xor(m->kenc, 0, nonce, buf, m->p.page_bytes);
+    return;
+  }
+  const uint64_t len = m->p.page_bytes - 16;
+  oracle_chacha20_xor(m->kenc, 1, nonce, buf, len);
+  aead_tag(m, nonce, buf, len, buf + len);
+}
+
+/* decrypt a page read from the host; with integrity its tag is checked
+ * first (ORC_E_INTEGRITY when it does not match: the host changed the page,
+ * or replayed an older version of it) */
+static int page_open(const omap_t* m, uint64_t q, uint64_t version, uint8_t* buf) {
+  if (m->nocrypt) return ORC_OK;
+  uint32_t nonce[3] = {(uint32_t)q, (uint32_t)version, (uint32_t)(version >> 32)};
+  if (!m->integrity) {
+    oracle_chacha20_xor(m->kenc, 0, nonce, buf, m->p.page_bytes);
+    return ORC_OK;
+  }
+  const uint64_t len = m->p.page_bytes - 16;
+  uint8_t tag[16];
+  aead_tag(m, nonce, buf, len, tag);
+  if (memcmp(tag, buf + len, 16)) return ORC_E_INTEGRITY;
+  oracle_chacha20_xor(m->kenc, 1, nonce, buf, len);
+  memset(buf + len, 0, 16);
+  return ORC_OK;
 }
 
 /* Build the plaintext of a page holding `cnt` tuples (sorted here), encrypt
@@ -419,7 +550,7 @@ static void page_store(omap_t* m, uint64_t q, tuple_t* t, uint32_t cnt, uint64_t
     memcpy(slot, &t[s].key, 8);
     memcpy(slot + 8, t[s].val, p->val_bytes);
   }
-  page_crypt(m, q, version, buf);
+  page_seal(m, q, version, buf);
   memcpy(m->pages + q * p->page_bytes, buf, p->page_bytes);
   free(buf);
 }
@@ -438,8 +569,7 @@ void oracle_page_decrypt(const uint32_t kenc[8], uint64_t q, uint64_t version,
 int oracle_decrypt_page(const omap_t* m, uint64_t q, uint8_t* out) {
   if (!m || !m->initialized || q >= m->p.M) return ORC_E_ARG;
   memcpy(out, m->pages + q * m->p.page_bytes, m->p.page_bytes);
-  page_crypt(m, q, m->version[q], out);
-  return ORC_OK;
+  return page_open(m, q, m->version[q], out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -750,15 +880,20 @@ static int access_batch(omap_t* m, const uint8_t* ops, const uint64_t* keys,
       nd++;
     }
   }
+  int open_rc = ORC_OK;
 #pragma omp parallel for schedule(static) if (nd >= 64)
   for (uint64_t d = 0; d < nd; d++) {
-    page_crypt(m, dp[d].q, m->version[dp[d].q], dp[d].plain);
+    if (page_open(m, dp[d].q, m->version[dp[d].q], dp[d].plain) != ORC_OK) {
+#pragma omp critical
+      open_rc = ORC_E_INTEGRITY;
+    }
     uint64_t bitmap;
     memcpy(&bitmap, dp[d].plain, 8);
     uint32_t cnt = 0;
     while (cnt < 64 && (bitmap >> cnt) & 1) cnt++;
     dp[d].cnt = cnt;
   }
+  if (open_rc) { rc = open_rc; goto out; }
 
   /* 4. find_remove (Alg. 1 lines 6 and 9): take each hit key out of the HBM
    *    store, the stash or its page; its bin's load drops by one. */

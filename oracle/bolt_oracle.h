@@ -63,6 +63,7 @@ typedef struct {
 #define ORC_E_OVERFLOW -3
 #define ORC_E_STATE -4
 #define ORC_E_DUPKEY -5
+#define ORC_E_INTEGRITY -8   /* a page read from the host failed its tag */
 
 /* parameter ids for oracle_set_param */
 #define ORC_PARAM_ALPHA 1      /* override the alpha policy (before init) */
@@ -70,6 +71,7 @@ typedef struct {
 #define ORC_PARAM_NOCRYPT 3    /* 1 = skip the page cipher (long simulations only) */
 #define ORC_PARAM_TRACE 4      /* 1 = record the host-access trace (default 1) */
 #define ORC_PARAM_BATCH 5      /* operations per batch, 1..65536 (default 65536) */
+#define ORC_PARAM_INTEGRITY 6  /* 1 = pages sealed by ChaCha20-Poly1305 (before init) */
 
 int oracle_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes,
                   uint64_t hbm_budget, omap_t** out);
@@ -118,6 +120,8 @@ int oracle_sizing(uint64_t N, uint32_t c, double alpha, uint32_t val_bytes,
                   oracle_info_t* out);
 int oracle_pair(const uint32_t kprf[8], uint32_t dom, uint64_t x, uint64_t B,
                 uint32_t* b1, uint32_t* b2);
+/* Poly1305 tag of len bytes under a 32-byte one-time key (RFC 8439) */
+void oracle_poly1305(const uint8_t key[32], const uint8_t* msg, uint64_t len, uint8_t tag[16]);
 /* the two working keys derived from a seed, as bolt_init derives them */
 void oracle_kdf(uint64_t seed, uint32_t kprf[8], uint32_t kenc[8]);
 /* decrypt one page ciphertext of page_bytes taken from page q at `version`

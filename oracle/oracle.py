@@ -19,7 +19,9 @@ OMP_LIB_PATH = os.path.join(HERE, "liboracle_omp.so")
 SRC_PATH = os.path.join(HERE, "bolt_oracle.c")
 
 PARAM_ALPHA, PARAM_C, PARAM_NOCRYPT, PARAM_TRACE, PARAM_BATCH = 1, 2, 3, 4, 5
+PARAM_INTEGRITY = 6
 OK, E_ARG, E_NOMEM, E_OVERFLOW, E_STATE, E_DUPKEY = 0, -1, -2, -3, -4, -5
+E_INTEGRITY = -8
 GET, PUT, DEL = 0, 1, 2
 
 
@@ -120,6 +122,8 @@ def _bind_all(L):
         L.oracle_page_decrypt.restype = None
         L.oracle_threads.argtypes = [i32]
         L.oracle_prepare.argtypes = [P, P, P, u64, u64, P, P, P, P, P]
+        L.oracle_poly1305.argtypes = [P, P, u64, P]
+        L.oracle_poly1305.restype = None
     return L
 
 
@@ -141,6 +145,15 @@ def chacha20_xor(key_words, counter, nonce_words, data: bytes) -> bytes:
     buf = np.frombuffer(bytearray(data), dtype=np.uint8).copy()
     lib().oracle_chacha20_xor(_ptr(k), counter, _ptr(nn), _ptr(buf), len(buf))
     return buf.tobytes()
+
+
+def poly1305(key: bytes, msg: bytes) -> bytes:
+    """The oracle's Poly1305 tag of msg under a 32-byte one-time key."""
+    k = np.frombuffer(bytes(key), dtype=np.uint8).copy()
+    mm = np.frombuffer(bytes(msg) + b"\0", dtype=np.uint8).copy()
+    tag = np.zeros(16, dtype=np.uint8)
+    lib().oracle_poly1305(_ptr(k), _ptr(mm), len(msg), _ptr(tag))
+    return tag.tobytes()
 
 
 def sizing(N: int, c: int, alpha: float, val_bytes: int) -> dict:
@@ -192,7 +205,7 @@ class OracleMap:
     """One oracle map instance (same call shapes as the product C ABI)."""
 
     def __init__(self, N, val_bytes, hbm_budget=2**64 - 1, key_bytes=8, alpha=None,
-                 c=None, nocrypt=False, trace=True, batch=None, omp=False):
+                 c=None, nocrypt=False, trace=True, batch=None, omp=False, integrity=False):
         """omp=True runs the same oracle from its OpenMP build (independent
         loops on all host cores; results identical to the plain build)."""
         self._L = omp_lib() if omp else lib()
@@ -204,6 +217,8 @@ class OracleMap:
             self.set_param(PARAM_C, c)
         if alpha is not None:
             self.set_param(PARAM_ALPHA, alpha)
+        if integrity:
+            self.set_param(PARAM_INTEGRITY, 1)
         if nocrypt:
             self.set_param(PARAM_NOCRYPT, 1)
         if not trace:
@@ -297,6 +312,15 @@ class OracleMap:
         if clear:
             self._L.oracle_trace_clear(self._h)
         return out
+
+    def host_pages(self):
+        """The host page store itself (writable: a test standing in for a
+        host that alters or replays pages)."""
+        i = self.info()
+        size = i["M"] * i["page_bytes"]
+        addr = self._L.oracle_pages(self._h)
+        buf = (ctypes.c_uint8 * size).from_address(addr)
+        return np.frombuffer(buf, dtype=np.uint8).reshape(i["M"], i["page_bytes"])
 
     def decrypt_page(self, q) -> np.ndarray:
         out = np.zeros(self.info()["page_bytes"], dtype=np.uint8)

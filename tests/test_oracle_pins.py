@@ -995,3 +995,98 @@ def test_owner_image_matches_the_built_map():
         got = slots[:, :8].copy().view(np.uint64)[:, 0]
         assert np.array_equal(got, np.sort(img["keys"][lo:lo + cnt]))
     m.close()
+
+
+# --------------------------------------------------------------------------
+# Page integrity (NEXT-4): pages sealed by ChaCha20-Poly1305, bound to (page, version)
+
+
+def test_poly1305_matches_the_cryptography_package():
+    """The oracle's Poly1305 (RFC 8439 Sec. 2.5, three 64-bit limbs) against
+    an independent implementation, on random keys and messages of every
+    length class (empty, short, exact blocks, ragged tails), and on keys
+    whose r and s sit at the edges of their ranges."""
+    from cryptography.hazmat.primitives.poly1305 import Poly1305
+    rng = np.random.default_rng(301)
+    keys = [rng.bytes(32) for _ in range(40)]
+    keys += [b"\xff" * 32, b"\x00" * 16 + b"\xff" * 16, b"\xff" * 16 + b"\x00" * 16]
+    for j, key in enumerate(keys):
+        for n in (0, 1, 15, 16, 17, 31, 32, 33, 64, 100, 511, 512, 1000):
+            msg = rng.bytes(n) if j % 3 else b"\xff" * n
+            assert O.poly1305(key, msg) == Poly1305.generate_tag(key, msg), (j, n)
+
+
+def test_sealed_pages_are_the_chacha20_poly1305_aead():
+    """With integrity on, every page of a built map, and every page an access
+    batch rewrote (under its bumped version), is the RFC 8439 AEAD
+    encryption of its plaintext under K_enc with nonce page || version and
+    no additional data -- checked by decrypting with the `cryptography`
+    package, which verifies the tag -- and the oracle's own decryption gives
+    the same plaintext.  The page size leaves room for the 16-byte tag."""
+    from cryptography.hazmat.primitives.ciphers.aead import ChaCha20Poly1305
+    N, vb = 1 << 12, 24
+    m = O.OracleMap(N, vb, integrity=True)
+    info = m.info()
+    assert info["page_bytes"] == (16 + info["lmax"] * (8 + vb) + 16 + 63) // 64 * 64
+    keys, vals = W.records(3000, vb, 302)
+    assert m.init(keys, vals, 7) == 0
+    _, kenc = m.keys()
+    aead = ChaCha20Poly1305(kenc.astype("<u4").tobytes())
+
+    def check_all():
+        pages = m.pages()
+        vers = m.versions()
+        for q in range(info["M"]):
+            nonce = int(q).to_bytes(4, "little") + int(vers[q]).to_bytes(8, "little")
+            plain = aead.decrypt(nonce, pages[q].tobytes(), None)
+            assert plain == m.decrypt_page(q)[:info["page_bytes"] - 16].tobytes()
+        return vers
+
+    v0 = check_all()
+    assert not v0.any()
+    ops, k, vin = W.op_stream(3000, 500, vb, 303, del_frac=0.1, absent_frac=0.1)
+    rc, vout, st = m.access(ops, k, vin)
+    assert rc == 0
+    model = DictModel(keys, vals)
+    ev, es = model.apply(ops, k, vin, vb)
+    assert np.array_equal(vout, ev) and np.array_equal(st, es)
+    assert check_all().any()
+    m.close()
+
+
+@pytest.mark.parametrize("attack", ["flip", "replay", "swap"])
+def test_sealed_pages_detect_host_changes(attack):
+    """A host that changes a page (one bit), replays an older version of it,
+    or puts another page's sealed bytes in its place is caught when the page
+    is next read: the access returns ORC_E_INTEGRITY (the version lives in
+    HBM, so an old ciphertext no longer matches its nonce).  Untouched pages
+    read fine."""
+    N, vb = 1 << 12, 8
+    m = O.OracleMap(N, vb, integrity=True, batch=1)
+    keys, vals = W.records(3000, vb, 304)
+    assert m.init(keys, vals, 9) == 0
+    store = m.host_pages()
+    old = store.copy()
+    # one access rewrites the pages of key 0's two bins (and the versions)
+    rc, _, _ = m.access(np.zeros(1, np.uint8), keys[:1], np.zeros((1, vb), np.uint8))
+    assert rc == 0
+    tr = m.trace()
+    written = sorted({int(e) & 0x7FFFFFFF for e in tr if e & 0x80000000})
+    q = written[0]
+    if attack == "flip":
+        store[q, 37] ^= 0x10
+    elif attack == "replay":
+        store[q] = old[q]
+    else:
+        other = (q + 1) % m.info()["M"]
+        store[q] = store[other]
+    # a Get whose DUMMY or stored pair reads page q: run single-op Gets on
+    # keys until one reads q (the trace says which pages each op read)
+    rc = 0
+    for i in range(1, 3000):
+        rc, _, _ = m.access(np.zeros(1, np.uint8), keys[i:i + 1], np.zeros((1, vb), np.uint8))
+        reads = {int(e) for e in m.trace() if not e & 0x80000000}
+        if rc != 0 or q in reads:
+            break
+    assert rc == O.E_INTEGRITY
+    m.close()
