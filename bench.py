@@ -380,29 +380,35 @@ def run_bolt(args) -> None:
                      "records": float(N * args.steps), "accesses": float(n_acc * args.steps)},
                     world, group)
 
-    # secondary roofline: the bitonic global pass of the build, algorithmic
-    # bytes = read + write of every 8-byte tag once per launch, against HBM
+    # secondary roofline: the build's grouping of host records by page (a
+    # counting scatter), algorithmic bytes = a 4-byte destination read per
+    # record, and per host-bin record an 8-byte tag write, the cursor's 4-byte
+    # read and write and a 4-byte run-end read, against HBM.  The host-bin
+    # record count comes from an untimed rebuild (same keys and seed: the same
+    # placement), read from the bin loads before any access.
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
-    sg = prof["sort_global"]
-    tag_cap = 1
-    while tag_cap < N:
-        tag_cap <<= 1
-    bytes_per_launch = 2 * 8 * tag_cap
+    sg = prof["page_group"]
+    m.set_param(B.BOLT_PARAM_PROFILE, 0)
+    assert m.init_device(d_keys, d_vals, SEED_MAP, stream=stream) == 0
+    assert m.sync() == 0
+    n_host = int(m.loads()[info["K"]:].astype(np.int64).sum())
+    bytes_per_launch = 4 * N + 20 * n_host
     avg_s = sg["ms"] / max(1, sg["spans"]) * 1e-3
     achieved = bytes_per_launch / avg_s / 1e9 if sg["spans"] else None
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
-            traffic = json.load(f).get("k_sort_global_u64<4>", {}).get("bytes_per_launch_full")
-    roofline_hbm = {"bound": "hbm", "kernel": "k_sort_global_u64 (bitonic, 4 fused strides)",
+            traffic = json.load(f).get("k_build_scatter", {}).get("bytes_per_launch_full")
+    roofline_hbm = {"bound": "hbm", "kernel": "k_build_scatter (host records grouped by page)",
                     "achieved": round(achieved, 1) if achieved else None,
                     "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(achieved / hbm_peak, 4) if achieved and hbm_peak else None,
                     "traffic": traffic, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"
                     if hbm_peak else "fallback 6400 GB/s",
                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                    "host_records": n_host,
                     "launches": sg["spans"], "avg_launch_ms": round(avg_s * 1e3, 4),
                     "share_of_step": round(sg["ms"] * 1e-3 / step_s, 4)}
 
@@ -541,8 +547,8 @@ def run_bolt(args) -> None:
     # chunks); phase shares from the event-timed kernel classes
     build_ms = build_s / args.steps * 1e3
     page_store = info["M"] * page_bytes
-    bk = {k: prof[k]["ms"] / args.steps for k in ("p2c_rounds", "sort_global", "sort_tile",
-                                                   "page_build", "key_check")}
+    bk = {k: prof[k]["ms"] / args.steps for k in ("p2c_rounds", "page_group", "sort_global",
+                                                   "sort_tile", "page_build", "key_check")}
     build = {"value": round(agg["records"] / agg["build_s"] / 1e6, 2), "unit": "Mrec/s",
              "ms_per_build": round(build_ms, 2),
              "share_of_step": round(agg["build_s"] / agg["step_s"], 4),
@@ -1081,6 +1087,75 @@ def run_scaling(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_integrity(args) -> None:
+    """The cost of sealed pages (BOLT_PARAM_INTEGRITY: ChaCha20-Poly1305 per
+    page, tag checked on every read): the headline map (N = 2^log_n records
+    of 32 B, uniform 50/50 GET/PUT on present keys) built and accessed with
+    plain pages, then with sealed pages -- device build time, one op per
+    batch (2000 ops of width 1) and batches of 4096 (2^22 ops), CUDA events
+    on the map's stream.  Keys and values are generated on the device."""
+    import torch
+    from paper_2509_01742_b300 import bolt as B
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    N, vb = 1 << args.log_n, VAL_BYTES
+    g = torch.Generator(device="cuda")
+    g.manual_seed(SEED_DATA)
+    with torch.cuda.stream(stream):
+        d_keys = W.key_of_torch(torch.arange(N, device="cuda", dtype=torch.int64))
+        d_vals = torch.randint(0, 256, (N, vb), dtype=torch.uint8, device="cuda", generator=g)
+    n_ops = args.accesses
+    ops, akeys, avin = W.op_stream(N, n_ops, vb, SEED_OPS, get_frac=0.5)
+    d_ops = torch.from_numpy(ops).cuda()
+    d_ak = torch.from_numpy(akeys.view(np.int64)).cuda()
+    d_av = torch.from_numpy(avin).cuda()
+    d_out = torch.empty((n_ops, vb), dtype=torch.uint8, device="cuda")
+    d_st = torch.empty(n_ops, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    rows = []
+    for sealed in (0, 1):
+        m = B.BoltMap(N, vb, integrity=bool(sealed))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        assert m.init_device(d_keys, d_vals, SEED_MAP, stream=stream) == 0  # warm-up build
+        ev[0].record(stream)
+        assert m.init_device(d_keys, d_vals, SEED_MAP, stream=stream) == 0
+        ev[1].record(stream)
+        n1 = 2000
+        assert m.access_device_batches(d_ops[:64], d_ak[:64], d_av[:64], d_out[:64], d_st[:64],
+                                       1, stream=stream) == 0
+        ev[2].record(stream)
+        assert m.access_device_batches(d_ops[:n1], d_ak[:n1], d_av[:n1], d_out[:n1], d_st[:n1],
+                                       1, stream=stream) == 0
+        ev[3].record(stream)
+        # warm-up batches, then the timed ones
+        assert m.access_device_batches(d_ops[:8 * BATCH], d_ak[:8 * BATCH], d_av[:8 * BATCH],
+                                       d_out[:8 * BATCH], d_st[:8 * BATCH], BATCH,
+                                       stream=stream) == 0
+        ev[4].record(stream)
+        assert m.access_device_batches(d_ops, d_ak, d_av, d_out, d_st, BATCH, stream=stream) == 0
+        ev[5].record(stream)
+        ev[5].synchronize()
+        assert m.sync() == 0
+        assert bool(d_st.all()), "every accessed key is present"
+        info = m.info()
+        rows.append({"sealed": sealed, "page_bytes": info["page_bytes"],
+                     "init_ms": round(ev[0].elapsed_time(ev[1]), 2),
+                     "w1_us_per_access": round(ev[2].elapsed_time(ev[3]) * 1e3 / n1, 2),
+                     "batched_accesses_per_s": round(n_ops / (ev[4].elapsed_time(ev[5]) * 1e-3), 1)})
+        print(json.dumps(rows[-1]), flush=True)
+        m.close()
+        torch.cuda.empty_cache()
+    line = {"metric": "accesses/s and build time, plain vs sealed pages", "unit": "accesses/s",
+            "n_gpus": 1, "data": "synthetic (device-generated keys and values)",
+            "config": {"workload": f"N=2^{args.log_n} x 32 B, uniform 50/50 GET/PUT on present "
+                                   f"keys, {n_ops} accesses in batches of {BATCH}"},
+            "rows": rows,
+            "sealed_vs_plain": round(rows[1]["batched_accesses_per_s"] /
+                                     rows[0]["batched_accesses_per_s"], 4)}
+    print(json.dumps(line), flush=True)
+
+
 def make_records_vb(n: int, vb: int, seed: int):
     keys = np.empty(n, dtype=np.uint64)
     for lo in range(0, n, 1 << 24):
@@ -1144,13 +1219,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("bolt", "reference"), default="bolt")
     ap.add_argument("--config", choices=("headline", "zipf", "w1", "serve", "big", "paper",
-                                         "validate", "scaling"),
+                                         "validate", "scaling", "integrity"),
                     default="headline",
                     help="headline: the JSON line above; zipf: batch-width sweep on the "
                          "skewed 2^24 x 64 B map; w1: one access per call vs batches of 4096; "
                          "serve: 64 maps behind the continuous-batching server; big: the "
                          "2^30 x 64 B map under a 16 GB budget; paper: the paper's 10^6 x "
-                         "(4 B key, 8 B value) workload, one op per call")
+                         "(4 B key, 8 B value) workload, one op per call; integrity: plain "
+                         "vs sealed pages on the headline map")
     ap.add_argument("--big-log-n", type=int, default=30)
     ap.add_argument("--width", type=int, default=4096,
                     help="batch width of --config validate")
@@ -1182,6 +1258,8 @@ def main():
         run_validate(args)
     elif args.config == "scaling":
         run_scaling(args)
+    elif args.config == "integrity":
+        run_integrity(args)
     elif args.config != "headline":
         run_sweep(args)
     else:

@@ -57,6 +57,8 @@ typedef struct bolt bolt_t;
 #define BOLT_E_DUPKEY -5   /* bolt_init keys are not unique (Sec. 2.1) */
 #define BOLT_E_CUDA -6     /* a CUDA runtime call failed */
 #define BOLT_E_TIMEOUT -7  /* a bounded device wait gave up */
+#define BOLT_E_INTEGRITY -8 /* a host page failed its tag (BOLT_PARAM_INTEGRITY):
+                               altered or replayed; handle poisoned */
 #define BOLT_E_INTERNAL -9 /* an internal consistency check failed */
 
 /* operation codes (Sec. 2.1; Delete is the paper's tombstone Put) */
@@ -96,6 +98,21 @@ typedef struct bolt bolt_t;
                                the host (default); 0 = the multi-kernel chain
                                of larger batches for every batch.  Results,
                                pages and trace are the same for both */
+#define BOLT_PARAM_INTEGRITY 14 /* 1 = seal every host page with ChaCha20-Poly1305
+                                    (RFC 8439 Sec. 2.8; the per-chunk authenticated
+                                    encryption of the paper's appendix on TEE
+                                    integrity): ciphertext from key-stream block 1,
+                                    a 16-byte tag over it and its length in the
+                                    page's last 16 bytes, nonce (page, version).
+                                    The versions stay in HBM, so a replayed older
+                                    page fails its tag as an altered one does.  A
+                                    page that fails is read as empty and the call
+                                    returns BOLT_E_INTEGRITY (handle poisoned until
+                                    bolt_init).  page_bytes grows by 16 (before the
+                                    64-byte rounding); re-plans the map (like
+                                    BOLT_PARAM_C).  Not with BOLT_PARAM_LOOKAHEAD
+                                    (BOLT_E_ARG): pages read ahead are not checked.
+                                    Default 0. */
 #define BOLT_PARAM_SPIN_LIMIT 12 /* iterations (of a ~256 ns sleep) a bounded device wait
                                     spins before it gives up, 0..2^22 (default 2^22,
                                     about one second): the build's grid barrier between
@@ -317,6 +334,15 @@ BOLT_API int bolt_get_stats(bolt_t* h, bolt_stats_t* out);
  * (ciphertext, page_bytes each) into dst (host). */
 BOLT_API int bolt_read_pages(bolt_t* h, uint64_t first, uint64_t count, void* dst);
 
+/* bolt_write_pages -- overwrite `count` host pages starting at page `first`
+ * with src (host, page_bytes each), after the handle's work in flight ends.
+ * The page store is the untrusted host's memory (Sec. 2.2 threat model):
+ * this is the host's own move, not a trusted update -- a page changed or
+ * replayed here decrypts to garbage, or, with BOLT_PARAM_INTEGRITY, fails
+ * its tag on its next read (BOLT_E_INTEGRITY).  Errors: BOLT_E_ARG,
+ * BOLT_E_CUDA. */
+BOLT_API int bolt_write_pages(bolt_t* h, uint64_t first, uint64_t count, const void* src);
+
 /* bolt_read_trace -- copy up to `cap` trace entries into dst (host) and
  * clear the trace; *len receives the number copied.  Entry encoding: page
  * number in bits 0-30, bit 31 set for a write. */
@@ -337,7 +363,7 @@ BOLT_API int bolt_read_rowcounts(bolt_t* h, uint8_t* dst);
  *  10 key check: bitonic global steps    11 key check: bitonic in-tile steps
  *  12 access: written pages copied to the host (side stream)
  *  13 access: lookahead position-map search + page reads (side stream)
- *  14 (unused: the search runs in class 6) 15 access: distinct pages + trace
+ *  14 build: host records grouped by page  15 access: distinct pages + trace
  *  16 access: find_remove + semantics    17 access: P2C remap
  *  18 access: PRF pairs, rows, grouping keys
  * ms[c] sums the event-timed durations of the spans[c] launches (or phases)

@@ -18,17 +18,18 @@ LIB_PATH = os.path.join(HERE, "libbolt.so")
 
 BOLT_OK, BOLT_E_ARG, BOLT_E_NOMEM, BOLT_E_OVERFLOW = 0, -1, -2, -3
 BOLT_E_STATE, BOLT_E_DUPKEY, BOLT_E_CUDA, BOLT_E_TIMEOUT, BOLT_E_INTERNAL = -4, -5, -6, -7, -9
+BOLT_E_INTEGRITY = -8
 BOLT_GET, BOLT_PUT, BOLT_DEL = 0, 1, 2
 BOLT_MAX_BATCH = 65536
 BOLT_NOALLOC_SCRATCH_BYTES = 7340800
 BOLT_PARAM_ALPHA, BOLT_PARAM_C, BOLT_PARAM_TRACE, BOLT_PARAM_BATCH = 1, 2, 4, 5
 BOLT_PARAM_TRACE_CAP, BOLT_PARAM_CHECK_KEYS, BOLT_PARAM_PROFILE = 6, 7, 8
 BOLT_PARAM_BATCH_CAP, BOLT_PARAM_LOOKAHEAD, BOLT_PARAM_DEFER_FLUSH = 9, 10, 11
-BOLT_PARAM_SPIN_LIMIT, BOLT_PARAM_FUSED = 12, 13
+BOLT_PARAM_SPIN_LIMIT, BOLT_PARAM_FUSED, BOLT_PARAM_INTEGRITY = 12, 13, 14
 BOLT_PROF_CLASSES = 19
 PROF_NAMES = ("sort_global", "sort_tile", "page_build", "p2c_rounds", "key_check",
               "access_batch", "gather", "evict", "build", "group", "ksort_global",
-              "ksort_tile", "flush", "ahead", "lookup", "pages", "find_exec", "remap",
+              "ksort_tile", "flush", "ahead", "page_group", "pages", "find_exec", "remap",
               "stage")
 
 if not os.path.exists(LIB_PATH):
@@ -115,6 +116,7 @@ _SIGS = {
     "bolt_get_info": ([_P, ctypes.POINTER(bolt_info_t)], _i),
     "bolt_get_stats": ([_P, ctypes.POINTER(bolt_stats_t)], _i),
     "bolt_read_pages": ([_P, _u64, _u64, _P], _i),
+    "bolt_write_pages": ([_P, _u64, _u64, _P], _i),
     "bolt_read_trace": ([_P, _P, _u64, ctypes.POINTER(_u64)], _i),
     "bolt_read_loads": ([_P, _P], _i),
     "bolt_read_rowcounts": ([_P, _P], _i),
@@ -173,7 +175,8 @@ class BoltMap:
     """One oblivious map handle (owns its device state and pinned pages)."""
 
     def __init__(self, N: int, val_bytes: int, hbm_budget: int = 2**64 - 1, alpha=None,
-                 c=None, trace: bool = False, batch=None, check_keys=None, key_bytes: int = 8):
+                 c=None, trace: bool = False, batch=None, check_keys=None, key_bytes: int = 8,
+                 integrity: bool = False):
         self._h = ctypes.c_void_p()
         _check(bolt_create(N, key_bytes, val_bytes, hbm_budget, ctypes.byref(self._h)),
                "bolt_create")
@@ -182,6 +185,8 @@ class BoltMap:
         self._kdt = np.uint32 if key_bytes == 4 else np.uint64
         if c is not None:
             self.set_param(BOLT_PARAM_C, c)
+        if integrity:
+            self.set_param(BOLT_PARAM_INTEGRITY, 1)
         if alpha is not None:
             self.set_param(BOLT_PARAM_ALPHA, alpha)
         if trace:
@@ -335,6 +340,15 @@ class BoltMap:
         out = np.zeros((count, i["page_bytes"]), dtype=np.uint8)
         _check(bolt_read_pages(self._h, first, count, _np_ptr(out)), "bolt_read_pages")
         return out
+
+    def write_pages(self, first: int, pages: np.ndarray):
+        """Overwrite host pages (the untrusted host's own move)."""
+        pages = np.ascontiguousarray(pages, dtype=np.uint8)
+        i = self.info()
+        if pages.ndim != 2 or pages.shape[1] != i["page_bytes"]:
+            raise ValueError("pages must be (count, page_bytes) bytes")
+        _check(bolt_write_pages(self._h, first, pages.shape[0], _np_ptr(pages)),
+               "bolt_write_pages")
 
     def trace(self, cap: int = 1 << 24) -> np.ndarray:
         out = np.zeros(cap, dtype=np.uint32)

@@ -550,22 +550,53 @@ __device__ __forceinline__ uint32_t prev_written(const BatchDev& b, uint32_t q) 
 enum : int { SRC_NONE = 0, SRC_HOST = 1, SRC_PREV = 2, SRC_PLAIN = 3 };
 
 // the rest of a page whose first 16 bytes per lane are in `first`: decrypt
-// (unless already plaintext) into the slot's buffer
+// (unless already plaintext) into the slot's buffer.  A sealed page (integrity
+// on) is opened as the AEAD of RFC 8439 Sec. 2.8: Poly1305 over its
+// ciphertext and lengths block, checked against the tag in its last 16
+// bytes; on a mismatch (the host altered or replayed the page) the slot gets
+// an empty page and ERR_INTEGRITY is raised, so nothing of the altered page
+// enters the map.  All 32 lanes call; SEALED = m.integrity.
+template <bool SEALED>
 __device__ __forceinline__ void page_in(const MapDev& m, const BatchDev& b, uint32_t slot,
                                         uint64_t q, int kind, const uint8_t* src, uint4 first,
                                         int lane) {
   uint8_t* dst = b.dbuf + (uint64_t)slot * m.page_bytes;
   const uint64_t v = kind == SRC_PLAIN ? 0 : m.version[q];
+  const uint32_t L = m.page_bytes - (SEALED ? 16u : 0u);
+  const uint32_t sealed = (SEALED && kind != SRC_PLAIN) ? 1u : 0u;
+  PolyWarp pw;
+  if (SEALED && sealed) pw = poly_begin(m, q, v);
+  uint4 stored = make_uint4(0, 0, 0, 0);
   for (uint32_t c = 0; c < m.page_bytes; c += 512) {
     const uint32_t off = c + 16 * lane;
     uint4 x = first;
     if (c > 0 && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
     if (kind != SRC_PLAIN) {
-      const uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)v,
-                                   (uint32_t)(v >> 32));
+      if (SEALED && sealed) {
+        if (off < L) {
+          poly_block(pw, off / 16, x);
+        } else if (off == L) {
+          stored = x;
+          poly_block(pw, off / 16, poly_lengths(L));
+        }
+      }
+      const uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2) + sealed, (uint32_t)q,
+                                   (uint32_t)v, (uint32_t)(v >> 32));
       x.x ^= ks.x; x.y ^= ks.y; x.z ^= ks.z; x.w ^= ks.w;
     }
-    if (off < m.page_bytes) *reinterpret_cast<uint4*>(dst + off) = x;
+    if (off < L) *reinterpret_cast<uint4*>(dst + off) = x;
+    else if (off < m.page_bytes) *reinterpret_cast<uint4*>(dst + off) = make_uint4(0, 0, 0, 0);
+  }
+  if (SEALED && sealed) {
+    const uint4 tag = poly_finish(pw, L / 16 + 1);
+    const bool bad = lane == (int)((L / 16) & 31) &&
+                     (tag.x != stored.x || tag.y != stored.y || tag.z != stored.z ||
+                      tag.w != stored.w);
+    if (__any_sync(0xffffffffu, bad)) {
+      if (lane == 0) set_err(m, ERR_INTEGRITY);
+      for (uint32_t off = 16 * lane; off < m.page_bytes; off += 512)
+        *reinterpret_cast<uint4*>(dst + off) = make_uint4(0, 0, 0, 0);
+    }
   }
   if (lane == 0) b.removed[slot] = 0;
 }
@@ -601,8 +632,9 @@ __device__ __forceinline__ void prefetch_eviction(const MapDev& m, uint32_t q, b
   }
 }
 
+template <bool SEALED>
 __device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, uint32_t i,
-                                          int lane, bool prefetch = false) {
+                                          int lane) {
   uint32_t found = NONE32;
   uint64_t fb = 0;
   if (b.leader[i] == i) {
@@ -676,9 +708,6 @@ __device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, ui
     if (kind[k] != SRC_NONE && 16 * lane < m.page_bytes)
       x[k] = *reinterpret_cast<const uint4*>(src[k] + 16 * lane);
   }
-  if (prefetch)
-#pragma unroll
-    for (int k = 0; k < 2; k++) prefetch_eviction(m, qs[k], kind[k] != SRC_NONE, lane);
   if (!b.la_on) {
 #pragma unroll
     for (int k = 0; k < 2; k++) {
@@ -693,7 +722,7 @@ __device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, ui
   }
 #pragma unroll
   for (int k = 0; k < 2; k++)
-    if (kind[k] != SRC_NONE) page_in(m, b, sl[k], qs[k], kind[k], src[k], x[k], lane);
+    if (kind[k] != SRC_NONE) page_in<SEALED>(m, b, sl[k], qs[k], kind[k], src[k], x[k], lane);
 }
 
 // ops over at most LOOKUP_BLOCKS_PER_SM blocks per SM: a warp waiting on host
@@ -701,11 +730,12 @@ __device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, ui
 // kernels on another stream) must still find room beside it
 constexpr uint32_t LOOKUP_BLOCKS_PER_SM = 2;
 
+template <bool SEALED>
 __global__ void __launch_bounds__(256) k_lookup(MapDev m, BatchDev b, uint32_t n) {
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw)
-    lookup_op(m, b, i, lane);
+    lookup_op<SEALED>(m, b, i, lane);
   dep_trigger();
 }
 
@@ -865,6 +895,7 @@ __device__ __forceinline__ void exec_op(const MapDev& m, const BatchDev& b, uint
 // The ciphertext goes to the page's slot in dbuf (the next batch reads it
 // there while the host copy is in flight) and, with to_host, also straight
 // to the host page.
+template <bool SEALED>
 __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, uint32_t e,
                                           uint8_t* plain, bool to_host) {
   const int lane = threadIdx.x & 31;
@@ -926,7 +957,7 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
   // the old plaintext in dbuf is no longer read: the ciphertext replaces it
   // and k_flush copies it to the host page (or this warp does, below)
   uint8_t* cipher = b.dbuf + (uint64_t)d * m.page_bytes;
-  page_encrypt_to(m, plain, cipher, q, ver);
+  page_encrypt_to<SEALED>(m, plain, cipher, q, ver);
   if (to_host)  // each lane stores the 16-byte pieces it encrypted
     for (uint32_t o = 16 * lane; o < m.page_bytes; o += 512)
       *reinterpret_cast<uint4*>(m.pages + q * m.page_bytes + o) =
@@ -955,12 +986,13 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
 }
 
 // warp per page of the batch (block `block` of the eviction blocks)
+template <bool SEALED>
 __device__ __forceinline__ void evict_page(const MapDev& m, const BatchDev& b, uint32_t block,
                                            uint8_t* sbuf) {
   const int wid = threadIdx.x >> 5;
   const uint32_t e = block * (blockDim.x >> 5) + wid;
   if (e >= *b.dcount) return;
-  evict_one(m, b, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), false);
+  evict_one<SEALED>(m, b, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), false);
 }
 
 // The first blocks run the ops' semantics (thread per op) and, when the
@@ -970,13 +1002,14 @@ __device__ __forceinline__ void evict_page(const MapDev& m, const BatchDev& b, u
 // count, so the two run side by side.
 constexpr uint32_t EVICT_WARPS_PER_BLOCK = 4;
 
+template <bool SEALED>
 __global__ void __launch_bounds__(EVICT_WARPS_PER_BLOCK * 32)
     k_exec_evict(MapDev m, BatchDev b, uint32_t n, uint32_t evict_blocks, int decide) {
   extern __shared__ __align__(16) uint8_t sbuf[];
   dep_wait();
   const uint32_t exec_blocks = gridDim.x - evict_blocks;
   if (blockIdx.x >= exec_blocks) {
-    evict_page(m, b, blockIdx.x - exec_blocks, sbuf);
+    evict_page<SEALED>(m, b, blockIdx.x - exec_blocks, sbuf);
     return;
   }
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1007,8 +1040,11 @@ __device__ __forceinline__ unsigned long long ring_take(const MapDev& m, bool ta
   return take ? base + __popc(mask & ((1u << lane) - 1u)) : ~0ull;
 }
 
+// (rev_slot: the entry of the destination page's reverse-index list this
+// item takes, already counted; NONE32 to count it here)
 __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, uint32_t i,
-                                            uint32_t dest, unsigned long long pos) {
+                                            uint32_t dest, unsigned long long pos,
+                                            uint32_t rev_slot = NONE32) {
   const uint64_t pr = b.rpair[i];
   const uint32_t which = dest == (uint32_t)(pr >> 32) ? 1u : 0u;
   if (pos >= m.ring_ctr[1]) {
@@ -1046,7 +1082,7 @@ __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, 
   m.vs_live[vs] = 1;
   if (!hbm) {
     const uint64_t q = dest - m.K;
-    const uint32_t r = byte_inc(m.revcnt, q);
+    const uint32_t r = rev_slot != NONE32 ? rev_slot : byte_inc(m.revcnt, q);
     if (r >= m.lmax) {
       set_err(m, ERR_REV);
       return;
@@ -1060,20 +1096,31 @@ __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, 
 // key), take a ring slot, write its entries.  All 32 lanes of the warp call.
 __device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& b, uint32_t i,
                                                bool go) {
-  uint32_t dest = 0, new_load = 0;
+  // the bin's load, the row's count (a new key), the destination page's
+  // reverse-index count (a host bin) and the free-ring position are taken
+  // together (independent atomics in flight at once), then checked; a count
+  // that ran over poisons the map (Sec. 3.3), so what else was taken then no
+  // longer matters
+  uint32_t dest = 0, new_load = 0, row_old = 0, rev_slot = NONE32;
+  bool fresh = false;
   if (go) {
     dest = b.rdest[i];
+    fresh = b.hit[i] == NONE32;
     new_load = byte_inc(m.load, dest) + 1;
+    if (fresh) row_old = byte_inc(m.rowcnt, b.rrow[i]);
+    if (dest >= m.K) rev_slot = byte_inc(m.revcnt, dest - m.K);
+  }
+  const unsigned long long pos = ring_take(m, go);
+  if (go) {
     if (new_load > m.lmax) {
       set_err(m, ERR_LOAD);
       go = false;
-    } else if (b.hit[i] == NONE32 && byte_inc(m.rowcnt, b.rrow[i]) + 1 > m.R) {
+    } else if (fresh && row_old + 1 > m.R) {
       set_err(m, ERR_ROW);
       go = false;
     }
   }
-  const unsigned long long pos = ring_take(m, go);
-  if (go) remap_place(m, b, i, dest, pos);
+  if (go) remap_place(m, b, i, dest, pos, rev_slot);
   stat_place(m, go, dest < m.K, new_load);
 }
 
@@ -1252,6 +1299,10 @@ __global__ void k_clear_keys(BatchDev b, uint32_t n) {
 // this kernel (no separate write-back launch): a caller issuing one
 // operation at a time pays one launch per operation.
 constexpr uint32_t FUSED_THREADS = 512;
+// the page table of a batch of <= FUSED_MAX_OPS ops: 4 x 2^ceil(log2 n)
+// entries, at least 256 (the runtime's sizing)
+constexpr uint32_t FUSED_TABLE = 256;
+static_assert(4 * FUSED_MAX_OPS <= FUSED_TABLE, "a small batch's page table fits the shared copy");
 
 // the P2C decision of op i on round-start counts read from L2: the counts
 // change by atomics between the rounds of this one launch
@@ -1278,11 +1329,17 @@ __device__ __forceinline__ void decide_op_l2(const MapDev& m, const BatchDev& b,
   }
 }
 
+template <bool SEALED>
 __global__ void __launch_bounds__(FUSED_THREADS)
     k_fused(MapDev m, BatchDev b, uint32_t n, uint64_t t0, uint32_t evict_warps) {
   extern __shared__ __align__(16) uint8_t sbuf[];
+  // the batch's read positions' host pages, their table slots, and a copy of
+  // the (empty) page table to insert the distinct pages into
+  __shared__ uint32_t s_posq[2 * FUSED_MAX_OPS], s_slot[2 * FUSED_MAX_OPS];
+  __shared__ uint32_t s_ht[FUSED_TABLE];
   const int lane = threadIdx.x & 31;
   const uint32_t wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (uint32_t h = threadIdx.x; h < FUSED_TABLE; h += blockDim.x) s_ht[h] = NONE32;
   // 1. per op the DUMMY pair, the REMAP pair and the position-map rows (one
   //    ChaCha20 block each); warp 3 groups the ops by key with n^2 compares:
   //    leader = first op on the key, previous writer of each op, last writer
@@ -1343,8 +1400,94 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     }
   }
   __syncthreads();
-  // 2. position-map search and page reads (warp per op)
-  for (uint32_t i = wid; i < n; i += nwarps) lookup_op(m, b, i, lane, true);
+  // 2. position-map search (warp per op): a hit reads its stored pair, every
+  //    other op its DUMMY pair; the host bins of each read position
+  for (uint32_t i = wid; i < n; i += nwarps) {
+    uint32_t found = NONE32;
+    uint64_t fb = 0;
+    if (b.leader[i] == i) found = pm_search(m, b, i, b.keys[i], lane, &fb);
+    const uint64_t pr = found != NONE32 ? fb : b.pair[i];
+    if (lane == 0) {
+      b.hit[i] = found;
+      if (found != NONE32) b.pair[i] = pr;
+    }
+    if (lane < 2) {
+      const uint32_t p = lane == 0 ? (uint32_t)pr : (uint32_t)(pr >> 32);
+      s_posq[2 * i + lane] = p >= m.K ? (uint32_t)(p - m.K) : NONE32;
+    }
+  }
+  __syncthreads();
+  // 2b. warp 0: the batch's page table -- each distinct page once, at the
+  //     slot linear probing gives it (inserted into a shared-memory copy of
+  //     the empty table), its first read position, the page list -- written
+  //     to the global table with plain stores
+  if (wid == 0) {
+    const uint32_t np = 2 * n;
+    uint32_t q[2], f[2];
+    bool valid[2], first[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const uint32_t p = lane + 32 * k;
+      q[k] = p < np ? s_posq[p] : NONE32;
+      valid[k] = q[k] != NONE32;
+      f[k] = p;
+      if (valid[k])
+        for (uint32_t j = 0; j < p; j++)
+          if (s_posq[j] == q[k]) {
+            f[k] = j;
+            break;
+          }
+      first[k] = valid[k] && f[k] == p;
+      if (first[k]) {
+        uint32_t h = ht_hash(q[k], b.ht_mask);
+        while (atomicCAS(&s_ht[h], NONE32, q[k]) != NONE32) h = (h + 1) & b.ht_mask;
+        s_slot[p] = h;
+      }
+    }
+    __syncwarp();
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t bf0 = __ballot_sync(0xffffffffu, first[0]);
+    const uint32_t bf1 = __ballot_sync(0xffffffffu, first[1]);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const uint32_t p = lane + 32 * k;
+      if (p >= np) continue;
+      b.pos_page[p] = q[k];
+      if (!valid[k]) continue;
+      const uint32_t h = s_slot[f[k]];
+      b.pos_slot[p] = h;
+      if (first[k]) {
+        const uint32_t d = k == 0 ? __popc(bf0 & below) : __popc(bf0) + __popc(bf1 & below);
+        b.ht_key[h] = q[k];
+        b.ht_min[h] = p;
+        b.dslot[d] = h;
+        b.dpage[d] = q[k];
+      }
+    }
+    if (lane == 0) *b.dcount = __popc(bf0) + __popc(bf1);
+  }
+  __syncthreads();
+  // 2c. warp per distinct page: read it (the previous batch's ciphertext if
+  //     that batch wrote it, else the host page) and decrypt it into its
+  //     slot's buffer; meanwhile bring its eviction's data into L2
+  {
+    const uint32_t nd = *b.dcount;
+    for (uint32_t d = wid; d < nd; d += nwarps) {
+      const uint32_t q = b.dpage[d], h = b.dslot[d];
+      const uint8_t* src = m.pages + (uint64_t)q * m.page_bytes;
+      uint4 x = make_uint4(0, 0, 0, 0);
+      if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + 16 * lane);
+      prefetch_eviction(m, q, true, lane);
+      int kind = SRC_HOST;
+      const uint32_t pd = prev_written(b, q);
+      if (pd != NONE32) {
+        kind = SRC_PREV;
+        src = b.prev_dbuf + (uint64_t)pd * m.page_bytes;
+        if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + 16 * lane);
+      }
+      page_in<SEALED>(m, b, h, q, kind, src, x, lane);
+    }
+  }
   __syncthreads();
   // 3. the host-access trace (every read position in order, then each
   //    distinct page once as a write); the previous batch's table is cleared
@@ -1384,7 +1527,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   } else if (wid < evict_warps) {
     const uint32_t nd = *b.dcount;
     for (uint32_t e = wid; e < nd; e += evict_warps)
-      evict_one(m, b, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), true);
+      evict_one<SEALED>(m, b, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), true);
   }
   __syncthreads();
   // 6. P2C remap in rounds of W_r op slots (warp 0, lane per op): decide on
@@ -1402,27 +1545,33 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   }
   __syncthreads();
   if (b.h_out) {
-    // results and the error word back to the caller's pinned staging
+    // results and the error word back to the caller's pinned staging, then
+    // the completion word the caller waits for (every thread's writes are
+    // fenced at system scope before it)
     const uint32_t words = (n * (m.vb + 1) + 15) / 16;
     for (uint32_t w = threadIdx.x; w < words; w += blockDim.x)
       reinterpret_cast<uint4*>(b.h_out)[w] = reinterpret_cast<const uint4*>(b.vout)[w];
     if (threadIdx.x == 0) *b.h_err = *(volatile uint32_t*)m.err;
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0 && b.h_done) *(volatile uint32_t*)b.h_done = b.done_seq;
   }
 }
 
 cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
                          cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  if (n > FUSED_MAX_OPS) return cudaErrorInvalidValue;
+  if (n > FUSED_MAX_OPS || b.ht_mask + 1 != FUSED_TABLE) return cudaErrorInvalidValue;
   ProfSpan whole(P_ACCESS, st);
   const uint32_t per_warp = m.page_bytes + 32 * 16;
   uint32_t ew = (200u << 10) / per_warp;
   // (the last warp runs the ops' semantics meanwhile)
   ew = ew < 1 ? 1 : (ew > FUSED_THREADS / 32 - 1 ? FUSED_THREADS / 32 - 1 : ew);
   const size_t smem = (size_t)ew * per_warp;
-  cudaError_t e = raise_smem_limit((const void*)k_fused, smem);
+  auto kf = m.integrity ? k_fused<true> : k_fused<false>;
+  cudaError_t e = raise_smem_limit((const void*)kf, smem);
   if (e != cudaSuccess) return e;
-  k_fused<<<1, FUSED_THREADS, smem, st>>>(m, b, n, t0, ew);
+  kf<<<1, FUSED_THREADS, smem, st>>>(m, b, n, t0, ew);
   count_launch();
   return cudaGetLastError();
 }
@@ -1494,7 +1643,8 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
     // position-map search fused with the page reads
     ProfSpan ps(P_GATHER, st);
     const uint32_t lb = LOOKUP_BLOCKS_PER_SM * (uint32_t)num_sms();
-    k_lookup<<<warp_blocks < lb ? warp_blocks : lb, 256, 0, st>>>(m, b, n);
+    auto kl = m.integrity ? k_lookup<true> : k_lookup<false>;
+    kl<<<warp_blocks < lb ? warp_blocks : lb, 256, 0, st>>>(m, b, n);
     count_launch();
   }
   if (m.trace_on) {
@@ -1540,11 +1690,12 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
     ProfSpan ps(P_EVICT, st);
     const uint32_t wpb = EVICT_WARPS_PER_BLOCK;
     const size_t smem = (size_t)wpb * (m.page_bytes + 32 * 16);
-    e = raise_smem_limit((const void*)k_exec_evict, smem);
+    auto kx = m.integrity ? k_exec_evict<true> : k_exec_evict<false>;
+    e = raise_smem_limit((const void*)kx, smem);
     if (e != cudaSuccess) return e;
     const uint32_t evict_blocks = (2 * n + wpb - 1) / wpb;
     const uint32_t exec_blocks = (n + wpb * 32 - 1) / (wpb * 32);
-    e = launch_dependent(k_exec_evict, evict_blocks + exec_blocks, wpb * 32, smem, st, m, b, n,
+    e = launch_dependent(kx, evict_blocks + exec_blocks, wpb * 32, smem, st, m, b, n,
                          evict_blocks, fused_decide);
     if (e != cudaSuccess) return e;
     count_launch();

@@ -88,6 +88,8 @@ struct BatchDev {
   const uint8_t* h_in;
   uint8_t* h_out;
   uint32_t* h_err;
+  uint32_t* h_done;    // then done_seq is written here, after everything else
+  uint32_t done_seq, pad4;
 };
 
 cudaError_t sort_batch_keys(uint64_t* keys, uint32_t n_pow2, cudaStream_t st);

@@ -24,6 +24,7 @@ enum : uint32_t {
   ERR_NOTFOUND = 1u << 4,  // a position-map hit was not found where it points
   ERR_PAGE = 1u << 5,      // a page held more than lmax tuples
   ERR_TIMEOUT = 1u << 6,   // a bounded device wait gave up
+  ERR_INTEGRITY = 1u << 7, // a page read from the host failed its tag
   ERR_OVERFLOW_MASK = ERR_LOAD | ERR_ROW | ERR_VS | ERR_REV | ERR_PAGE,
 };
 
@@ -70,7 +71,8 @@ struct MapDev {
   uint32_t* trace;     // host-access trace (optional)
   unsigned long long* trace_len;
   uint64_t trace_cap;
-  uint32_t trace_on, pad1;
+  uint32_t trace_on;
+  uint32_t integrity;  // 1: pages are ChaCha20-Poly1305 sealed (tag in the last 16 bytes)
 };
 
 // ---------------------------------------------------------------------------
@@ -276,9 +278,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* sh, ui
 }
 
 // --- warp-level ordering of up to 32 (key, source) items ------------------
-// ascending by key; lanes without an item carry src NONE32 (and key ~0) and
-// sort after every item, an item whose key is ~0 included: the order is on
-// (key, src == NONE32)
+// ascending on (key, src): lanes without an item carry src NONE32 (and key
+// ~0) and sort after every item, an item whose key is ~0 included; equal
+// keys (only with duplicate keys) go in source order, so the result never
+// depends on the order the items arrived in
 __device__ __forceinline__ void warp_sort_by_key(uint64_t& key, uint32_t& src) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -289,9 +292,8 @@ __device__ __forceinline__ void warp_sort_by_key(uint64_t& key, uint32_t& src) {
       uint32_t os = __shfl_xor_sync(0xffffffffu, src, j);
       bool asc = (lane & k) == 0;
       bool lower = (lane & j) == 0;
-      const bool mine_empty = src == NONE32, other_empty = os == NONE32;
-      const bool o_less = ok < key || (ok == key && !other_empty && mine_empty);
-      const bool o_greater = ok > key || (ok == key && other_empty && !mine_empty);
+      const bool o_less = ok < key || (ok == key && os < src);
+      const bool o_greater = ok > key || (ok == key && os > src);
       bool take = lower == asc ? o_less : o_greater;
       if (take) {
         key = ok;
@@ -301,28 +303,207 @@ __device__ __forceinline__ void warp_sort_by_key(uint64_t& key, uint32_t& src) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Poly1305 (RFC 8439 Sec. 2.5) over a sealed page, computed by a warp.
+// Numbers mod p = 2^130 - 5 are held in five 26-bit limbs; a product is
+// formed with 64-bit accumulators, the limbs past 2^130 folding back times 5.
+// The page's message blocks are the 16-byte pieces a lane already holds when
+// it encrypts or decrypts (block j = bytes [16j, 16j + 16) sits in lane
+// j mod 32, chunk j / 32), then one block of lengths; the tag
+//   sum_j m_j r^(K - j)  (+ s, mod 2^128),  K blocks,
+// is split per lane: Horner over the lane's own blocks with r^32, times
+// r^(K - last block of the lane), summed over the warp.
+struct P130 {
+  uint32_t l[5];
+};
+
+__device__ __forceinline__ P130 p130_norm(uint64_t d0, uint64_t d1, uint64_t d2, uint64_t d3,
+                                          uint64_t d4) {
+  const uint32_t M26 = (1u << 26) - 1;
+  P130 h;
+  uint64_t c;
+  c = d0 >> 26; h.l[0] = (uint32_t)d0 & M26; d1 += c;
+  c = d1 >> 26; h.l[1] = (uint32_t)d1 & M26; d2 += c;
+  c = d2 >> 26; h.l[2] = (uint32_t)d2 & M26; d3 += c;
+  c = d3 >> 26; h.l[3] = (uint32_t)d3 & M26; d4 += c;
+  c = d4 >> 26; h.l[4] = (uint32_t)d4 & M26;
+  uint64_t t = (uint64_t)h.l[0] + c * 5;
+  h.l[0] = (uint32_t)t & M26;
+  h.l[1] += (uint32_t)(t >> 26);
+  return h;
+}
+
+// a * b mod p, limbs of both below 2^27
+__device__ __forceinline__ P130 p130_mul(const P130& a, const P130& b) {
+  const uint64_t b0 = b.l[0], b1 = b.l[1], b2 = b.l[2], b3 = b.l[3], b4 = b.l[4];
+  const uint64_t s1 = b1 * 5, s2 = b2 * 5, s3 = b3 * 5, s4 = b4 * 5;
+  const uint64_t a0 = a.l[0], a1 = a.l[1], a2 = a.l[2], a3 = a.l[3], a4 = a.l[4];
+  return p130_norm(a0 * b0 + a1 * s4 + a2 * s3 + a3 * s2 + a4 * s1,
+                   a0 * b1 + a1 * b0 + a2 * s4 + a3 * s3 + a4 * s2,
+                   a0 * b2 + a1 * b1 + a2 * b0 + a3 * s4 + a4 * s3,
+                   a0 * b3 + a1 * b2 + a2 * b1 + a3 * b0 + a4 * s4,
+                   a0 * b4 + a1 * b3 + a2 * b2 + a3 * b1 + a4 * b0);
+}
+
+__device__ __forceinline__ P130 p130_add(const P130& a, const P130& b) {
+  return p130_norm((uint64_t)a.l[0] + b.l[0], (uint64_t)a.l[1] + b.l[1],
+                   (uint64_t)a.l[2] + b.l[2], (uint64_t)a.l[3] + b.l[3],
+                   (uint64_t)a.l[4] + b.l[4]);
+}
+
+// a 16-byte message block with the 2^128 bit set
+__device__ __forceinline__ P130 p130_block(uint4 w) {
+  const uint32_t M26 = (1u << 26) - 1;
+  P130 h;
+  h.l[0] = w.x & M26;
+  h.l[1] = ((w.x >> 26) | (w.y << 6)) & M26;
+  h.l[2] = ((w.y >> 20) | (w.z << 12)) & M26;
+  h.l[3] = ((w.z >> 14) | (w.w << 18)) & M26;
+  h.l[4] = (w.w >> 8) | (1u << 24);
+  return h;
+}
+
+__device__ __forceinline__ P130 p130_shfl(const P130& a, int src) {
+  P130 r;
+#pragma unroll
+  for (int i = 0; i < 5; i++) r.l[i] = __shfl_sync(0xffffffffu, a.l[i], src);
+  return r;
+}
+
+// The running state of a warp's Poly1305 over one page (see above).
+struct PolyWarp {
+  P130 acc;     // this lane's Horner sum
+  P130 rpow;    // r^(lane + 1)
+  P130 r32;     // r^32
+  uint4 s;      // the key's second half
+  int last;     // this lane's last block so far, -1 for none
+};
+
+// r and s from the one-time key: the first 32 bytes of the ChaCha20 block 0
+// of (K_enc, page, version); all 32 lanes call
+__device__ __forceinline__ PolyWarp poly_begin(const MapDev& m, uint64_t q, uint64_t version) {
+  const int lane = threadIdx.x & 31;
+  const uint4 ks = chacha_quad(m.kenc, 0, (uint32_t)q, (uint32_t)version,
+                               (uint32_t)(version >> 32));
+  uint4 r, s;
+  r.x = __shfl_sync(0xffffffffu, ks.x, 0); r.y = __shfl_sync(0xffffffffu, ks.y, 0);
+  r.z = __shfl_sync(0xffffffffu, ks.z, 0); r.w = __shfl_sync(0xffffffffu, ks.w, 0);
+  s.x = __shfl_sync(0xffffffffu, ks.x, 1); s.y = __shfl_sync(0xffffffffu, ks.y, 1);
+  s.z = __shfl_sync(0xffffffffu, ks.z, 1); s.w = __shfl_sync(0xffffffffu, ks.w, 1);
+  r.x &= 0x0fffffffu; r.y &= 0x0ffffffcu; r.z &= 0x0ffffffcu; r.w &= 0x0ffffffcu;
+  P130 rr = p130_block(r);
+  rr.l[4] &= (1u << 24) - 1;  // no 2^128 bit: r < 2^124
+  // r^(lane + 1) by an inclusive product scan over the warp
+  P130 x = rr;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const P130 y = p130_shfl(x, lane >= d ? lane - d : lane);
+    if (lane >= d) x = p130_mul(x, y);
+  }
+  PolyWarp w;
+  w.rpow = x;
+  w.r32 = p130_shfl(x, 31);
+  w.s = s;
+  w.last = -1;
+  for (int i = 0; i < 5; i++) w.acc.l[i] = 0;
+  return w;
+}
+
+// block j of the message, held by lane j % 32 (the caller passes only its own)
+__device__ __forceinline__ void poly_block(PolyWarp& w, int j, uint4 blk) {
+  w.acc = w.last < 0 ? p130_block(blk) : p130_add(p130_mul(w.acc, w.r32), p130_block(blk));
+  w.last = j;
+}
+
+// the tag after the K blocks (all lanes call); every lane gets it
+__device__ __forceinline__ uint4 poly_finish(const PolyWarp& w, int K) {
+  // this lane's part: acc * r^(K - last), r^e held by lane e - 1
+  const int e = w.last < 0 ? 1 : K - w.last;
+  const P130 re = p130_shfl(w.rpow, e - 1);
+  P130 part = p130_mul(w.acc, re);
+  if (w.last < 0)
+    for (int i = 0; i < 5; i++) part.l[i] = 0;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) part = p130_add(part, p130_shfl(part, (threadIdx.x & 31) ^ d));
+  // the sum as an exact integer in 32-bit words (limbs below 2^27: value
+  // below 2^131), bits from 2^130 up folded back times 5, then p subtracted
+  // once if still reached (the value is then below 2^130 + 5)
+  uint64_t acc = (uint64_t)part.l[0] + ((uint64_t)part.l[1] << 26);
+  uint32_t v0 = (uint32_t)acc; acc >>= 32;
+  acc += (uint64_t)part.l[2] << 20;
+  uint32_t v1 = (uint32_t)acc; acc >>= 32;
+  acc += (uint64_t)part.l[3] << 14;
+  uint32_t v2 = (uint32_t)acc; acc >>= 32;
+  acc += (uint64_t)part.l[4] << 8;
+  uint32_t v3 = (uint32_t)acc; acc >>= 32;
+  uint32_t v4 = (uint32_t)acc;
+  {
+    uint64_t t = (uint64_t)v0 + 5ull * (v4 >> 2);
+    v4 &= 3;
+    v0 = (uint32_t)t; t >>= 32;
+    t += v1; v1 = (uint32_t)t; t >>= 32;
+    t += v2; v2 = (uint32_t)t; t >>= 32;
+    t += v3; v3 = (uint32_t)t; t >>= 32;
+    v4 += (uint32_t)t;
+  }
+  {
+    // v >= p iff v + 5 reaches 2^130; then v - p = (v + 5) mod 2^130
+    uint64_t t = (uint64_t)v0 + 5;
+    const uint32_t u0 = (uint32_t)t; t >>= 32;
+    t += v1; const uint32_t u1 = (uint32_t)t; t >>= 32;
+    t += v2; const uint32_t u2 = (uint32_t)t; t >>= 32;
+    t += v3; const uint32_t u3 = (uint32_t)t; t >>= 32;
+    const uint32_t u4 = v4 + (uint32_t)t;
+    if (u4 >> 2) {
+      v0 = u0; v1 = u1; v2 = u2; v3 = u3;
+    }
+  }
+  // tag = (v + s) mod 2^128
+  uint64_t t = (uint64_t)v0 + w.s.x;
+  const uint32_t f0 = (uint32_t)t; t >>= 32;
+  t += (uint64_t)v1 + w.s.y;
+  const uint32_t f1 = (uint32_t)t; t >>= 32;
+  t += (uint64_t)v2 + w.s.z;
+  const uint32_t f2 = (uint32_t)t; t >>= 32;
+  t += (uint64_t)v3 + w.s.w;
+  return make_uint4(f0, f1, f2, (uint32_t)t);
+}
+
+// the lengths block of a sealed page: no additional data, L bytes of ciphertext
+__device__ __forceinline__ uint4 poly_lengths(uint32_t L) { return make_uint4(0, 0, L, 0); }
+
 // Encrypt a plaintext page (shared memory) into dst (page_bytes): lane L
 // handles bytes [16L, 16L+16) of each 512-byte chunk; the four lanes of a
-// quad compute the chunk's ChaCha20 block together.
+// quad compute the chunk's ChaCha20 block together.  Sealed pages (integrity
+// on) are the ChaCha20-Poly1305 AEAD of RFC 8439 Sec. 2.8: the first
+// page_bytes - 16 bytes encrypted from block 1, the tag over them and their
+// length in the last 16 bytes.  SEALED = m.integrity (kernels are compiled
+// for both, so the sealing's registers do not weigh on plain pages).
+template <bool SEALED>
 __device__ __forceinline__ void page_encrypt_to(const MapDev& m, const uint8_t* plain,
                                                 uint8_t* dst, uint64_t q, uint64_t version) {
   const int lane = threadIdx.x & 31;
+  constexpr uint32_t sealed = SEALED ? 1u : 0u;
+  const uint32_t L = m.page_bytes - 16 * sealed;
+  PolyWarp pw;
+  if (SEALED) pw = poly_begin(m, q, version);
   for (uint32_t c = 0; c < m.page_bytes; c += 512) {
-    uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2), (uint32_t)q, (uint32_t)version,
+    uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2) + sealed, (uint32_t)q, (uint32_t)version,
                            (uint32_t)(version >> 32));
     uint32_t off = c + 16 * lane;
-    if (off < m.page_bytes) {
+    if (off < L) {
       uint4 p = *reinterpret_cast<const uint4*>(plain + off);
       p.x ^= ks.x; p.y ^= ks.y; p.z ^= ks.z; p.w ^= ks.w;
       *reinterpret_cast<uint4*>(dst + off) = p;
+      if (SEALED) poly_block(pw, off / 16, p);
+    } else if (SEALED && off == L) {
+      poly_block(pw, off / 16, poly_lengths(L));
     }
   }
-}
-
-// ... straight into host page q
-__device__ __forceinline__ void page_encrypt_store(const MapDev& m, const uint8_t* plain,
-                                                   uint64_t q, uint64_t version) {
-  page_encrypt_to(m, plain, m.pages + q * m.page_bytes, q, version);
+  if (SEALED) {
+    const uint4 tag = poly_finish(pw, L / 16 + 1);
+    if (lane == (int)((L / 16) & 31)) *reinterpret_cast<uint4*>(dst + L) = tag;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -344,7 +525,7 @@ enum ProfClass : int {
   P_KSORT_TILE = 11,    // key-uniqueness check: bitonic in-tile steps
   P_FLUSH = 12,         // access: written pages copied to the host
   P_AHEAD = 13,         // access: lookahead search + page reads (side stream)
-  P_LOOKUP = 14,        // (unused: the search is fused with the page reads, P_GATHER)
+  P_PAGE_GROUP = 14,    // build: host records grouped by page (counting scatter)
   P_PAGES = 15,         // access: distinct pages, trace
   P_FINDEXEC = 16,      // access: find_remove + Get/Put/Delete semantics
   P_REMAP = 17,         // access: P2C remap

@@ -277,6 +277,37 @@ __global__ void k_build_tags(MapDev m, const uint32_t* __restrict__ dest, uint64
   }
 }
 
+// Host-bin records grouped by page without a sort: page q's run starts at
+// page_off[q] (the prefix of the page loads the rounds left), and each record
+// takes the next position of its run from a per-page cursor (a copy of
+// page_off).  The order inside a run is the atomics' order; the page build
+// orders every run by (key, record), so no page depends on it.  A record
+// whose bin is out of range (rounds that gave up leave `dest` unwritten) or
+// whose run is already full (loads and destinations disagree) is not
+// written and raises ERR_PAGE.
+__global__ void __launch_bounds__(256) k_build_scatter(MapDev m, const uint32_t* __restrict__ dest,
+                                                       uint64_t n,
+                                                       const uint32_t* __restrict__ page_off,
+                                                       uint32_t* __restrict__ cursor,
+                                                       uint64_t* __restrict__ tags) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t d = dest[i];
+    if (d < m.K) continue;  // an HBM bin: no page
+    if (d >= m.B) {
+      set_err(m, ERR_PAGE);
+      continue;
+    }
+    const uint32_t q = d - (uint32_t)m.K;
+    const uint32_t pos = atomicAdd(cursor + q, 1u);
+    if (pos >= page_off[q + 1]) {
+      set_err(m, ERR_PAGE);
+      continue;
+    }
+    tags[pos] = ((uint64_t)q << 32) | i;
+  }
+}
+
 // --- exclusive prefix sum of the M page loads (u8) -> u32 run starts ------
 constexpr int SCAN_BLOCK = 1024;
 constexpr int SCAN_ITEMS = 8;  // 8192 pages per block
@@ -338,7 +369,8 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_fill(MapDev m, const uint32
 // straight to the host page.
 // Without tags (a data owner's image, records already in bin-major order)
 // page q's run is records run_base[0] + page_off[q] ... of keys / vals, the
-// first n_rec of them being valid.
+// first n_rec of them being valid.  SEALED = m.integrity.
+template <bool SEALED>
 __global__ void k_page_build(MapDev m, const uint64_t* __restrict__ keys,
                              const uint8_t* __restrict__ vals, const uint64_t* __restrict__ tags,
                              const uint32_t* __restrict__ page_off, uint32_t warps_per_block,
@@ -389,8 +421,8 @@ __global__ void k_page_build(MapDev m, const uint64_t* __restrict__ keys,
         reinterpret_cast<uint64_t*>(slot + 8)[w] = vsrc[w];
     }
     __syncwarp();
-    page_encrypt_to(m, plain, out ? out + (q - q0) * m.page_bytes : m.pages + q * m.page_bytes, q,
-                    0);
+    page_encrypt_to<SEALED>(m, plain,
+                            out ? out + (q - q0) * m.page_bytes : m.pages + q * m.page_bytes, q, 0);
     __syncwarp();
   }
 }
@@ -536,7 +568,8 @@ static cudaError_t build_pages(const MapDev& m, const uint64_t* keys, const uint
   uint32_t wpb = (uint32_t)(65536 / m.page_bytes);
   wpb = wpb < 1 ? 1 : wpb > 8 ? 8 : wpb;
   size_t smem = (size_t)wpb * m.page_bytes;
-  cudaError_t e = raise_smem_limit((const void*)k_page_build, smem);
+  auto kp = m.integrity ? k_page_build<true> : k_page_build<false>;
+  cudaError_t e = raise_smem_limit((const void*)kp, smem);
   if (e != cudaSuccess) return e;
   const uint64_t cap = (uint64_t)sms * 32;
   const uint64_t stage_bytes = s.rows4 ? s.cap * sizeof(uint4) : 0;
@@ -545,7 +578,7 @@ static cudaError_t build_pages(const MapDev& m, const uint64_t* keys, const uint
   ProfSpan ps(P_PAGE_BUILD, st);
   if (!staged) {
     const uint64_t blocks = (m.M + wpb - 1) / wpb;
-    k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
+    kp<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
         m, keys, vals, tags, s.page_off, wpb, 0, m.M, nullptr, run_base, n_rec);
     count_launch();
     return cudaGetLastError();
@@ -558,7 +591,7 @@ static cudaError_t build_pages(const MapDev& m, const uint64_t* keys, const uint
     uint8_t* buf = stage + (uint64_t)k * chunk * m.page_bytes;
     if (c >= 2) cudaStreamWaitEvent(st, ev_copied[k], 0);
     const uint64_t blocks = (q1 - q0 + wpb - 1) / wpb;
-    k_page_build<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
+    kp<<<(unsigned)(blocks < cap ? blocks : cap), wpb * 32, smem, st>>>(
         m, keys, vals, tags, s.page_off, wpb, q0, q1, buf, run_base, n_rec);
     count_launch();
     cudaEventRecord(ev_built[k], st);
@@ -638,11 +671,24 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   }
   // 2. page run starts
   scan_page_runs(m, s, st);
-  // 3. tags + bitonic sort
-  k_build_tags<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.tag_cap, s.tags);
-  count_launch();
-  cudaError_t e = sort_tags_u64(s.tags, s.tag_cap, s.log_tile, st);
-  if (e != cudaSuccess) return e;
+  // 3. host records grouped by page: a counting scatter with the per-page
+  // cursors in the rows4 buffer (free between the rounds and the page
+  // staging); without room for them, tags + bitonic sort
+  cudaError_t e;
+  if (s.rows4 && s.cap * sizeof(uint4) >= m.M * sizeof(uint32_t)) {
+    ProfSpan ps(P_PAGE_GROUP, st);
+    uint32_t* cursor = reinterpret_cast<uint32_t*>(s.rows4);
+    e = cudaMemcpyAsync(cursor, s.page_off, m.M * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                        st);
+    if (e != cudaSuccess) return e;
+    k_build_scatter<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.page_off, cursor, s.tags);
+    count_launch();
+  } else {
+    k_build_tags<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.tag_cap, s.tags);
+    count_launch();
+    e = sort_tags_u64(s.tags, s.tag_cap, s.log_tile, st);
+    if (e != cudaSuccess) return e;
+  }
   // The position-map entries and HBM residents (k_build_place) are read by
   // none of the steps that follow, so after the rounds kernel they are
   // written on the side stream beside the page build, which is bound by the

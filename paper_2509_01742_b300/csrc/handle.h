@@ -29,6 +29,7 @@ struct bolt {
   int defer_flush = 0;        // BOLT_PARAM_DEFER_FLUSH: write-back after the next batch's reads
   uint32_t spin_limit = 1u << 22;  // BOLT_PARAM_SPIN_LIMIT: bounded device waits
   bool fused = true;          // BOLT_PARAM_FUSED: batches of <= FUSED_MAX_OPS in one launch
+  bool integrity = false;     // BOLT_PARAM_INTEGRITY: sealed pages (tag checked on read)
   bolt_info_t info{};
 
   bdev::MapDev m{};
@@ -48,6 +49,8 @@ struct bolt {
   uint8_t* h_vout = nullptr;
   uint8_t* h_status = nullptr;
   uint32_t* h_err = nullptr;
+  uint32_t* h_done = nullptr;  // completion word of a one-batch host call (pinned, mapped)
+  uint32_t done_seq = 0;
   ptrdiff_t io_dev_delta = 0;  // device address of the pinned staging minus its host address
   // bolt_access moves chunks of ops through two alternating sets of pinned
   // staging (set 0 is h_ops ... h_status) and device I/O buffers (set 0 is

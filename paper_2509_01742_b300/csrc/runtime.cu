@@ -6,6 +6,8 @@
 // directly), the batch staging buffers, and the error / poison state.  All
 // arithmetic of the method runs in the kernels of build.cu, sort.cu and
 // access.cu; this file only plans, allocates, copies and launches.
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -62,7 +64,9 @@ struct Plan {
 // Claim 3.2: lmax = c + ceil(log2 log2 N) + 1 (constant 1 in the O-term, as
 // in Sec. 3.3); Claims 3.3 / 3.4 with constant 1; position map of
 // ceil(N/16) rows holding 16 + ceil(log2 log2 N / log2 d) keys (Sec. 4.2).
-int plan_sizes(uint64_t N, uint32_t c, double alpha, uint32_t vb, bolt_info_t* o) {
+// A sealed page (integrity on) carries a 16-byte Poly1305 tag after them.
+int plan_sizes(uint64_t N, uint32_t c, double alpha, uint32_t vb, bolt_info_t* o,
+               bool integrity = false) {
   if (N < 64 || c < 1 || alpha < 0.0 || alpha >= 1.0) return BOLT_E_ARG;
   std::memset(o, 0, sizeof *o);
   const double llg = std::log2(std::log2((double)N));
@@ -87,7 +91,7 @@ int plan_sizes(uint64_t N, uint32_t c, double alpha, uint32_t vb, bolt_info_t* o
   o->vs_cap = (uint64_t)std::ceil(o->beta1 + o->beta2) + (N < MAXB ? N : MAXB);
   o->round_width = o->B / 256 > 0 ? o->B / 256 : 1;
   o->rec_bytes = 8 + vb;
-  o->page_bytes = (16 + o->lmax * o->rec_bytes + 63) / 64 * 64;
+  o->page_bytes = (16 + o->lmax * o->rec_bytes + (integrity ? 16 : 0) + 63) / 64 * 64;
   if (o->vs_cap >= (1ull << 29) || o->rows * o->R >= (1ull << 32)) return BOLT_E_ARG;
   return BOLT_OK;
 }
@@ -181,10 +185,11 @@ void destroy_streams(bolt* h) {
 }
 
 int choose_plan(bolt* h, bolt_info_t* o) {
-  if (h->alpha_override >= 0.0) return plan_sizes(h->N, h->c, h->alpha_override, h->vb, o);
+  if (h->alpha_override >= 0.0)
+    return plan_sizes(h->N, h->c, h->alpha_override, h->vb, o, h->integrity);
   static const double grid[] = {0.2, 0.1, 0.05, 0.01, 0.0};
   for (double a : grid) {
-    int rc = plan_sizes(h->N, h->c, a, h->vb, o);
+    int rc = plan_sizes(h->N, h->c, a, h->vb, o, h->integrity);
     if (rc) return rc;
     if ((double)o->vs_cap * (double)(8 + h->vb) <= (double)h->hbm_budget) return BOLT_OK;
   }
@@ -223,6 +228,7 @@ int alloc_state(bolt* h) {
   m.trace_cap = h->trace_cap;
   m.trace_on = h->trace_on ? 1 : 0;
   m.spin_limit = h->spin_limit;
+  m.integrity = h->integrity ? 1 : 0;
   void* hp = nullptr;
   cudaError_t e = cudaHostAlloc(&hp, I.M * I.page_bytes, cudaHostAllocMapped | cudaHostAllocPortable);
   if (e != cudaSuccess) { free_state(h); return BOLT_E_NOMEM; }
@@ -415,6 +421,8 @@ int err_to_rc(uint32_t err) {
   // a wait that gave up first: the steps after it may have flagged the
   // half-built state as well
   if (err & ERR_TIMEOUT) return BOLT_E_TIMEOUT;
+  // an altered page: what the batch did after reading it is void
+  if (err & ERR_INTEGRITY) return BOLT_E_INTEGRITY;
   if (err & ERR_OVERFLOW_MASK) return BOLT_E_OVERFLOW;
   if (err) return BOLT_E_INTERNAL;
   return BOLT_OK;
@@ -785,6 +793,7 @@ const char* bolt_strerror(int code) {
     case BOLT_E_DUPKEY: return "duplicate keys in bolt_init";
     case BOLT_E_CUDA: return "CUDA runtime error";
     case BOLT_E_TIMEOUT: return "bounded device wait timed out";
+    case BOLT_E_INTEGRITY: return "a host page failed its integrity tag (map poisoned until re-init)";
     case BOLT_E_INTERNAL: return "internal consistency check failed";
     default: return "unknown error";
   }
@@ -877,6 +886,8 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   h->h_ops = h->h_io[0].ops;
   h->h_status = h->h_io[0].status;
   h->h_err = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
+  h->h_done = h->h_err + 1;
+  *h->h_done = 0;
   int rc = alloc_state(h);
   if (rc) {
     cudaFreeHost(h->h_keys);
@@ -918,6 +929,7 @@ int bolt_set_param(bolt_t* h, int which, double v) {
       return BOLT_OK;
     case BOLT_PARAM_LOOKAHEAD:
       if (!(v >= 0.0 && v <= 1.0)) return BOLT_E_ARG;
+      if (v > 0.0 && h->integrity) return BOLT_E_ARG;  // ahead reads are not verified
       h->la_frac = v;
       return BOLT_OK;
     case BOLT_PARAM_DEFER_FLUSH:
@@ -928,6 +940,11 @@ int bolt_set_param(bolt_t* h, int which, double v) {
       if (!(v == 0.0 || v == 1.0)) return BOLT_E_ARG;
       h->fused = v != 0.0;
       return BOLT_OK;
+    case BOLT_PARAM_INTEGRITY:
+      if (!(v == 0.0 || v == 1.0)) return BOLT_E_ARG;
+      if (v != 0.0 && h->la_frac > 0.0) return BOLT_E_ARG;
+      h->integrity = v != 0.0;
+      break;
     case BOLT_PARAM_SPIN_LIMIT:
       if (!(v >= 0.0 && v <= (double)(1u << 22))) return BOLT_E_ARG;
       h->spin_limit = (uint32_t)v;
@@ -1170,9 +1187,24 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
     b.h_in = reinterpret_cast<const uint8_t*>(hp.keys) + h->io_dev_delta;
     b.h_out = hp.vout + h->io_dev_delta;
     b.h_err = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->h_err) + h->io_dev_delta);
+    b.h_done = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->h_done) + h->io_dev_delta);
+    b.done_seq = ++h->done_seq;
     cudaError_t e = fused_batch(h, b, (uint32_t)n, h->t, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return BOLT_E_CUDA;
+    // the kernel's completion word (written after its results) ends the wait;
+    // if it has not come within seconds, wait for the stream and let its
+    // error (or the missing word) speak
+    const volatile uint32_t* done = h->h_done;
+    const auto t_wait = std::chrono::steady_clock::now();
+    for (uint32_t spin = 1; *done != b.done_seq; spin++) {
+      if ((spin & 4095) == 0 &&
+          std::chrono::steady_clock::now() - t_wait > std::chrono::seconds(5)) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return BOLT_E_CUDA;
+        if (*done != b.done_seq) return BOLT_E_INTERNAL;
+        break;
+      }
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
     h->t += n;
     h->batches++;
     std::memcpy(vout, hp.vout, n * vb);
@@ -1288,6 +1320,14 @@ int bolt_read_pages(bolt_t* h, uint64_t first, uint64_t count, void* dst) {
     return BOLT_E_ARG;
   if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
   std::memcpy(dst, h->pages_host + first * h->info.page_bytes, count * h->info.page_bytes);
+  return BOLT_OK;
+}
+
+int bolt_write_pages(bolt_t* h, uint64_t first, uint64_t count, const void* src) {
+  if (!h || !h->allocated || !src || first > h->info.M || count > h->info.M - first)
+    return BOLT_E_ARG;
+  if (sync_all(h) != cudaSuccess) return BOLT_E_CUDA;
+  std::memcpy(h->pages_host + first * h->info.page_bytes, src, count * h->info.page_bytes);
   return BOLT_OK;
 }
 

@@ -30,6 +30,10 @@ def test_strerror_and_codes():
     assert b"poisoned" in B.bolt_strerror(B.BOLT_E_OVERFLOW)
     assert (B.BOLT_E_ARG, B.BOLT_E_NOMEM, B.BOLT_E_OVERFLOW, B.BOLT_E_STATE, B.BOLT_E_DUPKEY) == \
         (O.E_ARG, O.E_NOMEM, O.E_OVERFLOW, O.E_STATE, O.E_DUPKEY)
+    # a page that fails its tag (BOLT_PARAM_INTEGRITY) has the oracle's code too
+    assert B.BOLT_E_INTEGRITY == O.E_INTEGRITY
+    assert b"integrity" in B.bolt_strerror(B.BOLT_E_INTEGRITY)
+    assert B.BOLT_PARAM_INTEGRITY == 14
 
 
 @pytest.mark.parametrize("N,vb,alpha,c", [
