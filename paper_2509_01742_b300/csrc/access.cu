@@ -221,9 +221,10 @@ __device__ __forceinline__ uint32_t ht_insert(const BatchDev& b, uint32_t page, 
 // first row with a match, then its first matching slot).  Every slot's
 // metadata, key and bin pair of all four rows are loaded at once -- one
 // memory round trip instead of two per row -- and *bins receives the pair
-// of the matching slot (all lanes).
+// of the matching slot (all lanes), *hmeta (if given) its metadata.
 __device__ __forceinline__ uint32_t pm_search(const MapDev& m, const BatchDev& b, uint32_t i,
-                                              uint64_t key, int lane, uint64_t* bins) {
+                                              uint64_t key, int lane, uint64_t* bins,
+                                              uint32_t* hmeta = nullptr) {
   const uint4 rows = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
   const uint32_t rr[4] = {rows.x, rows.y, rows.z, rows.w};
   const bool in = lane < (int)m.R;
@@ -236,7 +237,7 @@ __device__ __forceinline__ uint32_t pm_search(const MapDev& m, const BatchDev& b
     k[j] = in ? m.pm_key[idx] : 0ull;
     pb[j] = in ? m.pm_bins[idx] : 0ull;
   }
-  uint32_t found = NONE32;
+  uint32_t found = NONE32, fm = 0;
   uint64_t fb = 0;
 #pragma unroll
   for (int j = 3; j >= 0; j--) {  // the lowest matching row wins
@@ -245,9 +246,11 @@ __device__ __forceinline__ uint32_t pm_search(const MapDev& m, const BatchDev& b
       const int s = __ffs(bal) - 1;
       found = (uint32_t)((uint64_t)rr[j] * m.R + s);
       fb = __shfl_sync(0xffffffffu, pb[j], s);
+      fm = __shfl_sync(0xffffffffu, meta[j], s);
     }
   }
   *bins = fb;
+  if (hmeta) *hmeta = fm;
   return found;
 }
 
@@ -616,8 +619,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 
 // While a claimed page's host read is in flight: bring what its eviction will
 // read into L2 -- the reverse-index count and list, then each listed stash
-// item's live flag, key and value (only entries below the count: those past
-// it are stale).  All 32 lanes call.
+// item's live flag, key, map slot and value (only entries below the count:
+// those past it are stale).  All 32 lanes call.
 __device__ __forceinline__ void prefetch_eviction(const MapDev& m, uint32_t q, bool claimed,
                                                   int lane) {
   uint32_t vs = NONE32;
@@ -628,6 +631,7 @@ __device__ __forceinline__ void prefetch_eviction(const MapDev& m, uint32_t q, b
   if (vs != NONE32) {
     prefetch_l2(m.vs_live + vs);
     prefetch_l2(m.vs_key + vs);
+    prefetch_l2(m.vs_pm + vs);
     prefetch_l2(m.vs_val + (uint64_t)vs * m.vb);
   }
 }
@@ -772,7 +776,7 @@ __device__ __forceinline__ void find_op(const MapDev& m, const BatchDev& b, uint
     if (lane == 0) b.init_present[i] = 0;
     return;
   }
-  const uint32_t meta = m.pm_meta[slot];
+  const uint32_t meta = b.hit_meta ? b.hit_meta[i] : m.pm_meta[slot];
   const uint64_t pr = b.pair[i];
   const uint32_t which = meta_which(meta);
   const uint32_t bin = which ? (uint32_t)(pr >> 32) : (uint32_t)pr;
@@ -902,6 +906,9 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
   ulonglong2* items = reinterpret_cast<ulonglong2*>(plain + m.page_bytes);
   const uint32_t d = b.dslot[e];
   const uint64_t q = b.dpage[e];
+  // loads whose results are needed only later are issued first (the stores
+  // below go through generic pointers, so the compiler keeps reads after them)
+  const uint64_t ver = m.version[q] + 1;
   const uint8_t* old = b.dbuf + (uint64_t)d * m.page_bytes;
   const uint64_t bitmap = *reinterpret_cast<const uint64_t*>(old);
   const uint64_t removed = b.removed[d];
@@ -915,10 +922,12 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
   const bool listed = lane < (int)rc && lane < (int)m.lmax;
   const uint32_t vs = listed ? rev_e : NONE32;
   uint64_t skey = 0;
+  uint32_t spm = 0;
   bool sv = false;
   if (listed) {
     sv = m.vs_live[vs] != 0;
     skey = m.vs_key[vs];
+    spm = m.vs_pm[vs];
   }
   const uint32_t pmask = __ballot_sync(0xffffffffu, pv);
   const uint32_t smask = __ballot_sync(0xffffffffu, sv);
@@ -927,6 +936,15 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
   if (tot > m.lmax) {  // cannot happen while every load is <= lmax
     if (lane == 0) set_err(m, ERR_PAGE);
     return;
+  }
+  // an evicted stash item's map entry (kept but for its location) and the
+  // free ring's tail for the items' value-store slots, ahead of the page
+  // build and encryption (one tail bump per warp)
+  const uint32_t smeta = sv ? m.pm_meta[spm] : 0u;
+  unsigned long long tail = 0;
+  if (smask && lane == __ffs(smask) - 1) {
+    tail = atomicAdd(m.ring_ctr + 1, (unsigned long long)__popc(smask));
+    stat_leave(m, false, __popc(smask));
   }
   if (pv)
     items[__popc(pmask & below)] =
@@ -953,7 +971,6 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
     for (uint32_t w = 0; w < m.vb / 8; w++) reinterpret_cast<uint64_t*>(slot + 8)[w] = val[w];
   }
   __syncwarp();
-  const uint64_t ver = m.version[q] + 1;
   // the old plaintext in dbuf is no longer read: the ciphertext replaces it
   // and k_flush copies it to the host page (or this warp does, below)
   uint8_t* cipher = b.dbuf + (uint64_t)d * m.page_bytes;
@@ -969,19 +986,12 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
     atomicAnd(m.revcnt + (q >> 2), ~(0xffu << sh));
   }
   // evicted stash items now live in the page; their value-store slots go
-  // back to the free ring (one tail bump per warp)
-  const uint32_t smask2 = __ballot_sync(0xffffffffu, sv);
-  unsigned long long tail = 0;
-  if (smask2 && lane == __ffs(smask2) - 1) {
-    tail = atomicAdd(m.ring_ctr + 1, (unsigned long long)__popc(smask2));
-    stat_leave(m, false, __popc(smask2));
-  }
-  tail = __shfl_sync(0xffffffffu, tail, smask2 ? __ffs(smask2) - 1 : 0);
+  // back to the free ring
+  tail = __shfl_sync(0xffffffffu, tail, smask ? __ffs(smask) - 1 : 0);
   if (sv) {
-    const uint32_t pmi = m.vs_pm[vs];
-    m.pm_meta[pmi] = meta_make(LOC_HOST, meta_which(m.pm_meta[pmi]), 0);
+    m.pm_meta[spm] = meta_make(LOC_HOST, meta_which(smeta), 0);
     m.vs_live[vs] = 0;
-    m.ring[(tail + __popc(smask2 & below)) % m.vs_cap] = vs;
+    m.ring[(tail + __popc(smask & below)) % m.vs_cap] = vs;
   }
 }
 
@@ -1031,12 +1041,38 @@ __global__ void k_remap_decide(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
 // One counter hands out ring positions to every lane of the warp that places
 // an item (one atomic per warp): returns this lane's position, or ~0 when the
 // lane does not take one.  All 32 lanes must call it.
-__device__ __forceinline__ unsigned long long ring_take(const MapDev& m, bool take) {
+// A fused batch's view of its map's free ring: the head and tail as the
+// batch found them and the entries from the head on, read while its host
+// pages are in flight.  Only the batch's own remap takes from the ring while
+// it runs (one warp, round after round) and its find_remove and eviction only
+// append past the tail, so the head moves only by the takes counted here and
+// the entries in the window do not change.
+constexpr uint32_t RING_WIN = 32;
+struct RingWin {
+  unsigned long long head, tail, taken;
+  uint32_t v[RING_WIN];
+};
+
+__device__ __forceinline__ unsigned long long ring_take(const MapDev& m, bool take,
+                                                        RingWin* w = nullptr) {
   const uint32_t mask = __ballot_sync(0xffffffffu, take);
   const int lane = threadIdx.x & 31;
   unsigned long long base = 0;
-  if (mask && lane == __ffs(mask) - 1) base = atomicAdd(m.ring_ctr, (unsigned long long)__popc(mask));
-  base = __shfl_sync(0xffffffffu, base, mask ? __ffs(mask) - 1 : 0);
+  if (w) {
+    // positions from the window's count; the shared head still moves (its
+    // result is not waited for)
+    base = w->head + w->taken;
+    __syncwarp();
+    if (mask && lane == __ffs(mask) - 1) {
+      w->taken += __popc(mask);
+      atomicAdd(m.ring_ctr, (unsigned long long)__popc(mask));
+    }
+    __syncwarp();
+  } else {
+    if (mask && lane == __ffs(mask) - 1)
+      base = atomicAdd(m.ring_ctr, (unsigned long long)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, mask ? __ffs(mask) - 1 : 0);
+  }
   return take ? base + __popc(mask & ((1u << lane) - 1u)) : ~0ull;
 }
 
@@ -1044,14 +1080,20 @@ __device__ __forceinline__ unsigned long long ring_take(const MapDev& m, bool ta
 // item takes, already counted; NONE32 to count it here)
 __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, uint32_t i,
                                             uint32_t dest, unsigned long long pos,
-                                            uint32_t rev_slot = NONE32) {
+                                            uint32_t rev_slot = NONE32,
+                                            const RingWin* w = nullptr) {
   const uint64_t pr = b.rpair[i];
   const uint32_t which = dest == (uint32_t)(pr >> 32) ? 1u : 0u;
-  if (pos >= m.ring_ctr[1]) {
-    set_err(m, ERR_VS);
-    return;
+  uint32_t vs;
+  if (w && pos < w->tail && pos - w->head < RING_WIN) {
+    vs = w->v[pos - w->head];
+  } else {
+    if (pos >= m.ring_ctr[1]) {
+      set_err(m, ERR_VS);
+      return;
+    }
+    vs = m.ring[pos % m.vs_cap];
   }
-  const uint32_t vs = m.ring[pos % m.vs_cap];
   const bool hbm = dest < m.K;
   const uint32_t meta = meta_make(hbm ? LOC_HBM : LOC_STASH, which, vs);
   uint32_t slot = b.hit[i];
@@ -1095,7 +1137,7 @@ __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, 
 // current round): bump the counts of its decided bin (and row, for a new
 // key), take a ring slot, write its entries.  All 32 lanes of the warp call.
 __device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& b, uint32_t i,
-                                               bool go) {
+                                               bool go, RingWin* w = nullptr) {
   // the bin's load, the row's count (a new key), the destination page's
   // reverse-index count (a host bin) and the free-ring position are taken
   // together (independent atomics in flight at once), then checked; a count
@@ -1110,7 +1152,7 @@ __device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& 
     if (fresh) row_old = byte_inc(m.rowcnt, b.rrow[i]);
     if (dest >= m.K) rev_slot = byte_inc(m.revcnt, dest - m.K);
   }
-  const unsigned long long pos = ring_take(m, go);
+  const unsigned long long pos = ring_take(m, go, w);
   if (go) {
     if (new_load > m.lmax) {
       set_err(m, ERR_LOAD);
@@ -1120,7 +1162,7 @@ __device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& 
       go = false;
     }
   }
-  if (go) remap_place(m, b, i, dest, pos, rev_slot);
+  if (go) remap_place(m, b, i, dest, pos, rev_slot, w);
   stat_place(m, go, dest < m.K, new_load);
 }
 
@@ -1329,87 +1371,151 @@ __device__ __forceinline__ void decide_op_l2(const MapDev& m, const BatchDev& b,
   }
 }
 
+// largest value the fused launch stages in shared memory (the ABI's limit)
+constexpr uint32_t FUSED_VB_MAX = 504;
+
 template <bool SEALED>
 __global__ void __launch_bounds__(FUSED_THREADS)
-    k_fused(MapDev m, BatchDev b, uint32_t n, uint64_t t0, uint32_t evict_warps) {
+    k_fused(MapDev m, BatchDev b, uint32_t n, uint64_t t0, uint32_t evict_warps,
+            uint32_t early_in) {
   extern __shared__ __align__(16) uint8_t sbuf[];
-  // the batch's read positions' host pages, their table slots, and a copy of
-  // the (empty) page table to insert the distinct pages into
-  __shared__ uint32_t s_posq[2 * FUSED_MAX_OPS], s_slot[2 * FUSED_MAX_OPS];
-  __shared__ uint32_t s_ht[FUSED_TABLE];
+  // Everything the batch reads back within itself lives in shared memory:
+  // the inputs, the grouping, pairs, rows, hits, the page table and its read
+  // positions, the found and re-placed values.  The shared helpers reach it
+  // through `L`, a copy of the batch descriptor whose pointers address these
+  // arrays (generic addressing), so a batch pays a memory round trip only for
+  // map state, pages and outputs.  The page buffers (dbuf), the global page
+  // table keys (read by the next batch) and the outputs stay in global memory.
+  __shared__ __align__(16) uint8_t s_in[FUSED_MAX_OPS * (9 + FUSED_VB_MAX) + 16];
+  __shared__ __align__(16) uint8_t s_vals[2 * FUSED_MAX_OPS * FUSED_VB_MAX];
+  __shared__ uint64_t s_pair[FUSED_MAX_OPS], s_rpair[FUSED_MAX_OPS], s_removed[FUSED_TABLE];
+  __shared__ __align__(16) uint32_t s_rows[4 * FUSED_MAX_OPS];
+  __shared__ uint32_t s_hit[FUSED_MAX_OPS], s_hmeta[FUSED_MAX_OPS], s_leader[FUSED_MAX_OPS],
+      s_prevw[FUSED_MAX_OPS], s_lastw[FUSED_MAX_OPS], s_rdest[FUSED_MAX_OPS],
+      s_rrow[FUSED_MAX_OPS];
+  __shared__ uint32_t s_posq[2 * FUSED_MAX_OPS], s_slot[2 * FUSED_MAX_OPS],
+      s_dslot[2 * FUSED_MAX_OPS], s_dpage[2 * FUSED_MAX_OPS];
+  __shared__ uint32_t s_ht[FUSED_TABLE], s_htmin[FUSED_TABLE], s_dcount;
+  __shared__ uint8_t s_initp[FUSED_MAX_OPS], s_fpres[FUSED_MAX_OPS];
+  __shared__ RingWin s_ring;
+  static_assert(RING_WIN >= FUSED_MAX_OPS, "the remap's takes fit the ring window");
   const int lane = threadIdx.x & 31;
   const uint32_t wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  BatchDev L = b;
+  L.keys = reinterpret_cast<uint64_t*>(s_in);
+  L.vin = s_in + 8 * n;
+  L.ops = s_in + (8 + m.vb) * n;
+  L.pair = s_pair; L.rpair = s_rpair; L.rows = s_rows;
+  L.hit = s_hit; L.hit_meta = s_hmeta;
+  L.leader = s_leader; L.prevw = s_prevw; L.lastw = s_lastw;
+  L.pos_page = s_posq; L.pos_slot = s_slot; L.ht_min = s_htmin;
+  L.removed = s_removed; L.dslot = s_dslot; L.dpage = s_dpage; L.dcount = &s_dcount;
+  L.init_val = s_vals; L.rval = s_vals + FUSED_MAX_OPS * FUSED_VB_MAX;
+  L.init_present = s_initp; L.fpres = s_fpres; L.rdest = s_rdest; L.rrow = s_rrow;
+  // Launched as a programmatic dependent of the previous kernel on the
+  // stream: it may start while that kernel runs, and passes dep_wait() before
+  // it touches anything another kernel writes.  Before the wait it computes
+  // what depends only on its own parameters (the DUMMY and REMAP pairs) and,
+  // with early_in, also stages its inputs, the position-map rows and the
+  // grouping (the caller guarantees the inputs are complete: host staging
+  // written before the launch, or a batch whose predecessor is an earlier
+  // batch of the same call).  It lets its successor start only after its own
+  // wait, so a successor never runs ahead of this kernel's predecessor.
   for (uint32_t h = threadIdx.x; h < FUSED_TABLE; h += blockDim.x) s_ht[h] = NONE32;
-  // 1. per op the DUMMY pair, the REMAP pair and the position-map rows (one
-  //    ChaCha20 block each); warp 3 groups the ops by key with n^2 compares:
-  //    leader = first op on the key, previous writer of each op, last writer
-  //    of each key group
-  if (threadIdx.x == 0) *b.dcount = 0;
-  if (b.h_in) {
-    // the inputs straight from the caller's pinned staging (16-byte reads
-    // over the link; both buffers hold the rounded-up tail)
-    const uint32_t words = (n * (9 + m.vb) + 15) / 16;
-    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x)
-      reinterpret_cast<uint4*>(b.keys)[w] = reinterpret_cast<const uint4*>(b.h_in)[w];
-    __syncthreads();
-  }
-  // (each kind of block in a warp of its own, lane = op, so the three run
-  // side by side instead of as divergent paths of one warp)
-  if (wid < 3 && (uint32_t)lane < n) {
+  if (threadIdx.x == 0) s_dcount = 0;
+  // 1a. per op the DUMMY pair and the REMAP pair (one ChaCha20 block each,
+  //     each kind in a warp of its own, lane = op)
+  if (wid < 2 && (uint32_t)lane < n) {
     const uint32_t i = lane;
     uint32_t p1, p2;
+    prf_pair(m, wid == 0 ? DOM_DUMMY : DOM_REMAP, t0 + i, p1, p2);
+    const uint64_t pr = (uint64_t)p1 | ((uint64_t)p2 << 32);
     if (wid == 0) {
-      prf_pair(m, DOM_DUMMY, t0 + i, p1, p2);
-      b.pair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
-    } else if (wid == 1) {
-      prf_pair(m, DOM_REMAP, t0 + i, p1, p2);
-      b.rpair[i] = (uint64_t)p1 | ((uint64_t)p2 << 32);
-      // the remap will read these loads and take a free value-store slot
+      s_pair[i] = pr;
+    } else {
+      s_rpair[i] = pr;
+      // the remap will read these loads (an address only: nothing is read)
       prefetch_l2(m.load + (p1 >> 2));
       prefetch_l2(m.load + (p2 >> 2));
-      if (i == 0) prefetch_l2(m.ring + (*m.ring_ctr % m.vs_cap));
+    }
+  }
+  // 0. the inputs, laid out keys | vin | ops: straight from the caller's
+  //    pinned staging (16-byte reads over the link; the staging holds the
+  //    rounded-up tail), or from the device arrays; then (1b) per op the
+  //    position-map rows (one ChaCha20 block, warp 2, lane = op) and the
+  //    grouping (warp 3, n^2 compares: leader = first op on the key,
+  //    previous writer of each op, last writer of each key group)
+  auto inputs_rows_group = [&]() {
+    if (b.h_in) {
+      const uint32_t words = (n * (9 + m.vb) + 15) / 16;
+      for (uint32_t w = threadIdx.x; w < words; w += blockDim.x)
+        reinterpret_cast<uint4*>(s_in)[w] = reinterpret_cast<const uint4*>(b.h_in)[w];
     } else {
+      const uint32_t vw = n * m.vb / 8;
+      for (uint32_t w = threadIdx.x; w < n + vw + n; w += blockDim.x) {
+        if (w < n)
+          L.keys[w] = b.keys[w];
+        else if (w < n + vw)
+          reinterpret_cast<uint64_t*>(L.vin)[w - n] =
+              reinterpret_cast<const uint64_t*>(b.vin)[w - n];
+        else
+          L.ops[w - n - vw] = b.ops[w - n - vw];
+      }
+    }
+    __syncthreads();
+    if (wid == 2 && (uint32_t)lane < n) {
+      const uint32_t i = lane;
       uint32_t rows[4];
-      prf_rows(m, b.keys[i], rows);
-      *reinterpret_cast<uint4*>(b.rows + 4 * (uint64_t)i) =
-          make_uint4(rows[0], rows[1], rows[2], rows[3]);
+      prf_rows(m, L.keys[i], rows);
+      *reinterpret_cast<uint4*>(s_rows + 4 * i) = make_uint4(rows[0], rows[1], rows[2], rows[3]);
 #pragma unroll
       for (int j = 0; j < 4; j++) prefetch_l2(m.rowcnt + (rows[j] >> 2));
     }
-  }
-  if (wid == 3) {
-    const bool mine = (uint32_t)lane < n;
-    const uint64_t key = mine ? b.keys[lane] : 0;
-    const uint32_t op = mine ? b.ops[lane] : OP_GET;
-    uint32_t lead = lane, prevw = NONE32, lastw = NONE32;
-    for (uint32_t j = 0; j < n; j++) {
-      const uint64_t kj = __shfl_sync(0xffffffffu, key, j);
-      const uint32_t oj = __shfl_sync(0xffffffffu, op, j);
-      if (!mine || kj != key) continue;
-      if (j < (uint32_t)lane) {
-        lead = min(lead, j);
-        if (oj != OP_GET) prevw = j;
-      } else if (oj != OP_GET) {
-        lastw = j;
+    if (wid == 3) {
+      const bool mine = (uint32_t)lane < n;
+      const uint64_t key = mine ? L.keys[lane] : 0;
+      const uint32_t op = mine ? L.ops[lane] : OP_GET;
+      uint32_t lead = lane, prevw = NONE32, lastw = NONE32;
+      for (uint32_t j = 0; j < n; j++) {
+        const uint64_t kj = __shfl_sync(0xffffffffu, key, j);
+        const uint32_t oj = __shfl_sync(0xffffffffu, op, j);
+        if (!mine || kj != key) continue;
+        if (j < (uint32_t)lane) {
+          lead = min(lead, j);
+          if (oj != OP_GET) prevw = j;
+        } else if (oj != OP_GET) {
+          lastw = j;
+        }
+      }
+      if (mine) {
+        s_leader[lane] = lead;
+        s_prevw[lane] = prevw;
+        s_lastw[lane] = lastw;
       }
     }
-    if (mine) {
-      b.leader[lane] = lead;
-      b.prevw[lane] = prevw;
-      if (lead == (uint32_t)lane) b.lastw[lane] = lastw;
-    }
-  }
+  };
+  if (early_in) inputs_rows_group();
+  dep_wait();
+  dep_trigger();
+  if (!early_in) inputs_rows_group();
+  // the remap's free value-store slot into L2
+  if (wid == 1 && lane == 0) prefetch_l2(m.ring + (*m.ring_ctr % m.vs_cap));
   __syncthreads();
   // 2. position-map search (warp per op): a hit reads its stored pair, every
-  //    other op its DUMMY pair; the host bins of each read position
+  //    other op its DUMMY pair; the host bins of each read position.  A hit
+  //    in the HBM store or the stash has its value brought into L2 for
+  //    find_remove.
   for (uint32_t i = wid; i < n; i += nwarps) {
-    uint32_t found = NONE32;
+    uint32_t found = NONE32, fm = 0;
     uint64_t fb = 0;
-    if (b.leader[i] == i) found = pm_search(m, b, i, b.keys[i], lane, &fb);
-    const uint64_t pr = found != NONE32 ? fb : b.pair[i];
+    if (s_leader[i] == i) found = pm_search(m, L, i, L.keys[i], lane, &fb, &fm);
+    const uint64_t pr = found != NONE32 ? fb : s_pair[i];
     if (lane == 0) {
-      b.hit[i] = found;
-      if (found != NONE32) b.pair[i] = pr;
+      s_hit[i] = found;
+      s_hmeta[i] = fm;
+      s_pair[i] = pr;
+      if (found != NONE32 && meta_loc(fm) != LOC_HOST)
+        prefetch_l2(m.vs_val + (uint64_t)meta_ptr(fm) * m.vb);
     }
     if (lane < 2) {
       const uint32_t p = lane == 0 ? (uint32_t)pr : (uint32_t)(pr >> 32);
@@ -1418,9 +1524,9 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   }
   __syncthreads();
   // 2b. warp 0: the batch's page table -- each distinct page once, at the
-  //     slot linear probing gives it (inserted into a shared-memory copy of
-  //     the empty table), its first read position, the page list -- written
-  //     to the global table with plain stores
+  //     slot linear probing gives it in the (empty) table, its first read
+  //     position, the page list in claim order; the table's keys also go to
+  //     the global table, where the next batch looks for pages this one wrote
   if (wid == 0) {
     const uint32_t np = 2 * n;
     uint32_t q[2], f[2];
@@ -1451,29 +1557,37 @@ __global__ void __launch_bounds__(FUSED_THREADS)
 #pragma unroll
     for (int k = 0; k < 2; k++) {
       const uint32_t p = lane + 32 * k;
-      if (p >= np) continue;
-      b.pos_page[p] = q[k];
-      if (!valid[k]) continue;
+      if (p >= np || !valid[k]) continue;
       const uint32_t h = s_slot[f[k]];
-      b.pos_slot[p] = h;
+      if (!first[k]) s_slot[p] = h;
       if (first[k]) {
         const uint32_t d = k == 0 ? __popc(bf0 & below) : __popc(bf0) + __popc(bf1 & below);
         b.ht_key[h] = q[k];
-        b.ht_min[h] = p;
-        b.dslot[d] = h;
-        b.dpage[d] = q[k];
+        s_htmin[h] = p;
+        s_dslot[d] = h;
+        s_dpage[d] = q[k];
       }
     }
-    if (lane == 0) *b.dcount = __popc(bf0) + __popc(bf1);
+    if (lane == 0) s_dcount = __popc(bf0) + __popc(bf1);
   }
   __syncthreads();
   // 2c. warp per distinct page: read it (the previous batch's ciphertext if
   //     that batch wrote it, else the host page) and decrypt it into its
-  //     slot's buffer; meanwhile bring its eviction's data into L2
+  //     slot's buffer; meanwhile bring its eviction's data into L2.  The
+  //     last warp first reads the free ring's window for the remap.
+  if (wid == nwarps - 1) {
+    const unsigned long long hd = m.ring_ctr[0], tl = m.ring_ctr[1];
+    if (lane < (int)RING_WIN && hd + lane < tl) s_ring.v[lane] = m.ring[(hd + lane) % m.vs_cap];
+    if (lane == 0) {
+      s_ring.head = hd;
+      s_ring.tail = tl;
+      s_ring.taken = 0;
+    }
+  }
   {
-    const uint32_t nd = *b.dcount;
+    const uint32_t nd = s_dcount;
     for (uint32_t d = wid; d < nd; d += nwarps) {
-      const uint32_t q = b.dpage[d], h = b.dslot[d];
+      const uint32_t q = s_dpage[d], h = s_dslot[d];
       const uint8_t* src = m.pages + (uint64_t)q * m.page_bytes;
       uint4 x = make_uint4(0, 0, 0, 0);
       if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + 16 * lane);
@@ -1485,7 +1599,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
         src = b.prev_dbuf + (uint64_t)pd * m.page_bytes;
         if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + 16 * lane);
       }
-      page_in<SEALED>(m, b, h, q, kind, src, x, lane);
+      page_in<SEALED>(m, L, h, q, kind, src, x, lane);
     }
   }
   __syncthreads();
@@ -1495,8 +1609,8 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     const uint32_t np = 2 * n;
     bool v0, f0, v1, f1;
     uint32_t q0, q1, s0, s1;
-    pos_flags(b, lane, np, v0, f0, q0, s0);
-    pos_flags(b, lane + 32, np, v1, f1, q1, s1);
+    pos_flags(L, lane, np, v0, f0, q0, s0);
+    pos_flags(L, lane + 32, np, v1, f1, q1, s1);
     const uint32_t bv0 = __ballot_sync(0xffffffffu, v0), bv1 = __ballot_sync(0xffffffffu, v1);
     const uint32_t bf0 = __ballot_sync(0xffffffffu, f0), bf1 = __ballot_sync(0xffffffffu, f1);
     const uint32_t below = (1u << lane) - 1u;
@@ -1517,29 +1631,34 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   }
   clear_prev_table(b, threadIdx.x, blockDim.x);
   // 4. find_remove (warp per op)
-  for (uint32_t i = wid; i < n; i += nwarps) find_op(m, b, i, lane);
+  for (uint32_t i = wid; i < n; i += nwarps) find_op(m, L, i, lane);
   __syncthreads();
   // 5. Get/Put/Delete semantics (the last warp, lane per op) beside the
   //    write-back with eviction (the other warps, warp per page, straight to
-  //    the host as well)
+  //    the host as well); a remap of one round decides its bins here too
+  //    (eviction changes no load or row count)
+  const bool one_round = n <= m.Wr;
   if (wid == nwarps - 1) {
-    if ((uint32_t)lane < n) exec_op(m, b, lane);
+    if ((uint32_t)lane < n) exec_op(m, L, lane);
+    __syncwarp();
+    if (one_round && (uint32_t)lane < n && s_leader[lane] == (uint32_t)lane && s_fpres[lane])
+      decide_op_l2(m, L, lane);
   } else if (wid < evict_warps) {
-    const uint32_t nd = *b.dcount;
+    const uint32_t nd = s_dcount;
     for (uint32_t e = wid; e < nd; e += evict_warps)
-      evict_one<SEALED>(m, b, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), true);
+      evict_one<SEALED>(m, L, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), true);
   }
   __syncthreads();
   // 6. P2C remap in rounds of W_r op slots (warp 0, lane per op): decide on
-  //    round-start counts, then place
+  //    round-start counts (a single round decided above), then place
   if (wid == 0) {
     for (uint64_t lo = 0; lo < n; lo += m.Wr) {
       const uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
       const uint32_t i = lane;
-      const bool act = i >= lo && i < hi && b.leader[i] == i && b.fpres[i];
-      if (act) decide_op_l2(m, b, i);
+      const bool act = i >= lo && i < hi && s_leader[i] == i && s_fpres[i];
+      if (act && !one_round) decide_op_l2(m, L, i);
       __syncwarp();
-      remap_apply_op(m, b, i, act);
+      remap_apply_op(m, L, i, act, &s_ring);
       __syncwarp();
     }
   }
@@ -1559,21 +1678,32 @@ __global__ void __launch_bounds__(FUSED_THREADS)
 }
 
 cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool early_in) {
   if (n == 0) return cudaSuccess;
   if (n > FUSED_MAX_OPS || b.ht_mask + 1 != FUSED_TABLE) return cudaErrorInvalidValue;
   ProfSpan whole(P_ACCESS, st);
+  if (m.vb > FUSED_VB_MAX) return cudaErrorInvalidValue;
+  auto kf = m.integrity ? k_fused<true> : k_fused<false>;
+  // the eviction warps' page buffers take what the kernel's own shared
+  // arrays leave of the 227 KB a block may use
+  static const size_t static_bytes[2] = {
+      [] { cudaFuncAttributes a{}; return cudaFuncGetAttributes(&a, k_fused<false>) == cudaSuccess
+                                              ? a.sharedSizeBytes : (size_t)(64u << 10); }(),
+      [] { cudaFuncAttributes a{}; return cudaFuncGetAttributes(&a, k_fused<true>) == cudaSuccess
+                                              ? a.sharedSizeBytes : (size_t)(64u << 10); }()};
+  const size_t budget = (227u << 10) - static_bytes[m.integrity ? 1 : 0];
   const uint32_t per_warp = m.page_bytes + 32 * 16;
-  uint32_t ew = (200u << 10) / per_warp;
+  uint32_t ew = (uint32_t)(budget / per_warp);
   // (the last warp runs the ops' semantics meanwhile)
   ew = ew < 1 ? 1 : (ew > FUSED_THREADS / 32 - 1 ? FUSED_THREADS / 32 - 1 : ew);
   const size_t smem = (size_t)ew * per_warp;
-  auto kf = m.integrity ? k_fused<true> : k_fused<false>;
+  if (smem > budget) return cudaErrorInvalidValue;
   cudaError_t e = raise_smem_limit((const void*)kf, smem);
   if (e != cudaSuccess) return e;
-  kf<<<1, FUSED_THREADS, smem, st>>>(m, b, n, t0, ew);
+  e = launch_dependent(kf, 1, FUSED_THREADS, smem, st, m, b, n, t0, ew, early_in ? 1u : 0u);
+  if (e != cudaSuccess) return e;
   count_launch();
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 // The batch's preparation depends only on its own inputs: the grouping keys

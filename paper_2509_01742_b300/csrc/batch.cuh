@@ -23,6 +23,8 @@ struct BatchDev {
   uint64_t* rpair;     // [cap] REMAP pair
   uint32_t* rows;      // [4 * cap] position-map rows
   uint32_t* hit;       // [cap] position-map slot of a leader hit, or NONE
+  uint32_t* hit_meta;  // [cap] that slot's metadata as the search read it (fused
+                       // launch only; null: find_remove reads the map)
   // pages read by the batch
   uint32_t* pos_page;  // [2 cap] host page of read position 2i + j, or NONE
   uint32_t* pos_slot;  // [2 cap] hash-table slot of that page
@@ -120,10 +122,14 @@ cudaError_t launch_prep(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t
 // host write-back of its pages) in one single-CTA launch; op i has sequence
 // number t0 + i.  Same tables, buffers, results, pages and trace as
 // launch_prep + launch_main + the write-back.  No write-back of an earlier
-// batch may still be in flight when it starts.
+// batch may still be in flight when it starts.  It is launched as a
+// programmatic dependent of the previous kernel on st; early_in = the inputs
+// (b.h_in, or b.keys / b.vin / b.ops) are complete even if that kernel is
+// not (host staging written before the launch, or the previous kernel is an
+// earlier fused batch of the same call), so they are read before the wait.
 constexpr uint32_t FUSED_MAX_OPS = 32;
 cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
-                         cudaStream_t st);
+                         cudaStream_t st, bool early_in = false);
 cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st,
                         const FlushCtx& fc);
 // The lookahead part of a batch (b.la_on = 1), after its preparation:

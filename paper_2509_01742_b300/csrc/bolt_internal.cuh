@@ -108,7 +108,10 @@ __device__ __forceinline__ void chacha_block(const uint32_t* key, uint32_t count
   uint32_t x4 = key[0], x5 = key[1], x6 = key[2], x7 = key[3];
   uint32_t x8 = key[4], x9 = key[5], x10 = key[6], x11 = key[7];
   uint32_t x12 = counter, x13 = n0, x14 = n1, x15 = n2;
-#pragma unroll
+  // the 10 double rounds stay a loop: unrolled, the block is ~1000
+  // instructions of straight-line code, and in the latency-bound kernels
+  // (one CTA per batch) fetching it costs more than the loop's branches
+#pragma unroll 1
   for (int r = 0; r < 10; r++) {
     BOLT_QR(x0, x4, x8, x12);
     BOLT_QR(x1, x5, x9, x13);
@@ -143,7 +146,7 @@ __device__ __forceinline__ uint4 chacha_quad(const uint32_t* key, uint32_t count
   const uint32_t id = g == 0 ? counter : g == 1 ? n0 : g == 2 ? n1 : n2;
   uint32_t a = c_const, b = ib, c = ic, d = id;
   const int s1 = base | ((g + 1) & 3), s2 = base | ((g + 2) & 3), s3 = base | ((g + 3) & 3);
-#pragma unroll
+#pragma unroll 1
   for (int r = 0; r < 10; r++) {
     BOLT_QR(a, b, c, d);
     b = __shfl_sync(0xffffffffu, b, s1);

@@ -514,7 +514,10 @@ cudaError_t main_batch(bolt* h, const BatchDev& b, uint32_t n, cudaStream_t st,
 // pages reach the host from the kernel itself, so it first orders st after
 // every write-back still in flight (one could be of a page it rewrites) and
 // leaves none pending.
-cudaError_t fused_batch(bolt* h, const BatchDev& b, uint32_t n, uint64_t t0, cudaStream_t st) {
+// early_in: the batch's inputs are complete even if the kernel before it on
+// st is not (see launch_fused)
+cudaError_t fused_batch(bolt* h, const BatchDev& b, uint32_t n, uint64_t t0, cudaStream_t st,
+                        bool early_in = false) {
   const int s = h->slot;
   for (int k = 0; k < 2; k++)
     if (h->flush_pending[k]) {
@@ -523,7 +526,7 @@ cudaError_t fused_batch(bolt* h, const BatchDev& b, uint32_t n, uint64_t t0, cud
       h->flush_pending[k] = false;
     }
   const BatchDev v = slot_view(h, b, n, s);
-  cudaError_t e = launch_fused(h->m, v, n, t0, st);
+  cudaError_t e = launch_fused(h->m, v, n, t0, st, early_in);
   if (e != cudaSuccess) return e;
   h->slot_ht_mask[s] = v.ht_mask;
   h->prev_valid = true;
@@ -571,11 +574,13 @@ cudaError_t access_batches(bolt* h, BatchDev b, uint64_t n, uint32_t w, cudaStre
     return e;
   }
   if (h->fused && w <= FUSED_MAX_OPS) {
-    // small batches: one launch each, in order on st
+    // small batches: one launch each, in order on st; from the second on,
+    // the kernel before each is the previous batch of this call, whose own
+    // start came after the caller's work, so the inputs are complete
     for (uint64_t j = 0; j < nb; j++) {
       uint32_t cnt = 0;
       const BatchDev x = slice(j, cnt);
-      cudaError_t e = fused_batch(h, x, cnt, h->t, st);
+      cudaError_t e = fused_batch(h, x, cnt, h->t, st, j > 0);
       if (e != cudaSuccess) return e;
       h->t += cnt;
       h->batches++;
@@ -1189,7 +1194,8 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
     b.h_err = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->h_err) + h->io_dev_delta);
     b.h_done = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->h_done) + h->io_dev_delta);
     b.done_seq = ++h->done_seq;
-    cudaError_t e = fused_batch(h, b, (uint32_t)n, h->t, st);
+    // (the inputs are in the staging, written before the launch)
+    cudaError_t e = fused_batch(h, b, (uint32_t)n, h->t, st, true);
     if (e != cudaSuccess) return BOLT_E_CUDA;
     // the kernel's completion word (written after its results) ends the wait;
     // if it has not come within seconds, wait for the stream and let its
