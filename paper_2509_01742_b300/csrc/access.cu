@@ -604,6 +604,40 @@ __device__ __forceinline__ void page_in(const MapDev& m, const BatchDev& b, uint
   if (lane == 0) b.removed[slot] = 0;
 }
 
+// the rest of a page whose first 16 bytes per lane are in `first`, copied as
+// it is (sealed ciphertext) into the slot's buffer.  All 32 lanes call.
+__device__ __forceinline__ void page_copy(const MapDev& m, const BatchDev& b, uint32_t slot,
+                                          const uint8_t* src, uint4 first, int lane) {
+  uint8_t* dst = b.dbuf + (uint64_t)slot * m.page_bytes;
+  for (uint32_t c = 0; c < m.page_bytes; c += 512) {
+    const uint32_t off = c + 16 * lane;
+    uint4 x = first;
+    if (c > 0 && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
+    if (off < m.page_bytes) *reinterpret_cast<uint4*>(dst + off) = x;
+  }
+  if (lane == 0) b.removed[slot] = 0;
+}
+
+// Sealed pages of a batch, a warp per page (claim order): the ciphertext
+// k_lookup left in the slot's buffer is checked against its tag and
+// decrypted in place (page_in; a page that fails reads as empty and raises
+// ERR_INTEGRITY).  Separate from k_lookup, whose warps wait on host reads, so
+// that the Poly1305 work runs on every warp of the GPU at once.
+__global__ void __launch_bounds__(256) k_open(MapDev m, BatchDev b) {
+  dep_wait();
+  const int lane = threadIdx.x & 31;
+  const uint32_t nd = *b.dcount;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t d = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; d < nd; d += nw) {
+    const uint32_t slot = b.dslot[d];
+    const uint64_t q = b.dpage[d];
+    const uint8_t* pg = b.dbuf + (uint64_t)slot * m.page_bytes;
+    uint4 x = make_uint4(0, 0, 0, 0);
+    if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(pg + 16 * lane);
+    page_in<true>(m, b, slot, q, SRC_HOST, pg, x, lane);
+  }
+}
+
 // warp per op (Alg. 1 lines 2-5 over a batch): leaders search the position
 // map -- a hit reads the stored pair, a miss and every non-leader the DUMMY
 // pair -- and the two bins' host pages enter the batch's page table.  The
@@ -725,8 +759,13 @@ __device__ __forceinline__ void lookup_op(const MapDev& m, const BatchDev& b, ui
     }
   }
 #pragma unroll
-  for (int k = 0; k < 2; k++)
-    if (kind[k] != SRC_NONE) page_in<SEALED>(m, b, sl[k], qs[k], kind[k], src[k], x[k], lane);
+  for (int k = 0; k < 2; k++) {
+    if (kind[k] == SRC_NONE) continue;
+    if (SEALED)  // k_open checks and decrypts it, a warp per page
+      page_copy(m, b, sl[k], src[k], x[k], lane);
+    else
+      page_in<false>(m, b, sl[k], qs[k], kind[k], src[k], x[k], lane);
+  }
 }
 
 // ops over at most LOOKUP_BLOCKS_PER_SM blocks per SM: a warp waiting on host
@@ -1803,6 +1842,14 @@ cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStre
     count_launch();
     e = cudaEventRecord(fc.prev_flushed, fc.flush_st);
     if (e != cudaSuccess) return e;
+  }
+  if (m.integrity) {
+    // the sealed pages' tags and decryption (warp per page)
+    ProfSpan ps(P_GATHER, st);
+    const uint32_t want = (2 * n * 32 + 255) / 256, cap = 8 * (uint32_t)num_sms();
+    e = launch_dependent(k_open, want < cap ? want : cap, 256, 0, st, m, b);
+    if (e != cudaSuccess) return e;
+    count_launch();
   }
   {
     ProfSpan ps(P_FINDEXEC, st);
