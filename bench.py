@@ -380,10 +380,10 @@ def run_bolt(args) -> None:
                      "records": float(N * args.steps), "accesses": float(n_acc * args.steps)},
                     world, group)
 
-    # secondary roofline: the build's grouping of host records by page (a
-    # counting scatter), algorithmic bytes = a 4-byte destination read per
-    # record, and per host-bin record an 8-byte tag write, the cursor's 4-byte
-    # read and write and a 4-byte run-end read, against HBM.  The host-bin
+    # secondary roofline: the build's grouping of host records by page (two
+    # bucket passes), algorithmic bytes = a 4-byte destination read per
+    # record, and per host-bin record its 8-byte tag written to its bucket,
+    # read back and written to its page's run, against HBM.  The host-bin
     # record count comes from an untimed rebuild (same keys and seed: the same
     # placement), read from the bin loads before any access.
     peaks = measured_peaks()
@@ -393,15 +393,16 @@ def run_bolt(args) -> None:
     assert m.init_device(d_keys, d_vals, SEED_MAP, stream=stream) == 0
     assert m.sync() == 0
     n_host = int(m.loads()[info["K"]:].astype(np.int64).sum())
-    bytes_per_launch = 4 * N + 20 * n_host
+    bytes_per_launch = 4 * N + 24 * n_host
     avg_s = sg["ms"] / max(1, sg["spans"]) * 1e-3
     achieved = bytes_per_launch / avg_s / 1e9 if sg["spans"] else None
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
-            traffic = json.load(f).get("k_build_scatter", {}).get("bytes_per_launch_full")
-    roofline_hbm = {"bound": "hbm", "kernel": "k_build_scatter (host records grouped by page)",
+            traffic = json.load(f).get("page_group", {}).get("bytes_per_launch_full")
+    roofline_hbm = {"bound": "hbm",
+                    "kernel": "k_group_buckets + k_group_pages (host records grouped by page)",
                     "achieved": round(achieved, 1) if achieved else None,
                     "peak": hbm_peak, "unit": "GB/s",
                     "frac": round(achieved / hbm_peak, 4) if achieved and hbm_peak else None,

@@ -277,19 +277,38 @@ __global__ void k_build_tags(MapDev m, const uint32_t* __restrict__ dest, uint64
   }
 }
 
-// Host-bin records grouped by page without a sort: page q's run starts at
-// page_off[q] (the prefix of the page loads the rounds left), and each record
-// takes the next position of its run from a per-page cursor (a copy of
-// page_off).  The order inside a run is the atomics' order; the page build
-// orders every run by (key, record), so no page depends on it.  A record
-// whose bin is out of range (rounds that gave up leave `dest` unwritten) or
-// whose run is already full (loads and destinations disagree) is not
-// written and raises ERR_PAGE.
-__global__ void __launch_bounds__(256) k_build_scatter(MapDev m, const uint32_t* __restrict__ dest,
-                                                       uint64_t n,
-                                                       const uint32_t* __restrict__ page_off,
-                                                       uint32_t* __restrict__ cursor,
-                                                       uint64_t* __restrict__ tags) {
+// Host-bin records grouped by page without a sort, in two passes.  Page q's
+// run starts at page_off[q] (the prefix of the page loads the rounds left),
+// so a bucket of GROUP_PAGES consecutive pages owns one contiguous run too.
+//   k_group_buckets: each record takes the next position of its bucket's run
+//     from the bucket's cursor (one counter per bucket: they stay in L2, and
+//     each bucket's writes advance sequentially, so L2 merges them into full
+//     lines) and writes its tag (page << 32 | record) there;
+//   k_group_pages: a CTA per bucket moves each tag of the bucket's run to the
+//     next position of its page's run (cursors in shared memory; all writes
+//     within the bucket's run).
+// The order inside a page's run is the atomics' order; the page build orders
+// every run by (key, record), so no page depends on it.  A record whose bin is
+// out of range (rounds that gave up leave `dest` unwritten) or whose run is
+// already full (loads and destinations disagree) is not written and raises
+// ERR_PAGE.
+constexpr uint32_t GROUP_PAGE_BITS = 9;
+constexpr uint32_t GROUP_PAGES = 1u << GROUP_PAGE_BITS;
+
+// bucket b's cursor and run end: page_off[b * GROUP_PAGES], page_off[min(..., M)]
+__global__ void k_group_init(MapDev m, const uint32_t* __restrict__ page_off, uint32_t nb,
+                             uint32_t* __restrict__ bcur, uint32_t* __restrict__ bend) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    const uint64_t q0 = (uint64_t)b << GROUP_PAGE_BITS, q1 = q0 + GROUP_PAGES;
+    bcur[b] = page_off[q0];
+    bend[b] = page_off[q1 < m.M ? q1 : m.M];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_group_buckets(MapDev m, const uint32_t* __restrict__ dest,
+                                                       uint64_t n, uint32_t* __restrict__ bcur,
+                                                       const uint32_t* __restrict__ bend,
+                                                       uint64_t* __restrict__ tmp) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t d = dest[i];
@@ -298,13 +317,44 @@ __global__ void __launch_bounds__(256) k_build_scatter(MapDev m, const uint32_t*
       set_err(m, ERR_PAGE);
       continue;
     }
-    const uint32_t q = d - (uint32_t)m.K;
-    const uint32_t pos = atomicAdd(cursor + q, 1u);
-    if (pos >= page_off[q + 1]) {
+    const uint32_t q = d - (uint32_t)m.K, b = q >> GROUP_PAGE_BITS;
+    const uint32_t pos = atomicAdd(bcur + b, 1u);
+    if (pos >= bend[b]) {
       set_err(m, ERR_PAGE);
       continue;
     }
-    tags[pos] = ((uint64_t)q << 32) | i;
+    tmp[pos] = ((uint64_t)q << 32) | i;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_group_pages(MapDev m, const uint32_t* __restrict__ page_off,
+                                                     uint32_t nb, const uint64_t* __restrict__ tmp,
+                                                     uint64_t* __restrict__ tags) {
+  __shared__ uint32_t cur[GROUP_PAGES], end[GROUP_PAGES];
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const uint64_t q0 = (uint64_t)b << GROUP_PAGE_BITS;
+    const uint64_t q1 = q0 + GROUP_PAGES < m.M ? q0 + GROUP_PAGES : m.M;
+    for (uint64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+      cur[q - q0] = page_off[q];
+      end[q - q0] = page_off[q + 1];
+    }
+    __syncthreads();
+    const uint32_t lo = page_off[q0], hi = page_off[q1];
+    for (uint32_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+      const uint64_t t = tmp[k];
+      const uint64_t q = t >> 32;
+      if (q < q0 || q >= q1) {  // a slot pass one left unwritten
+        set_err(m, ERR_PAGE);
+        continue;
+      }
+      const uint32_t pos = atomicAdd(&cur[q - q0], 1u);
+      if (pos >= end[q - q0]) {
+        set_err(m, ERR_PAGE);
+        continue;
+      }
+      tags[pos] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -671,18 +721,21 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   }
   // 2. page run starts
   scan_page_runs(m, s, st);
-  // 3. host records grouped by page: a counting scatter with the per-page
-  // cursors in the rows4 buffer (free between the rounds and the page
-  // staging); without room for them, tags + bitonic sort
+  // 3. host records grouped by page: two bucket passes with the bucket
+  // tags and cursors in the rows4 buffer (free between the rounds and the
+  // page staging); without it, tags + bitonic sort
   cudaError_t e;
-  if (s.rows4 && s.cap * sizeof(uint4) >= m.M * sizeof(uint32_t)) {
+  const uint32_t nbk = (uint32_t)((m.M + GROUP_PAGES - 1) >> GROUP_PAGE_BITS);
+  if (s.rows4 && s.cap * sizeof(uint4) >= n * sizeof(uint64_t) + 2ull * nbk * sizeof(uint32_t)) {
     ProfSpan ps(P_PAGE_GROUP, st);
-    uint32_t* cursor = reinterpret_cast<uint32_t*>(s.rows4);
-    e = cudaMemcpyAsync(cursor, s.page_off, m.M * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
-                        st);
-    if (e != cudaSuccess) return e;
-    k_build_scatter<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.page_off, cursor, s.tags);
-    count_launch();
+    uint64_t* tmp = reinterpret_cast<uint64_t*>(s.rows4);
+    uint32_t* bcur = reinterpret_cast<uint32_t*>(tmp + n);
+    uint32_t* bend = bcur + nbk;
+    k_group_init<<<(nbk + 255) / 256, 256, 0, st>>>(m, s.page_off, nbk, bcur, bend);
+    k_group_buckets<<<sms * 8, 256, 0, st>>>(m, s.dest, n, bcur, bend, tmp);
+    k_group_pages<<<nbk < (uint32_t)sms * 16 ? nbk : (uint32_t)sms * 16, 256, 0, st>>>(
+        m, s.page_off, nbk, tmp, s.tags);
+    count_launch(3);
   } else {
     k_build_tags<<<sms * 8, 256, 0, st>>>(m, s.dest, n, s.tag_cap, s.tags);
     count_launch();
