@@ -148,3 +148,49 @@ def test_integrity_excludes_lookahead():
         g.set_param(B.BOLT_PARAM_INTEGRITY, 1)
     assert e.value.rc == B.BOLT_E_ARG
     g.close()
+
+
+def test_sealed_prepared_load_matches_oracle():
+    """A data owner's image (Sec. 4.2) loaded into a sealed map gives the
+    oracle's sealed pages, and accesses afterwards the oracle's results."""
+    import torch
+    from tests.test_gpu_owner_build import _to_device
+    N, vb = 1 << 14, 24
+    keys, vals = W.records(12000, vb, 0x1AB0)
+    seed = 0x5EED0031
+    o = O.OracleMap(N, vb, integrity=True)
+    rc, img = o.prepare(keys, vals, seed)
+    assert rc == 0
+    g = B.BoltMap(N, vb, trace=True, integrity=True)
+    assert g.info() == o.info()
+    assert g.init_prepared(_to_device(img), len(keys), seed) == 0
+    assert np.array_equal(o.pages(), g.pages()), "sealed pages differ after the prepared load"
+    ops, k, vin = W.op_stream(12000, 2000, vb, 0x1AB1, get_frac=0.5, del_frac=0.1,
+                              absent_frac=0.1)
+    rc_o, vo, so = o.access(ops, k, vin)
+    rc_g, vg, sg = g.access(ops, k, vin)
+    assert rc_o == rc_g == 0
+    assert np.array_equal(so, sg) and np.array_equal(vo, vg)
+    _state_equal(o, g, "after a batch")
+    o.close(); g.close()
+
+
+def test_sealed_allocation_free_build_matches_oracle():
+    """bolt_init_device_noalloc (pages stored straight to the host from the
+    SMs) seals them as the oracle does."""
+    import ctypes
+    import torch
+    N, vb = 1 << 14, 8
+    keys, vals = W.records(N, vb, 0x1AC0)
+    seed = 0x5EED0032
+    o = O.OracleMap(N, vb, integrity=True)
+    assert o.init(keys, vals, seed) == 0
+    g = B.BoltMap(N, vb, integrity=True)
+    tk = torch.from_numpy(keys.view(np.int64)).cuda()
+    tv = torch.from_numpy(vals.copy()).cuda()
+    assert B.bolt_init_device_noalloc(g.handle, ctypes.c_void_p(tk.data_ptr()),
+                                      ctypes.c_void_p(tv.data_ptr()), N, seed,
+                                      ctypes.c_void_p(0)) == 0
+    assert np.array_equal(o.pages(), g.pages()), "sealed pages differ after the build"
+    assert np.array_equal(o.loads(), g.loads())
+    o.close(); g.close()
