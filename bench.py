@@ -747,6 +747,8 @@ def serve_measure(n_maps: int, n_requests: int, log_n_max: float = 26.0,
             try:
                 for i in range(len(reqs)):
                     while ids[i] is None:
+                        if failed:
+                            return
                         time.sleep(0)
                     j = reqs[i][0]
                     # timestamps only (the outputs are not copied out)
@@ -763,23 +765,40 @@ def serve_measure(n_maps: int, n_requests: int, log_n_max: float = 26.0,
         th = threading.Thread(target=waiter)
         th.start()
         total = sum(len(r[1]) for r in reqs)
-        g = np.random.default_rng(7)
         mean_n = total / len(reqs)
         start = time.perf_counter()
-        t_next = start
-        rid = ctypes.c_uint64()
-        for i, (j, ops, keys, vin, ptrs) in enumerate(reqs):
-            if rate_ops:
-                t_next += g.exponential(mean_n / rate_ops)
-                while time.perf_counter() < t_next:
-                    pass
-            rc = B.bolt_server_submit(srv._s, mids[j], ptrs[0], ptrs[1], ptrs[2], len(ops),
-                                      ctypes.byref(rid))
+
+        def submit_many(lo, hi):
+            P = ctypes.c_void_p * (hi - lo)
+            part = reqs[lo:hi]
+            mids_a = np.array([mids[r[0]] for r in part], dtype=np.uint32)
+            ns_a = np.array([len(r[1]) for r in part], dtype=np.uint32)
+            po, pk, pv = (P(*[r[4][x] for r in part]) for x in range(3))
+            out = np.zeros(hi - lo, dtype=np.uint64)
+            rc = B.bolt_server_submit_many(srv._s, hi - lo, mids_a.ctypes.data, po, pk, pv,
+                                           ns_a.ctypes.data, out.ctypes.data)
             if rc != 0:
-                raise RuntimeError(f"submit: {B.bolt_strerror(rc).decode()}")
-            ids[i] = rid.value
-            if failed:
-                break
+                raise RuntimeError(f"submit_many: {B.bolt_strerror(rc).decode()}")
+            for i in range(lo, hi):
+                ids[i] = int(out[i - lo])
+
+        if not rate_ops:
+            # closed loop: every request queued by one call (its arrival time
+            # is the call's; the copies into the server count)
+            submit_many(0, len(reqs))
+        else:
+            # open loop: Poisson arrival times at rate_ops; whenever requests
+            # are due, all of them are queued by one call (a request's
+            # arrival is that call), so the client keeps up with the rate
+            arrive = np.cumsum(np.random.default_rng(7).exponential(mean_n / rate_ops, len(reqs)))
+            k = 0
+            while k < len(reqs) and not failed:
+                m = int(np.searchsorted(arrive, time.perf_counter() - start, side="right"))
+                if m > k:
+                    submit_many(k, m)
+                    k = m
+                else:
+                    time.sleep(0)
         done_ev.wait()
         th.join()
         if failed:

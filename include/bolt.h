@@ -478,6 +478,17 @@ BOLT_API int bolt_server_add_map(bolt_server_t* s, uint64_t N, uint32_t val_byte
 BOLT_API int bolt_server_map_state(bolt_server_t* s, uint32_t map_id);
 /* remove once its queued requests are served; frees its memory */
 BOLT_API int bolt_server_remove_map(bolt_server_t* s, uint32_t map_id);
+/* bolt_server_submit_many -- queue `count` requests at once: request j is
+ * ns[j] ops on map map_ids[j] with HOST arrays ops[j], keys[j], vals_in[j]
+ * (each as bolt_server_submit takes them, copied); req_ids[j] receives its
+ * id.  All requests are checked first: on any error (BOLT_E_ARG, BOLT_E_STATE
+ * for a removed map, BOLT_E_NOMEM) none is queued.  Queued in array order,
+ * under one lock, with one wake-up of the scheduler: a client with many
+ * requests ready pays one call instead of one per request. */
+BOLT_API int bolt_server_submit_many(bolt_server_t* s, uint32_t count, const uint32_t* map_ids,
+                                     const uint8_t* const* ops, const void* const* keys,
+                                     const void* const* vals_in, const uint32_t* ns,
+                                     uint64_t* req_ids);
 /* queue a request (HOST pointers, copied): n <= max_batch ops */
 BOLT_API int bolt_server_submit(bolt_server_t* s, uint32_t map_id, const uint8_t* ops,
                                 const void* keys, const void* vals_in, uint32_t n,

@@ -131,6 +131,7 @@ _SIGS = {
     "bolt_server_map_state": ([_P, _u32], _i),
     "bolt_server_remove_map": ([_P, _u32], _i),
     "bolt_server_submit": ([_P, _u32, _P, _P, _P, _u32, ctypes.POINTER(_u64)], _i),
+    "bolt_server_submit_many": ([_P, _u32, _P, _P, _P, _P, _P, _P], _i),
     "bolt_server_wait": ([_P, _u64, _P, _P, ctypes.POINTER(bolt_req_info_t), _i], _i),
     "bolt_server_map_batches": ([_P, _u32, _P, _u64, ctypes.POINTER(_u64)], _i),
     "bolt_server_map_handle": ([_P, _u32, ctypes.POINTER(_P)], _i),
@@ -446,6 +447,26 @@ class BoltServer:
         _check(bolt_server_submit(self._s, mid, _np_ptr(ops), _np_ptr(keys), _np_ptr(vin),
                                   len(ops), ctypes.byref(rid)), "bolt_server_submit")
         return rid.value
+
+    def submit_many(self, reqs) -> list:
+        """Queue several requests in one call: reqs = [(map id, ops, keys,
+        vals_in), ...]; returns their ids."""
+        arrs = []
+        for mid, ops, keys, vin in reqs:
+            arrs.append((mid, np.ascontiguousarray(ops, dtype=np.uint8),
+                         np.ascontiguousarray(keys, dtype=np.uint64),
+                         np.ascontiguousarray(vin, dtype=np.uint8)))
+        c = len(arrs)
+        mids = np.array([a[0] for a in arrs], dtype=np.uint32)
+        ns = np.array([len(a[1]) for a in arrs], dtype=np.uint32)
+        P = ctypes.c_void_p * max(c, 1)
+        po = P(*[a[1].ctypes.data for a in arrs])
+        pk = P(*[a[2].ctypes.data for a in arrs])
+        pv = P(*[a[3].ctypes.data for a in arrs])
+        ids = np.zeros(max(c, 1), dtype=np.uint64)
+        _check(bolt_server_submit_many(self._s, c, _np_ptr(mids), po, pk, pv, _np_ptr(ns),
+                                       _np_ptr(ids)), "bolt_server_submit_many")
+        return [int(x) for x in ids[:c]]
 
     def wait(self, rid: int, n: int, mid: int, timeout_ms: int = -1):
         vout = np.zeros((n, self.vb[mid]), dtype=np.uint8)

@@ -455,6 +455,65 @@ int bolt_server_submit(bolt_server_t* s, uint32_t map_id, const uint8_t* ops, co
   return BOLT_OK;
 }
 
+int bolt_server_submit_many(bolt_server_t* s, uint32_t count, const uint32_t* map_ids,
+                            const uint8_t* const* ops, const void* const* keys,
+                            const void* const* vals_in, const uint32_t* ns, uint64_t* req_ids) {
+  if (!s || (count && (!map_ids || !ops || !keys || !vals_in || !ns || !req_ids))) return BOLT_E_ARG;
+  const double t = s->now_us();  // every request arrives with the call
+  std::vector<uint64_t> vbs(count);
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (uint32_t j = 0; j < count; j++) {
+      Map* m = find_map(s, map_ids[j]);
+      if (!m) return BOLT_E_ARG;
+      if (m->state == MAP_REMOVED || m->remove_requested) return BOLT_E_STATE;
+      vbs[j] = m->vb;
+    }
+  }
+  for (uint32_t j = 0; j < count; j++) {
+    if (ns[j] == 0 || ns[j] > s->max_batch || !ops[j] || !keys[j] || !vals_in[j]) return BOLT_E_ARG;
+    for (uint32_t i = 0; i < ns[j]; i++)
+      if (ops[j][i] > BOLT_DEL) return BOLT_E_ARG;
+  }
+  // copies outside the lock
+  std::vector<Request*> rs(count, nullptr);
+  for (uint32_t j = 0; j < count; j++) {
+    Request* r = new (std::nothrow) Request();
+    if (!r) {
+      for (Request* q : rs) delete q;
+      return BOLT_E_NOMEM;
+    }
+    const uint32_t n = ns[j];
+    r->map = map_ids[j];
+    r->n = n;
+    r->ops.assign(ops[j], ops[j] + n);
+    r->keys.assign(static_cast<const uint64_t*>(keys[j]), static_cast<const uint64_t*>(keys[j]) + n);
+    r->vin.assign(static_cast<const uint8_t*>(vals_in[j]),
+                  static_cast<const uint8_t*>(vals_in[j]) + (uint64_t)n * vbs[j]);
+    rs[j] = r;
+  }
+  std::unique_lock<std::mutex> lock(s->mu);
+  // a map removed while the requests were copied: queue none
+  for (uint32_t j = 0; j < count; j++) {
+    Map* m = find_map(s, map_ids[j]);
+    if (m->state == MAP_REMOVED || m->remove_requested) {
+      for (Request* q : rs) delete q;
+      return BOLT_E_STATE;
+    }
+  }
+  for (uint32_t j = 0; j < count; j++) {
+    Request* r = rs[j];
+    r->id = s->next_id++;
+    r->t_submit = t;
+    s->requests[r->id] = r;
+    find_map(s, map_ids[j])->queue.push_back(r);
+    req_ids[j] = r->id;
+  }
+  s->work_seq.fetch_add(1);
+  s->work_cv.notify_one();
+  return BOLT_OK;
+}
+
 int bolt_server_wait(bolt_server_t* s, uint64_t req_id, void* vals_out, uint8_t* status_out,
                      bolt_req_info_t* info, int timeout_ms) {
   if (!s) return BOLT_E_ARG;

@@ -163,6 +163,43 @@ def test_sixteen_maps_full_batches_match_oracle():
     srv.close()
 
 
+def test_submit_many_matches_dict_and_rejects_all_or_nothing():
+    """Requests of four maps queued by one bolt_server_submit_many call
+    (interleaved, in array order per map) give each request the values and
+    status of a plain dict applying that map's requests alone, in order.  A
+    call with one bad op code queues nothing (BOLT_E_ARG)."""
+    vb, n_req = 24, 20
+    sizes = [1 << 12, 1 << 14, 1 << 15, 1 << 17]
+    srv = B.BoltServer(hbm_budget=32 << 30, max_batch=4096)
+    maps, data, reqs = [], [], []
+    for j, N in enumerate(sizes):
+        keys, vals = W.records(N, vb, 1300 + j)
+        maps.append(srv.add_map(N, vb, keys, vals, 1400 + j))
+        data.append((keys, vals))
+        reqs.append(_requests(N, n_req, vb, 1500 + j, 4096))
+    batch = [(maps[j], *reqs[j][r]) for r in range(n_req) for j in range(len(sizes))]
+    bad = [list(x) for x in batch[:3]]
+    bad[2][1] = bad[2][1].copy()
+    bad[2][1][0] = 7
+    with pytest.raises(B.BoltError) as e:
+        srv.submit_many([tuple(x) for x in bad])
+    assert e.value.rc == B.BOLT_E_ARG
+    ids = srv.submit_many(batch)
+    assert len(set(ids)) == len(batch)
+    for j, (keys, vals) in enumerate(data):
+        model = DictModel(keys, vals)
+        for r in range(n_req):
+            ops, k, vin = reqs[j][r]
+            rid = ids[r * len(sizes) + j]
+            rc, vout, st, info = srv.wait(rid, len(ops), maps[j], timeout_ms=300000)
+            assert rc == 0
+            ev, es = model.apply(ops, k, vin, vb)
+            assert np.array_equal(vout, ev) and np.array_equal(st, es), f"map {j} request {r}"
+        # the rejected call queued nothing: the map ran exactly these ops
+        assert srv.batches(maps[j]).sum() == sum(len(reqs[j][r][0]) for r in range(n_req))
+    srv.close()
+
+
 def test_admission_by_budget():
     import time
     vb, N = 24, 1 << 16
