@@ -528,7 +528,7 @@ enum ProfClass : int {
   P_KSORT_TILE = 11,    // key-uniqueness check: bitonic in-tile steps
   P_FLUSH = 12,         // access: written pages copied to the host
   P_AHEAD = 13,         // access: lookahead search + page reads (side stream)
-  P_PAGE_GROUP = 14,    // build: host records grouped by page (counting scatter)
+  P_PAGE_GROUP = 14,    // build: host records grouped by page (two bucket passes)
   P_PAGES = 15,         // access: distinct pages, trace
   P_FINDEXEC = 16,      // access: find_remove + Get/Put/Delete semantics
   P_REMAP = 17,         // access: P2C remap

@@ -610,3 +610,27 @@ def test_link_probe_leaves_pages_unchanged():
     _run_batch(o, g, ops, k, vin, "after the probe")
     _assert_state_equal(o, g, "after the probe")
     o.close(); g.close()
+
+
+@pytest.mark.parametrize("vb", [248, 504])
+@pytest.mark.parametrize("batch,sealed", [(None, False), (16, False), (None, True), (16, True)])
+def test_largest_values_match_oracle(vb, batch, sealed):
+    """Values up to the ABI's limit (504 B; pages of several 512-byte chunks,
+    ~3.3 and ~6.7 KB here) through the multi-kernel chain (batches of 700)
+    and the fused single-CTA launch (batches of 16, fewer eviction warps fit
+    its shared memory), plain and sealed: values, status, page bytes, loads,
+    rows and trace equal the oracle's."""
+    N = 1 << 12
+    o = O.OracleMap(N, vb, batch=batch, integrity=sealed)
+    g = B.BoltMap(N, vb, trace=True, batch=batch, integrity=sealed)
+    assert o.info() == g.info()
+    assert g.info()["page_bytes"] > 3000
+    keys, vals = W.records(3000, vb, 0x1AD0 + vb)
+    assert o.init(keys, vals, 12) == 0 and g.init(keys, vals, 12) == 0
+    _assert_state_equal(o, g, "after build")
+    for rep in range(2):
+        ops, k, vin = W.op_stream(3000, 700, vb, 0x1AD8 + rep, get_frac=0.5, del_frac=0.1,
+                                  absent_frac=0.2)
+        _run_batch(o, g, ops, k, vin, f"rep {rep}")
+        _assert_state_equal(o, g, f"after rep {rep}")
+    o.close(); g.close()
