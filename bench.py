@@ -499,10 +499,16 @@ def run_bolt(args) -> None:
             eb += b_s
             ea += a_s
         assert np.array_equal(hvout.numpy(), vout), "host and device paths agree"
-        e2e = {"value": round(n_acc * e2e_steps / ea, 1), "unit": "accesses/s",
-               "h2d_bytes_per_step": N * (8 + VAL_BYTES) + n_acc * (1 + 8 + VAL_BYTES),
-               "d2h_bytes_per_step": n_acc * (VAL_BYTES + 1),
-               "build_mrec_s": round(N * e2e_steps / eb / 1e6, 2), "steps": e2e_steps}
+        # whole job over ranks, as for the headline value: the slowest rank's
+        # times, the sum of the work and of the copies
+        agg_e = aggregate({"build_s": eb, "access_s": ea, "step_s": eb + ea,
+                           "records": float(N * e2e_steps),
+                           "accesses": float(n_acc * e2e_steps)}, world, group)
+        e2e = {"value": round(agg_e["accesses"] / agg_e["access_s"], 1), "unit": "accesses/s",
+               "h2d_bytes_per_step": world * (N * (8 + VAL_BYTES) + n_acc * (1 + 8 + VAL_BYTES)),
+               "d2h_bytes_per_step": world * n_acc * (VAL_BYTES + 1),
+               "build_mrec_s": round(agg_e["records"] / agg_e["build_s"] / 1e6, 2),
+               "steps": e2e_steps}
         del hk, hv, ho, hak, havin, hvout, hst
 
     # The access path's roofline (the headline value): per batch, every
@@ -515,7 +521,8 @@ def run_bolt(args) -> None:
     page_bytes = info["page_bytes"]
     per_op = 2.0 * info["M"] / info["B"]  # expected host pages read per op
     probe = m.probe_link(int(round(per_op * BATCH)), 50)
-    acc_rate = agg["accesses"] / agg["access_s"]
+    # (per GPU: each rank's share of the work over the slowest rank's time)
+    acc_rate = agg["accesses"] / world / agg["access_s"]
     batch_s = BATCH / acc_rate
     link_bytes_per_batch = 2 * per_op * BATCH * page_bytes
     ach = link_bytes_per_batch / batch_s / 1e9
