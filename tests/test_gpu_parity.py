@@ -634,3 +634,46 @@ def test_largest_values_match_oracle(vb, batch, sealed):
         _run_batch(o, g, ops, k, vin, f"rep {rep}")
         _assert_state_equal(o, g, f"after rep {rep}")
     o.close(); g.close()
+
+
+def test_fused_batches_after_kernels_that_write_their_inputs():
+    """Each call's inputs are written by torch kernels on the same stream
+    right before it (keys XOR-ed into place, values and ops copied from
+    device scratch), then run as batches of one op (fused launches chained by
+    programmatic dependent launch, from the second batch on reading their
+    inputs before their wait).  Repeated over many calls; results and state
+    equal the oracle's."""
+    import torch
+    N, vb = 1 << 12, 16
+    o, g = _pair(N, vb, trace=False)
+    keys, vals = W.records(2000, vb, 91)
+    assert o.init(keys, vals, 5) == 0 and g.init(keys, vals, 5) == 0
+    stream = torch.cuda.Stream()
+    mask = np.uint64(0x9E3779B97F4A7C15)
+    n, calls = 24, 12
+    t_out = torch.zeros((n, vb), dtype=torch.uint8, device="cuda")
+    t_st = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    for c in range(calls):
+        ops, k, vin = W.op_stream(2000, n, vb, 920 + c, get_frac=0.5, del_frac=0.1,
+                                  absent_frac=0.2)
+        # the keys reach the device masked; a kernel on the call's stream
+        # unmasks them in place just before the call
+        src_k = torch.from_numpy((k ^ mask).view(np.int64)).cuda()
+        src_v = torch.from_numpy(vin).cuda()
+        src_o = torch.from_numpy(ops).cuda()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            t_k = torch.bitwise_xor(src_k, torch.tensor(np.int64(mask.view(np.int64)),
+                                                        device="cuda"))
+            t_vin = src_v.clone()
+            t_ops = src_o.clone()
+        assert g.access_device_batches(t_ops, t_k, t_vin, t_out, t_st, 1, stream=stream) == 0
+        stream.synchronize()
+        for b in range(n):
+            rc, vo, so = o.access(ops[b:b + 1], k[b:b + 1], vin[b:b + 1])
+            assert rc == 0
+            assert np.array_equal(vo[0], t_out[b].cpu().numpy()), f"call {c} op {b}"
+            assert so[0] == t_st[b].item(), f"call {c} op {b}"
+    assert g.sync() == 0
+    _assert_state_equal(o, g, "after the calls", trace=False)
+    o.close(); g.close()
