@@ -1176,7 +1176,8 @@ __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, 
 // current round): bump the counts of its decided bin (and row, for a new
 // key), take a ring slot, write its entries.  All 32 lanes of the warp call.
 __device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& b, uint32_t i,
-                                               bool go, RingWin* w = nullptr) {
+                                               bool go, RingWin* w = nullptr,
+                                               bool stash_peak = true) {
   // the bin's load, the row's count (a new key), the destination page's
   // reverse-index count (a host bin) and the free-ring position are taken
   // together (independent atomics in flight at once), then checked; a count
@@ -1202,7 +1203,7 @@ __device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& 
     }
   }
   if (go) remap_place(m, b, i, dest, pos, rev_slot, w);
-  stat_place(m, go, dest < m.K, new_load);
+  stat_place(m, go, dest < m.K, new_load, stash_peak);
 }
 
 __global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
@@ -1435,7 +1436,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   __shared__ uint32_t s_posq[2 * FUSED_MAX_OPS], s_slot[2 * FUSED_MAX_OPS],
       s_dslot[2 * FUSED_MAX_OPS], s_dpage[2 * FUSED_MAX_OPS];
   __shared__ uint32_t s_ht[FUSED_TABLE], s_htmin[FUSED_TABLE], s_dcount;
-  __shared__ uint8_t s_initp[FUSED_MAX_OPS], s_fpres[FUSED_MAX_OPS];
+  __shared__ uint8_t s_initp[FUSED_MAX_OPS], s_fpres[FUSED_MAX_OPS], s_defer[FUSED_MAX_OPS];
   __shared__ RingWin s_ring;
   static_assert(RING_WIN >= FUSED_MAX_OPS, "the remap's takes fit the ring window");
   const int lane = threadIdx.x & 31;
@@ -1674,14 +1675,30 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   __syncthreads();
   // 5. Get/Put/Delete semantics (the last warp, lane per op) beside the
   //    write-back with eviction (the other warps, warp per page, straight to
-  //    the host as well); a remap of one round decides its bins here too
-  //    (eviction changes no load or row count)
+  //    the host as well).  A remap of one round also decides its bins here
+  //    (eviction changes no load or row count) and, when the ring window
+  //    holds a slot for every take, places every key whose bin is not a page
+  //    of this batch: such a placement touches none of the pages, stash lists
+  //    or ring slots the eviction reads.  The others wait for the eviction;
+  //    the stash peak is then taken at the end of the batch.
   const bool one_round = n <= m.Wr;
+  const bool early = one_round && s_ring.tail - s_ring.head >= n;
   if (wid == nwarps - 1) {
     if ((uint32_t)lane < n) exec_op(m, L, lane);
     __syncwarp();
-    if (one_round && (uint32_t)lane < n && s_leader[lane] == (uint32_t)lane && s_fpres[lane])
-      decide_op_l2(m, L, lane);
+    const bool act =
+        one_round && (uint32_t)lane < n && s_leader[lane] == (uint32_t)lane && s_fpres[lane];
+    if (act) decide_op_l2(m, L, lane);
+    __syncwarp();
+    if (early) {
+      bool in_batch = false;
+      if (act && s_rdest[lane] >= m.K) {
+        const uint32_t q = s_rdest[lane] - (uint32_t)m.K, nd = s_dcount;
+        for (uint32_t d = 0; d < nd; d++) in_batch |= s_dpage[d] == q;
+      }
+      if ((uint32_t)lane < FUSED_MAX_OPS) s_defer[lane] = act && in_batch;
+      remap_apply_op(m, L, lane, act && !in_batch, &s_ring, false);
+    }
   } else if (wid < evict_warps) {
     const uint32_t nd = s_dcount;
     for (uint32_t e = wid; e < nd; e += evict_warps)
@@ -1689,8 +1706,11 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   }
   __syncthreads();
   // 6. P2C remap in rounds of W_r op slots (warp 0, lane per op): decide on
-  //    round-start counts (a single round decided above), then place
-  if (wid == 0) {
+  //    round-start counts (a single round decided above), then place; with
+  //    the early placements above, only the ones that waited for the eviction
+  if (wid == 0 && early) {
+    remap_apply_op(m, L, lane, s_defer[lane] != 0, &s_ring, false);
+  } else if (wid == 0) {
     for (uint64_t lo = 0; lo < n; lo += m.Wr) {
       const uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
       const uint32_t i = lane;
@@ -1702,6 +1722,10 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     }
   }
   __syncthreads();
+  // the stash peak of a batch whose placements ran beside its eviction: the
+  // count it ends with (what a remap after the eviction would have reached)
+  if (early && threadIdx.x == 0)
+    atomicMax(m.stat + ST_PEAK_STASH, atomicAdd(m.stat + ST_STASH, 0ull));
   if (b.h_out) {
     // results and the error word back to the caller's pinned staging, then
     // the completion word the caller waits for (every thread's writes are

@@ -229,8 +229,10 @@ enum : int { ST_HBM = 0, ST_STASH = 1, ST_PEAK_HBM = 2, ST_PEAK_STASH = 3, ST_PE
 // A warp's placements of the remap phase: `placed` lanes put one item into
 // the HBM store (hbm) or the stash, a bin reaching `new_load`.  All 32 lanes
 // call; one lane per warp updates the counters.
+// (stash_peak = false: the caller takes the stash peak at the end of the
+// batch instead, because evictions may still be running beside this remap)
 __device__ __forceinline__ void stat_place(const MapDev& m, bool placed, bool hbm,
-                                           uint32_t new_load) {
+                                           uint32_t new_load, bool stash_peak = true) {
   const uint32_t hm = __ballot_sync(0xffffffffu, placed && hbm);
   const uint32_t sm = __ballot_sync(0xffffffffu, placed && !hbm);
   const uint32_t top = __reduce_max_sync(0xffffffffu, placed ? new_load : 0u);
@@ -241,7 +243,10 @@ __device__ __forceinline__ void stat_place(const MapDev& m, bool placed, bool hb
     }
     if (sm) {
       const unsigned long long c = __popc(sm);
-      atomicMax(m.stat + ST_PEAK_STASH, atomicAdd(m.stat + ST_STASH, c) + c);
+      if (stash_peak)
+        atomicMax(m.stat + ST_PEAK_STASH, atomicAdd(m.stat + ST_STASH, c) + c);
+      else
+        atomicAdd(m.stat + ST_STASH, c);
     }
     if (top) atomicMax(m.stat + ST_PEAK_LOAD, (unsigned long long)top);
   }
