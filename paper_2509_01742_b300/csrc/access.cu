@@ -650,6 +650,17 @@ __global__ void __launch_bounds__(256) k_open(MapDev m, BatchDev b) {
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
+// every 128-byte line of [p, p + bytes) into L2
+__device__ __forceinline__ void prefetch_range_l2(const void* p, uint32_t bytes) {
+  const uintptr_t e = (uintptr_t)p + bytes;
+  for (uintptr_t a = (uintptr_t)p & ~(uintptr_t)127; a < e; a += 128)
+    prefetch_l2(reinterpret_cast<const void*>(a));
+}
+// [p, p + bytes) into L2 by the bulk-copy unit: p 16-byte aligned, bytes a
+// multiple of 16; exactly these bytes are read
+__device__ __forceinline__ void prefetch_bulk_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // While a claimed page's host read is in flight: bring what its eviction will
 // read into L2 -- the reverse-index count and list, then each listed stash
@@ -777,6 +788,9 @@ template <bool SEALED>
 __global__ void __launch_bounds__(256) k_lookup(MapDev m, BatchDev b, uint32_t n) {
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
+  // the previous batch's end counts into the peaks (a fused batch takes none
+  // while it places); nothing changes a count while this kernel runs
+  if (blockIdx.x == 0 && threadIdx.x == 0) stat_end_peaks(m);
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw)
     lookup_op<SEALED>(m, b, i, lane);
   dep_trigger();
@@ -937,10 +951,12 @@ __device__ __forceinline__ void exec_op(const MapDev& m, const BatchDev& b, uint
 // line 10): `plain` is this warp's page_bytes + 512 bytes of shared memory.
 // The ciphertext goes to the page's slot in dbuf (the next batch reads it
 // there while the host copy is in flight) and, with to_host, also straight
-// to the host page.
+// to the host page.  `ks` (or null): the page's new key stream, computed
+// ahead in shared memory.
 template <bool SEALED>
 __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, uint32_t e,
-                                          uint8_t* plain, bool to_host) {
+                                          uint8_t* plain, bool to_host,
+                                          const uint8_t* ks = nullptr) {
   const int lane = threadIdx.x & 31;
   ulonglong2* items = reinterpret_cast<ulonglong2*>(plain + m.page_bytes);
   const uint32_t d = b.dslot[e];
@@ -1013,7 +1029,7 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
   // the old plaintext in dbuf is no longer read: the ciphertext replaces it
   // and k_flush copies it to the host page (or this warp does, below)
   uint8_t* cipher = b.dbuf + (uint64_t)d * m.page_bytes;
-  page_encrypt_to<SEALED>(m, plain, cipher, q, ver);
+  page_encrypt_to<SEALED>(m, plain, cipher, q, ver, ks);
   if (to_host)  // each lane stores the 16-byte pieces it encrypted
     for (uint32_t o = 16 * lane; o < m.page_bytes; o += 512)
       *reinterpret_cast<uint4*>(m.pages + q * m.page_bytes + o) =
@@ -1172,12 +1188,21 @@ __device__ __forceinline__ void remap_place(const MapDev& m, const BatchDev& b, 
   }
 }
 
+// What a placement's counter atomics would return, known beforehand: the
+// bin's new load, the row's count before it (a new key) and the reverse-index
+// entry it takes (a host bin).
+struct PlaceCounts {
+  uint32_t load, row, rev;
+};
+
 // place op i if `go` (a leader whose key is present after the batch, in the
 // current round): bump the counts of its decided bin (and row, for a new
 // key), take a ring slot, write its entries.  All 32 lanes of the warp call.
+// With `known`, the counts are bumped by atomics nothing waits for.
 __device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& b, uint32_t i,
                                                bool go, RingWin* w = nullptr,
-                                               bool stash_peak = true) {
+                                               bool peaks = true,
+                                               const PlaceCounts* known = nullptr) {
   // the bin's load, the row's count (a new key), the destination page's
   // reverse-index count (a host bin) and the free-ring position are taken
   // together (independent atomics in flight at once), then checked; a count
@@ -1188,9 +1213,22 @@ __device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& 
   if (go) {
     dest = b.rdest[i];
     fresh = b.hit[i] == NONE32;
-    new_load = byte_inc(m.load, dest) + 1;
-    if (fresh) row_old = byte_inc(m.rowcnt, b.rrow[i]);
-    if (dest >= m.K) rev_slot = byte_inc(m.revcnt, dest - m.K);
+    if (known) {
+      byte_add(m.load, dest);
+      new_load = known->load;
+      if (fresh) {
+        byte_add(m.rowcnt, b.rrow[i]);
+        row_old = known->row;
+      }
+      if (dest >= m.K) {
+        byte_add(m.revcnt, dest - m.K);
+        rev_slot = known->rev;
+      }
+    } else {
+      new_load = byte_inc(m.load, dest) + 1;
+      if (fresh) row_old = byte_inc(m.rowcnt, b.rrow[i]);
+      if (dest >= m.K) rev_slot = byte_inc(m.revcnt, dest - m.K);
+    }
   }
   const unsigned long long pos = ring_take(m, go, w);
   if (go) {
@@ -1203,7 +1241,7 @@ __device__ __forceinline__ void remap_apply_op(const MapDev& m, const BatchDev& 
     }
   }
   if (go) remap_place(m, b, i, dest, pos, rev_slot, w);
-  stat_place(m, go, dest < m.K, new_load, stash_peak);
+  stat_place(m, go, dest < m.K, new_load, peaks);
 }
 
 __global__ void k_remap_apply(MapDev m, BatchDev b, uint32_t lo, uint32_t hi) {
@@ -1388,26 +1426,46 @@ static_assert(4 * FUSED_MAX_OPS <= FUSED_TABLE, "a small batch's page table fits
 
 // the P2C decision of op i on round-start counts read from L2: the counts
 // change by atomics between the rounds of this one launch
-__device__ __forceinline__ void decide_op_l2(const MapDev& m, const BatchDev& b, uint32_t i) {
+// With `c`, also the counts read for the decision: the chosen bin's load,
+// the chosen row's count and, for a host bin, its page's reverse-index count.
+// Every count is read at once (one round trip).
+__device__ __forceinline__ void decide_op_l2(const MapDev& m, const BatchDev& b, uint32_t i,
+                                             PlaceCounts* c = nullptr) {
   auto get = [](const uint32_t* w, uint64_t k) {
     return (__ldcg(w + (k >> 2)) >> ((uint32_t)(k & 3) * 8)) & 0xffu;
   };
   const uint64_t pr = b.rpair[i];
   const uint32_t p1 = (uint32_t)pr, p2 = (uint32_t)(pr >> 32);
-  b.rdest[i] = get(m.load, p1) <= get(m.load, p2) ? p1 : p2;
-  if (b.hit[i] == NONE32) {
-    const uint4 r4 = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
-    const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
-    uint32_t best = rr[0], bc = get(m.rowcnt, rr[0]);
+  const bool fresh = b.hit[i] == NONE32;
+  const uint4 r4 = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
+  const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+  const uint32_t l1 = get(m.load, p1), l2 = get(m.load, p2);
+  uint32_t r1 = 0, r2 = 0, rc[4] = {0, 0, 0, 0};
+  if (c) {
+    if (p1 >= m.K) r1 = get(m.revcnt, p1 - m.K);
+    if (p2 >= m.K) r2 = get(m.revcnt, p2 - m.K);
+  }
+  if (fresh) {
 #pragma unroll
-    for (int j = 1; j < 4; j++) {
-      const uint32_t c = get(m.rowcnt, rr[j]);
-      if (c < bc) {
+    for (int j = 0; j < 4; j++) rc[j] = get(m.rowcnt, rr[j]);
+  }
+  const bool first = l1 <= l2;
+  b.rdest[i] = first ? p1 : p2;
+  if (c) {
+    c->load = first ? l1 : l2;
+    c->rev = first ? r1 : r2;
+    c->row = 0;
+  }
+  if (fresh) {
+    uint32_t best = rr[0], bc = rc[0];
+#pragma unroll
+    for (int j = 1; j < 4; j++)
+      if (rc[j] < bc) {
         best = rr[j];
-        bc = c;
+        bc = rc[j];
       }
-    }
     b.rrow[i] = best;
+    if (c) c->row = bc;
   }
 }
 
@@ -1417,7 +1475,7 @@ constexpr uint32_t FUSED_VB_MAX = 504;
 template <bool SEALED>
 __global__ void __launch_bounds__(FUSED_THREADS)
     k_fused(MapDev m, BatchDev b, uint32_t n, uint64_t t0, uint32_t evict_warps,
-            uint32_t early_in) {
+            uint32_t early_in, const __grid_constant__ FusedInline inl) {
   extern __shared__ __align__(16) uint8_t sbuf[];
   // Everything the batch reads back within itself lives in shared memory:
   // the inputs, the grouping, pairs, rows, hits, the page table and its read
@@ -1465,28 +1523,34 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   if (threadIdx.x == 0) s_dcount = 0;
   // 1a. per op the DUMMY pair and the REMAP pair (one ChaCha20 block each,
   //     each kind in a warp of its own, lane = op)
-  if (wid < 2 && (uint32_t)lane < n) {
-    const uint32_t i = lane;
-    uint32_t p1, p2;
-    prf_pair(m, wid == 0 ? DOM_DUMMY : DOM_REMAP, t0 + i, p1, p2);
-    const uint64_t pr = (uint64_t)p1 | ((uint64_t)p2 << 32);
-    if (wid == 0) {
-      s_pair[i] = pr;
-    } else {
-      s_rpair[i] = pr;
-      // the remap will read these loads (an address only: nothing is read)
-      prefetch_l2(m.load + (p1 >> 2));
-      prefetch_l2(m.load + (p2 >> 2));
+  auto pairs = [&]() {
+    if (wid < 2 && (uint32_t)lane < n) {
+      const uint32_t i = lane;
+      uint32_t p1, p2;
+      prf_pair(m, wid == 0 ? DOM_DUMMY : DOM_REMAP, t0 + i, p1, p2);
+      const uint64_t pr = (uint64_t)p1 | ((uint64_t)p2 << 32);
+      if (wid == 0) {
+        s_pair[i] = pr;
+      } else {
+        s_rpair[i] = pr;
+        // the remap will read these loads (an address only: nothing is read)
+        prefetch_l2(m.load + (p1 >> 2));
+        prefetch_l2(m.load + (p2 >> 2));
+      }
     }
-  }
-  // 0. the inputs, laid out keys | vin | ops: straight from the caller's
-  //    pinned staging (16-byte reads over the link; the staging holds the
-  //    rounded-up tail), or from the device arrays; then (1b) per op the
-  //    position-map rows (one ChaCha20 block, warp 2, lane = op) and the
-  //    grouping (warp 3, n^2 compares: leader = first op on the key,
-  //    previous writer of each op, last writer of each key group)
-  auto inputs_rows_group = [&]() {
-    if (b.h_in) {
+  };
+  // 0. the inputs, laid out keys | vin | ops: from the launch's parameters,
+  //    straight from the caller's pinned staging (16-byte reads over the
+  //    link; the staging holds the rounded-up tail), or from the device
+  //    arrays; then (1b) per op the position-map rows (one ChaCha20 block,
+  //    warp 2, lane = op) and the grouping (warp 3, n^2 compares: leader =
+  //    first op on the key, previous writer of each op, last writer of each
+  //    key group)
+  auto inputs = [&]() {
+    if (inl.bytes) {
+      for (uint32_t w = threadIdx.x; w < (inl.bytes + 15) / 16; w += blockDim.x)
+        reinterpret_cast<uint4*>(s_in)[w] = inl.d[w];
+    } else if (b.h_in) {
       const uint32_t words = (n * (9 + m.vb) + 15) / 16;
       for (uint32_t w = threadIdx.x; w < words; w += blockDim.x)
         reinterpret_cast<uint4*>(s_in)[w] = reinterpret_cast<const uint4*>(b.h_in)[w];
@@ -1502,14 +1566,23 @@ __global__ void __launch_bounds__(FUSED_THREADS)
           L.ops[w - n - vw] = b.ops[w - n - vw];
       }
     }
-    __syncthreads();
+  };
+  auto rows_group = [&]() {
     if (wid == 2 && (uint32_t)lane < n) {
       const uint32_t i = lane;
       uint32_t rows[4];
       prf_rows(m, L.keys[i], rows);
       *reinterpret_cast<uint4*>(s_rows + 4 * i) = make_uint4(rows[0], rows[1], rows[2], rows[3]);
 #pragma unroll
-      for (int j = 0; j < 4; j++) prefetch_l2(m.rowcnt + (rows[j] >> 2));
+      for (int j = 0; j < 4; j++) {
+        prefetch_l2(m.rowcnt + (rows[j] >> 2));
+        // the rows the search reads (before the wait too: a line the
+        // previous kernel then writes is updated in L2 like any other)
+        const uint64_t at = (uint64_t)rows[j] * m.R;
+        prefetch_range_l2(m.pm_meta + at, 4 * m.R);
+        prefetch_range_l2(m.pm_key + at, 8 * m.R);
+        prefetch_range_l2(m.pm_bins + at, 8 * m.R);
+      }
     }
     if (wid == 3) {
       const bool mine = (uint32_t)lane < n;
@@ -1534,12 +1607,23 @@ __global__ void __launch_bounds__(FUSED_THREADS)
       }
     }
   };
-  if (early_in) inputs_rows_group();
+  // (with early_in the pairs, the rows and the grouping run side by side,
+  // after the inputs)
+  if (early_in) {
+    inputs();
+    __syncthreads();
+    pairs();
+    rows_group();
+  } else {
+    pairs();
+  }
   dep_wait();
   dep_trigger();
-  if (!early_in) inputs_rows_group();
-  // the remap's free value-store slot into L2
-  if (wid == 1 && lane == 0) prefetch_l2(m.ring + (*m.ring_ctr % m.vs_cap));
+  if (!early_in) {
+    inputs();
+    __syncthreads();
+    rows_group();
+  }
   __syncthreads();
   // 2. position-map search (warp per op): a hit reads its stored pair, every
   //    other op its DUMMY pair; the host bins of each read position.  A hit
@@ -1550,6 +1634,12 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     uint64_t fb = 0;
     if (s_leader[i] == i) found = pm_search(m, L, i, L.keys[i], lane, &fb, &fm);
     const uint64_t pr = found != NONE32 ? fb : s_pair[i];
+    if (lane < 2) {
+      // the op's host pages into L2 now, exactly their bytes: the reads in
+      // 2c start only after the page table is built
+      const uint32_t p = lane == 0 ? (uint32_t)pr : (uint32_t)(pr >> 32);
+      if (p >= m.K) prefetch_bulk_l2(m.pages + (uint64_t)(p - m.K) * m.page_bytes, m.page_bytes);
+    }
     if (lane == 0) {
       s_hit[i] = found;
       s_hmeta[i] = fm;
@@ -1616,6 +1706,9 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   //     slot's buffer; meanwhile bring its eviction's data into L2.  The
   //     last warp first reads the free ring's window for the remap.
   if (wid == nwarps - 1) {
+    // (the previous batch's end counts into the peaks: this batch's
+    // placements take none)
+    if (lane == 1) stat_end_peaks(m);
     const unsigned long long hd = m.ring_ctr[0], tl = m.ring_ctr[1];
     if (lane < (int)RING_WIN && hd + lane < tl) s_ring.v[lane] = m.ring[(hd + lane) % m.vs_cap];
     if (lane == 0) {
@@ -1640,6 +1733,20 @@ __global__ void __launch_bounds__(FUSED_THREADS)
         if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + 16 * lane);
       }
       page_in<SEALED>(m, L, h, q, kind, src, x, lane);
+    }
+    // meanwhile warp nd + d computes page d's key stream for its write-back
+    // (version + 1) into its own eviction buffer, which the eviction of
+    // page d then only XORs: the write-back's ChaCha20 leaves the path
+    // when every page has a spare warp and buffer
+    if (2 * nd <= evict_warps && wid >= nd && wid < 2 * nd) {
+      const uint32_t d = wid - nd;
+      const uint64_t q = s_dpage[d], v = m.version[q] + 1;
+      uint8_t* ks = sbuf + (size_t)wid * (m.page_bytes + 32 * 16);
+      for (uint32_t c = 0; c < m.page_bytes; c += 512) {
+        const uint4 k4 = chacha_quad(m.kenc, c / 64 + (lane >> 2) + (SEALED ? 1u : 0u),
+                                     (uint32_t)q, (uint32_t)v, (uint32_t)(v >> 32));
+        if (c + 16 * lane < m.page_bytes) *reinterpret_cast<uint4*>(ks + c + 16 * lane) = k4;
+      }
     }
   }
   __syncthreads();
@@ -1688,7 +1795,8 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     __syncwarp();
     const bool act =
         one_round && (uint32_t)lane < n && s_leader[lane] == (uint32_t)lane && s_fpres[lane];
-    if (act) decide_op_l2(m, L, lane);
+    PlaceCounts pc{0, 0, 0};
+    if (act) decide_op_l2(m, L, lane, &pc);
     __syncwarp();
     if (early) {
       bool in_batch = false;
@@ -1697,12 +1805,28 @@ __global__ void __launch_bounds__(FUSED_THREADS)
         for (uint32_t d = 0; d < nd; d++) in_batch |= s_dpage[d] == q;
       }
       if ((uint32_t)lane < FUSED_MAX_OPS) s_defer[lane] = act && in_batch;
-      remap_apply_op(m, L, lane, act && !in_batch, &s_ring, false);
+      // what each placement's counter atomics would return: the counts read
+      // for the decision (nothing else changes them before these
+      // placements) plus the placements of lower lanes on the same bin or
+      // row
+      const bool go = act && !in_batch, fresh = go && s_hit[lane] == NONE32;
+      const uint32_t below = (1u << lane) - 1u;
+      const uint32_t same_bin =
+          __match_any_sync(0xffffffffu, go ? s_rdest[lane] : NONE32) & __ballot_sync(0xffffffffu, go);
+      const uint32_t same_row =
+          __match_any_sync(0xffffffffu, fresh ? s_rrow[lane] : NONE32) &
+          __ballot_sync(0xffffffffu, fresh);
+      pc.load += __popc(same_bin & below) + 1;
+      pc.rev += __popc(same_bin & below);
+      pc.row += __popc(same_row & below);
+      remap_apply_op(m, L, lane, go, &s_ring, false, &pc);
     }
   } else if (wid < evict_warps) {
-    const uint32_t nd = s_dcount;
+    const uint32_t nd = s_dcount, per_warp = m.page_bytes + 32 * 16;
+    const bool ks_pre = 2 * nd <= evict_warps;
     for (uint32_t e = wid; e < nd; e += evict_warps)
-      evict_one<SEALED>(m, L, e, sbuf + (size_t)wid * (m.page_bytes + 32 * 16), true);
+      evict_one<SEALED>(m, L, e, sbuf + (size_t)wid * per_warp, true,
+                        ks_pre ? sbuf + (size_t)(nd + e) * per_warp : nullptr);
   }
   __syncthreads();
   // 6. P2C remap in rounds of W_r op slots (warp 0, lane per op): decide on
@@ -1722,10 +1846,6 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     }
   }
   __syncthreads();
-  // the stash peak of a batch whose placements ran beside its eviction: the
-  // count it ends with (what a remap after the eviction would have reached)
-  if (early && threadIdx.x == 0)
-    atomicMax(m.stat + ST_PEAK_STASH, atomicAdd(m.stat + ST_STASH, 0ull));
   if (b.h_out) {
     // results and the error word back to the caller's pinned staging, then
     // the completion word the caller waits for (every thread's writes are
@@ -1741,9 +1861,10 @@ __global__ void __launch_bounds__(FUSED_THREADS)
 }
 
 cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
-                         cudaStream_t st, bool early_in) {
+                         cudaStream_t st, bool early_in, const FusedInline* inl) {
   if (n == 0) return cudaSuccess;
   if (n > FUSED_MAX_OPS || b.ht_mask + 1 != FUSED_TABLE) return cudaErrorInvalidValue;
+  if (inl && inl->bytes != n * (9 + m.vb)) return cudaErrorInvalidValue;
   ProfSpan whole(P_ACCESS, st);
   if (m.vb > FUSED_VB_MAX) return cudaErrorInvalidValue;
   auto kf = m.integrity ? k_fused<true> : k_fused<false>;
@@ -1763,7 +1884,10 @@ cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_
   if (smem > budget) return cudaErrorInvalidValue;
   cudaError_t e = raise_smem_limit((const void*)kf, smem);
   if (e != cudaSuccess) return e;
-  e = launch_dependent(kf, 1, FUSED_THREADS, smem, st, m, b, n, t0, ew, early_in ? 1u : 0u);
+  FusedInline none;
+  none.bytes = 0;
+  e = launch_dependent(kf, 1, FUSED_THREADS, smem, st, m, b, n, t0, ew, early_in ? 1u : 0u,
+                       inl ? *inl : none);
   if (e != cudaSuccess) return e;
   count_launch();
   return cudaSuccess;

@@ -127,9 +127,20 @@ cudaError_t launch_prep(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t
 // (b.h_in, or b.keys / b.vin / b.ops) are complete even if that kernel is
 // not (host staging written before the launch, or the previous kernel is an
 // earlier fused batch of the same call), so they are read before the wait.
+// inl (or null): the batch's inputs carried in the launch's own parameters,
+// in the staging's layout (keys as 8-byte words | values | ops), so the
+// kernel reads none of them from host memory; they then take the place of
+// b.h_in / b.keys / b.vin / b.ops.
 constexpr uint32_t FUSED_MAX_OPS = 32;
+constexpr uint32_t FUSED_INLINE_MAX = 256;
+struct FusedInline {
+  uint32_t bytes;  // 0: no inputs here
+  uint32_t pad[3];
+  uint4 d[FUSED_INLINE_MAX / 16];
+};
 cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_t t0,
-                         cudaStream_t st, bool early_in = false);
+                         cudaStream_t st, bool early_in = false,
+                         const FusedInline* inl = nullptr);
 cudaError_t launch_main(const MapDev& m, const BatchDev& b, uint32_t n, cudaStream_t st,
                         const FlushCtx& fc);
 // The lookahead part of a batch (b.la_on = 1), after its preparation:

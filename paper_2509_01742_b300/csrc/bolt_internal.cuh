@@ -84,6 +84,11 @@ __device__ __forceinline__ uint32_t byte_inc(uint32_t* w, uint64_t i) {
   uint32_t sh = (uint32_t)(i & 3) * 8;
   return (atomicAdd(w + (i >> 2), 1u << sh) >> sh) & 0xffu;  // old value
 }
+// the increment alone (no result: nothing waits for the atomic)
+__device__ __forceinline__ void byte_add(uint32_t* w, uint64_t i) {
+  uint32_t sh = (uint32_t)(i & 3) * 8;
+  atomicAdd(w + (i >> 2), 1u << sh);
+}
 __device__ __forceinline__ void byte_dec(uint32_t* w, uint64_t i) {
   uint32_t sh = (uint32_t)(i & 3) * 8;
   atomicSub(w + (i >> 2), 1u << sh);
@@ -229,27 +234,42 @@ enum : int { ST_HBM = 0, ST_STASH = 1, ST_PEAK_HBM = 2, ST_PEAK_STASH = 3, ST_PE
 // A warp's placements of the remap phase: `placed` lanes put one item into
 // the HBM store (hbm) or the stash, a bin reaching `new_load`.  All 32 lanes
 // call; one lane per warp updates the counters.
-// (stash_peak = false: the caller takes the stash peak at the end of the
-// batch instead, because evictions may still be running beside this remap)
+// (peaks = false: only the counts move, by atomics nothing waits for; the
+// store and stash peaks are then the counts a batch ends with, which
+// stat_end_peaks records when the next batch starts)
 __device__ __forceinline__ void stat_place(const MapDev& m, bool placed, bool hbm,
-                                           uint32_t new_load, bool stash_peak = true) {
+                                           uint32_t new_load, bool peaks = true) {
   const uint32_t hm = __ballot_sync(0xffffffffu, placed && hbm);
   const uint32_t sm = __ballot_sync(0xffffffffu, placed && !hbm);
   const uint32_t top = __reduce_max_sync(0xffffffffu, placed ? new_load : 0u);
   if ((threadIdx.x & 31) == 0) {
     if (hm) {
       const unsigned long long c = __popc(hm);
-      atomicMax(m.stat + ST_PEAK_HBM, atomicAdd(m.stat + ST_HBM, c) + c);
+      if (peaks)
+        atomicMax(m.stat + ST_PEAK_HBM, atomicAdd(m.stat + ST_HBM, c) + c);
+      else
+        atomicAdd(m.stat + ST_HBM, c);
     }
     if (sm) {
       const unsigned long long c = __popc(sm);
-      if (stash_peak)
+      if (peaks)
         atomicMax(m.stat + ST_PEAK_STASH, atomicAdd(m.stat + ST_STASH, c) + c);
       else
         atomicAdd(m.stat + ST_STASH, c);
     }
     if (top) atomicMax(m.stat + ST_PEAK_LOAD, (unsigned long long)top);
   }
+}
+
+// The counts the previous batch ended with, into the peaks: one thread of a
+// batch calls it before the batch changes a count, and the host takes the
+// current counts into the peaks it reads.  A batch whose placements took no
+// peaks (stat_place with peaks = false) is covered so: its largest counts
+// are the ones it ends with (see above).
+__device__ __forceinline__ void stat_end_peaks(const MapDev& m) {
+  const unsigned long long h = __ldcg(m.stat + ST_HBM), s = __ldcg(m.stat + ST_STASH);
+  atomicMax(m.stat + ST_PEAK_HBM, h);
+  atomicMax(m.stat + ST_PEAK_STASH, s);
 }
 
 // items leaving the HBM store (hbm) or the stash
@@ -486,19 +506,26 @@ __device__ __forceinline__ uint4 poly_lengths(uint32_t L) { return make_uint4(0,
 // on) are the ChaCha20-Poly1305 AEAD of RFC 8439 Sec. 2.8: the first
 // page_bytes - 16 bytes encrypted from block 1, the tag over them and their
 // length in the last 16 bytes.  SEALED = m.integrity (kernels are compiled
-// for both, so the sealing's registers do not weigh on plain pages).
+// for both, so the sealing's registers do not weigh on plain pages).  With
+// ks_pre the page's key stream (the same bytes, offset by offset) was
+// computed ahead into shared memory and is only XORed here.
 template <bool SEALED>
 __device__ __forceinline__ void page_encrypt_to(const MapDev& m, const uint8_t* plain,
-                                                uint8_t* dst, uint64_t q, uint64_t version) {
+                                                uint8_t* dst, uint64_t q, uint64_t version,
+                                                const uint8_t* ks_pre = nullptr) {
   const int lane = threadIdx.x & 31;
   constexpr uint32_t sealed = SEALED ? 1u : 0u;
   const uint32_t L = m.page_bytes - 16 * sealed;
   PolyWarp pw;
   if (SEALED) pw = poly_begin(m, q, version);
   for (uint32_t c = 0; c < m.page_bytes; c += 512) {
-    uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2) + sealed, (uint32_t)q, (uint32_t)version,
-                           (uint32_t)(version >> 32));
     uint32_t off = c + 16 * lane;
+    uint4 ks;
+    if (ks_pre)
+      ks = off < L ? *reinterpret_cast<const uint4*>(ks_pre + off) : make_uint4(0, 0, 0, 0);
+    else
+      ks = chacha_quad(m.kenc, c / 64 + (lane >> 2) + sealed, (uint32_t)q, (uint32_t)version,
+                       (uint32_t)(version >> 32));
     if (off < L) {
       uint4 p = *reinterpret_cast<const uint4*>(plain + off);
       p.x ^= ks.x; p.y ^= ks.y; p.z ^= ks.z; p.w ^= ks.w;

@@ -6,6 +6,7 @@
 // directly), the batch staging buffers, and the error / poison state.  All
 // arithmetic of the method runs in the kernels of build.cu, sort.cu and
 // access.cu; this file only plans, allocates, copies and launches.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -517,7 +518,7 @@ cudaError_t main_batch(bolt* h, const BatchDev& b, uint32_t n, cudaStream_t st,
 // early_in: the batch's inputs are complete even if the kernel before it on
 // st is not (see launch_fused)
 cudaError_t fused_batch(bolt* h, const BatchDev& b, uint32_t n, uint64_t t0, cudaStream_t st,
-                        bool early_in = false) {
+                        bool early_in = false, const FusedInline* inl = nullptr) {
   const int s = h->slot;
   for (int k = 0; k < 2; k++)
     if (h->flush_pending[k]) {
@@ -526,7 +527,7 @@ cudaError_t fused_batch(bolt* h, const BatchDev& b, uint32_t n, uint64_t t0, cud
       h->flush_pending[k] = false;
     }
   const BatchDev v = slot_view(h, b, n, s);
-  cudaError_t e = launch_fused(h->m, v, n, t0, st, early_in);
+  cudaError_t e = launch_fused(h->m, v, n, t0, st, early_in, inl);
   if (e != cudaSuccess) return e;
   h->slot_ht_mask[s] = v.ht_mask;
   h->prev_valid = true;
@@ -1170,32 +1171,42 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
   }
   const uint32_t w = h->batch_width;
   if (h->fused && n <= FUSED_MAX_OPS && n <= w && n <= h->cap_batch) {
-    // one small batch: a single fused launch that reads its inputs from the
-    // pinned staging and writes its results and the error word back there,
-    // so the call is one launch and one stream wait (no copies)
+    // one small batch: a single fused launch that takes its inputs in its
+    // parameters (or, when they do not fit, from the pinned staging) and
+    // writes its results and the error word back to the staging, so the
+    // call is one launch and one stream wait (no copies)
     const IoPacked hp = io_packed(h->h_io[0], n, vb);
     const IoPacked dp = io_packed(h->d_io[0], n, vb);
+    FusedInline fi;
+    const uint64_t in_bytes = n * (9 + vb);
+    const bool inl = in_bytes <= FUSED_INLINE_MAX;
+    uint8_t* at = inl ? reinterpret_cast<uint8_t*>(fi.d) : reinterpret_cast<uint8_t*>(hp.keys);
+    if (inl) {
+      fi.bytes = (uint32_t)in_bytes;
+      fi.d[(in_bytes - 1) / 16] = make_uint4(0, 0, 0, 0);  // a defined tail
+    }
+    uint64_t* kdst = reinterpret_cast<uint64_t*>(at);
     if (h->kb == 4) {
       const uint32_t* k32 = reinterpret_cast<const uint32_t*>(kin);
-      for (uint64_t i = 0; i < n; i++) hp.keys[i] = k32[i];
+      for (uint64_t i = 0; i < n; i++) kdst[i] = k32[i];
     } else {
-      std::memcpy(hp.keys, kin, n * 8);
+      std::memcpy(kdst, kin, n * 8);
     }
-    std::memcpy(hp.vin, vin, n * vb);
-    std::memcpy(hp.ops, ops, n);
+    std::memcpy(at + n * 8, vin, n * vb);
+    std::memcpy(at + n * (8 + vb), ops, n);
     BatchDev b = h->b;
     b.ops = dp.ops;
     b.keys = dp.keys;
     b.vin = dp.vin;
     b.vout = dp.vout;
     b.status = dp.status;
-    b.h_in = reinterpret_cast<const uint8_t*>(hp.keys) + h->io_dev_delta;
+    b.h_in = inl ? nullptr : reinterpret_cast<const uint8_t*>(hp.keys) + h->io_dev_delta;
     b.h_out = hp.vout + h->io_dev_delta;
     b.h_err = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->h_err) + h->io_dev_delta);
     b.h_done = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->h_done) + h->io_dev_delta);
     b.done_seq = ++h->done_seq;
     // (the inputs are in the staging, written before the launch)
-    cudaError_t e = fused_batch(h, b, (uint32_t)n, h->t, st, true);
+    cudaError_t e = fused_batch(h, b, (uint32_t)n, h->t, st, true, inl ? &fi : nullptr);
     if (e != cudaSuccess) return BOLT_E_CUDA;
     // the kernel's completion word (written after its results) ends the wait;
     // if it has not come within seconds, wait for the stream and let its
@@ -1423,8 +1434,10 @@ int bolt_get_stats(bolt_t* h, bolt_stats_t* out) {
       cudaMemcpy(st, h->m.stat, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess)
     return BOLT_E_CUDA;
   out->trace_len = tl;
-  out->peak_hbm = st[ST_PEAK_HBM];
-  out->peak_stash = st[ST_PEAK_STASH];
+  // (the counts the last batch ended with: a fused batch leaves them to the
+  // next batch to take into the peaks)
+  out->peak_hbm = std::max(st[ST_PEAK_HBM], st[ST_HBM]);
+  out->peak_stash = std::max(st[ST_PEAK_STASH], st[ST_STASH]);
   out->peak_load = (uint32_t)st[ST_PEAK_LOAD];
   if (h->initialized && !h->poisoned && (st[ST_HBM] != out->n_hbm || st[ST_STASH] != out->n_stash))
     return BOLT_E_INTERNAL;
