@@ -1701,10 +1701,12 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     if (lane == 0) s_dcount = __popc(bf0) + __popc(bf1);
   }
   __syncthreads();
-  // 2c. warp per distinct page: read it (the previous batch's ciphertext if
-  //     that batch wrote it, else the host page) and decrypt it into its
-  //     slot's buffer; meanwhile bring its eviction's data into L2.  The
-  //     last warp first reads the free ring's window for the remap.
+  // 2c. read each distinct page (the previous batch's ciphertext if that
+  //     batch wrote it, else the host page) and decrypt it into its slot's
+  //     buffer: plain pages a warp per 512-byte chunk (the chunks' ChaCha20
+  //     blocks side by side), sealed pages a warp per page (one Poly1305
+  //     over the page); meanwhile bring each page's eviction data into L2.
+  //     The last warp first reads the free ring's window for the remap.
   if (wid == nwarps - 1) {
     // (the previous batch's end counts into the peaks: this batch's
     // placements take none)
@@ -1718,36 +1720,50 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     }
   }
   {
-    const uint32_t nd = s_dcount;
-    for (uint32_t d = wid; d < nd; d += nwarps) {
+    const uint32_t nd = s_dcount, nch = (m.page_bytes + 511) / 512;
+    const uint32_t per = SEALED ? 1u : nch, reads = nd * per;
+    for (uint32_t it = wid; it < reads; it += nwarps) {
+      const uint32_t d = it / per, c = it % per;
       const uint32_t q = s_dpage[d], h = s_dslot[d];
+      const uint32_t off = 512 * c + 16 * lane;
       const uint8_t* src = m.pages + (uint64_t)q * m.page_bytes;
       uint4 x = make_uint4(0, 0, 0, 0);
-      if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + 16 * lane);
-      prefetch_eviction(m, q, true, lane);
+      if (off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
+      if (c == 0) prefetch_eviction(m, q, true, lane);
       int kind = SRC_HOST;
       const uint32_t pd = prev_written(b, q);
       if (pd != NONE32) {
         kind = SRC_PREV;
         src = b.prev_dbuf + (uint64_t)pd * m.page_bytes;
-        if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + 16 * lane);
+        if (off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
       }
-      page_in<SEALED>(m, L, h, q, kind, src, x, lane);
+      if (SEALED) {
+        page_in<SEALED>(m, L, h, q, kind, src, x, lane);
+      } else {
+        const uint64_t v = m.version[q];
+        const uint4 k4 = chacha_quad(m.kenc, 8 * c + (lane >> 2), q, (uint32_t)v,
+                                     (uint32_t)(v >> 32));
+        x.x ^= k4.x; x.y ^= k4.y; x.z ^= k4.z; x.w ^= k4.w;
+        if (off < m.page_bytes)
+          *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) = x;
+        if (c == 0 && lane == 0) L.removed[h] = 0;
+      }
     }
-    // meanwhile warp nd + d computes page d's key stream for its write-back
-    // (version + 1) into its own eviction buffer, which the eviction of
-    // page d then only XORs: the write-back's ChaCha20 leaves the path
-    // when every page has a spare warp and buffer
-    if (2 * nd <= evict_warps && wid >= nd && wid < 2 * nd) {
-      const uint32_t d = wid - nd;
-      const uint64_t q = s_dpage[d], v = m.version[q] + 1;
-      uint8_t* ks = sbuf + (size_t)wid * (m.page_bytes + 32 * 16);
-      for (uint32_t c = 0; c < m.page_bytes; c += 512) {
-        const uint4 k4 = chacha_quad(m.kenc, c / 64 + (lane >> 2) + (SEALED ? 1u : 0u),
+    // meanwhile the warps after those compute each page's key stream for
+    // its write-back (version + 1), a warp per chunk, into the eviction
+    // buffer of warp nd + d, which the eviction of page d then only XORs:
+    // the write-back's ChaCha20 leaves the path when every page has a
+    // spare buffer
+    if (2 * nd <= evict_warps)
+      for (uint32_t j = (wid + nwarps - reads % nwarps) % nwarps; j < nd * nch; j += nwarps) {
+        const uint32_t d = j / nch, c = j % nch;
+        const uint64_t q = s_dpage[d], v = m.version[q] + 1;
+        uint8_t* ks = sbuf + (size_t)(nd + d) * (m.page_bytes + 32 * 16);
+        const uint4 k4 = chacha_quad(m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u),
                                      (uint32_t)q, (uint32_t)v, (uint32_t)(v >> 32));
-        if (c + 16 * lane < m.page_bytes) *reinterpret_cast<uint4*>(ks + c + 16 * lane) = k4;
+        if (512 * c + 16 * lane < m.page_bytes)
+          *reinterpret_cast<uint4*>(ks + 512 * c + 16 * lane) = k4;
       }
-    }
   }
   __syncthreads();
   // 3. the host-access trace (every read position in order, then each
