@@ -1115,7 +1115,8 @@ __device__ __forceinline__ unsigned long long ring_take(const MapDev& m, bool ta
   unsigned long long base = 0;
   if (w) {
     // positions from the window's count; the shared head still moves (its
-    // result is not waited for)
+    // result is not waited for: an atomic at the end of the batch would
+    // hold up the kernel's completion instead)
     base = w->head + w->taken;
     __syncwarp();
     if (mask && lane == __ffs(mask) - 1) {
@@ -1426,11 +1427,8 @@ static_assert(4 * FUSED_MAX_OPS <= FUSED_TABLE, "a small batch's page table fits
 
 // the P2C decision of op i on round-start counts read from L2: the counts
 // change by atomics between the rounds of this one launch
-// With `c`, also the counts read for the decision: the chosen bin's load,
-// the chosen row's count and, for a host bin, its page's reverse-index count.
-// Every count is read at once (one round trip).
-__device__ __forceinline__ void decide_op_l2(const MapDev& m, const BatchDev& b, uint32_t i,
-                                             PlaceCounts* c = nullptr) {
+// (every count it needs is read at once: one round trip)
+__device__ __forceinline__ void decide_op_l2(const MapDev& m, const BatchDev& b, uint32_t i) {
   auto get = [](const uint32_t* w, uint64_t k) {
     return (__ldcg(w + (k >> 2)) >> ((uint32_t)(k & 3) * 8)) & 0xffu;
   };
@@ -1440,22 +1438,12 @@ __device__ __forceinline__ void decide_op_l2(const MapDev& m, const BatchDev& b,
   const uint4 r4 = *reinterpret_cast<const uint4*>(b.rows + 4 * (uint64_t)i);
   const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
   const uint32_t l1 = get(m.load, p1), l2 = get(m.load, p2);
-  uint32_t r1 = 0, r2 = 0, rc[4] = {0, 0, 0, 0};
-  if (c) {
-    if (p1 >= m.K) r1 = get(m.revcnt, p1 - m.K);
-    if (p2 >= m.K) r2 = get(m.revcnt, p2 - m.K);
-  }
+  uint32_t rc[4] = {0, 0, 0, 0};
   if (fresh) {
 #pragma unroll
     for (int j = 0; j < 4; j++) rc[j] = get(m.rowcnt, rr[j]);
   }
-  const bool first = l1 <= l2;
-  b.rdest[i] = first ? p1 : p2;
-  if (c) {
-    c->load = first ? l1 : l2;
-    c->rev = first ? r1 : r2;
-    c->row = 0;
-  }
+  b.rdest[i] = l1 <= l2 ? p1 : p2;
   if (fresh) {
     uint32_t best = rr[0], bc = rc[0];
 #pragma unroll
@@ -1465,17 +1453,19 @@ __device__ __forceinline__ void decide_op_l2(const MapDev& m, const BatchDev& b,
         bc = rc[j];
       }
     b.rrow[i] = best;
-    if (c) c->row = bc;
   }
 }
 
 // largest value the fused launch stages in shared memory (the ABI's limit)
 constexpr uint32_t FUSED_VB_MAX = 504;
 
-template <bool SEALED>
-__global__ void __launch_bounds__(FUSED_THREADS)
-    k_fused(MapDev m, BatchDev b, uint32_t n, uint64_t t0, uint32_t evict_warps,
+// ONE: compiled for batches of a single op (n = 1 folded into the code,
+// which shrinks what a cold SM fetches)
+template <bool SEALED, bool ONE>
+__global__ void __launch_bounds__(FUSED_THREADS, 1)
+    k_fused(MapDev m, BatchDev b, uint32_t n_arg, uint64_t t0, uint32_t evict_warps,
             uint32_t early_in, const __grid_constant__ FusedInline inl) {
+  const uint32_t n = ONE ? 1u : n_arg;
   extern __shared__ __align__(16) uint8_t sbuf[];
   // Everything the batch reads back within itself lives in shared memory:
   // the inputs, the grouping, pairs, rows, hits, the page table and its read
@@ -1495,6 +1485,9 @@ __global__ void __launch_bounds__(FUSED_THREADS)
       s_dslot[2 * FUSED_MAX_OPS], s_dpage[2 * FUSED_MAX_OPS];
   __shared__ uint32_t s_ht[FUSED_TABLE], s_htmin[FUSED_TABLE], s_dcount;
   __shared__ uint8_t s_initp[FUSED_MAX_OPS], s_fpres[FUSED_MAX_OPS], s_defer[FUSED_MAX_OPS];
+  // a one-round remap's counts as read during the page reads: the REMAP
+  // pair's two loads and two reverse-index counts, a new key's four row counts
+  __shared__ uint8_t s_cnt[8][FUSED_MAX_OPS];
   __shared__ RingWin s_ring;
   static_assert(RING_WIN >= FUSED_MAX_OPS, "the remap's takes fit the ring window");
   const int lane = threadIdx.x & 31;
@@ -1764,6 +1757,26 @@ __global__ void __launch_bounds__(FUSED_THREADS)
         if (512 * c + 16 * lane < m.page_bytes)
           *reinterpret_cast<uint4*>(ks + 512 * c + 16 * lane) = k4;
       }
+    // the counts a one-round remap decides on, read now (nothing but
+    // find_remove changes them before the remap, and phase 5 takes its
+    // removals out)
+    if (wid == nwarps - 2 && (uint32_t)lane < n && n <= m.Wr) {
+      auto get = [](const uint32_t* w, uint64_t k) {
+        return (__ldcg(w + (k >> 2)) >> ((uint32_t)(k & 3) * 8)) & 0xffu;
+      };
+      const uint64_t pr = s_rpair[lane];
+      const uint32_t p1 = (uint32_t)pr, p2 = (uint32_t)(pr >> 32);
+      const bool fresh = s_hit[lane] == NONE32;
+      uint32_t c[8];
+      c[0] = get(m.load, p1);
+      c[1] = get(m.load, p2);
+      c[2] = p1 >= m.K ? get(m.revcnt, p1 - m.K) : 0u;
+      c[3] = p2 >= m.K ? get(m.revcnt, p2 - m.K) : 0u;
+#pragma unroll
+      for (int j = 0; j < 4; j++) c[4 + j] = fresh ? get(m.rowcnt, s_rows[4 * lane + j]) : 0u;
+#pragma unroll
+      for (int k = 0; k < 8; k++) s_cnt[k][lane] = (uint8_t)c[k];
+    }
   }
   __syncthreads();
   // 3. the host-access trace (every read position in order, then each
@@ -1802,9 +1815,8 @@ __global__ void __launch_bounds__(FUSED_THREADS)
   //    (eviction changes no load or row count) and, when the ring window
   //    holds a slot for every take, places every key whose bin is not a page
   //    of this batch: such a placement touches none of the pages, stash lists
-  //    or ring slots the eviction reads.  The others wait for the eviction;
-  //    the stash peak is then taken at the end of the batch.
-  const bool one_round = n <= m.Wr;
+  //    or ring slots the eviction reads.  The others wait for the eviction.
+  const bool one_round = ONE || n <= m.Wr;  // (W_r >= 1)
   const bool early = one_round && s_ring.tail - s_ring.head >= n;
   if (wid == nwarps - 1) {
     if ((uint32_t)lane < n) exec_op(m, L, lane);
@@ -1812,7 +1824,49 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     const bool act =
         one_round && (uint32_t)lane < n && s_leader[lane] == (uint32_t)lane && s_fpres[lane];
     PlaceCounts pc{0, 0, 0};
-    if (act) decide_op_l2(m, L, lane, &pc);
+    if (one_round) {
+      // the counts read in 2c less find_remove's removals: a leader's hit
+      // left its bin and, deleted, its row; then the lower load wins (the
+      // first bin on a tie), a new key takes its least-filled row
+      uint32_t rbin = NONE32, rrow = NONE32;
+      if ((uint32_t)lane < n && s_leader[lane] == (uint32_t)lane && s_hit[lane] != NONE32) {
+        const uint64_t pr = s_pair[lane];
+        rbin = meta_which(s_hmeta[lane]) ? (uint32_t)(pr >> 32) : (uint32_t)pr;
+        const uint32_t lw = s_lastw[lane];
+        if (lw != NONE32 && L.ops[lw] == OP_DEL) rrow = s_hit[lane] / m.R;
+      }
+      const uint64_t rp = s_rpair[lane];
+      const uint32_t p1 = (uint32_t)rp, p2 = (uint32_t)(rp >> 32);
+      const uint4 r4 = *reinterpret_cast<const uint4*>(s_rows + 4 * lane);
+      const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+      uint32_t l1 = s_cnt[0][lane], l2 = s_cnt[1][lane];
+      uint32_t rc[4] = {s_cnt[4][lane], s_cnt[5][lane], s_cnt[6][lane], s_cnt[7][lane]};
+      for (uint32_t j = 0; j < n; j++) {
+        const uint32_t bj = __shfl_sync(0xffffffffu, rbin, j);
+        const uint32_t wj = __shfl_sync(0xffffffffu, rrow, j);
+        l1 -= bj == p1 ? 1u : 0u;
+        l2 -= bj == p2 ? 1u : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) rc[k] -= wj == rr[k] ? 1u : 0u;
+      }
+      if (act) {
+        const bool first = l1 <= l2;
+        s_rdest[lane] = first ? p1 : p2;
+        pc.load = first ? l1 : l2;
+        pc.rev = first ? s_cnt[2][lane] : s_cnt[3][lane];
+        if (s_hit[lane] == NONE32) {
+          uint32_t best = rr[0], bc = rc[0];
+#pragma unroll
+          for (int k = 1; k < 4; k++)
+            if (rc[k] < bc) {
+              best = rr[k];
+              bc = rc[k];
+            }
+          s_rrow[lane] = best;
+          pc.row = bc;
+        }
+      }
+    }
     __syncwarp();
     if (early) {
       bool in_batch = false;
@@ -1826,15 +1880,21 @@ __global__ void __launch_bounds__(FUSED_THREADS)
       // placements) plus the placements of lower lanes on the same bin or
       // row
       const bool go = act && !in_batch, fresh = go && s_hit[lane] == NONE32;
-      const uint32_t below = (1u << lane) - 1u;
-      const uint32_t same_bin =
-          __match_any_sync(0xffffffffu, go ? s_rdest[lane] : NONE32) & __ballot_sync(0xffffffffu, go);
-      const uint32_t same_row =
-          __match_any_sync(0xffffffffu, fresh ? s_rrow[lane] : NONE32) &
-          __ballot_sync(0xffffffffu, fresh);
-      pc.load += __popc(same_bin & below) + 1;
-      pc.rev += __popc(same_bin & below);
-      pc.row += __popc(same_row & below);
+      const uint32_t dst = s_rdest[lane], row = s_rrow[lane];
+      const uint32_t flags = (go ? 1u : 0u) | (fresh ? 2u : 0u);
+      uint32_t rb = 0, rw = 0;
+      for (uint32_t j = 0; j < n; j++) {
+        const uint32_t dj = __shfl_sync(0xffffffffu, dst, j);
+        const uint32_t rj = __shfl_sync(0xffffffffu, row, j);
+        const uint32_t fj = __shfl_sync(0xffffffffu, flags, j);
+        if (j < (uint32_t)lane) {
+          rb += (fj & 1u) && dj == dst ? 1u : 0u;
+          rw += (fj & 2u) && rj == row ? 1u : 0u;
+        }
+      }
+      pc.load += rb + 1;
+      pc.rev += rb;
+      pc.row += rw;
       remap_apply_op(m, L, lane, go, &s_ring, false, &pc);
     }
   } else if (wid < evict_warps) {
@@ -1862,6 +1922,7 @@ __global__ void __launch_bounds__(FUSED_THREADS)
     }
   }
   __syncthreads();
+
   if (b.h_out) {
     // results and the error word back to the caller's pinned staging, then
     // the completion word the caller waits for (every thread's writes are
@@ -1883,15 +1944,23 @@ cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_
   if (inl && inl->bytes != n * (9 + m.vb)) return cudaErrorInvalidValue;
   ProfSpan whole(P_ACCESS, st);
   if (m.vb > FUSED_VB_MAX) return cudaErrorInvalidValue;
-  auto kf = m.integrity ? k_fused<true> : k_fused<false>;
+  using Kf = void (*)(MapDev, BatchDev, uint32_t, uint64_t, uint32_t, uint32_t, FusedInline);
+  static const Kf kfs[4] = {k_fused<false, false>, k_fused<false, true>, k_fused<true, false>,
+                            k_fused<true, true>};
+  const int which = (m.integrity ? 2 : 0) + (n == 1 ? 1 : 0);
+  const Kf kf = kfs[which];
   // the eviction warps' page buffers take what the kernel's own shared
   // arrays leave of the 227 KB a block may use
-  static const size_t static_bytes[2] = {
-      [] { cudaFuncAttributes a{}; return cudaFuncGetAttributes(&a, k_fused<false>) == cudaSuccess
+  static const size_t static_bytes[4] = {
+      [] { cudaFuncAttributes a{}; return cudaFuncGetAttributes(&a, kfs[0]) == cudaSuccess
                                               ? a.sharedSizeBytes : (size_t)(64u << 10); }(),
-      [] { cudaFuncAttributes a{}; return cudaFuncGetAttributes(&a, k_fused<true>) == cudaSuccess
+      [] { cudaFuncAttributes a{}; return cudaFuncGetAttributes(&a, kfs[1]) == cudaSuccess
+                                              ? a.sharedSizeBytes : (size_t)(64u << 10); }(),
+      [] { cudaFuncAttributes a{}; return cudaFuncGetAttributes(&a, kfs[2]) == cudaSuccess
+                                              ? a.sharedSizeBytes : (size_t)(64u << 10); }(),
+      [] { cudaFuncAttributes a{}; return cudaFuncGetAttributes(&a, kfs[3]) == cudaSuccess
                                               ? a.sharedSizeBytes : (size_t)(64u << 10); }()};
-  const size_t budget = (227u << 10) - static_bytes[m.integrity ? 1 : 0];
+  const size_t budget = (227u << 10) - static_bytes[which];
   const uint32_t per_warp = m.page_bytes + 32 * 16;
   uint32_t ew = (uint32_t)(budget / per_warp);
   // (the last warp runs the ops' semantics meanwhile)

@@ -107,6 +107,28 @@ def test_access_parity_batch_widths(batch, fused):
     o.close(); g.close()
 
 
+@pytest.mark.parametrize("N,batch", [(1 << 12, 2), (1 << 14, 8), (1 << 16, 32)])
+def test_one_round_fused_batches_match_oracle(N, batch):
+    """Fused batches that fit one P2C round (batch <= W_r): the launch decides
+    on bin, row and reverse-index counts read while its pages are in flight,
+    less what find_remove takes out, and places beside the eviction.  Keys
+    from a small pool (duplicates, deletes and re-inserts inside a batch)
+    and absent keys (new rows) on maps small enough that a removal's bin or
+    a deleted key's row often meets another op's choices."""
+    o, g = _pair(N, 8, batch=batch)
+    assert g.info()["round_width"] >= batch
+    g.set_param(B.BOLT_PARAM_FUSED, 1)
+    keys, vals = W.records(N * 3 // 4, 8, 0x0E0D)
+    assert o.init(keys, vals, 17) == 0 and g.init(keys, vals, 17) == 0
+    for rep, (pool, dfrac, afrac) in enumerate([(64, 0.2, 0.2), (N * 3 // 4, 0.1, 0.3),
+                                                (16, 0.3, 0.1)]):
+        ops, k, vin = W.op_stream(pool, 1500, 8, 0x0E10 + rep, get_frac=0.3, del_frac=dfrac,
+                                  absent_frac=afrac)
+        _run_batch(o, g, ops, k, vin, f"rep {rep}")
+        _assert_state_equal(o, g, f"rep {rep}")
+    o.close(); g.close()
+
+
 @pytest.mark.parametrize("trace", [True, False])
 def test_fused_and_chain_batches_interleaved_match_oracle(trace):
     """Calls whose batches run as single fused launches (widths 1, 5, 32)
