@@ -952,11 +952,13 @@ __device__ __forceinline__ void exec_op(const MapDev& m, const BatchDev& b, uint
 // The ciphertext goes to the page's slot in dbuf (the next batch reads it
 // there while the host copy is in flight) and, with to_host, also straight
 // to the host page.  `ks` (or null): the page's new key stream, computed
-// ahead in shared memory.
+// ahead in shared memory; `poly` (or null, sealed pages): its tag's start
+// state, likewise.
 template <bool SEALED>
 __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, uint32_t e,
                                           uint8_t* plain, bool to_host,
-                                          const uint8_t* ks = nullptr) {
+                                          const uint8_t* ks = nullptr,
+                                          const uint32_t* poly = nullptr) {
   const int lane = threadIdx.x & 31;
   ulonglong2* items = reinterpret_cast<ulonglong2*>(plain + m.page_bytes);
   const uint32_t d = b.dslot[e];
@@ -1029,7 +1031,7 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
   // the old plaintext in dbuf is no longer read: the ciphertext replaces it
   // and k_flush copies it to the host page (or this warp does, below)
   uint8_t* cipher = b.dbuf + (uint64_t)d * m.page_bytes;
-  page_encrypt_to<SEALED>(m, plain, cipher, q, ver, ks);
+  page_encrypt_to<SEALED>(m, plain, cipher, q, ver, ks, poly);
   if (to_host)  // each lane stores the 16-byte pieces it encrypted
     for (uint32_t o = 16 * lane; o < m.page_bytes; o += 512)
       *reinterpret_cast<uint4*>(m.pages + q * m.page_bytes + o) =
@@ -1488,6 +1490,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
   // a one-round remap's counts as read during the page reads: the REMAP
   // pair's two loads and two reverse-index counts, a new key's four row counts
   __shared__ uint8_t s_cnt[8][FUSED_MAX_OPS];
+  // (sealed) the write-back tags' start states (a page per spare warp pair:
+  // at most 7 pages) and the pages whose tag failed
+  __shared__ uint32_t s_poly[SEALED ? 7 : 1][POLY_WORDS];
+  __shared__ unsigned long long s_bad;
   __shared__ RingWin s_ring;
   static_assert(RING_WIN >= FUSED_MAX_OPS, "the remap's takes fit the ring window");
   const int lane = threadIdx.x & 31;
@@ -1513,7 +1519,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
   // batch of the same call).  It lets its successor start only after its own
   // wait, so a successor never runs ahead of this kernel's predecessor.
   for (uint32_t h = threadIdx.x; h < FUSED_TABLE; h += blockDim.x) s_ht[h] = NONE32;
-  if (threadIdx.x == 0) s_dcount = 0;
+  if (threadIdx.x == 0) {
+    s_dcount = 0;
+    s_bad = 0;
+  }
   // 1a. per op the DUMMY pair and the REMAP pair (one ChaCha20 block each,
   //     each kind in a warp of its own, lane = op)
   auto pairs = [&]() {
@@ -1696,10 +1705,12 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
   __syncthreads();
   // 2c. read each distinct page (the previous batch's ciphertext if that
   //     batch wrote it, else the host page) and decrypt it into its slot's
-  //     buffer: plain pages a warp per 512-byte chunk (the chunks' ChaCha20
-  //     blocks side by side), sealed pages a warp per page (one Poly1305
-  //     over the page); meanwhile bring each page's eviction data into L2.
-  //     The last warp first reads the free ring's window for the remap.
+  //     buffer, a warp per 512-byte chunk (the chunks' ChaCha20 blocks side
+  //     by side); meanwhile bring each page's eviction data into L2.  A
+  //     sealed page's tag is checked beside its decryption by a warp of its
+  //     own (one Poly1305 over the page); a page that fails it is emptied
+  //     after the phase.  The last warp first reads the free ring's window
+  //     for the remap.
   if (wid == nwarps - 1) {
     // (the previous batch's end counts into the peaks: this batch's
     // placements take none)
@@ -1713,50 +1724,86 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     }
   }
   {
-    const uint32_t nd = s_dcount, nch = (m.page_bytes + 511) / 512;
-    const uint32_t per = SEALED ? 1u : nch, reads = nd * per;
+    const uint32_t nd = s_dcount, nch = (m.page_bytes + 511) / 512, reads = nd * nch;
+    const uint32_t Lc = m.page_bytes - (SEALED ? 16u : 0u);  // the ciphertext's bytes
+    // where page d's bytes come from: the previous batch's ciphertext if that
+    // batch wrote it (its host copy may still be in flight), else the host page
+    auto source = [&](uint32_t q) {
+      const uint32_t pd = prev_written(b, q);
+      return pd != NONE32 ? b.prev_dbuf + (uint64_t)pd * m.page_bytes
+                          : m.pages + (uint64_t)q * m.page_bytes;
+    };
     for (uint32_t it = wid; it < reads; it += nwarps) {
-      const uint32_t d = it / per, c = it % per;
+      const uint32_t d = it / nch, c = it % nch;
       const uint32_t q = s_dpage[d], h = s_dslot[d];
       const uint32_t off = 512 * c + 16 * lane;
       const uint8_t* src = m.pages + (uint64_t)q * m.page_bytes;
       uint4 x = make_uint4(0, 0, 0, 0);
       if (off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
       if (c == 0) prefetch_eviction(m, q, true, lane);
-      int kind = SRC_HOST;
-      const uint32_t pd = prev_written(b, q);
-      if (pd != NONE32) {
-        kind = SRC_PREV;
-        src = b.prev_dbuf + (uint64_t)pd * m.page_bytes;
-        if (off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
-      }
-      if (SEALED) {
-        page_in<SEALED>(m, L, h, q, kind, src, x, lane);
-      } else {
-        const uint64_t v = m.version[q];
-        const uint4 k4 = chacha_quad(m.kenc, 8 * c + (lane >> 2), q, (uint32_t)v,
-                                     (uint32_t)(v >> 32));
-        x.x ^= k4.x; x.y ^= k4.y; x.z ^= k4.z; x.w ^= k4.w;
-        if (off < m.page_bytes)
-          *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) = x;
-        if (c == 0 && lane == 0) L.removed[h] = 0;
-      }
+      const uint8_t* at = source(q);
+      if (at != src && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(at + off);
+      const uint64_t v = m.version[q];
+      const uint4 k4 = chacha_quad(m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u), q,
+                                   (uint32_t)v, (uint32_t)(v >> 32));
+      x.x ^= k4.x; x.y ^= k4.y; x.z ^= k4.z; x.w ^= k4.w;
+      if (off < Lc)
+        *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) = x;
+      else if (off < m.page_bytes)
+        *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) =
+            make_uint4(0, 0, 0, 0);
+      if (c == 0 && lane == 0) L.removed[h] = 0;
     }
-    // meanwhile the warps after those compute each page's key stream for
-    // its write-back (version + 1), a warp per chunk, into the eviction
-    // buffer of warp nd + d, which the eviction of page d then only XORs:
-    // the write-back's ChaCha20 leaves the path when every page has a
-    // spare buffer
-    if (2 * nd <= evict_warps)
-      for (uint32_t j = (wid + nwarps - reads % nwarps) % nwarps; j < nd * nch; j += nwarps) {
-        const uint32_t d = j / nch, c = j % nch;
+    // meanwhile the warps after those: (sealed) a warp per page checks its
+    // tag; each page's key stream for its write-back (version + 1), a warp
+    // per chunk, into the eviction buffer of warp nd + d, which the eviction
+    // of page d then only XORs; (sealed) a warp per page computes that
+    // write-back's tag start state.  The write-back's ChaCha20 and Poly1305
+    // key leave the path when every page has a spare buffer.
+    const bool ks_pre = 2 * nd <= evict_warps;
+    const uint32_t n_chk = SEALED ? nd : 0u, n_ks = ks_pre ? nd * nch : 0u;
+    const uint32_t n_pk = SEALED && ks_pre ? nd : 0u;
+    for (uint32_t t = (wid + nwarps - reads % nwarps) % nwarps; t < n_chk + n_ks + n_pk;
+         t += nwarps) {
+      if (t < n_chk) {
+        const uint32_t d = t, q = s_dpage[d];
+        const uint8_t* at = source(q);
+        uint4 x = make_uint4(0, 0, 0, 0);
+        if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(at + 16 * lane);
+        PolyWarp pw = poly_begin(m, q, m.version[q]);
+        uint4 stored = make_uint4(0, 0, 0, 0);
+        for (uint32_t c = 0; c < m.page_bytes; c += 512) {
+          const uint32_t off = c + 16 * lane;
+          if (c > 0 && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(at + off);
+          if (off < Lc) {
+            poly_block(pw, off / 16, x);
+          } else if (off == Lc) {
+            stored = x;
+            poly_block(pw, off / 16, poly_lengths(Lc));
+          }
+        }
+        const uint4 tag = poly_finish(pw, Lc / 16 + 1);
+        const bool bad = lane == (int)((Lc / 16) & 31) &&
+                         (tag.x != stored.x || tag.y != stored.y || tag.z != stored.z ||
+                          tag.w != stored.w);
+        if (__any_sync(0xffffffffu, bad) && lane == 0) {
+          set_err(m, ERR_INTEGRITY);
+          atomicOr(&s_bad, 1ull << d);
+        }
+      } else if (t < n_chk + n_ks) {
+        const uint32_t d = (t - n_chk) / nch, c = (t - n_chk) % nch;
         const uint64_t q = s_dpage[d], v = m.version[q] + 1;
         uint8_t* ks = sbuf + (size_t)(nd + d) * (m.page_bytes + 32 * 16);
         const uint4 k4 = chacha_quad(m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u),
                                      (uint32_t)q, (uint32_t)v, (uint32_t)(v >> 32));
         if (512 * c + 16 * lane < m.page_bytes)
           *reinterpret_cast<uint4*>(ks + 512 * c + 16 * lane) = k4;
+      } else {
+        const uint32_t d = t - n_chk - n_ks;
+        const uint64_t q = s_dpage[d];
+        poly_store(poly_begin(m, q, m.version[q] + 1), s_poly[d]);
       }
+    }
     // the counts a one-round remap decides on, read now (nothing but
     // find_remove changes them before the remap, and phase 5 takes its
     // removals out)
@@ -1779,6 +1826,16 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     }
   }
   __syncthreads();
+  // (sealed) a page that failed its tag reads as empty: nothing of it enters
+  // the map, and the batch ends with ERR_INTEGRITY
+  if (SEALED && s_bad) {
+    for (uint32_t d = 0; d < s_dcount; d++)
+      if ((s_bad >> d) & 1)
+        for (uint32_t off = 16 * threadIdx.x; off < m.page_bytes; off += 16 * blockDim.x)
+          *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)s_dslot[d] * m.page_bytes + off) =
+              make_uint4(0, 0, 0, 0);
+    __syncthreads();
+  }
   // 3. the host-access trace (every read position in order, then each
   //    distinct page once as a write); the previous batch's table is cleared
   if (m.trace_on && wid == 0) {
@@ -1902,7 +1959,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     const bool ks_pre = 2 * nd <= evict_warps;
     for (uint32_t e = wid; e < nd; e += evict_warps)
       evict_one<SEALED>(m, L, e, sbuf + (size_t)wid * per_warp, true,
-                        ks_pre ? sbuf + (size_t)(nd + e) * per_warp : nullptr);
+                        ks_pre ? sbuf + (size_t)(nd + e) * per_warp : nullptr,
+                        SEALED && ks_pre ? s_poly[e] : nullptr);
   }
   __syncthreads();
   // 6. P2C remap in rounds of W_r op slots (warp 0, lane per op): decide on

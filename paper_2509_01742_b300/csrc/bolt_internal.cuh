@@ -438,6 +438,32 @@ __device__ __forceinline__ PolyWarp poly_begin(const MapDev& m, uint64_t q, uint
 }
 
 // block j of the message, held by lane j % 32 (the caller passes only its own)
+// A warp's start state (after poly_begin) kept in shared memory: lane L's
+// r^(L + 1) in words 5L..5L+4, then r^32 and s.  All 32 lanes call.
+constexpr uint32_t POLY_WORDS = 32 * 5 + 5 + 4;
+__device__ __forceinline__ void poly_store(const PolyWarp& w, uint32_t* sm) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 5; i++) sm[5 * lane + i] = w.rpow.l[i];
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < 5; i++) sm[160 + i] = w.r32.l[i];
+    sm[165] = w.s.x; sm[166] = w.s.y; sm[167] = w.s.z; sm[168] = w.s.w;
+  }
+}
+__device__ __forceinline__ PolyWarp poly_load(const uint32_t* sm) {
+  const int lane = threadIdx.x & 31;
+  PolyWarp w;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    w.rpow.l[i] = sm[5 * lane + i];
+    w.r32.l[i] = sm[160 + i];
+    w.acc.l[i] = 0;
+  }
+  w.s = make_uint4(sm[165], sm[166], sm[167], sm[168]);
+  w.last = -1;
+  return w;
+}
 __device__ __forceinline__ void poly_block(PolyWarp& w, int j, uint4 blk) {
   w.acc = w.last < 0 ? p130_block(blk) : p130_add(p130_mul(w.acc, w.r32), p130_block(blk));
   w.last = j;
@@ -508,16 +534,18 @@ __device__ __forceinline__ uint4 poly_lengths(uint32_t L) { return make_uint4(0,
 // length in the last 16 bytes.  SEALED = m.integrity (kernels are compiled
 // for both, so the sealing's registers do not weigh on plain pages).  With
 // ks_pre the page's key stream (the same bytes, offset by offset) was
-// computed ahead into shared memory and is only XORed here.
+// computed ahead into shared memory and is only XORed here; with poly_pre
+// (sealed) the tag's start state was too (poly_store).
 template <bool SEALED>
 __device__ __forceinline__ void page_encrypt_to(const MapDev& m, const uint8_t* plain,
                                                 uint8_t* dst, uint64_t q, uint64_t version,
-                                                const uint8_t* ks_pre = nullptr) {
+                                                const uint8_t* ks_pre = nullptr,
+                                                const uint32_t* poly_pre = nullptr) {
   const int lane = threadIdx.x & 31;
   constexpr uint32_t sealed = SEALED ? 1u : 0u;
   const uint32_t L = m.page_bytes - 16 * sealed;
   PolyWarp pw;
-  if (SEALED) pw = poly_begin(m, q, version);
+  if (SEALED) pw = poly_pre ? poly_load(poly_pre) : poly_begin(m, q, version);
   for (uint32_t c = 0; c < m.page_bytes; c += 512) {
     uint32_t off = c + 16 * lane;
     uint4 ks;
