@@ -207,6 +207,138 @@ __global__ void __launch_bounds__(256) k_build_rounds(MapDev m, const uint64_t* 
   }
 }
 
+// The same barrier in two halves, so a block can work between its arrival
+// and its wait: grid_arrive after the block's writes of the phase (returns
+// the generation to wait on), grid_wait before reading what the other blocks
+// wrote.  The wait is bounded like grid_barrier's.
+__device__ __forceinline__ unsigned int grid_arrive(unsigned int* bar) {
+  __shared__ unsigned int s_gen;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    }
+    s_gen = g;
+  }
+  __syncthreads();
+  return s_gen;
+}
+__device__ __forceinline__ bool grid_wait(const MapDev& m, unsigned int* bar, unsigned int g) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    volatile unsigned int* gen = bar + 1;
+    ok = 1;
+    uint32_t it = 0;
+    while (*gen == g) {
+      if (++it > m.spin_limit) {
+        ok = 0;
+        set_err(m, ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(256);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// The rounds with each record's PRF computed inside them, for grids of at
+// least W_r / ROUNDS_KPT threads (each thread owns at most ROUNDS_KPT records
+// of a round, records lo + tid + k * nthreads): while a block waits at the
+// decide barrier it computes its records' pairs PRF(INIT, i) for the next
+// round, and while it waits at the apply barrier their rows PRF(PM, key), so
+// the PRF costs no pass of its own.  Pairs still go to `bins` (the placement
+// reads them); decisions, counts and claims are those of k_build_rounds.
+constexpr uint32_t ROUNDS_KPT = 4;
+
+__global__ void __launch_bounds__(256) k_build_rounds_prf(MapDev m,
+                                                          const uint64_t* __restrict__ keys,
+                                                          uint64_t n, uint64_t* __restrict__ bins,
+                                                          uint32_t* __restrict__ dest,
+                                                          uint32_t* __restrict__ prow,
+                                                          unsigned int* bar) {
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t pr[ROUNDS_KPT];
+  uint32_t rw[ROUNDS_KPT][4], dst[ROUNDS_KPT], row[ROUNDS_KPT];
+  auto pairs = [&](uint64_t lo) {
+    const uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
+#pragma unroll
+    for (uint32_t k = 0; k < ROUNDS_KPT; k++) {
+      const uint64_t i = lo + tid + k * nthreads;
+      if (i < hi) {
+        uint32_t b1, b2;
+        prf_pair(m, DOM_INIT, i, b1, b2);
+        pr[k] = (uint64_t)b1 | ((uint64_t)b2 << 32);
+        bins[i] = pr[k];
+      }
+    }
+  };
+  auto rows = [&](uint64_t lo) {
+    const uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
+#pragma unroll
+    for (uint32_t k = 0; k < ROUNDS_KPT; k++) {
+      const uint64_t i = lo + tid + k * nthreads;
+      if (i < hi) prf_rows(m, keys[i], rw[k]);
+    }
+  };
+  if (n == 0) return;
+  pairs(0);
+  rows(0);
+  for (uint64_t lo = 0; lo < n; lo += m.Wr) {
+    const uint64_t hi = lo + m.Wr < n ? lo + m.Wr : n;
+    // decide on round-start counts (read from L2)
+#pragma unroll
+    for (uint32_t k = 0; k < ROUNDS_KPT; k++) {
+      const uint64_t i = lo + tid + k * nthreads;
+      if (i >= hi) continue;
+      const uint32_t b1 = (uint32_t)pr[k], b2 = (uint32_t)(pr[k] >> 32);
+      const uint32_t l1 = byte_get_l2(m.load, b1), l2 = byte_get_l2(m.load, b2);
+      dst[k] = l1 <= l2 ? b1 : b2;
+      dest[i] = dst[k];
+      uint32_t best = rw[k][0], bc = byte_get_l2(m.rowcnt, rw[k][0]);
+#pragma unroll
+      for (int j = 1; j < 4; j++) {
+        const uint32_t c = byte_get_l2(m.rowcnt, rw[k][j]);
+        if (c < bc) {
+          best = rw[k][j];
+          bc = c;
+        }
+      }
+      row[k] = best;
+    }
+    const uint64_t next = lo + m.Wr;
+    unsigned int g = grid_arrive(bar);
+    if (next < n) pairs(next);
+    if (!grid_wait(m, bar, g)) return;
+    // the counts, in round order: the order-dependent part
+#pragma unroll
+    for (uint32_t k = 0; k < ROUNDS_KPT; k++) {
+      const uint64_t i = lo + tid + k * nthreads;
+      if (i >= hi) continue;
+      uint32_t tag = NONE32;
+      if (byte_inc(m.load, dst[k]) + 1 > m.lmax) {
+        set_err(m, ERR_LOAD);
+      } else {
+        const uint32_t slot = byte_inc(m.rowcnt, row[k]);
+        if (slot >= m.R) set_err(m, ERR_ROW);
+        else tag = row[k] | (slot << PROW_SLOT_SHIFT);
+      }
+      prow[i] = tag;
+    }
+    g = grid_arrive(bar);
+    if (next < n) rows(next);
+    if (!grid_wait(m, bar, g)) return;
+  }
+}
+
 // write every record's position-map entry (row and slot claimed in the
 // rounds) and give HBM-bin records a value-store slot.  The slots come from
 // one counter, taken once per warp for all its HBM-bin records (which slot a
@@ -677,7 +809,36 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
   {
     ProfSpan ps(P_P2C, st);
     bool done = false;
-    if (s.rows4 && n) {
+    int per_sm_prf = 0;
+    if (s.rows4 && n &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_prf, k_build_rounds_prf, 256, 0) ==
+            cudaSuccess && per_sm_prf > 0) {
+      // the rounds with the PRF inside them, when the co-resident grid has a
+      // thread for every ROUNDS_KPT records of a round
+      unsigned int* bar = reinterpret_cast<unsigned int*>(s.counters + 1);
+      const uint64_t want = (m.Wr + 255) / 256;
+      const uint64_t cap = (uint64_t)sms * (per_sm_prf < 4 ? per_sm_prf : 4);
+      const unsigned int blocks = (unsigned int)(want < cap ? want : cap);
+      if ((uint64_t)blocks * 256 * ROUNDS_KPT >= m.Wr) {
+        cudaMemsetAsync(bar, 0, 8, st);
+        const uint64_t* kp = keys;
+        uint64_t nn = n;
+        uint64_t* bp = s.bins;
+        uint32_t* dp = s.dest;
+        uint32_t* pp = s.prow;
+        MapDev mm = m;
+        void* args[] = {&mm, &kp, &nn, &bp, &dp, &pp, &bar};
+        if (cudaLaunchCooperativeKernel((const void*)k_build_rounds_prf, dim3(blocks), dim3(256),
+                                        args, 0, st) == cudaSuccess) {
+          count_launch();
+          done = true;
+          deferred_place = true;
+        } else {
+          cudaGetLastError();  // clear; the PRF pass and the rounds kernel follow
+        }
+      }
+    }
+    if (!done && s.rows4 && n) {
       k_build_prf<<<sms * 16, 256, 0, st>>>(m, keys, n, s.bins, s.rows4);
       count_launch();
       int per_sm = 0;
