@@ -1765,7 +1765,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     const uint32_t n_pk = SEALED && ks_pre ? nd : 0u;
     for (uint32_t t = (wid + nwarps - reads % nwarps) % nwarps; t < n_chk + n_ks + n_pk;
          t += nwarps) {
-      if (t < n_chk) {
+      if (SEALED && t < n_chk) {
         const uint32_t d = t, q = s_dpage[d];
         const uint8_t* at = source(q);
         uint4 x = make_uint4(0, 0, 0, 0);
