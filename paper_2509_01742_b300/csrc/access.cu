@@ -1981,17 +1981,24 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
   }
   __syncthreads();
 
-  if (b.h_out) {
-    // results and the error word back to the caller's pinned staging, then
-    // the completion word the caller waits for (every thread's writes are
-    // fenced at system scope before it)
-    const uint32_t words = (n * (m.vb + 1) + 15) / 16;
-    for (uint32_t w = threadIdx.x; w < words; w += blockDim.x)
-      reinterpret_cast<uint4*>(b.h_out)[w] = reinterpret_cast<const uint4*>(b.vout)[w];
-    if (threadIdx.x == 0) *b.h_err = *(volatile uint32_t*)m.err;
-    __threadfence_system();
-    __syncthreads();
-    if (threadIdx.x == 0 && b.h_done) *(volatile uint32_t*)b.h_done = b.done_seq;
+  if (b.h_res) {
+    // results vout | status (packed in the device buffer) and the error word
+    // to the caller's pinned staging as 8-byte words of 7 stream bytes and
+    // the call's tag: each is one store the host sees whole, so the host
+    // takes the results once every word is tagged, with no system-scope
+    // fence here and no completion word after it
+    const uint32_t nb = n * (m.vb + 1), total = nb + 4;
+    for (uint32_t w = threadIdx.x; w < (total + 6) / 7; w += blockDim.x) {
+      uint64_t v = (uint64_t)b.res_tag << 56;
+      for (uint32_t k = 0; k < 7; k++) {
+        const uint32_t at = 7 * w + k;
+        uint32_t byte = 0;
+        if (at < nb) byte = b.vout[at];
+        else if (at < total) byte = (*(volatile uint32_t*)m.err >> (8 * (at - nb))) & 0xffu;
+        v |= (uint64_t)byte << (8 * k);
+      }
+      *(volatile uint64_t*)(b.h_res + w) = v;
+    }
   }
 }
 

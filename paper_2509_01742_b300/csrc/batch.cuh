@@ -85,13 +85,12 @@ struct BatchDev {
   uint32_t prev_kt_mask, pad2;
   // a host-pointer call of one small batch (fused launch only): the packed
   // inputs keys | vin | ops in pinned host staging, copied by the kernel into
-  // the device inputs above (laid out the same way from `keys`); the packed
-  // results vout | status copied back to h_out, and the error word to h_err
+  // the device inputs above (laid out the same way from `keys`); the results
+  // vout | status (packed) and the error word back to h_res as 8-byte words,
+  // each 7 bytes of that stream and res_tag in its top byte
   const uint8_t* h_in;
-  uint8_t* h_out;
-  uint32_t* h_err;
-  uint32_t* h_done;    // then done_seq is written here, after everything else
-  uint32_t done_seq, pad4;
+  uint64_t* h_res;
+  uint32_t res_tag, pad4;
 };
 
 cudaError_t sort_batch_keys(uint64_t* keys, uint32_t n_pow2, cudaStream_t st);

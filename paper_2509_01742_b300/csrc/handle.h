@@ -49,7 +49,10 @@ struct bolt {
   uint8_t* h_vout = nullptr;
   uint8_t* h_status = nullptr;
   uint32_t* h_err = nullptr;
-  uint32_t* h_done = nullptr;  // completion word of a one-batch host call (pinned, mapped)
+  // a one-batch host call's results as tagged words (pinned, mapped; room
+  // for FUSED_MAX_OPS ops) and the count of such calls, whose low byte
+  // (never 0) tags them
+  uint64_t* h_res = nullptr;
   uint32_t done_seq = 0;
   ptrdiff_t io_dev_delta = 0;  // device address of the pinned staging minus its host address
   // bolt_access moves chunks of ops through two alternating sets of pinned

@@ -863,7 +863,8 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   }
   void* p = nullptr;
   const uint64_t set_bytes = MAXB * (1 + 8 + 2 * (uint64_t)val_bytes + 1);
-  e = cudaHostAlloc(&p, 2 * set_bytes + 64, cudaHostAllocMapped);
+  const uint64_t res_bytes = (FUSED_MAX_OPS * (val_bytes + 1) + 4 + 6) / 7 * 8;
+  e = cudaHostAlloc(&p, 2 * set_bytes + 64 + res_bytes, cudaHostAllocMapped);
   void* pd = nullptr;
   if (e == cudaSuccess && cudaHostGetDevicePointer(&pd, p, 0) != cudaSuccess) {
     cudaFreeHost(p);
@@ -892,8 +893,7 @@ int bolt_create(uint64_t N, uint32_t key_bytes, uint32_t val_bytes, uint64_t hbm
   h->h_ops = h->h_io[0].ops;
   h->h_status = h->h_io[0].status;
   h->h_err = reinterpret_cast<uint32_t*>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
-  h->h_done = h->h_err + 1;
-  *h->h_done = 0;
+  h->h_res = reinterpret_cast<uint64_t*>(h->h_err + 2);
   int rc = alloc_state(h);
   if (rc) {
     cudaFreeHost(h->h_keys);
@@ -1201,32 +1201,48 @@ int bolt_access(bolt_t* h, const uint8_t* ops, const void* keys, const void* val
     b.vout = dp.vout;
     b.status = dp.status;
     b.h_in = inl ? nullptr : reinterpret_cast<const uint8_t*>(hp.keys) + h->io_dev_delta;
-    b.h_out = hp.vout + h->io_dev_delta;
-    b.h_err = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->h_err) + h->io_dev_delta);
-    b.h_done = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(h->h_done) + h->io_dev_delta);
-    b.done_seq = ++h->done_seq;
+    // the result words start untagged; the kernel tags each one it writes
+    const uint64_t res_words = (n * (vb + 1) + 4 + 6) / 7;
+    volatile uint64_t* res = h->h_res;
+    for (uint64_t w = 0; w < res_words; w++) res[w] = 0;
+    b.h_res = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(h->h_res) + h->io_dev_delta);
+    b.res_tag = ++h->done_seq % 255 + 1;
     // (the inputs are in the staging, written before the launch)
     cudaError_t e = fused_batch(h, b, (uint32_t)n, h->t, st, true, inl ? &fi : nullptr);
     if (e != cudaSuccess) return BOLT_E_CUDA;
-    // the kernel's completion word (written after its results) ends the wait;
-    // if it has not come within seconds, wait for the stream and let its
-    // error (or the missing word) speak
-    const volatile uint32_t* done = h->h_done;
+    // the wait ends when every result word carries the call's tag (each is
+    // one 8-byte store the host sees whole: no completion word, and no
+    // system-scope fence in the kernel before one); if they have not all come
+    // within seconds, wait for the stream and let its error (or the missing
+    // words) speak
+    const uint64_t tag = (uint64_t)b.res_tag << 56;
+    uint64_t got = 0;
     const auto t_wait = std::chrono::steady_clock::now();
-    for (uint32_t spin = 1; *done != b.done_seq; spin++) {
-      if ((spin & 4095) == 0 &&
+    for (uint32_t spin = 1; got < res_words; spin++) {
+      while (got < res_words && (res[got] & (0xffull << 56)) == tag) got++;
+      if (got < res_words && (spin & 4095) == 0 &&
           std::chrono::steady_clock::now() - t_wait > std::chrono::seconds(5)) {
         if (cudaStreamSynchronize(st) != cudaSuccess) return BOLT_E_CUDA;
-        if (*done != b.done_seq) return BOLT_E_INTERNAL;
-        break;
+        while (got < res_words && (res[got] & (0xffull << 56)) == tag) got++;
+        if (got < res_words) return BOLT_E_INTERNAL;
       }
     }
     std::atomic_thread_fence(std::memory_order_acquire);
     h->t += n;
     h->batches++;
-    std::memcpy(vout, hp.vout, n * vb);
-    if (status_out) std::memcpy(status_out, hp.status, n);
-    const int rc = err_to_rc(*h->h_err);
+    // the stream vout | status | error word, 7 bytes per word
+    const uint64_t nv = n * vb;
+    uint32_t err = 0;
+    for (uint64_t w = 0; w < res_words; w++) {
+      const uint64_t v = res[w];
+      for (uint64_t k = 0, i = 7 * w; k < 7; k++, i++) {
+        const uint8_t byte = (uint8_t)(v >> (8 * k));
+        if (i < nv) vout[i] = byte;
+        else if (i < nv + n) { if (status_out) status_out[i - nv] = byte; }
+        else if (i < nv + n + 4) err |= (uint32_t)byte << (8 * (i - nv - n));
+      }
+    }
+    const int rc = err_to_rc(err);
     if (rc) h->poisoned = true;
     return rc;
   }
