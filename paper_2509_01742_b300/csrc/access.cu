@@ -26,6 +26,8 @@
 //               encrypted, written back to the host page
 //   k_remap_*   P2C remap of every key present after the batch, in rounds of
 //               W_r operation slots decided on round-start loads
+// A batch of at most FUSED_MAX_OPS operations runs all of these steps in one
+// CTA instead (k_fused, below).
 #include "bolt_internal.cuh"
 #include "batch.cuh"
 
@@ -1420,7 +1422,11 @@ __global__ void k_clear_keys(BatchDev b, uint32_t n) {
 // boundaries: the same device functions on the same tables and buffers, so
 // the same results, pages and trace.  Its written pages go to the host from
 // this kernel (no separate write-back launch): a caller issuing one
-// operation at a time pays one launch per operation.
+// operation at a time pays one launch per operation.  The kernel is bound by
+// dependent round trips (the host page, the position map and counters in
+// L2), so it starts everything it can early: the host pages' prefetch as
+// soon as the search has a pair, the write-back's key streams and tag keys
+// and the remap's counts in spare warps during the host read.
 constexpr uint32_t FUSED_THREADS = 512;
 // the page table of a batch of <= FUSED_MAX_OPS ops: 4 x 2^ceil(log2 n)
 // entries, at least 256 (the runtime's sizing)
