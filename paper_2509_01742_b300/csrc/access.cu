@@ -578,12 +578,8 @@ __device__ __forceinline__ void page_in(const MapDev& m, const BatchDev& b, uint
     if (c > 0 && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
     if (kind != SRC_PLAIN) {
       if (SEALED && sealed) {
-        if (off < L) {
-          poly_block(pw, off / 16, x);
-        } else if (off == L) {
-          stored = x;
-          poly_block(pw, off / 16, poly_lengths(L));
-        }
+        if (off == L) stored = x;
+        if (off <= L) poly_block(pw, off / 16, off < L ? x : poly_lengths(L));
       }
       const uint4 ks = chacha_quad(m.kenc, c / 64 + (lane >> 2) + sealed, (uint32_t)q,
                                    (uint32_t)v, (uint32_t)(v >> 32));
@@ -1781,12 +1777,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         for (uint32_t c = 0; c < m.page_bytes; c += 512) {
           const uint32_t off = c + 16 * lane;
           if (c > 0 && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(at + off);
-          if (off < Lc) {
-            poly_block(pw, off / 16, x);
-          } else if (off == Lc) {
-            stored = x;
-            poly_block(pw, off / 16, poly_lengths(Lc));
-          }
+          if (off == Lc) stored = x;
+          if (off <= Lc) poly_block(pw, off / 16, off < Lc ? x : poly_lengths(Lc));
         }
         const uint4 tag = poly_finish(pw, Lc / 16 + 1);
         const bool bad = lane == (int)((Lc / 16) & 31) &&

@@ -477,8 +477,15 @@ __device__ __forceinline__ uint4 poly_finish(const PolyWarp& w, int K) {
   P130 part = p130_mul(w.acc, re);
   if (w.last < 0)
     for (int i = 0; i < 5; i++) part.l[i] = 0;
+  // the warp's sum: raw limb sums (32 limbs below 2^26 stay below 2^31),
+  // then one normalisation
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) part = p130_add(part, p130_shfl(part, (threadIdx.x & 31) ^ d));
+  for (int d = 16; d > 0; d >>= 1) {
+    const P130 o = p130_shfl(part, (threadIdx.x & 31) ^ d);
+#pragma unroll
+    for (int i = 0; i < 5; i++) part.l[i] += o.l[i];
+  }
+  part = p130_norm(part.l[0], part.l[1], part.l[2], part.l[3], part.l[4]);
   // the sum as an exact integer in 32-bit words (limbs below 2^27: value
   // below 2^131), bits from 2^130 up folded back times 5, then p subtracted
   // once if still reached (the value is then below 2^130 + 5)
@@ -554,14 +561,15 @@ __device__ __forceinline__ void page_encrypt_to(const MapDev& m, const uint8_t* 
     else
       ks = chacha_quad(m.kenc, c / 64 + (lane >> 2) + sealed, (uint32_t)q, (uint32_t)version,
                        (uint32_t)(version >> 32));
+    uint4 blk = SEALED ? poly_lengths(L) : make_uint4(0, 0, 0, 0);
     if (off < L) {
       uint4 p = *reinterpret_cast<const uint4*>(plain + off);
       p.x ^= ks.x; p.y ^= ks.y; p.z ^= ks.z; p.w ^= ks.w;
       *reinterpret_cast<uint4*>(dst + off) = p;
-      if (SEALED) poly_block(pw, off / 16, p);
-    } else if (SEALED && off == L) {
-      poly_block(pw, off / 16, poly_lengths(L));
+      blk = p;
     }
+    // (the ciphertext's blocks and, at L, the lengths block: one call)
+    if (SEALED && off <= L) poly_block(pw, off / 16, blk);
   }
   if (SEALED) {
     const uint4 tag = poly_finish(pw, L / 16 + 1);
