@@ -1520,7 +1520,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
   // written before the launch, or a batch whose predecessor is an earlier
   // batch of the same call).  It lets its successor start only after its own
   // wait, so a successor never runs ahead of this kernel's predecessor.
-  for (uint32_t h = threadIdx.x; h < FUSED_TABLE; h += blockDim.x) s_ht[h] = NONE32;
+  for (uint32_t h = threadIdx.x; h < FUSED_TABLE; h += blockDim.x) {
+    s_ht[h] = NONE32;
+    s_htmin[h] = NONE32;
+  }
   if (threadIdx.x == 0) {
     s_dcount = 0;
     s_bad = 0;
@@ -1658,50 +1661,48 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
   }
   __syncthreads();
   // 2b. warp 0: the batch's page table -- each distinct page once, at the
-  //     slot linear probing gives it in the (empty) table, its first read
-  //     position, the page list in claim order; the table's keys also go to
-  //     the global table, where the next batch looks for pages this one wrote
+  //     slot linear probing gives it, its first read position, the page
+  //     list in claim order; the table's keys also go to the global table,
+  //     where the next batch looks for pages this one wrote.  Every read
+  //     position finds or claims its page's slot at once (lane per
+  //     position), and the smallest position on a slot is the page's first.
   if (wid == 0) {
     const uint32_t np = 2 * n;
-    uint32_t q[2], f[2];
-    bool valid[2], first[2];
+    uint32_t q[2], hs[2];
+    bool valid[2];
 #pragma unroll
     for (int k = 0; k < 2; k++) {
       const uint32_t p = lane + 32 * k;
       q[k] = p < np ? s_posq[p] : NONE32;
       valid[k] = q[k] != NONE32;
-      f[k] = p;
-      if (valid[k])
-        for (uint32_t j = 0; j < p; j++)
-          if (s_posq[j] == q[k]) {
-            f[k] = j;
-            break;
-          }
-      first[k] = valid[k] && f[k] == p;
-      if (first[k]) {
+      hs[k] = 0;
+      if (valid[k]) {
         uint32_t h = ht_hash(q[k], b.ht_mask);
-        while (atomicCAS(&s_ht[h], NONE32, q[k]) != NONE32) h = (h + 1) & b.ht_mask;
+        for (uint32_t probe = 0; probe <= b.ht_mask; probe++) {
+          const uint32_t prev = atomicCAS(&s_ht[h], NONE32, q[k]);
+          if (prev == NONE32 || prev == q[k]) break;
+          h = (h + 1) & b.ht_mask;
+        }
+        hs[k] = h;
         s_slot[p] = h;
+        atomicMin(&s_htmin[h], p);
       }
     }
     __syncwarp();
+    bool first[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) first[k] = valid[k] && s_htmin[hs[k]] == lane + 32u * k;
     const uint32_t below = (1u << lane) - 1u;
     const uint32_t bf0 = __ballot_sync(0xffffffffu, first[0]);
     const uint32_t bf1 = __ballot_sync(0xffffffffu, first[1]);
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-      const uint32_t p = lane + 32 * k;
-      if (p >= np || !valid[k]) continue;
-      const uint32_t h = s_slot[f[k]];
-      if (!first[k]) s_slot[p] = h;
+    for (int k = 0; k < 2; k++)
       if (first[k]) {
         const uint32_t d = k == 0 ? __popc(bf0 & below) : __popc(bf0) + __popc(bf1 & below);
-        b.ht_key[h] = q[k];
-        s_htmin[h] = p;
-        s_dslot[d] = h;
+        b.ht_key[hs[k]] = q[k];
+        s_dslot[d] = hs[k];
         s_dpage[d] = q[k];
       }
-    }
     if (lane == 0) s_dcount = __popc(bf0) + __popc(bf1);
   }
   __syncthreads();
@@ -1735,26 +1736,48 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
       return pd != NONE32 ? b.prev_dbuf + (uint64_t)pd * m.page_bytes
                           : m.pages + (uint64_t)q * m.page_bytes;
     };
-    for (uint32_t it = wid; it < reads; it += nwarps) {
-      const uint32_t d = it / nch, c = it % nch;
-      const uint32_t q = s_dpage[d], h = s_dslot[d];
-      const uint32_t off = 512 * c + 16 * lane;
-      const uint8_t* src = m.pages + (uint64_t)q * m.page_bytes;
-      uint4 x = make_uint4(0, 0, 0, 0);
-      if (off < m.page_bytes) x = *reinterpret_cast<const uint4*>(src + off);
-      if (c == 0) prefetch_eviction(m, q, true, lane);
-      const uint8_t* at = source(q);
-      if (at != src && off < m.page_bytes) x = *reinterpret_cast<const uint4*>(at + off);
-      const uint64_t v = m.version[q];
-      const uint4 k4 = chacha_quad(m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u), q,
-                                   (uint32_t)v, (uint32_t)(v >> 32));
-      x.x ^= k4.x; x.y ^= k4.y; x.z ^= k4.z; x.w ^= k4.w;
-      if (off < Lc)
-        *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) = x;
-      else if (off < m.page_bytes)
-        *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) =
-            make_uint4(0, 0, 0, 0);
-      if (c == 0 && lane == 0) L.removed[h] = 0;
+    // (a warp's items in groups of up to 4: every item's host load and page
+    // version are issued before the first one is decrypted; a one-op batch's
+    // reads fit one item per warp)
+    constexpr uint32_t GRP = ONE ? 1 : 4;
+    for (uint32_t base = wid; base < reads; base += GRP * nwarps) {
+      uint4 xs[GRP];
+      uint64_t vs[GRP];
+#pragma unroll
+      for (uint32_t g = 0; g < GRP; g++) {
+        const uint32_t it = base + g * nwarps;
+        xs[g] = make_uint4(0, 0, 0, 0);
+        vs[g] = 0;
+        if (it < reads) {
+          const uint32_t d = it / nch, c = it % nch, off = 512 * c + 16 * lane;
+          const uint32_t q = s_dpage[d];
+          if (off < m.page_bytes)
+            xs[g] = *reinterpret_cast<const uint4*>(m.pages + (uint64_t)q * m.page_bytes + off);
+          vs[g] = m.version[q];
+          if (c == 0) prefetch_eviction(m, q, true, lane);
+        }
+      }
+#pragma unroll
+      for (uint32_t g = 0; g < GRP; g++) {
+        const uint32_t it = base + g * nwarps;
+        if (it >= reads) break;
+        const uint32_t d = it / nch, c = it % nch, off = 512 * c + 16 * lane;
+        const uint32_t q = s_dpage[d], h = s_dslot[d];
+        uint4 x = xs[g];
+        const uint8_t* at = source(q);
+        if (at != m.pages + (uint64_t)q * m.page_bytes && off < m.page_bytes)
+          x = *reinterpret_cast<const uint4*>(at + off);
+        const uint64_t v = vs[g];
+        const uint4 k4 = chacha_quad(m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u), q,
+                                     (uint32_t)v, (uint32_t)(v >> 32));
+        x.x ^= k4.x; x.y ^= k4.y; x.z ^= k4.z; x.w ^= k4.w;
+        if (off < Lc)
+          *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) = x;
+        else if (off < m.page_bytes)
+          *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) =
+              make_uint4(0, 0, 0, 0);
+        if (c == 0 && lane == 0) L.removed[h] = 0;
+      }
     }
     // meanwhile the warps after those: (sealed) a warp per page checks its
     // tag; each page's key stream for its write-back (version + 1), a warp
