@@ -952,7 +952,9 @@ __device__ __forceinline__ void exec_op(const MapDev& m, const BatchDev& b, uint
 // to the host page.  `ks` (or null): the page's new key stream, computed
 // ahead in shared memory; `poly` (or null, sealed pages): its tag's start
 // state, likewise.
-template <bool SEALED>
+// (LAT: the key streams from chacha_lane16, for the latency-bound fused
+// batch)
+template <bool SEALED, bool LAT = false>
 __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, uint32_t e,
                                           uint8_t* plain, bool to_host,
                                           const uint8_t* ks = nullptr,
@@ -1029,7 +1031,7 @@ __device__ __forceinline__ void evict_one(const MapDev& m, const BatchDev& b, ui
   // the old plaintext in dbuf is no longer read: the ciphertext replaces it
   // and k_flush copies it to the host page (or this warp does, below)
   uint8_t* cipher = b.dbuf + (uint64_t)d * m.page_bytes;
-  page_encrypt_to<SEALED>(m, plain, cipher, q, ver, ks, poly);
+  page_encrypt_to<SEALED, LAT>(m, plain, cipher, q, ver, ks, poly);
   if (to_host)  // each lane stores the 16-byte pieces it encrypted
     for (uint32_t o = 16 * lane; o < m.page_bytes; o += 512)
       *reinterpret_cast<uint4*>(m.pages + q * m.page_bytes + o) =
@@ -1709,7 +1711,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
   // 2c. read each distinct page (the previous batch's ciphertext if that
   //     batch wrote it, else the host page) and decrypt it into its slot's
   //     buffer, a warp per 512-byte chunk (the chunks' ChaCha20 blocks side
-  //     by side); meanwhile bring each page's eviction data into L2.  A
+  //     by side; a one-op batch, whose few warps wait on them, takes each
+  //     block from chacha_lane16); meanwhile bring each page's eviction data
+  //     into L2.  A
   //     sealed page's tag is checked beside its decryption by a warp of its
   //     own (one Poly1305 over the page); a page that fails it is emptied
   //     after the phase.  The last warp first reads the free ring's window
@@ -1768,8 +1772,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         if (at != m.pages + (uint64_t)q * m.page_bytes && off < m.page_bytes)
           x = *reinterpret_cast<const uint4*>(at + off);
         const uint64_t v = vs[g];
-        const uint4 k4 = chacha_quad(m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u), q,
-                                     (uint32_t)v, (uint32_t)(v >> 32));
+        const uint4 k4 = (ONE ? chacha_lane16 : chacha_quad)(
+            m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u), q, (uint32_t)v, (uint32_t)(v >> 32));
         x.x ^= k4.x; x.y ^= k4.y; x.z ^= k4.z; x.w ^= k4.w;
         if (off < Lc)
           *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) = x;
@@ -1795,7 +1799,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         const uint8_t* at = source(q);
         uint4 x = make_uint4(0, 0, 0, 0);
         if (16 * lane < m.page_bytes) x = *reinterpret_cast<const uint4*>(at + 16 * lane);
-        PolyWarp pw = poly_begin(m, q, m.version[q]);
+        PolyWarp pw = poly_begin<ONE>(m, q, m.version[q]);
         uint4 stored = make_uint4(0, 0, 0, 0);
         for (uint32_t c = 0; c < m.page_bytes; c += 512) {
           const uint32_t off = c + 16 * lane;
@@ -1815,14 +1819,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         const uint32_t d = (t - n_chk) / nch, c = (t - n_chk) % nch;
         const uint64_t q = s_dpage[d], v = m.version[q] + 1;
         uint8_t* ks = sbuf + (size_t)(nd + d) * (m.page_bytes + 32 * 16);
-        const uint4 k4 = chacha_quad(m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u),
-                                     (uint32_t)q, (uint32_t)v, (uint32_t)(v >> 32));
+        const uint4 k4 = (ONE ? chacha_lane16 : chacha_quad)(
+            m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u), (uint32_t)q, (uint32_t)v,
+            (uint32_t)(v >> 32));
         if (512 * c + 16 * lane < m.page_bytes)
           *reinterpret_cast<uint4*>(ks + 512 * c + 16 * lane) = k4;
       } else {
         const uint32_t d = t - n_chk - n_ks;
         const uint64_t q = s_dpage[d];
-        poly_store(poly_begin(m, q, m.version[q] + 1), s_poly[d]);
+        poly_store(poly_begin<ONE>(m, q, m.version[q] + 1), s_poly[d]);
       }
     }
     // the counts a one-round remap decides on, read now (nothing but
@@ -1979,7 +1984,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     const uint32_t nd = s_dcount, per_warp = m.page_bytes + 32 * 16;
     const bool ks_pre = 2 * nd <= evict_warps;
     for (uint32_t e = wid; e < nd; e += evict_warps)
-      evict_one<SEALED>(m, L, e, sbuf + (size_t)wid * per_warp, true,
+      evict_one<SEALED, ONE>(m, L, e, sbuf + (size_t)wid * per_warp, true,
                         ks_pre ? sbuf + (size_t)(nd + e) * per_warp : nullptr,
                         SEALED && ks_pre ? s_poly[e] : nullptr);
   }

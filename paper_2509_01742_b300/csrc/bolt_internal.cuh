@@ -180,6 +180,24 @@ __device__ __forceinline__ uint4 chacha_quad(const uint32_t* key, uint32_t count
   return make_uint4(pick(r0), pick(r1), pick(r2), pick(r3));
 }
 
+// The 16 key-stream bytes chacha_quad gives this lane (words 4g..4g+3 of
+// block `counter`, g = lane & 3), from the whole block computed by this lane
+// alone: the four lanes of a quad compute the same block, four times
+// chacha_quad's arithmetic, but no shuffle sits in the rounds' dependency
+// chain, so the bytes come about twice as soon.  For the single-CTA fused
+// batch, whose warps wait on them; the batched kernels, bound by
+// throughput, keep chacha_quad.
+__device__ __forceinline__ uint4 chacha_lane16(const uint32_t* key, uint32_t counter,
+                                               uint32_t n0, uint32_t n1, uint32_t n2) {
+  uint32_t x[16];
+  chacha_block(key, counter, n0, n1, n2, x);
+  const int g = threadIdx.x & 3;
+  auto pick = [&](int k) {
+    return g == 0 ? x[k] : g == 1 ? x[4 + k] : g == 2 ? x[8 + k] : x[12 + k];
+  };
+  return make_uint4(pick(0), pick(1), pick(2), pick(3));
+}
+
 // PRF(dom, x) = ChaCha20(K_prf, counter 0, nonce = dom || x)
 __device__ __forceinline__ void prf(const MapDev& m, uint32_t dom, uint64_t x, uint32_t w[16]) {
   chacha_block(m.kprf, 0, dom, (uint32_t)x, (uint32_t)(x >> 32), w);
@@ -409,9 +427,11 @@ struct PolyWarp {
 
 // r and s from the one-time key: the first 32 bytes of the ChaCha20 block 0
 // of (K_enc, page, version); all 32 lanes call
+// (LAT: the block from chacha_lane16, for the latency-bound fused batch)
+template <bool LAT = false>
 __device__ __forceinline__ PolyWarp poly_begin(const MapDev& m, uint64_t q, uint64_t version) {
   const int lane = threadIdx.x & 31;
-  const uint4 ks = chacha_quad(m.kenc, 0, (uint32_t)q, (uint32_t)version,
+  const uint4 ks = (LAT ? chacha_lane16 : chacha_quad)(m.kenc, 0, (uint32_t)q, (uint32_t)version,
                                (uint32_t)(version >> 32));
   uint4 r, s;
   r.x = __shfl_sync(0xffffffffu, ks.x, 0); r.y = __shfl_sync(0xffffffffu, ks.y, 0);
@@ -543,7 +563,7 @@ __device__ __forceinline__ uint4 poly_lengths(uint32_t L) { return make_uint4(0,
 // ks_pre the page's key stream (the same bytes, offset by offset) was
 // computed ahead into shared memory and is only XORed here; with poly_pre
 // (sealed) the tag's start state was too (poly_store).
-template <bool SEALED>
+template <bool SEALED, bool LAT = false>
 __device__ __forceinline__ void page_encrypt_to(const MapDev& m, const uint8_t* plain,
                                                 uint8_t* dst, uint64_t q, uint64_t version,
                                                 const uint8_t* ks_pre = nullptr,
@@ -552,14 +572,15 @@ __device__ __forceinline__ void page_encrypt_to(const MapDev& m, const uint8_t* 
   constexpr uint32_t sealed = SEALED ? 1u : 0u;
   const uint32_t L = m.page_bytes - 16 * sealed;
   PolyWarp pw;
-  if (SEALED) pw = poly_pre ? poly_load(poly_pre) : poly_begin(m, q, version);
+  if (SEALED) pw = poly_pre ? poly_load(poly_pre) : poly_begin<LAT>(m, q, version);
   for (uint32_t c = 0; c < m.page_bytes; c += 512) {
     uint32_t off = c + 16 * lane;
     uint4 ks;
     if (ks_pre)
       ks = off < L ? *reinterpret_cast<const uint4*>(ks_pre + off) : make_uint4(0, 0, 0, 0);
     else
-      ks = chacha_quad(m.kenc, c / 64 + (lane >> 2) + sealed, (uint32_t)q, (uint32_t)version,
+      ks = (LAT ? chacha_lane16 : chacha_quad)(m.kenc, c / 64 + (lane >> 2) + sealed, (uint32_t)q,
+                                               (uint32_t)version,
                        (uint32_t)(version >> 32));
     uint4 blk = SEALED ? poly_lengths(L) : make_uint4(0, 0, 0, 0);
     if (off < L) {
