@@ -113,6 +113,15 @@ typedef struct bolt bolt_t;
                                     BOLT_PARAM_C).  Not with BOLT_PARAM_LOOKAHEAD
                                     (BOLT_E_ARG): pages read ahead are not checked.
                                     Default 0. */
+#define BOLT_PARAM_ROUNDS_PRF 15 /* where the build computes the records' PRF (their
+                                    INIT pairs and position-map rows): 0 = automatic
+                                    (default): inside the persistent P2C rounds, in the
+                                    blocks' barrier waits, when the round's grid has a
+                                    block on every SM, else in a pass before them; 1 =
+                                    inside the rounds wherever the co-resident grid
+                                    has a thread for every 4 records of a round; 2 =
+                                    always a pass before them.  The map built is the
+                                    same either way */
 #define BOLT_PARAM_SPIN_LIMIT 12 /* iterations (of a ~256 ns sleep) a bounded device wait
                                     spins before it gives up, 0..2^22 (default 2^22,
                                     about one second): the build's grid barrier between

@@ -26,6 +26,7 @@ BOLT_PARAM_ALPHA, BOLT_PARAM_C, BOLT_PARAM_TRACE, BOLT_PARAM_BATCH = 1, 2, 4, 5
 BOLT_PARAM_TRACE_CAP, BOLT_PARAM_CHECK_KEYS, BOLT_PARAM_PROFILE = 6, 7, 8
 BOLT_PARAM_BATCH_CAP, BOLT_PARAM_LOOKAHEAD, BOLT_PARAM_DEFER_FLUSH = 9, 10, 11
 BOLT_PARAM_SPIN_LIMIT, BOLT_PARAM_FUSED, BOLT_PARAM_INTEGRITY = 12, 13, 14
+BOLT_PARAM_ROUNDS_PRF = 15
 BOLT_PROF_CLASSES = 19
 PROF_NAMES = ("sort_global", "sort_tile", "page_build", "p2c_rounds", "key_check",
               "access_batch", "gather", "evict", "build", "group", "ksort_global",

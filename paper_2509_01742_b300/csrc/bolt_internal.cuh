@@ -700,6 +700,8 @@ cudaError_t sort_tags_u64(uint64_t* tags, uint64_t n_pow2, int log_tile, cudaStr
 struct BuildScratch {
   uint64_t cap = 0;        // records the buffers hold
   uint64_t tag_cap = 0;    // tag buffer elements (power of two)
+  int prf_rounds = 0;      // BOLT_PARAM_ROUNDS_PRF: 0 automatic, 1 the PRF inside
+                           // the P2C rounds where the grid allows, 2 a PRF pass
   uint64_t* tags = nullptr;
   uint64_t* bins = nullptr;   // per record b1 | b2 << 32
   uint32_t* dest = nullptr;   // per record destination bin

@@ -810,16 +810,19 @@ cudaError_t launch_build(const MapDev& m, const uint64_t* keys, const uint8_t* v
     ProfSpan ps(P_P2C, st);
     bool done = false;
     int per_sm_prf = 0;
-    if (s.rows4 && n &&
+    if (s.rows4 && n && s.prf_rounds != 2 &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_prf, k_build_rounds_prf, 256, 0) ==
             cudaSuccess && per_sm_prf > 0) {
       // the rounds with the PRF inside them, when the co-resident grid has a
-      // thread for every ROUNDS_KPT records of a round
+      // thread for every ROUNDS_KPT records of a round and a block on every
+      // SM: the PRF then fills the barrier waits of a full grid (with a few
+      // blocks a round has no wait to hide it in, and a PRF pass is faster)
       unsigned int* bar = reinterpret_cast<unsigned int*>(s.counters + 1);
       const uint64_t want = (m.Wr + 255) / 256;
       const uint64_t cap = (uint64_t)sms * (per_sm_prf < 4 ? per_sm_prf : 4);
       const unsigned int blocks = (unsigned int)(want < cap ? want : cap);
-      if ((uint64_t)blocks * 256 * ROUNDS_KPT >= m.Wr) {
+      if ((uint64_t)blocks * 256 * ROUNDS_KPT >= m.Wr &&
+          (blocks >= (unsigned int)sms || s.prf_rounds == 1)) {
         cudaMemsetAsync(bar, 0, 8, st);
         const uint64_t* kp = keys;
         uint64_t nn = n;

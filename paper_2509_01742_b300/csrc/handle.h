@@ -28,6 +28,7 @@ struct bolt {
   double la_frac = 0.0;       // BOLT_PARAM_LOOKAHEAD: share of a batch's pages read ahead
   int defer_flush = 0;        // BOLT_PARAM_DEFER_FLUSH: write-back after the next batch's reads
   uint32_t spin_limit = 1u << 22;  // BOLT_PARAM_SPIN_LIMIT: bounded device waits
+  int prf_rounds = 0;              // BOLT_PARAM_ROUNDS_PRF
   bool fused = true;          // BOLT_PARAM_FUSED: batches of <= FUSED_MAX_OPS in one launch
   bool integrity = false;     // BOLT_PARAM_INTEGRITY: sealed pages (tag checked on read)
   bolt_info_t info{};

@@ -765,6 +765,7 @@ int init_impl(bolt* h, const uint64_t* d_keys, const uint8_t* d_vals, uint64_t n
     e = key_check(st, bs.tags);  // in line, before the build reuses `tags`
     if (e != cudaSuccess) return BOLT_E_CUDA;
   }
+  bs.prf_rounds = h->prf_rounds;
   e = launch_build(m, d_keys, d_vals, n, bs, st, vals_ready, h->st2, h->ev_pfork, h->ev_pjoin,
                    h->st_fl, h->ev_evicted, h->ev_flushed);
   if (e != cudaSuccess) return BOLT_E_CUDA;
@@ -951,6 +952,10 @@ int bolt_set_param(bolt_t* h, int which, double v) {
       if (v != 0.0 && h->la_frac > 0.0) return BOLT_E_ARG;
       h->integrity = v != 0.0;
       break;
+    case BOLT_PARAM_ROUNDS_PRF:
+      if (!(v == 0.0 || v == 1.0 || v == 2.0)) return BOLT_E_ARG;
+      h->prf_rounds = (int)v;
+      return BOLT_OK;
     case BOLT_PARAM_SPIN_LIMIT:
       if (!(v >= 0.0 && v <= (double)(1u << 22))) return BOLT_E_ARG;
       h->spin_limit = (uint32_t)v;

@@ -34,6 +34,7 @@ def test_strerror_and_codes():
     assert B.BOLT_E_INTEGRITY == O.E_INTEGRITY
     assert b"integrity" in B.bolt_strerror(B.BOLT_E_INTEGRITY)
     assert B.BOLT_PARAM_INTEGRITY == 14
+    assert B.BOLT_PARAM_ROUNDS_PRF == 15
 
 
 @pytest.mark.parametrize("N,vb,alpha,c", [

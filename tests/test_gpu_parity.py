@@ -52,15 +52,23 @@ def _run_batch(o, g, ops, keys, vin, what=""):
     return vg, sg
 
 
-def test_build_parity_small_config():
-    """N=2^16 records of 16 B (8 B key + 8 B value): the build's pages,
-    loads and position-map rows equal the oracle's."""
-    N = 1 << 16
+@pytest.mark.parametrize("N,prf", [(1 << 16, 0), (1 << 16, 1), (1 << 16, 2), (1 << 20, 1)])
+def test_build_parity_small_config(N, prf):
+    """Records of 16 B (8 B key + 8 B value): the build's pages, loads and
+    position-map rows equal the oracle's, with the records' PRF computed
+    where the build picks (prf = 0), inside the persistent P2C rounds (1;
+    on these maps the automatic choice is a pass) or in a pass before them
+    (2), and with every access afterwards too."""
     o, g = _pair(N, 8)
+    g.set_param(B.BOLT_PARAM_ROUNDS_PRF, prf)
     keys, vals = W.records(N, 8, 0x5EED0001)
     assert o.init(keys, vals, 42) == 0
     assert g.init(keys, vals, 42) == 0
     _assert_state_equal(o, g, "after build")
+    ops, k, vin = W.op_stream(N, 2048, 8, 0x5EED0002, get_frac=0.5, del_frac=0.1,
+                              absent_frac=0.1)
+    _run_batch(o, g, ops, k, vin, "after the build")
+    _assert_state_equal(o, g, "after a batch")
     o.close(); g.close()
 
 
