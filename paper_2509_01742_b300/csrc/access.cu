@@ -1470,7 +1470,7 @@ constexpr uint32_t FUSED_VB_MAX = 504;
 template <bool SEALED, bool ONE>
 __global__ void __launch_bounds__(FUSED_THREADS, 1)
     k_fused(MapDev m, BatchDev b, uint32_t n_arg, uint64_t t0, uint32_t evict_warps,
-            uint32_t early_in, const __grid_constant__ FusedInline inl) {
+            uint32_t early_in, uint32_t ks_slots, const __grid_constant__ FusedInline inl) {
   const uint32_t n = ONE ? 1u : n_arg;
   extern __shared__ __align__(16) uint8_t sbuf[];
   // Everything the batch reads back within itself lives in shared memory:
@@ -1494,8 +1494,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
   // a one-round remap's counts as read during the page reads: the REMAP
   // pair's two loads and two reverse-index counts, a new key's four row counts
   __shared__ uint8_t s_cnt[8][FUSED_MAX_OPS];
-  // (sealed) the write-back tags' start states (a page per spare warp pair:
-  // at most 7 pages) and the pages whose tag failed
+  // (sealed) the write-back tags' start states (batches of at most 7 pages;
+  // wider ones derive them in the eviction) and the pages whose tag failed
   __shared__ uint32_t s_poly[SEALED ? 7 : 1][POLY_WORDS];
   __shared__ unsigned long long s_bad;
   __shared__ RingWin s_ring;
@@ -1785,13 +1785,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     }
     // meanwhile the warps after those: (sealed) a warp per page checks its
     // tag; each page's key stream for its write-back (version + 1), a warp
-    // per chunk, into the eviction buffer of warp nd + d, which the eviction
-    // of page d then only XORs; (sealed) a warp per page computes that
-    // write-back's tag start state.  The write-back's ChaCha20 and Poly1305
-    // key leave the path when every page has a spare buffer.
-    const bool ks_pre = 2 * nd <= evict_warps;
+    // per chunk, into the key-stream region after the eviction buffers (room
+    // for ks_slots pages), which the eviction of page d then only XORs;
+    // (sealed, at most 7 pages) a warp per page computes that write-back's
+    // tag start state.  The write-back's ChaCha20 (and Poly1305 key) leave
+    // the eviction's path.
+    const bool ks_pre = nd <= ks_slots;
+    uint8_t* const ks_base = sbuf + (size_t)evict_warps * (m.page_bytes + 32 * 16);
     const uint32_t n_chk = SEALED ? nd : 0u, n_ks = ks_pre ? nd * nch : 0u;
-    const uint32_t n_pk = SEALED && ks_pre ? nd : 0u;
+    const uint32_t n_pk = SEALED && ks_pre && nd <= 7 ? nd : 0u;
     for (uint32_t t = (wid + nwarps - reads % nwarps) % nwarps; t < n_chk + n_ks + n_pk;
          t += nwarps) {
       if (SEALED && t < n_chk) {
@@ -1818,7 +1820,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
       } else if (t < n_chk + n_ks) {
         const uint32_t d = (t - n_chk) / nch, c = (t - n_chk) % nch;
         const uint64_t q = s_dpage[d], v = m.version[q] + 1;
-        uint8_t* ks = sbuf + (size_t)(nd + d) * (m.page_bytes + 32 * 16);
+        uint8_t* ks = ks_base + (size_t)d * m.page_bytes;
         const uint4 k4 = (ONE ? chacha_lane16 : chacha_quad)(
             m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u), (uint32_t)q, (uint32_t)v,
             (uint32_t)(v >> 32));
@@ -1982,11 +1984,12 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     }
   } else if (wid < evict_warps) {
     const uint32_t nd = s_dcount, per_warp = m.page_bytes + 32 * 16;
-    const bool ks_pre = 2 * nd <= evict_warps;
+    const bool ks_pre = nd <= ks_slots;
+    uint8_t* const ks_base = sbuf + (size_t)evict_warps * per_warp;
     for (uint32_t e = wid; e < nd; e += evict_warps)
       evict_one<SEALED, ONE>(m, L, e, sbuf + (size_t)wid * per_warp, true,
-                        ks_pre ? sbuf + (size_t)(nd + e) * per_warp : nullptr,
-                        SEALED && ks_pre ? s_poly[e] : nullptr);
+                             ks_pre ? ks_base + (size_t)e * m.page_bytes : nullptr,
+                             SEALED && ks_pre && nd <= 7 ? s_poly[e] : nullptr);
   }
   __syncthreads();
   // 6. P2C remap in rounds of W_r op slots (warp 0, lane per op): decide on
@@ -2035,7 +2038,8 @@ cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_
   if (inl && inl->bytes != n * (9 + m.vb)) return cudaErrorInvalidValue;
   ProfSpan whole(P_ACCESS, st);
   if (m.vb > FUSED_VB_MAX) return cudaErrorInvalidValue;
-  using Kf = void (*)(MapDev, BatchDev, uint32_t, uint64_t, uint32_t, uint32_t, FusedInline);
+  using Kf = void (*)(MapDev, BatchDev, uint32_t, uint64_t, uint32_t, uint32_t, uint32_t,
+                      FusedInline);
   static const Kf kfs[4] = {k_fused<false, false>, k_fused<false, true>, k_fused<true, false>,
                             k_fused<true, true>};
   const int which = (m.integrity ? 2 : 0) + (n == 1 ? 1 : 0);
@@ -2056,14 +2060,18 @@ cudaError_t launch_fused(const MapDev& m, const BatchDev& b, uint32_t n, uint64_
   uint32_t ew = (uint32_t)(budget / per_warp);
   // (the last warp runs the ops' semantics meanwhile)
   ew = ew < 1 ? 1 : (ew > FUSED_THREADS / 32 - 1 ? FUSED_THREADS / 32 - 1 : ew);
-  const size_t smem = (size_t)ew * per_warp;
+  size_t smem = (size_t)ew * per_warp;
   if (smem > budget) return cudaErrorInvalidValue;
+  // then the write-back key streams of up to 2n pages, as many as fit
+  uint64_t ks_slots = (budget - smem) / m.page_bytes;
+  if (ks_slots > 2ull * n) ks_slots = 2ull * n;
+  smem += ks_slots * m.page_bytes;
   cudaError_t e = raise_smem_limit((const void*)kf, smem);
   if (e != cudaSuccess) return e;
   FusedInline none;
   none.bytes = 0;
   e = launch_dependent(kf, 1, FUSED_THREADS, smem, st, m, b, n, t0, ew, early_in ? 1u : 0u,
-                       inl ? *inl : none);
+                       (uint32_t)ks_slots, inl ? *inl : none);
   if (e != cudaSuccess) return e;
   count_launch();
   return cudaSuccess;
