@@ -1954,10 +1954,17 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     }
     __syncwarp();
     if (early) {
+      // (a page of this batch: a probe of its page table)
       bool in_batch = false;
       if (act && s_rdest[lane] >= m.K) {
-        const uint32_t q = s_rdest[lane] - (uint32_t)m.K, nd = s_dcount;
-        for (uint32_t d = 0; d < nd; d++) in_batch |= s_dpage[d] == q;
+        const uint32_t q = s_rdest[lane] - (uint32_t)m.K;
+        uint32_t h = ht_hash(q, b.ht_mask);
+        for (uint32_t probe = 0; probe <= b.ht_mask; probe++) {
+          const uint32_t k = s_ht[h];
+          if (k == q) in_batch = true;
+          if (k == q || k == NONE32) break;
+          h = (h + 1) & b.ht_mask;
+        }
       }
       if ((uint32_t)lane < FUSED_MAX_OPS) s_defer[lane] = act && in_batch;
       // what each placement's counter atomics would return: the counts read
@@ -1965,17 +1972,12 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
       // placements) plus the placements of lower lanes on the same bin or
       // row
       const bool go = act && !in_batch, fresh = go && s_hit[lane] == NONE32;
-      const uint32_t dst = s_rdest[lane], row = s_rrow[lane];
-      const uint32_t flags = (go ? 1u : 0u) | (fresh ? 2u : 0u);
-      uint32_t rb = 0, rw = 0;
-      for (uint32_t j = 0; j < n; j++) {
-        const uint32_t dj = __shfl_sync(0xffffffffu, dst, j);
-        const uint32_t rj = __shfl_sync(0xffffffffu, row, j);
-        const uint32_t fj = __shfl_sync(0xffffffffu, flags, j);
-        if (j < (uint32_t)lane) {
-          rb += (fj & 1u) && dj == dst ? 1u : 0u;
-          rw += (fj & 2u) && rj == row ? 1u : 0u;
-        }
+      uint32_t rb = 0, rw = 0;  // (a single op has no lower lanes)
+      if (!ONE) {
+        const uint32_t below = (1u << lane) - 1u;
+        const uint32_t gm = __ballot_sync(0xffffffffu, go), fm = __ballot_sync(0xffffffffu, fresh);
+        rb = __popc(__match_any_sync(0xffffffffu, go ? s_rdest[lane] : NONE32) & gm & below);
+        rw = __popc(__match_any_sync(0xffffffffu, fresh ? s_rrow[lane] : NONE32) & fm & below);
       }
       pc.load += rb + 1;
       pc.rev += rb;
