@@ -1761,19 +1761,21 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
           if (c == 0) prefetch_eviction(m, q, true, lane);
         }
       }
-#pragma unroll
-      for (uint32_t g = 0; g < GRP; g++) {
-        const uint32_t it = base + g * nwarps;
-        if (it >= reads) break;
-        const uint32_t d = it / nch, c = it % nch, off = 512 * c + 16 * lane;
-        const uint32_t q = s_dpage[d], h = s_dslot[d];
+      // each item: its bytes (the previous batch's ciphertext instead when
+      // that batch wrote the page), decrypted into its slot's buffer; a
+      // warp's items two by two, their ChaCha20 blocks side by side
+      auto bytes_of = [&](uint32_t g) {
+        const uint32_t it = base + g * nwarps, d = it / nch, c = it % nch;
+        const uint32_t off = 512 * c + 16 * lane, q = s_dpage[d];
         uint4 x = xs[g];
         const uint8_t* at = source(q);
         if (at != m.pages + (uint64_t)q * m.page_bytes && off < m.page_bytes)
           x = *reinterpret_cast<const uint4*>(at + off);
-        const uint64_t v = vs[g];
-        const uint4 k4 = (ONE ? chacha_lane16 : chacha_quad)(
-            m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u), q, (uint32_t)v, (uint32_t)(v >> 32));
+        return x;
+      };
+      auto put = [&](uint32_t g, uint4 x, uint4 k4) {
+        const uint32_t it = base + g * nwarps, d = it / nch, c = it % nch;
+        const uint32_t off = 512 * c + 16 * lane, h = s_dslot[d];
         x.x ^= k4.x; x.y ^= k4.y; x.z ^= k4.z; x.w ^= k4.w;
         if (off < Lc)
           *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) = x;
@@ -1781,6 +1783,29 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
           *reinterpret_cast<uint4*>(L.dbuf + (uint64_t)h * m.page_bytes + off) =
               make_uint4(0, 0, 0, 0);
         if (c == 0 && lane == 0) L.removed[h] = 0;
+      };
+      auto ctr_of = [&](uint32_t g) {
+        return 8 * ((base + g * nwarps) % nch) + (lane >> 2) + (SEALED ? 1u : 0u);
+      };
+      auto page_of = [&](uint32_t g) { return s_dpage[(base + g * nwarps) / nch]; };
+#pragma unroll
+      for (uint32_t g = 0; g < GRP; g += 2) {
+        if (base + g * nwarps >= reads) break;
+        const uint4 x0 = bytes_of(g);
+        const uint64_t v0 = vs[g];
+        if (GRP > 1 && base + (g + 1) * nwarps < reads) {
+          const uint4 x1 = bytes_of(g + 1);
+          const uint64_t v1 = vs[g + 1];
+          uint4 k0, k1;
+          chacha_quad2(m.kenc, ctr_of(g), page_of(g), (uint32_t)v0, (uint32_t)(v0 >> 32),
+                       ctr_of(g + 1), page_of(g + 1), (uint32_t)v1, (uint32_t)(v1 >> 32), k0,
+                       k1);
+          put(g, x0, k0);
+          put(g + 1, x1, k1);
+        } else {
+          put(g, x0, (ONE ? chacha_lane16 : chacha_quad)(m.kenc, ctr_of(g), page_of(g),
+                                                          (uint32_t)v0, (uint32_t)(v0 >> 32)));
+        }
       }
     }
     // meanwhile the warps after those: (sealed) a warp per page checks its

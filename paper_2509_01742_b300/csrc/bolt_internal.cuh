@@ -180,6 +180,63 @@ __device__ __forceinline__ uint4 chacha_quad(const uint32_t* key, uint32_t count
   return make_uint4(pick(r0), pick(r1), pick(r2), pick(r3));
 }
 
+// Two chacha_quad blocks at once (same key, their own counters and nonces):
+// the two blocks' quarter-rounds and shuffles are independent, so they
+// overlap and a warp that needs both waits for about one.
+__device__ __forceinline__ void chacha_quad2(const uint32_t* key, uint32_t ctr0, uint32_t n00,
+                                             uint32_t n01, uint32_t n02, uint32_t ctr1,
+                                             uint32_t n10, uint32_t n11, uint32_t n12,
+                                             uint4& out0, uint4& out1) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane & 3;
+  const int base = lane & ~3;
+  const uint32_t c_const = g == 0 ? 0x61707865u : g == 1 ? 0x3320646eu
+                         : g == 2 ? 0x79622d32u : 0x6b206574u;
+  const uint32_t ib = g == 0 ? key[0] : g == 1 ? key[1] : g == 2 ? key[2] : key[3];
+  const uint32_t ic = g == 0 ? key[4] : g == 1 ? key[5] : g == 2 ? key[6] : key[7];
+  const uint32_t id0 = g == 0 ? ctr0 : g == 1 ? n00 : g == 2 ? n01 : n02;
+  const uint32_t id1 = g == 0 ? ctr1 : g == 1 ? n10 : g == 2 ? n11 : n12;
+  uint32_t a0 = c_const, b0 = ib, c0 = ic, d0 = id0;
+  uint32_t a1 = c_const, b1 = ib, c1 = ic, d1 = id1;
+  const int s1 = base | ((g + 1) & 3), s2 = base | ((g + 2) & 3), s3 = base | ((g + 3) & 3);
+#pragma unroll 1
+  for (int r = 0; r < 10; r++) {
+    BOLT_QR(a0, b0, c0, d0);
+    BOLT_QR(a1, b1, c1, d1);
+    b0 = __shfl_sync(0xffffffffu, b0, s1);
+    b1 = __shfl_sync(0xffffffffu, b1, s1);
+    c0 = __shfl_sync(0xffffffffu, c0, s2);
+    c1 = __shfl_sync(0xffffffffu, c1, s2);
+    d0 = __shfl_sync(0xffffffffu, d0, s3);
+    d1 = __shfl_sync(0xffffffffu, d1, s3);
+    BOLT_QR(a0, b0, c0, d0);
+    BOLT_QR(a1, b1, c1, d1);
+    b0 = __shfl_sync(0xffffffffu, b0, s3);
+    b1 = __shfl_sync(0xffffffffu, b1, s3);
+    c0 = __shfl_sync(0xffffffffu, c0, s2);
+    c1 = __shfl_sync(0xffffffffu, c1, s2);
+    d0 = __shfl_sync(0xffffffffu, d0, s1);
+    d1 = __shfl_sync(0xffffffffu, d1, s1);
+  }
+  a0 += c_const; b0 += ib; c0 += ic; d0 += id0;
+  a1 += c_const; b1 += ib; c1 += ic; d1 += id1;
+  // the quad's transpose, as in chacha_quad
+  auto transpose = [&](uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    uint32_t v[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      const int want = (g - r) & 3;
+      const uint32_t send = want == 0 ? a : want == 1 ? b : want == 2 ? c : d;
+      v[r] = __shfl_sync(0xffffffffu, send, base | ((g + r) & 3));
+    }
+    const int r0 = (0 - g) & 3, r1 = (1 - g) & 3, r2 = (2 - g) & 3, r3 = (3 - g) & 3;
+    auto pick = [&](int r) { return r == 0 ? v[0] : r == 1 ? v[1] : r == 2 ? v[2] : v[3]; };
+    return make_uint4(pick(r0), pick(r1), pick(r2), pick(r3));
+  };
+  out0 = transpose(a0, b0, c0, d0);
+  out1 = transpose(a1, b1, c1, d1);
+}
+
 // The 16 key-stream bytes chacha_quad gives this lane (words 4g..4g+3 of
 // block `counter`, g = lane & 3), from the whole block computed by this lane
 // alone: the four lanes of a quad compute the same block, four times
