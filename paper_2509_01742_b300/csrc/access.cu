@@ -1843,14 +1843,30 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
           atomicOr(&s_bad, 1ull << d);
         }
       } else if (t < n_chk + n_ks) {
-        const uint32_t d = (t - n_chk) / nch, c = (t - n_chk) % nch;
-        const uint64_t q = s_dpage[d], v = m.version[q] + 1;
-        uint8_t* ks = ks_base + (size_t)d * m.page_bytes;
-        const uint4 k4 = (ONE ? chacha_lane16 : chacha_quad)(
-            m.kenc, 8 * c + (lane >> 2) + (SEALED ? 1u : 0u), (uint32_t)q, (uint32_t)v,
-            (uint32_t)(v >> 32));
-        if (512 * c + 16 * lane < m.page_bytes)
-          *reinterpret_cast<uint4*>(ks + 512 * c + 16 * lane) = k4;
+        // (this warp's next key-stream item too, when it has one: the two
+        // blocks side by side)
+        const bool two = !ONE && t + nwarps < n_chk + n_ks;
+        const uint32_t j0 = t - n_chk, j1 = two ? j0 + nwarps : j0;
+        const uint32_t d0 = j0 / nch, c0 = j0 % nch, d1 = j1 / nch, c1 = j1 % nch;
+        const uint64_t q0 = s_dpage[d0], v0 = m.version[q0] + 1;
+        const uint64_t q1 = s_dpage[d1], v1 = m.version[q1] + 1;
+        const uint32_t sc = (lane >> 2) + (SEALED ? 1u : 0u);
+        uint4 k0, k1;
+        if (two)
+          chacha_quad2(m.kenc, 8 * c0 + sc, (uint32_t)q0, (uint32_t)v0, (uint32_t)(v0 >> 32),
+                       8 * c1 + sc, (uint32_t)q1, (uint32_t)v1, (uint32_t)(v1 >> 32), k0, k1);
+        else
+          k0 = (ONE ? chacha_lane16 : chacha_quad)(m.kenc, 8 * c0 + sc, (uint32_t)q0,
+                                                    (uint32_t)v0, (uint32_t)(v0 >> 32));
+        if (512 * c0 + 16 * lane < m.page_bytes)
+          *reinterpret_cast<uint4*>(ks_base + (size_t)d0 * m.page_bytes + 512 * c0 + 16 * lane) =
+              k0;
+        if (two) {
+          if (512 * c1 + 16 * lane < m.page_bytes)
+            *reinterpret_cast<uint4*>(ks_base + (size_t)d1 * m.page_bytes + 512 * c1 +
+                                      16 * lane) = k1;
+          t += nwarps;  // (taken)
+        }
       } else {
         const uint32_t d = t - n_chk - n_ks;
         const uint64_t q = s_dpage[d];
